@@ -1,0 +1,691 @@
+/*
+ * dem_oracle.c -- plain FP64 CPU oracle of the per-timestep DEM contact pipeline of
+ * arXiv 2311.04648 (Chrono DEM-Engine).  TEST INFRASTRUCTURE ONLY; see dem_oracle.h.
+ *
+ * Deliberately slow and literal: brute-force O(N^2) contact search every step, one
+ * contact at a time in lexicographic (i, j) order, no blocking or fusion.  Build with
+ * -O2 -ffp-contract=off.
+ */
+#include "dem_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ small vectors */
+
+static double dot3(const double a[3], const double b[3]) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
+static void cross3(const double a[3], const double b[3], double out[3])
+{
+    double c0 = a[1] * b[2] - a[2] * b[1];
+    double c1 = a[2] * b[0] - a[0] * b[2];
+    double c2 = a[0] * b[1] - a[1] * b[0];
+    out[0] = c0; out[1] = c1; out[2] = c2;
+}
+
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+
+/* Rotation matrix of a unit quaternion (w, x, y, z), row-major. */
+static void quat_matrix(const double q[4], double R[9])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double xx = x * x, yy = y * y, zz = z * z;
+    double xy = x * y, xz = x * z, yz = y * z;
+    double wx = w * x, wy = w * y, wz = w * z;
+    R[0] = 1.0 - 2.0 * (yy + zz); R[1] = 2.0 * (xy - wz);       R[2] = 2.0 * (xz + wy);
+    R[3] = 2.0 * (xy + wz);       R[4] = 1.0 - 2.0 * (xx + zz); R[5] = 2.0 * (yz - wx);
+    R[6] = 2.0 * (xz - wy);       R[7] = 2.0 * (yz + wx);       R[8] = 1.0 - 2.0 * (xx + yy);
+}
+
+static void mat_vec(const double R[9], const double a[3], double out[3])
+{
+    double o0 = (R[0] * a[0] + R[1] * a[1]) + R[2] * a[2];
+    double o1 = (R[3] * a[0] + R[4] * a[1]) + R[5] * a[2];
+    double o2 = (R[6] * a[0] + R[7] * a[1]) + R[8] * a[2];
+    out[0] = o0; out[1] = o1; out[2] = o2;
+}
+
+static void mat_tvec(const double R[9], const double a[3], double out[3])
+{
+    double o0 = (R[0] * a[0] + R[3] * a[1]) + R[6] * a[2];
+    double o1 = (R[1] * a[0] + R[4] * a[1]) + R[7] * a[2];
+    double o2 = (R[2] * a[0] + R[5] * a[1]) + R[8] * a[2];
+    out[0] = o0; out[1] = o1; out[2] = o2;
+}
+
+/* Hamilton product a (x) b. */
+static void quat_mul(const double a[4], const double b[4], double out[4])
+{
+    double w = ((a[0] * b[0] - a[1] * b[1]) - a[2] * b[2]) - a[3] * b[3];
+    double x = ((a[0] * b[1] + a[1] * b[0]) + a[2] * b[3]) - a[3] * b[2];
+    double y = ((a[0] * b[2] - a[1] * b[3]) + a[2] * b[0]) + a[3] * b[1];
+    double z = ((a[0] * b[3] + a[1] * b[2]) - a[2] * b[1]) + a[3] * b[0];
+    out[0] = w; out[1] = x; out[2] = y; out[3] = z;
+}
+
+/* ------------------------------------------------------------------ materials */
+
+/* E* and G* of a contact.  The paper calls a routine for this (Sec. 4.2.1, material
+ * properties) without printing it; the reading adopted is the standard Hertz-Mindlin
+ * combination 1/E* = sum (1 - nu^2)/E and 1/G* = sum 2 (2 - nu)(1 + nu)/E. */
+void orc_effective_moduli(double E_a, double nu_a, double E_b, double nu_b, double *E_star, double *G_star)
+{
+    double ia = (1.0 - nu_a * nu_a) / E_a;
+    double ib = (1.0 - nu_b * nu_b) / E_b;
+    *E_star = 1.0 / (ia + ib);
+    double ga = 2.0 * (2.0 - nu_a) * (1.0 + nu_a) / E_a;
+    double gb = 2.0 * (2.0 - nu_b) * (1.0 + nu_b) / E_b;
+    *G_star = 1.0 / (ga + gb);
+}
+
+/* Damping ratio from the restitution coefficient, CoR clamped below at 1e-12
+ * (Sec. 4.2.1, normal force): beta = ln e / sqrt(ln^2 e + pi^2) <= 0. */
+static double damping_beta(double cor)
+{
+    double e = cor < 1e-12 ? 1e-12 : cor;
+    double le = log(e);
+    return le / sqrt(le * le + ORC_PI * ORC_PI);
+}
+
+/* ------------------------------------------------------------------ history */
+
+typedef struct {
+    int64_t n, cap;
+    int64_t *i, *j;      /* j >= 0 sphere, j < 0 wall -1-j */
+    double *ut;          /* 3 per entry */
+} orc_hist;
+
+/* Sort key of the partner: spheres first by id, then walls by wall id. */
+static int64_t partner_key(int64_t j) { return j >= 0 ? j : ((int64_t)1 << 62) + (-1 - j); }
+
+static int key_less(int64_t ia, int64_t ja, int64_t ib, int64_t jb)
+{
+    if (ia != ib) return ia < ib;
+    return partner_key(ja) < partner_key(jb);
+}
+
+void *orc_history_new(void)
+{
+    orc_hist *h = (orc_hist *)calloc(1, sizeof(orc_hist));
+    return h;
+}
+
+void orc_history_free(void *hp)
+{
+    orc_hist *h = (orc_hist *)hp;
+    if (!h) return;
+    free(h->i); free(h->j); free(h->ut); free(h);
+}
+
+int64_t orc_history_size(const void *hp) { return hp ? ((const orc_hist *)hp)->n : 0; }
+
+static int hist_reserve(orc_hist *h, int64_t n)
+{
+    if (n <= h->cap) return 0;
+    int64_t c = h->cap ? h->cap : 64;
+    while (c < n) c *= 2;
+    int64_t *ni = (int64_t *)realloc(h->i, (size_t)c * sizeof(int64_t));
+    if (!ni) return ORC_ERR_NOMEM;
+    h->i = ni;
+    int64_t *nj = (int64_t *)realloc(h->j, (size_t)c * sizeof(int64_t));
+    if (!nj) return ORC_ERR_NOMEM;
+    h->j = nj;
+    double *nu = (double *)realloc(h->ut, (size_t)c * 3 * sizeof(double));
+    if (!nu) return ORC_ERR_NOMEM;
+    h->ut = nu;
+    h->cap = c;
+    return 0;
+}
+
+/* Binary search; returns the entry index or -1. */
+static int64_t hist_find(const orc_hist *h, int64_t i, int64_t j)
+{
+    int64_t lo = 0, hi = h->n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (key_less(h->i[mid], h->j[mid], i, j)) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < h->n && h->i[lo] == i && h->j[lo] == j) return lo;
+    return -1;
+}
+
+int orc_history_set(void *hp, int64_t n, const int64_t *i, const int64_t *j, const double *ut)
+{
+    orc_hist *h = (orc_hist *)hp;
+    if (!h || n < 0) return ORC_ERR_ARG;
+    if (hist_reserve(h, n)) return ORC_ERR_NOMEM;
+    /* insertion sort into place (test inputs are small) */
+    h->n = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t pos = h->n;
+        while (pos > 0 && key_less(i[k], j[k], h->i[pos - 1], h->j[pos - 1])) {
+            h->i[pos] = h->i[pos - 1]; h->j[pos] = h->j[pos - 1];
+            memcpy(&h->ut[3 * pos], &h->ut[3 * (pos - 1)], 3 * sizeof(double));
+            --pos;
+        }
+        h->i[pos] = i[k]; h->j[pos] = j[k];
+        memcpy(&h->ut[3 * pos], &ut[3 * k], 3 * sizeof(double));
+        h->n++;
+    }
+    return 0;
+}
+
+int orc_history_get(const void *hp, int64_t cap, int64_t *n, int64_t *i, int64_t *j, double *ut)
+{
+    const orc_hist *h = (const orc_hist *)hp;
+    if (!h) return ORC_ERR_ARG;
+    *n = h->n;
+    if (h->n > cap) return ORC_ERR_CAPACITY;
+    for (int64_t k = 0; k < h->n; ++k) {
+        i[k] = h->i[k]; j[k] = h->j[k];
+        ut[3 * k] = h->ut[3 * k]; ut[3 * k + 1] = h->ut[3 * k + 1]; ut[3 * k + 2] = h->ut[3 * k + 2];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ geometry */
+
+int orc_sphere_positions(const orc_world *w, double *p)
+{
+    for (int64_t s = 0; s < w->n_sphere; ++s) {
+        int64_t o = w->owner[s];
+        double R[9], r[3];
+        quat_matrix(&w->q[4 * o], R);
+        mat_vec(R, &w->rloc[3 * s], r);
+        p[3 * s + 0] = w->x[3 * o + 0] + r[0];
+        p[3 * s + 1] = w->x[3 * o + 1] + r[1];
+        p[3 * s + 2] = w->x[3 * o + 2] + r[2];
+    }
+    return 0;
+}
+
+/* Signed gap from a sphere centre c to a wall surface (positive on the domain side)
+ * and the unit normal from the wall towards the centre.  Returns 0 if the normal is
+ * undefined (centre on a cylinder or cone axis), 1 otherwise. */
+static int wall_gap(const orc_wall *wl, const double c[3], double *gap, double nrm[3])
+{
+    const double *a = wl->p, *u = wl->n;
+    double d[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    if (wl->type == ORC_WALL_PLANE) {
+        *gap = (d[0] * u[0] + d[1] * u[1]) + d[2] * u[2];
+        nrm[0] = u[0]; nrm[1] = u[1]; nrm[2] = u[2];
+        return 1;
+    }
+    double z = (d[0] * u[0] + d[1] * u[1]) + d[2] * u[2];
+    double rp[3] = {d[0] - z * u[0], d[1] - z * u[1], d[2] - z * u[2]};
+    double rho = sqrt((rp[0] * rp[0] + rp[1] * rp[1]) + rp[2] * rp[2]);
+    if (wl->type == ORC_WALL_CYLINDER) {
+        *gap = wl->r0 - rho;
+        if (!(rho > 0.0)) return 0;
+        nrm[0] = -rp[0] / rho; nrm[1] = -rp[1] / rho; nrm[2] = -rp[2] / rho;
+        return 1;
+    }
+    /* cone segment: closest point of the generator segment in the (rho, z) half plane */
+    double dr = wl->r1 - wl->r0, dz = wl->z1 - wl->z0;
+    double len2 = dr * dr + dz * dz;
+    double t = ((rho - wl->r0) * dr + (z - wl->z0) * dz) / len2;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    double cr = wl->r0 + t * dr, cz = wl->z0 + t * dz;
+    double Dr = rho - cr, Dz = z - cz;
+    double dist = sqrt(Dr * Dr + Dz * Dz);
+    /* inward normal of the generator line: the one with a negative radial part */
+    double len = sqrt(len2);
+    double inr = -dz / len, inz = dr / len;
+    if (inr > 0.0) { inr = -inr; inz = -inz; }
+    double side = Dr * inr + Dz * inz;
+    double sgn = side >= 0.0 ? 1.0 : -1.0;
+    *gap = sgn * dist;
+    if (!(rho > 0.0) || !(dist > 0.0)) return 0;
+    double n2r = sgn * Dr / dist, n2z = sgn * Dz / dist;
+    double er[3] = {rp[0] / rho, rp[1] / rho, rp[2] / rho};
+    nrm[0] = n2r * er[0] + n2z * u[0];
+    nrm[1] = n2r * er[1] + n2z * u[1];
+    nrm[2] = n2r * er[2] + n2z * u[2];
+    return 1;
+}
+
+static int owner_is_active(const orc_world *w, int64_t o) { return w->active ? w->active[o] != 0 : 1; }
+
+int orc_listed_pairs_f64(int64_t n, const double *p, const double *rad, const int64_t *owner,
+                         const uint8_t *sphere_active, double beta, int64_t cap,
+                         int64_t *count, int64_t *pi, int64_t *pj)
+{
+    int64_t c = 0;
+    double b2 = 2.0 * beta;
+    for (int64_t i = 0; i < n; ++i) {
+        if (sphere_active && !sphere_active[i]) continue;
+        for (int64_t j = i + 1; j < n; ++j) {
+            if (sphere_active && !sphere_active[j]) continue;
+            if (owner[i] == owner[j]) continue;
+            double dx = p[3 * i + 0] - p[3 * j + 0];
+            double dy = p[3 * i + 1] - p[3 * j + 1];
+            double dz = p[3 * i + 2] - p[3 * j + 2];
+            double s = (dx * dx + dy * dy) + dz * dz;
+            double t = (rad[i] + rad[j]) + b2;
+            if (s < t * t) {
+                if (c < cap) { pi[c] = i; pj[c] = j; }
+                ++c;
+            }
+        }
+    }
+    *count = c;
+    return c > cap ? ORC_ERR_CAPACITY : 0;
+}
+
+int orc_listed_pairs_voxel_f32(int64_t n, const int32_t *cell, const float *off, float L,
+                               const float *rad, const int64_t *owner,
+                               const uint8_t *sphere_active, float beta, int64_t cap,
+                               int64_t *count, int64_t *pi, int64_t *pj)
+{
+    int64_t c = 0;
+    float b2 = 2.0f * beta;
+    for (int64_t i = 0; i < n; ++i) {
+        if (sphere_active && !sphere_active[i]) continue;
+        for (int64_t j = i + 1; j < n; ++j) {
+            if (sphere_active && !sphere_active[j]) continue;
+            if (owner[i] == owner[j]) continue;
+            float d[3];
+            for (int k = 0; k < 3; ++k) {
+                float dc = (float)(cell[3 * i + k] - cell[3 * j + k]);
+                float doff = off[3 * i + k] - off[3 * j + k];
+                float cl = dc * L;
+                d[k] = cl + doff;
+            }
+            float s = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+            float t = (rad[i] + rad[j]) + b2;
+            if (s < t * t) {
+                if (c < cap) { pi[c] = i; pj[c] = j; }
+                ++c;
+            }
+        }
+    }
+    *count = c;
+    return c > cap ? ORC_ERR_CAPACITY : 0;
+}
+
+int orc_listed_wall_pairs(const orc_world *w, const double *p, double beta, int64_t cap,
+                          int64_t *count, int64_t *si, int64_t *wi)
+{
+    int64_t c = 0;
+    for (int64_t s = 0; s < w->n_sphere; ++s) {
+        if (!owner_is_active(w, w->owner[s])) continue;
+        for (int32_t k = 0; k < w->n_wall; ++k) {
+            double gap, nrm[3];
+            wall_gap(&w->walls[k], &p[3 * s], &gap, nrm);
+            if (gap < w->rad[s] + beta) {
+                if (c < cap) { si[c] = s; wi[c] = k; }
+                ++c;
+            }
+        }
+    }
+    *count = c;
+    return c > cap ? ORC_ERR_CAPACITY : 0;
+}
+
+/* ------------------------------------------------------------------ contact force */
+
+/* Kinematic inputs of one contact: A is a sphere; B is a sphere or a wall. */
+typedef struct {
+    double n[3];       /* unit normal from B to A */
+    double delta;      /* overlap, > 0 */
+    double c[3];       /* contact point */
+    double uA[3];      /* velocity of the contact point as a point of A */
+    double uB[3];      /* ... as a point of B */
+    double Rbar, mbar;
+    double Estar, Gstar, beta, mu;
+} contact_in;
+
+/* The default history-based Hertz-Mindlin model (Sec. 4.1 Eqs. 1-4 as the listing of
+ * Sec. 4.2.1 computes them).  ut is updated in place; F is the force on A. */
+static void hertz_mindlin(const contact_in *ci, double h, double ut[3], double F[3])
+{
+    const double *n = ci->n;
+    double u[3] = {ci->uA[0] - ci->uB[0], ci->uA[1] - ci->uB[1], ci->uA[2] - ci->uB[2]};
+    double proj = dot3(u, n);
+    double vt[3] = {u[0] - proj * n[0], u[1] - proj * n[1], u[2] - proj * n[2]};
+
+    /* history update precedes the force: accumulate h*vt, then remove the normal part */
+    ut[0] = ut[0] + h * vt[0];
+    ut[1] = ut[1] + h * vt[1];
+    ut[2] = ut[2] + h * vt[2];
+    double up = dot3(ut, n);
+    ut[0] = ut[0] - up * n[0];
+    ut[1] = ut[1] - up * n[1];
+    ut[2] = ut[2] - up * n[2];
+
+    double c56 = sqrt(5.0 / 6.0);
+    double sqrtRd = sqrt(ci->delta * ci->Rbar);
+    double Sn = 2.0 * ci->Estar * sqrtRd;
+    double kn = (2.0 / 3.0) * Sn;
+    double gn = 2.0 * c56 * ci->beta * sqrt(Sn * ci->mbar);
+    double fn = kn * ci->delta + gn * proj;
+    F[0] = fn * n[0]; F[1] = fn * n[1]; F[2] = fn * n[2];
+
+    if (ci->mu > 0.0) {
+        double kt = 8.0 * ci->Gstar * sqrtRd;
+        double gt = -2.0 * c56 * ci->beta * sqrt(ci->mbar * kt);
+        double Ft[3] = {-kt * ut[0] - gt * vt[0], -kt * ut[1] - gt * vt[1], -kt * ut[2] - gt * vt[2]};
+        double ft = norm3(Ft);
+        if (ft > 1e-12) {
+            double ftmax = norm3(F) * ci->mu;
+            if (ft > ftmax) {
+                double sc = ftmax / ft;
+                Ft[0] = sc * Ft[0]; Ft[1] = sc * Ft[1]; Ft[2] = sc * Ft[2];
+                ut[0] = (Ft[0] + gt * vt[0]) / (-kt);
+                ut[1] = (Ft[1] + gt * vt[1]) / (-kt);
+                ut[2] = (Ft[2] + gt * vt[2]) / (-kt);
+            }
+        } else {
+            Ft[0] = 0.0; Ft[1] = 0.0; Ft[2] = 0.0;
+        }
+        F[0] = F[0] + Ft[0]; F[1] = F[1] + Ft[1]; F[2] = F[2] + Ft[2];
+    }
+}
+
+/* Velocity of a point `c` carried by owner o: v + (R(q) wb) x (c - x). */
+static void owner_point_velocity(const orc_world *w, int64_t o, const double c[3], double out[3])
+{
+    double R[9], wg[3], r[3], vr[3];
+    quat_matrix(&w->q[4 * o], R);
+    mat_vec(R, &w->wb[3 * o], wg);
+    r[0] = c[0] - w->x[3 * o + 0]; r[1] = c[1] - w->x[3 * o + 1]; r[2] = c[2] - w->x[3 * o + 2];
+    cross3(wg, r, vr);
+    out[0] = w->v[3 * o + 0] + vr[0];
+    out[1] = w->v[3 * o + 1] + vr[1];
+    out[2] = w->v[3 * o + 2] + vr[2];
+}
+
+/* Fill the pair-dependent material part of a contact. */
+static void contact_material(const orc_world *w, int32_t ma, int32_t mb, contact_in *ci)
+{
+    orc_effective_moduli(w->E[ma], w->nu[ma], w->E[mb], w->nu[mb], &ci->Estar, &ci->Gstar);
+    ci->beta = damping_beta(w->cor[ma * w->n_mat + mb]);
+    ci->mu = w->mu[ma * w->n_mat + mb];
+}
+
+/* Geometry of the sphere pair (A = i, B = j).  Returns 1 if delta > 0. */
+static int sphere_pair_contact(const orc_world *w, const double *p, int64_t i, int64_t j, contact_in *ci)
+{
+    double dx[3] = {p[3 * i + 0] - p[3 * j + 0], p[3 * i + 1] - p[3 * j + 1], p[3 * i + 2] - p[3 * j + 2]};
+    double d = sqrt((dx[0] * dx[0] + dx[1] * dx[1]) + dx[2] * dx[2]);
+    double RA = w->rad[i], RB = w->rad[j];
+    double delta = (RA + RB) - d;
+    if (!(delta > 0.0) || !(d > 0.0)) return 0;
+    double inv = 1.0 / d;
+    ci->n[0] = dx[0] * inv; ci->n[1] = dx[1] * inv; ci->n[2] = dx[2] * inv;
+    ci->delta = delta;
+    /* contact point: midpoint of the overlap segment along the normal */
+    double a = RA - 0.5 * delta;
+    ci->c[0] = p[3 * i + 0] - a * ci->n[0];
+    ci->c[1] = p[3 * i + 1] - a * ci->n[1];
+    ci->c[2] = p[3 * i + 2] - a * ci->n[2];
+    int64_t oa = w->owner[i], ob = w->owner[j];
+    owner_point_velocity(w, oa, ci->c, ci->uA);
+    owner_point_velocity(w, ob, ci->c, ci->uB);
+    ci->Rbar = (RA * RB) / (RA + RB);
+    ci->mbar = (w->mass[oa] * w->mass[ob]) / (w->mass[oa] + w->mass[ob]);
+    contact_material(w, w->mat[i], w->mat[j], ci);
+    return 1;
+}
+
+/* Geometry of sphere i against wall k (A = sphere, B = wall: infinite radius and mass). */
+static int sphere_wall_contact(const orc_world *w, const double *p, int64_t i, int32_t k, contact_in *ci)
+{
+    const orc_wall *wl = &w->walls[k];
+    double gap, nrm[3];
+    if (!wall_gap(wl, &p[3 * i], &gap, nrm)) return 0;
+    double RA = w->rad[i];
+    double delta = RA - gap;
+    if (!(delta > 0.0)) return 0;
+    ci->n[0] = nrm[0]; ci->n[1] = nrm[1]; ci->n[2] = nrm[2];
+    ci->delta = delta;
+    double a = RA - 0.5 * delta;
+    ci->c[0] = p[3 * i + 0] - a * nrm[0];
+    ci->c[1] = p[3 * i + 1] - a * nrm[1];
+    ci->c[2] = p[3 * i + 2] - a * nrm[2];
+    int64_t oa = w->owner[i];
+    owner_point_velocity(w, oa, ci->c, ci->uA);
+    double r[3] = {ci->c[0] - wl->p[0], ci->c[1] - wl->p[1], ci->c[2] - wl->p[2]};
+    cross3(wl->omega, r, ci->uB);
+    ci->Rbar = RA;
+    ci->mbar = w->mass[oa];
+    contact_material(w, w->mat[i], wl->mat, ci);
+    return 1;
+}
+
+/* ------------------------------------------------------------------ one evaluation */
+
+typedef struct {
+    int64_t n, cap;
+    orc_contact *c;
+} contact_buf;
+
+static int cbuf_push(contact_buf *b, const orc_contact *c)
+{
+    if (b->n == b->cap) {
+        int64_t nc = b->cap ? 2 * b->cap : 256;
+        orc_contact *nb = (orc_contact *)realloc(b->c, (size_t)nc * sizeof(orc_contact));
+        if (!nb) return ORC_ERR_NOMEM;
+        b->c = nb; b->cap = nc;
+    }
+    b->c[b->n++] = *c;
+    return 0;
+}
+
+/* Every contact with delta > 0 in (i, partner) order, each with its force and updated
+ * history; per-owner force (gravity first, then contacts) and torque sums. */
+static int evaluate(const orc_world *w, const double *p, double *F, double *T, contact_buf *out)
+{
+    const orc_hist *h = (const orc_hist *)w->hist;
+    int64_t M = w->n_owner, N = w->n_sphere;
+    for (int64_t o = 0; o < M; ++o) {
+        double m = w->mass[o];
+        int act = owner_is_active(w, o);
+        F[3 * o + 0] = act ? m * w->g[0] : 0.0;
+        F[3 * o + 1] = act ? m * w->g[1] : 0.0;
+        F[3 * o + 2] = act ? m * w->g[2] : 0.0;
+        T[3 * o + 0] = 0.0; T[3 * o + 1] = 0.0; T[3 * o + 2] = 0.0;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t oa = w->owner[i];
+        if (!owner_is_active(w, oa)) continue;
+        /* sphere partners j > i first, then walls in ascending id */
+        for (int64_t jj = i + 1; jj < N + w->n_wall; ++jj) {
+            contact_in ci;
+            int64_t j, ob = -1;
+            if (jj < N) {
+                j = jj;
+                ob = w->owner[j];
+                if (ob == oa || !owner_is_active(w, ob)) continue;
+                if (!sphere_pair_contact(w, p, i, j, &ci)) continue;
+            } else {
+                int32_t k = (int32_t)(jj - N);
+                j = -1 - (int64_t)k;
+                if (!sphere_wall_contact(w, p, i, k, &ci)) continue;
+            }
+            orc_contact rec;
+            memset(&rec, 0, sizeof(rec));
+            rec.i = i; rec.j = j;
+            int64_t hk = h ? hist_find(h, i, j) : -1;
+            if (hk >= 0) { rec.ut[0] = h->ut[3 * hk]; rec.ut[1] = h->ut[3 * hk + 1]; rec.ut[2] = h->ut[3 * hk + 2]; }
+            hertz_mindlin(&ci, w->h, rec.ut, rec.force);
+            memcpy(rec.point, ci.c, sizeof(ci.c));
+            memcpy(rec.normal, ci.n, sizeof(ci.n));
+            rec.overlap = ci.delta;
+            /* reduction onto the owners: F on A, -F on B; torques about the centres of mass */
+            double rA[3] = {ci.c[0] - w->x[3 * oa], ci.c[1] - w->x[3 * oa + 1], ci.c[2] - w->x[3 * oa + 2]};
+            double tA[3];
+            cross3(rA, rec.force, tA);
+            for (int k = 0; k < 3; ++k) { F[3 * oa + k] += rec.force[k]; T[3 * oa + k] += tA[k]; }
+            if (ob >= 0) {
+                double rB[3] = {ci.c[0] - w->x[3 * ob], ci.c[1] - w->x[3 * ob + 1], ci.c[2] - w->x[3 * ob + 2]};
+                double mf[3] = {-rec.force[0], -rec.force[1], -rec.force[2]};
+                double tB[3];
+                cross3(rB, mf, tB);
+                for (int k = 0; k < 3; ++k) { F[3 * ob + k] += mf[k]; T[3 * ob + k] += tB[k]; }
+            }
+            if (out) { int e = cbuf_push(out, &rec); if (e) return e; }
+        }
+    }
+    return 0;
+}
+
+int orc_eval(const orc_world *w, double *F, double *T, int64_t cap, int64_t *count, orc_contact *contacts)
+{
+    double *p = (double *)malloc((size_t)(w->n_sphere > 0 ? w->n_sphere : 1) * 3 * sizeof(double));
+    if (!p) return ORC_ERR_NOMEM;
+    orc_sphere_positions(w, p);
+    contact_buf buf = {0, 0, NULL};
+    int e = evaluate(w, p, F, T, &buf);
+    free(p);
+    if (e) { free(buf.c); return e; }
+    if (count) *count = buf.n;
+    if (contacts) {
+        int64_t nc = buf.n < cap ? buf.n : cap;
+        memcpy(contacts, buf.c, (size_t)nc * sizeof(orc_contact));
+    }
+    free(buf.c);
+    if (contacts && buf.n > cap) return ORC_ERR_CAPACITY;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ integration */
+
+/* Semi-implicit Euler (reading adopted for the unstated scheme): v, then wb with the
+ * body-frame Euler equations, then x with the new v, then q with the new wb. */
+static void integrate_owner(orc_world *w, int64_t o, const double Fo[3], const double To[3])
+{
+    double h = w->h, m = w->mass[o];
+    double *v = &w->v[3 * o], *x = &w->x[3 * o], *wb = &w->wb[3 * o], *q = &w->q[4 * o];
+    const double *I = &w->moi[3 * o];
+    for (int k = 0; k < 3; ++k) {
+        double a = Fo[k] / m;
+        v[k] = v[k] + h * a;
+    }
+    double R[9], Tb[3];
+    quat_matrix(q, R);
+    mat_tvec(R, To, Tb);
+    double Iw[3] = {I[0] * wb[0], I[1] * wb[1], I[2] * wb[2]};
+    double gyro[3] = {0.0, 0.0, 0.0};
+    if (w->gyroscopic) cross3(wb, Iw, gyro);
+    for (int k = 0; k < 3; ++k) {
+        double dw = (Tb[k] - gyro[k]) / I[k];
+        wb[k] = wb[k] + h * dw;
+    }
+    for (int k = 0; k < 3; ++k) x[k] = x[k] + h * v[k];
+    double wn = norm3(wb);
+    if (wn >= 1e-30) {
+        double half = 0.5 * h * wn;
+        double s = sin(half) / wn;
+        double dq[4] = {cos(half), s * wb[0], s * wb[1], s * wb[2]};
+        double nq[4];
+        quat_mul(q, dq, nq);
+        double qn = sqrt(((nq[0] * nq[0] + nq[1] * nq[1]) + nq[2] * nq[2]) + nq[3] * nq[3]);
+        q[0] = nq[0] / qn; q[1] = nq[1] / qn; q[2] = nq[2] / qn; q[3] = nq[3] / qn;
+    }
+}
+
+static int replace_history(orc_world *w, const contact_buf *b)
+{
+    orc_hist *h = (orc_hist *)w->hist;
+    if (!h) return 0;
+    if (hist_reserve(h, b->n)) return ORC_ERR_NOMEM;
+    for (int64_t k = 0; k < b->n; ++k) {
+        h->i[k] = b->c[k].i; h->j[k] = b->c[k].j;
+        h->ut[3 * k] = b->c[k].ut[0]; h->ut[3 * k + 1] = b->c[k].ut[1]; h->ut[3 * k + 2] = b->c[k].ut[2];
+    }
+    h->n = b->n;
+    return 0;
+}
+
+int orc_step(orc_world *w, int64_t nsteps)
+{
+    int64_t M = w->n_owner, N = w->n_sphere;
+    double *p = (double *)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(double));
+    double *F = (double *)malloc((size_t)(M > 0 ? M : 1) * 3 * sizeof(double));
+    double *T = (double *)malloc((size_t)(M > 0 ? M : 1) * 3 * sizeof(double));
+    contact_buf buf = {0, 0, NULL};
+    int err = 0;
+    if (!p || !F || !T) { err = ORC_ERR_NOMEM; goto done; }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        orc_sphere_positions(w, p);
+        buf.n = 0;
+        err = evaluate(w, p, F, T, &buf);
+        if (err) goto done;
+        err = replace_history(w, &buf);
+        if (err) goto done;
+        for (int64_t o = 0; o < M; ++o)
+            if (owner_is_active(w, o)) integrate_owner(w, o, &F[3 * o], &T[3 * o]);
+        if (w->has_sink && w->active) {
+            for (int64_t o = 0; o < M; ++o) {
+                if (!w->active[o]) continue;
+                double d[3] = {w->x[3 * o] - w->sink_p[0], w->x[3 * o + 1] - w->sink_p[1], w->x[3 * o + 2] - w->sink_p[2]};
+                if (dot3(d, w->sink_n) < 0.0) {
+                    w->active[o] = 0;
+                    w->v[3 * o] = w->v[3 * o + 1] = w->v[3 * o + 2] = 0.0;
+                    w->wb[3 * o] = w->wb[3 * o + 1] = w->wb[3 * o + 2] = 0.0;
+                }
+            }
+        }
+        if (w->v_err > 0.0) {
+            for (int64_t o = 0; o < M; ++o) {
+                double sp = norm3(&w->v[3 * o]);
+                if (!(sp <= w->v_err)) { err = ORC_ERR_DIVERGED; goto done; }
+            }
+        }
+    }
+done:
+    free(p); free(F); free(T); free(buf.c);
+    return err;
+}
+
+/* ------------------------------------------------------------------ diagnostics */
+
+int orc_diagnostics(const orc_world *w, double *ke, double *pe, double *elastic, double *mom, double *angmom)
+{
+    int64_t M = w->n_owner, N = w->n_sphere;
+    double k = 0.0, u = 0.0, el = 0.0;
+    double P[3] = {0.0, 0.0, 0.0}, L[3] = {0.0, 0.0, 0.0};
+    for (int64_t o = 0; o < M; ++o) {
+        const double *v = &w->v[3 * o], *x = &w->x[3 * o], *wb = &w->wb[3 * o], *I = &w->moi[3 * o];
+        double m = w->mass[o];
+        k += 0.5 * m * dot3(v, v);
+        k += 0.5 * ((I[0] * wb[0] * wb[0] + I[1] * wb[1] * wb[1]) + I[2] * wb[2] * wb[2]);
+        u -= m * dot3(w->g, x);
+        double mv[3] = {m * v[0], m * v[1], m * v[2]};
+        P[0] += mv[0]; P[1] += mv[1]; P[2] += mv[2];
+        double orb[3], R[9], Iw[3] = {I[0] * wb[0], I[1] * wb[1], I[2] * wb[2]}, spin[3];
+        cross3(x, mv, orb);
+        quat_matrix(&w->q[4 * o], R);
+        mat_vec(R, Iw, spin);
+        L[0] += orb[0] + spin[0]; L[1] += orb[1] + spin[1]; L[2] += orb[2] + spin[2];
+    }
+    double *p = (double *)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(double));
+    if (!p) return ORC_ERR_NOMEM;
+    orc_sphere_positions(w, p);
+    for (int64_t i = 0; i < N; ++i) {
+        if (!owner_is_active(w, w->owner[i])) continue;
+        for (int64_t jj = i + 1; jj < N + w->n_wall; ++jj) {
+            contact_in ci;
+            if (jj < N) {
+                if (w->owner[jj] == w->owner[i] || !owner_is_active(w, w->owner[jj])) continue;
+                if (!sphere_pair_contact(w, p, i, jj, &ci)) continue;
+            } else {
+                if (!sphere_wall_contact(w, p, i, (int32_t)(jj - N), &ci)) continue;
+            }
+            el += (8.0 / 15.0) * ci.Estar * sqrt(ci.Rbar) * ci.delta * ci.delta * sqrt(ci.delta);
+        }
+    }
+    free(p);
+    if (ke) *ke = k;
+    if (pe) *pe = u;
+    if (elastic) *elastic = el;
+    if (mom) { mom[0] = P[0]; mom[1] = P[1]; mom[2] = P[2]; }
+    if (angmom) { angmom[0] = L[0]; angmom[1] = L[1]; angmom[2] = L[2]; }
+    return 0;
+}

@@ -1,0 +1,411 @@
+"""Seeded synthetic scenes shaped like the paper's workloads.
+
+This module holds scene *descriptions* only (geometry, materials, initial state drawn
+from seeded generators); it contains none of the DEM method's arithmetic.  It is the one
+module that both the CUDA library's tests/benchmarks and the CPU oracle's tests consume.
+
+Scenes (SI units throughout):
+  - ``settle_box``      : N monodisperse spheres placed by random sequential addition
+                          without overlap in a walled box (2,000 spheres, R = 1 mm,
+                          40 x 40 x 80 mm box, dt = 1e-6 s).
+  - ``settling_column`` : polydisperse spheres (R ~ U[0.8, 1.2] mm) on a jittered cubic
+                          lattice in a 0.3 x 0.3 x 1.2 m walled box, small random initial
+                          velocities, dt = 2e-6 s; ``column_width`` restricts the same
+                          generator to a central column (the 20k-sphere sub-box).
+  - ``clump_drum``      : 3-sphere rods and 4-sphere tetrahedra (component R ~ U[1, 2] mm)
+                          in a drum of radius 0.6 m spinning at 1 rad/s about x.
+  - ``cone_hopper``     : polydisperse spheres (R ~ U[1, 2] mm) above a 30-degree conical
+                          hopper with a sink below the orifice.
+  - ``column_collapse`` : one granular column of a batch of independent scenes.
+Material: rho = 2600 kg/m^3, E = 1e7 Pa, nu = 0.3 unless stated.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+RHO = 2600.0
+PLANE, CYLINDER, CONE = 0, 1, 2
+
+
+@dataclass
+class Template:
+    rel_xyz: np.ndarray          # (n, 3) component centres about the centre of mass, principal frame
+    radii: np.ndarray            # (n,)
+    mats: np.ndarray             # (n,) material ids
+    mass: float
+    moi: np.ndarray              # (3,) principal moments
+
+
+@dataclass
+class Scene:
+    box_lo: np.ndarray
+    box_hi: np.ndarray
+    E: np.ndarray
+    nu: np.ndarray
+    cor: np.ndarray              # (nm, nm)
+    mu: np.ndarray               # (nm, nm)
+    walls: list
+    templates: list
+    owner_template: np.ndarray   # (M,)
+    owner_scale: np.ndarray | None
+    x: np.ndarray                # (M, 3)
+    q: np.ndarray                # (M, 4) (w, x, y, z)
+    v: np.ndarray                # (M, 3)
+    wb: np.ndarray               # (M, 3) body-frame angular velocity
+    h: float
+    g: np.ndarray
+    gyroscopic: bool = True
+    sink: tuple | None = None
+    v_err: float = 0.0
+    r_max: float = 0.0
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_owner(self):
+        return len(self.owner_template)
+
+    @property
+    def n_sphere(self):
+        counts = np.array([len(t.radii) for t in self.templates], np.int64)
+        return int(counts[np.asarray(self.owner_template, np.int64)].sum())
+
+
+def sphere_template(R: float, mat: int = 0, rho: float = RHO) -> Template:
+    m = rho * 4.0 / 3.0 * math.pi * R ** 3
+    I = 0.4 * m * R * R
+    return Template(np.zeros((1, 3)), np.array([R]), np.array([mat], np.int32), m, np.array([I, I, I]))
+
+
+def rod_template(R: float, mat: int = 0, rho: float = RHO) -> Template:
+    """Three tangent collinear spheres along x (spacing 2R)."""
+    m1 = rho * 4.0 / 3.0 * math.pi * R ** 3
+    i1 = 0.4 * m1 * R * R
+    xs = np.array([[-2 * R, 0, 0], [0, 0, 0], [2 * R, 0, 0]], np.float64)
+    Ixx = 3 * i1
+    Iyy = 3 * i1 + 2 * m1 * (2 * R) ** 2
+    return Template(xs, np.full(3, R), np.full(3, mat, np.int32), 3 * m1, np.array([Ixx, Iyy, Iyy]))
+
+
+def tetra_template(R: float, mat: int = 0, rho: float = RHO) -> Template:
+    """Four tangent spheres on the vertices of a regular tetrahedron of edge 2R."""
+    m1 = rho * 4.0 / 3.0 * math.pi * R ** 3
+    i1 = 0.4 * m1 * R * R
+    a = 2 * R / (2 * math.sqrt(2))   # vertices (+-a,+-a,+-a) with an even number of minus signs
+    xs = np.array([[a, a, a], [a, -a, -a], [-a, a, -a], [-a, -a, a]], np.float64)
+    d2 = 2 * a * a                   # squared distance of each vertex from any coordinate axis
+    I = 4 * i1 + 4 * m1 * d2
+    return Template(xs, np.full(4, R), np.full(4, mat, np.int32), 4 * m1, np.array([I, I, I]))
+
+
+def _single_material(E, nu, e, mu):
+    return (np.array([E], np.float64), np.array([nu], np.float64),
+            np.array([[e]], np.float64), np.array([[mu]], np.float64))
+
+
+def box_walls(lo, hi, mat=0):
+    walls = []
+    for a in range(3):
+        n = np.zeros(3); n[a] = 1.0
+        walls.append(dict(type=PLANE, mat=mat, p=np.array(lo, np.float64), n=n.copy()))
+        walls.append(dict(type=PLANE, mat=mat, p=np.array(hi, np.float64), n=-n))
+    return walls
+
+
+def _identity_quats(M):
+    q = np.zeros((M, 4))
+    q[:, 0] = 1.0
+    return q
+
+
+def _random_quats(rng, M):
+    q = rng.normal(size=(M, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q[q[:, 0] < 0] *= -1.0
+    return q
+
+
+def settle_box(n=2000, R=1e-3, box=(0.04, 0.04, 0.08), E=1e7, nu=0.3, e=0.5, mu=0.4,
+               seed=1, vel_sigma=0.0, h=1e-6, gap=1e-5, g=(0.0, 0.0, -9.81), walls=True) -> Scene:
+    """Random sequential addition of monodisperse spheres without overlap (reject if the
+    centre distance is below 2R + gap), optionally with N(0, vel_sigma^2) velocities."""
+    rng = np.random.default_rng(seed)
+    lo = np.zeros(3)
+    hi = np.array(box, np.float64)
+    pts = np.empty((n, 3))
+    cell = 2 * R + gap
+    grid = {}
+    k = 0
+    tries = 0
+    while k < n:
+        tries += 1
+        if tries > 200 * n:
+            raise RuntimeError("random sequential addition did not converge")
+        c = lo + R + gap + rng.random(3) * (hi - lo - 2 * (R + gap))
+        key = tuple((c // cell).astype(int))
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for m in grid.get((key[0] + dx, key[1] + dy, key[2] + dz), ()):
+                        if np.sum((pts[m] - c) ** 2) < (2 * R + gap) ** 2:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            pts[k] = c
+            grid.setdefault(key, []).append(k)
+            k += 1
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    v = rng.normal(scale=vel_sigma, size=(n, 3)) if vel_sigma > 0 else np.zeros((n, 3))
+    return Scene(lo, hi, Em, num, corm, mum, box_walls(lo, hi) if walls else [], [sphere_template(R)],
+                 np.zeros(n, np.int64), None, pts, _identity_quats(n), v, np.zeros((n, 3)), h,
+                 np.array(g, np.float64), r_max=R, name=f"settle_box_n{n}_seed{seed}")
+
+
+def settling_column(n=4_000_000, box=(0.3, 0.3, 1.2), r_lo=0.8e-3, r_hi=1.2e-3, spacing=2.45e-3,
+                    jitter=0.02e-3, vel_sigma=0.05, seed=3, E=1e7, nu=0.3, e=0.5, mu=0.4, h=2e-6,
+                    column_width=None) -> Scene:
+    """Jittered cubic lattice filled layer by layer from z = r_hi upward; R ~ U[r_lo, r_hi].
+    With ``column_width`` the lattice is restricted to a central square column of that
+    width (same generator, fewer sites per layer), the box shrunk to it."""
+    rng = np.random.default_rng(seed)
+    lo = np.zeros(3)
+    hi = np.array(box, np.float64)
+    if column_width is not None:
+        cx = 0.5 * (lo[0] + hi[0])
+        cy = 0.5 * (lo[1] + hi[1])
+        lo = np.array([cx - column_width / 2, cy - column_width / 2, 0.0])
+        hi = np.array([cx + column_width / 2, cy + column_width / 2, box[2]])
+    nx = int(math.floor((hi[0] - lo[0] - 2 * r_hi) / spacing)) + 1
+    ny = int(math.floor((hi[1] - lo[1] - 2 * r_hi) / spacing)) + 1
+    per_layer = nx * ny
+    layers = int(math.ceil(n / per_layer))
+    zmax = r_hi + (layers - 1) * spacing
+    if zmax + r_hi > hi[2]:
+        raise ValueError("column does not fit the box")
+    ii = np.arange(n)
+    lz = ii // per_layer
+    rem = ii % per_layer
+    ly = rem // nx
+    lx = rem % nx
+    x0 = lo[0] + r_hi + 0.5 * (hi[0] - lo[0] - 2 * r_hi - (nx - 1) * spacing)
+    y0 = lo[1] + r_hi + 0.5 * (hi[1] - lo[1] - 2 * r_hi - (ny - 1) * spacing)
+    pts = np.stack([x0 + lx * spacing, y0 + ly * spacing, lo[2] + r_hi + lz * spacing], axis=1)
+    pts += rng.uniform(-jitter, jitter, size=(n, 3))
+    R = rng.uniform(r_lo, r_hi, size=n)
+    v = rng.normal(scale=vel_sigma, size=(n, 3))
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    tpl = sphere_template(1e-3)
+    return Scene(lo, hi, Em, num, corm, mum, box_walls(lo, hi), [tpl], np.zeros(n, np.int64), R / 1e-3,
+                 pts, _identity_quats(n), v, np.zeros((n, 3)), h, np.array([0.0, 0.0, -9.81]),
+                 r_max=r_hi, name=f"settling_column_n{n}", meta=dict(nx=nx, ny=ny, layers=layers))
+
+
+def clump_drum(n_clumps=20_000_000, drum_radius=0.6, omega=1.0, r_lo=1e-3, r_hi=2e-3, mu=0.5, e=0.5,
+               E=1e7, nu=0.3, fill=0.40, solid_fraction=0.55, seed=4, h=2e-6, length=None) -> Scene:
+    """Half 3-sphere rods, half 4-sphere tetrahedra, component R ~ U[r_lo, r_hi] per clump,
+    in a drum about the x axis.  The drum length L is chosen so that the clumps at the
+    stated solid fraction fill ``fill`` of the drum volume; placement is a lattice in
+    the lower half of the drum with random orientations."""
+    rng = np.random.default_rng(seed)
+    kinds = rng.random(n_clumps) < 0.5           # True: rod, False: tetra
+    Rc = rng.uniform(r_lo, r_hi, size=n_clumps)
+    vol = np.where(kinds, 3.0, 4.0) * (4.0 / 3.0) * math.pi * Rc ** 3
+    if length is None:
+        length = float(vol.sum() / solid_fraction / (fill * math.pi * drum_radius ** 2))
+    spacing = 6.2 * r_hi             # a rod spans 6R: lattice pitch above the largest clump extent
+    # lattice sites inside the lower half disc (y, z) times x
+    ys = np.arange(-drum_radius + spacing, drum_radius - spacing, spacing)
+    zs = np.arange(-drum_radius + spacing, 0.0, spacing)
+    Y, Z = np.meshgrid(ys, zs, indexing="ij")
+    ok = (Y ** 2 + Z ** 2) < (drum_radius - spacing) ** 2
+    yz = np.stack([Y[ok], Z[ok]], axis=1)
+    xs = np.arange(-length / 2 + spacing / 2, length / 2 - spacing / 2 + 1e-12, spacing)
+    nsite = len(xs) * len(yz)
+    if nsite < n_clumps:
+        # stack further up into the upper half if the lower half is full
+        zs2 = np.arange(-drum_radius + spacing, drum_radius - spacing, spacing)
+        Y, Z = np.meshgrid(ys, zs2, indexing="ij")
+        ok = (Y ** 2 + Z ** 2) < (drum_radius - spacing) ** 2
+        yz = np.stack([Y[ok], Z[ok]], axis=1)
+        order = np.argsort(yz[:, 1], kind="stable")
+        yz = yz[order]
+        nsite = len(xs) * len(yz)
+        if nsite < n_clumps:
+            raise ValueError("drum too short for the requested clumps")
+    # fill from the bottom: sites ordered by z then y then x
+    order = np.lexsort((yz[:, 0], yz[:, 1]))
+    yz = yz[order]
+    site = np.arange(n_clumps)
+    iyz = site // len(xs)
+    ix = site % len(xs)
+    pts = np.stack([xs[ix], yz[iyz, 0], yz[iyz, 1]], axis=1)
+    q = _random_quats(rng, n_clumps)
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    templates = [rod_template(1e-3), tetra_template(1e-3)]
+    owner_t = np.where(kinds, 0, 1).astype(np.int64)
+    axis = np.array([1.0, 0.0, 0.0])
+    walls = [dict(type=CYLINDER, mat=0, p=np.zeros(3), n=axis, r0=drum_radius, omega=omega * axis),
+             dict(type=PLANE, mat=0, p=np.array([-length / 2, 0, 0]), n=axis.copy(), omega=omega * axis),
+             dict(type=PLANE, mat=0, p=np.array([length / 2, 0, 0]), n=-axis, omega=omega * axis)]
+    lo = np.array([-length / 2, -drum_radius, -drum_radius])
+    hi = np.array([length / 2, drum_radius, drum_radius])
+    return Scene(lo, hi, Em, num, corm, mum, walls, templates, owner_t, Rc / 1e-3, pts, q,
+                 np.zeros((n_clumps, 3)), np.zeros((n_clumps, 3)), h, np.array([0.0, 0.0, -9.81]),
+                 r_max=r_hi, name=f"clump_drum_n{n_clumps}", meta=dict(length=length))
+
+
+def cone_hopper(n=10_000_000, r_lo=1e-3, r_hi=2e-3, half_angle_deg=30.0, e=0.5, mu=0.4, E=1e7, nu=0.3,
+                seed=6, h=2e-6, vel_sigma=0.0) -> Scene:
+    """Polydisperse spheres on a lattice inside a conical hopper (wall 30 degrees from the
+    vertical, orifice radius 10 R_max) with a sink plane below the orifice."""
+    rng = np.random.default_rng(seed)
+    spacing = 2 * r_hi * 1.05
+    r_orifice = 10 * r_hi
+    tan = math.tan(math.radians(half_angle_deg))
+    # choose the fill height so that the cone frustum holds n sites at lattice density
+    z = 0.0
+    count = 0
+    site_z = []
+    while count < n:
+        rz = r_orifice + (z + spacing) * tan - spacing
+        m = int(math.floor(2 * rz / spacing))
+        layer = m * m if m > 0 else 0
+        # sites inside the disc of radius rz
+        if m > 0:
+            c = (np.arange(m) - (m - 1) / 2) * spacing
+            X, Y = np.meshgrid(c, c, indexing="ij")
+            inside = int(np.count_nonzero(X ** 2 + Y ** 2 < rz ** 2))
+        else:
+            inside = 0
+        site_z.append((z, rz, inside))
+        count += inside
+        z += spacing
+    pts = []
+    need = n
+    for (zl, rz, inside) in site_z:
+        m = int(math.floor(2 * rz / spacing))
+        c = (np.arange(m) - (m - 1) / 2) * spacing
+        X, Y = np.meshgrid(c, c, indexing="ij")
+        sel = X ** 2 + Y ** 2 < rz ** 2
+        layer = np.stack([X[sel], Y[sel], np.full(int(sel.sum()), zl + spacing)], axis=1)
+        take = min(need, len(layer))
+        pts.append(layer[:take])
+        need -= take
+        if need == 0:
+            break
+    pts = np.concatenate(pts, axis=0)
+    z_top = float(pts[:, 2].max()) + 4 * r_hi
+    R = rng.uniform(r_lo, r_hi, size=n)
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    axis = np.array([0.0, 0.0, 1.0])
+    r_top = r_orifice + z_top * tan
+    walls = [dict(type=CONE, mat=0, p=np.zeros(3), n=axis, r0=r_orifice, z0=0.0, r1=r_top, z1=z_top)]
+    lo = np.array([-r_top, -r_top, -0.05])
+    hi = np.array([r_top, r_top, z_top])
+    v = rng.normal(scale=vel_sigma, size=(n, 3)) if vel_sigma > 0 else np.zeros((n, 3))
+    return Scene(lo, hi, Em, num, corm, mum, walls, [sphere_template(1e-3)], np.zeros(n, np.int64), R / 1e-3,
+                 pts, _identity_quats(n), v, np.zeros((n, 3)), h, np.array([0.0, 0.0, -9.81]),
+                 sink=(np.array([0.0, 0.0, -0.02]), axis.copy()), r_max=r_hi, name=f"cone_hopper_n{n}",
+                 meta=dict(r_orifice=r_orifice, z_top=z_top))
+
+
+def column_collapse(n, aspect, mu, e, seed, r_lo=0.9e-3, r_hi=1.1e-3, E=1e7, nu=0.3, h=2e-6,
+                    solid_fraction=0.55) -> Scene:
+    """A granular column of N spheres with aspect ratio a = height/width, depth 10 R_max,
+    on a floor with a flume of length (a + 3) w; the confining wall is absent from t = 0."""
+    rng = np.random.default_rng(seed)
+    vbar = (4.0 / 3.0) * math.pi * ((r_lo + r_hi) / 2) ** 3
+    D = 10 * r_hi
+    w = math.sqrt(n * vbar / (solid_fraction * aspect * D))
+    H = aspect * w
+    spacing = 2 * r_hi * 1.02
+    nx = max(1, int(math.floor((w - 2 * r_hi) / spacing)) + 1)
+    ny = max(1, int(math.floor((D - 2 * r_hi) / spacing)) + 1)
+    per = nx * ny
+    ii = np.arange(n)
+    lz = ii // per
+    rem = ii % per
+    ly = rem // nx
+    lx = rem % nx
+    pts = np.stack([r_hi + lx * spacing, r_hi + ly * spacing, r_hi + lz * spacing], axis=1)
+    pts += rng.uniform(-0.01 * r_hi, 0.01 * r_hi, size=(n, 3))
+    R = rng.uniform(r_lo, r_hi, size=n)
+    L = (aspect + 3) * w
+    top = max(H, float(pts[:, 2].max()) + r_hi) * 1.5
+    lo = np.zeros(3)
+    hi = np.array([max(L, float(pts[:, 0].max()) + 2 * r_hi), D, top])
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    walls = [dict(type=PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0])),
+             dict(type=PLANE, mat=0, p=np.zeros(3), n=np.array([1.0, 0.0, 0.0])),
+             dict(type=PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 1.0, 0.0])),
+             dict(type=PLANE, mat=0, p=np.array([0.0, D, 0.0]), n=np.array([0.0, -1.0, 0.0])),
+             dict(type=PLANE, mat=0, p=np.array([hi[0], 0.0, 0.0]), n=np.array([-1.0, 0.0, 0.0]))]
+    return Scene(lo, hi, Em, num, corm, mum, walls, [sphere_template(1e-3)], np.zeros(n, np.int64), R / 1e-3,
+                 pts, _identity_quats(n), np.zeros((n, 3)), np.zeros((n, 3)), h, np.array([0.0, 0.0, -9.81]),
+                 r_max=r_hi, name=f"column_collapse_n{n}", meta=dict(aspect=aspect, width=w))
+
+
+def batch_scenes(n_scenes=512, n_lo=1000, n_hi=50_000, seed=5):
+    """Independent column collapses: N log-uniform in [n_lo, n_hi], mu ~ U[0.2, 0.8],
+    e ~ U[0.3, 0.9], aspect ~ U[0.5, 4]."""
+    rng = np.random.default_rng(seed)
+    Ns = np.round(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=n_scenes))).astype(int)
+    mus = rng.uniform(0.2, 0.8, size=n_scenes)
+    es = rng.uniform(0.3, 0.9, size=n_scenes)
+    aspects = rng.uniform(0.5, 4.0, size=n_scenes)
+    return [column_collapse(int(Ns[k]), float(aspects[k]), float(mus[k]), float(es[k]), seed=1000 + k)
+            for k in range(n_scenes)]
+
+
+def two_spheres(R=1e-3, v0=1.0, E=1e7, nu=0.3, e=1.0, mu=0.0, h=1e-7, gap=1e-6, rho=RHO) -> Scene:
+    """Head-on pair along x closing at speed v0, no gravity, no walls."""
+    m = rho * 4.0 / 3.0 * math.pi * R ** 3
+    x = np.array([[-(R + gap / 2), 0.0, 0.0], [R + gap / 2, 0.0, 0.0]])
+    v = np.array([[v0 / 2, 0.0, 0.0], [-v0 / 2, 0.0, 0.0]])
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    return Scene(np.array([-1.0, -1.0, -1.0]), np.array([1.0, 1.0, 1.0]), Em, num, corm, mum, [],
+                 [sphere_template(R, rho=rho)], np.zeros(2, np.int64), None, x, _identity_quats(2), v,
+                 np.zeros((2, 3)), h, np.zeros(3), r_max=R, name="two_spheres", meta=dict(mass=m))
+
+
+def free_spheres(n=200, R=1e-3, box=0.03, vel_sigma=0.5, E=1e7, nu=0.3, e=0.7, mu=0.3, seed=7, h=1e-6) -> Scene:
+    """Spheres with random velocities, no walls, no gravity (momentum tests)."""
+    s = settle_box(n=n, R=R, box=(box, box, box), E=E, nu=nu, e=e, mu=mu, seed=seed, vel_sigma=vel_sigma,
+                   h=h, g=(0.0, 0.0, 0.0), walls=False)
+    rng = np.random.default_rng(seed + 100)
+    s.wb = rng.normal(scale=vel_sigma / R, size=(n, 3))
+    s.name = f"free_spheres_n{n}"
+    return s
+
+
+def free_clumps(n=60, R=1e-3, box=0.03, vel_sigma=0.5, E=1e7, nu=0.3, e=0.7, mu=0.3, seed=8, h=1e-6,
+                g=(0.0, 0.0, 0.0), walls=False) -> Scene:
+    """Rods and tetrahedra with random poses and velocities (on a coarse lattice)."""
+    rng = np.random.default_rng(seed)
+    sp = 7.0 * R
+    m = int(math.floor(box / sp))
+    sites = np.stack(np.meshgrid(*[np.arange(m)] * 3, indexing="ij"), axis=-1).reshape(-1, 3)
+    if len(sites) < n:
+        raise ValueError("box too small")
+    sel = rng.permutation(len(sites))[:n]
+    x = (sites[sel] + 0.5) * sp
+    kinds = (np.arange(n) % 2).astype(np.int64)
+    q = _random_quats(rng, n)
+    v = rng.normal(scale=vel_sigma, size=(n, 3))
+    wb = rng.normal(scale=vel_sigma / R, size=(n, 3))
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    lo = np.zeros(3)
+    hi = np.full(3, box)
+    return Scene(lo, hi, Em, num, corm, mum, box_walls(lo, hi) if walls else [],
+                 [rod_template(R), tetra_template(R)], kinds, None, x, q, v, wb, h, np.array(g, np.float64),
+                 r_max=R, name=f"free_clumps_n{n}")

@@ -1,0 +1,565 @@
+"""Pins of the FP64 CPU oracle to what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks a closed form, an
+invariant, a special case or a brute-force enumeration that a plausible mistake in the
+oracle (dropped term, wrong sign or index, transposed operand) would break.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_04648_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def one_material(E=1e7, nu=0.3, e=0.5, mu=0.4):
+    return (np.array([E]), np.array([nu]), np.array([[e]]), np.array([[mu]]))
+
+
+def make_scene(x, v=None, wb=None, q=None, templates=None, owner_t=None, scale=None, walls=(), g=(0, 0, 0),
+               h=1e-6, mat=one_material(), **kw):
+    x = np.asarray(x, np.float64).reshape(-1, 3)
+    M = len(x)
+    if templates is None:
+        templates = [W.sphere_template(1e-3)]
+    if owner_t is None:
+        owner_t = np.zeros(M, np.int64)
+    if q is None:
+        q = np.zeros((M, 4)); q[:, 0] = 1
+    v = np.zeros((M, 3)) if v is None else np.asarray(v, np.float64).reshape(M, 3)
+    wb = np.zeros((M, 3)) if wb is None else np.asarray(wb, np.float64).reshape(M, 3)
+    E, nu, cor, mu = mat
+    return W.Scene(np.full(3, -1.0), np.full(3, 1.0), E, nu, cor, mu, list(walls), templates,
+                   np.asarray(owner_t, np.int64), scale, x, np.asarray(q, np.float64), v, wb, h,
+                   np.asarray(g, np.float64), **kw)
+
+
+# ----------------------------------------------------------------------------- pairs
+
+def numpy_pairs(p, rad, owner, beta):
+    n = len(rad)
+    out = []
+    for i in range(n):
+        d = p[i] - p[i + 1:]
+        s = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        t = (rad[i] + rad[i + 1:]) + 2.0 * beta
+        hit = (s < t * t) & (owner[i + 1:] != owner[i])
+        for j in np.nonzero(hit)[0]:
+            out.append((i, i + 1 + j))
+    return out
+
+
+def test_listed_pairs_match_direct_enumeration():
+    rng = np.random.default_rng(11)
+    n = 400
+    p = rng.uniform(0, 0.02, size=(n, 3))
+    rad = rng.uniform(0.8e-3, 1.2e-3, size=n)
+    owner = np.arange(n) // 3            # clumps of 3 spheres: same-owner pairs excluded
+    for beta in (0.0, 5e-5):
+        pi, pj = oracle.listed_pairs_f64(p, rad, owner, beta)
+        got = list(zip(pi.tolist(), pj.tolist()))
+        assert got == numpy_pairs(p, rad, owner, beta)
+        assert len(got) > 100
+        assert got == sorted(got)
+
+
+def test_listed_pairs_voxel_f32_matches_float32_enumeration():
+    rng = np.random.default_rng(12)
+    n = 300
+    L = np.float32(2.5e-3)
+    cell = rng.integers(0, 6, size=(n, 3)).astype(np.int32)
+    off = (rng.random((n, 3)) * float(L)).astype(np.float32)
+    rad = rng.uniform(0.8e-3, 1.2e-3, size=n).astype(np.float32)
+    owner = np.arange(n)
+    beta = np.float32(5e-5)
+    pi, pj = oracle.listed_pairs_voxel_f32(cell, off, L, rad, owner, beta)
+    want = []
+    for i in range(n):
+        dc = (cell[i] - cell[i + 1:]).astype(np.float32)
+        d = dc * L + (off[i] - off[i + 1:])
+        s = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        t = (rad[i] + rad[i + 1:]) + np.float32(2) * beta
+        for j in np.nonzero(s < t * t)[0]:
+            want.append((i, i + 1 + j))
+    assert list(zip(pi.tolist(), pj.tolist())) == want
+    # the FP64 set on the same positions differs only for pairs within rounding of the threshold
+    p64 = cell.astype(np.float64) * float(L) + off.astype(np.float64)
+    qi, qj = oracle.listed_pairs_f64(p64, rad.astype(np.float64), owner, float(beta))
+    a = set(zip(pi.tolist(), pj.tolist()))
+    b = set(zip(qi.tolist(), qj.tolist()))
+    for (i, j) in a ^ b:
+        d = np.linalg.norm(p64[i] - p64[j])
+        t = float(rad[i]) + float(rad[j]) + 2 * float(beta)
+        assert abs(d - t) < 1e-6 * t
+
+
+def test_contacts_are_the_listed_set_at_zero_margin_and_inside_any_margin():
+    s = W.settle_box(n=250, box=(0.015, 0.015, 0.015), seed=5, gap=-2e-4)  # overlapping placement
+    ow = oracle.OracleWorld(s)
+    p = ow.sphere_positions()
+    F, T, cs = ow.eval()
+    sph = cs[cs["j"] >= 0]
+    contact = set(zip(sph["i"].tolist(), sph["j"].tolist()))
+    assert len(contact) > 50
+    assert np.all(sph["overlap"] > 0)
+    li, lj = oracle.listed_pairs_f64(p, ow.rad, ow.owner, 1e-5)
+    assert contact <= set(zip(li.tolist(), lj.tolist()))
+    # every listed pair at zero margin with a strictly positive overlap is a contact
+    li0, lj0 = oracle.listed_pairs_f64(p, ow.rad, ow.owner, 0.0)
+    for i, j in zip(li0.tolist(), lj0.tolist()):
+        d = np.linalg.norm(p[i] - p[j])
+        if (ow.rad[i] + ow.rad[j]) - d > 0:
+            assert (i, j) in contact
+
+
+# ----------------------------------------------------------------------------- Hertz head-on
+
+def headon_run(v0, e, R=1e-3, E=1e7, nu=0.3, steps_per_tc=4000, rho=W.RHO):
+    m = rho * 4 / 3 * math.pi * R ** 3
+    mbar = m / 2
+    Rbar = R / 2
+    Es = E / (2 * (1 - nu ** 2))
+    tc = 2.868 * (mbar ** 2 / (Rbar * Es ** 2 * v0)) ** 0.2
+    h = tc / steps_per_tc
+    s = W.two_spheres(R=R, v0=v0, E=E, nu=nu, e=e, h=h, gap=0.0, rho=rho)
+    s.x[0, 0] += 0.0
+    ow = oracle.OracleWorld(s)
+    dmax = 0.0
+    t_in = None
+    t_out = None
+    for k in range(4 * steps_per_tc):
+        F, T, cs = ow.eval()
+        if len(cs):
+            dmax = max(dmax, float(cs["overlap"].max()))
+            if t_in is None:
+                t_in = k * h
+        elif t_in is not None:
+            t_out = k * h
+            break
+        ow.step(1)
+    vrel = ow.v[1, 0] - ow.v[0, 0]
+    return dict(dmax=dmax, tc=t_out - t_in, e_out=vrel / v0, mbar=mbar, Rbar=Rbar, Es=Es, h=h)
+
+
+def test_hertz_headon_undamped_matches_closed_form():
+    """Hertz impact: delta_max = (15 mbar v0^2 / (16 E* sqrt(Rbar)))^(2/5) and duration
+    t_c = 2 (delta_max / v0) * (2/5) B(2/5, 1/2); restitution 1 without damping."""
+    v0 = 1.0
+    r = headon_run(v0, e=1.0)
+    dmax = (15 * r["mbar"] * v0 ** 2 / (16 * r["Es"] * math.sqrt(r["Rbar"]))) ** 0.4
+    beta_fn = math.gamma(0.4) * math.gamma(0.5) / math.gamma(0.9)
+    tc = 2 * dmax / v0 * 0.4 * beta_fn
+    assert r["dmax"] == pytest.approx(dmax, rel=2e-3)
+    assert r["tc"] == pytest.approx(tc, rel=2e-3)
+    assert r["e_out"] == pytest.approx(1.0, abs=2e-3)
+    # the worked numbers for this material at 1 m/s: delta_max ~ 7.0e-5 m, t_c ~ 2.07e-4 s
+    assert dmax == pytest.approx(7.05e-5, rel=1e-2)
+    assert tc == pytest.approx(2.07e-4, rel=1e-2)
+
+
+def ode_restitution(e, v0, mbar, Rbar, Es):
+    """Normal-only 1-D impact in the overlap x: the normal force on A is
+    k_n x + g_n (u.n) with u.n = -x' (A approaches B against the normal), so
+    m x'' = -(k_n(x) x - g_n(x) x'), integrated by classical RK4 with 2e5 steps per
+    contact: an independent integrator for the oracle's first-order 3-D step."""
+    le = math.log(max(e, 1e-12))
+    b = le / math.sqrt(le * le + math.pi ** 2)
+
+    def acc(x, xd):
+        if x <= 0:
+            return 0.0
+        sn = 2 * Es * math.sqrt(Rbar * x)
+        kn = 2.0 / 3.0 * sn
+        gn = 2 * math.sqrt(5.0 / 6.0) * b * math.sqrt(sn * mbar)
+        return -(kn * x - gn * xd) / mbar
+
+    tc = 2.868 * (mbar ** 2 / (Rbar * Es ** 2 * v0)) ** 0.2
+    n = 200_000
+    h = 2 * tc / n
+    x, xd = 0.0, v0
+    for _ in range(n):
+        k1x, k1v = xd, acc(x, xd)
+        k2x, k2v = xd + 0.5 * h * k1v, acc(x + 0.5 * h * k1x, xd + 0.5 * h * k1v)
+        k3x, k3v = xd + 0.5 * h * k2v, acc(x + 0.5 * h * k2x, xd + 0.5 * h * k2v)
+        k4x, k4v = xd + h * k3v, acc(x + h * k3x, xd + h * k3v)
+        x += h / 6 * (k1x + 2 * k2x + 2 * k3x + k4x)
+        xd += h / 6 * (k1v + 2 * k2v + 2 * k3v + k4v)
+        if x < 0 and xd < 0:
+            break
+    return -xd / v0
+
+
+@pytest.mark.slow
+def test_hertz_headon_damped_velocity_independent_and_matches_1d_solve():
+    """The damping of Sec. 4.1 scales as delta^(1/4), which makes the outcome independent of
+    the impact speed; the 3-D oracle must converge to the 1-D normal impact."""
+    outs = [headon_run(v0, e=0.5, steps_per_tc=2000) for v0 in (0.1, 1.0, 5.0)]
+    es = [o["e_out"] for o in outs]
+    assert max(es) - min(es) < 1e-3
+    assert 0.4 < es[0] < 1.0
+    r = outs[1]
+    e_ode = ode_restitution(0.5, 1.0, r["mbar"], r["Rbar"], r["Es"])
+    assert es[1] == pytest.approx(e_ode, abs=2e-3)
+    # monotone in the input restitution coefficient
+    e_lo = headon_run(1.0, e=0.2, steps_per_tc=2000)["e_out"]
+    e_hi = headon_run(1.0, e=0.8, steps_per_tc=2000)["e_out"]
+    assert e_lo < es[1] < e_hi < 1.0
+
+
+def test_mixer_material_restitution_velocity_independent():
+    gm = read_golden("mixer_material_sec5.txt")
+    rs = [headon_run(v0, e=gm["cor"], E=gm["E_pa"], nu=gm["nu"], rho=gm["density_kgpm3"], steps_per_tc=1500)["e_out"]
+          for v0 in (0.5, 2.0)]
+    assert abs(rs[0] - rs[1]) < 1e-3
+    assert 0.0 < rs[0] < 1.0
+
+
+# ----------------------------------------------------------------------------- balance laws
+
+def test_linear_and_angular_momentum_conserved_without_walls():
+    s = W.free_spheres(n=150, box=0.0135, vel_sigma=0.8, seed=3, h=2e-6)
+    ow = oracle.OracleWorld(s)
+    d0 = ow.diagnostics()
+    m = ow.mass
+    scale_p = float(np.sum(m * np.linalg.norm(ow.v, axis=1)))
+    scale_l = float(np.sum(np.linalg.norm(np.cross(ow.x, m[:, None] * ow.v), axis=1))) + \
+        float(np.sum(ow.moi[:, 0] * np.linalg.norm(ow.wb, axis=1)))
+    ncont = 0
+    for _ in range(10):
+        ow.step(40)
+        ncont += len(ow.eval()[2])
+    assert ncont > 20
+    d1 = ow.diagnostics()
+    assert np.max(np.abs(d1["momentum"] - d0["momentum"])) < 1e-12 * scale_p
+    assert np.max(np.abs(d1["angmom"] - d0["angmom"])) < 1e-11 * scale_l
+
+
+def test_energy_conserved_when_elastic_and_frictionless():
+    s = W.settle_box(n=150, box=(0.0135, 0.0135, 0.0135), seed=4, vel_sigma=0.3, e=1.0, mu=0.0, h=2e-7, gap=1e-5)
+    ow = oracle.OracleWorld(s)
+
+    def emech():
+        d = ow.diagnostics()
+        return d["ke"] + d["pe"] + d["elastic"]
+
+    ke0 = ow.diagnostics()["ke"]
+    e0 = emech()
+    worst = 0.0
+    for _ in range(20):
+        ow.step(100)
+        worst = max(worst, abs(emech() - e0))
+    assert worst < 1e-3 * ke0
+
+
+def test_energy_non_increasing_with_damping_and_friction():
+    s = W.settle_box(n=150, box=(0.0135, 0.0135, 0.0135), seed=4, vel_sigma=0.3, e=0.5, mu=0.4, h=5e-7, gap=1e-5)
+    ow = oracle.OracleWorld(s)
+    d = ow.diagnostics()
+    prev = d["ke"] + d["pe"] + d["elastic"]
+    e0 = abs(prev)
+    first = prev
+    for _ in range(20):
+        ow.step(50)
+        d = ow.diagnostics()
+        cur = d["ke"] + d["pe"] + d["elastic"]
+        assert cur <= prev + 1e-6 * e0
+        prev = cur
+    assert prev < first - 1e-3 * abs(first)
+
+
+# ----------------------------------------------------------------------------- statics
+
+def test_static_stack_settles_to_hertz_overlaps():
+    """A vertical column of k spheres on a floor: the contact under n spheres carries
+    W = n m g and settles to delta = (3 W / (4 E* sqrt(Rbar)))^(2/3), with Rbar = R/2
+    between spheres and Rbar = R at the floor (wall curvature infinite)."""
+    k, R, E, nu, g = 5, 1e-3, 1e7, 0.3, 9.81
+    x = np.array([[0.0, 0.0, R + 2 * R * i] for i in range(k)])
+    floor = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    s = make_scene(x, walls=[floor], g=(0, 0, -g), h=1e-6, mat=one_material(E=E, nu=nu, e=0.1, mu=0.3))
+    ow = oracle.OracleWorld(s)
+    ow.step(120000)
+    F, T, cs = ow.eval()
+    m = ow.mass[0]
+    Es_ss = E / (2 * (1 - nu ** 2))
+    Es_sw = E / (2 * (1 - nu ** 2))          # wall made of the same material
+    got = {}
+    for c in cs:
+        got[(int(c["i"]), int(c["j"]))] = float(c["overlap"])
+    for i in range(k - 1):
+        Wn = (k - 1 - i) * m * g
+        want = (3 * Wn / (4 * Es_ss * math.sqrt(R / 2))) ** (2 / 3)
+        assert got[(i, i + 1)] == pytest.approx(want, rel=1e-6)
+    want_floor = (3 * k * m * g / (4 * Es_sw * math.sqrt(R))) ** (2 / 3)
+    assert got[(0, -1)] == pytest.approx(want_floor, rel=1e-6)
+    assert np.max(np.abs(ow.v)) < 1e-9
+
+
+# ----------------------------------------------------------------------------- friction
+
+def incline_run(alpha_deg, t_end=1.5):
+    gd = read_golden("incline_sec4_3_1.txt")
+    r, m, mu = gd["radius_m"], gd["mass_kg"], gd["mu"]
+    rho = m / (4 / 3 * math.pi * r ** 3)
+    tpl = W.sphere_template(r, rho=rho)
+    a = math.radians(alpha_deg)
+    g = 9.81 * np.array([-math.sin(a), 0.0, -math.cos(a)])
+    Es = gd["E_pa"] / (2 * (1 - gd["nu"] ** 2))
+    d0 = (3 * m * 9.81 * math.cos(a) / (4 * Es * math.sqrt(r))) ** (2 / 3)
+    x = np.array([[0.0, 0.0, r - d0]])
+    plane = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    h = 2e-5
+    s = make_scene(x, v=[[gd["v0_up_incline_mps"], 0, 0]], templates=[tpl], walls=[plane], g=g, h=h,
+                   mat=one_material(E=gd["E_pa"], nu=gd["nu"], e=gd["cor"], mu=mu))
+    ow = oracle.OracleWorld(s)
+    ts, vs, slips, arms = [], [], [], []
+    n = int(t_end / h)
+    for k in range(0, n, 50):
+        ow.step(50)
+        qw, qx, qy, qz = ow.q[0]
+        Rm = np.array([[1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)],
+                       [2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)],
+                       [2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)]])
+        wg = Rm @ ow.wb[0]
+        F, T, cs = ow.eval()
+        # slip = velocity of the material point of the sphere at the contact point
+        arm = np.array(cs["point"][0]) - ow.x[0]
+        ts.append((k + 50) * h)
+        vs.append(ow.v[0, 0])
+        slips.append(ow.v[0, 0] + np.cross(wg, arm)[0])
+        arms.append(np.linalg.norm(arm))
+    return np.array(ts), np.array(vs), np.array(slips), mu, a, float(np.mean(arms[len(arms) // 2:])), r
+
+
+@pytest.mark.parametrize("alpha", [30.0, 38.0])
+def test_incline_below_threshold_ends_in_pure_rolling(alpha):
+    """Sec. 4.3.1 with C_r = 0: pure rolling iff tan(alpha) <= 3.5 mu; rolling down an
+    incline accelerates at (5/7) g sin(alpha)."""
+    ts, vs, slips, mu, a, arm, r = incline_run(alpha)
+    assert math.tan(a) < 3.5 * mu
+    late = ts > ts[-1] * 0.6
+    assert np.max(np.abs(slips[late])) < 1e-3 * np.max(np.abs(vs[late]))
+    acc = np.polyfit(ts[late], vs[late], 1)[0]
+    assert acc == pytest.approx(-5.0 / 7.0 * 9.81 * math.sin(a), rel=5e-3)
+
+
+@pytest.mark.parametrize("alpha", [45.0, 55.0])
+def test_incline_above_threshold_slips_at_the_coulomb_rate(alpha):
+    """Above the threshold the contact slides: the slip speed at the contact point grows at
+    g (sin(alpha) - mu cos(alpha) (1 + a^2 / (2/5 r^2))) for Coulomb friction mu N acting
+    at the lever arm a (= r minus half the overlap; 3.5 mu for a = r), MOI 2/5 m r^2."""
+    ts, vs, slips, mu, a, arm, r = incline_run(alpha)
+    assert math.tan(a) > 3.5 * mu
+    late = ts > ts[-1] * 0.5
+    rate = np.polyfit(ts[late], slips[late], 1)[0]
+    want = -9.81 * (math.sin(a) - mu * math.cos(a) * (1 + arm * arm / (0.4 * r * r)))
+    assert rate == pytest.approx(want, rel=2e-3)
+    acc = np.polyfit(ts[late], vs[late], 1)[0]
+    assert acc == pytest.approx(-9.81 * (math.sin(a) - mu * math.cos(a)), rel=1e-2)
+
+
+def test_history_lifetime_created_at_zero_and_dropped_on_separation():
+    """Contact wildcards (Sec. 4.2): allocated at zero when a contact appears, freed when it
+    vanishes.  An oblique frictional graze builds a history which disappears after."""
+    R = 1e-3
+    x = np.array([[0.0, 0.0, 0.0], [2 * R + 1e-7, 0.3 * R, 0.0]])
+    s = make_scene(x, v=[[0.5, 0, 0], [-0.5, 0, 0]], h=1e-7, mat=one_material(e=0.5, mu=0.5))
+    ow = oracle.OracleWorld(s)
+    seen = False
+    for _ in range(6000):
+        ow.step(1)
+        i, j, ut = ow.history()
+        if len(i):
+            seen = True
+            assert (i[0], j[0]) == (0, 1)
+            assert np.abs(ut[0, 2]) < 1e-15 and np.linalg.norm(ut[0]) > 0
+        elif seen:
+            break
+    assert seen
+    assert len(ow.history()[0]) == 0
+    # the history is orthogonal to the current normal after every update
+    F, T, cs = ow.eval()
+    assert len(cs) == 0
+
+
+# ----------------------------------------------------------------------------- rigid bodies
+
+def test_torque_free_symmetric_top_precesses_at_euler_rate():
+    """Euler's equations for I2 = I3: omega_1 is constant and (omega_2, omega_3) rotates at
+    lambda = (I2 - I1) omega_1 / I2; the gyroscopic sign decides the direction."""
+    tpl = W.rod_template(1e-3)
+    I1, I2 = tpl.moi[0], tpl.moi[1]
+    w0 = np.array([200.0, 30.0, 0.0])
+    h = 1e-6
+    s = make_scene([[0, 0, 0]], wb=[w0], templates=[tpl], h=h)
+    ow = oracle.OracleWorld(s)
+    d0 = ow.diagnostics()
+    n = 20000
+    ow.step(n)
+    t = n * h
+    lam = (I2 - I1) * w0[0] / I2
+    want = np.array([w0[0], w0[1] * math.cos(lam * t), -w0[1] * math.sin(lam * t)])
+    assert np.allclose(ow.wb[0], want, atol=2e-3 * np.linalg.norm(w0))
+    d1 = ow.diagnostics()
+    assert np.linalg.norm(d1["angmom"]) == pytest.approx(np.linalg.norm(d0["angmom"]), rel=1e-3)
+
+
+def test_quaternion_rotation_about_a_principal_axis_is_exact():
+    """Constant body rate about a principal axis: after n steps the orientation is the
+    rotation by n h |omega| about that axis (each step composes an exact rotation)."""
+    tpl = W.rod_template(1e-3)
+    w = 37.0
+    h = 1e-5
+    s = make_scene([[0, 0, 0]], wb=[[0.0, 0.0, w]], templates=[tpl], h=h)
+    ow = oracle.OracleWorld(s)
+    n = 5000
+    ow.step(n)
+    ang = n * h * w
+    want = np.array([math.cos(ang / 2), 0.0, 0.0, math.sin(ang / 2)])
+    assert np.allclose(ow.q[0], want, atol=1e-12)
+    # a sphere offset rotates with the body: local +x goes to (cos, sin, 0)
+    p = ow.sphere_positions()
+    assert np.allclose(p[2], [2e-3 * math.cos(ang), 2e-3 * math.sin(ang), 0.0], atol=1e-15)
+
+
+def test_clump_mass_properties_are_the_parallel_axis_sums():
+    R = 1e-3
+    for tpl in (W.rod_template(R), W.tetra_template(R)):
+        m1 = W.RHO * 4 / 3 * math.pi * R ** 3
+        I = np.zeros((3, 3))
+        for c in tpl.rel_xyz:
+            I += 0.4 * m1 * R * R * np.eye(3) + m1 * (np.dot(c, c) * np.eye(3) - np.outer(c, c))
+        assert np.allclose(np.diag(I), tpl.moi, rtol=1e-12)
+        assert np.allclose(I - np.diag(np.diag(I)), 0, atol=1e-20)
+        assert np.allclose(tpl.rel_xyz.sum(axis=0), 0, atol=1e-18)
+        d = np.linalg.norm(tpl.rel_xyz[:, None] - tpl.rel_xyz[None], axis=-1)
+        assert np.isclose(np.min(d[d > 0]), 2 * R)
+
+
+# ----------------------------------------------------------------------------- walls
+
+def test_sphere_resting_on_plane_and_in_drum_settles_to_hertz_overlap():
+    R, E, nu, g = 1e-3, 1e7, 0.3, 9.81
+    Es = E / (2 * (1 - nu ** 2))
+    m = W.RHO * 4 / 3 * math.pi * R ** 3
+    want = (3 * m * g / (4 * Es * math.sqrt(R))) ** (2 / 3)
+    plane = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    drum = dict(type=W.CYLINDER, mat=0, p=np.zeros(3), n=np.array([1.0, 0.0, 0.0]), r0=0.05)
+    for wall, x0 in ((plane, [0.0, 0.0, R]), (drum, [0.0, 0.0, -0.05 + R])):
+        s = make_scene([x0], walls=[wall], g=(0, 0, -g), h=1e-6, mat=one_material(E=E, nu=nu, e=0.1, mu=0.3))
+        ow = oracle.OracleWorld(s)
+        ow.step(120000)
+        F, T, cs = ow.eval()
+        assert len(cs) == 1 and cs["j"][0] == -1
+        assert cs["overlap"][0] == pytest.approx(want, rel=1e-6)
+
+
+def test_spinning_wall_drags_a_resting_sphere_along_its_surface_velocity():
+    R = 1e-3
+    plane = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]), omega=np.array([0, 0, 5.0]))
+    s = make_scene([[0.01, 0.0, R - 1e-6]], walls=[plane], g=(0, 0, -9.81), h=1e-6)
+    ow = oracle.OracleWorld(s)
+    ow.step(200)
+    vwall = np.cross([0, 0, 5.0], [0.01, 0.0, 0.0])          # +y at this point
+    assert ow.v[0, 1] > 0 and abs(ow.v[0, 0]) < 1e-3 * ow.v[0, 1]
+    assert np.dot(ow.v[0], vwall) > 0
+
+
+def cone_min_distance(pt, r0, z0, r1, z1, nseg=4000):
+    z = pt[2]
+    rho = math.hypot(pt[0], pt[1])
+    lo, hi = 0.0, 1.0
+    for _ in range(3):                   # sample, then resample around the best point
+        t = np.linspace(lo, hi, nseg)
+        d = np.hypot(rho - (r0 + t * (r1 - r0)), z - (z0 + t * (z1 - z0)))
+        k = int(np.argmin(d))
+        step = (hi - lo) / (nseg - 1)
+        lo, hi = max(0.0, t[k] - 2 * step), min(1.0, t[k] + 2 * step)
+    return float(d[k])
+
+
+def test_cone_wall_overlap_matches_sampled_surface_distance():
+    r0, z0, r1, z1 = 0.02, 0.0, 0.0777, 0.1
+    cone = dict(type=W.CONE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]), r0=r0, z0=z0, r1=r1, z1=z1)
+    rng = np.random.default_rng(2)
+    R = 1e-3
+    tan = (r1 - r0) / (z1 - z0)
+    checked = 0
+    for _ in range(40):
+        z = rng.uniform(0.01, 0.09)
+        phi = rng.uniform(0, 2 * math.pi)
+        rw = r0 + z * tan
+        rho = rw - rng.uniform(0.2, 1.0) * R * math.cos(math.atan(tan))
+        pt = np.array([rho * math.cos(phi), rho * math.sin(phi), z])
+        s = make_scene([pt], walls=[cone], h=1e-6)
+        ow = oracle.OracleWorld(s)
+        F, T, cs = ow.eval()
+        dist = cone_min_distance(pt, r0, z0, r1, z1)
+        if R - dist > 1e-6:
+            assert len(cs) == 1
+            assert cs["overlap"][0] == pytest.approx(R - dist, abs=2e-8)
+            # the normal points from the wall towards the axis side and lies in the meridian plane
+            n = cs["normal"][0]
+            assert n[0] * pt[0] + n[1] * pt[1] < 0
+            checked += 1
+    assert checked > 20
+
+
+def test_sink_removes_owners_below_the_plane():
+    x = np.array([[0.0, 0.0, 0.001], [0.0, 0.01, 0.5]])
+    s = make_scene(x, v=[[0, 0, -5.0], [0, 0, 0]], g=(0, 0, -9.81), h=1e-5,
+                   sink=(np.zeros(3), np.array([0.0, 0.0, 1.0])))
+    ow = oracle.OracleWorld(s)
+    ow.step(40)
+    assert ow.active.tolist() == [0, 1]
+    z_frozen = ow.x[0, 2]
+    ow.step(10)
+    assert ow.x[0, 2] == z_frozen and ow.x[1, 2] < 0.5
+
+
+def test_clump_collisions_conserve_linear_momentum_and_nearly_angular():
+    """Rods and tetrahedra colliding without walls or gravity: forces are pairwise
+    antisymmetric, so linear momentum is constant to rounding; the explicit gyroscopic
+    update conserves angular momentum only to O(h)."""
+    s = W.free_clumps(n=60, box=0.045, vel_sigma=1.5, seed=9, h=2e-6)
+    ow = oracle.OracleWorld(s)
+    d0 = ow.diagnostics()
+    m = ow.mass
+    scale_p = float(np.sum(m * np.linalg.norm(ow.v, axis=1)))
+    n_contacts = 0
+    for _ in range(400):
+        ow.step(10)
+        n_contacts += len(ow.eval()[2])
+    assert n_contacts > 5
+    d1 = ow.diagnostics()
+    assert np.max(np.abs(d1["momentum"] - d0["momentum"])) < 1e-12 * scale_p
+    assert np.linalg.norm(d1["angmom"] - d0["angmom"]) < 1e-2 * np.linalg.norm(d0["angmom"])
+
+
+def test_gyroscopic_angular_momentum_drift_is_first_order_in_h():
+    """The explicit body-frame update drifts |L| by O(h): halving h halves the drift."""
+    tpl = W.rod_template(1e-3)
+    drift = []
+    for h in (4e-6, 2e-6):
+        s = make_scene([[0, 0, 0]], wb=[[300.0, 80.0, -40.0]], templates=[tpl], h=h)
+        ow = oracle.OracleWorld(s)
+        L0 = ow.diagnostics()["angmom"].copy()
+        ow.step(int(round(0.02 / h)))
+        drift.append(np.linalg.norm(ow.diagnostics()["angmom"] - L0))
+    assert 1.8 < drift[0] / drift[1] < 2.2
