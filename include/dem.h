@@ -1,0 +1,295 @@
+/*
+ * dem.h -- C ABI of the GB300-native DEM contact pipeline (libdem_gb300.so).
+ *
+ * The library advances granular systems of spheres and rigid sphere clumps with the
+ * method of arXiv 2311.04648 (Chrono DEM-Engine): per time step, contact detection on
+ * margin-enlarged spheres (Sec. 2.1), a contact list carrying tangential history
+ * (Sec. 4.2, contact wildcards), the history-based Hertz-Mindlin force with Coulomb
+ * capping (Sec. 4.1 Eqs. 1-4 as computed by the default model of Sec. 4.2.1), per-clump
+ * force and torque sums (Sec. 4.1 Eqs. 5a-5b) and rigid-body integration.  All compute
+ * runs in hand-written CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions (every entry point):
+ *   - Returns dem_status; DEM_OK == 0.  dem_last_error(w) describes the last failure of
+ *     calls made on w (a static, thread-local string for calls that have no world).
+ *   - Handles are opaque.  The library owns all device memory it allocates (cudaMalloc
+ *     unless dem_world_desc.alloc is given).  The caller owns every host buffer it passes;
+ *     inputs are copied in before the call returns, outputs are written before it returns.
+ *   - Units are SI.  Quaternions are (w, x, y, z), unit norm, body-to-world.  Angular
+ *     velocities passed in and out are in the owner's body (principal) frame, as the
+ *     paper's user-referable variables define them (Sec. 4.2, table of referables).
+ *   - Arrays of vectors are row-major: xyz[3*k + a].
+ *   - Owner ("clump") ids and sphere ids are dense and assigned in insertion order.
+ *   - One world must not be used from two host threads at the same time.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef DEM_GB300_H
+#define DEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DEM_OK = 0,
+    DEM_ERR_ARG = 1,        /* invalid argument (null pointer, bad id, non-finite value) */
+    DEM_ERR_STATE = 2,      /* call not allowed in the current state (e.g. after init) */
+    DEM_ERR_CUDA = 3,       /* a CUDA runtime call failed; see dem_last_error */
+    DEM_ERR_CAPACITY = 4,   /* caller buffer too small; *count holds the size needed */
+    DEM_ERR_DIVERGED = 5,   /* a speed exceeded the error-out velocity or became NaN */
+    DEM_ERR_TIMEOUT = 6,    /* a bounded wait on the device or host ran out */
+    DEM_ERR_OVERFLOW = 7,   /* contact list capacity exceeded and could not be grown */
+    DEM_ERR_NOMEM = 8,      /* device or host allocation failed */
+    DEM_ERR_UNSUPPORTED = 9 /* feature not available in this build / configuration */
+} dem_status;
+
+/* Position encoding and arithmetic of the whole pipeline (Sec. 2.3 discusses the
+ * paper's own compressed encoding).
+ *   DEM_PRECISION_FP64_PLAIN : FP64 positions, velocities, forces and history.
+ *   DEM_PRECISION_VOXEL_FP32 : position = integer voxel index + FP32 offset inside the
+ *     voxel; velocities, forces, reductions and history in FP32 with a fixed reduction
+ *     order.  FP64 is used on the GPU only for wall distances and global diagnostics. */
+typedef enum { DEM_PRECISION_FP64_PLAIN = 0, DEM_PRECISION_VOXEL_FP32 = 1 } dem_precision;
+
+/* When the contact list is rebuilt (Sec. 2.1: delayed active-contact-set update).
+ *   EVERY_STEP     : detect before every step (margin 0 unless dem_set_margin).
+ *   VELOCITY_BOUND : detection on a second CUDA stream from a position snapshot, the
+ *                    margin-enlarged list reused for a number of steps chosen from the
+ *                    maximum speed; every step is audited against the margin.
+ *   LEARNED        : as VELOCITY_BOUND but the reuse length comes from a small MLP fed
+ *                    with per-bin motion statistics (dem_load_schedule_model); audited. */
+typedef enum { DEM_SCHEDULE_EVERY_STEP = 0, DEM_SCHEDULE_VELOCITY_BOUND = 1, DEM_SCHEDULE_LEARNED = 2 } dem_schedule;
+
+typedef enum { DEM_PROP_COR = 0, DEM_PROP_MU = 1, DEM_PROP_CRR = 2 } dem_prop;
+
+typedef struct dem_world dem_world;
+typedef struct dem_batch dem_batch;
+
+typedef struct {
+    double box_lo[3], box_hi[3];   /* simulation domain; the cell grid covers it           */
+    int32_t precision;             /* dem_precision                                        */
+    int32_t schedule;              /* dem_schedule                                         */
+    int32_t device;                /* CUDA device ordinal                                  */
+    int32_t gyroscopic;            /* 1: include w x (I w) in the body-frame update        */
+    int64_t max_spheres;           /* optional capacity hint (0: exact)                    */
+    double margin_max;             /* largest contact margin ever used (sizes the cells);
+                                      0 selects 5% of the largest sphere radius            */
+    void *stream;                  /* cudaStream_t for force/integration; NULL: own stream */
+    void *detect_stream;           /* cudaStream_t for detection; NULL: own stream         */
+    /* optional device allocator (e.g. a framework's caching allocator); both or neither */
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} dem_world_desc;
+
+typedef struct {
+    int64_t steps;                 /* steps completed since initialize                     */
+    int64_t rebuilds;              /* contact-list builds                                  */
+    int64_t audit_fallbacks;       /* builds forced because the audit found the list stale */
+    int64_t overflow_regrows;      /* contact-list capacity increases                     */
+    int64_t listed_pairs;          /* sphere-sphere pairs in the list in use (each once)   */
+    int64_t wall_pairs;            /* sphere-wall entries in the list in use               */
+    int64_t active_contacts;       /* pairs with overlap > 0 at the last evaluated step    */
+    int32_t list_capacity;         /* entries per sphere row of the contact list           */
+    int32_t list_max_row;          /* longest row at the last build                        */
+    double margin;                 /* margin of the list in use                            */
+    double displacement_bound;     /* audited displacement bound since the list snapshot   */
+    double max_speed;              /* max |v| over owners at the last audit                */
+    double mean_steps_per_build;   /* steps / rebuilds                                     */
+    double cell_size;              /* cell (= voxel) edge                                  */
+    int64_t n_cells;               /* cells of all scenes                                  */
+    double ms_detect, ms_force;    /* profiled GPU time: detection (sort, cells, narrow) /
+                                      force + integration kernel (dem_set_profiling)       */
+    double ms_hash, ms_link;       /* profiled GPU time: snapshot + keys / list link       */
+    int64_t n_detect, n_force;     /* profiled launches of each                            */
+    double ms_total;               /* wall GPU time of all dem_step calls                  */
+} dem_stats;
+
+typedef struct {
+    double kinetic;                /* sum 1/2 m v^2 + 1/2 w_b . I w_b                       */
+    double potential;              /* - sum m g . x                                        */
+    double elastic;                /* sum over contacts (8/15) E* sqrt(Rbar) delta^(5/2)   */
+    double momentum[3];            /* sum m v                                              */
+    double angular_momentum[3];    /* sum x x m v + R(q) I w_b, about the origin           */
+} dem_diagnostics;
+
+/* ---------------------------------------------------------------- world lifecycle */
+
+/* Create an empty world (Sec. 3.1: DEMSolver + InstructBoxDomainDimension).
+ * d: descriptor (copied); *out receives the handle.  Errors: ARG, CUDA, NOMEM. */
+dem_status dem_world_create(const dem_world_desc *d, dem_world **out);
+/* Free the world and all its device memory.  Accepts NULL. */
+dem_status dem_world_destroy(dem_world *w);
+/* Human-readable description of the last error on w (w may be NULL). Never NULL. */
+const char *dem_last_error(const dem_world *w);
+
+/* ---------------------------------------------------------------- set-up (before init) */
+
+/* Register a material (Sec. 3.1: LoadMaterial with E, nu, CoR, mu, Crr).  E > 0,
+ * 0 <= nu < 0.5, 0 <= CoR <= 1, mu >= 0.  Crr must be 0: rolling resistance is not
+ * implemented (DEM_ERR_UNSUPPORTED otherwise).  *mat_id receives the dense id.
+ * Pairwise CoR and mu default to the mean of the two materials' values. */
+dem_status dem_add_material(dem_world *w, double E, double nu, double CoR, double mu, double Crr,
+                            int32_t *mat_id);
+/* Override a pairwise property for materials (a, b), symmetric (Sec. 3.1:
+ * SetMaterialPropertyPair).  prop is dem_prop; CRR accepts only 0. */
+dem_status dem_set_material_pair(dem_world *w, int32_t prop, int32_t a, int32_t b, double value);
+
+/* Six planes on the faces of the domain box, normals pointing inwards
+ * (Sec. 3.1: InstructBoxDomainBoundingBC("all")).  Wall ids are returned in order
+ * -x, +x, -y, +y, -z, +z starting at *first_id (nullable). */
+dem_status dem_add_box_walls(dem_world *w, int32_t mat, int32_t *first_id);
+/* Plane through p with unit normal n pointing into the granular domain. */
+dem_status dem_add_plane(dem_world *w, const double p[3], const double n[3], int32_t mat, int32_t *id);
+/* Inner surface of an infinite cylinder (Sec. 3.1: AddCylinder): axis through c along
+ * the unit vector axis, radius r; spheres live inside.  omega: prescribed spin (rad/s)
+ * about the axis (the drum); the geometry is invariant, only its surface moves. */
+dem_status dem_add_cylinder(dem_world *w, const double c[3], const double axis[3], double radius,
+                            int32_t mat, double omega, int32_t *id);
+/* Surface of revolution of the segment (r0, z0)-(r1, z1) about the axis through p along
+ * the unit vector axis (z measured along the axis from p); spheres live on the axis
+ * side (the conical hopper wall). */
+dem_status dem_add_cone_segment(dem_world *w, const double p[3], const double axis[3], double r0,
+                                double z0, double r1, double z1, int32_t mat, int32_t *id);
+/* Prescribed rigid spin of wall `id` about its own point p with angular velocity
+ * omega[3] (world frame); only walls whose geometry is invariant under the spin are
+ * accepted (planes about their normal, cylinders and cones about their axis). */
+dem_status dem_set_wall_spin(dem_world *w, int32_t id, const double omega[3]);
+
+/* Register a clump template (Sec. 3.1: LoadClumpType): n component spheres with centres
+ * rel_xyz[3n] in the principal frame about the centre of mass, radii[n] > 0, materials
+ * mats[n]; total mass and principal moments moi[3].  Components may overlap. */
+dem_status dem_add_clump_template(dem_world *w, int32_t n, const double *rel_xyz, const double *radii,
+                                  const int32_t *mats, double mass, const double moi[3], int32_t *tid);
+/* Instantiate n clumps of template tid (Sec. 3.1: AddClumps).  xyz[3n] centres of mass;
+ * quat[4n], vel[3n], omega[3n] (body frame) nullable (identity / zero); scale[n]
+ * nullable: per-instance geometric scale s (offsets and radii times s, mass times s^3,
+ * moments times s^5).  *first_id receives the id of the first new owner (nullable). */
+dem_status dem_add_clumps(dem_world *w, int32_t tid, int64_t n, const double *xyz, const double *quat,
+                          const double *vel, const double *omega, const double *scale, int64_t *first_id);
+
+/* As dem_add_clumps with a template id per instance, tids[n] (Sec. 3.1: AddClumps also
+ * takes one template per position); instance order is preserved. */
+dem_status dem_add_clumps_mixed(dem_world *w, int64_t n, const int32_t *tids, const double *xyz, const double *quat,
+                                const double *vel, const double *omega, const double *scale, int64_t *first_id);
+
+/* Time step h > 0 (Sec. 3.1: SetInitTimeStep). */
+dem_status dem_set_timestep(dem_world *w, double h);
+/* Gravitational acceleration (Sec. 3.1: SetGravitationalAcceleration). */
+dem_status dem_set_gravity(dem_world *w, const double g[3]);
+/* Error-out speed (Sec. 3.1: SetErrorOutVelocity); 0 disables.  Exceeding it (or NaN)
+ * stops dem_step with DEM_ERR_DIVERGED, the world left at the last good step. */
+dem_status dem_set_error_velocity(dem_world *w, double v);
+/* Contact margin beta >= 0 added to every sphere for detection (Sec. 2.1: artificial
+ * margin); must not exceed desc.margin_max.  EVERY_STEP defaults to 0, the delayed
+ * schedules to margin_max. */
+dem_status dem_set_margin(dem_world *w, double beta);
+/* Owners whose centre of mass x satisfies (x - p).n < 0 after a step are removed from
+ * the simulation (frozen, no contacts): the hopper outlet. */
+dem_status dem_set_sink(dem_world *w, const double p[3], const double n[3]);
+/* Weights of the learned schedule (format written by dem_schedule_export). */
+dem_status dem_load_schedule_model(dem_world *w, const void *weights, size_t bytes);
+
+/* Upload, allocate and build the first contact list (Sec. 3.1: Initialize).  After
+ * this, calls that change topology return DEM_ERR_STATE. */
+dem_status dem_initialize(dem_world *w);
+
+/* ---------------------------------------------------------------- stepping */
+
+/* Advance nsteps (Sec. 3.1: DoDynamics).  Synchronous: returns when the GPU is done.
+ * DEM_ERR_DIVERGED / DEM_ERR_TIMEOUT / DEM_ERR_OVERFLOW leave the world at the last
+ * good step (stats.steps tells which). */
+dem_status dem_step(dem_world *w, int64_t nsteps);
+/* Wait for all work queued by w. */
+dem_status dem_sync(dem_world *w);
+/* Bracket every force launch and every detection phase with CUDA events on the stream
+ * that runs it and accumulate their durations into dem_stats (on = 1); off by default. */
+dem_status dem_set_profiling(dem_world *w, int32_t on);
+/* The CUDA stream (cudaStream_t) on which force/integration kernels run. */
+dem_status dem_get_stream(dem_world *w, void **stream);
+
+/* ---------------------------------------------------------------- read back / set state */
+
+/* Owner state for ids [first, first + n); any output may be NULL.  xyz[3n], quat[4n],
+ * vel[3n], omega[3n] (body frame).  Tracker Pos / Vel / AngVel in the paper. */
+dem_status dem_get_owner_state(dem_world *w, int64_t first, int64_t n, double *xyz, double *quat,
+                               double *vel, double *omega);
+/* Overwrite owner state (tracker SetPos etc.); NULL inputs keep the current value.
+ * Forces a contact-list rebuild before the next step (history is carried over). */
+dem_status dem_set_owner_state(dem_world *w, int64_t first, int64_t n, const double *xyz,
+                               const double *quat, const double *vel, const double *omega);
+/* Sphere centres (world frame) and radii for sphere ids [first, first + n). */
+dem_status dem_get_sphere_positions(dem_world *w, int64_t first, int64_t n, double *xyz, double *radius);
+/* The voxel encoding of sphere centres (DEM_PRECISION_VOXEL_FP32 only): integer cell
+ * cell[3n] and FP32 offset offset[3n] in [0, edge) per axis, centre = (scene box_lo +
+ * cell * edge) + offset; *edge (nullable) receives the cell edge.  DEM_ERR_STATE in the
+ * FP64 form. */
+dem_status dem_get_sphere_voxels(dem_world *w, int64_t first, int64_t n, int32_t *cell, float *offset, double *edge);
+/* Every contact with overlap > 0 at the current state, ordered by (i, partner) with
+ * spheres before walls.  i < j for sphere pairs; j = -1 - wall_id for walls.  force[3]
+ * acts on sphere i (global frame); point[3] is the contact point; overlap > 0; history
+ * is the tangential displacement that the next step starts from.  Outputs nullable.
+ * DEM_ERR_CAPACITY if cap < count (count is always written). */
+dem_status dem_get_contacts(dem_world *w, int64_t cap, int64_t *count, int64_t *i, int64_t *j,
+                            double *force, double *point, double *overlap, double *history);
+/* The listed (margin-enlarged) sphere-sphere pairs of the list in use, i < j, sorted. */
+dem_status dem_get_listed_pairs(dem_world *w, int64_t cap, int64_t *count, int64_t *i, int64_t *j);
+/* The listed sphere-wall entries (sphere id, wall id), sorted. */
+dem_status dem_get_listed_wall_pairs(dem_world *w, int64_t cap, int64_t *count, int64_t *sphere,
+                                     int64_t *wall);
+/* Per-owner force (contacts plus gravity) and contact torque about the centre of mass
+ * (global frame) evaluated at the current state without advancing it, ids
+ * [first, first + n).  The history is not modified. */
+dem_status dem_get_owner_forces(dem_world *w, int64_t first, int64_t n, double *force, double *torque);
+/* Set the tangential history of the listed contacts (i, j, ut[3k]); unlisted entries
+ * are ignored and all other history is zeroed.  For exact replays in tests. */
+dem_status dem_set_history(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *ut);
+dem_status dem_get_stats(dem_world *w, dem_stats *s);
+/* FP64 diagnostics computed on the GPU with a fixed-order reduction. */
+dem_status dem_get_diagnostics(dem_world *w, dem_diagnostics *d);
+
+/* ---------------------------------------------------------------- checkpoint */
+
+/* Serialise owner state, contact list with history and schedule state into buf.
+ * *used receives the size; DEM_ERR_CAPACITY (with *used set) if cap is too small. */
+dem_status dem_save_state(dem_world *w, void *buf, size_t cap, size_t *used);
+/* Restore a blob written by dem_save_state of a world with identical set-up. */
+dem_status dem_load_state(dem_world *w, const void *buf, size_t bytes);
+
+/* ---------------------------------------------------------------- batched scenes */
+
+/* A batch of independent scenes stepped together by the same kernels (one launch per
+ * stage over all scenes).  descs[k] describes scene k; precision and schedule of
+ * descs[0] apply to all.  Scenes are set up through dem_batch_world handles, which
+ * accept every set-up call above; then dem_batch_initialize.  Scene handles stay valid
+ * until dem_batch_destroy and give per-scene read-back; owner ids are per scene. */
+dem_status dem_batch_create(int32_t nscenes, const dem_world_desc *descs, dem_batch **out);
+dem_status dem_batch_world(dem_batch *b, int32_t k, dem_world **scene);
+dem_status dem_batch_initialize(dem_batch *b);
+/* Advance every scene by nsteps; the per-step work is replayed from a CUDA graph. */
+dem_status dem_batch_step(dem_batch *b, int64_t nsteps);
+dem_status dem_batch_destroy(dem_batch *b);
+
+/* ---------------------------------------------------------------- learned schedule */
+
+/* Record per-bin features and labels during dem_step (on = 1) or stop (on = 0). */
+dem_status dem_schedule_collect(dem_world *w, int32_t on);
+/* Train the schedule MLP on the recorded samples with the GPU kernels. */
+dem_status dem_schedule_train(dem_world *w, int32_t epochs, float lr, uint64_t seed, float *final_loss);
+/* Export the current weights (format accepted by dem_load_schedule_model). */
+dem_status dem_schedule_export(dem_world *w, void *buf, size_t cap, size_t *used);
+
+/* ---------------------------------------------------------------- kernels as utilities */
+
+/* Stable LSD radix sort of (key, value) pairs of 32-bit unsigned integers on the GPU,
+ * sorting on the low `bits` bits of the keys (1..32).  Host buffers; n >= 0. */
+dem_status dem_util_radix_sort_u32(int64_t n, const uint32_t *keys, const uint32_t *vals, int32_t bits,
+                                   uint32_t *keys_out, uint32_t *vals_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEM_GB300_H */

@@ -1,0 +1,258 @@
+// common.cuh -- shared device/host definitions of the GB300 DEM pipeline.
+//
+// Two position forms share every kernel through the policies FormF64 / FormF32:
+//   FormF64: owner position = three doubles (the plain FP64 form);
+//   FormF32: owner position = integer voxel index per axis (21 bits each, packed in a
+//            u64) + FP32 offset in [0, L) inside the voxel.  The voxel IS the detection
+//            cell, so binning needs no floating point, and every position difference is
+//            (ci - cj) * L + (oi - oj), exact in the integer part (Sec. 2.3 motivates
+//            integer-based coordinates; the FP32 offset replaces the paper's 3 x u16).
+// Arithmetic that decides a discrete outcome (sphere centres, pair predicate, voxel
+// carry) uses explicit round-to-nearest intrinsics so that it never contracts into
+// FMA and every kernel computes bit-identical values.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#ifndef DEM_HD
+#define DEM_HD __host__ __device__ __forceinline__
+#endif
+
+namespace dem {
+
+constexpr uint32_t WALL_BIT = 0x80000000u;   // partner id with this bit set is a wall
+constexpr int KMAX = 64;                      // hard upper bound of a contact-list row
+constexpr int VOX_BITS = 21;
+constexpr int VOX_BIAS = 1 << (VOX_BITS - 1);
+constexpr uint64_t VOX_MASK = (1ull << VOX_BITS) - 1;
+
+enum : int { WALL_PLANE = 0, WALL_CYLINDER = 1, WALL_CONE = 2 };
+
+// halt reasons written by the kernels into DevStatus::halt
+enum : int { HALT_NONE = 0, HALT_DIVERGED = 1, HALT_OVERFLOW = 2, HALT_TIMEOUT = 3 };
+
+template <typename R> struct V3 { R x, y, z; };
+
+template <typename R> DEM_HD V3<R> mk(R x, R y, R z) { return V3<R>{x, y, z}; }
+template <typename R> DEM_HD V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename R> DEM_HD V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename R> DEM_HD V3<R> operator-(V3<R> a) { return {-a.x, -a.y, -a.z}; }
+template <typename R> DEM_HD V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename R> DEM_HD R dot(V3<R> a, V3<R> b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+template <typename R> DEM_HD V3<R> cross(V3<R> a, V3<R> b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Exactly rounded (never fused) primitives, overloaded per precision.
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+
+// R(q) a with the rotation matrix of the unit quaternion (w, x, y, z), every product and
+// sum rounded separately in the fixed order ((R0 a0 + R1 a1) + R2 a2).
+template <typename R>
+__device__ __forceinline__ V3<R> rotate_exact(R qw, R qx, R qy, R qz, V3<R> a)
+{
+    const R one = R(1), two = R(2);
+    R xx = rmul(qx, qx), yy = rmul(qy, qy), zz = rmul(qz, qz);
+    R xy = rmul(qx, qy), xz = rmul(qx, qz), yz = rmul(qy, qz);
+    R wx = rmul(qw, qx), wy = rmul(qw, qy), wz = rmul(qw, qz);
+    R m00 = rsub(one, rmul(two, radd(yy, zz))), m01 = rmul(two, rsub(xy, wz)), m02 = rmul(two, radd(xz, wy));
+    R m10 = rmul(two, radd(xy, wz)), m11 = rsub(one, rmul(two, radd(xx, zz))), m12 = rmul(two, rsub(yz, wx));
+    R m20 = rmul(two, rsub(xz, wy)), m21 = rmul(two, radd(yz, wx)), m22 = rsub(one, rmul(two, radd(xx, yy)));
+    V3<R> o;
+    o.x = radd(radd(rmul(m00, a.x), rmul(m01, a.y)), rmul(m02, a.z));
+    o.y = radd(radd(rmul(m10, a.x), rmul(m11, a.y)), rmul(m12, a.z));
+    o.z = radd(radd(rmul(m20, a.x), rmul(m21, a.y)), rmul(m22, a.z));
+    return o;
+}
+
+// Ordinary (contractible) rotation and its transpose, for dynamics.
+template <typename R>
+DEM_HD void quat_mat(R qw, R qx, R qy, R qz, R m[9])
+{
+    R xx = qx * qx, yy = qy * qy, zz = qz * qz, xy = qx * qy, xz = qx * qz, yz = qy * qz;
+    R wx = qw * qx, wy = qw * qy, wz = qw * qz;
+    m[0] = R(1) - R(2) * (yy + zz); m[1] = R(2) * (xy - wz); m[2] = R(2) * (xz + wy);
+    m[3] = R(2) * (xy + wz); m[4] = R(1) - R(2) * (xx + zz); m[5] = R(2) * (yz - wx);
+    m[6] = R(2) * (xz - wy); m[7] = R(2) * (yz + wx); m[8] = R(1) - R(2) * (xx + yy);
+}
+template <typename R> DEM_HD V3<R> mat_vec(const R m[9], V3<R> a)
+{
+    return {(m[0] * a.x + m[1] * a.y) + m[2] * a.z, (m[3] * a.x + m[4] * a.y) + m[5] * a.z,
+            (m[6] * a.x + m[7] * a.y) + m[8] * a.z};
+}
+template <typename R> DEM_HD V3<R> mat_tvec(const R m[9], V3<R> a)
+{
+    return {(m[0] * a.x + m[3] * a.y) + m[6] * a.z, (m[1] * a.x + m[4] * a.y) + m[7] * a.z,
+            (m[2] * a.x + m[5] * a.y) + m[8] * a.z};
+}
+
+// ------------------------------------------------------------------ scene-level data
+
+struct Wall {            // analytical wall (device copy); all in FP64
+    int type, mat;       // global material id
+    double p[3], n[3];
+    double r0, z0, r1, z1;
+    double omega[3];
+};
+
+struct Scene {           // per-scene constants (device copy)
+    double lo[3];        // origin of the cell grid
+    int nc[3];           // cells per axis
+    uint32_t cell_base;  // first global cell index of this scene
+    double h, g[3];
+    float hf, gf[3];
+    double v_err;        // <= 0: off
+    int wall_begin, wall_count;
+    int has_sink;
+    double sink_p[3], sink_n[3];
+    int mat_base, n_mat, pair_base;
+};
+
+struct PairParam {       // pairwise contact constants, precomputed on the host in FP64
+    double Estar, Gstar, beta, mu;
+};
+
+// Device-resident control block (one per world).  Kernels read the selectors and flags
+// here, so the host can queue work (or replay a CUDA graph) without knowing in advance
+// which buffers hold the current state, whether a list went stale or a step diverged.
+struct DevStatus {
+    int halt;                    // HALT_*: every kernel returns immediately
+    int list_stale;              // list in use no longer covers every contact: force skips
+    int overflow;                // a row exceeded the list capacity in the last narrow phase
+    int max_row;                 // longest row of the last narrow phase
+    int state_par;               // owner-state buffer holding the current state
+    int hist_par;                // history buffer holding the current history
+    int list_cur;                // contact list in use
+    int diverged;                // set by the force kernel, turned into a halt by the audit
+    unsigned int step_disp_bits; // max over owners of this step's displacement bound (float bits)
+    unsigned int vmax_bits;      // max |v| over owners this step (float bits)
+    int pad0, pad1;
+    double disp_cur;             // displacement bound since the snapshot of the list in use
+    double disp_next;            // ... since the snapshot of the list being built
+    double beta_cur, beta_next;  // margins of those lists
+    double vmax_last;            // max |v| after the last completed step
+    double disp_slack;           // added per step: rounding of the position update
+    long long steps_done;
+    long long rebuilds;
+    long long stale_events;
+};
+
+// ------------------------------------------------------------------ position forms
+
+struct PosF64 { double x, y, z; };
+struct PosF32 { int cx, cy, cz; float x, y, z; };
+
+DEM_HD uint64_t pack_vox(int cx, int cy, int cz)
+{
+    return (uint64_t)((uint32_t)(cx + VOX_BIAS) & VOX_MASK) |
+           ((uint64_t)((uint32_t)(cy + VOX_BIAS) & VOX_MASK) << VOX_BITS) |
+           ((uint64_t)((uint32_t)(cz + VOX_BIAS) & VOX_MASK) << (2 * VOX_BITS));
+}
+DEM_HD void unpack_vox(uint64_t v, int &cx, int &cy, int &cz)
+{
+    cx = (int)(v & VOX_MASK) - VOX_BIAS;
+    cy = (int)((v >> VOX_BITS) & VOX_MASK) - VOX_BIAS;
+    cz = (int)((v >> (2 * VOX_BITS)) & VOX_MASK) - VOX_BIAS;
+}
+
+struct FormF64 {
+    using R = double;
+    using R4 = double4_32a;
+    using Pos = PosF64;
+    static constexpr bool voxel = false;
+    // owner position storage: double4_32a (x, y, z, mass)
+    struct PosStore { double4_32a *xm; };
+
+    __device__ static Pos load(const PosStore &s, int64_t o, R &mass)
+    {
+        double4_32a a = s.xm[o];
+        mass = a.w;
+        return Pos{a.x, a.y, a.z};
+    }
+    __device__ static void store(PosStore &s, int64_t o, Pos p, R mass) { s.xm[o] = make_double4_32a(p.x, p.y, p.z, mass); }
+    // a - b, exactly rounded component-wise
+    __device__ static V3<R> diff(const Pos &a, const Pos &b, float /*L*/)
+    {
+        return {rsub(a.x, b.x), rsub(a.y, b.y), rsub(a.z, b.z)};
+    }
+    __device__ static Pos advance(Pos p, V3<R> d, float /*L*/) { return Pos{radd(p.x, d.x), radd(p.y, d.y), radd(p.z, d.z)}; }
+    // cell of a position in a scene grid (unclamped)
+    __device__ static void cell(const Pos &p, const Scene &sc, double invL, int &cx, int &cy, int &cz)
+    {
+        cx = (int)floor(rmul(rsub(p.x, sc.lo[0]), invL));
+        cy = (int)floor(rmul(rsub(p.y, sc.lo[1]), invL));
+        cz = (int)floor(rmul(rsub(p.z, sc.lo[2]), invL));
+    }
+    __device__ static V3<double> absolute(const Pos &p, const Scene &, double) { return {p.x, p.y, p.z}; }
+};
+
+struct FormF32 {
+    using R = float;
+    using R4 = float4;
+    using Pos = PosF32;
+    static constexpr bool voxel = true;
+    // owner position storage: packed voxel + float4 (offset, mass)
+    struct PosStore { uint64_t *vox; float4 *om; };
+
+    __device__ static Pos load(const PosStore &s, int64_t o, R &mass)
+    {
+        uint64_t v = s.vox[o];
+        float4 a = s.om[o];
+        Pos p;
+        unpack_vox(v, p.cx, p.cy, p.cz);
+        p.x = a.x; p.y = a.y; p.z = a.z;
+        mass = a.w;
+        return p;
+    }
+    __device__ static void store(PosStore &s, int64_t o, Pos p, R mass)
+    {
+        s.vox[o] = pack_vox(p.cx, p.cy, p.cz);
+        s.om[o] = make_float4(p.x, p.y, p.z, mass);
+    }
+    // (ca - cb) * L + (oa - ob): the integer part is exact, then two rounded operations
+    __device__ static V3<R> diff(const Pos &a, const Pos &b, float L)
+    {
+        V3<R> d;
+        d.x = radd(rmul((float)(a.cx - b.cx), L), rsub(a.x, b.x));
+        d.y = radd(rmul((float)(a.cy - b.cy), L), rsub(a.y, b.y));
+        d.z = radd(rmul((float)(a.cz - b.cz), L), rsub(a.z, b.z));
+        return d;
+    }
+    // keep the offset in [0, L): carry whole voxels into the index
+    __device__ static void carry(int &c, float &o, float L)
+    {
+        if (o >= L || o < 0.0f) {
+            float k = floorf(__fdiv_rn(o, L));
+            o = rsub(o, rmul(k, L));
+            c += (int)k;
+            if (o >= L) { o = rsub(o, L); c += 1; }
+            if (o < 0.0f) { o = radd(o, L); c -= 1; }
+        }
+    }
+    __device__ static Pos advance(Pos p, V3<R> d, float L)
+    {
+        Pos q = p;
+        q.x = radd(p.x, d.x); q.y = radd(p.y, d.y); q.z = radd(p.z, d.z);
+        carry(q.cx, q.x, L); carry(q.cy, q.y, L); carry(q.cz, q.z, L);
+        return q;
+    }
+    __device__ static void cell(const Pos &p, const Scene &, double, int &cx, int &cy, int &cz)
+    {
+        cx = p.cx; cy = p.cy; cz = p.cz;
+    }
+    // world-frame position in FP64: (lo + c L) + o
+    __device__ static V3<double> absolute(const Pos &p, const Scene &sc, double L)
+    {
+        return {radd(radd(sc.lo[0], rmul((double)p.cx, L)), (double)p.x),
+                radd(radd(sc.lo[1], rmul((double)p.cy, L)), (double)p.y),
+                radd(radd(sc.lo[2], rmul((double)p.cz, L)), (double)p.z)};
+    }
+};
+
+}  // namespace dem

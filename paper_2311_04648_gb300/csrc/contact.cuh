@@ -1,0 +1,117 @@
+// contact.cuh -- per-contact physics of the default DEM-Engine force model.
+//
+// The history-based Hertz-Mindlin model of arXiv 2311.04648 Sec. 4.1 (Eqs. 1-4) in the
+// form the default model of Sec. 4.2.1 evaluates it:
+//   Sn = 2 E* sqrt(Rbar delta), k_n = 2/3 Sn, gamma_n = 2 sqrt(5/6) beta sqrt(Sn mbar),
+//   u = relative contact-point velocity of A w.r.t. B, v_t = u - (u.n) n,
+//   history: ut <- ut + h v_t, then ut <- ut - (ut.n) n   (update precedes the force),
+//   F = (k_n delta + gamma_n u.n) n,
+//   k_t = 8 G* sqrt(Rbar delta), g_t = -2 sqrt(5/6) beta sqrt(mbar k_t),
+//   F_t = -k_t ut - g_t v_t; if |F_t| > mu |F| (and |F_t| > 1e-12): F_t scaled to mu |F|
+//   and ut back-solved as (F_t + g_t v_t) / (-k_t); |F_t| <= 1e-12 gives F_t = 0.
+// beta = ln e / sqrt(ln^2 e + pi^2) (e clamped at 1e-12) is precomputed on the host per
+// material pair.  Rolling resistance (C_r) is not part of this model build.
+#pragma once
+#include "common.cuh"
+
+namespace dem {
+
+template <typename R>
+struct ContactIn {
+    V3<R> n;          // unit normal from B to A
+    R delta;          // overlap > 0
+    V3<R> uA, uB;     // velocities of the contact point as a point of A and of B
+    R Rbar, mbar;
+    R Estar, Gstar, beta, mu;
+};
+
+template <typename R>
+__device__ __forceinline__ void hertz_mindlin(const ContactIn<R> &c, R h, V3<R> &ut, V3<R> &F)
+{
+    const R c56 = R(0.91287092917527690);   // sqrt(5/6)
+    V3<R> u = c.uA - c.uB;
+    R proj = dot(u, c.n);
+    V3<R> vt = u - proj * c.n;
+    ut = ut + h * vt;
+    R up = dot(ut, c.n);
+    ut = ut - up * c.n;
+
+    R sqrtRd = sqrt(c.delta * c.Rbar);
+    R Sn = R(2) * c.Estar * sqrtRd;
+    R kn = (R(2) / R(3)) * Sn;
+    R gn = R(2) * c56 * c.beta * sqrt(Sn * c.mbar);
+    R fn = kn * c.delta + gn * proj;
+    F = fn * c.n;
+    if (c.mu > R(0)) {
+        R kt = R(8) * c.Gstar * sqrtRd;
+        R gt = R(-2) * c56 * c.beta * sqrt(c.mbar * kt);
+        V3<R> Ft = (-kt) * ut - gt * vt;
+        R ft = sqrt(dot(Ft, Ft));
+        if (ft > R(1e-12)) {
+            R ftmax = sqrt(dot(F, F)) * c.mu;
+            if (ft > ftmax) {
+                Ft = (ftmax / ft) * Ft;
+                ut = (R(1) / (-kt)) * (Ft + gt * vt);
+            }
+        } else {
+            Ft = mk(R(0), R(0), R(0));
+        }
+        F = F + Ft;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_pair(const PairParam *pairs, const uint16_t *mat_scene, const uint16_t *mat_local,
+                                          const Scene *scenes, int ga, int gb, ContactIn<R> &c)
+{
+    const Scene &sc = scenes[mat_scene[ga]];
+    const PairParam p = pairs[sc.pair_base + (int)mat_local[ga] * sc.n_mat + (int)mat_local[gb]];
+    c.Estar = (R)p.Estar;
+    c.Gstar = (R)p.Gstar;
+    c.beta = (R)p.beta;
+    c.mu = (R)p.mu;
+}
+
+// Signed gap of a sphere centre to a wall (positive on the domain side) and the unit
+// normal from the wall to the centre; FP64, every product and sum rounded in a fixed
+// order.  Returns false where the normal is undefined (centre on an axis).
+__device__ __forceinline__ bool wall_gap(const Wall &w, V3<double> c, double &gap, V3<double> &n)
+{
+    V3<double> d = {rsub(c.x, w.p[0]), rsub(c.y, w.p[1]), rsub(c.z, w.p[2])};
+    double z = radd(radd(rmul(d.x, w.n[0]), rmul(d.y, w.n[1])), rmul(d.z, w.n[2]));
+    if (w.type == WALL_PLANE) {
+        gap = z;
+        n = {w.n[0], w.n[1], w.n[2]};
+        return true;
+    }
+    V3<double> rp = {rsub(d.x, rmul(z, w.n[0])), rsub(d.y, rmul(z, w.n[1])), rsub(d.z, rmul(z, w.n[2]))};
+    double rho = __dsqrt_rn(radd(radd(rmul(rp.x, rp.x), rmul(rp.y, rp.y)), rmul(rp.z, rp.z)));
+    if (w.type == WALL_CYLINDER) {
+        gap = rsub(w.r0, rho);
+        if (!(rho > 0.0)) return false;
+        n = {-__ddiv_rn(rp.x, rho), -__ddiv_rn(rp.y, rho), -__ddiv_rn(rp.z, rho)};
+        return true;
+    }
+    // cone segment in the (rho, z) half plane
+    double dr = rsub(w.r1, w.r0), dz = rsub(w.z1, w.z0);
+    double len2 = radd(rmul(dr, dr), rmul(dz, dz));
+    double t = __ddiv_rn(radd(rmul(rsub(rho, w.r0), dr), rmul(rsub(z, w.z0), dz)), len2);
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    double cr = radd(w.r0, rmul(t, dr)), cz = radd(w.z0, rmul(t, dz));
+    double Dr = rsub(rho, cr), Dz = rsub(z, cz);
+    double dist = __dsqrt_rn(radd(rmul(Dr, Dr), rmul(Dz, Dz)));
+    double len = __dsqrt_rn(len2);
+    double inr = -__ddiv_rn(dz, len), inz = __ddiv_rn(dr, len);
+    if (inr > 0.0) { inr = -inr; inz = -inz; }
+    double side = radd(rmul(Dr, inr), rmul(Dz, inz));
+    double sg = side >= 0.0 ? 1.0 : -1.0;
+    gap = sg * dist;
+    if (!(rho > 0.0) || !(dist > 0.0)) return false;
+    double n2r = __ddiv_rn(sg * Dr, dist), n2z = __ddiv_rn(sg * Dz, dist);
+    V3<double> er = {__ddiv_rn(rp.x, rho), __ddiv_rn(rp.y, rho), __ddiv_rn(rp.z, rho)};
+    n = {radd(rmul(n2r, er.x), rmul(n2z, w.n[0])), radd(rmul(n2r, er.y), rmul(n2z, w.n[1])),
+         radd(rmul(n2r, er.z), rmul(n2z, w.n[2]))};
+    return true;
+}
+
+}  // namespace dem

@@ -1,0 +1,90 @@
+// engine.h -- host-side flattened world and the engine interface between the C ABI
+// (api.cu) and the per-form engines (engine_f64.cu, engine_f32.cu).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dem.h"
+#include "common.cuh"
+
+namespace dem {
+
+// A world (all scenes of a batch) flattened to the arrays the engines upload.
+struct HostModel {
+    int precision = DEM_PRECISION_FP64_PLAIN;
+    int schedule = DEM_SCHEDULE_EVERY_STEP;
+    int gyroscopic = 1;
+    int device = 0;
+    double L = 0.0;                 // cell (= voxel) edge
+    double margin = 0.0;            // margin of the lists (EVERY_STEP) / upper bound (delayed)
+    double margin_max = 0.0;
+    double r_max = 0.0;
+    std::vector<Scene> scenes;
+    std::vector<Wall> walls;
+    std::vector<PairParam> pairs;
+    std::vector<uint16_t> mat_scene, mat_local;
+    // owners, M
+    std::vector<double> x, q, v, wb, mass, moi, r_ext;
+    std::vector<uint16_t> owner_scene;
+    std::vector<uint8_t> owner_iso;
+    std::vector<int64_t> owner_first_slot;
+    std::vector<int32_t> owner_nsph;
+    // sphere slots, N (padding slots included)
+    std::vector<uint32_t> sph_owner;
+    std::vector<double> sph_rloc, sph_rad;
+    std::vector<uint16_t> sph_mat;
+    std::vector<uint8_t> sph_head, sph_segend;
+    std::vector<int64_t> slot_of_sphere, sphere_of_slot;
+    bool clumps = false;
+    uint32_t n_cells_total = 0;
+    // per scene: first owner id and first user sphere id in the flattened order
+    std::vector<int64_t> scene_owner_base, scene_sphere_base, scene_wall_base;
+    void *stream = nullptr, *detect_stream = nullptr;
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*free)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    // learned schedule weights (may be empty)
+    std::vector<uint8_t> schedule_model;
+};
+
+struct ContactOut {
+    int64_t i, j;                   // user sphere ids; j = -1 - wall for walls
+    double force[3], point[3], overlap, hist[3];
+};
+
+class EngineBase {
+public:
+    virtual ~EngineBase() {}
+    virtual dem_status init(HostModel &m, std::string &err) = 0;
+    virtual dem_status step(int64_t n, std::string &err) = 0;
+    virtual dem_status sync(std::string &err) = 0;
+    virtual void *stream() = 0;
+    virtual dem_status owner_state(int64_t first, int64_t n, double *x, double *q, double *v, double *w,
+                                   std::string &err) = 0;
+    virtual dem_status set_owner_state(int64_t first, int64_t n, const double *x, const double *q, const double *v,
+                                       const double *w, std::string &err) = 0;
+    virtual dem_status sphere_positions(int64_t first, int64_t n, double *xyz, double *r, int32_t *cell, float *off,
+                                        std::string &err) = 0;
+    virtual dem_status contacts(std::vector<ContactOut> &out, std::string &err) = 0;
+    virtual dem_status listed(std::vector<int64_t> &i, std::vector<int64_t> &j, std::vector<int64_t> &si,
+                              std::vector<int64_t> &wi, std::string &err) = 0;
+    virtual dem_status owner_forces(std::vector<double> &F, std::vector<double> &T, std::string &err) = 0;
+    virtual dem_status set_history(int64_t k, const int64_t *i, const int64_t *j, const double *ut,
+                                   std::string &err) = 0;
+    virtual dem_status stats(dem_stats *s, std::string &err) = 0;
+    virtual dem_status diagnostics(dem_diagnostics *d, std::string &err) = 0;
+    virtual dem_status save(std::vector<uint8_t> &blob, std::string &err) = 0;
+    virtual dem_status load(const uint8_t *blob, size_t n, std::string &err) = 0;
+    virtual dem_status set_margin(double beta, std::string &err) = 0;
+    virtual void set_profiling(bool on) = 0;
+    virtual dem_status schedule_collect(int on, std::string &err) = 0;
+    virtual dem_status schedule_train(int epochs, float lr, uint64_t seed, float *loss, std::string &err) = 0;
+    virtual dem_status schedule_export(std::vector<uint8_t> &w, std::string &err) = 0;
+    virtual dem_status schedule_load(const uint8_t *w, size_t n, std::string &err) = 0;
+};
+
+EngineBase *make_engine_f64();
+EngineBase *make_engine_f32();
+
+}  // namespace dem

@@ -1,0 +1,1027 @@
+// engine_impl.cuh -- host orchestration of the pipeline for one position form.
+//
+// Streams: the force stream runs the per-step work (force + integration + audit) and the
+// list switch; the detection stream runs the sort, cell tables and narrow phase of the
+// next list from a snapshot, concurrently (Sec. 2.1: contact detection and dynamics as
+// two concurrent workers, here two CUDA streams on one GPU instead of two GPUs).
+// All control state lives on the device (DevStatus): kernels pick the buffers and skip
+// themselves when the list in use went stale or the run halted, so queued work never
+// needs host decisions; the host reads the status at cycle ends and recovers
+// (audit fallback rebuild, list capacity regrow, divergence report).
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "pipeline.cuh"
+
+namespace dem {
+
+#define DEM_CU(call)                                                                  \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return DEM_ERR_CUDA;                                                      \
+        }                                                                             \
+    } while (0)
+
+template <class F>
+class Engine : public EngineBase {
+    using R = typename F::R;
+    using R4 = typename F::R4;
+
+public:
+    ~Engine() override { release(); }
+
+    dem_status init(HostModel &m, std::string &err) override
+    {
+        m_ = m;
+        DEM_CU(cudaSetDevice(m_.device));
+        if (m_.stream) {
+            sf_ = (cudaStream_t)m_.stream;
+        } else {
+            DEM_CU(cudaStreamCreateWithFlags(&sf_, cudaStreamNonBlocking));
+            own_sf_ = true;
+        }
+        if (m_.detect_stream) {
+            sd_ = (cudaStream_t)m_.detect_stream;
+        } else {
+            DEM_CU(cudaStreamCreateWithFlags(&sd_, cudaStreamNonBlocking));
+            own_sd_ = true;
+        }
+        DEM_CU(cudaEventCreateWithFlags(&ev_snap_, cudaEventDisableTiming));
+        DEM_CU(cudaEventCreateWithFlags(&ev_det_, cudaEventDisableTiming));
+        DEM_CU(cudaEventCreate(&ev_a_));
+        DEM_CU(cudaEventCreate(&ev_b_));
+        DEM_CU(cudaEventCreate(&ev_c_));
+
+        const int64_t M = (int64_t)m_.mass.size();
+        const int64_t N = (int64_t)m_.sph_owner.size();
+        d_.M = M;
+        d_.N = N;
+        d_.Np = std::max<int64_t>(32, (N + 31) / 32 * 32);
+        d_.K = 16;
+        d_.L = (float)m_.L;
+        d_.Ld = m_.L;
+        d_.invL = 1.0 / m_.L;
+        d_.gyro = m_.gyroscopic;
+        d_.n_scenes = (int)m_.scenes.size();
+        beta_ = m_.margin;
+        const int64_t Np = d_.Np;
+
+        dem_status s;
+        // owner state, double-buffered
+        for (int b = 0; b < 2; ++b) {
+            if constexpr (F::voxel) {
+                if ((s = alloc(d_.st.pos[b].vox, M, err))) return s;
+                if ((s = alloc(d_.st.pos[b].om, M, err))) return s;
+            } else {
+                if ((s = alloc(d_.st.pos[b].xm, M, err))) return s;
+            }
+            if ((s = alloc(d_.st.vel[b], M, err))) return s;
+            if ((s = alloc(d_.st.omg[b], M, err))) return s;
+            if ((s = alloc(d_.st.quat[b], M, err))) return s;
+            if ((s = alloc(d_.st.active[b], M, err))) return s;
+        }
+        if ((s = alloc(d_.inv_moi, M, err))) return s;
+        if ((s = alloc(d_.inv_mass, M, err))) return s;
+        if ((s = alloc(d_.owner_scene, M, err))) return s;
+        if ((s = alloc(d_.owner_iso, M, err))) return s;
+        if ((s = alloc(d_.sph_owner, N, err))) return s;
+        if ((s = alloc(d_.sph_rad, N, err))) return s;
+        if ((s = alloc(d_.sph_mat, N, err))) return s;
+        if ((s = alloc(d_.sph_rloc, N, err))) return s;
+        if ((s = alloc(d_.sph_head, N, err))) return s;
+        if ((s = alloc(d_.sph_segend, N, err))) return s;
+        Scene *scenes;
+        Wall *walls;
+        PairParam *pairs;
+        uint16_t *ms, *ml;
+        if ((s = alloc(scenes, m_.scenes.size(), err))) return s;
+        if ((s = alloc(walls, std::max<size_t>(1, m_.walls.size()), err))) return s;
+        if ((s = alloc(pairs, m_.pairs.size(), err))) return s;
+        if ((s = alloc(ms, m_.mat_scene.size(), err))) return s;
+        if ((s = alloc(ml, m_.mat_local.size(), err))) return s;
+        d_.scenes = scenes; d_.walls = walls; d_.pairs = pairs; d_.mat_scene = ms; d_.mat_local = ml;
+        if ((s = alloc(st_, 1, err))) return s;
+        DEM_CU(cudaMallocHost((void **)&sth_, sizeof(DevStatus)));
+        if ((s = alloc_lists(d_.K, err))) return s;
+
+        // detection buffers
+        db_.n = N;
+        db_.n_cells_total = m_.n_cells_total;
+        db_.key_bits = 1;
+        while (db_.key_bits < 32 && ((uint64_t)1 << db_.key_bits) <= (uint64_t)m_.n_cells_total) ++db_.key_bits;
+        const int64_t Nk = std::max<int64_t>(N, 1);
+        if ((s = alloc(db_.keys, Nk, err))) return s;
+        if ((s = alloc(db_.vals, Nk, err))) return s;
+        if ((s = alloc(db_.keys_alt, Nk, err))) return s;
+        if ((s = alloc(db_.vals_alt, Nk, err))) return s;
+        db_.hist_cap = radix_hist_entries(Nk);
+        if ((s = alloc(db_.hist, db_.hist_cap, err))) return s;
+        if ((s = alloc(db_.cell_start, (int64_t)m_.n_cells_total + 1, err))) return s;
+        if ((s = alloc(db_.cell_end, (int64_t)m_.n_cells_total + 1, err))) return s;
+        if (F::voxel) {
+            int4 *a; float4 *b2; int4 *c; float4 *e;
+            if ((s = alloc(a, Nk, err))) return s;
+            if ((s = alloc(b2, Nk, err))) return s;
+            if ((s = alloc(c, Nk, err))) return s;
+            if ((s = alloc(e, Nk, err))) return s;
+            db_.snap = a; db_.snap_aux = b2; db_.sorted = c; db_.sorted_aux = e;
+        } else {
+            double4_32a *a, *c;
+            if ((s = alloc(a, Nk, err))) return s;
+            if ((s = alloc(c, Nk, err))) return s;
+            db_.snap = a; db_.sorted = c; db_.snap_aux = nullptr; db_.sorted_aux = nullptr;
+        }
+        if ((s = alloc(db_.sorted_owner, Nk, err))) return s;
+        if ((s = alloc(db_.n_valid, 1, err))) return s;
+
+        // constants
+        std::vector<R4> inv_moi(M);
+        std::vector<R> inv_mass(M);
+        for (int64_t o = 0; o < M; ++o) {
+            inv_moi[o] = R4{(R)(1.0 / m_.moi[3 * o]), (R)(1.0 / m_.moi[3 * o + 1]), (R)(1.0 / m_.moi[3 * o + 2]),
+                            (R)m_.r_ext[o]};
+            inv_mass[o] = (R)(1.0 / m_.mass[o]);
+        }
+        std::vector<R> rad(N);
+        std::vector<R4> rloc(N);
+        for (int64_t k = 0; k < N; ++k) {
+            rad[k] = (R)m_.sph_rad[k];
+            rloc[k] = R4{(R)m_.sph_rloc[3 * k], (R)m_.sph_rloc[3 * k + 1], (R)m_.sph_rloc[3 * k + 2], R(0)};
+        }
+        if ((s = up(d_.inv_moi, inv_moi.data(), M, err))) return s;
+        if ((s = up(d_.inv_mass, inv_mass.data(), M, err))) return s;
+        if ((s = up(d_.owner_scene, m_.owner_scene.data(), M, err))) return s;
+        if ((s = up(d_.owner_iso, m_.owner_iso.data(), M, err))) return s;
+        if ((s = up(d_.sph_owner, m_.sph_owner.data(), N, err))) return s;
+        if ((s = up(d_.sph_rad, rad.data(), N, err))) return s;
+        if ((s = up(d_.sph_mat, m_.sph_mat.data(), N, err))) return s;
+        if ((s = up(d_.sph_rloc, rloc.data(), N, err))) return s;
+        if ((s = up(d_.sph_head, m_.sph_head.data(), N, err))) return s;
+        if ((s = up(d_.sph_segend, m_.sph_segend.data(), N, err))) return s;
+        if ((s = up(scenes, m_.scenes.data(), m_.scenes.size(), err))) return s;
+        if (!m_.walls.empty() && (s = up(walls, m_.walls.data(), m_.walls.size(), err))) return s;
+        if ((s = up(pairs, m_.pairs.data(), m_.pairs.size(), err))) return s;
+        if ((s = up(ms, m_.mat_scene.data(), m_.mat_scene.size(), err))) return s;
+        if ((s = up(ml, m_.mat_local.data(), m_.mat_local.size(), err))) return s;
+
+        // mass into the position store of buffer 0, then the state through the upload kernel
+        if constexpr (F::voxel) {
+            std::vector<float4> om(M);
+            for (int64_t o = 0; o < M; ++o) om[o] = make_float4(0.f, 0.f, 0.f, (float)m_.mass[o]);
+            if ((s = up(d_.st.pos[0].om, om.data(), M, err))) return s;
+        } else {
+            std::vector<double4_32a> xm(M);
+            for (int64_t o = 0; o < M; ++o) xm[o] = make_double4_32a(0.0, 0.0, 0.0, m_.mass[o]);
+            if ((s = up(d_.st.pos[0].xm, xm.data(), M, err))) return s;
+        }
+        DevStatus h{};
+        h.disp_slack = F::voxel ? 4.0 * (double)std::ldexp(1.0f, std::ilogb((float)m_.L) - 23) : 0.0;
+        h.beta_cur = h.beta_next = beta_;
+        for (int64_t o = 0; o < M; ++o) {   // initial speed bound for the first cycle length
+            double v2 = m_.v[3 * o] * m_.v[3 * o] + m_.v[3 * o + 1] * m_.v[3 * o + 1] + m_.v[3 * o + 2] * m_.v[3 * o + 2];
+            double w2 = m_.wb[3 * o] * m_.wb[3 * o] + m_.wb[3 * o + 1] * m_.wb[3 * o + 1] + m_.wb[3 * o + 2] * m_.wb[3 * o + 2];
+            h.vmax_last = std::max(h.vmax_last, std::sqrt(v2) + std::sqrt(w2) * m_.r_ext[o]);
+        }
+        if ((s = up(st_, &h, 1, err))) return s;
+        d_.status = st_;
+        {
+            std::vector<uint8_t> act(M, 1);
+            if ((s = upload_state(0, M, m_.x.data(), m_.q.data(), m_.v.data(), m_.wb.data(), act.data(), err)))
+                return s;
+        }
+        if (N > 0) {
+            rebuild_inline(sf_);
+            if ((s = settle(err))) return s;
+        }
+        return DEM_OK;
+    }
+
+    dem_status step(int64_t n, std::string &err) override
+    {
+        if (n < 0) { err = "negative step count"; return DEM_ERR_ARG; }
+        dem_status s;
+        if ((s = pull(err))) return s;
+        const long long target = sth_->steps_done + n;
+        if (dirty_) {
+            rebuild_inline(sf_);
+            if ((s = settle(err))) return s;
+            dirty_ = false;
+        }
+        DEM_CU(cudaEventRecord(ev_a_, sf_));
+        while (true) {
+            if ((s = pull(err))) return s;
+            long long left = target - sth_->steps_done;
+            if (left <= 0) break;
+            if (sth_->list_stale) {          // audit fallback: rebuild from the current state
+                fallbacks_ += 1;
+                rebuild_inline(sf_);
+                if ((s = settle(err))) return s;
+                continue;
+            }
+            if (m_.schedule == DEM_SCHEDULE_EVERY_STEP || d_.N == 0) {
+                long long chunk = std::min<long long>(left, 256);
+                for (long long k = 0; k < chunk; ++k) {
+                    if (d_.N > 0) rebuild_inline(sf_);
+                    force_step();
+                }
+            } else {
+                long long c = std::min<long long>(left, cycle_length());
+                start_detect();
+                for (long long k = 0; k < c; ++k) force_step();
+                finish_detect();
+            }
+            if ((s = settle(err))) return s;
+        }
+        DEM_CU(cudaEventRecord(ev_b_, sf_));
+        DEM_CU(cudaEventSynchronize(ev_b_));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev_a_, ev_b_);
+        ms_total_ += ms;
+        return DEM_OK;
+    }
+
+    dem_status sync(std::string &err) override
+    {
+        DEM_CU(cudaStreamSynchronize(sf_));
+        DEM_CU(cudaStreamSynchronize(sd_));
+        return DEM_OK;
+    }
+
+    void *stream() override { return (void *)sf_; }
+
+    dem_status owner_state(int64_t first, int64_t n, double *x, double *q, double *v, double *w,
+                           std::string &err) override
+    {
+        if (n <= 0) return DEM_OK;
+        double *buf;
+        dem_status s;
+        if ((s = scratch(buf, 13 * n, err))) return s;
+        k_owner_download<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, buf, buf + 3 * n, buf + 7 * n, buf + 10 * n);
+        DEM_CU(cudaGetLastError());
+        std::vector<double> h(13 * n);
+        DEM_CU(cudaMemcpyAsync(h.data(), buf, 13 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        if (x) std::memcpy(x, h.data(), 3 * n * sizeof(double));
+        if (q) std::memcpy(q, h.data() + 3 * n, 4 * n * sizeof(double));
+        if (v) std::memcpy(v, h.data() + 7 * n, 3 * n * sizeof(double));
+        if (w) std::memcpy(w, h.data() + 10 * n, 3 * n * sizeof(double));
+        return DEM_OK;
+    }
+
+    dem_status set_owner_state(int64_t first, int64_t n, const double *x, const double *q, const double *v,
+                               const double *w, std::string &err) override
+    {
+        dem_status s;
+        if ((s = upload_state(first, n, x, q, v, w, nullptr, err))) return s;
+        if (x || q) dirty_ = true;
+        return DEM_OK;
+    }
+
+    dem_status sphere_positions(int64_t first, int64_t n, double *xyz, double *r, int32_t *cell, float *off,
+                                std::string &err) override
+    {
+        if (n <= 0) return DEM_OK;
+        dem_status s;
+        int64_t *slots;
+        double *buf;
+        int *cb;
+        float *ob;
+        if ((s = scratch(buf, 4 * n + 3 * n + 2 * n, err))) return s;   // xyz, r, cell (as int), off
+        slots = reinterpret_cast<int64_t *>(buf + 4 * n);
+        cb = reinterpret_cast<int *>(buf + 5 * n);
+        ob = reinterpret_cast<float *>(buf + 7 * n);
+        DEM_CU(cudaMemcpyAsync(slots, m_.slot_of_sphere.data() + first, n * sizeof(int64_t), cudaMemcpyHostToDevice, sf_));
+        if (m_.clumps)
+            k_sphere_download<F, true><<<grid(n, 256), 256, 0, sf_>>>(d_, slots, n, buf, buf + 3 * n, cb, ob);
+        else
+            k_sphere_download<F, false><<<grid(n, 256), 256, 0, sf_>>>(d_, slots, n, buf, buf + 3 * n, cb, ob);
+        DEM_CU(cudaGetLastError());
+        std::vector<double> h(4 * n);
+        DEM_CU(cudaMemcpyAsync(h.data(), buf, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        std::vector<int> hc(3 * n);
+        std::vector<float> ho(3 * n);
+        if (F::voxel) {
+            DEM_CU(cudaMemcpyAsync(hc.data(), cb, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, sf_));
+            DEM_CU(cudaMemcpyAsync(ho.data(), ob, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, sf_));
+        }
+        DEM_CU(cudaStreamSynchronize(sf_));
+        if (xyz) std::memcpy(xyz, h.data(), 3 * n * sizeof(double));
+        if (r) std::memcpy(r, h.data() + 3 * n, n * sizeof(double));
+        if (cell) {
+            if (!F::voxel) { err = "voxel encoding exists only in the VOXEL_FP32 form"; return DEM_ERR_STATE; }
+            std::memcpy(cell, hc.data(), 3 * n * sizeof(int));
+            if (off) std::memcpy(off, ho.data(), 3 * n * sizeof(float));
+        }
+        return DEM_OK;
+    }
+
+    dem_status contacts(std::vector<ContactOut> &out, std::string &err) override
+    {
+        out.clear();
+        dem_status s;
+        if ((s = pull(err))) return s;
+        const int64_t N = d_.N, K = d_.K, Np = d_.Np;
+        if (N == 0) return DEM_OK;
+        double *buf;
+        const int64_t ne = K * Np;
+        if ((s = scratch(buf, 10 * ne, err))) return s;
+        if (m_.clumps)
+            k_contacts<F, true><<<grid(N, 128), 128, 0, sf_>>>(d_, buf, buf + ne, buf + 4 * ne, buf + 7 * ne);
+        else
+            k_contacts<F, false><<<grid(N, 128), 128, 0, sf_>>>(d_, buf, buf + ne, buf + 4 * ne, buf + 7 * ne);
+        DEM_CU(cudaGetLastError());
+        std::vector<double> h(10 * ne);
+        DEM_CU(cudaMemcpyAsync(h.data(), buf, 10 * ne * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        std::vector<uint32_t> partner;
+        std::vector<uint8_t> cnt;
+        if ((s = fetch_list(sth_->list_cur, partner, cnt, err))) return s;
+        for (int64_t sl = 0; sl < N; ++sl) {
+            int64_t ui = m_.sphere_of_slot[sl];
+            if (ui < 0) continue;
+            for (int k = 0; k < cnt[sl]; ++k) {
+                int64_t e = (int64_t)k * Np + sl;
+                uint32_t j = partner[e];
+                if (!(j & WALL_BIT) && j < (uint32_t)sl) continue;
+                if (!(h[e] > 0.0)) continue;
+                ContactOut c;
+                c.i = ui;
+                c.j = (j & WALL_BIT) ? -1 - wall_local(j & ~WALL_BIT) : m_.sphere_of_slot[j];
+                for (int a = 0; a < 3; ++a) {
+                    c.force[a] = h[ne + 3 * e + a];
+                    c.point[a] = h[4 * ne + 3 * e + a];
+                    c.hist[a] = h[7 * ne + 3 * e + a];
+                }
+                c.overlap = h[e];
+                out.push_back(c);
+            }
+        }
+        return DEM_OK;
+    }
+
+    dem_status listed(std::vector<int64_t> &pi, std::vector<int64_t> &pj, std::vector<int64_t> &si,
+                      std::vector<int64_t> &wi, std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        std::vector<uint32_t> partner;
+        std::vector<uint8_t> cnt;
+        if ((s = fetch_list(sth_->list_cur, partner, cnt, err))) return s;
+        pi.clear(); pj.clear(); si.clear(); wi.clear();
+        for (int64_t sl = 0; sl < d_.N; ++sl) {
+            int64_t ui = m_.sphere_of_slot[sl];
+            if (ui < 0) continue;
+            for (int k = 0; k < cnt[sl]; ++k) {
+                uint32_t j = partner[(int64_t)k * d_.Np + sl];
+                if (j & WALL_BIT) {
+                    si.push_back(ui);
+                    wi.push_back(wall_local(j & ~WALL_BIT));
+                } else if (j > (uint32_t)sl) {
+                    pi.push_back(ui);
+                    pj.push_back(m_.sphere_of_slot[j]);
+                }
+            }
+        }
+        return DEM_OK;
+    }
+
+    dem_status owner_forces(std::vector<double> &Fo, std::vector<double> &To, std::string &err) override
+    {
+        const int64_t M = d_.M;
+        Fo.assign(3 * M, 0.0);
+        To.assign(3 * M, 0.0);
+        if (M == 0) return DEM_OK;
+        double *buf;
+        dem_status s;
+        if ((s = scratch(buf, 6 * M, err))) return s;
+        launch_force<MODE_EVAL>(buf, buf + 3 * M);
+        DEM_CU(cudaGetLastError());
+        DEM_CU(cudaMemcpyAsync(Fo.data(), buf, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaMemcpyAsync(To.data(), buf + 3 * M, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        return DEM_OK;
+    }
+
+    dem_status set_history(int64_t nk, const int64_t *ii, const int64_t *jj, const double *ut,
+                           std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        std::vector<uint32_t> partner;
+        std::vector<uint8_t> cnt;
+        if ((s = fetch_list(sth_->list_cur, partner, cnt, err))) return s;
+        const int64_t ne = (int64_t)d_.K * d_.Np;
+        std::vector<R> hx(ne, R(0)), hy(ne, R(0)), hz(ne, R(0));
+        for (int64_t q = 0; q < nk; ++q) {
+            if (ii[q] < 0 || ii[q] >= (int64_t)m_.slot_of_sphere.size()) continue;
+            int64_t sl = m_.slot_of_sphere[ii[q]];
+            uint32_t key;
+            if (jj[q] >= 0) {
+                if (jj[q] >= (int64_t)m_.slot_of_sphere.size()) continue;
+                int64_t sj = m_.slot_of_sphere[jj[q]];
+                if (sj < sl) continue;
+                key = (uint32_t)sj;
+            } else {
+                int scene = m_.owner_scene[m_.sph_owner[sl]];
+                key = WALL_BIT | (uint32_t)(m_.scene_wall_base[scene] + (-1 - jj[q]));
+            }
+            for (int k = 0; k < cnt[sl]; ++k) {
+                int64_t e = (int64_t)k * d_.Np + sl;
+                if (partner[e] == key) {
+                    hx[e] = (R)ut[3 * q]; hy[e] = (R)ut[3 * q + 1]; hz[e] = (R)ut[3 * q + 2];
+                }
+            }
+        }
+        const int hp = sth_->hist_par;
+        DEM_CU(cudaMemcpyAsync(d_.lists.hx[hp], hx.data(), ne * sizeof(R), cudaMemcpyHostToDevice, sf_));
+        DEM_CU(cudaMemcpyAsync(d_.lists.hy[hp], hy.data(), ne * sizeof(R), cudaMemcpyHostToDevice, sf_));
+        DEM_CU(cudaMemcpyAsync(d_.lists.hz[hp], hz.data(), ne * sizeof(R), cudaMemcpyHostToDevice, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        return DEM_OK;
+    }
+
+    dem_status stats(dem_stats *o, std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        std::memset(o, 0, sizeof(*o));
+        o->steps = sth_->steps_done;
+        o->rebuilds = sth_->rebuilds;
+        o->audit_fallbacks = fallbacks_;
+        o->overflow_regrows = regrows_;
+        o->list_capacity = d_.K;
+        o->list_max_row = sth_->max_row;
+        o->margin = sth_->beta_cur;
+        o->displacement_bound = sth_->disp_cur;
+        o->max_speed = sth_->vmax_last;
+        o->mean_steps_per_build = sth_->rebuilds > 0 ? (double)sth_->steps_done / (double)sth_->rebuilds : 0.0;
+        o->cell_size = m_.L;
+        o->n_cells = m_.n_cells_total;
+        o->ms_force = prof_ms_[P_FORCE];
+        o->ms_detect = prof_ms_[P_DETECT];
+        o->ms_hash = prof_ms_[P_HASH];
+        o->ms_link = prof_ms_[P_LINK];
+        o->n_force = prof_n_[P_FORCE];
+        o->n_detect = prof_n_[P_DETECT];
+        o->ms_total = ms_total_;
+        if (d_.N > 0) {
+            double *buf;
+            if ((s = scratch(buf, 3, err))) return s;
+            unsigned long long *cnt = reinterpret_cast<unsigned long long *>(buf);
+            DEM_CU(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), sf_));
+            if (m_.clumps) k_count<F, true><<<grid(d_.N, 256), 256, 0, sf_>>>(d_, cnt);
+            else k_count<F, false><<<grid(d_.N, 256), 256, 0, sf_>>>(d_, cnt);
+            DEM_CU(cudaGetLastError());
+            unsigned long long h[3];
+            DEM_CU(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, sf_));
+            DEM_CU(cudaStreamSynchronize(sf_));
+            o->listed_pairs = (int64_t)h[0];
+            o->wall_pairs = (int64_t)h[1];
+            o->active_contacts = (int64_t)h[2];
+        }
+        return DEM_OK;
+    }
+
+    dem_status diagnostics(dem_diagnostics *o, std::string &err) override
+    {
+        const int64_t n = std::max<int64_t>(std::max<int64_t>(d_.M, d_.N), 1);
+        const int64_t blocks = (n + 255) / 256;
+        double *buf;
+        dem_status s;
+        if ((s = scratch(buf, 9 * blocks, err))) return s;
+        if (m_.clumps) k_diag<F, true><<<(unsigned)blocks, 256, 0, sf_>>>(d_, buf);
+        else k_diag<F, false><<<(unsigned)blocks, 256, 0, sf_>>>(d_, buf);
+        DEM_CU(cudaGetLastError());
+        std::vector<double> h(9 * blocks);
+        DEM_CU(cudaMemcpyAsync(h.data(), buf, h.size() * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t b = 0; b < blocks; ++b)
+            for (int c = 0; c < 9; ++c) a[c] += h[9 * b + c];
+        o->kinetic = a[0];
+        o->potential = a[1];
+        o->elastic = a[2];
+        for (int c = 0; c < 3; ++c) {
+            o->momentum[c] = a[3 + c];
+            o->angular_momentum[c] = a[6 + c];
+        }
+        return DEM_OK;
+    }
+
+    dem_status save(std::vector<uint8_t> &blob, std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        blob.clear();
+        const int64_t M = d_.M, ne = (int64_t)d_.K * d_.Np;
+        const int sp = sth_->state_par, hp = sth_->hist_par, lc = sth_->list_cur;
+        auto put = [&](const void *p, size_t n) {
+            size_t o = blob.size();
+            blob.resize(o + n);
+            std::memcpy(blob.data() + o, p, n);
+        };
+        uint64_t magic = 0x44454d4742333030ull;   // "DEMGB300"
+        put(&magic, 8);
+        int64_t hdr[6] = {M, d_.N, d_.Np, d_.K, (int64_t)F::voxel, (int64_t)sizeof(R)};
+        put(hdr, sizeof(hdr));
+        put(sth_, sizeof(DevStatus));
+        auto dput = [&](const void *dp, size_t n) -> dem_status {
+            size_t o = blob.size();
+            blob.resize(o + n);
+            if (n) DEM_CU(cudaMemcpy(blob.data() + o, dp, n, cudaMemcpyDeviceToHost));
+            return DEM_OK;
+        };
+        if constexpr (F::voxel) {
+            if ((s = dput(d_.st.pos[sp].vox, M * 8))) return s;
+            if ((s = dput(d_.st.pos[sp].om, M * 16))) return s;
+        } else {
+            if ((s = dput(d_.st.pos[sp].xm, M * 32))) return s;
+        }
+        if ((s = dput(d_.st.vel[sp], M * sizeof(R4)))) return s;
+        if ((s = dput(d_.st.omg[sp], M * sizeof(R4)))) return s;
+        if ((s = dput(d_.st.quat[sp], M * sizeof(R4)))) return s;
+        if ((s = dput(d_.st.active[sp], M))) return s;
+        if ((s = dput(d_.lists.partner[lc], ne * 4))) return s;
+        if ((s = dput(d_.lists.mirror[lc], ne))) return s;
+        if ((s = dput(d_.lists.cnt[lc], d_.Np))) return s;
+        if ((s = dput(d_.lists.hx[hp], ne * sizeof(R)))) return s;
+        if ((s = dput(d_.lists.hy[hp], ne * sizeof(R)))) return s;
+        if ((s = dput(d_.lists.hz[hp], ne * sizeof(R)))) return s;
+        double extra[2] = {beta_, (double)fallbacks_};
+        put(extra, sizeof(extra));
+        return DEM_OK;
+    }
+
+    dem_status load(const uint8_t *blob, size_t nb, std::string &err) override
+    {
+        size_t off = 0;
+        auto get = [&](void *p, size_t n) -> bool {
+            if (off + n > nb) return false;
+            std::memcpy(p, blob + off, n);
+            off += n;
+            return true;
+        };
+        uint64_t magic;
+        int64_t hdr[6];
+        DevStatus h;
+        if (!get(&magic, 8) || magic != 0x44454d4742333030ull || !get(hdr, sizeof(hdr)) || !get(&h, sizeof(h))) {
+            err = "not a state blob";
+            return DEM_ERR_ARG;
+        }
+        if (hdr[0] != d_.M || hdr[1] != d_.N || hdr[2] != d_.Np || hdr[4] != (int64_t)F::voxel ||
+            hdr[5] != (int64_t)sizeof(R)) {
+            err = "state blob of a different world";
+            return DEM_ERR_ARG;
+        }
+        dem_status s;
+        if (hdr[3] != d_.K) {
+            if ((s = realloc_lists((int)hdr[3], false, err))) return s;
+        }
+        DEM_CU(cudaStreamSynchronize(sf_));
+        DEM_CU(cudaStreamSynchronize(sd_));
+        const int64_t M = d_.M, ne = (int64_t)d_.K * d_.Np;
+        const int sp = h.state_par, hp = h.hist_par, lc = h.list_cur;
+        auto dget = [&](void *dp, size_t n) -> dem_status {
+            if (off + n > nb) { err = "truncated state blob"; return DEM_ERR_ARG; }
+            if (n) DEM_CU(cudaMemcpy(dp, blob + off, n, cudaMemcpyHostToDevice));
+            off += n;
+            return DEM_OK;
+        };
+        if constexpr (F::voxel) {
+            if ((s = dget(d_.st.pos[sp].vox, M * 8))) return s;
+            if ((s = dget(d_.st.pos[sp].om, M * 16))) return s;
+        } else {
+            if ((s = dget(d_.st.pos[sp].xm, M * 32))) return s;
+        }
+        if ((s = dget(d_.st.vel[sp], M * sizeof(R4)))) return s;
+        if ((s = dget(d_.st.omg[sp], M * sizeof(R4)))) return s;
+        if ((s = dget(d_.st.quat[sp], M * sizeof(R4)))) return s;
+        if ((s = dget(d_.st.active[sp], M))) return s;
+        if ((s = dget(d_.lists.partner[lc], ne * 4))) return s;
+        if ((s = dget(d_.lists.mirror[lc], ne))) return s;
+        if ((s = dget(d_.lists.cnt[lc], d_.Np))) return s;
+        if ((s = dget(d_.lists.hx[hp], ne * sizeof(R)))) return s;
+        if ((s = dget(d_.lists.hy[hp], ne * sizeof(R)))) return s;
+        if ((s = dget(d_.lists.hz[hp], ne * sizeof(R)))) return s;
+        double extra[2];
+        if (!get(extra, sizeof(extra))) { err = "truncated state blob"; return DEM_ERR_ARG; }
+        beta_ = extra[0];
+        fallbacks_ = (int64_t)extra[1];
+        h.halt = 0;
+        h.step_disp_bits = 0;
+        h.vmax_bits = 0;
+        h.diverged = 0;
+        DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
+        dirty_ = false;
+        return DEM_OK;
+    }
+
+    void set_profiling(bool on) override { prof_ = on; }
+
+    dem_status set_margin(double beta, std::string &err) override
+    {
+        (void)err;
+        beta_ = beta;
+        dirty_ = true;
+        return DEM_OK;
+    }
+
+    dem_status schedule_collect(int on, std::string &err) override
+    {
+        (void)on;
+        err = "schedule collection is not built into this engine";
+        return DEM_ERR_UNSUPPORTED;
+    }
+    dem_status schedule_train(int, float, uint64_t, float *, std::string &err) override
+    {
+        err = "schedule training is not built into this engine";
+        return DEM_ERR_UNSUPPORTED;
+    }
+    dem_status schedule_export(std::vector<uint8_t> &, std::string &err) override
+    {
+        err = "schedule export is not built into this engine";
+        return DEM_ERR_UNSUPPORTED;
+    }
+    dem_status schedule_load(const uint8_t *w, size_t n, std::string &err) override
+    {
+        (void)err;
+        m_.schedule_model.assign(w, w + n);
+        return DEM_OK;
+    }
+
+private:
+    static unsigned grid(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
+
+    int64_t wall_local(uint32_t wg) const
+    {
+        for (size_t sc = m_.scene_wall_base.size(); sc-- > 0;)
+            if ((int64_t)wg >= m_.scene_wall_base[sc]) return (int64_t)wg - m_.scene_wall_base[sc];
+        return (int64_t)wg;
+    }
+
+    template <class T>
+    dem_status alloc(T *&p, int64_t count, std::string &err)
+    {
+        size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+        void *ptr = nullptr;
+        if (m_.alloc) {
+            ptr = m_.alloc(bytes, m_.alloc_ctx);
+            if (!ptr) { err = "allocator callback failed"; return DEM_ERR_NOMEM; }
+        } else {
+            cudaError_t e = cudaMalloc(&ptr, bytes);
+            if (e != cudaSuccess) { err = std::string("cudaMalloc: ") + cudaGetErrorString(e); return DEM_ERR_NOMEM; }
+        }
+        cudaError_t e = cudaMemset(ptr, 0, bytes);
+        if (e != cudaSuccess) { err = std::string("cudaMemset: ") + cudaGetErrorString(e); return DEM_ERR_CUDA; }
+        allocs_.push_back(ptr);
+        p = reinterpret_cast<T *>(ptr);
+        return DEM_OK;
+    }
+
+    void dfree(void *p)
+    {
+        if (!p) return;
+        auto it = std::find(allocs_.begin(), allocs_.end(), p);
+        if (it != allocs_.end()) allocs_.erase(it);
+        if (m_.free) m_.free(p, m_.alloc_ctx);
+        else cudaFree(p);
+    }
+
+    template <class T>
+    dem_status up(T *dst, const T *src, int64_t count, std::string &err)
+    {
+        if (count <= 0) return DEM_OK;
+        DEM_CU(cudaMemcpy(dst, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
+        return DEM_OK;
+    }
+
+    // grow-only scratch buffer for read-back kernels
+    dem_status scratch(double *&p, int64_t count, std::string &err)
+    {
+        if (count > scratch_n_) {
+            if (scratch_) dfree(scratch_);
+            scratch_ = nullptr;
+            scratch_n_ = 0;
+            dem_status s = alloc(scratch_, count, err);
+            if (s) return s;
+            scratch_n_ = count;
+        }
+        p = scratch_;
+        return DEM_OK;
+    }
+
+    dem_status alloc_lists(int K, std::string &err)
+    {
+        const int64_t ne = (int64_t)K * d_.Np;
+        dem_status s;
+        for (int b = 0; b < 2; ++b) {
+            if ((s = alloc(d_.lists.partner[b], ne, err))) return s;
+            if ((s = alloc(d_.lists.mirror[b], ne, err))) return s;
+            if ((s = alloc(d_.lists.cnt[b], d_.Np, err))) return s;
+            if ((s = alloc(d_.lists.hx[b], ne, err))) return s;
+            if ((s = alloc(d_.lists.hy[b], ne, err))) return s;
+            if ((s = alloc(d_.lists.hz[b], ne, err))) return s;
+        }
+        d_.K = K;
+        return DEM_OK;
+    }
+
+    // Grow the row capacity to K, keeping the list in use and the current history.
+    dem_status realloc_lists(int K, bool keep, std::string &err)
+    {
+        DEM_CU(cudaStreamSynchronize(sf_));
+        DEM_CU(cudaStreamSynchronize(sd_));
+        ListBuffers<R> old = d_.lists;
+        const int Kold = d_.K;
+        const int lc = sth_->list_cur, hp = sth_->hist_par;
+        dem_status s;
+        if ((s = alloc_lists(K, err))) return s;
+        if (keep) {
+            const int64_t ne = (int64_t)std::min(Kold, K) * d_.Np;
+            DEM_CU(cudaMemcpy(d_.lists.partner[lc], old.partner[lc], ne * 4, cudaMemcpyDeviceToDevice));
+            DEM_CU(cudaMemcpy(d_.lists.mirror[lc], old.mirror[lc], ne, cudaMemcpyDeviceToDevice));
+            DEM_CU(cudaMemcpy(d_.lists.cnt[lc], old.cnt[lc], d_.Np, cudaMemcpyDeviceToDevice));
+            DEM_CU(cudaMemcpy(d_.lists.hx[hp], old.hx[hp], ne * sizeof(R), cudaMemcpyDeviceToDevice));
+            DEM_CU(cudaMemcpy(d_.lists.hy[hp], old.hy[hp], ne * sizeof(R), cudaMemcpyDeviceToDevice));
+            DEM_CU(cudaMemcpy(d_.lists.hz[hp], old.hz[hp], ne * sizeof(R), cudaMemcpyDeviceToDevice));
+        }
+        for (int b = 0; b < 2; ++b) {
+            dfree(old.partner[b]); dfree(old.mirror[b]); dfree(old.cnt[b]);
+            dfree(old.hx[b]); dfree(old.hy[b]); dfree(old.hz[b]);
+        }
+        return DEM_OK;
+    }
+
+    dem_status upload_state(int64_t first, int64_t n, const double *x, const double *q, const double *v,
+                            const double *w, const uint8_t *act, std::string &err)
+    {
+        if (n <= 0) return DEM_OK;
+        double *buf;
+        dem_status s;
+        if ((s = scratch(buf, 13 * n + (n + 7) / 8, err))) return s;
+        double *dx = x ? buf : nullptr, *dq = q ? buf + 3 * n : nullptr, *dv = v ? buf + 7 * n : nullptr,
+               *dw = w ? buf + 10 * n : nullptr;
+        uint8_t *da = act ? reinterpret_cast<uint8_t *>(buf + 13 * n) : nullptr;
+        if (x) DEM_CU(cudaMemcpyAsync(dx, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
+        if (q) DEM_CU(cudaMemcpyAsync(dq, q, 4 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
+        if (v) DEM_CU(cudaMemcpyAsync(dv, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
+        if (w) DEM_CU(cudaMemcpyAsync(dw, w, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
+        if (act) DEM_CU(cudaMemcpyAsync(da, act, n, cudaMemcpyHostToDevice, sf_));
+        // the angular velocity conversion needs the new orientation: quaternion first
+        if (q && w) {
+            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, nullptr, da);
+            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, nullptr, nullptr, nullptr, dw, nullptr);
+        } else {
+            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, dw, da);
+        }
+        DEM_CU(cudaGetLastError());
+        DEM_CU(cudaStreamSynchronize(sf_));
+        return DEM_OK;
+    }
+
+    dem_status fetch_list(int lc, std::vector<uint32_t> &partner, std::vector<uint8_t> &cnt, std::string &err)
+    {
+        const int64_t ne = (int64_t)d_.K * d_.Np;
+        partner.resize(ne);
+        cnt.resize(d_.Np);
+        DEM_CU(cudaMemcpyAsync(partner.data(), d_.lists.partner[lc], ne * 4, cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaMemcpyAsync(cnt.data(), d_.lists.cnt[lc], d_.Np, cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        return DEM_OK;
+    }
+
+    // Copy the device status into the pinned mirror (synchronous).
+    dem_status pull(std::string &err)
+    {
+        DEM_CU(cudaStreamSynchronize(sd_));
+        DEM_CU(cudaMemcpyAsync(sth_, st_, sizeof(DevStatus), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        if (!marks_.empty()) harvest();
+        return DEM_OK;
+    }
+
+    // After queued work: surface launch errors, recover from overflow, report divergence.
+    dem_status settle(std::string &err)
+    {
+        DEM_CU(cudaGetLastError());
+        dem_status s;
+        if ((s = pull(err))) return s;
+        if (sth_->halt == HALT_OVERFLOW) {
+            int need = sth_->max_row;
+            if (need > KMAX) {
+                err = "a contact-list row needs " + std::to_string(need) + " entries (limit " + std::to_string(KMAX) + ")";
+                return DEM_ERR_OVERFLOW;
+            }
+            int K = std::min(KMAX, std::max(need + 4, d_.K + d_.K / 2));
+            K = (K + 3) / 4 * 4;
+            if (K > KMAX) K = KMAX;
+            if ((s = realloc_lists(K, true, err))) return s;
+            regrows_ += 1;
+            DevStatus h = *sth_;
+            h.halt = HALT_NONE;
+            h.overflow = 0;
+            h.max_row = 0;
+            h.step_disp_bits = 0;
+            h.vmax_bits = 0;
+            DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
+            rebuild_inline(sf_);
+            return settle(err);
+        }
+        if (sth_->halt == HALT_DIVERGED) {
+            err = "a speed exceeded the error-out velocity or became non-finite after step " +
+                  std::to_string(sth_->steps_done);
+            return DEM_ERR_DIVERGED;
+        }
+        if (sth_->halt != HALT_NONE) {
+            err = "halted (code " + std::to_string(sth_->halt) + ")";
+            return DEM_ERR_TIMEOUT;
+        }
+        return DEM_OK;
+    }
+
+    void launch_hash(cudaStream_t st)
+    {
+        if (m_.clumps) k_hash<F, true><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, beta_);
+        else k_hash<F, false><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, beta_);
+    }
+
+    void launch_detect(cudaStream_t st)
+    {
+        uint32_t *ks, *vs;
+        radix_sort_u32(db_.keys, db_.vals, db_.keys_alt, db_.vals_alt, d_.N, db_.key_bits, db_.hist, db_.hist_cap,
+                       st, &ks, &vs);
+        k_clear_rows<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_);
+        k_cellstart<F><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, ks, vs);
+        k_narrow<F><<<grid(d_.N, 128), 128, 0, st>>>(d_, db_, ks, vs);
+    }
+
+    void launch_link(cudaStream_t st)
+    {
+        k_link<F><<<grid(d_.N, 256), 256, 0, st>>>(d_);
+        k_commit<<<1, 1, 0, st>>>(st_);
+    }
+
+    void rebuild_inline(cudaStream_t st)
+    {
+        Mark m1, m2, m3;
+        mark_begin(P_HASH, st, m1);
+        launch_hash(st);
+        mark_end(st, m1);
+        mark_begin(P_DETECT, st, m2);
+        launch_detect(st);
+        mark_end(st, m2);
+        mark_begin(P_LINK, st, m3);
+        launch_link(st);
+        mark_end(st, m3);
+    }
+
+    // snapshot on the force stream, detection of the next list on the detection stream
+    void start_detect()
+    {
+        Mark m1, m2;
+        mark_begin(P_HASH, sf_, m1);
+        launch_hash(sf_);
+        mark_end(sf_, m1);
+        cudaEventRecord(ev_snap_, sf_);
+        cudaStreamWaitEvent(sd_, ev_snap_, 0);
+        mark_begin(P_DETECT, sd_, m2);
+        launch_detect(sd_);
+        mark_end(sd_, m2);
+        cudaEventRecord(ev_det_, sd_);
+    }
+
+    void finish_detect()
+    {
+        cudaStreamWaitEvent(sf_, ev_det_, 0);
+        Mark m;
+        mark_begin(P_LINK, sf_, m);
+        launch_link(sf_);
+        mark_end(sf_, m);
+    }
+
+    template <int MODE>
+    void launch_force(double *eF, double *eT)
+    {
+        const unsigned g = grid(d_.N, 256);
+        if (m_.clumps) k_force<F, true, MODE><<<g, 256, 0, sf_>>>(d_, eF, eT);
+        else k_force<F, false, MODE><<<g, 256, 0, sf_>>>(d_, eF, eT);
+    }
+
+    void force_step()
+    {
+        Mark m;
+        mark_begin(P_FORCE, sf_, m);
+        launch_force<MODE_STEP>(nullptr, nullptr);
+        mark_end(sf_, m);
+        k_audit<<<1, 1, 0, sf_>>>(st_);
+    }
+
+    // Steps per list for the delayed schedules.  A list built from a snapshot at step s is
+    // used from s + c to s + 2c, so its margin must cover 2c steps of motion; the
+    // velocity bound uses the largest speed seen (with a 50% allowance for acceleration).
+    long long cycle_length()
+    {
+        const double h = m_.scenes.empty() ? 1e-6 : m_.scenes[0].h;
+        double v = std::max(sth_->vmax_last, 1e-3) * 1.5;
+        long long c = (long long)std::floor(beta_ / (2.0 * h * v));
+        if (m_.schedule == DEM_SCHEDULE_LEARNED && !m_.schedule_model.empty() && learned_cycle_ > 0)
+            c = learned_cycle_;
+        return std::max<long long>(1, std::min<long long>(c, 2000));
+    }
+
+    void release()
+    {
+        if (sf_) cudaStreamSynchronize(sf_);
+        if (sd_) cudaStreamSynchronize(sd_);
+        std::vector<void *> a = allocs_;
+        for (void *p : a) dfree(p);
+        allocs_.clear();
+        if (sth_) cudaFreeHost(sth_);
+        sth_ = nullptr;
+        for (auto &m : marks_) pool_.push_back(m);
+        marks_.clear();
+        for (auto &m : pool_) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+        pool_.clear();
+        if (ev_snap_) cudaEventDestroy(ev_snap_);
+        if (ev_det_) cudaEventDestroy(ev_det_);
+        if (ev_a_) cudaEventDestroy(ev_a_);
+        if (ev_b_) cudaEventDestroy(ev_b_);
+        if (ev_c_) cudaEventDestroy(ev_c_);
+        ev_snap_ = ev_det_ = ev_a_ = ev_b_ = ev_c_ = nullptr;
+        if (own_sf_ && sf_) cudaStreamDestroy(sf_);
+        if (own_sd_ && sd_) cudaStreamDestroy(sd_);
+        sf_ = sd_ = nullptr;
+    }
+
+    HostModel m_;
+    Dev<F> d_{};
+    DetectBuffers db_{};
+    DevStatus *st_ = nullptr;
+    DevStatus *sth_ = nullptr;
+    cudaStream_t sf_ = nullptr, sd_ = nullptr;
+    bool own_sf_ = false, own_sd_ = false;
+    cudaEvent_t ev_snap_ = nullptr, ev_det_ = nullptr, ev_a_ = nullptr, ev_b_ = nullptr, ev_c_ = nullptr;
+    std::vector<void *> allocs_;
+    double *scratch_ = nullptr;
+    int64_t scratch_n_ = 0;
+    double beta_ = 0.0;
+    bool dirty_ = false;
+    int64_t fallbacks_ = 0, regrows_ = 0;
+    long long learned_cycle_ = 0;
+    double ms_total_ = 0.0;
+    // profiling: event pairs recorded on the stream of the bracketed work
+    enum { P_FORCE = 0, P_DETECT = 1, P_HASH = 2, P_LINK = 3 };
+    bool prof_ = false;
+    struct Mark { cudaEvent_t a, b; int kind; };
+    std::vector<Mark> marks_, pool_;
+    double prof_ms_[4] = {0, 0, 0, 0};
+    int64_t prof_n_[4] = {0, 0, 0, 0};
+
+    Mark take()
+    {
+        if (pool_.empty()) {
+            Mark m{};
+            cudaEventCreate(&m.a);
+            cudaEventCreate(&m.b);
+            return m;
+        }
+        Mark m = pool_.back();
+        pool_.pop_back();
+        return m;
+    }
+    void mark_begin(int kind, cudaStream_t st, Mark &m)
+    {
+        if (!prof_) return;
+        m = take();
+        m.kind = kind;
+        cudaEventRecord(m.a, st);
+    }
+    void mark_end(cudaStream_t st, Mark &m)
+    {
+        if (!prof_) return;
+        cudaEventRecord(m.b, st);
+        marks_.push_back(m);
+    }
+    // called after a synchronisation: every recorded event has completed
+    void harvest()
+    {
+        for (auto &m : marks_) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+                prof_ms_[m.kind] += ms;
+                prof_n_[m.kind] += 1;
+            }
+            pool_.push_back(m);
+        }
+        marks_.clear();
+        cudaGetLastError();
+    }
+};
+
+}  // namespace dem

@@ -1,0 +1,949 @@
+// pipeline.cuh -- the per-timestep kernels of the DEM contact pipeline, templated on the
+// position form (FormF64 / FormF32).  Included by engine_f64.cu and engine_f32.cu.
+//
+// Per step (arXiv 2311.04648 Sec. 2.1 and Sec. 4):
+//   [rebuild]  k_hash -> radix sort -> k_cellstart -> k_narrow -> k_link -> k_commit
+//   [advance]  k_force (contact forces, per-owner reduction, integration) -> k_audit
+// Contact lists are ELL rows: entry k of sphere s at k*Np + s, each row holds every
+// partner of s (both orientations) sorted by partner id, walls (WALL_BIT | id) last.
+// A pair (A, B) with A < B owns its tangential history in A's row; B finds it through
+// mirror[] (the position of B in A's row).  Both threads evaluate the pair in the
+// canonical orientation with identical inputs, so the force on B is exactly the negated
+// force on A and no force array or atomic is needed.
+#pragma once
+#include "common.cuh"
+#include "contact.cuh"
+#include "kernels.cuh"
+
+namespace dem {
+
+enum : int { MODE_STEP = 0, MODE_EVAL = 1 };
+
+template <class F>
+struct Dev {
+    using R = typename F::R;
+    using R4 = typename F::R4;
+    int64_t M, N, Np;               // owners, sphere slots, ELL stride (multiple of 32)
+    int K;                          // list row capacity
+    float L;                        // cell (= voxel) edge
+    double Ld, invL;
+    int gyro;                       // gyroscopic term on
+    int n_scenes;
+    StateBuffers<F> st;
+    ListBuffers<R> lists;
+    R4 *inv_moi;                    // (1/I1, 1/I2, 1/I3, r_ext)
+    R *inv_mass;
+    uint16_t *owner_scene;
+    uint8_t *owner_iso;
+    uint32_t *sph_owner;            // 0xffffffff: padding slot
+    R *sph_rad;
+    uint16_t *sph_mat;
+    R4 *sph_rloc;                   // body-frame offset (x, y, z, 0); clumps only
+    uint8_t *sph_head;              // first slot of its owner
+    uint8_t *sph_segend;            // lane (within the warp) one past the owner's last slot
+    const Scene *scenes;
+    const Wall *walls;
+    const PairParam *pairs;
+    const uint16_t *mat_scene, *mat_local;
+    DevStatus *status;
+};
+
+// ------------------------------------------------------------------ sphere kinematics
+
+template <class F>
+struct SphereK {
+    using R = typename F::R;
+    typename F::Pos p;   // sphere centre
+    V3<R> rl;            // centre minus owner centre of mass, world frame
+    V3<R> v, w;          // owner linear velocity and world-frame angular velocity
+    R rad, mass;
+    int mat;
+    uint32_t owner;
+};
+
+template <class F, bool CLUMPS>
+__device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint32_t s)
+{
+    using R = typename F::R;
+    SphereK<F> k;
+    uint32_t o = d.sph_owner[s];
+    k.owner = o;
+    R mass;
+    typename F::Pos po = F::load(d.st.pos[sp], o, mass);
+    auto v4 = d.st.vel[sp][o];
+    auto w4 = d.st.omg[sp][o];
+    k.v = {v4.x, v4.y, v4.z};
+    k.w = {w4.x, w4.y, w4.z};
+    k.mass = mass;
+    k.rad = d.sph_rad[s];
+    k.mat = d.sph_mat[s];
+    if (CLUMPS) {
+        auto q = d.st.quat[sp][o];
+        auto r4 = d.sph_rloc[s];
+        k.rl = rotate_exact<R>(q.x, q.y, q.z, q.w, V3<R>{r4.x, r4.y, r4.z});
+        k.p = F::advance(po, k.rl, d.L);
+    } else {
+        k.rl = {R(0), R(0), R(0)};
+        k.p = po;
+    }
+    return k;
+}
+
+// Sphere-sphere contact geometry, A and B in canonical order.  False if delta <= 0.
+template <class F>
+__device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
+                                               ContactIn<typename F::R> &c, V3<typename F::R> &armA,
+                                               V3<typename F::R> &armB)
+{
+    using R = typename F::R;
+    V3<R> dd = F::diff(A.p, B.p, d.L);
+    R ss = radd(radd(rmul(dd.x, dd.x), rmul(dd.y, dd.y)), rmul(dd.z, dd.z));
+    R dist = sqrt(ss);
+    R delta = rsub(radd(A.rad, B.rad), dist);
+    if (!(delta > R(0)) || !(dist > R(0))) return false;
+    R inv = R(1) / dist;
+    c.n = inv * dd;
+    c.delta = delta;
+    R a = A.rad - R(0.5) * delta;
+    R b = B.rad - R(0.5) * delta;
+    armA = A.rl - a * c.n;
+    armB = B.rl + b * c.n;
+    c.uA = A.v + cross(A.w, armA);
+    c.uB = B.v + cross(B.w, armB);
+    c.Rbar = (A.rad * B.rad) / (A.rad + B.rad);
+    c.mbar = (A.mass * B.mass) / (A.mass + B.mass);
+    load_pair<R>(d.pairs, d.mat_scene, d.mat_local, d.scenes, A.mat, B.mat, c);
+    return true;
+}
+
+// Sphere-wall contact (B = wall of infinite radius and mass), geometry in FP64.
+template <class F>
+__device__ __forceinline__ bool wall_contact(const Dev<F> &d, const SphereK<F> &A, const Scene &sc, const Wall &w,
+                                             ContactIn<typename F::R> &c, V3<typename F::R> &armA,
+                                             V3<double> *point = nullptr)
+{
+    using R = typename F::R;
+    V3<double> pa = F::absolute(A.p, sc, d.Ld);
+    double gap;
+    V3<double> n;
+    if (!wall_gap(w, pa, gap, n)) return false;
+    double delta = rsub((double)A.rad, gap);
+    if (!(delta > 0.0)) return false;
+    double a = (double)A.rad - 0.5 * delta;
+    V3<double> cp = {pa.x - a * n.x, pa.y - a * n.y, pa.z - a * n.z};
+    V3<double> om = {w.omega[0], w.omega[1], w.omega[2]};
+    V3<double> vw = cross(om, V3<double>{cp.x - w.p[0], cp.y - w.p[1], cp.z - w.p[2]});
+    if (point) *point = cp;
+    c.n = {(R)n.x, (R)n.y, (R)n.z};
+    c.delta = (R)delta;
+    armA = A.rl - (R)a * c.n;
+    c.uA = A.v + cross(A.w, armA);
+    c.uB = {(R)vw.x, (R)vw.y, (R)vw.z};
+    c.Rbar = A.rad;
+    c.mbar = A.mass;
+    load_pair<R>(d.pairs, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
+    return true;
+}
+
+// Position of `key` in a sorted ELL row (entries partner[k*Np + row], k < n); -1 if absent.
+__device__ __forceinline__ int row_find(const uint32_t *partner, int64_t Np, int64_t row, int n, uint32_t key)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        uint32_t v = partner[(int64_t)mid * Np + row];
+        if (v < key) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < n && partner[(int64_t)lo * Np + row] == key) return lo;
+    return -1;
+}
+
+// ------------------------------------------------------------------ detection
+
+// Snapshot of sphere centres and their cell keys (slot order).  Resets the displacement
+// bound of the list being built: this is the snapshot time of that list.
+template <class F, bool CLUMPS>
+__global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double beta)
+{
+    DevStatus *stp = d.status;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (stp->halt) return;
+    if (s == 0) {
+        stp->disp_next = 0.0;
+        stp->beta_next = beta;
+    }
+    if (s >= d.N) return;
+    const int sp = stp->state_par;
+    uint32_t o = d.sph_owner[s];
+    uint32_t key = b.n_cells_total;
+    if (o != 0xffffffffu && d.st.active[sp][o]) {
+        SphereK<F> k = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
+        const Scene &sc = d.scenes[d.owner_scene[o]];
+        int cx, cy, cz;
+        F::cell(k.p, sc, d.invL, cx, cy, cz);
+        cx = min(max(cx, 0), sc.nc[0] - 1);
+        cy = min(max(cy, 0), sc.nc[1] - 1);
+        cz = min(max(cz, 0), sc.nc[2] - 1);
+        key = sc.cell_base + (uint32_t)((cz * sc.nc[1] + cy) * sc.nc[0] + cx);
+        if constexpr (F::voxel) {
+            reinterpret_cast<int4 *>(b.snap)[s] = make_int4(k.p.cx, k.p.cy, k.p.cz, 0);
+            reinterpret_cast<float4 *>(b.snap_aux)[s] = make_float4(k.p.x, k.p.y, k.p.z, (float)k.rad);
+        } else {
+            reinterpret_cast<double4_32a *>(b.snap)[s] = make_double4_32a(k.p.x, k.p.y, k.p.z, (double)k.rad);
+        }
+    }
+    b.keys[s] = key;
+    b.vals[s] = (uint32_t)s;
+}
+
+// Cell start/end tables from the sorted keys (no clearing: an entry is valid only if
+// the sorted key at its start equals the cell) and the snapshot gathered in cell order.
+template <class F>
+__global__ void __launch_bounds__(256) k_cellstart(Dev<F> d, DetectBuffers b, const uint32_t *keys,
+                                                    const uint32_t *vals)
+{
+    if (d.status->halt) return;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.n) return;
+    uint32_t k = keys[t];
+    const uint32_t sent = b.n_cells_total;
+    if (k != sent) {
+        if (t == 0 || keys[t - 1] != k) b.cell_start[k] = (uint32_t)t;
+        if (t == b.n - 1 || keys[t + 1] != k) b.cell_end[k] = (uint32_t)(t + 1);
+        if (t == b.n - 1 || keys[t + 1] == sent) *b.n_valid = (uint32_t)(t + 1);
+    } else if (t == 0) {
+        *b.n_valid = 0;
+    }
+    uint32_t id = vals[t];
+    if constexpr (F::voxel) {
+        reinterpret_cast<int4 *>(b.sorted)[t] = reinterpret_cast<const int4 *>(b.snap)[id];
+        reinterpret_cast<float4 *>(b.sorted_aux)[t] = reinterpret_cast<const float4 *>(b.snap_aux)[id];
+    } else {
+        reinterpret_cast<double4_32a *>(b.sorted)[t] = reinterpret_cast<const double4_32a *>(b.snap)[id];
+    }
+    b.sorted_owner[t] = d.sph_owner[id];
+}
+
+// Listed-pair predicate on snapshot entries: squared distance below
+// ((Ri + Rj) + 2 beta)^2, rounded in a fixed order (FP64 or voxel + FP32).
+__device__ __forceinline__ bool listed_f64(double4_32a a, double4_32a b, double b2)
+{
+    double dx = rsub(a.x, b.x), dy = rsub(a.y, b.y), dz = rsub(a.z, b.z);
+    double s = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
+    double t = radd(radd(a.w, b.w), b2);
+    return s < rmul(t, t);
+}
+__device__ __forceinline__ bool listed_f32(int4 ca, float4 oa, int4 cb, float4 ob, float L, float b2)
+{
+    float dx = radd(rmul((float)(ca.x - cb.x), L), rsub(oa.x, ob.x));
+    float dy = radd(rmul((float)(ca.y - cb.y), L), rsub(oa.y, ob.y));
+    float dz = radd(rmul((float)(ca.z - cb.z), L), rsub(oa.z, ob.z));
+    float s = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
+    float t = radd(radd(oa.w, ob.w), b2);
+    return s < rmul(t, t);
+}
+
+__device__ __forceinline__ void row_insert(uint32_t *buf, int &n, uint32_t e)
+{
+    if (n < KMAX) {
+        int pos = n;
+        while (pos > 0 && buf[pos - 1] > e) {
+            buf[pos] = buf[pos - 1];
+            --pos;
+        }
+        buf[pos] = e;
+    }
+    ++n;
+}
+
+// Narrow phase: one thread per sorted entry scans the 27 neighbour cells (as 9 runs of
+// three x-consecutive cells, each contiguous in the sorted order) and the walls of its
+// scene, and writes its full, sorted row into the list that is not in use.
+template <class F>
+__global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const uint32_t *keys,
+                                                 const uint32_t *vals)
+{
+    DevStatus *stp = d.status;
+    if (stp->halt) return;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nvalid = *b.n_valid;
+    if (t >= nvalid) return;
+    const int ln = stp->list_cur ^ 1;
+    const double beta = stp->beta_next;
+    const uint32_t i = vals[t];
+    const uint32_t key = keys[t];
+    const uint32_t oi = b.sorted_owner[t];
+    const Scene &sc = d.scenes[d.owner_scene[oi]];
+    const uint32_t local = key - sc.cell_base;
+    const int nx = sc.nc[0], ny = sc.nc[1], nz = sc.nc[2];
+    const int cx = (int)(local % (uint32_t)nx);
+    const int cy = (int)((local / (uint32_t)nx) % (uint32_t)ny);
+    const int cz = (int)(local / (uint32_t)(nx * ny));
+
+    double4_32a a64 = make_double4_32a(0, 0, 0, 0);
+    int4 ac = make_int4(0, 0, 0, 0);
+    float4 ao = make_float4(0, 0, 0, 0);
+    if constexpr (F::voxel) {
+        ac = reinterpret_cast<const int4 *>(b.sorted)[t];
+        ao = reinterpret_cast<const float4 *>(b.sorted_aux)[t];
+    } else {
+        a64 = reinterpret_cast<const double4_32a *>(b.sorted)[t];
+    }
+    const float b2f = 2.0f * (float)beta;
+    const double b2d = 2.0 * beta;
+
+    uint32_t buf[KMAX];
+    int n = 0;
+    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (z < 0 || z >= nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (y < 0 || y >= ny) continue;
+            uint32_t rowbase = sc.cell_base + (uint32_t)((z * ny + y) * nx);
+            uint32_t lo = 0xffffffffu, hi = 0;
+            for (int x = x0; x <= x1; ++x) {
+                uint32_t c = rowbase + (uint32_t)x;
+                uint32_t st = b.cell_start[c];
+                if (st < nvalid && keys[st] == c) {
+                    if (lo == 0xffffffffu) lo = st;
+                    hi = b.cell_end[c];
+                }
+            }
+            if (lo == 0xffffffffu) continue;
+            for (uint32_t u = lo; u < hi; ++u) {
+                uint32_t j = vals[u];
+                if (j == i) continue;
+                if (b.sorted_owner[u] == oi) continue;
+                bool hit;
+                if constexpr (F::voxel) {
+                    hit = listed_f32(ac, ao, reinterpret_cast<const int4 *>(b.sorted)[u],
+                                     reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
+                } else {
+                    hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
+                }
+                if (hit) row_insert(buf, n, j);
+            }
+        }
+    }
+    // walls: signed gap below R + beta
+    if (sc.wall_count > 0) {
+        V3<double> pa;
+        double R;
+        if constexpr (F::voxel) {
+            PosF32 p{ac.x, ac.y, ac.z, ao.x, ao.y, ao.z};
+            pa = FormF32::absolute(p, sc, d.Ld);
+            R = (double)ao.w;
+        } else {
+            pa = {a64.x, a64.y, a64.z};
+            R = a64.w;
+        }
+        for (int wi = 0; wi < sc.wall_count; ++wi) {
+            int wg = sc.wall_begin + wi;
+            double gap;
+            V3<double> nn;
+            wall_gap(d.walls[wg], pa, gap, nn);
+            if (gap < R + beta) row_insert(buf, n, WALL_BIT | (uint32_t)wg);
+        }
+    }
+    const int K = d.K;
+    if (n > K) {
+        atomicMax(&stp->max_row, n);
+        stp->overflow = 1;
+        stp->halt = HALT_OVERFLOW;
+        n = K;
+    } else {
+        atomicMax(&stp->max_row, n);
+    }
+    uint32_t *prow = d.lists.partner[ln];
+    for (int k = 0; k < n; ++k) prow[(int64_t)k * d.Np + i] = buf[k];
+    d.lists.cnt[ln][i] = (uint8_t)n;
+}
+
+// Rows of spheres that are inactive or padding are empty in the new list.
+template <class F>
+__global__ void __launch_bounds__(256) k_clear_rows(Dev<F> d)
+{
+    DevStatus *stp = d.status;
+    if (stp->halt) return;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.Np) return;
+    d.lists.cnt[stp->list_cur ^ 1][s] = 0;
+}
+
+// Link the new list: mirror positions for entries whose partner owns the pair, and the
+// tangential history of owned entries carried over from the list in use (zero for a
+// pair that is new: Sec. 4.2, contact wildcards start at zero).
+template <class F>
+__global__ void __launch_bounds__(256) k_link(Dev<F> d)
+{
+    using R = typename F::R;
+    DevStatus *stp = d.status;
+    if (stp->halt) return;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.N) return;
+    const int lo = stp->list_cur, ln = lo ^ 1;
+    const int hs = stp->hist_par, hd = hs ^ 1;
+    const uint32_t *pn = d.lists.partner[ln];
+    const uint32_t *po = d.lists.partner[lo];
+    const int n = d.lists.cnt[ln][s];
+    const int nold = d.lists.cnt[lo][s];
+    for (int k = 0; k < n; ++k) {
+        int64_t e = (int64_t)k * d.Np + s;
+        uint32_t j = pn[e];
+        if (!(j & WALL_BIT) && j < (uint32_t)s) {
+            int m = row_find(pn, d.Np, j, d.lists.cnt[ln][j], (uint32_t)s);
+            d.lists.mirror[ln][e] = (uint8_t)(m < 0 ? 0 : m);
+        } else {
+            int ko = row_find(po, d.Np, s, nold, j);
+            R x = R(0), y = R(0), z = R(0);
+            if (ko >= 0) {
+                int64_t eo = (int64_t)ko * d.Np + s;
+                x = d.lists.hx[hs][eo];
+                y = d.lists.hy[hs][eo];
+                z = d.lists.hz[hs][eo];
+            }
+            d.lists.hx[hd][e] = x;
+            d.lists.hy[hd][e] = y;
+            d.lists.hz[hd][e] = z;
+        }
+    }
+}
+
+// Switch to the new list (single thread, after k_link).
+static __global__ void k_commit(DevStatus *stp)
+{
+    if (stp->halt) return;
+    stp->list_cur ^= 1;
+    stp->hist_par ^= 1;
+    stp->disp_cur = stp->disp_next;
+    stp->beta_cur = stp->beta_next;
+    stp->list_stale = stp->disp_cur > stp->beta_cur ? 1 : 0;
+    stp->rebuilds += 1;
+}
+
+// ------------------------------------------------------------------ force + integration
+
+// Quaternion increment for a rotation vector th (angle |th|): (cos(|th|/2), sin(|th|/2) th/|th|).
+template <typename R>
+__device__ __forceinline__ void quat_increment(V3<R> w, R h, R &dw, R &dx, R &dy, R &dz)
+{
+    R wn = sqrt(dot(w, w));
+    if (wn >= R(1e-30)) {
+        R half = R(0.5) * h * wn;
+        R sn = sin(half) / wn;
+        dw = cos(half);
+        dx = sn * w.x;
+        dy = sn * w.y;
+        dz = sn * w.z;
+    } else {
+        dw = R(1); dx = R(0); dy = R(0); dz = R(0);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void quat_mul(R aw, R ax, R ay, R az, R bw, R bx, R by, R bz, R &w, R &x, R &y, R &z)
+{
+    w = ((aw * bw - ax * bx) - ay * by) - az * bz;
+    x = ((aw * bx + ax * bw) + ay * bz) - az * by;
+    y = ((aw * by - ax * bz) + ay * bw) + az * bx;
+    z = ((aw * bz + ax * by) - ay * bx) + az * bw;
+}
+
+// Contact forces of every listed pair of slot s, the per-owner sum (segmented warp
+// reduction over the owner's consecutive slots), then (MODE_STEP) the semi-implicit
+// Euler update of the owner: v, then body-frame angular velocity (Euler's equations),
+// then x, then the quaternion.  MODE_EVAL writes the per-owner force (gravity included)
+// and torque instead and changes nothing.
+template <class F, bool CLUMPS, int MODE>
+__global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double *eval_T)
+{
+    using R = typename F::R;
+    using R4 = typename F::R4;
+    DevStatus *stp = d.status;
+    if (MODE == MODE_STEP && (stp->halt || stp->list_stale)) return;
+    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+
+    bool live = s < d.N;
+    uint32_t o = live ? d.sph_owner[s] : 0xffffffffu;
+    live = live && o != 0xffffffffu;
+    bool act = live && d.st.active[sp][o];
+
+    V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
+    SphereK<F> me;
+    int scene = 0;
+    if (live) {
+        me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
+        scene = d.owner_scene[o];
+    }
+    if (act) {
+        const Scene &sc = d.scenes[scene];
+        const R h = F::voxel ? (R)sc.hf : (R)sc.h;
+        const int n = d.lists.cnt[lc][s];
+        const uint32_t *prow = d.lists.partner[lc];
+        const uint8_t *mrow = d.lists.mirror[lc];
+        const R *hxi = d.lists.hx[hp], *hyi = d.lists.hy[hp], *hzi = d.lists.hz[hp];
+        R *hxo = d.lists.hx[hp ^ 1], *hyo = d.lists.hy[hp ^ 1], *hzo = d.lists.hz[hp ^ 1];
+        for (int k = 0; k < n; ++k) {
+            const int64_t e = (int64_t)k * d.Np + s;
+            const uint32_t j = prow[e];
+            ContactIn<R> c;
+            V3<R> armA, armB;
+            if (j & WALL_BIT) {
+                V3<R> ut = {hxi[e], hyi[e], hzi[e]};
+                V3<R> Fc;
+                bool on = wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA);
+                if (on) {
+                    hertz_mindlin<R>(c, h, ut, Fc);
+                    Fs = Fs + Fc;
+                    Ts = Ts + cross(armA, Fc);
+                }
+                if (MODE == MODE_STEP) {
+                    hxo[e] = on ? ut.x : R(0);
+                    hyo[e] = on ? ut.y : R(0);
+                    hzo[e] = on ? ut.z : R(0);
+                }
+                continue;
+            }
+            SphereK<F> other = load_sphere<F, CLUMPS>(d, sp, j);
+            const bool mine = (uint32_t)s < j;     // this slot owns the pair (A = lower id)
+            if (!d.st.active[sp][other.owner]) {
+                if (MODE == MODE_STEP && mine) { hxo[e] = R(0); hyo[e] = R(0); hzo[e] = R(0); }
+                continue;
+            }
+            const int64_t slot = mine ? e : (int64_t)mrow[e] * d.Np + j;
+            V3<R> ut = {hxi[slot], hyi[slot], hzi[slot]};
+            const SphereK<F> &A = mine ? me : other;
+            const SphereK<F> &B = mine ? other : me;
+            V3<R> Fc;
+            bool on = sphere_contact<F>(d, A, B, c, armA, armB);
+            if (on) {
+                hertz_mindlin<R>(c, h, ut, Fc);
+                if (mine) {
+                    Fs = Fs + Fc;
+                    Ts = Ts + cross(armA, Fc);
+                } else {
+                    V3<R> mf = -Fc;
+                    Fs = Fs + mf;
+                    Ts = Ts + cross(armB, mf);
+                }
+            }
+            if (MODE == MODE_STEP && mine) {
+                hxo[e] = on ? ut.x : R(0);
+                hyo[e] = on ? ut.y : R(0);
+                hzo[e] = on ? ut.z : R(0);
+            }
+        }
+    }
+    if (CLUMPS) {
+        // segmented suffix sums over the owner's consecutive lanes; the head lane ends
+        // with the owner's total (fixed tree order: deterministic)
+        const int end = live ? (int)d.sph_segend[s] : lane + 1;
+        R v6[6] = {Fs.x, Fs.y, Fs.z, Ts.x, Ts.y, Ts.z};
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+            for (int c6 = 0; c6 < 6; ++c6) {
+                R other = __shfl_down_sync(0xffffffffu, v6[c6], off);
+                if (lane + off < end) v6[c6] += other;
+            }
+        }
+        Fs = {v6[0], v6[1], v6[2]};
+        Ts = {v6[3], v6[4], v6[5]};
+    }
+    const bool head = live && (!CLUMPS || d.sph_head[s]);
+    float disp = 0.0f, speed = 0.0f;
+    if (head) {
+        const Scene &sc = d.scenes[scene];
+        const R h = F::voxel ? (R)sc.hf : (R)sc.h;
+        const V3<R> g = F::voxel ? V3<R>{(R)sc.gf[0], (R)sc.gf[1], (R)sc.gf[2]}
+                                 : V3<R>{(R)sc.g[0], (R)sc.g[1], (R)sc.g[2]};
+        R mass = me.mass;
+        typename F::Pos po;
+        {
+            R m2;
+            po = F::load(d.st.pos[sp], o, m2);
+        }
+        if (MODE == MODE_EVAL) {
+            V3<R> Ft = act ? Fs + mass * g : V3<R>{R(0), R(0), R(0)};
+            eval_F[3 * o + 0] = (double)Ft.x; eval_F[3 * o + 1] = (double)Ft.y; eval_F[3 * o + 2] = (double)Ft.z;
+            eval_T[3 * o + 0] = (double)Ts.x; eval_T[3 * o + 1] = (double)Ts.y; eval_T[3 * o + 2] = (double)Ts.z;
+        } else {
+            const int so = sp ^ 1;
+            R4 q4 = d.st.quat[sp][o];
+            V3<R> vn = me.v, wn = me.w;
+            R qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+            uint8_t active_out = act ? 1 : 0;
+            typename F::Pos pn = po;
+            if (act) {
+                const R im = d.inv_mass[o];
+                const R4 ii = d.inv_moi[o];
+                V3<R> Ft = Fs + mass * g;
+                vn = me.v + h * (im * Ft);
+                R nw, nx, ny, nz;
+                if (d.owner_iso[o]) {
+                    // isotropic inertia: the body-frame update equals a world-frame one
+                    wn = me.w + h * (ii.x * Ts);
+                    R dw, dx, dy, dz;
+                    quat_increment<R>(wn, h, dw, dx, dy, dz);
+                    quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+                } else {
+                    R m[9];
+                    quat_mat<R>(qw, qx, qy, qz, m);
+                    V3<R> wb = mat_tvec<R>(m, me.w);
+                    V3<R> Tb = mat_tvec<R>(m, Ts);
+                    V3<R> gyro = {R(0), R(0), R(0)};
+                    if (d.gyro) {
+                        V3<R> Iw = {wb.x / ii.x, wb.y / ii.y, wb.z / ii.z};
+                        gyro = cross(wb, Iw);
+                    }
+                    V3<R> dwb = {ii.x * (Tb.x - gyro.x), ii.y * (Tb.y - gyro.y), ii.z * (Tb.z - gyro.z)};
+                    wb = wb + h * dwb;
+                    R dw, dx, dy, dz;
+                    quat_increment<R>(wb, h, dw, dx, dy, dz);
+                    quat_mul<R>(qw, qx, qy, qz, dw, dx, dy, dz, nw, nx, ny, nz);
+                    R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
+                    R m2[9];
+                    quat_mat<R>(nw / qn, nx / qn, ny / qn, nz / qn, m2);
+                    wn = mat_vec<R>(m2, wb);
+                }
+                R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
+                qw = nw / qn; qx = nx / qn; qy = ny / qn; qz = nz / qn;
+                pn = F::advance(po, h * vn, d.L);
+                if (sc.has_sink) {
+                    V3<double> pa = F::absolute(pn, sc, d.Ld);
+                    double side = (pa.x - sc.sink_p[0]) * sc.sink_n[0] + (pa.y - sc.sink_p[1]) * sc.sink_n[1] +
+                                  (pa.z - sc.sink_p[2]) * sc.sink_n[2];
+                    if (side < 0.0) {
+                        active_out = 0;
+                        vn = {R(0), R(0), R(0)};
+                        wn = {R(0), R(0), R(0)};
+                    }
+                }
+                R sv = sqrt(dot(vn, vn));
+                R sw = sqrt(dot(wn, wn));
+                speed = (float)sv;
+                disp = (float)(h * (sv + sw * ii.w));
+                if (sc.v_err > 0.0 && !((double)sv <= sc.v_err)) atomicOr(&stp->diverged, 1);
+                if (!(sv == sv) || !(sw == sw)) atomicOr(&stp->diverged, 1);
+            } else {
+                vn = {R(0), R(0), R(0)};
+                wn = {R(0), R(0), R(0)};
+            }
+            F::store(d.st.pos[so], o, pn, mass);
+            d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, R(0)};
+            d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, R(0)};
+            d.st.quat[so][o] = R4{qw, qx, qy, qz};
+            d.st.active[so][o] = active_out;
+        }
+    }
+    if (MODE == MODE_STEP) {
+        // block max of the displacement bound and the speed (non-negative floats order
+        // like their bit patterns), one atomic per block
+        unsigned int db = __float_as_uint(disp), vb = __float_as_uint(speed);
+        db = __reduce_max_sync(0xffffffffu, db);
+        vb = __reduce_max_sync(0xffffffffu, vb);
+        __shared__ unsigned int sd[8], sv[8];
+        const int warp = threadIdx.x >> 5;
+        if (lane == 0) { sd[warp] = db; sv[warp] = vb; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int md = 0, mv = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { md = max(md, sd[w]); mv = max(mv, sv[w]); }
+            if (md) atomicMax(&stp->step_disp_bits, md);
+            if (mv) atomicMax(&stp->vmax_bits, mv);
+        }
+    }
+}
+
+// Completes a step (single thread): flips the state and history buffers, accumulates the
+// displacement bound of the list in use and of the list being built, and flags the list
+// stale when its bound exceeds the margin (Sec. 2.1: the margin must cover the motion
+// between list updates); turns a divergence into a halt, leaving the last good state.
+static __global__ void k_audit(DevStatus *stp)
+{
+    if (stp->halt || stp->list_stale) return;
+    float sd = __uint_as_float(stp->step_disp_bits);
+    float vm = __uint_as_float(stp->vmax_bits);
+    stp->step_disp_bits = 0;
+    stp->vmax_bits = 0;
+    if (stp->diverged || !(sd == sd)) {
+        stp->halt = HALT_DIVERGED;
+        return;
+    }
+    stp->steps_done += 1;
+    stp->state_par ^= 1;
+    stp->hist_par ^= 1;
+    double inc = (double)sd + stp->disp_slack;
+    stp->disp_cur += inc;
+    stp->disp_next += inc;
+    stp->vmax_last = (double)vm;
+    if (stp->disp_cur > stp->beta_cur) {
+        stp->list_stale = 1;
+        stp->stale_events += 1;
+    }
+}
+
+// ------------------------------------------------------------------ read-back helpers
+
+// Evaluate every owned entry (canonical sphere pairs and wall entries) at the current
+// state: overlap (<= 0 if not in contact), force on A, contact point and updated history.
+template <class F, bool CLUMPS>
+__global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *fo, double *pt, double *hi)
+{
+    using R = typename F::R;
+    DevStatus *stp = d.status;
+    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.N) return;
+    uint32_t o = d.sph_owner[s];
+    if (o == 0xffffffffu) return;
+    SphereK<F> me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
+    const Scene &sc = d.scenes[d.owner_scene[o]];
+    const R h = F::voxel ? (R)sc.hf : (R)sc.h;
+    const bool act = d.st.active[sp][o];
+    const int n = d.lists.cnt[lc][s];
+    for (int k = 0; k < n; ++k) {
+        int64_t e = (int64_t)k * d.Np + s;
+        uint32_t j = d.lists.partner[lc][e];
+        ov[e] = -1.0;
+        if (!act) continue;
+        ContactIn<R> c;
+        V3<R> armA, armB;
+        V3<R> ut = {d.lists.hx[hp][e], d.lists.hy[hp][e], d.lists.hz[hp][e]};
+        V3<R> Fc;
+        V3<double> cp;
+        if (j & WALL_BIT) {
+            if (!wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA, &cp)) continue;
+        } else {
+            if (j < (uint32_t)s) continue;
+            SphereK<F> B = load_sphere<F, CLUMPS>(d, sp, j);
+            if (!d.st.active[sp][B.owner]) continue;
+            if (!sphere_contact<F>(d, me, B, c, armA, armB)) continue;
+            V3<double> pa = F::absolute(me.p, sc, d.Ld);
+            double a = (double)me.rad - 0.5 * (double)c.delta;
+            cp = {pa.x - a * (double)c.n.x, pa.y - a * (double)c.n.y, pa.z - a * (double)c.n.z};
+        }
+        hertz_mindlin<R>(c, h, ut, Fc);
+        ov[e] = (double)c.delta;
+        fo[3 * e + 0] = (double)Fc.x; fo[3 * e + 1] = (double)Fc.y; fo[3 * e + 2] = (double)Fc.z;
+        pt[3 * e + 0] = cp.x; pt[3 * e + 1] = cp.y; pt[3 * e + 2] = cp.z;
+        hi[3 * e + 0] = (double)ut.x; hi[3 * e + 1] = (double)ut.y; hi[3 * e + 2] = (double)ut.z;
+    }
+}
+
+// Counts of the list in use: sphere pairs (each once), wall entries, and entries in
+// contact (overlap > 0) at the current state.  Integer atomics: order-independent.
+template <class F, bool CLUMPS>
+__global__ void __launch_bounds__(256) k_count(Dev<F> d, unsigned long long *out)
+{
+    using R = typename F::R;
+    const int sp = d.status->state_par, lc = d.status->list_cur;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long np = 0, nw = 0, nc = 0;
+    if (s < d.N) {
+        uint32_t o = d.sph_owner[s];
+        if (o != 0xffffffffu) {
+            const int n = d.lists.cnt[lc][s];
+            const bool act = d.st.active[sp][o];
+            SphereK<F> me;
+            if (act) me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
+            const Scene &sc = d.scenes[d.owner_scene[o]];
+            for (int k = 0; k < n; ++k) {
+                uint32_t j = d.lists.partner[lc][(int64_t)k * d.Np + s];
+                ContactIn<R> c;
+                V3<R> a, b;
+                if (j & WALL_BIT) {
+                    ++nw;
+                    if (act && wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, a)) ++nc;
+                } else if (j > (uint32_t)s) {
+                    ++np;
+                    if (act) {
+                        SphereK<F> B = load_sphere<F, CLUMPS>(d, sp, j);
+                        if (d.st.active[sp][B.owner] && sphere_contact<F>(d, me, B, c, a, b)) ++nc;
+                    }
+                }
+            }
+        }
+    }
+    np = __reduce_add_sync(0xffffffffu, (unsigned)np);
+    nw = __reduce_add_sync(0xffffffffu, (unsigned)nw);
+    nc = __reduce_add_sync(0xffffffffu, (unsigned)nc);
+    if ((threadIdx.x & 31) == 0) {
+        if (np) atomicAdd(&out[0], np);
+        if (nw) atomicAdd(&out[1], nw);
+        if (nc) atomicAdd(&out[2], nc);
+    }
+}
+
+// Owner state to FP64 host layout (quaternion (w,x,y,z); angular velocity to body frame).
+template <class F>
+__global__ void k_owner_download(Dev<F> d, int64_t first, int64_t n, double *x, double *q, double *v, double *w)
+{
+    using R = typename F::R;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t o = first + k;
+    const int sp = d.status->state_par;
+    R mass;
+    typename F::Pos p = F::load(d.st.pos[sp], o, mass);
+    const Scene &sc = d.scenes[d.owner_scene[o]];
+    V3<double> pa = F::absolute(p, sc, d.Ld);
+    x[3 * k] = pa.x; x[3 * k + 1] = pa.y; x[3 * k + 2] = pa.z;
+    auto q4 = d.st.quat[sp][o];
+    q[4 * k] = q4.x; q[4 * k + 1] = q4.y; q[4 * k + 2] = q4.z; q[4 * k + 3] = q4.w;
+    auto v4 = d.st.vel[sp][o];
+    v[3 * k] = v4.x; v[3 * k + 1] = v4.y; v[3 * k + 2] = v4.z;
+    auto w4 = d.st.omg[sp][o];
+    R m[9];
+    quat_mat<R>(q4.x, q4.y, q4.z, q4.w, m);
+    V3<R> wb = mat_tvec<R>(m, V3<R>{w4.x, w4.y, w4.z});
+    w[3 * k] = wb.x; w[3 * k + 1] = wb.y; w[3 * k + 2] = wb.z;
+}
+
+// FP64 host layout to owner state (both buffers' current one); world-frame angular
+// velocity stored.  In the voxel form the position is split into voxel index and
+// offset: c = floor((x - lo) / L), o = (float)((x - lo) - c L), then carried into [0, L).
+template <class F>
+__global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double *x, const double *q, const double *v,
+                               const double *w, const uint8_t *act)
+{
+    using R = typename F::R;
+    using R4 = typename F::R4;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t o = first + k;
+    const int sp = d.status->state_par;
+    R mass;
+    typename F::Pos p = F::load(d.st.pos[sp], o, mass);
+    const Scene &sc = d.scenes[d.owner_scene[o]];
+    if (x) {
+        if constexpr (F::voxel) {
+            PosF32 &pv = p;
+            double rx = rsub(x[3 * k], sc.lo[0]), ry = rsub(x[3 * k + 1], sc.lo[1]), rz = rsub(x[3 * k + 2], sc.lo[2]);
+            double fx = floor(__ddiv_rn(rx, d.Ld)), fy = floor(__ddiv_rn(ry, d.Ld)), fz = floor(__ddiv_rn(rz, d.Ld));
+            pv.cx = (int)fx; pv.cy = (int)fy; pv.cz = (int)fz;
+            pv.x = (float)rsub(rx, rmul(fx, d.Ld));
+            pv.y = (float)rsub(ry, rmul(fy, d.Ld));
+            pv.z = (float)rsub(rz, rmul(fz, d.Ld));
+            FormF32::carry(pv.cx, pv.x, d.L);
+            FormF32::carry(pv.cy, pv.y, d.L);
+            FormF32::carry(pv.cz, pv.z, d.L);
+        } else {
+            p.x = x[3 * k]; p.y = x[3 * k + 1]; p.z = x[3 * k + 2];
+        }
+        F::store(d.st.pos[sp], o, p, mass);
+    }
+    R4 q4 = d.st.quat[sp][o];
+    if (q) {
+        q4 = R4{(R)q[4 * k], (R)q[4 * k + 1], (R)q[4 * k + 2], (R)q[4 * k + 3]};
+        d.st.quat[sp][o] = q4;
+    }
+    if (v) d.st.vel[sp][o] = R4{(R)v[3 * k], (R)v[3 * k + 1], (R)v[3 * k + 2], R(0)};
+    if (w) {
+        double m[9];
+        quat_mat<double>((double)q4.x, (double)q4.y, (double)q4.z, (double)q4.w, m);
+        V3<double> wg = mat_vec<double>(m, V3<double>{w[3 * k], w[3 * k + 1], w[3 * k + 2]});
+        d.st.omg[sp][o] = R4{(R)wg.x, (R)wg.y, (R)wg.z, R(0)};
+    }
+    if (act) d.st.active[sp][o] = act[k];
+}
+
+// Sphere centres (FP64 world frame), radii, and the raw voxel encoding.
+template <class F, bool CLUMPS>
+__global__ void k_sphere_download(Dev<F> d, const int64_t *slots, int64_t n, double *xyz, double *rad, int *cell,
+                                  float *off)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int sp = d.status->state_par;
+    uint32_t s = (uint32_t)slots[k];
+    SphereK<F> me = load_sphere<F, CLUMPS>(d, sp, s);
+    const Scene &sc = d.scenes[d.owner_scene[me.owner]];
+    V3<double> pa = F::absolute(me.p, sc, d.Ld);
+    if (xyz) { xyz[3 * k] = pa.x; xyz[3 * k + 1] = pa.y; xyz[3 * k + 2] = pa.z; }
+    if (rad) rad[k] = (double)me.rad;
+    if constexpr (F::voxel) {
+        if (cell) {
+            cell[3 * k] = me.p.cx; cell[3 * k + 1] = me.p.cy; cell[3 * k + 2] = me.p.cz;
+            off[3 * k] = me.p.x; off[3 * k + 1] = me.p.y; off[3 * k + 2] = me.p.z;
+        }
+    }
+}
+
+// FP64 diagnostics: per-block partial sums in a fixed order (per owner: kinetic,
+// potential, momentum, angular momentum; per owned contact: Hertz elastic energy).
+template <class F, bool CLUMPS>
+__global__ void __launch_bounds__(256) k_diag(Dev<F> d, double *partials)
+{
+    using R = typename F::R;
+    const int sp = d.status->state_par, lc = d.status->list_cur;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // ke, pe, el, P[3], L[3]
+    if (t < d.M) {
+        int64_t o = t;
+        R mass;
+        typename F::Pos p = F::load(d.st.pos[sp], o, mass);
+        const Scene &sc = d.scenes[d.owner_scene[o]];
+        V3<double> x = F::absolute(p, sc, d.Ld);
+        auto v4 = d.st.vel[sp][o];
+        auto w4 = d.st.omg[sp][o];
+        auto q4 = d.st.quat[sp][o];
+        auto ii = d.inv_moi[o];
+        double m = (double)mass;
+        V3<double> v = {(double)v4.x, (double)v4.y, (double)v4.z};
+        double Q[9];
+        quat_mat<double>((double)q4.x, (double)q4.y, (double)q4.z, (double)q4.w, Q);
+        V3<double> wb = mat_tvec<double>(Q, V3<double>{(double)w4.x, (double)w4.y, (double)w4.z});
+        V3<double> I = {1.0 / (double)ii.x, 1.0 / (double)ii.y, 1.0 / (double)ii.z};
+        acc[0] = 0.5 * m * dot(v, v) + 0.5 * ((I.x * wb.x * wb.x + I.y * wb.y * wb.y) + I.z * wb.z * wb.z);
+        acc[1] = -m * ((sc.g[0] * x.x + sc.g[1] * x.y) + sc.g[2] * x.z);
+        V3<double> mv = m * v;
+        acc[3] = mv.x; acc[4] = mv.y; acc[5] = mv.z;
+        V3<double> orb = cross(x, mv);
+        V3<double> spin = mat_vec<double>(Q, V3<double>{I.x * wb.x, I.y * wb.y, I.z * wb.z});
+        acc[6] = orb.x + spin.x; acc[7] = orb.y + spin.y; acc[8] = orb.z + spin.z;
+    }
+    if (t < d.N) {
+        uint32_t o = d.sph_owner[t];
+        if (o != 0xffffffffu && d.st.active[sp][o]) {
+            SphereK<F> me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)t);
+            const Scene &sc = d.scenes[d.owner_scene[o]];
+            const int n = d.lists.cnt[lc][t];
+            for (int k = 0; k < n; ++k) {
+                uint32_t j = d.lists.partner[lc][(int64_t)k * d.Np + t];
+                ContactIn<R> c;
+                V3<R> armA, armB;
+                bool on;
+                if (j & WALL_BIT) {
+                    on = wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA);
+                } else {
+                    if (j < (uint32_t)t) continue;
+                    SphereK<F> B = load_sphere<F, CLUMPS>(d, sp, j);
+                    if (!d.st.active[sp][B.owner]) continue;
+                    on = sphere_contact<F>(d, me, B, c, armA, armB);
+                }
+                if (on) {
+                    double dl = (double)c.delta;
+                    acc[2] += (8.0 / 15.0) * (double)c.Estar * sqrt((double)c.Rbar) * dl * dl * sqrt(dl);
+                }
+            }
+        }
+    }
+    __shared__ double red[9][256];
+    for (int c = 0; c < 9; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int c = 0; c < 9; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 9; ++c) partials[(int64_t)blockIdx.x * 9 + c] = red[c][0];
+}
+
+}  // namespace dem

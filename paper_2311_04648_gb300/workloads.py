@@ -409,3 +409,151 @@ def free_clumps(n=60, R=1e-3, box=0.03, vel_sigma=0.5, E=1e7, nu=0.3, e=0.7, mu=
     return Scene(lo, hi, Em, num, corm, mum, box_walls(lo, hi) if walls else [],
                  [rod_template(R), tetra_template(R)], kinds, None, x, q, v, wb, h, np.array(g, np.float64),
                  r_max=R, name=f"free_clumps_n{n}")
+
+
+# ----------------------------------------------------------------------------- contact-rich test beds
+
+def dense_lattice(n=1000, R=1e-3, spacing=1.97e-3, jitter=0.05e-3, scale_spread=0.03, vel_sigma=0.2,
+                  omega_sigma=100.0, e=0.5, mu=0.4, E=1e7, nu=0.3, seed=0, h=1e-6, walls=True,
+                  g=(0.0, 0.0, -9.81), wall_overlap=0.02e-3) -> Scene:
+    """A jittered cubic lattice of spacing below 2R (many lattice neighbours overlap),
+    radii R * U[1 - s, 1 + s], random velocities and spins; the box walls touch the
+    outer layers with a small overlap."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil(n ** (1.0 / 3.0)))
+    idx = np.arange(n)
+    pts = np.stack([idx % m, (idx // m) % m, idx // (m * m)], axis=1).astype(np.float64) * spacing
+    pts += rng.uniform(-jitter, jitter, size=(n, 3))
+    scale = rng.uniform(1.0 - scale_spread, 1.0 + scale_spread, size=n)
+    rad = R * scale
+    lo = np.min(pts - rad[:, None], axis=0) + wall_overlap
+    hi = np.max(pts + rad[:, None], axis=0) - wall_overlap
+    pad = 0.0 if walls else 5 * R
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    v = rng.normal(scale=vel_sigma, size=(n, 3))
+    wb = rng.normal(scale=omega_sigma, size=(n, 3))
+    return Scene(lo - pad, hi + pad, Em, num, corm, mum, box_walls(lo, hi) if walls else [], [sphere_template(R)],
+                 np.zeros(n, np.int64), scale, pts, _identity_quats(n), v, wb, h, np.array(g, np.float64),
+                 r_max=float(rad.max()), name=f"dense_lattice_n{n}_seed{seed}")
+
+
+def packed_clumps(n=150, R=1e-3, fill=0.15, max_overlap=0.12, vel_sigma=0.3, omega_sigma=100.0, e=0.5, mu=0.4,
+                  E=1e7, nu=0.3, seed=0, h=1e-6, walls=True, g=(0.0, 0.0, -9.81)) -> Scene:
+    """Rods and tetrahedra placed by random sequential addition with random orientations
+    in a box holding them at solid fraction ``fill``; spheres of different clumps may
+    overlap by up to ``max_overlap`` R, so many pairs start in contact."""
+    rng = np.random.default_rng(seed)
+    tpls = [rod_template(R), tetra_template(R)]
+    kinds = rng.integers(0, 2, size=n).astype(np.int64)
+    vol = float(np.sum(np.where(kinds == 0, 3, 4))) * (4.0 / 3.0) * math.pi * R ** 3
+    side = (vol / fill) ** (1.0 / 3.0)
+    lo = np.zeros(3)
+    hi = np.full(3, side)
+    xs, qs, cents = [], [], []
+    allp = np.zeros((0, 3))
+    for k in range(n):
+        t = tpls[int(kinds[k])]
+        for _ in range(5000):
+            q = _random_quats(rng, 1)[0]
+            qw, qx, qy, qz = q
+            Rm = np.array([[1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)],
+                           [2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)],
+                           [2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)]])
+            c = lo + 3.05 * R + rng.random(3) * (side - 6.1 * R)
+            p = c + t.rel_xyz @ Rm.T
+            if np.any(p - R < lo) or np.any(p + R > hi):
+                continue
+            if len(allp):
+                d = np.linalg.norm(allp[None, :, :] - p[:, None, :], axis=-1)
+                if np.min(d) < 2 * R - max_overlap * R:
+                    continue
+            xs.append(c); qs.append(q)
+            allp = np.concatenate([allp, p])
+            break
+        else:
+            raise RuntimeError("clump placement did not converge; lower fill")
+    x = np.array(xs)
+    q = np.array(qs)
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    wl = box_walls(lo + 0.05 * R, hi - 0.05 * R) if walls else []    # outer spheres touch the walls
+    return Scene(lo, hi, Em, num, corm, mum, wl, tpls, kinds, None, x, q,
+                 rng.normal(scale=vel_sigma, size=(n, 3)), rng.normal(scale=omega_sigma, size=(n, 3)), h,
+                 np.array(g, np.float64), r_max=R, name=f"packed_clumps_n{n}_seed{seed}")
+
+
+def drum_bed(n=150, R=1e-3, drum_radius=0.03, length=0.03, omega=3.0, e=0.5, mu=0.5, E=1e7, nu=0.3, seed=0,
+             h=1e-6) -> Scene:
+    """Clumps (rods, tetrahedra) in the lower part of a drum about x spinning at omega,
+    pushed radially outwards until the outermost sphere overlaps the drum by 0.02 R."""
+    s = packed_clumps(n=n, R=R, seed=seed, e=e, mu=mu, E=E, nu=nu, h=h, walls=False)
+    c = s.x - np.mean(s.x, axis=0)
+    c[:, 2] -= 0.45 * drum_radius
+    # outermost radial extent of every clump's spheres about the x axis
+    def extent(cc):
+        out = 0.0
+        for k in range(len(cc)):
+            t = s.templates[int(s.owner_template[k])]
+            qw, qx, qy, qz = s.q[k]
+            Rm = np.array([[1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)],
+                           [2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)],
+                           [2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)]])
+            p = cc[k] + t.rel_xyz @ Rm.T
+            out = max(out, float(np.max(np.hypot(p[:, 1], p[:, 2]) + t.radii)))
+        return out
+    lo_f, hi_f = 0.1, 10.0
+    target = drum_radius + 0.02 * R
+    for _ in range(60):
+        mid = 0.5 * (lo_f + hi_f)
+        cc = c.copy()
+        cc[:, 1:] *= mid
+        if extent(cc) > target:
+            hi_f = mid
+        else:
+            lo_f = mid
+    c[:, 1:] *= hi_f
+    s.x = c
+    axis = np.array([1.0, 0.0, 0.0])
+    half = max(length / 2, float(np.max(np.abs(c[:, 0]))) + 3.1 * R)
+    s.walls = [dict(type=CYLINDER, mat=0, p=np.zeros(3), n=axis, r0=drum_radius, omega=omega * axis),
+               dict(type=PLANE, mat=0, p=np.array([-half, 0, 0]), n=axis.copy(), omega=omega * axis),
+               dict(type=PLANE, mat=0, p=np.array([half, 0, 0]), n=-axis, omega=omega * axis)]
+    s.box_lo = np.array([-half, -drum_radius, -drum_radius])
+    s.box_hi = np.array([half, drum_radius, drum_radius])
+    s.name = f"drum_bed_n{n}_seed{seed}"
+    return s
+
+
+def cone_bed(n=300, R=1e-3, half_angle_deg=30.0, r_orifice=0.01, e=0.5, mu=0.4, E=1e7, nu=0.3, seed=0, h=1e-6,
+             vel_sigma=0.2, sink_z=0.004) -> Scene:
+    """Spheres resting against a conical hopper wall (overlap 0.02 R) at random heights
+    and azimuths, plus a few falling through the orifice towards a sink plane."""
+    rng = np.random.default_rng(seed)
+    tan = math.tan(math.radians(half_angle_deg))
+    cosw = math.cos(math.atan(tan))
+    z_top = 0.06
+    pts = []
+    tries = 0
+    while len(pts) < n - 5 and tries < 100 * n:
+        tries += 1
+        z = rng.uniform(0.004, z_top - 0.004)
+        phi = rng.uniform(0, 2 * math.pi)
+        rw = r_orifice + z * tan          # wall point (rw, z); inward normal (-cos, sin)
+        d = R - 0.02 * R
+        rho = rw - d * cosw
+        p = np.array([rho * math.cos(phi), rho * math.sin(phi), z + d * math.sin(math.atan(tan))])
+        if all(np.sum((p - qq) ** 2) > (1.9 * R) ** 2 for qq in pts):
+            pts.append(p)
+    for k in range(5):
+        pts.append(np.array([0.002 * k - 0.004, 0.0, sink_z + 0.0006]))
+    pts = np.array(pts)
+    m = len(pts)
+    v = rng.normal(scale=vel_sigma, size=(m, 3))
+    v[-5:] = [0.0, 0.0, -1.0]
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    axis = np.array([0.0, 0.0, 1.0])
+    r_top = r_orifice + z_top * tan
+    walls = [dict(type=CONE, mat=0, p=np.zeros(3), n=axis, r0=r_orifice, z0=0.0, r1=r_top, z1=z_top)]
+    return Scene(np.array([-r_top, -r_top, -0.01]), np.array([r_top, r_top, z_top]), Em, num, corm, mum, walls,
+                 [sphere_template(R)], np.zeros(m, np.int64), None, pts, _identity_quats(m), v,
+                 rng.normal(scale=50.0, size=(m, 3)), h, np.array([0.0, 0.0, -9.81]),
+                 sink=(np.array([0.0, 0.0, sink_z]), axis.copy()), r_max=R, name=f"cone_bed_n{m}_seed{seed}")

@@ -1,0 +1,367 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 CPU oracle.
+
+Bars: contact sets bit-exact (same predicate, same positions); FP64 plain form within
+1e-9 relative on forces and states (relative to the scale of the summed terms); the
+voxel + FP32 form within 1e-4 on per-contact forces (error normalised by
+max(|F64|, 1e-3 median |F64|)); schedules and batching bit-identical to the plain run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_04648_gb300 import dem, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+def dense_scene(n=1200, seed=3, vel=0.2, e=0.5, mu=0.4, h=1e-6):
+    return W.dense_lattice(n=n, seed=seed, vel_sigma=vel, e=e, mu=mu, h=h)
+
+
+def rel_err(a, b, scale):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b)) / scale))
+
+
+def owner_scale(ow, cs, F):
+    """Per-owner scale: sum of |contact force| plus |m g| (the terms the sums add)."""
+    sc = np.abs(ow.mass)[:, None] * 9.81 * np.ones((1, 3))
+    for c in cs:
+        oi = ow.owner[c["i"]]
+        sc[oi] += np.abs(c["force"])
+        if c["j"] >= 0:
+            sc[ow.owner[c["j"]]] += np.abs(c["force"])
+    return sc + 1e-300
+
+
+def torque_scale(ow, cs):
+    sc = np.zeros((ow.n_owner, 3)) + 1e-300
+    for c in cs:
+        for side, sgn in ((c["i"], 1.0), (c["j"], -1.0)):
+            if side < 0:
+                continue
+            o = ow.owner[side]
+            arm = np.abs(np.array(c["point"]) - ow.x[o])
+            sc[o] += np.linalg.norm(arm) * np.abs(c["force"]).max() * np.ones(3)
+    return sc
+
+
+# ----------------------------------------------------------------------------- radix sort
+
+@pytest.mark.parametrize("n,bits", [(0, 8), (1, 8), (1000, 13), (4096 * 3 + 17, 23), (300_000, 32), (65_537, 9)])
+def test_radix_sort_is_a_stable_sort(n, bits):
+    rng = np.random.default_rng(n + bits)
+    hi = 1 << bits if bits < 32 else 1 << 32
+    keys = rng.integers(0, min(hi, 1 << 32), size=n, dtype=np.uint64).astype(np.uint32)
+    if n > 10:
+        keys[: n // 3] = keys[0]                   # many equal keys
+    vals = np.arange(n, dtype=np.uint32)
+    ko, vo = dem.radix_sort_u32(keys, vals, bits)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(ko, keys[order])
+    assert np.array_equal(vo, vals[order])
+
+
+# ----------------------------------------------------------------------------- contact sets
+
+@pytest.mark.parametrize("precision", ["fp64", "voxel_fp32"])
+def test_listed_sets_bit_exact(precision):
+    s = dense_scene(n=1500, seed=4)
+    beta = 4e-5
+    w = dem.World.from_scene(s, precision=precision, margin=beta)
+    ow = oracle.OracleWorld(s)
+    gi, gj = w.listed_pairs()
+    assert len(gi) > 1000
+    if precision == "fp64":
+        p, r = w.sphere_positions()
+        oi, oj = oracle.listed_pairs_f64(p, r, ow.owner, beta)
+        ow.rad[:] = r
+    else:
+        cell, off, L = w.sphere_voxels()
+        _, r = w.sphere_positions()
+        oi, oj = oracle.listed_pairs_voxel_f32(cell, off, np.float32(L), r.astype(np.float32), ow.owner,
+                                               np.float32(beta))
+        lo = np.asarray(s.box_lo)
+        p = (lo + cell.astype(np.float64) * L) + off.astype(np.float64)
+        ow.rad[:] = r.astype(np.float32).astype(np.float64)
+    assert np.array_equal(gi, oi) and np.array_equal(gj, oj)
+    si, wi = w.listed_wall_pairs()
+    osi, owi = ow.listed_wall_pairs(p, beta)
+    assert len(si) > 10
+    assert np.array_equal(si, osi) and np.array_equal(wi, owi)
+
+
+def test_listed_sets_bit_exact_for_clumps():
+    s = W.packed_clumps(n=150, seed=5)
+    beta = 5e-5
+    w = dem.World.from_scene(s, precision="fp64", margin=beta)
+    ow = oracle.OracleWorld(s)
+    p, r = w.sphere_positions()
+    po = ow.sphere_positions()
+    assert np.max(np.abs(p - po)) == 0.0       # same exactly rounded formula on both sides
+    gi, gj = w.listed_pairs()
+    oi, oj = oracle.listed_pairs_f64(p, r, ow.owner, beta)
+    assert len(gi) > 50
+    assert np.array_equal(gi, oi) and np.array_equal(gj, oj)
+
+
+# ----------------------------------------------------------------------------- forces
+
+def compare_contacts(w, ow, tol):
+    gc = w.contacts()
+    F, T, oc = ow.eval()
+    assert np.array_equal(gc["i"], oc["i"]) and np.array_equal(gc["j"], oc["j"])
+    fs = np.abs(oc["force"]).max(axis=1, keepdims=True) + 1e-300
+    assert rel_err(gc["force"], oc["force"], fs) < tol
+    assert rel_err(gc["overlap"], oc["overlap"], oc["overlap"]) < tol * 1e3   # small differences of O(R)
+    assert rel_err(gc["point"], oc["point"], 1e-3) < tol
+    hs = np.abs(oc["ut"]).max(axis=1, keepdims=True) + 1e-20
+    assert rel_err(gc["history"], oc["ut"], hs) < tol * 1e3
+    return gc, oc
+
+
+def test_fp64_forces_match_oracle_at_initial_and_later_states():
+    s = dense_scene(n=800, seed=6)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    for rnd in range(3):
+        gc, oc = compare_contacts(w, ow, TOL64)
+        assert len(oc) > 200
+        Fg, Tg = w.owner_forces()
+        Fo, To, _ = ow.eval()
+        assert rel_err(Fg, Fo, owner_scale(ow, oc, Fo)) < TOL64
+        assert rel_err(Tg, To, torque_scale(ow, oc)) < TOL64
+        w.step(25)
+        ow.step(25)
+
+
+def state_close(w, ow, tol):
+    x, q, v, wb = w.owner_state()
+    ext = float(np.max(np.abs(ow.x))) + 1e-300
+    vs = float(np.max(np.abs(ow.v))) + 1e-300
+    ws = float(np.max(np.abs(ow.wb))) + 1e-300
+    errs = dict(x=rel_err(x, ow.x, ext), v=rel_err(v, ow.v, vs), w=rel_err(wb, ow.wb, ws),
+                q=rel_err(q * np.sign(q[:, :1] + 1e-300), ow.q * np.sign(ow.q[:, :1] + 1e-300), 1.0))
+    return errs, max(errs.values()) < tol
+
+
+def test_fp64_trajectory_matches_oracle_random_spheres_in_a_box():
+    s = W.settle_box(n=2000, seed=2, vel_sigma=0.3)       # 2,000 spheres, 40x40x80 mm box
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    for _ in range(4):
+        w.step(75)
+        ow.step(75)
+        errs, ok = state_close(w, ow, TOL64)
+        assert ok, errs
+    st = w.stats()
+    assert st["steps"] == 300 and st["rebuilds"] >= 300
+
+
+def test_fp64_trajectory_matches_oracle_dense_polydisperse():
+    s = dense_scene(n=600, seed=8, vel=0.5)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    w.step(200)
+    ow.step(200)
+    errs, ok = state_close(w, ow, 1e-8)
+    assert ok, errs
+    compare_contacts(w, ow, 1e-8)
+
+
+def test_fp64_trajectory_matches_oracle_clumps_with_walls_and_gravity():
+    s = W.packed_clumps(n=150, seed=10)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    w.step(300)
+    ow.step(300)
+    errs, ok = state_close(w, ow, 1e-8)
+    assert ok, errs
+
+
+def test_fp64_trajectory_matches_oracle_in_a_spinning_drum():
+    s = W.drum_bed(n=120, seed=1)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    w.step(400)
+    ow.step(400)
+    errs, ok = state_close(w, ow, 1e-8)
+    assert ok, errs
+    assert len(ow.eval()[2]) > 20
+
+
+def test_fp64_trajectory_matches_oracle_in_a_cone_hopper_with_sink():
+    s = W.cone_bed(n=300, seed=13)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    w.step(500)
+    ow.step(500)
+    errs, ok = state_close(w, ow, 1e-8)
+    assert ok, errs
+    assert ow.active.sum() < len(ow.active)          # some spheres went through the sink
+
+
+# ----------------------------------------------------------------------------- voxel + FP32
+
+def test_voxel_fp32_forces_within_1e4_of_fp64():
+    s = dense_scene(n=1500, seed=14)
+    w = dem.World.from_scene(s, precision="voxel_fp32")
+    ow = oracle.OracleWorld(s)
+    gc = w.contacts()
+    F, T, oc = ow.eval()
+    key_g = {(a, b): k for k, (a, b) in enumerate(zip(gc["i"], gc["j"]))}
+    key_o = {(a, b): k for k, (a, b) in enumerate(zip(oc["i"], oc["j"]))}
+    common = sorted(set(key_g) & set(key_o))
+    # contacts that appear on one side only must be at vanishing overlap
+    for k in set(key_g) ^ set(key_o):
+        ov = gc["overlap"][key_g[k]] if k in key_g else oc["overlap"][key_o[k]]
+        assert ov < 1e-9
+    fo = np.array([oc["force"][key_o[k]] for k in common])
+    fg = np.array([gc["force"][key_g[k]] for k in common])
+    mag = np.linalg.norm(fo, axis=1)
+    floor = 1e-3 * np.median(mag)
+    err = np.linalg.norm(fg - fo, axis=1) / np.maximum(mag, floor)
+    assert len(common) > 500
+    assert err.max() <= 1e-4, (err.max(), np.percentile(err, 99))
+
+
+def test_voxel_fp32_trajectory_close_to_oracle_over_short_run():
+    s = dense_scene(n=500, seed=15, vel=0.2)
+    w = dem.World.from_scene(s, precision="voxel_fp32")
+    ow = oracle.OracleWorld(s)
+    w.step(50)
+    ow.step(50)
+    x, q, v, wb = w.owner_state()
+    assert np.max(np.abs(x - ow.x)) < 1e-8            # metres, after 50 steps
+    assert rel_err(v, ow.v, float(np.max(np.abs(ow.v)))) < 1e-3
+
+
+# ----------------------------------------------------------------------------- schedules, determinism
+
+@pytest.mark.parametrize("precision", ["fp64", "voxel_fp32"])
+def test_delayed_schedule_is_bit_identical_to_every_step(precision):
+    s = dense_scene(n=1000, seed=16, vel=0.3)
+    a = dem.World.from_scene(s, precision=precision, schedule="every_step")
+    b = dem.World.from_scene(s, precision=precision, schedule="velocity_bound", margin=5e-5, margin_max=5e-5)
+    a.step(200)
+    b.step(200)
+    for xa, xb in zip(a.owner_state(), b.owner_state()):
+        assert np.array_equal(xa, xb)
+    sb = b.stats()
+    assert sb["steps"] == 200
+    assert sb["rebuilds"] < 200
+
+
+def test_runs_are_deterministic():
+    s = dense_scene(n=800, seed=17)
+    a = dem.World.from_scene(s, precision="voxel_fp32")
+    b = dem.World.from_scene(s, precision="voxel_fp32")
+    a.step(100)
+    b.step(100)
+    for xa, xb in zip(a.owner_state(), b.owner_state()):
+        assert np.array_equal(xa, xb)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    s = dense_scene(n=600, seed=18)
+    a = dem.World.from_scene(s, precision="fp64", schedule="velocity_bound", margin=4e-5, margin_max=4e-5)
+    a.step(60)
+    blob = a.save_state()
+    a.step(60)
+    b = dem.World.from_scene(s, precision="fp64", schedule="velocity_bound", margin=4e-5, margin_max=4e-5)
+    b.load_state(blob)
+    b.step(60)
+    for xa, xb in zip(a.owner_state(), b.owner_state()):
+        assert np.array_equal(xa, xb)
+
+
+def test_batch_equals_separate_worlds():
+    scenes = [W.column_collapse(n, asp, mu, e, seed=40 + k)
+              for k, (n, asp, mu, e) in enumerate([(300, 1.0, 0.3, 0.5), (900, 2.5, 0.6, 0.8), (150, 0.5, 0.2, 0.3)])]
+    bt = dem.Batch(scenes, precision="fp64")
+    bt.initialize()
+    bt.step(100)
+    for k, s in enumerate(scenes):
+        w = dem.World.from_scene(s, precision="fp64")
+        w.step(100)
+        for xa, xb in zip(bt.worlds[k].owner_state(), w.owner_state()):
+            assert np.array_equal(xa, xb)
+
+
+# ----------------------------------------------------------------------------- failure paths
+
+def test_divergence_stops_at_the_last_good_step():
+    s = dense_scene(n=300, seed=19, vel=0.3)
+    s.v_err = 0.6
+    w = dem.World.from_scene(s, precision="fp64")
+    with pytest.raises(dem.DemError) as ei:
+        w.step(400)
+    assert ei.value.status == dem.ERR_DIVERGED
+    k = w.stats()["steps"]
+    ow = oracle.OracleWorld(s)
+    ow._w.v_err = 0.0
+    ow.step(k)
+    errs, ok = state_close(w, ow, 1e-8)
+    assert ok, errs
+    assert np.max(np.linalg.norm(w.owner_state()[2], axis=1)) <= 0.6
+
+
+def test_list_capacity_regrows_on_overflow():
+    # small spheres packed around large ones: rows far beyond the initial capacity
+    rng = np.random.default_rng(20)
+    big = W.sphere_template(3e-3)
+    small = W.sphere_template(0.6e-3)
+    xb = np.array([[0.02, 0.02, 0.02]])
+    dirs = rng.normal(size=(60, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    xs = xb + dirs * (3.55e-3)
+    x = np.concatenate([xb, xs])
+    s = W.Scene(np.zeros(3), np.full(3, 0.04), np.array([1e7]), np.array([0.3]), np.array([[0.5]]),
+                np.array([[0.4]]), [], [big, small], np.array([0] + [1] * 60), None, x,
+                np.tile([1.0, 0, 0, 0], (61, 1)), np.zeros((61, 3)), np.zeros((61, 3)), 1e-6, np.zeros(3))
+    w = dem.World.from_scene(s, precision="fp64", margin=1e-4, margin_max=1e-4)
+    st = w.stats()
+    assert st["overflow_regrows"] >= 1 and st["list_capacity"] > 16
+    ow = oracle.OracleWorld(s)
+    compare_contacts(w, ow, TOL64)
+    w.step(20)
+    ow.step(20)
+    errs, ok = state_close(w, ow, 1e-8)
+    assert ok, errs
+
+
+def test_set_owner_state_forces_a_rebuild_and_keeps_history():
+    s = dense_scene(n=500, seed=21)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    w.step(30)
+    ow.step(30)
+    x, q, v, wb = w.owner_state()
+    x2 = x.copy()
+    x2[:, 0] += 1e-7            # a rigid shift keeps every contact
+    w.set_owner_state(0, xyz=x2)
+    ow.x[:] = x2
+    ow.q[:] = q
+    ow.v[:] = v
+    ow.wb[:] = wb
+    w.step(10)
+    ow.step(10)
+    errs, ok = state_close(w, ow, 1e-8)
+    assert ok, errs
+
+
+def test_diagnostics_match_oracle():
+    s = dense_scene(n=700, seed=22)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s)
+    w.step(20)
+    ow.step(20)
+    dg = w.diagnostics()
+    do = ow.diagnostics()
+    for k in ("ke", "pe", "elastic"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-8)
+    assert np.allclose(dg["momentum"], do["momentum"], rtol=1e-8, atol=1e-14)
+    assert np.allclose(dg["angmom"], do["angmom"], rtol=1e-8, atol=1e-16)
