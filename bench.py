@@ -337,7 +337,7 @@ def main():
                 "d2h_bytes_per_step": e2e["bytes_out"],
                 "how": "dem_set_owner_state from pinned host buffers + dem_step(1) + dem_get_owner_state "
                        "to pinned host buffers, every step"},
-        "gpu_launches": int(2 * steps + 15 * res["chosen"]["rebuilds"]),
+        "gpu_launches": int(2 * steps + 18 * res["chosen"]["rebuilds"]),
         "clocks": res["chosen"]["clocks"],
     }
     if plain:

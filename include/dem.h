@@ -99,7 +99,7 @@ typedef struct {
     double displacement_bound;     /* audited displacement bound since the list snapshot   */
     double max_speed;              /* max |v| over owners at the last audit                */
     double mean_steps_per_build;   /* steps / rebuilds                                     */
-    double cell_size;              /* cell (= voxel) edge                                  */
+    double cell_size;              /* detection cell edge                                  */
     int64_t n_cells;               /* cells of all scenes                                  */
     double ms_detect, ms_force;    /* profiled GPU time: detection (sort, cells, narrow) /
                                       force + integration kernel (dem_set_profiling)       */
@@ -185,7 +185,9 @@ dem_status dem_set_gravity(dem_world *w, const double g[3]);
 dem_status dem_set_error_velocity(dem_world *w, double v);
 /* Contact margin beta >= 0 added to every sphere for detection (Sec. 2.1: artificial
  * margin); must not exceed desc.margin_max.  EVERY_STEP defaults to 0, the delayed
- * schedules to margin_max. */
+ * schedules to margin_max.  A floor of 16 ulps of the largest centre distance in the
+ * form's precision is always applied, so that the listed predicate never drops a
+ * touching pair to rounding. */
 dem_status dem_set_margin(dem_world *w, double beta);
 /* Owners whose centre of mass x satisfies (x - p).n < 0 after a step are removed from
  * the simulation (frozen, no contacts): the hopper outlet. */
@@ -223,10 +225,10 @@ dem_status dem_set_owner_state(dem_world *w, int64_t first, int64_t n, const dou
                                const double *quat, const double *vel, const double *omega);
 /* Sphere centres (world frame) and radii for sphere ids [first, first + n). */
 dem_status dem_get_sphere_positions(dem_world *w, int64_t first, int64_t n, double *xyz, double *radius);
-/* The voxel encoding of sphere centres (DEM_PRECISION_VOXEL_FP32 only): integer cell
- * cell[3n] and FP32 offset offset[3n] in [0, edge) per axis, centre = (scene box_lo +
- * cell * edge) + offset; *edge (nullable) receives the cell edge.  DEM_ERR_STATE in the
- * FP64 form. */
+/* The voxel encoding of sphere centres (DEM_PRECISION_VOXEL_FP32 only): integer voxel
+ * index cell[3n] and FP32 offset offset[3n] in [0, edge) per axis, centre = (scene
+ * box_lo + cell * edge) + offset; *edge (nullable) receives the voxel edge, a power of
+ * two at most 1/16 of the detection cell.  DEM_ERR_STATE in the FP64 form. */
 dem_status dem_get_sphere_voxels(dem_world *w, int64_t first, int64_t n, int32_t *cell, float *offset, double *edge);
 /* Every contact with overlap > 0 at the current state, ordered by (i, partner) with
  * spheres before walls.  i < j for sphere pairs; j = -1 - wall_id for walls.  force[3]

@@ -161,16 +161,36 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
     if (rmax <= 0.0) rmax = 1e-3;
     m.r_max = rmax;
     double mmax = d0.margin_max > 0 ? d0.margin_max : 0.05 * rmax;
-    double margin = 0.0;
+    double margin = -1.0;
     for (auto &sc : W.scenes) margin = std::max(margin, sc.margin);
     if (margin < 0) margin = (d0.schedule == DEM_SCHEDULE_EVERY_STEP) ? 0.0 : mmax;
     if (margin > mmax) {
         err = "margin exceeds margin_max";
         return DEM_ERR_ARG;
     }
+    // The listed predicate is evaluated in the form's own precision while contacts are
+    // decided from an (almost) exact overlap: a floor of a few ulps of the largest
+    // centre distance keeps every touching pair listed even at margin 0.
+    const bool vox = d0.precision == DEM_PRECISION_VOXEL_FP32;
+    const double floor_margin = vox ? 16.0 * std::ldexp(1.0, std::ilogb(2.0 * (rmax + mmax)) - 23)
+                                    : 16.0 * std::ldexp(1.0, std::ilogb(2.0 * (rmax + mmax)) - 52);
+    if (margin < floor_margin) margin = floor_margin;
+    if (mmax < margin) mmax = margin;
     m.margin = margin;
     m.margin_max = mmax;
-    m.L = 1.001 * 2.0 * (rmax + mmax);
+    const double Lmin = 1.001 * 2.0 * (rmax + mmax);
+    if (vox) {
+        // voxels: a power of two at most 1/16 of the cell, so that integer voxel
+        // differences times the voxel edge are exact in FP32 and the FP32 offset inside
+        // a voxel resolves ~2^-24 of it; a cell is a whole number of voxels
+        m.Lv = std::ldexp(1.0, (int)std::floor(std::log2(Lmin / 16.0)));
+        m.vpc = (int)std::ceil(Lmin / m.Lv);
+        m.L = m.vpc * m.Lv;
+    } else {
+        m.L = Lmin;
+        m.Lv = Lmin;
+        m.vpc = 1;
+    }
     m.clumps = clumps;
 
     uint64_t cell_base = 0;
@@ -237,6 +257,8 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
             w.mat = g.mat_base + ws.mat;
             for (int a = 0; a < 3; ++a) { w.p[a] = ws.p[a]; w.n[a] = ws.n[a]; w.omega[a] = ws.omega[a]; }
             w.r0 = ws.r0; w.z0 = ws.z0; w.r1 = ws.r1; w.z1 = ws.z1;
+            for (int a = 0; a < 3; ++a) { w.pf[a] = (float)ws.p[a]; w.nf[a] = (float)ws.n[a]; }
+            w.r0f = (float)ws.r0;
             m.walls.push_back(w);
         }
         m.scenes.push_back(g);
@@ -260,6 +282,7 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
             for (int a = 0; a < 3; ++a) m.x.push_back(sc.inst_x[3 * k + a]);
             double q[4] = {sc.inst_q[4 * k], sc.inst_q[4 * k + 1], sc.inst_q[4 * k + 2], sc.inst_q[4 * k + 3]};
             double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+            if (std::fabs(qn - 1.0) < 1e-14) qn = 1.0;          // unit input is kept bit for bit
             for (int a = 0; a < 4; ++a) m.q.push_back(q[a] / qn);
             for (int a = 0; a < 3; ++a) { m.v.push_back(sc.inst_v[3 * k + a]); m.wb.push_back(sc.inst_w[3 * k + a]); }
             m.mass.push_back(t.mass * s * s * s);
@@ -736,7 +759,7 @@ dem_status dem_get_sphere_voxels(dem_world *w, int64_t first, int64_t n, int32_t
     if (first < 0 || n < 0 || first + n > scene_spheres(w)) return fail(w, DEM_ERR_ARG, "sphere range out of bounds");
     if (w->impl->desc.precision != DEM_PRECISION_VOXEL_FP32)
         return fail(w, DEM_ERR_STATE, "voxel encoding exists only in the VOXEL_FP32 form");
-    if (edge) *edge = w->impl->model.L;
+    if (edge) *edge = w->impl->model.Lv;
     if (n == 0) return DEM_OK;
     if (!cell || !offset) return fail(w, DEM_ERR_ARG, "null output");
     std::string err;

@@ -94,11 +94,13 @@ template <typename R> DEM_HD V3<R> mat_tvec(const R m[9], V3<R> a)
 
 // ------------------------------------------------------------------ scene-level data
 
-struct Wall {            // analytical wall (device copy); all in FP64
+struct Wall {            // analytical wall (device copy); geometry in FP64
     int type, mat;       // global material id
     double p[3], n[3];
     double r0, z0, r1, z1;
     double omega[3];
+    float pf[3], nf[3];  // FP32 copies for screening tests (never decide a contact)
+    float r0f, pad;
 };
 
 struct Scene {           // per-scene constants (device copy)
@@ -117,6 +119,9 @@ struct Scene {           // per-scene constants (device copy)
 struct PairParam {       // pairwise contact constants, precomputed on the host in FP64
     double Estar, Gstar, beta, mu;
 };
+struct PairParamF {      // the same rounded to FP32 once, for the voxel form
+    float Estar, Gstar, beta, mu;
+};
 
 // Device-resident control block (one per world).  Kernels read the selectors and flags
 // here, so the host can queue work (or replay a CUDA graph) without knowing in advance
@@ -133,6 +138,9 @@ struct DevStatus {
     unsigned int step_disp_bits; // max over owners of this step's displacement bound (float bits)
     unsigned int vmax_bits;      // max |v| over owners this step (float bits)
     int pad0, pad1;
+    // per-warp maxima land in AUDIT_SLOTS spread slots (float bits), reduced by k_audit
+    unsigned int disp_slots[64];
+    unsigned int vmax_slots[64];
     double disp_cur;             // displacement bound since the snapshot of the list in use
     double disp_next;            // ... since the snapshot of the list being built
     double beta_cur, beta_next;  // margins of those lists
@@ -183,7 +191,7 @@ struct FormF64 {
     }
     __device__ static Pos advance(Pos p, V3<R> d, float /*L*/) { return Pos{radd(p.x, d.x), radd(p.y, d.y), radd(p.z, d.z)}; }
     // cell of a position in a scene grid (unclamped)
-    __device__ static void cell(const Pos &p, const Scene &sc, double invL, int &cx, int &cy, int &cz)
+    __device__ static void cell(const Pos &p, const Scene &sc, double invL, int /*vpc*/, int &cx, int &cy, int &cz)
     {
         cx = (int)floor(rmul(rsub(p.x, sc.lo[0]), invL));
         cy = (int)floor(rmul(rsub(p.y, sc.lo[1]), invL));
@@ -242,9 +250,11 @@ struct FormF32 {
         carry(q.cx, q.x, L); carry(q.cy, q.y, L); carry(q.cz, q.z, L);
         return q;
     }
-    __device__ static void cell(const Pos &p, const Scene &, double, int &cx, int &cy, int &cz)
+    // detection cell of a voxel: floor division by the voxels per cell edge
+    __device__ static int floordiv(int a, int b) { int q = a / b; return (a % b != 0 && a < 0) ? q - 1 : q; }
+    __device__ static void cell(const Pos &p, const Scene &, double, int vpc, int &cx, int &cy, int &cz)
     {
-        cx = p.cx; cy = p.cy; cz = p.cz;
+        cx = floordiv(p.cx, vpc); cy = floordiv(p.cy, vpc); cz = floordiv(p.cz, vpc);
     }
     // world-frame position in FP64: (lo + c L) + o
     __device__ static V3<double> absolute(const Pos &p, const Scene &sc, double L)

@@ -60,16 +60,83 @@ __device__ __forceinline__ void hertz_mindlin(const ContactIn<R> &c, R h, V3<R> 
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void load_pair(const PairParam *pairs, const uint16_t *mat_scene, const uint16_t *mat_local,
-                                          const Scene *scenes, int ga, int gb, ContactIn<R> &c)
+// Error-free transformations in FP32 (Knuth's TwoSum; the product error from an FMA).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Overlap (Ra + Rb) - |pa - pb| of two voxel-form centres, evaluated in float-float so
+// that it keeps ~2^-44 of the centre distance (the paper keeps the penetration in a
+// wider type than the rest of the force arithmetic, Sec. 2.3); FP32 pipes only.  Also
+// returns the rounded difference vector and distance for the rest of the contact.
+__device__ __forceinline__ float overlap_ff(const PosF32 &a, const PosF32 &b, float Lv, float ra_hi, float ra_lo,
+                                            float rb_hi, float rb_lo, V3<float> &dv, float &dist)
+{
+    const int ca[3] = {a.cx, a.cy, a.cz}, cb[3] = {b.cx, b.cy, b.cz};
+    const float oa[3] = {a.x, a.y, a.z}, ob[3] = {b.x, b.y, b.z};
+    float xs[3];
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float ax = __fmul_rn((float)(ca[k] - cb[k]), Lv);       // exact: small integer times 2^e
+        float bh, bl;
+        two_sum(oa[k], -ob[k], bh, bl);                          // exact offset difference
+        float xh, xl;
+        two_sum(ax, bh, xh, xl);
+        xl = __fadd_rn(xl, bl);
+        xs[k] = xh;
+        float p = __fmul_rn(xh, xh);
+        float pe = __fmaf_rn(xh, xh, -p);
+        float t, te;
+        two_sum(sh, p, t, te);
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(te, pe), __fmul_rn(2.0f * xh, xl)));
+    }
+    float s2, e2;
+    two_sum(sh, sl, s2, e2);
+    float dh = __fsqrt_rn(s2);
+    float res = __fadd_rn(__fmaf_rn(-dh, dh, s2), e2);           // s - dh^2, exact residual + low part
+    float dl = __fdiv_rn(res, 2.0f * dh);
+    float rh, rl;
+    two_sum(ra_hi, rb_hi, rh, rl);
+    rl = __fadd_rn(rl, __fadd_rn(ra_lo, rb_lo));
+    dv = {xs[0], xs[1], xs[2]};
+    dist = dh;
+    return __fadd_rn(__fsub_rn(rh, dh), __fsub_rn(rl, dl));
+}
+
+__device__ __forceinline__ void load_pair(const PairParam *pairs, const PairParamF *, const uint16_t *mat_scene,
+                                          const uint16_t *mat_local, const Scene *scenes, int ga, int gb,
+                                          ContactIn<double> &c)
 {
     const Scene &sc = scenes[mat_scene[ga]];
     const PairParam p = pairs[sc.pair_base + (int)mat_local[ga] * sc.n_mat + (int)mat_local[gb]];
-    c.Estar = (R)p.Estar;
-    c.Gstar = (R)p.Gstar;
-    c.beta = (R)p.beta;
-    c.mu = (R)p.mu;
+    c.Estar = p.Estar;
+    c.Gstar = p.Gstar;
+    c.beta = p.beta;
+    c.mu = p.mu;
+}
+__device__ __forceinline__ void load_pair(const PairParam *, const PairParamF *pairs, const uint16_t *mat_scene,
+                                          const uint16_t *mat_local, const Scene *scenes, int ga, int gb,
+                                          ContactIn<float> &c)
+{
+    const Scene &sc = scenes[mat_scene[ga]];
+    const PairParamF p = pairs[sc.pair_base + (int)mat_local[ga] * sc.n_mat + (int)mat_local[gb]];
+    c.Estar = p.Estar;
+    c.Gstar = p.Gstar;
+    c.beta = p.beta;
+    c.mu = p.mu;
+}
+
+// FP32 screen of a plane: true if the centre may be within `reach` of the plane.  The
+// allowance covers the rounding of the FP32 evaluation for coordinates of size `scale`.
+__device__ __forceinline__ bool plane_may_reach(const Wall &w, float3 p, float reach, float scale)
+{
+    float g = (p.x - w.pf[0]) * w.nf[0] + (p.y - w.pf[1]) * w.nf[1] + (p.z - w.pf[2]) * w.nf[2];
+    return g <= reach + 1e-5f * scale + 1e-9f;
 }
 
 // Signed gap of a sphere centre to a wall (positive on the domain side) and the unit

@@ -16,7 +16,9 @@ struct HostModel {
     int schedule = DEM_SCHEDULE_EVERY_STEP;
     int gyroscopic = 1;
     int device = 0;
-    double L = 0.0;                 // cell (= voxel) edge
+    double L = 0.0;                 // cell edge
+    double Lv = 0.0;                // voxel edge (voxel form: a power of two, L = vpc * Lv)
+    int vpc = 1;                    // voxels per cell edge
     double margin = 0.0;            // margin of the lists (EVERY_STEP) / upper bound (delayed)
     double margin_max = 0.0;
     double r_max = 0.0;

@@ -65,9 +65,11 @@ public:
         d_.N = N;
         d_.Np = std::max<int64_t>(32, (N + 31) / 32 * 32);
         d_.K = 16;
-        d_.L = (float)m_.L;
-        d_.Ld = m_.L;
+        // position unit: the voxel edge in the voxel form, the cell edge in the FP64 form
+        d_.L = (float)(F::voxel ? m_.Lv : m_.L);
+        d_.Ld = F::voxel ? m_.Lv : m_.L;
         d_.invL = 1.0 / m_.L;
+        d_.vpc = m_.vpc;
         d_.gyro = m_.gyroscopic;
         d_.n_scenes = (int)m_.scenes.size();
         beta_ = m_.margin;
@@ -93,6 +95,7 @@ public:
         if ((s = alloc(d_.owner_iso, M, err))) return s;
         if ((s = alloc(d_.sph_owner, N, err))) return s;
         if ((s = alloc(d_.sph_rad, N, err))) return s;
+        if ((s = alloc(d_.sph_rlo, N, err))) return s;
         if ((s = alloc(d_.sph_mat, N, err))) return s;
         if ((s = alloc(d_.sph_rloc, N, err))) return s;
         if ((s = alloc(d_.sph_head, N, err))) return s;
@@ -100,13 +103,16 @@ public:
         Scene *scenes;
         Wall *walls;
         PairParam *pairs;
+        PairParamF *pairs_f;
         uint16_t *ms, *ml;
         if ((s = alloc(scenes, m_.scenes.size(), err))) return s;
         if ((s = alloc(walls, std::max<size_t>(1, m_.walls.size()), err))) return s;
         if ((s = alloc(pairs, m_.pairs.size(), err))) return s;
+        if ((s = alloc(pairs_f, m_.pairs.size(), err))) return s;
         if ((s = alloc(ms, m_.mat_scene.size(), err))) return s;
         if ((s = alloc(ml, m_.mat_local.size(), err))) return s;
-        d_.scenes = scenes; d_.walls = walls; d_.pairs = pairs; d_.mat_scene = ms; d_.mat_local = ml;
+        d_.scenes = scenes; d_.walls = walls; d_.pairs = pairs; d_.pairs_f = pairs_f;
+        d_.mat_scene = ms; d_.mat_local = ml;
         if ((s = alloc(st_, 1, err))) return s;
         DEM_CU(cudaMallocHost((void **)&sth_, sizeof(DevStatus)));
         if ((s = alloc_lists(d_.K, err))) return s;
@@ -150,9 +156,11 @@ public:
             inv_mass[o] = (R)(1.0 / m_.mass[o]);
         }
         std::vector<R> rad(N);
+        std::vector<float> rlo(N, 0.0f);
         std::vector<R4> rloc(N);
         for (int64_t k = 0; k < N; ++k) {
             rad[k] = (R)m_.sph_rad[k];
+            if (F::voxel) rlo[k] = (float)(m_.sph_rad[k] - (double)rad[k]);
             rloc[k] = R4{(R)m_.sph_rloc[3 * k], (R)m_.sph_rloc[3 * k + 1], (R)m_.sph_rloc[3 * k + 2], R(0)};
         }
         if ((s = up(d_.inv_moi, inv_moi.data(), M, err))) return s;
@@ -161,6 +169,7 @@ public:
         if ((s = up(d_.owner_iso, m_.owner_iso.data(), M, err))) return s;
         if ((s = up(d_.sph_owner, m_.sph_owner.data(), N, err))) return s;
         if ((s = up(d_.sph_rad, rad.data(), N, err))) return s;
+        if ((s = up(d_.sph_rlo, rlo.data(), N, err))) return s;
         if ((s = up(d_.sph_mat, m_.sph_mat.data(), N, err))) return s;
         if ((s = up(d_.sph_rloc, rloc.data(), N, err))) return s;
         if ((s = up(d_.sph_head, m_.sph_head.data(), N, err))) return s;
@@ -168,6 +177,13 @@ public:
         if ((s = up(scenes, m_.scenes.data(), m_.scenes.size(), err))) return s;
         if (!m_.walls.empty() && (s = up(walls, m_.walls.data(), m_.walls.size(), err))) return s;
         if ((s = up(pairs, m_.pairs.data(), m_.pairs.size(), err))) return s;
+        {
+            std::vector<PairParamF> pf(m_.pairs.size());
+            for (size_t k = 0; k < pf.size(); ++k)
+                pf[k] = PairParamF{(float)m_.pairs[k].Estar, (float)m_.pairs[k].Gstar, (float)m_.pairs[k].beta,
+                                   (float)m_.pairs[k].mu};
+            if ((s = up(pairs_f, pf.data(), pf.size(), err))) return s;
+        }
         if ((s = up(ms, m_.mat_scene.data(), m_.mat_scene.size(), err))) return s;
         if ((s = up(ml, m_.mat_local.data(), m_.mat_local.size(), err))) return s;
 
@@ -182,7 +198,7 @@ public:
             if ((s = up(d_.st.pos[0].xm, xm.data(), M, err))) return s;
         }
         DevStatus h{};
-        h.disp_slack = F::voxel ? 4.0 * (double)std::ldexp(1.0f, std::ilogb((float)m_.L) - 23) : 0.0;
+        h.disp_slack = F::voxel ? 4.0 * std::ldexp(1.0, std::ilogb(m_.Lv) - 23) : 0.0;
         h.beta_cur = h.beta_next = beta_;
         for (int64_t o = 0; o < M; ++o) {   // initial speed bound for the first cycle length
             double v2 = m_.v[3 * o] * m_.v[3 * o] + m_.v[3 * o + 1] * m_.v[3 * o + 1] + m_.v[3 * o + 2] * m_.v[3 * o + 2];
@@ -326,7 +342,7 @@ public:
     {
         out.clear();
         dem_status s;
-        if ((s = pull(err))) return s;
+        if ((s = fresh(err))) return s;
         const int64_t N = d_.N, K = d_.K, Np = d_.Np;
         if (N == 0) return DEM_OK;
         double *buf;
@@ -399,6 +415,7 @@ public:
         if (M == 0) return DEM_OK;
         double *buf;
         dem_status s;
+        if ((s = fresh(err))) return s;
         if ((s = scratch(buf, 6 * M, err))) return s;
         launch_force<MODE_EVAL>(buf, buf + 3 * M);
         DEM_CU(cudaGetLastError());
@@ -449,7 +466,7 @@ public:
     dem_status stats(dem_stats *o, std::string &err) override
     {
         dem_status s;
-        if ((s = pull(err))) return s;
+        if ((s = fresh(err))) return s;
         std::memset(o, 0, sizeof(*o));
         o->steps = sth_->steps_done;
         o->rebuilds = sth_->rebuilds;
@@ -494,6 +511,7 @@ public:
         const int64_t blocks = (n + 255) / 256;
         double *buf;
         dem_status s;
+        if ((s = fresh(err))) return s;
         if ((s = scratch(buf, 9 * blocks, err))) return s;
         if (m_.clumps) k_diag<F, true><<<(unsigned)blocks, 256, 0, sf_>>>(d_, buf);
         else k_diag<F, false><<<(unsigned)blocks, 256, 0, sf_>>>(d_, buf);
@@ -803,6 +821,20 @@ private:
         DEM_CU(cudaMemcpyAsync(sth_, st_, sizeof(DevStatus), cudaMemcpyDeviceToHost, sf_));
         DEM_CU(cudaStreamSynchronize(sf_));
         if (!marks_.empty()) harvest();
+        return DEM_OK;
+    }
+
+    // Read-backs that depend on the current contacts need a list that covers them: after
+    // a step the list in use may be stale (every-step lists are built before the step).
+    dem_status fresh(std::string &err)
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        if (sth_->halt == HALT_NONE && (sth_->list_stale || dirty_) && d_.N > 0) {
+            rebuild_inline(sf_);
+            if ((s = settle(err))) return s;
+            dirty_ = false;
+        }
         return DEM_OK;
     }
 

@@ -29,6 +29,7 @@ struct Dev {
     double Ld, invL;
     int gyro;                       // gyroscopic term on
     int n_scenes;
+    int vpc;                        // voxels per cell edge (voxel form)
     StateBuffers<F> st;
     ListBuffers<R> lists;
     R4 *inv_moi;                    // (1/I1, 1/I2, 1/I3, r_ext)
@@ -37,6 +38,7 @@ struct Dev {
     uint8_t *owner_iso;
     uint32_t *sph_owner;            // 0xffffffff: padding slot
     R *sph_rad;
+    float *sph_rlo;                 // voxel form: radius minus its FP32 rounding (float-float)
     uint16_t *sph_mat;
     R4 *sph_rloc;                   // body-frame offset (x, y, z, 0); clumps only
     uint8_t *sph_head;              // first slot of its owner
@@ -44,9 +46,23 @@ struct Dev {
     const Scene *scenes;
     const Wall *walls;
     const PairParam *pairs;
+    const PairParamF *pairs_f;
     const uint16_t *mat_scene, *mat_local;
     DevStatus *status;
 };
+
+// FP32 position of a sphere centre for screening tests (FP64 form: rounded absolute;
+// voxel form: grid origin + voxel * edge + offset in FP32).
+template <class F>
+__device__ __forceinline__ float3 approx_pos(const typename F::Pos &p, const Scene &sc, float L)
+{
+    if constexpr (F::voxel) {
+        return make_float3((float)sc.lo[0] + (float)p.cx * L + p.x, (float)sc.lo[1] + (float)p.cy * L + p.y,
+                           (float)sc.lo[2] + (float)p.cz * L + p.z);
+    } else {
+        return make_float3((float)p.x, (float)p.y, (float)p.z);
+    }
+}
 
 // ------------------------------------------------------------------ sphere kinematics
 
@@ -57,6 +73,7 @@ struct SphereK {
     V3<R> rl;            // centre minus owner centre of mass, world frame
     V3<R> v, w;          // owner linear velocity and world-frame angular velocity
     R rad, mass;
+    float rlo;           // low word of the radius (voxel form)
     int mat;
     uint32_t owner;
 };
@@ -76,6 +93,7 @@ __device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint3
     k.w = {w4.x, w4.y, w4.z};
     k.mass = mass;
     k.rad = d.sph_rad[s];
+    k.rlo = F::voxel ? d.sph_rlo[s] : 0.0f;
     k.mat = d.sph_mat[s];
     if (CLUMPS) {
         auto q = d.st.quat[sp][o];
@@ -89,30 +107,54 @@ __device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint3
     return k;
 }
 
-// Sphere-sphere contact geometry, A and B in canonical order.  False if delta <= 0.
+// Velocity of the contact point as a point of a body: v + w x arm, and the arm
+// rl + s * n, each product and sum rounded on its own so that the two threads of a pair
+// compute bit-identical values for the same side.
+template <typename R>
+__device__ __forceinline__ V3<R> arm_of(V3<R> rl, R s, V3<R> n)
+{
+    return {radd(rl.x, rmul(s, n.x)), radd(rl.y, rmul(s, n.y)), radd(rl.z, rmul(s, n.z))};
+}
+template <typename R>
+__device__ __forceinline__ V3<R> point_velocity(V3<R> v, V3<R> w, V3<R> r)
+{
+    return {radd(v.x, rsub(rmul(w.y, r.z), rmul(w.z, r.y))), radd(v.y, rsub(rmul(w.z, r.x), rmul(w.x, r.z))),
+            radd(v.z, rsub(rmul(w.x, r.y), rmul(w.y, r.x)))};
+}
+
+// Sphere-sphere contact seen from A (the calling thread's sphere) against B.  Every term
+// is an odd function of the orientation and IEEE round-to-nearest is symmetric under
+// negation, so B's thread, calling with the roles exchanged (and the history negated),
+// obtains exactly the negated force: no canonical reordering is needed.  False if the
+// overlap is not positive.
 template <class F>
 __device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
                                                ContactIn<typename F::R> &c, V3<typename F::R> &armA,
                                                V3<typename F::R> &armB)
 {
     using R = typename F::R;
-    V3<R> dd = F::diff(A.p, B.p, d.L);
-    R ss = radd(radd(rmul(dd.x, dd.x), rmul(dd.y, dd.y)), rmul(dd.z, dd.z));
-    R dist = sqrt(ss);
-    R delta = rsub(radd(A.rad, B.rad), dist);
+    V3<R> dd;
+    R dist, delta;
+    if constexpr (F::voxel) {
+        delta = overlap_ff(A.p, B.p, d.L, A.rad, A.rlo, B.rad, B.rlo, dd, dist);
+    } else {
+        dd = F::diff(A.p, B.p, d.L);
+        R ss = radd(radd(rmul(dd.x, dd.x), rmul(dd.y, dd.y)), rmul(dd.z, dd.z));
+        dist = sqrt(ss);
+        delta = rsub(radd(A.rad, B.rad), dist);
+    }
     if (!(delta > R(0)) || !(dist > R(0))) return false;
     R inv = R(1) / dist;
-    c.n = inv * dd;
+    c.n = {rmul(inv, dd.x), rmul(inv, dd.y), rmul(inv, dd.z)};
     c.delta = delta;
-    R a = A.rad - R(0.5) * delta;
-    R b = B.rad - R(0.5) * delta;
-    armA = A.rl - a * c.n;
-    armB = B.rl + b * c.n;
-    c.uA = A.v + cross(A.w, armA);
-    c.uB = B.v + cross(B.w, armB);
+    const R half = rmul(R(0.5), delta);
+    armA = arm_of(A.rl, -rsub(A.rad, half), c.n);
+    armB = arm_of(B.rl, rsub(B.rad, half), c.n);
+    c.uA = point_velocity(A.v, A.w, armA);
+    c.uB = point_velocity(B.v, B.w, armB);
     c.Rbar = (A.rad * B.rad) / (A.rad + B.rad);
     c.mbar = (A.mass * B.mass) / (A.mass + B.mass);
-    load_pair<R>(d.pairs, d.mat_scene, d.mat_local, d.scenes, A.mat, B.mat, c);
+    load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, B.mat, c);
     return true;
 }
 
@@ -123,25 +165,30 @@ __device__ __forceinline__ bool wall_contact(const Dev<F> &d, const SphereK<F> &
                                              V3<double> *point = nullptr)
 {
     using R = typename F::R;
+    if (w.type == WALL_PLANE) {
+        const float3 pf = approx_pos<F>(A.p, sc, d.L);
+        if (!plane_may_reach(w, pf, (float)A.rad, fabsf(pf.x) + fabsf(pf.y) + fabsf(pf.z) + 1.0f)) return false;
+    }
     V3<double> pa = F::absolute(A.p, sc, d.Ld);
     double gap;
     V3<double> n;
     if (!wall_gap(w, pa, gap, n)) return false;
-    double delta = rsub((double)A.rad, gap);
+    const double Rd = (double)A.rad + (double)A.rlo;
+    double delta = rsub(Rd, gap);
     if (!(delta > 0.0)) return false;
-    double a = (double)A.rad - 0.5 * delta;
+    double a = Rd - 0.5 * delta;
     V3<double> cp = {pa.x - a * n.x, pa.y - a * n.y, pa.z - a * n.z};
     V3<double> om = {w.omega[0], w.omega[1], w.omega[2]};
     V3<double> vw = cross(om, V3<double>{cp.x - w.p[0], cp.y - w.p[1], cp.z - w.p[2]});
     if (point) *point = cp;
     c.n = {(R)n.x, (R)n.y, (R)n.z};
     c.delta = (R)delta;
-    armA = A.rl - (R)a * c.n;
-    c.uA = A.v + cross(A.w, armA);
+    armA = arm_of(A.rl, -(R)a, c.n);
+    c.uA = point_velocity(A.v, A.w, armA);
     c.uB = {(R)vw.x, (R)vw.y, (R)vw.z};
     c.Rbar = A.rad;
     c.mbar = A.mass;
-    load_pair<R>(d.pairs, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
+    load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
     return true;
 }
 
@@ -181,7 +228,7 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
         SphereK<F> k = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
         const Scene &sc = d.scenes[d.owner_scene[o]];
         int cx, cy, cz;
-        F::cell(k.p, sc, d.invL, cx, cy, cz);
+        F::cell(k.p, sc, d.invL, d.vpc, cx, cy, cz);
         cx = min(max(cx, 0), sc.nc[0] - 1);
         cy = min(max(cy, 0), sc.nc[1] - 1);
         cz = min(max(cz, 0), sc.nc[2] - 1);
@@ -328,23 +375,35 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             }
         }
     }
-    // walls: signed gap below R + beta
+    // walls: signed gap below R + beta; FP32 screens first (FP64 throughput is scarce on
+    // this part), the exact FP64 test only for walls that survive them
     if (sc.wall_count > 0) {
-        V3<double> pa;
         double R;
+        float3 pf;
+        typename F::Pos pp;
         if constexpr (F::voxel) {
-            PosF32 p{ac.x, ac.y, ac.z, ao.x, ao.y, ao.z};
-            pa = FormF32::absolute(p, sc, d.Ld);
+            pp = PosF32{ac.x, ac.y, ac.z, ao.x, ao.y, ao.z};
             R = (double)ao.w;
         } else {
-            pa = {a64.x, a64.y, a64.z};
+            pp = PosF64{a64.x, a64.y, a64.z};
             R = a64.w;
         }
+        pf = approx_pos<F>(pp, sc, d.L);
+        const float reach = (float)R + (float)beta;
+        const float scale = fabsf(pf.x) + fabsf(pf.y) + fabsf(pf.z) + 1.0f;
+        bool have64 = false;
+        V3<double> pa;
         for (int wi = 0; wi < sc.wall_count; ++wi) {
             int wg = sc.wall_begin + wi;
+            const Wall &wl = d.walls[wg];
+            if (wl.type == WALL_PLANE && !plane_may_reach(wl, pf, reach, scale)) continue;
+            if (!have64) {
+                pa = F::absolute(pp, sc, d.Ld);
+                have64 = true;
+            }
             double gap;
             V3<double> nn;
-            wall_gap(d.walls[wg], pa, gap, nn);
+            wall_gap(wl, pa, gap, nn);
             if (gap < R + beta) row_insert(buf, n, WALL_BIT | (uint32_t)wg);
         }
     }
@@ -469,7 +528,8 @@ __global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double 
     const int lane = threadIdx.x & 31;
 
     bool live = s < d.N;
-    uint32_t o = live ? d.sph_owner[s] : 0xffffffffu;
+    // a world of single spheres has one slot per owner, in owner order
+    uint32_t o = live ? (CLUMPS ? d.sph_owner[s] : (uint32_t)s) : 0xffffffffu;
     live = live && o != 0xffffffffu;
     bool act = live && d.st.active[sp][o];
 
@@ -515,22 +575,17 @@ __global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double 
                 if (MODE == MODE_STEP && mine) { hxo[e] = R(0); hyo[e] = R(0); hzo[e] = R(0); }
                 continue;
             }
+            // the pair is evaluated in this thread's own orientation; the history is
+            // stored in the owner's orientation, so the other side negates it
             const int64_t slot = mine ? e : (int64_t)mrow[e] * d.Np + j;
             V3<R> ut = {hxi[slot], hyi[slot], hzi[slot]};
-            const SphereK<F> &A = mine ? me : other;
-            const SphereK<F> &B = mine ? other : me;
+            if (!mine) ut = -ut;
             V3<R> Fc;
-            bool on = sphere_contact<F>(d, A, B, c, armA, armB);
+            bool on = sphere_contact<F>(d, me, other, c, armA, armB);
             if (on) {
                 hertz_mindlin<R>(c, h, ut, Fc);
-                if (mine) {
-                    Fs = Fs + Fc;
-                    Ts = Ts + cross(armA, Fc);
-                } else {
-                    V3<R> mf = -Fc;
-                    Fs = Fs + mf;
-                    Ts = Ts + cross(armB, mf);
-                }
+                Fs = Fs + Fc;
+                Ts = Ts + cross(armA, Fc);
             }
             if (MODE == MODE_STEP && mine) {
                 hxo[e] = on ? ut.x : R(0);
@@ -642,20 +697,15 @@ __global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double 
         }
     }
     if (MODE == MODE_STEP) {
-        // block max of the displacement bound and the speed (non-negative floats order
-        // like their bit patterns), one atomic per block
-        unsigned int db = __float_as_uint(disp), vb = __float_as_uint(speed);
-        db = __reduce_max_sync(0xffffffffu, db);
-        vb = __reduce_max_sync(0xffffffffu, vb);
-        __shared__ unsigned int sd[8], sv[8];
-        const int warp = threadIdx.x >> 5;
-        if (lane == 0) { sd[warp] = db; sv[warp] = vb; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned int md = 0, mv = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { md = max(md, sd[w]); mv = max(mv, sv[w]); }
-            if (md) atomicMax(&stp->step_disp_bits, md);
-            if (mv) atomicMax(&stp->vmax_bits, mv);
+        // warp max of the displacement bound and the speed (non-negative floats order
+        // like their bit patterns), one atomic per warp into one of 64 slots: no block
+        // barrier, little contention; k_audit reduces the slots
+        unsigned int db = __reduce_max_sync(0xffffffffu, __float_as_uint(disp));
+        unsigned int vb = __reduce_max_sync(0xffffffffu, __float_as_uint(speed));
+        if (lane == 0) {
+            const int slot = (int)((s >> 5) & 63);
+            if (db) atomicMax(&stp->disp_slots[slot], db);
+            if (vb) atomicMax(&stp->vmax_slots[slot], vb);
         }
     }
 }
@@ -667,10 +717,15 @@ __global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double 
 static __global__ void k_audit(DevStatus *stp)
 {
     if (stp->halt || stp->list_stale) return;
-    float sd = __uint_as_float(stp->step_disp_bits);
-    float vm = __uint_as_float(stp->vmax_bits);
-    stp->step_disp_bits = 0;
-    stp->vmax_bits = 0;
+    unsigned int md = 0, mv = 0;
+    for (int k = 0; k < 64; ++k) {
+        md = max(md, stp->disp_slots[k]);
+        mv = max(mv, stp->vmax_slots[k]);
+        stp->disp_slots[k] = 0;
+        stp->vmax_slots[k] = 0;
+    }
+    float sd = __uint_as_float(md);
+    float vm = __uint_as_float(mv);
     if (stp->diverged || !(sd == sd)) {
         stp->halt = HALT_DIVERGED;
         return;
@@ -725,7 +780,7 @@ __global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *
             if (!d.st.active[sp][B.owner]) continue;
             if (!sphere_contact<F>(d, me, B, c, armA, armB)) continue;
             V3<double> pa = F::absolute(me.p, sc, d.Ld);
-            double a = (double)me.rad - 0.5 * (double)c.delta;
+            double a = ((double)me.rad + (double)me.rlo) - 0.5 * (double)c.delta;
             cp = {pa.x - a * (double)c.n.x, pa.y - a * (double)c.n.y, pa.z - a * (double)c.n.z};
         }
         hertz_mindlin<R>(c, h, ut, Fc);
@@ -866,7 +921,7 @@ __global__ void k_sphere_download(Dev<F> d, const int64_t *slots, int64_t n, dou
     const Scene &sc = d.scenes[d.owner_scene[me.owner]];
     V3<double> pa = F::absolute(me.p, sc, d.Ld);
     if (xyz) { xyz[3 * k] = pa.x; xyz[3 * k + 1] = pa.y; xyz[3 * k + 2] = pa.z; }
-    if (rad) rad[k] = (double)me.rad;
+    if (rad) rad[k] = (double)me.rad + (double)me.rlo;
     if constexpr (F::voxel) {
         if (cell) {
             cell[3 * k] = me.p.cx; cell[3 * k + 1] = me.p.cy; cell[3 * k + 2] = me.p.cz;

@@ -482,10 +482,10 @@ def packed_clumps(n=150, R=1e-3, fill=0.15, max_overlap=0.12, vel_sigma=0.3, ome
 
 
 def drum_bed(n=150, R=1e-3, drum_radius=0.03, length=0.03, omega=3.0, e=0.5, mu=0.5, E=1e7, nu=0.3, seed=0,
-             h=1e-6) -> Scene:
+             h=1e-6, vel_sigma=1.0) -> Scene:
     """Clumps (rods, tetrahedra) in the lower part of a drum about x spinning at omega,
     pushed radially outwards until the outermost sphere overlaps the drum by 0.02 R."""
-    s = packed_clumps(n=n, R=R, seed=seed, e=e, mu=mu, E=E, nu=nu, h=h, walls=False)
+    s = packed_clumps(n=n, R=R, seed=seed, e=e, mu=mu, E=E, nu=nu, h=h, walls=False, fill=0.1, vel_sigma=vel_sigma)
     c = s.x - np.mean(s.x, axis=0)
     c[:, 2] -= 0.45 * drum_radius
     # outermost radial extent of every clump's spheres about the x axis
