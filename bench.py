@@ -115,21 +115,26 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- algorithmic bytes
 
-def force_bytes(precision, n_spheres, listed_pairs, clumps=False):
-    """Algorithmic DRAM bytes of one force + integration launch: every owner's state read
-    and written once, its constants read once, and per listed pair both row entries,
-    one mirror byte and the tangential history read and written once."""
+def kernel_bytes(precision, n, n_with_entries, pairs, clumps=False):
+    """Algorithmic DRAM bytes per launch of the two per-step kernels, each distinct array
+    element counted once (state, constants, list rows, history, per-owner force/torque).
+
+    k_integrate (per owner): state read and written, constants, the owner's list-row
+    length, the per-owner accumulators, and the contact force/torque of owners with
+    listed partners.  k_contact: the row length and active flag of every sphere; for a
+    sphere with listed partners its state and constants and the force/torque it writes;
+    per listed pair both row entries, one mirror byte, history read and written."""
     if precision == "voxel_fp32":
-        per_sphere = 72 + 35 + 73
-        per_pair = 33
-        if clumps:
-            per_sphere += 18
+        integ = n * (1 + 1 + 24 + 16 + 16 + 16 + 4 + 16 + 2 + 1 + 8      # reads
+                     + 24 + 16 + 16 + 16 + 1 + 8) + 32 * n_with_entries   # writes, force/torque read
+        contact = 2 * n + n_with_entries * (24 + 16 + 16 + 4 + 4 + 2 + 2 + 32) + 33 * pairs
     else:
-        per_sphere = 128 + 59 + 129
-        per_pair = 57
-        if clumps:
-            per_sphere += 34
-    return per_sphere * n_spheres + per_pair * listed_pairs
+        integ = n * (1 + 1 + 32 + 32 + 32 + 32 + 8 + 32 + 2 + 1 + 8
+                     + 32 + 32 + 32 + 32 + 1 + 8) + 64 * n_with_entries
+        contact = 2 * n + n_with_entries * (32 + 32 + 32 + 8 + 2 + 2 + 64) + 57 * pairs
+    if clumps:
+        contact += n * (16 if precision == "voxel_fp32" else 32)
+    return {"integrate": integ, "contact": contact}
 
 
 def peaks():
@@ -147,6 +152,34 @@ def peaks():
 def make_scene(n):
     from paper_2311_04648_gb300 import workloads as W
     return W.settling_column(n=n)
+
+
+def profile_delta(p0, p1):
+    nf = p1["n_force"] - p0["n_force"]
+    ni = p1["n_integrate"] - p0["n_integrate"]
+    nd = p1["n_detect"] - p0["n_detect"]
+    return dict(contact_ms=(p1["ms_force"] - p0["ms_force"]) / max(nf, 1), n_contact=nf,
+                integrate_ms=(p1["ms_integrate"] - p0["ms_integrate"]) / max(ni, 1), n_integrate=ni,
+                detect_ms=(p1["ms_detect"] - p0["ms_detect"]) / max(nd, 1), n_detect=nd,
+                hash_ms=(p1["ms_hash"] - p0["ms_hash"]) / max(nd, 1),
+                link_ms=(p1["ms_link"] - p0["ms_link"]) / max(nd, 1),
+                listed_pairs=p1["listed_pairs"], active_contacts=p1["active_contacts"],
+                with_entries=p1["spheres_with_entries"], list_capacity=p1["list_capacity"])
+
+
+def roofline(precision, n, prof, peak, peak_kind):
+    kb = kernel_bytes(precision, n, prof["with_entries"], prof["listed_pairs"])
+    per = {}
+    for k in ("contact", "integrate"):
+        ms = prof[f"{k}_ms"]
+        per[k] = {"ms": ms, "bytes": kb[k], "gbs": kb[k] / (ms / 1000.0) / 1e9 if ms > 0 else None}
+    dom = max(per, key=lambda k: per[k]["ms"])
+    a = per[dom]["gbs"]
+    return {"bound": "hbm", "kernel": {"contact": "k_contact (pair forces + per-owner sums)",
+                                       "integrate": "k_integrate (owner update + audit)"}[dom],
+            "achieved": a, "peak": peak, "unit": "GB/s", "frac": (a / peak) if a else None, "traffic": None,
+            "peak_kind": peak_kind, "bytes_per_launch": per[dom]["bytes"], "avg_launch_ms": per[dom]["ms"],
+            "kernels": per, "listed_pairs": prof["listed_pairs"], "spheres_with_entries": prof["with_entries"]}
 
 
 def run_ours(args, device):
@@ -184,14 +217,7 @@ def run_ours(args, device):
     w.step(max(20, args.steps // 4))
     p1 = w.stats()
     w.set_profiling(False)
-    nf = p1["n_force"] - p0["n_force"]
-    nd = p1["n_detect"] - p0["n_detect"]
-    out["profile"] = dict(force_ms=(p1["ms_force"] - p0["ms_force"]) / max(nf, 1), n_force=nf,
-                          detect_ms=(p1["ms_detect"] - p0["ms_detect"]) / max(nd, 1), n_detect=nd,
-                          hash_ms=(p1["ms_hash"] - p0["ms_hash"]) / max(nd, 1),
-                          link_ms=(p1["ms_link"] - p0["ms_link"]) / max(nd, 1),
-                          listed_pairs=p1["listed_pairs"], active_contacts=p1["active_contacts"],
-                          list_capacity=p1["list_capacity"])
+    out["profile"] = profile_delta(p0, p1)
     # e2e through the C ABI with host buffers: state in from pinned memory, one step,
     # state out to pinned memory, every step
     n_own = scene.n_owner
@@ -231,11 +257,7 @@ def run_ours(args, device):
         q0 = wp.stats()
         wp.step(5)
         q1 = wp.stats()
-        nfp = q1["n_force"] - q0["n_force"]
-        out["plain"] = dict(ms=msp, steps=p1["steps"] - p0["steps"],
-                            force_ms=(q1["ms_force"] - q0["ms_force"]) / max(nfp, 1),
-                            detect_ms=(q1["ms_detect"] - q0["ms_detect"]) / max(q1["n_detect"] - q0["n_detect"], 1),
-                            listed_pairs=q1["listed_pairs"])
+        out["plain"] = dict(ms=msp, steps=p1["steps"] - p0["steps"], profile=profile_delta(q0, q1))
         wp.close()
     return out
 
@@ -310,8 +332,6 @@ def main():
         return 0
     prof = res["profile"]
     peak, peak_kind = peaks()
-    fb = force_bytes("voxel_fp32", n_sph, prof["listed_pairs"])
-    achieved = fb / (prof["force_ms"] / 1000.0) / 1e9 if prof["force_ms"] > 0 else None
     e2e = res["e2e"]
     e2e_val = n_sph * e2e["steps"] / e2e["seconds"] * world
     plain = res.get("plain")
@@ -326,27 +346,24 @@ def main():
                    "rebuilds_in_timed_region": res["chosen"]["rebuilds"],
                    "l2": "inputs larger than L2 (owner state + contact lists > 0.5 GB)",
                    "parallelism": f"replica x{world}"},
-        "roofline": {"bound": "hbm", "kernel": "k_force (contact forces + reduction + integration)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "peak_kind": peak_kind, "bytes_per_launch": fb, "avg_launch_ms": prof["force_ms"],
-                     "listed_pairs": prof["listed_pairs"]},
-        "kernels_ms": {"force": prof["force_ms"], "detect": prof["detect_ms"], "hash": prof["hash_ms"],
-                       "link": prof["link_ms"]},
+        "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind),
+        "kernels_ms": {"contact": prof["contact_ms"], "integrate": prof["integrate_ms"],
+                       "detect": prof["detect_ms"], "hash": prof["hash_ms"], "link": prof["link_ms"]},
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": e2e["bytes_in"],
                 "d2h_bytes_per_step": e2e["bytes_out"],
                 "how": "dem_set_owner_state from pinned host buffers + dem_step(1) + dem_get_owner_state "
                        "to pinned host buffers, every step"},
-        "gpu_launches": int(2 * steps + 18 * res["chosen"]["rebuilds"]),
+        "gpu_launches": int(3 * steps + 18 * res["chosen"]["rebuilds"]),
         "clocks": res["chosen"]["clocks"],
     }
     if plain:
         pv = n_sph * plain["steps"] / (plain["ms"] / 1000.0) * world
-        pfb = force_bytes("fp64", n_sph, plain["listed_pairs"])
+        pp = plain["profile"]
         line["plain"] = {"value": pv, "unit": METRIC, "ms_per_step": plain["ms"] / max(plain["steps"], 1),
-                         "dtype": "f64", "schedule": "every step", "force_ms": plain["force_ms"],
-                         "detect_ms": plain["detect_ms"],
-                         "force_gbs": pfb / (plain["force_ms"] / 1000.0) / 1e9 if plain["force_ms"] > 0 else None,
+                         "dtype": "f64", "schedule": "every step",
+                         "kernels_ms": {"contact": pp["contact_ms"], "integrate": pp["integrate_ms"],
+                                        "detect": pp["detect_ms"]},
+                         "roofline": roofline("fp64", n_sph, pp, peak, peak_kind),
                          "chosen_over_plain": value / pv}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)

@@ -102,10 +102,15 @@ typedef struct {
     double cell_size;              /* detection cell edge                                  */
     int64_t n_cells;               /* cells of all scenes                                  */
     double ms_detect, ms_force;    /* profiled GPU time: detection (sort, cells, narrow) /
-                                      force + integration kernel (dem_set_profiling)       */
+                                      contact-force kernel (dem_set_profiling)             */
     double ms_hash, ms_link;       /* profiled GPU time: snapshot + keys / list link       */
     int64_t n_detect, n_force;     /* profiled launches of each                            */
     double ms_total;               /* wall GPU time of all dem_step calls                  */
+    int64_t last_cycle;            /* steps per list chosen by the delayed schedules       */
+    int64_t schedule_samples;      /* (features, label) rows collected for the schedule    */
+    double ms_integrate;           /* profiled GPU time of the integration kernel          */
+    int64_t n_integrate;           /* profiled launches of it                              */
+    int64_t spheres_with_entries;  /* spheres whose row of the list in use is not empty    */
 } dem_stats;
 
 typedef struct {
@@ -277,14 +282,30 @@ dem_status dem_batch_destroy(dem_batch *b);
 
 /* ---------------------------------------------------------------- learned schedule */
 
-/* Record per-bin features and labels during dem_step (on = 1) or stop (on = 0). */
+/* Record per-bin features and labels during dem_step (on = 1) or stop (on = 0).  Bins
+ * are 8 x 8 x 8 detection cells; every 256 steps each occupied bin yields one sample:
+ * 16 motion features at the window start (speeds, accelerations, spins in units of the
+ * margin per step, list density, gravity) and, as labels, log2 of the steps until the
+ * largest per-owner displacement bound in the bin passed the margin and half of it,
+ * stored relative to the kinematic estimate (margin over the largest displacement per
+ * step in the bin) so that the network learns the correction to it. */
 dem_status dem_schedule_collect(dem_world *w, int32_t on);
-/* Train the schedule MLP on the recorded samples with the GPU kernels. */
+/* Train the schedule MLP (16 -> 64 -> 64 -> 2, BF16 tensor-core products, FP32 Adam)
+ * on the recorded samples with the GPU kernels; *final_loss (nullable) receives the mean
+ * loss of the last epoch. */
 dem_status dem_schedule_train(dem_world *w, int32_t epochs, float lr, uint64_t seed, float *final_loss);
 /* Export the current weights (format accepted by dem_load_schedule_model). */
 dem_status dem_schedule_export(dem_world *w, void *buf, size_t cap, size_t *used);
 
 /* ---------------------------------------------------------------- kernels as utilities */
+
+/* The schedule network's forward pass and loss gradient on the GPU for given parameters
+ * (flat FP32, 5378 values: W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]),
+ * host buffers X[rows][16], Y[rows][2], out[rows][2], grad[5378].  The loss is the mean
+ * over rows and outputs of w (y_hat - y)^2 with w = 4 where y_hat > y, else 1. */
+dem_status dem_util_mlp_forward(const float *params, int32_t rows, const float *X, float *out);
+dem_status dem_util_mlp_loss_grad(const float *params, int32_t rows, const float *X, const float *Y, float *loss,
+                                  float *grad);
 
 /* Stable LSD radix sort of (key, value) pairs of 32-bit unsigned integers on the GPU,
  * sorting on the low `bits` bits of the keys (1..32).  Host buffers; n >= 0. */

@@ -11,6 +11,7 @@
 
 #include "engine.h"
 #include "kernels.cuh"
+#include "mlp.h"
 
 using namespace dem;
 
@@ -237,6 +238,9 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
         g.mat_base = mat_base;
         g.n_mat = nm;
         g.pair_base = pair_base;
+        for (int a = 0; a < 3; ++a) g.nb[a] = (g.nc[a] + BIN_CELLS - 1) / BIN_CELLS;
+        g.bin_base = m.n_bins;
+        m.n_bins += g.nb[0] * g.nb[1] * g.nb[2];
         for (int a = 0; a < nm; ++a) {
             m.mat_scene.push_back((uint16_t)si);
             m.mat_local.push_back((uint16_t)a);
@@ -1001,6 +1005,49 @@ dem_status dem_schedule_export(dem_world *w, void *buf, size_t cap, size_t *used
     if (blob.size() > cap || !buf) return fail(w, DEM_ERR_CAPACITY, "weight buffer too small");
     std::memcpy(buf, blob.data(), blob.size());
     return DEM_OK;
+}
+
+static dem_status mlp_util(const float *params, int32_t rows, const float *X, const float *Y, float *out, float *loss,
+                           float *grad)
+{
+    if (!params || rows < 1 || !X) return fail(nullptr, DEM_ERR_ARG, "bad MLP arguments");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(nullptr, DEM_ERR_CUDA, "no CUDA device available");
+    Mlp net;
+    float *dx = nullptr, *dy = nullptr, *dout = nullptr;
+    cudaError_t e = net.set_params(params, 0);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dx, (size_t)rows * MLP_IN * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dx, X, (size_t)rows * MLP_IN * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && out) {
+        e = cudaMalloc((void **)&dout, (size_t)rows * MLP_OUT * sizeof(float));
+        if (e == cudaSuccess) e = net.forward(dx, rows, dout, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)rows * MLP_OUT * sizeof(float), cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess && Y) {
+        e = cudaMalloc((void **)&dy, (size_t)rows * MLP_OUT * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(dy, Y, (size_t)rows * MLP_OUT * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = net.loss_grad(dx, dy, rows, loss, grad, 0);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (dx) cudaFree(dx);
+    if (dy) cudaFree(dy);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, DEM_ERR_CUDA, cudaGetErrorString(e));
+    return DEM_OK;
+}
+
+dem_status dem_util_mlp_forward(const float *params, int32_t rows, const float *X, float *out)
+{
+    if (!out) return fail(nullptr, DEM_ERR_ARG, "null output");
+    return mlp_util(params, rows, X, nullptr, out, nullptr, nullptr);
+}
+
+dem_status dem_util_mlp_loss_grad(const float *params, int32_t rows, const float *X, const float *Y, float *loss,
+                                  float *grad)
+{
+    if (!Y || !grad) return fail(nullptr, DEM_ERR_ARG, "null labels or gradient");
+    return mlp_util(params, rows, X, Y, nullptr, loss, grad);
 }
 
 dem_status dem_util_radix_sort_u32(int64_t n, const uint32_t *keys, const uint32_t *vals, int32_t bits,

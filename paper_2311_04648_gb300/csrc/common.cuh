@@ -114,7 +114,12 @@ struct Scene {           // per-scene constants (device copy)
     int has_sink;
     double sink_p[3], sink_n[3];
     int mat_base, n_mat, pair_base;
+    int nb[3];           // schedule bins per axis (BIN_CELLS cells each)
+    int bin_base;        // first global bin of this scene
 };
+
+constexpr int BIN_CELLS = 8;     // cells per schedule-bin edge
+constexpr int NSTAT = 10;        // per-bin motion statistics
 
 struct PairParam {       // pairwise contact constants, precomputed on the host in FP64
     double Estar, Gstar, beta, mu;
@@ -134,12 +139,15 @@ struct DevStatus {
     int state_par;               // owner-state buffer holding the current state
     int hist_par;                // history buffer holding the current history
     int list_cur;                // contact list in use
+    int acc_par;                 // displacement accumulator of the list in use (the other: next)
+    int pad2;
     int diverged;                // set by the force kernel, turned into a halt by the audit
     unsigned int step_disp_bits; // max over owners of this step's displacement bound (float bits)
     unsigned int vmax_bits;      // max |v| over owners this step (float bits)
     int pad0, pad1;
     // per-warp maxima land in AUDIT_SLOTS spread slots (float bits), reduced by k_audit
     unsigned int disp_slots[64];
+    unsigned int disp2_slots[64];
     unsigned int vmax_slots[64];
     double disp_cur;             // displacement bound since the snapshot of the list in use
     double disp_next;            // ... since the snapshot of the list being built

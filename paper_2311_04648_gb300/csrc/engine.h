@@ -40,6 +40,7 @@ struct HostModel {
     std::vector<int64_t> slot_of_sphere, sphere_of_slot;
     bool clumps = false;
     uint32_t n_cells_total = 0;
+    int n_bins = 0;                 // schedule bins of all scenes
     // per scene: first owner id and first user sphere id in the flattened order
     std::vector<int64_t> scene_owner_base, scene_sphere_base, scene_wall_base;
     void *stream = nullptr, *detect_stream = nullptr;

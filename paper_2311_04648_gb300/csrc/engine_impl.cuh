@@ -12,10 +12,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
 #include "engine.h"
+#include "mlp.h"
 #include "pipeline.cuh"
 
 namespace dem {
@@ -41,16 +43,20 @@ public:
     {
         m_ = m;
         DEM_CU(cudaSetDevice(m_.device));
+        // the force stream gets the highest priority: the detection of the next list fills
+        // the SMs only where the step in progress leaves room
+        int prio_lo = 0, prio_hi = 0;
+        DEM_CU(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
         if (m_.stream) {
             sf_ = (cudaStream_t)m_.stream;
         } else {
-            DEM_CU(cudaStreamCreateWithFlags(&sf_, cudaStreamNonBlocking));
+            DEM_CU(cudaStreamCreateWithPriority(&sf_, cudaStreamNonBlocking, prio_hi));
             own_sf_ = true;
         }
         if (m_.detect_stream) {
             sd_ = (cudaStream_t)m_.detect_stream;
         } else {
-            DEM_CU(cudaStreamCreateWithFlags(&sd_, cudaStreamNonBlocking));
+            DEM_CU(cudaStreamCreateWithPriority(&sd_, cudaStreamNonBlocking, prio_lo));
             own_sd_ = true;
         }
         DEM_CU(cudaEventCreateWithFlags(&ev_snap_, cudaEventDisableTiming));
@@ -93,6 +99,13 @@ public:
         if ((s = alloc(d_.inv_mass, M, err))) return s;
         if ((s = alloc(d_.owner_scene, M, err))) return s;
         if ((s = alloc(d_.owner_iso, M, err))) return s;
+        if ((s = alloc(d_.acc[0], M, err))) return s;
+        if ((s = alloc(d_.acc[1], M, err))) return s;
+        if ((s = alloc(d_.fo, M, err))) return s;
+        if ((s = alloc(d_.to, M, err))) return s;
+        if ((s = alloc(d_.owner_first, M, err))) return s;
+        if ((s = alloc(d_.owner_nsph, M, err))) return s;
+        d_.amag = nullptr;
         if ((s = alloc(d_.sph_owner, N, err))) return s;
         if ((s = alloc(d_.sph_rad, N, err))) return s;
         if ((s = alloc(d_.sph_rlo, N, err))) return s;
@@ -167,6 +180,12 @@ public:
         if ((s = up(d_.inv_mass, inv_mass.data(), M, err))) return s;
         if ((s = up(d_.owner_scene, m_.owner_scene.data(), M, err))) return s;
         if ((s = up(d_.owner_iso, m_.owner_iso.data(), M, err))) return s;
+        if ((s = up(d_.owner_first, m_.owner_first_slot.data(), M, err))) return s;
+        {
+            std::vector<uint8_t> ns(M);
+            for (int64_t o = 0; o < M; ++o) ns[o] = (uint8_t)m_.owner_nsph[o];
+            if ((s = up(d_.owner_nsph, ns.data(), M, err))) return s;
+        }
         if ((s = up(d_.sph_owner, m_.sph_owner.data(), N, err))) return s;
         if ((s = up(d_.sph_rad, rad.data(), N, err))) return s;
         if ((s = up(d_.sph_rlo, rlo.data(), N, err))) return s;
@@ -254,6 +273,7 @@ public:
                 finish_detect();
             }
             if ((s = settle(err))) return s;
+            if ((s = collect_roll(err))) return s;
         }
         DEM_CU(cudaEventRecord(ev_b_, sf_));
         DEM_CU(cudaEventSynchronize(ev_b_));
@@ -486,21 +506,26 @@ public:
         o->ms_link = prof_ms_[P_LINK];
         o->n_force = prof_n_[P_FORCE];
         o->n_detect = prof_n_[P_DETECT];
+        o->ms_integrate = prof_ms_[P_INTEG];
+        o->n_integrate = prof_n_[P_INTEG];
         o->ms_total = ms_total_;
+        o->last_cycle = last_cycle_;
+        o->schedule_samples = (int64_t)(ds_y_.size() / MLP_OUT);
         if (d_.N > 0) {
             double *buf;
-            if ((s = scratch(buf, 3, err))) return s;
+            if ((s = scratch(buf, 4, err))) return s;
             unsigned long long *cnt = reinterpret_cast<unsigned long long *>(buf);
-            DEM_CU(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), sf_));
+            DEM_CU(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), sf_));
             if (m_.clumps) k_count<F, true><<<grid(d_.N, 256), 256, 0, sf_>>>(d_, cnt);
             else k_count<F, false><<<grid(d_.N, 256), 256, 0, sf_>>>(d_, cnt);
             DEM_CU(cudaGetLastError());
-            unsigned long long h[3];
+            unsigned long long h[4];
             DEM_CU(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, sf_));
             DEM_CU(cudaStreamSynchronize(sf_));
             o->listed_pairs = (int64_t)h[0];
             o->wall_pairs = (int64_t)h[1];
             o->active_contacts = (int64_t)h[2];
+            o->spheres_with_entries = (int64_t)h[3];
         }
         return DEM_OK;
     }
@@ -571,6 +596,8 @@ public:
         if ((s = dput(d_.lists.hx[hp], ne * sizeof(R)))) return s;
         if ((s = dput(d_.lists.hy[hp], ne * sizeof(R)))) return s;
         if ((s = dput(d_.lists.hz[hp], ne * sizeof(R)))) return s;
+        if ((s = dput(d_.acc[0], M * sizeof(float)))) return s;
+        if ((s = dput(d_.acc[1], M * sizeof(float)))) return s;
         double extra[2] = {beta_, (double)fallbacks_};
         put(extra, sizeof(extra));
         return DEM_OK;
@@ -627,6 +654,8 @@ public:
         if ((s = dget(d_.lists.hx[hp], ne * sizeof(R)))) return s;
         if ((s = dget(d_.lists.hy[hp], ne * sizeof(R)))) return s;
         if ((s = dget(d_.lists.hz[hp], ne * sizeof(R)))) return s;
+        if ((s = dget(d_.acc[0], M * sizeof(float)))) return s;
+        if ((s = dget(d_.acc[1], M * sizeof(float)))) return s;
         double extra[2];
         if (!get(extra, sizeof(extra))) { err = "truncated state blob"; return DEM_ERR_ARG; }
         beta_ = extra[0];
@@ -652,26 +681,64 @@ public:
 
     dem_status schedule_collect(int on, std::string &err) override
     {
-        (void)on;
-        err = "schedule collection is not built into this engine";
-        return DEM_ERR_UNSUPPORTED;
-    }
-    dem_status schedule_train(int, float, uint64_t, float *, std::string &err) override
-    {
-        err = "schedule training is not built into this engine";
-        return DEM_ERR_UNSUPPORTED;
-    }
-    dem_status schedule_export(std::vector<uint8_t> &, std::string &err) override
-    {
-        err = "schedule export is not built into this engine";
-        return DEM_ERR_UNSUPPORTED;
-    }
-    dem_status schedule_load(const uint8_t *w, size_t n, std::string &err) override
-    {
-        (void)err;
-        m_.schedule_model.assign(w, w + n);
+        dem_status s;
+        if ((s = sched_buffers(err))) return s;
+        if ((s = pull(err))) return s;
+        if (on && !collect_) {
+            collect_ = true;
+            if ((s = window_start(err))) return s;
+        } else if (!on && collect_) {
+            if ((s = window_finish(err))) return s;
+            collect_ = false;
+        }
         return DEM_OK;
     }
+
+    dem_status schedule_train(int epochs, float lr, uint64_t seed, float *loss, std::string &err) override
+    {
+        dem_status s;
+        if ((s = sched_buffers(err))) return s;
+        if (collect_) {
+            if ((s = pull(err))) return s;
+            if ((s = window_finish(err))) return s;
+            if ((s = window_start(err))) return s;
+        }
+        if (ds_y_.empty()) { err = "no schedule samples collected (dem_schedule_collect)"; return DEM_ERR_STATE; }
+        if (epochs < 1 || !(lr > 0.0f)) { err = "need epochs >= 1 and lr > 0"; return DEM_ERR_ARG; }
+        DEM_CU(mlp_->train(ds_x_, ds_y_, epochs, lr, seed, loss, sf_));
+        return DEM_OK;
+    }
+
+    dem_status schedule_export(std::vector<uint8_t> &w, std::string &err) override
+    {
+        if (!mlp_ || !mlp_->ready()) { err = "the schedule model has no weights yet"; return DEM_ERR_STATE; }
+        std::vector<float> p(MLP_NPARAM);
+        DEM_CU(mlp_->get_params(p.data(), sf_));
+        w.resize(12 + MLP_NPARAM * sizeof(float));
+        std::memcpy(w.data(), "DEMSCHD1", 8);
+        uint32_t np = MLP_NPARAM;
+        std::memcpy(w.data() + 8, &np, 4);
+        std::memcpy(w.data() + 12, p.data(), MLP_NPARAM * sizeof(float));
+        return DEM_OK;
+    }
+
+    dem_status schedule_load(const uint8_t *w, size_t n, std::string &err) override
+    {
+        uint32_t np = 0;
+        if (n < 12 || std::memcmp(w, "DEMSCHD1", 8) != 0 || (std::memcpy(&np, w + 8, 4), np != (uint32_t)MLP_NPARAM) ||
+            n != 12 + MLP_NPARAM * sizeof(float)) {
+            err = "not a schedule weight blob";
+            return DEM_ERR_ARG;
+        }
+        dem_status s;
+        if ((s = sched_buffers(err))) return s;
+        std::vector<float> p(MLP_NPARAM);
+        std::memcpy(p.data(), w + 12, MLP_NPARAM * sizeof(float));
+        DEM_CU(mlp_->set_params(p.data(), sf_));
+        return DEM_OK;
+    }
+
+    int64_t schedule_samples() const { return (int64_t)(ds_y_.size() / MLP_OUT); }
 
 private:
     static unsigned grid(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
@@ -824,6 +891,113 @@ private:
         return DEM_OK;
     }
 
+    // ---- learned schedule
+    dem_status sched_buffers(std::string &err)
+    {
+        if (!mlp_) mlp_.reset(new Mlp());
+        if (bin_stats_) return DEM_OK;
+        const int nb = std::max(1, m_.n_bins);
+        dem_status s;
+        if ((s = alloc(bin_stats_, (int64_t)nb * NSTAT, err))) return s;
+        if ((s = alloc(obin_, d_.M, err))) return s;
+        if ((s = alloc(X_, (int64_t)nb * 16, err))) return s;
+        if ((s = alloc(valid_, nb, err))) return s;
+        if ((s = alloc(pred_, (int64_t)nb * MLP_OUT, err))) return s;
+        if ((s = alloc(predmin_, 1, err))) return s;
+        if ((s = alloc(bin_scene_, nb, err))) return s;
+        if ((s = alloc(acc_lab_, d_.M, err))) return s;
+        if ((s = alloc(cross_, 2 * (int64_t)nb, err))) return s;
+        if ((s = alloc(d_.amag, d_.M, err))) return s;
+        std::vector<int> bs(nb, 0);
+        for (size_t sc = 0; sc < m_.scenes.size(); ++sc) {
+            const Scene &g = m_.scenes[sc];
+            for (int b = 0; b < g.nb[0] * g.nb[1] * g.nb[2]; ++b) bs[g.bin_base + b] = (int)sc;
+        }
+        if ((s = up(bin_scene_, bs.data(), nb, err))) return s;
+        if (!m_.schedule_model.empty() && !mlp_->ready()) {
+            if ((s = schedule_load(m_.schedule_model.data(), m_.schedule_model.size(), err))) return s;
+        }
+        return DEM_OK;
+    }
+
+    // Per-bin features of the current state into X_ / valid_ (force stream).
+    dem_status features(std::string &err)
+    {
+        const int nb = std::max(1, m_.n_bins);
+        DEM_CU(cudaMemsetAsync(bin_stats_, 0, (size_t)nb * NSTAT * sizeof(float), sf_));
+        if (d_.M > 0) k_bin_stats<F><<<grid(d_.M, 256), 256, 0, sf_>>>(d_, bin_stats_, obin_);
+        k_bin_features<<<grid(nb, 256), 256, 0, sf_>>>(bin_stats_, nb, bin_scene_, d_.scenes, (float)beta_,
+                                                        (float)m_.r_max, X_, valid_);
+        DEM_CU(cudaGetLastError());
+        return DEM_OK;
+    }
+
+    dem_status window_start(std::string &err)
+    {
+        dem_status s;
+        if ((s = features(err))) return s;
+        const int nb = std::max(1, m_.n_bins);
+        win_x_.resize((size_t)nb * 16);
+        win_valid_.resize(nb);
+        DEM_CU(cudaMemcpyAsync(win_x_.data(), X_, win_x_.size() * sizeof(float), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaMemcpyAsync(win_valid_.data(), valid_, nb * sizeof(int), cudaMemcpyDeviceToHost, sf_));
+        std::vector<int> init(2 * (size_t)nb, win_len_);
+        DEM_CU(cudaMemcpyAsync(cross_, init.data(), init.size() * sizeof(int), cudaMemcpyHostToDevice, sf_));
+        DEM_CU(cudaMemsetAsync(acc_lab_, 0, (size_t)std::max<int64_t>(d_.M, 1) * sizeof(float), sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        win_start_ = sth_->steps_done;
+        return DEM_OK;
+    }
+
+    // Close the window: label every occupied bin with log2 of the steps its largest
+    // displacement bound took to pass beta and beta/2 (censored at the window length).
+    dem_status window_finish(std::string &err)
+    {
+        const long long len = sth_->steps_done - win_start_;
+        if (win_start_ < 0 || len < 8) return DEM_OK;      // too short to label anything
+        const int nb = std::max(1, m_.n_bins);
+        std::vector<int> cr(2 * (size_t)nb);
+        DEM_CU(cudaMemcpyAsync(cr.data(), cross_, cr.size() * sizeof(int), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        const int cap = (int)std::min<long long>(len, win_len_);
+        for (int b = 0; b < nb; ++b) {
+            if (!win_valid_[b]) continue;
+            for (int k = 0; k < 16; ++k) ds_x_.push_back(win_x_[(size_t)b * 16 + k]);
+            // target: residual over the kinematic estimate log2(1 / feature 13)
+            const float lin = std::log2(std::max(win_x_[(size_t)b * 16 + 13], 1e-6f));
+            for (int j = 0; j < 2; ++j)
+                ds_y_.push_back(std::log2((float)std::max(1, std::min(cr[2 * b + j], cap))) + lin);
+        }
+        return DEM_OK;
+    }
+
+    // After a synchronisation: roll the collection window when it is long enough.
+    dem_status collect_roll(std::string &err)
+    {
+        if (!collect_ || sth_->steps_done - win_start_ < win_len_) return DEM_OK;
+        dem_status s;
+        if ((s = window_finish(err))) return s;
+        return window_start(err);
+    }
+
+    // Learned cycle length: the smallest predicted log2(steps until a bin passes beta) over
+    // the occupied bins; a list is used from c to 2c steps after its snapshot, so c is
+    // half of it, with a 20% allowance.
+    long long learned_cycle(std::string &err)
+    {
+        if (sched_buffers(err) || !mlp_->ready()) return 0;
+        const int nb = std::max(1, m_.n_bins);
+        if (features(err)) return 0;
+        if (mlp_->forward(X_, nb, pred_, sf_) != cudaSuccess) return 0;
+        k_min_pred<<<1, 256, 0, sf_>>>(pred_, X_, valid_, nb, predmin_);
+        float p = 0.0f;
+        if (cudaMemcpyAsync(&p, predmin_, sizeof(float), cudaMemcpyDeviceToHost, sf_) != cudaSuccess) return 0;
+        if (cudaStreamSynchronize(sf_) != cudaSuccess) return 0;
+        if (!(p == p) || p > 30.0f) p = 30.0f;
+        double n = std::exp2((double)p);
+        return std::max<long long>(1, (long long)std::floor(0.4 * n));
+    }
+
     // Read-backs that depend on the current contacts need a list that covers them: after
     // a step the list in use may be stale (every-step lists are built before the step).
     dem_status fresh(std::string &err)
@@ -937,21 +1111,29 @@ private:
         mark_end(sf_, m);
     }
 
+    // k_contact needs ~140 registers: small blocks let an SM hold several, so a block
+    // whose spheres have no partners frees its slot at once
     template <int MODE>
     void launch_force(double *eF, double *eT)
     {
-        const unsigned g = grid(d_.N, 256);
-        if (m_.clumps) k_force<F, true, MODE><<<g, 256, 0, sf_>>>(d_, eF, eT);
-        else k_force<F, false, MODE><<<g, 256, 0, sf_>>>(d_, eF, eT);
+        const unsigned g = grid(d_.N, CONTACT_BLOCK);
+        if (m_.clumps) k_contact<F, true, MODE><<<g, CONTACT_BLOCK, 0, sf_>>>(d_, eF, eT);
+        else k_contact<F, false, MODE><<<g, CONTACT_BLOCK, 0, sf_>>>(d_, eF, eT);
     }
 
     void force_step()
     {
-        Mark m;
+        Mark m, m2;
         mark_begin(P_FORCE, sf_, m);
         launch_force<MODE_STEP>(nullptr, nullptr);
         mark_end(sf_, m);
+        mark_begin(P_INTEG, sf_, m2);
+        if (m_.clumps) k_integrate<F, true><<<grid(d_.M, 256), 256, 0, sf_>>>(d_);
+        else k_integrate<F, false><<<grid(d_.M, 256), 256, 0, sf_>>>(d_);
+        mark_end(sf_, m2);
         k_audit<<<1, 1, 0, sf_>>>(st_);
+        if (collect_ && d_.M > 0)
+            k_collect_step<F><<<grid(d_.M, 256), 256, 0, sf_>>>(d_, acc_lab_, obin_, cross_, win_start_, (float)beta_);
     }
 
     // Steps per list for the delayed schedules.  A list built from a snapshot at step s is
@@ -962,10 +1144,15 @@ private:
         const double h = m_.scenes.empty() ? 1e-6 : m_.scenes[0].h;
         double v = std::max(sth_->vmax_last, 1e-3) * 1.5;
         long long c = (long long)std::floor(beta_ / (2.0 * h * v));
-        if (m_.schedule == DEM_SCHEDULE_LEARNED && !m_.schedule_model.empty() && learned_cycle_ > 0)
-            c = learned_cycle_;
-        return std::max<long long>(1, std::min<long long>(c, 2000));
+        if (m_.schedule == DEM_SCHEDULE_LEARNED) {
+            std::string err;
+            long long lc = learned_cycle(err);
+            if (lc > 0) c = lc;
+        }
+        last_cycle_ = std::max<long long>(1, std::min<long long>(c, 2000));
+        return last_cycle_;
     }
+    long long last_cycle_ = 0;
 
     void release()
     {
@@ -1005,15 +1192,24 @@ private:
     double beta_ = 0.0;
     bool dirty_ = false;
     int64_t fallbacks_ = 0, regrows_ = 0;
-    long long learned_cycle_ = 0;
     double ms_total_ = 0.0;
+    // learned schedule
+    std::unique_ptr<Mlp> mlp_;
+    float *bin_stats_ = nullptr, *X_ = nullptr, *pred_ = nullptr, *predmin_ = nullptr, *acc_lab_ = nullptr;
+    int *obin_ = nullptr, *valid_ = nullptr, *bin_scene_ = nullptr, *cross_ = nullptr;
+    bool collect_ = false;
+    long long win_start_ = -1;
+    int win_len_ = 256;
+    std::vector<float> win_x_;
+    std::vector<int> win_valid_;
+    std::vector<float> ds_x_, ds_y_;
     // profiling: event pairs recorded on the stream of the bracketed work
-    enum { P_FORCE = 0, P_DETECT = 1, P_HASH = 2, P_LINK = 3 };
+    enum { P_FORCE = 0, P_DETECT = 1, P_HASH = 2, P_LINK = 3, P_INTEG = 4 };
     bool prof_ = false;
     struct Mark { cudaEvent_t a, b; int kind; };
     std::vector<Mark> marks_, pool_;
-    double prof_ms_[4] = {0, 0, 0, 0};
-    int64_t prof_n_[4] = {0, 0, 0, 0};
+    double prof_ms_[5] = {0, 0, 0, 0, 0};
+    int64_t prof_n_[5] = {0, 0, 0, 0, 0};
 
     Mark take()
     {

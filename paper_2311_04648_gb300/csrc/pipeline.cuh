@@ -43,6 +43,12 @@ struct Dev {
     R4 *sph_rloc;                   // body-frame offset (x, y, z, 0); clumps only
     uint8_t *sph_head;              // first slot of its owner
     uint8_t *sph_segend;            // lane (within the warp) one past the owner's last slot
+    int64_t *owner_first;           // first sphere slot of each owner
+    uint8_t *owner_nsph;            // spheres of each owner
+    float *acc[2];                  // per owner: accumulated displacement bound since the
+                                    // snapshot of the list in use / the list being built
+    float *amag;                    // per owner |F|/m of the last step (schedule features)
+    R4 *fo, *to;                    // per owner contact force and torque of the step
     const Scene *scenes;
     const Wall *walls;
     const PairParam *pairs;
@@ -223,6 +229,7 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
     if (s >= d.N) return;
     const int sp = stp->state_par;
     uint32_t o = d.sph_owner[s];
+    if (o != 0xffffffffu && d.sph_head[s]) d.acc[stp->acc_par ^ 1][o] = 0.0f;
     uint32_t key = b.n_cells_total;
     if (o != 0xffffffffu && d.st.active[sp][o]) {
         SphereK<F> k = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
@@ -477,6 +484,7 @@ static __global__ void k_commit(DevStatus *stp)
     if (stp->halt) return;
     stp->list_cur ^= 1;
     stp->hist_par ^= 1;
+    stp->acc_par ^= 1;
     stp->disp_cur = stp->disp_next;
     stp->beta_cur = stp->beta_next;
     stp->list_stale = stp->disp_cur > stp->beta_cur ? 1 : 0;
@@ -511,13 +519,15 @@ __device__ __forceinline__ void quat_mul(R aw, R ax, R ay, R az, R bw, R bx, R b
     z = ((aw * bz + ax * by) - ay * bx) + az * bw;
 }
 
-// Contact forces of every listed pair of slot s, the per-owner sum (segmented warp
-// reduction over the owner's consecutive slots), then (MODE_STEP) the semi-implicit
-// Euler update of the owner: v, then body-frame angular velocity (Euler's equations),
-// then x, then the quaternion.  MODE_EVAL writes the per-owner force (gravity included)
-// and torque instead and changes nothing.
+// Contact forces of every listed pair of slot s and the per-owner sums (segmented warp
+// reduction over the owner's consecutive slots).  MODE_STEP writes the owner's contact
+// force and torque (fo, to) for k_integrate and the updated tangential history; a single
+// sphere without listed partners leaves at once.  MODE_EVAL writes the per-owner force
+// (gravity included) and torque in FP64 and changes nothing.
+constexpr int CONTACT_BLOCK = 64;
+
 template <class F, bool CLUMPS, int MODE>
-__global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double *eval_T)
+__global__ void __launch_bounds__(CONTACT_BLOCK) k_contact(Dev<F> d, double *eval_F, double *eval_T)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
@@ -531,7 +541,9 @@ __global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double 
     // a world of single spheres has one slot per owner, in owner order
     uint32_t o = live ? (CLUMPS ? d.sph_owner[s] : (uint32_t)s) : 0xffffffffu;
     live = live && o != 0xffffffffu;
+    const int n = live ? d.lists.cnt[lc][s] : 0;
     bool act = live && d.st.active[sp][o];
+    if (!CLUMPS && MODE == MODE_STEP && (!act || n == 0)) return;
 
     V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
     SphereK<F> me;
@@ -543,7 +555,6 @@ __global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double 
     if (act) {
         const Scene &sc = d.scenes[scene];
         const R h = F::voxel ? (R)sc.hf : (R)sc.h;
-        const int n = d.lists.cnt[lc][s];
         const uint32_t *prow = d.lists.partner[lc];
         const uint8_t *mrow = d.lists.mirror[lc];
         const R *hxi = d.lists.hx[hp], *hyi = d.lists.hy[hp], *hzi = d.lists.hz[hp];
@@ -611,136 +622,313 @@ __global__ void __launch_bounds__(256) k_force(Dev<F> d, double *eval_F, double 
         Ts = {v6[3], v6[4], v6[5]};
     }
     const bool head = live && (!CLUMPS || d.sph_head[s]);
-    float disp = 0.0f, speed = 0.0f;
-    if (head) {
+    if (!head) return;
+    if (MODE == MODE_EVAL) {
         const Scene &sc = d.scenes[scene];
-        const R h = F::voxel ? (R)sc.hf : (R)sc.h;
         const V3<R> g = F::voxel ? V3<R>{(R)sc.gf[0], (R)sc.gf[1], (R)sc.gf[2]}
                                  : V3<R>{(R)sc.g[0], (R)sc.g[1], (R)sc.g[2]};
-        R mass = me.mass;
-        typename F::Pos po;
-        {
-            R m2;
-            po = F::load(d.st.pos[sp], o, m2);
-        }
-        if (MODE == MODE_EVAL) {
-            V3<R> Ft = act ? Fs + mass * g : V3<R>{R(0), R(0), R(0)};
-            eval_F[3 * o + 0] = (double)Ft.x; eval_F[3 * o + 1] = (double)Ft.y; eval_F[3 * o + 2] = (double)Ft.z;
-            eval_T[3 * o + 0] = (double)Ts.x; eval_T[3 * o + 1] = (double)Ts.y; eval_T[3 * o + 2] = (double)Ts.z;
-        } else {
-            const int so = sp ^ 1;
-            R4 q4 = d.st.quat[sp][o];
-            V3<R> vn = me.v, wn = me.w;
-            R qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
-            uint8_t active_out = act ? 1 : 0;
-            typename F::Pos pn = po;
-            if (act) {
-                const R im = d.inv_mass[o];
-                const R4 ii = d.inv_moi[o];
-                V3<R> Ft = Fs + mass * g;
-                vn = me.v + h * (im * Ft);
-                R nw, nx, ny, nz;
-                if (d.owner_iso[o]) {
-                    // isotropic inertia: the body-frame update equals a world-frame one
-                    wn = me.w + h * (ii.x * Ts);
-                    R dw, dx, dy, dz;
-                    quat_increment<R>(wn, h, dw, dx, dy, dz);
-                    quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
-                } else {
-                    R m[9];
-                    quat_mat<R>(qw, qx, qy, qz, m);
-                    V3<R> wb = mat_tvec<R>(m, me.w);
-                    V3<R> Tb = mat_tvec<R>(m, Ts);
-                    V3<R> gyro = {R(0), R(0), R(0)};
-                    if (d.gyro) {
-                        V3<R> Iw = {wb.x / ii.x, wb.y / ii.y, wb.z / ii.z};
-                        gyro = cross(wb, Iw);
-                    }
-                    V3<R> dwb = {ii.x * (Tb.x - gyro.x), ii.y * (Tb.y - gyro.y), ii.z * (Tb.z - gyro.z)};
-                    wb = wb + h * dwb;
-                    R dw, dx, dy, dz;
-                    quat_increment<R>(wb, h, dw, dx, dy, dz);
-                    quat_mul<R>(qw, qx, qy, qz, dw, dx, dy, dz, nw, nx, ny, nz);
-                    R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
-                    R m2[9];
-                    quat_mat<R>(nw / qn, nx / qn, ny / qn, nz / qn, m2);
-                    wn = mat_vec<R>(m2, wb);
-                }
-                R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
-                qw = nw / qn; qx = nx / qn; qy = ny / qn; qz = nz / qn;
-                pn = F::advance(po, h * vn, d.L);
-                if (sc.has_sink) {
-                    V3<double> pa = F::absolute(pn, sc, d.Ld);
-                    double side = (pa.x - sc.sink_p[0]) * sc.sink_n[0] + (pa.y - sc.sink_p[1]) * sc.sink_n[1] +
-                                  (pa.z - sc.sink_p[2]) * sc.sink_n[2];
-                    if (side < 0.0) {
-                        active_out = 0;
-                        vn = {R(0), R(0), R(0)};
-                        wn = {R(0), R(0), R(0)};
-                    }
-                }
-                R sv = sqrt(dot(vn, vn));
-                R sw = sqrt(dot(wn, wn));
-                speed = (float)sv;
-                disp = (float)(h * (sv + sw * ii.w));
-                if (sc.v_err > 0.0 && !((double)sv <= sc.v_err)) atomicOr(&stp->diverged, 1);
-                if (!(sv == sv) || !(sw == sw)) atomicOr(&stp->diverged, 1);
-            } else {
-                vn = {R(0), R(0), R(0)};
-                wn = {R(0), R(0), R(0)};
-            }
-            F::store(d.st.pos[so], o, pn, mass);
-            d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, R(0)};
-            d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, R(0)};
-            d.st.quat[so][o] = R4{qw, qx, qy, qz};
-            d.st.active[so][o] = active_out;
-        }
-    }
-    if (MODE == MODE_STEP) {
-        // warp max of the displacement bound and the speed (non-negative floats order
-        // like their bit patterns), one atomic per warp into one of 64 slots: no block
-        // barrier, little contention; k_audit reduces the slots
-        unsigned int db = __reduce_max_sync(0xffffffffu, __float_as_uint(disp));
-        unsigned int vb = __reduce_max_sync(0xffffffffu, __float_as_uint(speed));
-        if (lane == 0) {
-            const int slot = (int)((s >> 5) & 63);
-            if (db) atomicMax(&stp->disp_slots[slot], db);
-            if (vb) atomicMax(&stp->vmax_slots[slot], vb);
-        }
+        V3<R> Ft = act ? Fs + me.mass * g : V3<R>{R(0), R(0), R(0)};
+        eval_F[3 * o + 0] = (double)Ft.x; eval_F[3 * o + 1] = (double)Ft.y; eval_F[3 * o + 2] = (double)Ft.z;
+        eval_T[3 * o + 0] = (double)Ts.x; eval_T[3 * o + 1] = (double)Ts.y; eval_T[3 * o + 2] = (double)Ts.z;
+    } else {
+        d.fo[o] = R4{Fs.x, Fs.y, Fs.z, R(0)};
+        d.to[o] = R4{Ts.x, Ts.y, Ts.z, R(0)};
     }
 }
 
-// Completes a step (single thread): flips the state and history buffers, accumulates the
-// displacement bound of the list in use and of the list being built, and flags the list
-// stale when its bound exceeds the margin (Sec. 2.1: the margin must cover the motion
-// between list updates); turns a divergence into a halt, leaving the last good state.
+// Semi-implicit Euler update of each owner (one thread per owner, streaming): v with the
+// contact force plus gravity, then the body-frame angular velocity (Euler's equations,
+// gyroscopic term switchable), then x with the new v, then the quaternion with the new
+// angular velocity; removal by the sink; the per-owner displacement bounds of the audit.
+template <class F, bool CLUMPS>
+__global__ void __launch_bounds__(256) k_integrate(Dev<F> d)
+{
+    using R = typename F::R;
+    using R4 = typename F::R4;
+    DevStatus *stp = d.status;
+    if (stp->halt || stp->list_stale) return;
+    const int sp = stp->state_par, lc = stp->list_cur;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
+    if (o < d.M) {
+        const bool act = d.st.active[sp][o];
+        const bool has = CLUMPS ? true : d.lists.cnt[lc][o] > 0;
+        R mass;
+        const typename F::Pos po = F::load(d.st.pos[sp], o, mass);
+        const R4 v4 = d.st.vel[sp][o], w4 = d.st.omg[sp][o], q4 = d.st.quat[sp][o];
+        const Scene &sc = d.scenes[d.owner_scene[o]];
+        const int so = sp ^ 1;
+        V3<R> vn = {v4.x, v4.y, v4.z}, wn = {w4.x, w4.y, w4.z};
+        R qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+        uint8_t active_out = act ? 1 : 0;
+        typename F::Pos pn = po;
+        if (act) {
+            const R h = F::voxel ? (R)sc.hf : (R)sc.h;
+            const V3<R> g = F::voxel ? V3<R>{(R)sc.gf[0], (R)sc.gf[1], (R)sc.gf[2]}
+                                     : V3<R>{(R)sc.g[0], (R)sc.g[1], (R)sc.g[2]};
+            V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
+            if (has) {
+                const R4 f4 = d.fo[o], t4 = d.to[o];
+                Fs = {f4.x, f4.y, f4.z};
+                Ts = {t4.x, t4.y, t4.z};
+            }
+            const R im = d.inv_mass[o];
+            const R4 ii = d.inv_moi[o];
+            const V3<R> Ft = Fs + mass * g;
+            vn = vn + h * (im * Ft);
+            R nw, nx, ny, nz;
+            if (d.owner_iso[o]) {
+                // isotropic inertia: the body-frame update equals a world-frame one
+                wn = wn + h * (ii.x * Ts);
+                R dw, dx, dy, dz;
+                quat_increment<R>(wn, h, dw, dx, dy, dz);
+                quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+            } else {
+                R m[9];
+                quat_mat<R>(qw, qx, qy, qz, m);
+                V3<R> wb = mat_tvec<R>(m, wn);
+                V3<R> Tb = mat_tvec<R>(m, Ts);
+                V3<R> gyro = {R(0), R(0), R(0)};
+                if (d.gyro) {
+                    V3<R> Iw = {wb.x / ii.x, wb.y / ii.y, wb.z / ii.z};
+                    gyro = cross(wb, Iw);
+                }
+                V3<R> dwb = {ii.x * (Tb.x - gyro.x), ii.y * (Tb.y - gyro.y), ii.z * (Tb.z - gyro.z)};
+                wb = wb + h * dwb;
+                R dw, dx, dy, dz;
+                quat_increment<R>(wb, h, dw, dx, dy, dz);
+                quat_mul<R>(qw, qx, qy, qz, dw, dx, dy, dz, nw, nx, ny, nz);
+                R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
+                R m2[9];
+                quat_mat<R>(nw / qn, nx / qn, ny / qn, nz / qn, m2);
+                wn = mat_vec<R>(m2, wb);
+            }
+            R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
+            qw = nw / qn; qx = nx / qn; qy = ny / qn; qz = nz / qn;
+            pn = F::advance(po, h * vn, d.L);
+            if (sc.has_sink) {
+                V3<double> pa = F::absolute(pn, sc, d.Ld);
+                double side = (pa.x - sc.sink_p[0]) * sc.sink_n[0] + (pa.y - sc.sink_p[1]) * sc.sink_n[1] +
+                              (pa.z - sc.sink_p[2]) * sc.sink_n[2];
+                if (side < 0.0) {
+                    active_out = 0;
+                    vn = {R(0), R(0), R(0)};
+                    wn = {R(0), R(0), R(0)};
+                }
+            }
+            R sv = sqrt(dot(vn, vn));
+            R sw = sqrt(dot(wn, wn));
+            speed = (float)sv;
+            // displacement bound of this step (centre moves h|v|, a component centre at
+            // most h|w| r_ext more) plus the rounding slack of the position update,
+            // accumulated per owner since each list's snapshot
+            const float step_d = (float)(h * (sv + sw * ii.w)) * 1.0000005f + (float)stp->disp_slack;
+            const int ap = stp->acc_par;
+            const float a0 = d.acc[ap][o] + step_d;
+            const float a1 = d.acc[ap ^ 1][o] + step_d;
+            d.acc[ap][o] = a0;
+            d.acc[ap ^ 1][o] = a1;
+            disp = a0;
+            disp2 = a1;
+            if (d.amag) d.amag[o] = (float)(sqrt(dot(Ft, Ft)) * im);
+            if (sc.v_err > 0.0 && !((double)sv <= sc.v_err)) atomicOr(&stp->diverged, 1);
+            if (!(sv == sv) || !(sw == sw)) atomicOr(&stp->diverged, 1);
+        } else {
+            vn = {R(0), R(0), R(0)};
+            wn = {R(0), R(0), R(0)};
+        }
+        F::store(d.st.pos[so], o, pn, mass);
+        d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, R(0)};
+        d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, R(0)};
+        d.st.quat[so][o] = R4{qw, qx, qy, qz};
+        d.st.active[so][o] = active_out;
+    }
+    // warp max of the displacement bounds and the speed (non-negative floats order like
+    // their bit patterns), one atomic per warp into one of 64 slots: no block barrier,
+    // little contention; k_audit reduces the slots
+    unsigned int db = __reduce_max_sync(0xffffffffu, __float_as_uint(disp));
+    unsigned int db2 = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
+    unsigned int vb = __reduce_max_sync(0xffffffffu, __float_as_uint(speed));
+    if (lane == 0) {
+        const int slot = (int)((o >> 5) & 63);
+        if (db) atomicMax(&stp->disp_slots[slot], db);
+        if (db2) atomicMax(&stp->disp2_slots[slot], db2);
+        if (vb) atomicMax(&stp->vmax_slots[slot], vb);
+    }
+}
+
+// Completes a step (single thread): flips the state and history buffers, takes the largest
+// per-owner displacement bound of the list in use and of the list being built, and flags
+// the list stale when its bound exceeds the margin (Sec. 2.1: the margin must cover the
+// motion between list updates); turns a divergence into a halt, leaving the last good
+// state.  A pair touching now was, at the snapshot, at most R_i + R_j + acc_i + acc_j
+// apart, so every touching pair is listed while the largest acc stays below the margin.
 static __global__ void k_audit(DevStatus *stp)
 {
     if (stp->halt || stp->list_stale) return;
-    unsigned int md = 0, mv = 0;
+    unsigned int md = 0, md2 = 0, mv = 0;
     for (int k = 0; k < 64; ++k) {
         md = max(md, stp->disp_slots[k]);
+        md2 = max(md2, stp->disp2_slots[k]);
         mv = max(mv, stp->vmax_slots[k]);
         stp->disp_slots[k] = 0;
+        stp->disp2_slots[k] = 0;
         stp->vmax_slots[k] = 0;
     }
     float sd = __uint_as_float(md);
+    float sd2 = __uint_as_float(md2);
     float vm = __uint_as_float(mv);
-    if (stp->diverged || !(sd == sd)) {
+    if (stp->diverged || !(sd == sd) || !(vm == vm)) {
         stp->halt = HALT_DIVERGED;
         return;
     }
     stp->steps_done += 1;
     stp->state_par ^= 1;
     stp->hist_par ^= 1;
-    double inc = (double)sd + stp->disp_slack;
-    stp->disp_cur += inc;
-    stp->disp_next += inc;
+    // largest per-owner accumulated bound of each list (owners accumulate on their own)
+    stp->disp_cur = (double)sd;
+    stp->disp_next = (double)sd2;
     stp->vmax_last = (double)vm;
     if (stp->disp_cur > stp->beta_cur) {
         stp->list_stale = 1;
         stp->stale_events += 1;
     }
+}
+
+// ------------------------------------------------------------------ learned schedule
+
+// Bin of an owner: its centre of mass's cell divided by BIN_CELLS per axis.
+template <class F>
+__device__ __forceinline__ int owner_bin(const Dev<F> &d, int sp, int64_t o, const Scene &sc)
+{
+    typename F::R mass;
+    typename F::Pos p = F::load(d.st.pos[sp], o, mass);
+    int cx, cy, cz;
+    F::cell(p, sc, d.invL, d.vpc, cx, cy, cz);
+    cx = min(max(cx, 0), sc.nc[0] - 1) / BIN_CELLS;
+    cy = min(max(cy, 0), sc.nc[1] - 1) / BIN_CELLS;
+    cz = min(max(cz, 0), sc.nc[2] - 1) / BIN_CELLS;
+    return sc.bin_base + (cz * sc.nb[1] + cy) * sc.nb[0] + cx;
+}
+
+// Per-bin motion statistics of the active owners: count, sum |v|, sum |v|^2, max |v|,
+// sum |a|, max |a|, sum |w| r_ext, max |w| r_ext, sum of list rows, max list row.  Also
+// records each owner's bin (for labels).  Float atomics: order-dependent last bits only
+// affect the schedule's choice, never the trajectory (lists are audited).
+template <class F>
+__global__ void __launch_bounds__(256) k_bin_stats(Dev<F> d, float *stats, int *obin)
+{
+    const int sp = d.status->state_par, lc = d.status->list_cur;
+    int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= d.M) return;
+    const Scene &sc = d.scenes[d.owner_scene[o]];
+    const int b = owner_bin(d, sp, o, sc);
+    obin[o] = b;
+    if (!d.st.active[sp][o]) return;
+    auto v4 = d.st.vel[sp][o];
+    auto w4 = d.st.omg[sp][o];
+    float v = sqrtf((float)(v4.x * v4.x + v4.y * v4.y + v4.z * v4.z));
+    float wr = sqrtf((float)(w4.x * w4.x + w4.y * w4.y + w4.z * w4.z)) * (float)d.inv_moi[o].w;
+    float a = d.amag ? d.amag[o] : 0.0f;
+    float rows = 0.0f, rmax = 0.0f;
+    const int64_t first = d.owner_first[o];
+    for (int c = 0; c < (int)d.owner_nsph[o]; ++c) {     // list rows of the owner's spheres
+        float r = (float)d.lists.cnt[lc][first + c];
+        rows += r;
+        rmax = fmaxf(rmax, r);
+    }
+    float *st = stats + (int64_t)b * NSTAT;
+    atomicAdd(&st[0], 1.0f);
+    atomicAdd(&st[1], v);
+    atomicAdd(&st[2], v * v);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[3]), __float_as_uint(v));
+    atomicAdd(&st[4], a);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[5]), __float_as_uint(a));
+    atomicAdd(&st[6], wr);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[7]), __float_as_uint(wr));
+    atomicAdd(&st[8], rows);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[9]), __float_as_uint(rmax));
+}
+
+// The 16 features of each bin, made dimensionless with the step h and the margin beta
+// (displacements per step over beta); X[bin][16], valid[bin] = owners present.
+static __global__ void k_bin_features(const float *stats, int nbins, const int *bin_scene, const Scene *scenes, float beta,
+                               float r_max, float *X, int *valid)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const float *st = stats + (int64_t)b * NSTAT;
+    const Scene &sc = scenes[bin_scene[b]];
+    const float n = st[0];
+    float *x = X + (int64_t)b * 16;
+    valid[b] = n > 0.0f ? 1 : 0;
+    const float inv = n > 0.0f ? 1.0f / n : 0.0f;
+    const float q = sc.hf / fmaxf(beta, 1e-30f);
+    const float mv = st[1] * inv;
+    const float sv = sqrtf(fmaxf(st[2] * inv - mv * mv, 0.0f));
+    const float g = sqrtf(sc.gf[0] * sc.gf[0] + sc.gf[1] * sc.gf[1] + sc.gf[2] * sc.gf[2]);
+    x[0] = log2f(1.0f + n) / 8.0f;
+    x[1] = st[3] * q;
+    x[2] = mv * q;
+    x[3] = sv * q;
+    x[4] = st[5] * sc.hf * q;
+    x[5] = st[4] * inv * sc.hf * q;
+    x[6] = st[7] * q;
+    x[7] = st[6] * inv * q;
+    x[8] = st[8] * inv / 16.0f;
+    x[9] = st[9] / 16.0f;
+    x[10] = g * sc.hf * q;
+    x[11] = log2f(1.0f + 1.0f / (x[1] + x[6] + 1e-6f)) / 16.0f;
+    x[12] = sqrtf(x[4]);
+    x[13] = x[1] + x[6];
+    x[14] = beta / fmaxf(r_max, 1e-30f);
+    x[15] = 1.0f;
+}
+
+// Labels: after each step of a collection window, owners accumulate their displacement
+// bound; the first step at which an owner of a bin passes beta / 2 and beta is recorded
+// per bin (atomicMin over owners: order-independent).
+template <class F>
+__global__ void __launch_bounds__(256) k_collect_step(Dev<F> d, float *acc_lab, const int *obin, int *cross,
+                                                      long long window_start, float beta)
+{
+    const DevStatus *stp = d.status;
+    int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= d.M) return;
+    const int sp = stp->state_par;
+    if (!d.st.active[sp][o]) return;
+    const Scene &sc = d.scenes[d.owner_scene[o]];
+    auto v4 = d.st.vel[sp][o];
+    auto w4 = d.st.omg[sp][o];
+    float v = sqrtf((float)(v4.x * v4.x + v4.y * v4.y + v4.z * v4.z));
+    float w = sqrtf((float)(w4.x * w4.x + w4.y * w4.y + w4.z * w4.z));
+    float a0 = acc_lab[o];
+    float a1 = a0 + sc.hf * (v + w * (float)d.inv_moi[o].w);
+    acc_lab[o] = a1;
+    const int k = (int)(stp->steps_done - window_start);
+    const int b = obin[o];
+    if (a0 <= 0.5f * beta && a1 > 0.5f * beta) atomicMin(&cross[2 * b + 1], k);
+    if (a0 <= beta && a1 > beta) atomicMin(&cross[2 * b + 0], k);
+}
+
+// Smallest predicted log2(steps) over the occupied bins (one block, fixed order).  The
+// network predicts the residual over the kinematic estimate log2(beta / (h (|v| + |w| r)
+// max)) = -log2(feature 13), added back here.
+static __global__ void __launch_bounds__(256) k_min_pred(const float *out, const float *X, const int *valid, int nbins,
+                                                         float *res)
+{
+    __shared__ float red[256];
+    float m = 1e30f;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (valid[b]) m = fminf(m, out[2 * b] - log2f(fmaxf(X[(int64_t)b * 16 + 13], 1e-6f)));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fminf(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *res = red[0];
 }
 
 // ------------------------------------------------------------------ read-back helpers
@@ -799,11 +987,12 @@ __global__ void __launch_bounds__(256) k_count(Dev<F> d, unsigned long long *out
     using R = typename F::R;
     const int sp = d.status->state_par, lc = d.status->list_cur;
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long np = 0, nw = 0, nc = 0;
+    unsigned long long np = 0, nw = 0, nc = 0, ne = 0;
     if (s < d.N) {
         uint32_t o = d.sph_owner[s];
         if (o != 0xffffffffu) {
             const int n = d.lists.cnt[lc][s];
+            ne = n > 0 ? 1 : 0;
             const bool act = d.st.active[sp][o];
             SphereK<F> me;
             if (act) me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
@@ -828,10 +1017,12 @@ __global__ void __launch_bounds__(256) k_count(Dev<F> d, unsigned long long *out
     np = __reduce_add_sync(0xffffffffu, (unsigned)np);
     nw = __reduce_add_sync(0xffffffffu, (unsigned)nw);
     nc = __reduce_add_sync(0xffffffffu, (unsigned)nc);
+    ne = __reduce_add_sync(0xffffffffu, (unsigned)ne);
     if ((threadIdx.x & 31) == 0) {
         if (np) atomicAdd(&out[0], np);
         if (nw) atomicAdd(&out[1], nw);
         if (nc) atomicAdd(&out[2], nc);
+        if (ne) atomicAdd(&out[3], ne);
     }
 }
 

@@ -46,7 +46,9 @@ class Stats(C.Structure):
                 ("margin", C.c_double), ("displacement_bound", C.c_double), ("max_speed", C.c_double),
                 ("mean_steps_per_build", C.c_double), ("cell_size", C.c_double), ("n_cells", C.c_int64),
                 ("ms_detect", C.c_double), ("ms_force", C.c_double), ("ms_hash", C.c_double),
-                ("ms_link", C.c_double), ("n_detect", C.c_int64), ("n_force", C.c_int64), ("ms_total", C.c_double)]
+                ("ms_link", C.c_double), ("n_detect", C.c_int64), ("n_force", C.c_int64), ("ms_total", C.c_double),
+                ("last_cycle", C.c_int64), ("schedule_samples", C.c_int64), ("ms_integrate", C.c_double),
+                ("n_integrate", C.c_int64), ("spheres_with_entries", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +83,7 @@ def _sigs(L):
         "dem_schedule_collect": [P, I32], "dem_schedule_train": [P, I32, C.c_float, C.c_uint64, P],
         "dem_schedule_export": [P, P, SZ, P],
         "dem_util_radix_sort_u32": [I64, P, P, I32, P, P],
+        "dem_util_mlp_forward": [P, I32, P, P], "dem_util_mlp_loss_grad": [P, I32, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -132,6 +135,27 @@ def radix_sort_u32(keys, vals, bits=32):
     vo = np.empty_like(vals)
     _check(load().dem_util_radix_sort_u32(len(keys), _p(keys), _p(vals), bits, _p(ko), _p(vo)))
     return ko, vo
+
+
+MLP_NPARAM = 64 * 16 + 64 + 64 * 64 + 64 + 2 * 64 + 2
+
+
+def mlp_forward(params, X):
+    params = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32).reshape(-1, 16)
+    out = np.empty((len(X), 2), np.float32)
+    _check(load().dem_util_mlp_forward(_p(params), len(X), _p(X), _p(out)))
+    return out
+
+
+def mlp_loss_grad(params, X, Y):
+    params = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32).reshape(-1, 16)
+    Y = np.ascontiguousarray(Y, np.float32).reshape(-1, 2)
+    loss = C.c_float()
+    grad = np.empty(MLP_NPARAM, np.float32)
+    _check(load().dem_util_mlp_loss_grad(_p(params), len(X), _p(X), _p(Y), C.byref(loss), _p(grad)))
+    return loss.value, grad
 
 
 class World:
@@ -251,6 +275,25 @@ class World:
 
     def sync(self):
         self._c(self.L.dem_sync(self.h))
+
+    def schedule_collect(self, on=True):
+        self._c(self.L.dem_schedule_collect(self.h, 1 if on else 0))
+
+    def schedule_train(self, epochs=30, lr=1e-3, seed=0):
+        loss = C.c_float()
+        self._c(self.L.dem_schedule_train(self.h, epochs, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def schedule_export(self):
+        used = C.c_size_t()
+        self.L.dem_schedule_export(self.h, None, 0, C.byref(used))
+        buf = (C.c_uint8 * used.value)()
+        self._c(self.L.dem_schedule_export(self.h, C.cast(buf, C.c_void_p), used.value, C.byref(used)))
+        return bytes(buf)
+
+    def load_schedule_model(self, blob: bytes):
+        buf = (C.c_uint8 * len(blob)).from_buffer_copy(blob)
+        self._c(self.L.dem_load_schedule_model(self.h, C.cast(buf, C.c_void_p), len(blob)))
 
     def set_profiling(self, on=True):
         self._c(self.L.dem_set_profiling(self.h, 1 if on else 0))

@@ -1,0 +1,69 @@
+"""GPU: the tensor-core schedule network against its FP64 oracle, and the learned,
+audited detection schedule against the plain one."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2311_04648_gb300 import dem, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tensor_core_forward_matches_oracle():
+    rng = np.random.default_rng(3)
+    p = rng.normal(scale=0.3, size=omlp.NPARAM).astype(np.float32)
+    for rows in (1, 17, 333):
+        X = rng.normal(size=(rows, 16)).astype(np.float32)
+        got = dem.mlp_forward(p, X)
+        want = omlp.forward(p.astype(np.float64), X.astype(np.float64), bf=True)
+        assert np.max(np.abs(got - want)) <= 1e-3 * (1.0 + np.max(np.abs(want)))
+
+
+def test_tensor_core_gradient_matches_oracle():
+    rng = np.random.default_rng(4)
+    p = rng.normal(scale=0.3, size=omlp.NPARAM).astype(np.float32)
+    X = rng.normal(size=(257, 16)).astype(np.float32)
+    Y = rng.normal(size=(257, 2)).astype(np.float32)
+    L, g = dem.mlp_loss_grad(p, X, Y)
+    Lo, go = omlp.loss_grad(p.astype(np.float64), X.astype(np.float64), Y.astype(np.float64), bf=True)
+    assert L == pytest.approx(Lo, rel=1e-3)
+    assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
+    # and the exact (unrounded) gradient is within BF16 accuracy
+    Le, ge = omlp.loss_grad(p.astype(np.float64), X.astype(np.float64), Y.astype(np.float64), bf=False)
+    assert np.linalg.norm(g - ge) <= 5e-2 * np.linalg.norm(ge)
+
+
+def _scene():
+    return W.settle_box(n=1500, box=(0.03, 0.03, 0.06), seed=21, vel_sigma=0.4, h=1e-6)
+
+
+def test_learned_schedule_trains_and_stays_bit_identical():
+    scene = _scene()
+    beta = 5e-5
+    teacher = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", margin=beta,
+                                   margin_max=beta)
+    teacher.schedule_collect(True)
+    teacher.step(1600)
+    teacher.schedule_collect(False)
+    st = teacher.stats()
+    assert st["schedule_samples"] > 30
+    loss0 = teacher.schedule_train(epochs=1, lr=1e-3, seed=1)
+    loss = teacher.schedule_train(epochs=60, lr=3e-3, seed=1)
+    assert loss < loss0
+    blob = teacher.schedule_export()
+    # a fresh world with the learned schedule and the plain every-step world
+    a = dem.World.from_scene(scene, precision="voxel_fp32", schedule="every_step", margin_max=beta)
+    b = dem.World.from_scene(scene, precision="voxel_fp32", schedule="learned", margin=beta, margin_max=beta)
+    c = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
+    b.load_schedule_model(blob)
+    for w in (a, b, c):
+        w.step(800)
+    for xa, xb in zip(a.owner_state(), b.owner_state()):
+        assert np.array_equal(xa, xb)
+    for xa, xc in zip(a.owner_state(), c.owner_state()):
+        assert np.array_equal(xa, xc)
+    sb, sc = b.stats(), c.stats()
+    cost_b = sb["rebuilds"] + 2 * sb["audit_fallbacks"]
+    cost_c = sc["rebuilds"] + 2 * sc["audit_fallbacks"]
+    print("learned", sb["rebuilds"], sb["audit_fallbacks"], "velocity bound", sc["rebuilds"], sc["audit_fallbacks"])
+    assert cost_b < cost_c
