@@ -563,3 +563,55 @@ def test_gyroscopic_angular_momentum_drift_is_first_order_in_h():
         ow.step(int(round(0.02 / h)))
         drift.append(np.linalg.norm(ow.diagnostics()["angmom"] - L0))
     assert 1.8 < drift[0] / drift[1] < 2.2
+
+
+@pytest.mark.parametrize("nu", [0.2, 0.3, 0.45])
+def test_tangential_to_normal_stiffness_is_mindlins_ratio(nu):
+    """Mindlin: for like materials the tangential stiffness of a Hertzian contact is
+    2(1 - nu)/(2 - nu) times the incremental normal stiffness dF_n/d(delta).  Undamped
+    (e = 1) so that the tangential force is the spring alone; one step of tangential
+    sliding velocity builds the displacement."""
+    R, E, h, delta = 1e-3, 1e7, 1e-7, 2e-5
+    x = np.array([[0.0, 0.0, 0.0], [2 * R - delta, 0.0, 0.0]])
+    s = make_scene(x, v=[[0.0, 0.01, 0.0], [0.0, 0.0, 0.0]], h=h, mat=one_material(E=E, nu=nu, e=1.0, mu=10.0))
+    ow = oracle.OracleWorld(s)
+    F, T, cs = ow.eval()
+    assert len(cs) == 1
+    c = cs[0]
+    n = np.array(c["normal"])
+    f = np.array(c["force"])
+    ft = f - np.dot(f, n) * n
+    kt = np.linalg.norm(ft) / np.linalg.norm(c["ut"])
+    fn = abs(np.dot(f, n))
+    kn_incr = 1.5 * fn / c["overlap"]              # F_n ~ delta^(3/2)
+    assert kt / kn_incr == pytest.approx(2 * (1 - nu) / (2 - nu), rel=1e-9)
+
+
+def test_hertz_headon_unlike_materials_and_radii():
+    """Hertz impact of unlike spheres: delta_max = (15 mbar v^2 / (16 E* sqrt(Rbar)))^(2/5)
+    with 1/E* = sum (1 - nu_i^2)/E_i, Rbar = R1 R2/(R1 + R2), mbar = m1 m2/(m1 + m2)."""
+    R1, R2, E1, E2, n1, n2, v0 = 1e-3, 1.7e-3, 1e7, 3e7, 0.25, 0.4, 0.8
+    t1 = W.sphere_template(R1, mat=0)
+    t2 = W.sphere_template(R2, mat=1)
+    m1, m2 = t1.mass, t2.mass
+    mbar = m1 * m2 / (m1 + m2)
+    Rbar = R1 * R2 / (R1 + R2)
+    Es = 1.0 / ((1 - n1 ** 2) / E1 + (1 - n2 ** 2) / E2)
+    dmax = (15 * mbar * v0 ** 2 / (16 * Es * math.sqrt(Rbar))) ** 0.4
+    tc = 2 * dmax / v0 * 0.4 * math.gamma(0.4) * math.gamma(0.5) / math.gamma(0.9)
+    h = tc / 4000
+    x = np.array([[0.0, 0.0, 0.0], [R1 + R2, 0.0, 0.0]])
+    v = np.array([[v0 * m2 / (m1 + m2), 0, 0], [-v0 * m1 / (m1 + m2), 0, 0]])
+    mat = (np.array([E1, E2]), np.array([n1, n2]), np.ones((2, 2)), np.zeros((2, 2)))
+    s = make_scene(x, v=v, templates=[t1, t2], owner_t=[0, 1], h=h, mat=mat)
+    ow = oracle.OracleWorld(s)
+    best = 0.0
+    for _ in range(3 * 4000):
+        ow.step(1)
+        cs = ow.eval()[2]
+        if len(cs):
+            best = max(best, float(cs["overlap"][0]))
+        elif best > 0:
+            break
+    assert best == pytest.approx(dmax, rel=2e-3)
+    assert ow.v[1, 0] - ow.v[0, 0] == pytest.approx(v0, rel=2e-3)   # elastic: speed of separation = v0
