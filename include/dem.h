@@ -312,6 +312,28 @@ dem_status dem_util_mlp_loss_grad(const float *params, int32_t rows, const float
 dem_status dem_util_radix_sort_u32(int64_t n, const uint32_t *keys, const uint32_t *vals, int32_t bits,
                                    uint32_t *keys_out, uint32_t *vals_out);
 
+/* ---------------------------------------------------------------- no-allocation variant */
+
+/* The paper has no counterpart of this entry point: it serves callers that cannot call
+ * cudaMalloc (code running while a CUDA graph is captured, frameworks that own device
+ * memory through their own pools, loops where an allocation could synchronise the
+ * device).  Same stable LSD radix sort as dem_util_radix_sort_u32, but on DEVICE
+ * buffers owned by the caller: keys[n], vals[n] in, keys_out[n], vals_out[n] out (the
+ * outputs must not alias the inputs or each other), queued on `stream` (a cudaStream_t;
+ * NULL = legacy default stream) and returning once queued.  It allocates nothing: its
+ * temporary storage is one array of device memory inside the library, sized for
+ * DEM_NOALLOC_SORT_MAX keys (about 8.7 MB), which every GPU that loads the library keeps
+ * until the process exits.  n above the maximum returns DEM_ERR_CAPACITY before any work.
+ * The first call on each device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  Every
+ * call shares the array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller; nothing in it needs clearing
+ * between calls.  Errors are described by dem_util_noalloc_error(). */
+#define DEM_NOALLOC_SORT_MAX (1 << 20)
+dem_status dem_util_radix_sort_u32_noalloc(int64_t n, const uint32_t *keys, const uint32_t *vals, int32_t bits,
+                                           uint32_t *keys_out, uint32_t *vals_out, void *stream);
+const char *dem_util_noalloc_error(void);
+
 #ifdef __cplusplus
 }
 #endif

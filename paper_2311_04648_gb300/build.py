@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libdem_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
-SOURCES = ["api.cu", "engine_f64.cu", "engine_f32.cu", "sort.cu", "mlp.cu"]
+SOURCES = ["api.cu", "engine_f64.cu", "engine_f32.cu", "sort.cu", "mlp.cu", "sort_noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -84,6 +84,7 @@ def _sigs(L):
         "dem_schedule_export": [P, P, SZ, P],
         "dem_util_radix_sort_u32": [I64, P, P, I32, P, P],
         "dem_util_mlp_forward": [P, I32, P, P], "dem_util_mlp_loss_grad": [P, I32, P, P, P, P],
+        "dem_util_radix_sort_u32_noalloc": [I64, P, P, I32, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -91,6 +92,8 @@ def _sigs(L):
         f.restype = C.c_int
     L.dem_last_error.argtypes = [P]
     L.dem_last_error.restype = C.c_char_p
+    L.dem_util_noalloc_error.argtypes = []
+    L.dem_util_noalloc_error.restype = C.c_char_p
 
 
 def load(path: str | None = None):
