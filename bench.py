@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=4000)
     ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
-    ap.add_argument("--profile-only", action="store_true", help="small run for ncu captures")
+    ap.add_argument("--tune-steps", type=int, default=60, help="steps per autotuner trial (0: no tuning)")
     return ap.parse_args()
 
 
@@ -203,6 +203,7 @@ def run_ours(args, device):
 
     # chosen form: voxel + FP32, delayed detection on the second stream, audited
     w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
+    out["tuning"] = w.autotune(steps=args.tune_steps) if args.tune_steps > 0 else w.tuning()
     w.step(args.warmup)
     s0 = w.stats()
     with ClockSampler(device) as clk:
@@ -344,6 +345,7 @@ def main():
                    "schedule": "delayed detection on a second stream, velocity-bound cycle, audited every step",
                    "margin_m": res["chosen"]["stats"]["margin"],
                    "rebuilds_in_timed_region": res["chosen"]["rebuilds"],
+                   "tuning": res["tuning"],
                    "l2": "inputs larger than L2 (owner state + contact lists > 0.5 GB)",
                    "parallelism": f"replica x{world}"},
         "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind),
@@ -353,7 +355,7 @@ def main():
                 "d2h_bytes_per_step": e2e["bytes_out"],
                 "how": "dem_set_owner_state from pinned host buffers + dem_step(1) + dem_get_owner_state "
                        "to pinned host buffers, every step"},
-        "gpu_launches": int(3 * steps + 18 * res["chosen"]["rebuilds"]),
+        "gpu_launches": int(3 * steps + 20 * res["chosen"]["rebuilds"]),
         "clocks": res["chosen"]["clocks"],
     }
     if plain:

@@ -212,6 +212,29 @@ dem_status dem_initialize(dem_world *w);
 dem_status dem_step(dem_world *w, int64_t nsteps);
 /* Wait for all work queued by w. */
 dem_status dem_sync(dem_world *w);
+/* Launch shapes and placement of the detection work, chosen by dem_autotune or set
+ * directly.  Results do not depend on them (every choice gives bit-identical states). */
+typedef struct {
+    int32_t contact_block;         /* threads per block of the contact kernel: 32, 64, 128  */
+    int32_t integrate_block;       /* threads per block of the integration kernel: 128..512 */
+    int32_t narrow_block;          /* threads per block of the narrow phase: 64..256        */
+    int32_t detect_inline;         /* delayed schedules: 0 = detection on the second stream
+                                      beside the steps, 1 = on the force stream at the
+                                      cycle boundary                                        */
+    double step_ms;                /* dem_autotune: measured time per step of the choice   */
+} dem_tuning;
+
+dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);
+dem_status dem_get_tuning(dem_world *w, dem_tuning *t);
+/* Time `steps` steps (at least 2 cycles) for each candidate configuration from a
+ * checkpoint of the current state, restore the state, and keep the fastest.  With
+ * cache_path (nullable) the choice is read from / appended to that file, keyed by the
+ * world's size, form, schedule and GPU name; a cached choice skips the trials. */
+dem_status dem_autotune(dem_world *w, int32_t steps, const char *cache_path, dem_tuning *chosen);
+/* Replay the per-step (every-step schedule) or per-cycle (delayed schedules) work from
+ * captured CUDA graphs (on = 1, the default) or launch kernels one by one (on = 0). */
+dem_status dem_set_graphs(dem_world *w, int32_t on);
+
 /* Bracket every force launch and every detection phase with CUDA events on the stream
  * that runs it and accumulate their durations into dem_stats (on = 1); off by default. */
 dem_status dem_set_profiling(dem_world *w, int32_t on);

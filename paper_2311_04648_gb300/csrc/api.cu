@@ -716,6 +716,40 @@ dem_status dem_set_profiling(dem_world *w, int32_t on)
     return DEM_OK;
 }
 
+dem_status dem_set_tuning(dem_world *w, const dem_tuning *t)
+{
+    CHECK_INIT(w);
+    if (!t) return fail(w, DEM_ERR_ARG, "null tuning");
+    std::string err;
+    dem_status s = w->impl->engine->set_tuning(t, err);
+    return s ? fail(w, s, err) : DEM_OK;
+}
+
+dem_status dem_get_tuning(dem_world *w, dem_tuning *t)
+{
+    CHECK_INIT(w);
+    if (!t) return fail(w, DEM_ERR_ARG, "null tuning");
+    std::string err;
+    dem_status s = w->impl->engine->get_tuning(t, err);
+    return s ? fail(w, s, err) : DEM_OK;
+}
+
+dem_status dem_autotune(dem_world *w, int32_t steps, const char *cache_path, dem_tuning *chosen)
+{
+    CHECK_INIT(w);
+    if (steps < 1) return fail(w, DEM_ERR_ARG, "steps must be >= 1");
+    std::string err;
+    dem_status s = w->impl->engine->autotune(steps, cache_path, chosen, err);
+    return s ? fail(w, s, err) : DEM_OK;
+}
+
+dem_status dem_set_graphs(dem_world *w, int32_t on)
+{
+    CHECK_INIT(w);
+    w->impl->engine->set_graphs(on != 0);
+    return DEM_OK;
+}
+
 dem_status dem_get_stream(dem_world *w, void **stream)
 {
     CHECK_INIT(w);

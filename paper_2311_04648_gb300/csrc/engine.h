@@ -81,6 +81,11 @@ public:
     virtual dem_status load(const uint8_t *blob, size_t n, std::string &err) = 0;
     virtual dem_status set_margin(double beta, std::string &err) = 0;
     virtual void set_profiling(bool on) = 0;
+    // launch shapes and detection placement; autotune times candidates on a checkpoint
+    virtual dem_status set_tuning(const dem_tuning *t, std::string &err) = 0;
+    virtual dem_status get_tuning(dem_tuning *t, std::string &err) = 0;
+    virtual dem_status autotune(int steps, const char *cache_path, dem_tuning *chosen, std::string &err) = 0;
+    virtual void set_graphs(bool on) = 0;
     virtual dem_status schedule_collect(int on, std::string &err) = 0;
     virtual dem_status schedule_train(int epochs, float lr, uint64_t seed, float *loss, std::string &err) = 0;
     virtual dem_status schedule_export(std::vector<uint8_t> &w, std::string &err) = 0;

@@ -11,6 +11,7 @@
 #pragma once
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -79,6 +80,11 @@ public:
         d_.gyro = m_.gyroscopic;
         d_.n_scenes = (int)m_.scenes.size();
         beta_ = m_.margin;
+        {
+            int sms = 0;
+            DEM_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m_.device));
+            n_sm_ = std::max(1, sms);
+        }
         const int64_t Np = d_.Np;
 
         dem_status s;
@@ -260,17 +266,26 @@ public:
                 if ((s = settle(err))) return s;
                 continue;
             }
+            const bool use_graphs = graphs_on_ && !prof_ && !collect_ && d_.N > 0;
             if (m_.schedule == DEM_SCHEDULE_EVERY_STEP || d_.N == 0) {
                 long long chunk = std::min<long long>(left, 256);
+                cudaGraphExec_t gx = use_graphs ? graph_for(0) : nullptr;
                 for (long long k = 0; k < chunk; ++k) {
+                    if (gx) {
+                        DEM_CU(cudaGraphLaunch(gx, sf_));
+                        continue;
+                    }
                     if (d_.N > 0) rebuild_inline(sf_);
                     force_step();
                 }
             } else {
-                long long c = std::min<long long>(left, cycle_length());
-                start_detect();
-                for (long long k = 0; k < c; ++k) force_step();
-                finish_detect();
+                long long c = quantize_cycle(std::min<long long>(left, cycle_length()));
+                cudaGraphExec_t gx = use_graphs ? graph_for(c) : nullptr;
+                if (gx) {
+                    DEM_CU(cudaGraphLaunch(gx, sf_));
+                } else {
+                    enqueue_cycle(c);
+                }
             }
             if ((s = settle(err))) return s;
             if ((s = collect_roll(err))) return s;
@@ -665,17 +680,24 @@ public:
         h.vmax_bits = 0;
         h.diverged = 0;
         DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
+        recompact_current();
+        DEM_CU(cudaStreamSynchronize(sf_));
         dirty_ = false;
         return DEM_OK;
     }
 
-    void set_profiling(bool on) override { prof_ = on; }
+    void set_profiling(bool on) override
+    {
+        prof_ = on;
+        drop_graphs();
+    }
 
     dem_status set_margin(double beta, std::string &err) override
     {
         (void)err;
         beta_ = beta;
         dirty_ = true;
+        drop_graphs();
         return DEM_OK;
     }
 
@@ -812,7 +834,12 @@ private:
             if ((s = alloc(d_.lists.hx[b], ne, err))) return s;
             if ((s = alloc(d_.lists.hy[b], ne, err))) return s;
             if ((s = alloc(d_.lists.hz[b], ne, err))) return s;
+            if (!act_alloc_) {
+                if ((s = alloc(d_.lists.act[b], d_.Np, err))) return s;
+                if ((s = alloc(d_.lists.n_act[b], 1, err))) return s;
+            }
         }
+        act_alloc_ = true;
         d_.K = K;
         return DEM_OK;
     }
@@ -820,6 +847,7 @@ private:
     // Grow the row capacity to K, keeping the list in use and the current history.
     dem_status realloc_lists(int K, bool keep, std::string &err)
     {
+        drop_graphs();
         DEM_CU(cudaStreamSynchronize(sf_));
         DEM_CU(cudaStreamSynchronize(sd_));
         ListBuffers<R> old = d_.lists;
@@ -840,6 +868,7 @@ private:
             dfree(old.partner[b]); dfree(old.mirror[b]); dfree(old.cnt[b]);
             dfree(old.hx[b]); dfree(old.hy[b]); dfree(old.hz[b]);
         }
+        if (keep) recompact_current();
         return DEM_OK;
     }
 
@@ -891,6 +920,201 @@ private:
         return DEM_OK;
     }
 
+    // ---- cycles, graphs, tuning
+    // One cycle of a delayed schedule: snapshot, detection of the next list (beside the
+    // steps on the detection stream, or before them on the force stream), c steps with
+    // the list in use, switch.
+    void enqueue_cycle(long long c)
+    {
+        if (tune_.detect_inline) {
+            Mark m1, m2;
+            mark_begin(P_HASH, sf_, m1);
+            launch_hash(sf_);
+            mark_end(sf_, m1);
+            mark_begin(P_DETECT, sf_, m2);
+            launch_detect(sf_);
+            mark_end(sf_, m2);
+            for (long long k = 0; k < c; ++k) force_step();
+            Mark m3;
+            mark_begin(P_LINK, sf_, m3);
+            launch_link(sf_);
+            mark_end(sf_, m3);
+        } else {
+            start_detect();
+            for (long long k = 0; k < c; ++k) force_step();
+            finish_detect();
+        }
+    }
+
+    // Cycle lengths are rounded down to {1, 2, 3} and {4, 5, 6, 7} x 2^j so that a few
+    // captured graphs serve every cycle (the schedule only affects timing, not results).
+    static long long quantize_cycle(long long c)
+    {
+        if (c <= 3) return std::max<long long>(c, 1);
+        long long p = 4;
+        while (p * 2 <= c) p *= 2;
+        long long step = p / 4;
+        return p + ((c - p) / step) * step;
+    }
+
+    // Captured graph of one every-step step (c = 0) or one delayed cycle of length c.
+    cudaGraphExec_t graph_for(long long c)
+    {
+        for (auto &g : graphs_)
+            if (g.c == c) return g.exec;
+        if (graphs_.size() >= 24) drop_graphs();
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(sf_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (c == 0) {
+            rebuild_inline(sf_);
+            force_step();
+        } else {
+            enqueue_cycle(c);
+        }
+        if (cudaStreamEndCapture(sf_, &graph) != cudaSuccess || !graph) {
+            cudaGetLastError();
+            graphs_on_ = false;                      // fall back to direct launches
+            return nullptr;
+        }
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(graph);
+            graphs_on_ = false;
+            return nullptr;
+        }
+        cudaGraphDestroy(graph);
+        graphs_.push_back({c, exec});
+        return exec;
+    }
+
+    void drop_graphs()
+    {
+        for (auto &g : graphs_) cudaGraphExecDestroy(g.exec);
+        graphs_.clear();
+    }
+
+    dem_status set_tuning(const dem_tuning *t, std::string &err) override
+    {
+        if (t->contact_block < 32 || t->contact_block > CONTACT_BLOCK_MAX || t->contact_block % 32 ||
+            t->integrate_block < 32 || t->integrate_block > INTEGRATE_BLOCK_MAX || t->integrate_block % 32 ||
+            t->narrow_block < 32 || t->narrow_block > 256 || t->narrow_block % 32) {
+            err = "block sizes must be multiples of 32 within the kernels' limits";
+            return DEM_ERR_ARG;
+        }
+        dem_status s;
+        if ((s = sync(err))) return s;
+        tune_ = *t;
+        drop_graphs();
+        return DEM_OK;
+    }
+
+    dem_status get_tuning(dem_tuning *t, std::string &err) override
+    {
+        (void)err;
+        *t = tune_;
+        return DEM_OK;
+    }
+
+    void set_graphs(bool on) override
+    {
+        graphs_on_ = on;
+        if (!on) drop_graphs();
+    }
+
+    std::string tune_key()
+    {
+        cudaDeviceProp prop;
+        std::string gpu = "gpu";
+        if (cudaGetDeviceProperties(&prop, m_.device) == cudaSuccess) gpu = prop.name;
+        for (auto &ch : gpu)
+            if (ch == ' ' || ch == '"') ch = '_';
+        return std::string(F::voxel ? "voxel_fp32" : "fp64") + "|" + std::to_string(m_.schedule) + "|" +
+               std::to_string(d_.N) + "|" + std::to_string(d_.M) + "|" + std::to_string((int)m_.clumps) + "|" + gpu;
+    }
+
+    dem_status autotune(int steps, const char *cache_path, dem_tuning *chosen, std::string &err) override
+    {
+        dem_status s;
+        const std::string key = tune_key();
+        if (cache_path) {
+            FILE *f = std::fopen(cache_path, "r");
+            if (f) {
+                char line[512];
+                dem_tuning best{};
+                bool found = false;
+                while (std::fgets(line, sizeof line, f)) {
+                    char k[300];
+                    dem_tuning t{};
+                    if (std::sscanf(line, "{\"key\": \"%299[^\"]\", \"contact_block\": %d, \"integrate_block\": %d, "
+                                          "\"narrow_block\": %d, \"detect_inline\": %d, \"step_ms\": %lf}",
+                                    k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
+                                    &t.step_ms) == 6 &&
+                        key == k) {
+                        best = t;
+                        found = true;
+                    }
+                }
+                std::fclose(f);
+                if (found) {
+                    if ((s = set_tuning(&best, err))) return s;
+                    if (chosen) *chosen = best;
+                    return DEM_OK;
+                }
+            }
+        }
+        std::vector<uint8_t> blob;
+        if ((s = save(blob, err))) return s;
+        const bool delayed = m_.schedule != DEM_SCHEDULE_EVERY_STEP;
+        dem_tuning best = tune_;
+        double best_ms = 1e300;
+        auto trial = [&](const dem_tuning &t) -> dem_status {
+            dem_status st;
+            if ((st = set_tuning(&t, err))) return st;
+            if ((st = load(blob.data(), blob.size(), err))) return st;
+            if ((st = step(std::max(2, steps / 4), err))) return st;     // warm-up, graph capture
+            DEM_CU(cudaEventRecord(ev_c_, sf_));
+            if ((st = step(steps, err))) return st;
+            DEM_CU(cudaEventRecord(ev_b_, sf_));
+            DEM_CU(cudaEventSynchronize(ev_b_));
+            float ms = 0.0f;
+            DEM_CU(cudaEventElapsedTime(&ms, ev_c_, ev_b_));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+            return DEM_OK;
+        };
+        // phase 1: contact block and detection placement; phase 2: the other two shapes
+        for (int cb : {32, 64, 128})
+            for (int di = 0; di <= (delayed ? 1 : 0); ++di)
+                if ((s = trial(dem_tuning{cb, 256, 128, di, 0.0}))) return s;
+        const dem_tuning b1 = best;
+        for (int ib : {256, 512})
+            for (int nb : {128, 256})
+                if (ib != b1.integrate_block || nb != b1.narrow_block)
+                    if ((s = trial(dem_tuning{b1.contact_block, ib, nb, b1.detect_inline, 0.0}))) return s;
+        best.step_ms = best_ms / steps;
+        if ((s = set_tuning(&best, err))) return s;
+        if ((s = load(blob.data(), blob.size(), err))) return s;
+        if (chosen) *chosen = best;
+        if (cache_path) {
+            FILE *f = std::fopen(cache_path, "a");
+            if (f) {
+                std::fprintf(f,
+                             "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
+                             "%d, \"detect_inline\": %d, \"step_ms\": %.6f}\n",
+                             key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
+                             best.detect_inline, best.step_ms);
+                std::fclose(f);
+            }
+        }
+        return DEM_OK;
+    }
+
     // ---- learned schedule
     dem_status sched_buffers(std::string &err)
     {
@@ -908,6 +1132,7 @@ private:
         if ((s = alloc(acc_lab_, d_.M, err))) return s;
         if ((s = alloc(cross_, 2 * (int64_t)nb, err))) return s;
         if ((s = alloc(d_.amag, d_.M, err))) return s;
+        drop_graphs();                                   // captured launches hold the old view
         std::vector<int> bs(nb, 0);
         for (size_t sc = 0; sc < m_.scenes.size(); ++sc) {
             const Scene &g = m_.scenes[sc];
@@ -1064,13 +1289,22 @@ private:
                        st, &ks, &vs);
         k_clear_rows<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_);
         k_cellstart<F><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, ks, vs);
-        k_narrow<F><<<grid(d_.N, 128), 128, 0, st>>>(d_, db_, ks, vs);
+        k_narrow<F><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
     }
 
     void launch_link(cudaStream_t st)
     {
         k_link<F><<<grid(d_.N, 256), 256, 0, st>>>(d_);
+        k_act_reset<F><<<1, 1, 0, st>>>(d_, 0);
+        k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, 0, m_.clumps ? 1 : 0);
         k_commit<<<1, 1, 0, st>>>(st_);
+    }
+
+    // rebuild the compacted work of the list in use (after a restore or a regrow)
+    void recompact_current()
+    {
+        k_act_reset<F><<<1, 1, 0, sf_>>>(d_, 1);
+        k_compact<F><<<grid(d_.Np, 256), 256, 0, sf_>>>(d_, 1, m_.clumps ? 1 : 0);
     }
 
     void rebuild_inline(cudaStream_t st)
@@ -1111,14 +1345,32 @@ private:
         mark_end(sf_, m);
     }
 
-    // k_contact needs ~140 registers: small blocks let an SM hold several, so a block
-    // whose spheres have no partners frees its slot at once
+    // The time step runs k_contact persistently over the compacted work of the list: as
+    // many blocks as the SMs hold at once, never more than the slots need.
     template <int MODE>
     void launch_force(double *eF, double *eT)
     {
-        const unsigned g = grid(d_.N, CONTACT_BLOCK);
-        if (m_.clumps) k_contact<F, true, MODE><<<g, CONTACT_BLOCK, 0, sf_>>>(d_, eF, eT);
-        else k_contact<F, false, MODE><<<g, CONTACT_BLOCK, 0, sf_>>>(d_, eF, eT);
+        const int b = tune_.contact_block;
+        unsigned g = grid(d_.N, b);
+        if (MODE == MODE_STEP) {
+            const unsigned cap = (unsigned)contact_per_sm(b) * (unsigned)n_sm_;
+            g = std::min(g, std::max(1u, cap));
+        }
+        if (m_.clumps) k_contact<F, true, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
+        else k_contact<F, false, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
+    }
+
+    int contact_per_sm(int b)
+    {
+        if (b == occ_block_) return occ_per_sm_;
+        int per_sm = 0;
+        cudaError_t e = m_.clumps
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, true, MODE_STEP>, b, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, false, MODE_STEP>, b, 0);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        occ_block_ = b;
+        occ_per_sm_ = per_sm;
+        return per_sm;
     }
 
     void force_step()
@@ -1128,8 +1380,9 @@ private:
         launch_force<MODE_STEP>(nullptr, nullptr);
         mark_end(sf_, m);
         mark_begin(P_INTEG, sf_, m2);
-        if (m_.clumps) k_integrate<F, true><<<grid(d_.M, 256), 256, 0, sf_>>>(d_);
-        else k_integrate<F, false><<<grid(d_.M, 256), 256, 0, sf_>>>(d_);
+        const int ib = tune_.integrate_block;
+        if (m_.clumps) k_integrate<F, true><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
+        else k_integrate<F, false><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
         mark_end(sf_, m2);
         k_audit<<<1, 1, 0, sf_>>>(st_);
         if (collect_ && d_.M > 0)
@@ -1156,6 +1409,7 @@ private:
 
     void release()
     {
+        drop_graphs();
         if (sf_) cudaStreamSynchronize(sf_);
         if (sd_) cudaStreamSynchronize(sd_);
         std::vector<void *> a = allocs_;
@@ -1193,6 +1447,12 @@ private:
     bool dirty_ = false;
     int64_t fallbacks_ = 0, regrows_ = 0;
     double ms_total_ = 0.0;
+    dem_tuning tune_{64, 256, 128, 0, 0.0};
+    int n_sm_ = 1, occ_block_ = 0, occ_per_sm_ = 1;
+    bool act_alloc_ = false;
+    bool graphs_on_ = true;
+    struct GraphEntry { long long c; cudaGraphExec_t exec; };
+    std::vector<GraphEntry> graphs_;
     // learned schedule
     std::unique_ptr<Mlp> mlp_;
     float *bin_stats_ = nullptr, *X_ = nullptr, *pred_ = nullptr, *predmin_ = nullptr, *acc_lab_ = nullptr;

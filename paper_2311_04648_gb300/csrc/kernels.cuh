@@ -31,6 +31,10 @@ struct ListBuffers {
     uint8_t *mirror[2];
     uint8_t *cnt[2];
     R *hx[2], *hy[2], *hz[2];
+    // compacted work of each list: slots with listed partners (single spheres) or
+    // 32-slot groups containing any (clumps), and their number
+    uint32_t *act[2];
+    uint32_t *n_act[2];
 };
 
 // Owner-state double buffers.

@@ -439,6 +439,50 @@ __global__ void __launch_bounds__(256) k_clear_rows(Dev<F> d)
     d.lists.cnt[stp->list_cur ^ 1][s] = 0;
 }
 
+// Reset the work counter of the new list (which = 0) or of the list in use (which = 1).
+template <class F>
+__global__ void k_act_reset(Dev<F> d, int which)
+{
+    const int l = d.status->list_cur ^ (which ? 0 : 1);
+    *d.lists.n_act[l] = 0;
+}
+
+// Compact the work of a list: slots with a non-empty row (single spheres) or 32-slot
+// groups with any (clumps: the segmented reduction needs whole warps).  The order of the
+// entries depends on scheduling; results do not (every slot's outputs are its own).
+template <class F>
+__global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int warp_level)
+{
+    DevStatus *stp = d.status;
+    if (stp->halt) return;
+    const int l = stp->list_cur ^ (which ? 0 : 1);
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool busy = s < d.N && d.lists.cnt[l][s] > 0;
+    const unsigned int ball = __ballot_sync(0xffffffffu, busy);
+    if (warp_level) {
+        if (lane == 0 && ball) {
+            unsigned int pos = atomicAdd(d.lists.n_act[l], 1u);
+            d.lists.act[l][pos] = (uint32_t)(s >> 5);
+        }
+        // owners never span two groups: an idle group's owners get no contact force for as
+        // long as this list is in use, and the steps of the previous list are done
+        if (!ball && s < d.N && d.sph_head[s]) {
+            using R = typename F::R;
+            const uint32_t o = d.sph_owner[s];
+            if (o != 0xffffffffu) {
+                d.fo[o] = typename F::R4{R(0), R(0), R(0), R(0)};
+                d.to[o] = typename F::R4{R(0), R(0), R(0), R(0)};
+            }
+        }
+    } else {
+        unsigned int base = 0;
+        if (lane == 0 && ball) base = atomicAdd(d.lists.n_act[l], (unsigned int)__popc(ball));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (busy) d.lists.act[l][base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)s;
+    }
+}
+
 // Link the new list: mirror positions for entries whose partner owns the pair, and the
 // tangential history of owned entries carried over from the list in use (zero for a
 // pair that is new: Sec. 4.2, contact wildcards start at zero).
@@ -524,19 +568,16 @@ __device__ __forceinline__ void quat_mul(R aw, R ax, R ay, R az, R bw, R bx, R b
 // force and torque (fo, to) for k_integrate and the updated tangential history; a single
 // sphere without listed partners leaves at once.  MODE_EVAL writes the per-owner force
 // (gravity included) and torque in FP64 and changes nothing.
-constexpr int CONTACT_BLOCK = 64;
+constexpr int CONTACT_BLOCK_MAX = 128;   // launch shapes are tuned at run time up to these
+constexpr int INTEGRATE_BLOCK_MAX = 512;
 
 template <class F, bool CLUMPS, int MODE>
-__global__ void __launch_bounds__(CONTACT_BLOCK) k_contact(Dev<F> d, double *eval_F, double *eval_T)
+__device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int sp, int hp, int lc, double *eval_F,
+                                             double *eval_T)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
-    DevStatus *stp = d.status;
-    if (MODE == MODE_STEP && (stp->halt || stp->list_stale)) return;
-    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-
     bool live = s < d.N;
     // a world of single spheres has one slot per owner, in owner order
     uint32_t o = live ? (CLUMPS ? d.sph_owner[s] : (uint32_t)s) : 0xffffffffu;
@@ -636,12 +677,41 @@ __global__ void __launch_bounds__(CONTACT_BLOCK) k_contact(Dev<F> d, double *eva
     }
 }
 
+// MODE_STEP: persistent grid-stride loop over the compacted work of the list in use
+// (every thread busy, whichever fraction of the spheres has listed partners); for clumps
+// a whole warp takes a 32-slot group.  MODE_EVAL: one thread per slot over all slots.
+template <class F, bool CLUMPS, int MODE>
+__global__ void __launch_bounds__(CONTACT_BLOCK_MAX, 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
+{
+    DevStatus *stp = d.status;
+    if (MODE == MODE_STEP && (stp->halt || stp->list_stale)) return;
+    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
+    if (MODE == MODE_EVAL) {
+        contact_slot<F, CLUMPS, MODE>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, sp, hp, lc, eval_F, eval_T);
+        return;
+    }
+    // the counter never exceeds the slots (or 32-slot groups); the clamp keeps every
+    // index in bounds whatever the counter holds
+    const int64_t cap = CLUMPS ? (d.Np >> 5) : d.Np;
+    const int64_t nw = min((int64_t)*d.lists.n_act[lc], cap);
+    const uint32_t *act = d.lists.act[lc];
+    if (CLUMPS) {
+        const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps)
+            contact_slot<F, CLUMPS, MODE>(d, ((int64_t)act[w] << 5) + (threadIdx.x & 31), sp, hp, lc, eval_F, eval_T);
+    } else {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += stride)
+            contact_slot<F, CLUMPS, MODE>(d, (int64_t)act[t], sp, hp, lc, eval_F, eval_T);
+    }
+}
+
 // Semi-implicit Euler update of each owner (one thread per owner, streaming): v with the
 // contact force plus gravity, then the body-frame angular velocity (Euler's equations,
 // gyroscopic term switchable), then x with the new v, then the quaternion with the new
 // angular velocity; removal by the sink; the per-owner displacement bounds of the audit.
 template <class F, bool CLUMPS>
-__global__ void __launch_bounds__(256) k_integrate(Dev<F> d)
+__global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
 {
     using R = typename F::R;
     using R4 = typename F::R4;

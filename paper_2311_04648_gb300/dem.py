@@ -54,6 +54,14 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("contact_block", C.c_int32), ("integrate_block", C.c_int32), ("narrow_block", C.c_int32),
+                ("detect_inline", C.c_int32), ("step_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Diagnostics(C.Structure):
     _fields_ = [("kinetic", C.c_double), ("potential", C.c_double), ("elastic", C.c_double),
                 ("momentum", C.c_double * 3), ("angular_momentum", C.c_double * 3)]
@@ -71,7 +79,8 @@ def _sigs(L):
         "dem_set_timestep": [P, D], "dem_set_gravity": [P, P], "dem_set_error_velocity": [P, D],
         "dem_set_margin": [P, D], "dem_set_sink": [P, P, P], "dem_load_schedule_model": [P, P, SZ],
         "dem_initialize": [P], "dem_step": [P, I64], "dem_sync": [P], "dem_get_stream": [P, P],
-        "dem_set_profiling": [P, I32],
+        "dem_set_profiling": [P, I32], "dem_set_tuning": [P, P], "dem_get_tuning": [P, P],
+        "dem_autotune": [P, I32, C.c_char_p, P], "dem_set_graphs": [P, I32],
         "dem_get_owner_state": [P, I64, I64, P, P, P, P], "dem_set_owner_state": [P, I64, I64, P, P, P, P],
         "dem_get_sphere_positions": [P, I64, I64, P, P], "dem_get_sphere_voxels": [P, I64, I64, P, P, P],
         "dem_get_contacts": [P, I64, P, P, P, P, P, P, P], "dem_get_listed_pairs": [P, I64, P, P, P],
@@ -297,6 +306,27 @@ class World:
     def load_schedule_model(self, blob: bytes):
         buf = (C.c_uint8 * len(blob)).from_buffer_copy(blob)
         self._c(self.L.dem_load_schedule_model(self.h, C.cast(buf, C.c_void_p), len(blob)))
+
+    def autotune(self, steps=50, cache_path=None):
+        t = Tuning()
+        cp = cache_path.encode() if cache_path else None
+        self._c(self.L.dem_autotune(self.h, steps, cp, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        self._c(self.L.dem_get_tuning(self.h, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        self._c(self.L.dem_set_tuning(self.h, C.byref(t)))
+
+    def tuning(self):
+        t = Tuning()
+        self._c(self.L.dem_get_tuning(self.h, C.byref(t)))
+        return t.as_dict()
+
+    def set_graphs(self, on=True):
+        self._c(self.L.dem_set_graphs(self.h, 1 if on else 0))
 
     def set_profiling(self, on=True):
         self._c(self.L.dem_set_profiling(self.h, 1 if on else 0))
