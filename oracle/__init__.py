@@ -61,7 +61,7 @@ class _World(C.Structure):
                 ("owner", C.c_void_p), ("rloc", C.c_void_p), ("rad", C.c_void_p), ("mat", C.c_void_p),
                 ("h", C.c_double), ("g", C.c_double * 3), ("gyroscopic", C.c_int32), ("has_sink", C.c_int32),
                 ("sink_p", C.c_double * 3), ("sink_n", C.c_double * 3), ("v_err", C.c_double),
-                ("hist", C.c_void_p)]
+                ("hist", C.c_void_p), ("cell_list", C.c_int32)]
 
 
 class Contact(C.Structure):
@@ -151,7 +151,7 @@ class OracleWorld:
     """A world for the oracle, built from a scene description (duck-typed; see
     paper_2311_04648_gb300.workloads.Scene for the fields read here)."""
 
-    def __init__(self, scene):
+    def __init__(self, scene, cell_list: bool = False):
         s = scene
         self.n_mat = len(s.E)
         self.E = np.ascontiguousarray(s.E, np.float64)
@@ -214,6 +214,7 @@ class OracleWorld:
                 w.sink_p[a] = float(sink[0][a]); w.sink_n[a] = float(sink[1][a])
         w.v_err = float(getattr(s, "v_err", 0.0) or 0.0)
         w.hist = lib().orc_history_new()
+        w.cell_list = 1 if cell_list else 0
 
     def __del__(self):
         try:

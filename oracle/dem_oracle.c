@@ -477,6 +477,185 @@ static int cbuf_push(contact_buf *b, const orc_contact *c)
     return 0;
 }
 
+/* One candidate partner jj of sphere i (a sphere when jj < N, else wall jj - N): if the
+ * two touch, the contact's force with its updated history, added to the owners' sums. */
+static int visit_partner(const orc_world *w, const double *p, const orc_hist *h, int64_t i, int64_t jj,
+                         double *F, double *T, contact_buf *out)
+{
+    int64_t N = w->n_sphere;
+    int64_t oa = w->owner[i];
+    contact_in ci;
+    int64_t j, ob = -1;
+    if (jj < N) {
+        j = jj;
+        ob = w->owner[j];
+        if (ob == oa || !owner_is_active(w, ob)) return 0;
+        if (!sphere_pair_contact(w, p, i, j, &ci)) return 0;
+    } else {
+        int32_t k = (int32_t)(jj - N);
+        j = -1 - (int64_t)k;
+        if (!sphere_wall_contact(w, p, i, k, &ci)) return 0;
+    }
+    orc_contact rec;
+    memset(&rec, 0, sizeof(rec));
+    rec.i = i; rec.j = j;
+    int64_t hk = h ? hist_find(h, i, j) : -1;
+    if (hk >= 0) { rec.ut[0] = h->ut[3 * hk]; rec.ut[1] = h->ut[3 * hk + 1]; rec.ut[2] = h->ut[3 * hk + 2]; }
+    hertz_mindlin(&ci, w->h, rec.ut, rec.force);
+    memcpy(rec.point, ci.c, sizeof(ci.c));
+    memcpy(rec.normal, ci.n, sizeof(ci.n));
+    rec.overlap = ci.delta;
+    /* reduction onto the owners: F on A, -F on B; torques about the centres of mass */
+    double rA[3] = {ci.c[0] - w->x[3 * oa], ci.c[1] - w->x[3 * oa + 1], ci.c[2] - w->x[3 * oa + 2]};
+    double tA[3];
+    cross3(rA, rec.force, tA);
+    for (int k = 0; k < 3; ++k) { F[3 * oa + k] += rec.force[k]; T[3 * oa + k] += tA[k]; }
+    if (ob >= 0) {
+        double rB[3] = {ci.c[0] - w->x[3 * ob], ci.c[1] - w->x[3 * ob + 1], ci.c[2] - w->x[3 * ob + 2]};
+        double mf[3] = {-rec.force[0], -rec.force[1], -rec.force[2]};
+        double tB[3];
+        cross3(rB, mf, tB);
+        for (int k = 0; k < 3; ++k) { F[3 * ob + k] += mf[k]; T[3 * ob + k] += tB[k]; }
+    }
+    if (out) return cbuf_push(out, &rec);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ optional grid
+ * A faster way to enumerate the same candidates (cell_list = 1).  Spheres of active
+ * owners are binned into cubes of edge 2 r_max (1 + 1e-6): two spheres that touch are
+ * less than r_i + r_j <= 2 r_max apart, so they sit in the same or adjacent cubes.  The
+ * candidates j > i of the 27 cubes around sphere i are sorted ascending and visited in
+ * that order, so the contacts, their order and every floating-point sum equal those of
+ * the plain loop over all j > i (a test checks trajectories bit for bit).  Positions
+ * that are not finite, or too far apart for 64-bit cube indices, fall back to the plain
+ * loop. */
+typedef struct { int64_t c[3]; int64_t idx; } grid_ent;
+
+static int grid_ent_cmp(const void *a, const void *b)
+{
+    const grid_ent *x = (const grid_ent *)a, *y = (const grid_ent *)b;
+    for (int k = 0; k < 3; ++k) {
+        if (x->c[k] != y->c[k]) return x->c[k] < y->c[k] ? -1 : 1;
+    }
+    return x->idx < y->idx ? -1 : (x->idx > y->idx ? 1 : 0);
+}
+
+static int i64_cmp(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* first entry whose cube is not below c (entries sorted by grid_ent_cmp) */
+static int64_t grid_lower(const grid_ent *e, int64_t n, const int64_t c[3])
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        int below = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (e[mid].c[k] != c[k]) { below = e[mid].c[k] < c[k]; break; }
+        }
+        if (below) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+/* Bins the spheres of active owners; returns 1 with *out (sorted, n entries, caller
+ * frees) on success, 0 when the plain loop must be used, or a negative error. */
+static int grid_build(const orc_world *w, const double *p, grid_ent **out, int64_t *n_out, int64_t **home_out)
+{
+    int64_t N = w->n_sphere;
+    double rmax = 0.0;
+    for (int64_t s = 0; s < N; ++s) rmax = w->rad[s] > rmax ? w->rad[s] : rmax;
+    if (!(rmax > 0.0)) return 0;
+    double cube = 2.0 * rmax * (1.0 + 1e-6);
+    double lo[3] = {0.0, 0.0, 0.0};
+    int any = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!owner_is_active(w, w->owner[s])) continue;
+        for (int k = 0; k < 3; ++k) {
+            double v = p[3 * s + k];
+            if (!isfinite(v)) return 0;
+            if (!any || v < lo[k]) lo[k] = v;
+        }
+        any = 1;
+    }
+    grid_ent *e = (grid_ent *)malloc((size_t)(N > 0 ? N : 1) * sizeof(grid_ent));
+    int64_t *home = (int64_t *)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(int64_t));
+    if (!e || !home) { free(e); free(home); return ORC_ERR_NOMEM; }
+    int64_t n = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!owner_is_active(w, w->owner[s])) continue;
+        for (int k = 0; k < 3; ++k) {
+            double u = floor((p[3 * s + k] - lo[k]) / cube);
+            if (!(u >= 0.0 && u < 1e15)) { free(e); free(home); return 0; }
+            e[n].c[k] = (int64_t)u;
+            home[3 * s + k] = (int64_t)u;
+        }
+        e[n].idx = s;
+        ++n;
+    }
+    qsort(e, (size_t)n, sizeof(grid_ent), grid_ent_cmp);
+    *out = e;
+    *n_out = n;
+    *home_out = home;
+    return 1;
+}
+
+/* Where each cube's entries start, when the cubes spanned are few (at most 8 per sphere
+ * plus 4096): start[c] for the linear cube index c = (cx * ny + cy) * nz + cz, with
+ * start[ncube] = n.  Returns NULL when the span is larger (binary search is used). */
+static int64_t *grid_starts(const grid_ent *e, int64_t n, int64_t dims[3])
+{
+    int64_t span[3] = {0, 0, 0};
+    for (int64_t a = 0; a < n; ++a)
+        for (int k = 0; k < 3; ++k) span[k] = e[a].c[k] + 1 > span[k] ? e[a].c[k] + 1 : span[k];
+    double cubes = (double)span[0] * (double)span[1] * (double)span[2];
+    if (n == 0 || cubes > 8.0 * (double)n + 4096.0) return NULL;
+    int64_t nc = span[0] * span[1] * span[2];
+    int64_t *start = (int64_t *)malloc((size_t)(nc + 1) * sizeof(int64_t));
+    if (!start) return NULL;
+    int64_t a = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        start[c] = a;
+        while (a < n && (e[a].c[0] * span[1] + e[a].c[1]) * span[2] + e[a].c[2] == c) ++a;
+    }
+    start[nc] = n;
+    for (int k = 0; k < 3; ++k) dims[k] = span[k];
+    return start;
+}
+
+/* The candidates j > i of the 27 cubes around sphere i, ascending; returns their number. */
+static int64_t grid_candidates(const grid_ent *e, int64_t n, const int64_t *start, const int64_t dims[3],
+                               const int64_t home[3], int64_t i, int64_t *cand)
+{
+    int64_t nc = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                int64_t c[3] = {home[0] + dx, home[1] + dy, home[2] + dz};
+                int64_t a, b;
+                if (start) {
+                    if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= dims[0] || c[1] >= dims[1] || c[2] >= dims[2])
+                        continue;
+                    int64_t lin = (c[0] * dims[1] + c[1]) * dims[2] + c[2];
+                    a = start[lin];
+                    b = start[lin + 1];
+                } else {
+                    a = grid_lower(e, n, c);
+                    b = n;
+                }
+                for (; a < b; ++a) {
+                    if (e[a].c[0] != c[0] || e[a].c[1] != c[1] || e[a].c[2] != c[2]) break;
+                    if (e[a].idx > i) cand[nc++] = e[a].idx;
+                }
+            }
+    qsort(cand, (size_t)nc, sizeof(int64_t), i64_cmp);
+    return nc;
+}
+
 /* Every contact with delta > 0 in (i, partner) order, each with its force and updated
  * history; per-owner force (gravity first, then contacts) and torque sums. */
 static int evaluate(const orc_world *w, const double *p, double *F, double *T, contact_buf *out)
@@ -491,48 +670,36 @@ static int evaluate(const orc_world *w, const double *p, double *F, double *T, c
         F[3 * o + 2] = act ? m * w->g[2] : 0.0;
         T[3 * o + 0] = 0.0; T[3 * o + 1] = 0.0; T[3 * o + 2] = 0.0;
     }
-    for (int64_t i = 0; i < N; ++i) {
-        int64_t oa = w->owner[i];
-        if (!owner_is_active(w, oa)) continue;
-        /* sphere partners j > i first, then walls in ascending id */
-        for (int64_t jj = i + 1; jj < N + w->n_wall; ++jj) {
-            contact_in ci;
-            int64_t j, ob = -1;
-            if (jj < N) {
-                j = jj;
-                ob = w->owner[j];
-                if (ob == oa || !owner_is_active(w, ob)) continue;
-                if (!sphere_pair_contact(w, p, i, j, &ci)) continue;
-            } else {
-                int32_t k = (int32_t)(jj - N);
-                j = -1 - (int64_t)k;
-                if (!sphere_wall_contact(w, p, i, k, &ci)) continue;
-            }
-            orc_contact rec;
-            memset(&rec, 0, sizeof(rec));
-            rec.i = i; rec.j = j;
-            int64_t hk = h ? hist_find(h, i, j) : -1;
-            if (hk >= 0) { rec.ut[0] = h->ut[3 * hk]; rec.ut[1] = h->ut[3 * hk + 1]; rec.ut[2] = h->ut[3 * hk + 2]; }
-            hertz_mindlin(&ci, w->h, rec.ut, rec.force);
-            memcpy(rec.point, ci.c, sizeof(ci.c));
-            memcpy(rec.normal, ci.n, sizeof(ci.n));
-            rec.overlap = ci.delta;
-            /* reduction onto the owners: F on A, -F on B; torques about the centres of mass */
-            double rA[3] = {ci.c[0] - w->x[3 * oa], ci.c[1] - w->x[3 * oa + 1], ci.c[2] - w->x[3 * oa + 2]};
-            double tA[3];
-            cross3(rA, rec.force, tA);
-            for (int k = 0; k < 3; ++k) { F[3 * oa + k] += rec.force[k]; T[3 * oa + k] += tA[k]; }
-            if (ob >= 0) {
-                double rB[3] = {ci.c[0] - w->x[3 * ob], ci.c[1] - w->x[3 * ob + 1], ci.c[2] - w->x[3 * ob + 2]};
-                double mf[3] = {-rec.force[0], -rec.force[1], -rec.force[2]};
-                double tB[3];
-                cross3(rB, mf, tB);
-                for (int k = 0; k < 3; ++k) { F[3 * ob + k] += mf[k]; T[3 * ob + k] += tB[k]; }
-            }
-            if (out) { int e = cbuf_push(out, &rec); if (e) return e; }
+    grid_ent *ge = NULL;
+    int64_t ng = 0, *home = NULL, *cand = NULL, *start = NULL, dims[3] = {0, 0, 0};
+    int use_grid = 0;
+    if (w->cell_list) {
+        use_grid = grid_build(w, p, &ge, &ng, &home);
+        if (use_grid < 0) return use_grid;
+        if (use_grid) {
+            cand = (int64_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
+            if (!cand) { free(ge); free(home); return ORC_ERR_NOMEM; }
+            start = grid_starts(ge, ng, dims);
         }
     }
-    return 0;
+    int err = 0;
+    for (int64_t i = 0; i < N && !err; ++i) {
+        if (!owner_is_active(w, w->owner[i])) continue;
+        /* sphere partners j > i first, then walls in ascending id */
+        if (use_grid) {
+            int64_t nc = grid_candidates(ge, ng, start, dims, &home[3 * i], i, cand);
+            for (int64_t a = 0; a < nc && !err; ++a) err = visit_partner(w, p, h, i, cand[a], F, T, out);
+            for (int64_t jj = N; jj < N + w->n_wall && !err; ++jj) err = visit_partner(w, p, h, i, jj, F, T, out);
+        } else {
+            for (int64_t jj = i + 1; jj < N + w->n_wall && !err; ++jj)
+                err = visit_partner(w, p, h, i, jj, F, T, out);
+        }
+    }
+    free(start);
+    free(cand);
+    free(home);
+    free(ge);
+    return err;
 }
 
 int orc_eval(const orc_world *w, double *F, double *T, int64_t cap, int64_t *count, orc_contact *contacts)

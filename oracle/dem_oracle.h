@@ -73,6 +73,9 @@ typedef struct {
     double sink_p[3], sink_n[3];    /* owners with (x - sink_p).sink_n < 0 are removed    */
     double v_err;                   /* |v| above this (or NaN) is divergence; <= 0: off  */
     void *hist;                     /* opaque history object (orc_history_new)            */
+    int32_t cell_list;              /* 1: enumerate candidates from a uniform grid instead
+                                       of all j > i; the same contacts in the same order,
+                                       so results are bit-identical (a faster variant)   */
 } orc_world;
 
 /* One resolved contact.  j >= 0 is a sphere, j < 0 is wall (-1 - j).  force acts on
