@@ -213,16 +213,26 @@ def settling_column(n=4_000_000, box=(0.3, 0.3, 1.2), r_lo=0.8e-3, r_hi=1.2e-3, 
 def clump_drum(n_clumps=20_000_000, drum_radius=0.6, omega=1.0, r_lo=1e-3, r_hi=2e-3, mu=0.5, e=0.5,
                E=1e7, nu=0.3, fill=0.40, solid_fraction=0.55, seed=4, h=2e-6, length=None) -> Scene:
     """Half 3-sphere rods, half 4-sphere tetrahedra, component R ~ U[r_lo, r_hi] per clump,
-    in a drum about the x axis.  The drum length L is chosen so that the clumps at the
-    stated solid fraction fill ``fill`` of the drum volume; placement is a lattice in
-    the lower half of the drum with random orientations."""
+    in a drum about the x axis, placed on a lattice (filled from the bottom) with random
+    orientations.  The drum length L is chosen so that the clumps at the stated solid
+    fraction fill ``fill`` of the drum volume, unless the lattice needs a longer drum:
+    randomly oriented clumps on a lattice whose pitch clears the longest clump hold only
+    a few percent solids, so a large clump count sets L by the lattice instead (the
+    effective fill at the stated solid fraction is recorded in ``meta``)."""
     rng = np.random.default_rng(seed)
     kinds = rng.random(n_clumps) < 0.5           # True: rod, False: tetra
     Rc = rng.uniform(r_lo, r_hi, size=n_clumps)
     vol = np.where(kinds, 3.0, 4.0) * (4.0 / 3.0) * math.pi * Rc ** 3
-    if length is None:
-        length = float(vol.sum() / solid_fraction / (fill * math.pi * drum_radius ** 2))
+    length_fill = float(vol.sum() / solid_fraction / (fill * math.pi * drum_radius ** 2))
     spacing = 6.2 * r_hi             # a rod spans 6R: lattice pitch above the largest clump extent
+    if length is None:
+        length = length_fill
+        ys_all = np.arange(-drum_radius + spacing, drum_radius - spacing, spacing)
+        Yf, Zf = np.meshgrid(ys_all, ys_all, indexing="ij")
+        per_slice = int(np.count_nonzero((Yf ** 2 + Zf ** 2) < (drum_radius - spacing) ** 2))
+        slices = len(np.arange(-length / 2 + spacing / 2, length / 2 - spacing / 2 + 1e-12, spacing))
+        if per_slice * slices < n_clumps:
+            length = (math.ceil(n_clumps / per_slice) + 1) * spacing
     # lattice sites inside the lower half disc (y, z) times x
     ys = np.arange(-drum_radius + spacing, drum_radius - spacing, spacing)
     zs = np.arange(-drum_radius + spacing, 0.0, spacing)
@@ -261,7 +271,9 @@ def clump_drum(n_clumps=20_000_000, drum_radius=0.6, omega=1.0, r_lo=1e-3, r_hi=
     hi = np.array([length / 2, drum_radius, drum_radius])
     return Scene(lo, hi, Em, num, corm, mum, walls, templates, owner_t, Rc / 1e-3, pts, q,
                  np.zeros((n_clumps, 3)), np.zeros((n_clumps, 3)), h, np.array([0.0, 0.0, -9.81]),
-                 r_max=r_hi, name=f"clump_drum_n{n_clumps}", meta=dict(length=length))
+                 r_max=r_hi, name=f"clump_drum_n{n_clumps}",
+                 meta=dict(length=length, length_fill=length_fill,
+                           fill_effective=float(vol.sum() / solid_fraction / (math.pi * drum_radius ** 2 * length))))
 
 
 def cone_hopper(n=10_000_000, r_lo=1e-3, r_hi=2e-3, half_angle_deg=30.0, e=0.5, mu=0.4, E=1e7, nu=0.3,

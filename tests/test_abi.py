@@ -66,3 +66,13 @@ def test_calls_without_a_device_fail_cleanly():
     # argument validation needs no device
     st = L.dem_world_create(None, C.byref(h))
     assert st == dem.ERR_ARG
+
+
+def test_smoke_scene_builds_and_has_contacts():
+    import __graft_entry__ as g
+    import oracle
+
+    s = g.smoke_scene()
+    o = oracle.OracleWorld(s)
+    assert o.step(5) == 0
+    assert len(o.eval()[2]) > 100
