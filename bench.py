@@ -35,8 +35,8 @@ METRIC = "sphere-steps/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5000, help="timed steps (the configuration runs 5,000)")
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4_000_000, help="spheres (default: the 4M settling column)")
     ap.add_argument("--plain-steps", type=int, default=40, help="timed steps of the plain FP64 every-step form")
@@ -45,6 +45,15 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=4000)
     ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
     ap.add_argument("--tune-steps", type=int, default=60, help="steps per autotuner trial (0: no tuning)")
+    ap.add_argument("--tune-at", type=int, default=2500,
+                    help="the autotuner times its candidates from the state after this many steps "
+                         "(then the initial state is restored)")
+    ap.add_argument("--workload", default="column", choices=["column", "drum", "hopper", "batch"],
+                    help="column: the headline settling column; the others run one configuration at full size")
+    ap.add_argument("--set-tuning", default="",
+                    help="tuning fields applied after the autotuner, e.g. integrate_staged=1,contact_block=64")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (JSON lines): a later run with the same key reuses its result")
     return ap.parse_args()
 
 
@@ -115,26 +124,74 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- algorithmic bytes
 
-def kernel_bytes(precision, n, n_with_entries, pairs, clumps=False):
-    """Algorithmic DRAM bytes per launch of the two per-step kernels, each distinct array
-    element counted once (state, constants, list rows, history, per-owner force/torque).
-
-    k_integrate (per owner): state read and written, constants, the owner's list-row
-    length, the per-owner accumulators, and the contact force/torque of owners with
-    listed partners.  k_contact: the row length and active flag of every sphere; for a
-    sphere with listed partners its state and constants and the force/torque it writes;
-    per listed pair both row entries, one mirror byte, history read and written."""
+def algorithmic_bytes(precision, n, pairs, clumps=False):
+    """Algorithmic bytes per launch of the two per-step kernels, from the per-unit figures
+    of the method's force+integrate step: the owner state read and written once (voxel
+    form: voxel 8 + offset 12 + v 12 + w 12 = 44 B each way, 88 B; FP64 form: 3 x 24 B each
+    way, 144 B), clumps adding the quaternion (16 B each way), and per listed pair the two
+    ids (8 B) with the tangential history read and written (voxel form 12 + 12 B; FP64
+    24 + 24 B)."""
     if precision == "voxel_fp32":
-        integ = n * (1 + 1 + 24 + 16 + 16 + 16 + 4 + 16 + 2 + 1 + 8      # reads
-                     + 24 + 16 + 16 + 16 + 1 + 8) + 32 * n_with_entries   # writes, force/torque read
-        contact = 2 * n + n_with_entries * (24 + 16 + 16 + 4 + 4 + 2 + 2 + 32) + 33 * pairs
+        integ = 88 * n + (32 * n if clumps else 0)
+        contact = 32 * pairs
     else:
-        integ = n * (1 + 1 + 32 + 32 + 32 + 32 + 8 + 32 + 2 + 1 + 8
-                     + 32 + 32 + 32 + 32 + 1 + 8) + 64 * n_with_entries
-        contact = 2 * n + n_with_entries * (32 + 32 + 32 + 8 + 2 + 2 + 64) + 57 * pairs
+        integ = 144 * n + (32 * n if clumps else 0)
+        contact = 56 * pairs
+    return {"integrate": integ, "contact": contact}
+
+
+def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
+    """Bytes the kernels actually move in this implementation's layout, each distinct
+    array element counted once per launch (context for the algorithmic figure).
+
+    k_integrate (per owner): state read and written (16-byte vectors: mass kept beside
+    the offset, the two audit accumulators in the fourth lanes of v and w; quaternion),
+    constants, row length, flags, and the force/torque of owners with listed partners.  k_contact: per sphere with
+    listed partners its compacted work entry (slot, row length), active flag, state,
+    packed constants and the force/torque it writes; per listed pair both row entries,
+    one mirror byte, the history vector read by both sides and written once."""
+    if precision == "voxel_fp32":
+        integ = n * (1 + 1 + 24 + 16 + 16 + 16 + 4 + 16 + 2 + 1         # reads
+                     + 24 + 16 + 16 + 16 + 1) + 32 * n_with_entries       # writes, force/torque read
+        contact = n_with_entries * (8 + 1 + 24 + 16 + 16 + 16 + 32) + pairs * (8 + 1 + 16 + 16)
+    else:
+        integ = n * (1 + 1 + 32 + 32 + 32 + 32 + 8 + 32 + 2 + 1
+                     + 32 + 32 + 32 + 32 + 1) + 64 * n_with_entries
+        contact = n_with_entries * (8 + 1 + 32 + 32 + 32 + 16 + 64) + pairs * (8 + 1 + 32 + 32)
     if clumps:
         contact += n * (16 if precision == "voxel_fp32" else 32)
     return {"integrate": integ, "contact": contact}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture of the 4M-sphere bench workload (profiles/dram_traffic_settling_column_4M.md),
+# valid while the kernel's source text hashes to the recorded value.
+MEASURED_TRAFFIC = {
+    "integrate": {"n": 4_000_000, "bytes": 745.1e6, "source": [("k_integrate(Dev<F> d)", "f9ed49db846000ab")]},
+    "contact": {"n": 4_000_000, "bytes": 244.3e6,
+                "source": [("k_contact(Dev<F> d, double *eval_F, double *eval_T)", "0d146a79dd095f7c"),
+                           ("contact_slot(const Dev<F> &d", "c8f2a259de1dbfb0")]},
+}
+
+
+def kernel_source_hash(signature):
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2311_04648_gb300", "csrc", "pipeline.cuh")) as f:
+        src = f.read()
+    i = src.find(signature)
+    if i < 0:
+        return None
+    j = src.index("\n}\n", i)
+    return hashlib.sha1(src[i:j].encode()).hexdigest()[:16]
+
+
+def measured_traffic(kernel, n):
+    t = MEASURED_TRAFFIC.get(kernel)
+    if not t or t["n"] != n:
+        return None
+    if any(kernel_source_hash(sig) != hv for sig, hv in t["source"]):
+        return None
+    return t["bytes"]
 
 
 def peaks():
@@ -163,22 +220,31 @@ def profile_delta(p0, p1):
                 detect_ms=(p1["ms_detect"] - p0["ms_detect"]) / max(nd, 1), n_detect=nd,
                 hash_ms=(p1["ms_hash"] - p0["ms_hash"]) / max(nd, 1),
                 link_ms=(p1["ms_link"] - p0["ms_link"]) / max(nd, 1),
-                listed_pairs=p1["listed_pairs"], active_contacts=p1["active_contacts"],
-                with_entries=p1["spheres_with_entries"], list_capacity=p1["list_capacity"])
+                # per-step averages over the profiled steps (the contact count grows as the
+                # column settles)
+                listed_pairs=(p1["pair_steps"] - p0["pair_steps"]) / max(p1["steps"] - p0["steps"], 1),
+                with_entries=(p1["busy_steps"] - p0["busy_steps"]) / max(p1["steps"] - p0["steps"], 1),
+                listed_pairs_end=p1["listed_pairs"], with_entries_end=p1["spheres_with_entries"],
+                active_contacts=p1["active_contacts"], list_capacity=p1["list_capacity"])
 
 
 def roofline(precision, n, prof, peak, peak_kind):
-    kb = kernel_bytes(precision, n, prof["with_entries"], prof["listed_pairs"])
+    ab = algorithmic_bytes(precision, n, prof["listed_pairs"])
+    lb = layout_bytes(precision, n, prof["with_entries"], prof["listed_pairs"])
     per = {}
     for k in ("contact", "integrate"):
         ms = prof[f"{k}_ms"]
-        per[k] = {"ms": ms, "bytes": kb[k], "gbs": kb[k] / (ms / 1000.0) / 1e9 if ms > 0 else None}
+        sec = ms / 1000.0
+        per[k] = {"ms": ms, "bytes": ab[k], "gbs": ab[k] / sec / 1e9 if ms > 0 else None,
+                  "moved_bytes": lb[k], "moved_gbs": lb[k] / sec / 1e9 if ms > 0 else None}
     dom = max(per, key=lambda k: per[k]["ms"])
     a = per[dom]["gbs"]
     return {"bound": "hbm", "kernel": {"contact": "k_contact (pair forces + per-owner sums)",
                                        "integrate": "k_integrate (owner update + audit)"}[dom],
-            "achieved": a, "peak": peak, "unit": "GB/s", "frac": (a / peak) if a else None, "traffic": None,
+            "achieved": a, "peak": peak, "unit": "GB/s", "frac": (a / peak) if a else None,
+            "traffic": measured_traffic(dom, n) if precision == "voxel_fp32" else None,
             "peak_kind": peak_kind, "bytes_per_launch": per[dom]["bytes"], "avg_launch_ms": per[dom]["ms"],
+            "moved_frac": (per[dom]["moved_gbs"] / peak) if per[dom]["moved_gbs"] else None,
             "kernels": per, "listed_pairs": prof["listed_pairs"], "spheres_with_entries": prof["with_entries"]}
 
 
@@ -190,35 +256,59 @@ def run_ours(args, device):
     scene = make_scene(args.n)
     out = {}
 
-    def timed(world, steps):
+    def timed(world, steps, label):
         stream = torch.cuda.ExternalStream(world.stream(), device=device)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        # the NVTX range lets a profiler keep only the timed launches
+        torch.cuda.nvtx.range_push(label)
         e0.record(stream)
         world.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         return e0.elapsed_time(e1)
 
-    # chosen form: voxel + FP32, delayed detection on the second stream, audited
+    # chosen form: voxel + FP32, delayed detection on the second stream, audited; tuned on
+    # a mid-run state (contacts grow as the column settles), then started from step 0
     w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
-    out["tuning"] = w.autotune(steps=args.tune_steps) if args.tune_steps > 0 else w.tuning()
+    if args.tune_steps > 0:
+        start = w.save_state()
+        w.step(args.tune_at)
+        out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache)
+        w.load_state(start)
+        del start
+    else:
+        out["tuning"] = w.tuning()
+    if args.set_tuning:
+        kw = {}
+        for item in args.set_tuning.split(","):
+            k, v = item.split("=")
+            kw[k.strip()] = float(v) if k.strip() == "cell_factor" else int(v)
+        w.set_tuning(**kw)
+        out["tuning"] = w.tuning()
     w.step(args.warmup)
+    after_warmup = w.save_state()
     s0 = w.stats()
     with ClockSampler(device) as clk:
-        ms = timed(w, args.steps)
+        ms = timed(w, args.steps, "timed_chosen")
     s1 = w.stats()
     steps = s1["steps"] - s0["steps"]
     rebuilds = s1["rebuilds"] - s0["rebuilds"]
     out["chosen"] = dict(ms=ms, steps=steps, rebuilds=rebuilds, clocks=clk.summary(), stats=s1)
-    # profiled pass for per-kernel durations (events on each kernel's own stream)
+    # profiled pass over the same steps (restored from the checkpoint) for per-kernel
+    # durations: events on each kernel's own stream
+    end_state = w.save_state()
+    w.load_state(after_warmup)
     w.set_profiling(True)
     p0 = w.stats()
-    w.step(max(20, args.steps // 4))
+    w.step(args.steps)
     p1 = w.stats()
     w.set_profiling(False)
     out["profile"] = profile_delta(p0, p1)
+    w.load_state(end_state)
+    del after_warmup, end_state
     # e2e through the C ABI with host buffers: state in from pinned memory, one step,
     # state out to pinned memory, every step
     n_own = scene.n_owner
@@ -252,7 +342,7 @@ def run_ours(args, device):
         wp = dem.World.from_scene(scene, precision="fp64", schedule="every_step", device=device)
         wp.step(3)
         p0 = wp.stats()
-        msp = timed(wp, args.plain_steps)
+        msp = timed(wp, args.plain_steps, "timed_plain")
         p1 = wp.stats()
         wp.set_profiling(True)
         q0 = wp.stats()
@@ -260,6 +350,113 @@ def run_ours(args, device):
         q1 = wp.stats()
         out["plain"] = dict(ms=msp, steps=p1["steps"] - p0["steps"], profile=profile_delta(q0, q1))
         wp.close()
+    return out
+
+
+def run_scale(args, device, rank=0, world=1):
+    """The other configurations at full size, one JSON line each (not the headline):
+    drum   -- 20M rods and tetrahedra (~70M spheres) in a drum spinning at 1 rad/s;
+    hopper -- 10M spheres in a 30-degree conical hopper with a sink: the learned schedule
+              (network trained on trajectories of the 2k-sphere box and a 1M-sphere
+              section of the settling column) against the velocity-bound and every-step
+              schedules, all audited;
+    batch  -- 512 column collapses of 1k-50k spheres in one engine, autotuned; with N
+              ranks the scenes are split by greedy bin packing on spheres x steps and
+              each rank steps its share as one batch (no exchange until the end)."""
+    import torch
+    from paper_2311_04648_gb300 import dem
+    from paper_2311_04648_gb300 import workloads as W
+
+    torch.cuda.set_device(device)
+
+    def timed(step_fn, stream_ptr, steps, label):
+        stream = torch.cuda.ExternalStream(stream_ptr, device=device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(label)
+        e0.record(stream)
+        step_fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        return e0.elapsed_time(e1)
+
+    steps = args.steps
+    out = {"workload": args.workload}
+    t0 = time.perf_counter()
+    if args.workload == "drum":
+        scene = W.clump_drum(n_clumps=args.n if args.n != 4_000_000 else 20_000_000)
+        w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
+        out["setup_s"] = time.perf_counter() - t0
+        out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache) if args.tune_steps > 0 else w.tuning()
+        w.step(args.warmup)
+        s0 = w.stats()
+        with ClockSampler(device) as clk:
+            ms = timed(w.step, w.stream(), steps, "timed_drum")
+        s1 = w.stats()
+        n_sph = scene.n_sphere
+        out.update(n_spheres=n_sph, n_clumps=scene.n_owner, ms=ms, steps=steps, clocks=clk.summary(),
+                   rebuilds=s1["rebuilds"] - s0["rebuilds"], fallbacks=s1["audit_fallbacks"] - s0["audit_fallbacks"],
+                   listed_pairs=s1["listed_pairs"], contacts=s1["active_contacts"],
+                   value=n_sph * steps / (ms / 1000.0), drum_length_m=scene.meta.get("length"))
+        w.close()
+    elif args.workload == "hopper":
+        # train on the method's own trajectories of the first two configurations
+        teach = [W.settle_box(n=2000, vel_sigma=0.3, seed=2), W.settling_column(n=1_000_000)]
+        blob = None
+        tw = None
+        for k, sc in enumerate(teach):
+            tw = dem.World.from_scene(sc, precision="voxel_fp32", schedule="velocity_bound", device=device)
+            if blob is not None:
+                tw.load_schedule_model(blob)
+            tw.schedule_collect(True)
+            tw.step(2048 if k == 0 else 1536)
+            tw.schedule_collect(False)
+            out[f"train_samples_{k}"] = tw.stats()["schedule_samples"]
+            out[f"train_loss_{k}"] = tw.schedule_train(epochs=60, lr=3e-3, seed=1)
+            blob = tw.schedule_export()
+            tw.close()
+        scene = W.cone_hopper(n=args.n if args.n != 4_000_000 else 10_000_000)
+        n_sph = scene.n_sphere
+        out["setup_s"] = time.perf_counter() - t0
+        res = {}
+        for sched in ("learned", "velocity_bound", "every_step"):
+            w = dem.World.from_scene(scene, precision="voxel_fp32", schedule=sched, device=device,
+                                     margin=None if sched == "every_step" else 6e-5, margin_max=6e-5)
+            if sched == "learned":
+                w.load_schedule_model(blob)
+            w.step(args.warmup)
+            s0 = w.stats()
+            k = steps if sched != "every_step" else max(1, min(steps, args.plain_steps))
+            ms = timed(w.step, w.stream(), k, f"timed_hopper_{sched}")
+            s1 = w.stats()
+            res[sched] = dict(value=n_sph * k / (ms / 1000.0), steps=k, ms=ms,
+                              rebuilds=s1["rebuilds"] - s0["rebuilds"],
+                              fallbacks=s1["audit_fallbacks"] - s0["audit_fallbacks"])
+            w.close()
+        out.update(n_spheres=n_sph, steps=steps, schedules=res, value=res["learned"]["value"],
+                   ms=res["learned"]["ms"])
+    elif args.workload == "batch":
+        from paper_2311_04648_gb300 import shard
+        all_scenes = W.batch_scenes(512)
+        parts = shard.assign([sc.n_sphere for sc in all_scenes], world)
+        scenes = [all_scenes[k] for k in parts[rank]]
+        out["n_spheres_total"] = int(sum(sc.n_sphere for sc in all_scenes))
+        b = dem.Batch(scenes, precision="voxel_fp32", schedule="velocity_bound", device=device)
+        b.initialize()
+        out["setup_s"] = time.perf_counter() - t0
+        w0 = b.worlds[0]
+        out["tuning"] = w0.autotune(steps=args.tune_steps, cache_path=args.tune_cache) if args.tune_steps > 0 else w0.tuning()
+        b.step(args.warmup)
+        s0 = w0.stats()
+        with ClockSampler(device) as clk:
+            ms = timed(b.step, w0.stream(), steps, "timed_batch")
+        s1 = w0.stats()
+        n_sph = int(sum(sc.n_sphere for sc in scenes))
+        out.update(n_spheres=n_sph, n_scenes=len(scenes), ms=ms, steps=steps, clocks=clk.summary(),
+                   rebuilds=s1["rebuilds"] - s0["rebuilds"], value=n_sph * steps / (ms / 1000.0))
+        b.close()
     return out
 
 
@@ -310,6 +507,35 @@ def main():
         return 0
 
     import torch
+    if args.workload != "column":
+        if args.workload != "batch" or world == 1:
+            if rank != 0:
+                return 0
+            r = run_scale(args, local)
+            line = {"metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": 1, "steps": r["steps"],
+                    "warmup": args.warmup, "ms_per_step": r["ms"] / max(r["steps"], 1), "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                    "config": {"workload": args.workload}, "details": r}
+            print(json.dumps(line))
+            return 0
+        # batch over N ranks: each steps its share of the 512 scenes; the slowest sets the time
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        r = run_scale(args, local, rank, world)
+        t = torch.tensor([r["ms"]], device=f"cuda:{local}", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tdist.barrier()
+        ms = float(t.item())
+        if rank == 0:
+            value = r["n_spheres_total"] * r["steps"] / (ms / 1000.0)
+            line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": r["steps"],
+                    "warmup": args.warmup, "ms_per_step": ms / max(r["steps"], 1), "higher_is_better": True,
+                    "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                    "config": {"workload": "batch", "parallelism": f"scenes split over {world} ranks"},
+                    "details": r}
+            print(json.dumps(line))
+        tdist.destroy_process_group()
+        return 0
     if world > 1:
         import torch.distributed as tdist
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))

@@ -111,6 +111,10 @@ typedef struct {
     double ms_integrate;           /* profiled GPU time of the integration kernel          */
     int64_t n_integrate;           /* profiled launches of it                              */
     int64_t spheres_with_entries;  /* spheres whose row of the list in use is not empty    */
+    int64_t pair_steps;            /* sum over completed steps of the listed sphere-sphere
+                                      pairs in use (each pair once): per-step averages     */
+    int64_t busy_steps;            /* sum over completed steps of the spheres with listed
+                                      partners                                              */
 } dem_stats;
 
 typedef struct {
@@ -212,8 +216,9 @@ dem_status dem_initialize(dem_world *w);
 dem_status dem_step(dem_world *w, int64_t nsteps);
 /* Wait for all work queued by w. */
 dem_status dem_sync(dem_world *w);
-/* Launch shapes and placement of the detection work, chosen by dem_autotune or set
- * directly.  Results do not depend on them (every choice gives bit-identical states). */
+/* Launch shapes, detection cell size and placement of the detection work, chosen by
+ * dem_autotune or set directly.  Results do not depend on them (every choice gives
+ * bit-identical states).  For a batch, a scene handle's tuning applies to all scenes. */
 typedef struct {
     int32_t contact_block;         /* threads per block of the contact kernel: 32, 64, 128  */
     int32_t integrate_block;       /* threads per block of the integration kernel: 128..512 */
@@ -222,6 +227,20 @@ typedef struct {
                                       beside the steps, 1 = on the force stream at the
                                       cycle boundary                                        */
     double step_ms;                /* dem_autotune: measured time per step of the choice   */
+    double cell_factor;            /* detection cell edge over the smallest usable one
+                                      (2 r_max + 2 margin_max, rounded up to whole voxels
+                                      in the voxel form), 1 <= f <= 4: larger cells mean
+                                      fewer cells and more candidates per sphere.  The
+                                      voxel edge stays that of f = 1, so positions and
+                                      contact lists are the same for every f.  0 reads
+                                      as 1.                                                 */
+    int32_t integrate_staged;      /* voxel form: 1 = integration streams whole tiles of
+                                      owners through shared memory with bulk asynchronous
+                                      copies (TMA), 0 = one thread per owner reading global
+                                      memory directly; ignored by the FP64 form             */
+    int32_t contact_lean;          /* 1 = the contact kernel compiled for more resident
+                                      warps (fewer registers, some spilled), 0 = fewer warps
+                                      with every value in registers                         */
 } dem_tuning;
 
 dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);

@@ -69,6 +69,52 @@ struct dem_batch {
     std::vector<dem_world *> handles;
 };
 
+namespace dem {
+
+dem_status layout_cells(HostModel &m, double factor, std::string &err)
+{
+    if (!(factor >= 1.0 && factor <= 4.0)) {
+        err = "cell_factor must be in [1, 4]";
+        return DEM_ERR_ARG;
+    }
+    if (m.precision == DEM_PRECISION_VOXEL_FP32) {
+        m.vpc = (int)std::ceil(factor * m.vpc_min - 1e-9);
+        m.L = m.vpc * m.Lv;
+    } else {
+        m.vpc = 1;
+        m.L = factor * m.L_min;
+    }
+    uint64_t cell_base = 0;
+    for (size_t si = 0; si < m.scenes.size(); ++si) {
+        Scene &g = m.scenes[si];
+        for (int a = 0; a < 3; ++a) {
+            double n = std::ceil(m.scene_ext[3 * si + a] / m.L);
+            if (n < 1) n = 1;
+            if (n > (double)(1 << 19)) {
+                err = "too many cells along an axis";
+                return DEM_ERR_ARG;
+            }
+            g.nc[a] = (int)n;
+        }
+        uint64_t nc = (uint64_t)g.nc[0] * (uint64_t)g.nc[1] * (uint64_t)g.nc[2];
+        if (nc >= (1ull << 31)) {
+            err = "scene cell grid too large";
+            return DEM_ERR_ARG;
+        }
+        g.cell_base = (uint32_t)cell_base;
+        cell_base += nc;
+        if (cell_base >= 0xffffffffull) {
+            err = "total cell count exceeds 2^32 - 1";
+            return DEM_ERR_ARG;
+        }
+    }
+    m.n_cells_total = (uint32_t)cell_base;
+    m.cell_factor = factor;
+    return DEM_OK;
+}
+
+}  // namespace dem
+
 namespace {
 
 dem_status fail(dem_world *w, dem_status s, const std::string &msg)
@@ -181,51 +227,44 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
     m.margin_max = mmax;
     const double Lmin = 1.001 * 2.0 * (rmax + mmax);
     if (vox) {
-        // voxels: a power of two at most 1/16 of the cell, so that integer voxel
+        // voxels: a power of two at most 1/16 of the smallest cell, so that integer voxel
         // differences times the voxel edge are exact in FP32 and the FP32 offset inside
         // a voxel resolves ~2^-24 of it; a cell is a whole number of voxels
         m.Lv = std::ldexp(1.0, (int)std::floor(std::log2(Lmin / 16.0)));
-        m.vpc = (int)std::ceil(Lmin / m.Lv);
-        m.L = m.vpc * m.Lv;
+        m.vpc_min = (int)std::ceil(Lmin / m.Lv);
+        m.L_min = m.vpc_min * m.Lv;
     } else {
-        m.L = Lmin;
+        m.L_min = Lmin;
         m.Lv = Lmin;
-        m.vpc = 1;
+        m.vpc_min = 1;
     }
     m.clumps = clumps;
+    m.scene_ext.clear();
+    for (auto &sc : W.scenes)
+        for (int a = 0; a < 3; ++a) m.scene_ext.push_back(sc.desc.box_hi[a] - sc.desc.box_lo[a]);
 
-    uint64_t cell_base = 0;
     int mat_base = 0, pair_base = 0;
     for (size_t si = 0; si < W.scenes.size(); ++si) {
         SceneSetup &sc = W.scenes[si];
         Scene g{};
         for (int a = 0; a < 3; ++a) {
             g.lo[a] = sc.desc.box_lo[a];
-            double ext = sc.desc.box_hi[a] - sc.desc.box_lo[a];
-            double n = std::ceil(ext / m.L);
+            double n = std::ceil(m.scene_ext[3 * si + a] / m.L_min);
             if (n < 1) n = 1;
             if (n > (double)(1 << 19)) {
                 err = "too many cells along an axis";
                 return DEM_ERR_ARG;
             }
-            g.nc[a] = (int)n;
+            g.nbc[a] = (int)n;
+            g.lof[a] = (float)g.lo[a];
             g.g[a] = sc.g[a];
             g.gf[a] = (float)sc.g[a];
-        }
-        uint64_t nc = (uint64_t)g.nc[0] * (uint64_t)g.nc[1] * (uint64_t)g.nc[2];
-        if (nc >= (1ull << 31)) {
-            err = "scene cell grid too large";
-            return DEM_ERR_ARG;
-        }
-        g.cell_base = (uint32_t)cell_base;
-        cell_base += nc;
-        if (cell_base >= 0xffffffffull) {
-            err = "total cell count exceeds 2^32 - 1";
-            return DEM_ERR_ARG;
         }
         g.h = sc.h;
         g.hf = (float)sc.h;
         g.v_err = sc.v_err;
+        g.v_errf = (float)sc.v_err;
+        if ((double)g.v_errf > sc.v_err) g.v_errf = std::nextafter(g.v_errf, -INFINITY);
         g.wall_begin = (int)m.walls.size();
         g.wall_count = (int)sc.walls.size();
         g.has_sink = sc.has_sink ? 1 : 0;
@@ -238,7 +277,7 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
         g.mat_base = mat_base;
         g.n_mat = nm;
         g.pair_base = pair_base;
-        for (int a = 0; a < 3; ++a) g.nb[a] = (g.nc[a] + BIN_CELLS - 1) / BIN_CELLS;
+        for (int a = 0; a < 3; ++a) g.nb[a] = (g.nbc[a] + BIN_CELLS - 1) / BIN_CELLS;
         g.bin_base = m.n_bins;
         m.n_bins += g.nb[0] * g.nb[1] * g.nb[2];
         for (int a = 0; a < nm; ++a) {
@@ -262,12 +301,29 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
             for (int a = 0; a < 3; ++a) { w.p[a] = ws.p[a]; w.n[a] = ws.n[a]; w.omega[a] = ws.omega[a]; }
             w.r0 = ws.r0; w.z0 = ws.z0; w.r1 = ws.r1; w.z1 = ws.z1;
             for (int a = 0; a < 3; ++a) { w.pf[a] = (float)ws.p[a]; w.nf[a] = (float)ws.n[a]; }
-            w.r0f = (float)ws.r0;
+            w.r0f = (float)ws.r0; w.r1f = (float)ws.r1; w.z0f = (float)ws.z0; w.z1f = (float)ws.z1;
+            {
+                // An FP32 evaluation of the gap (about ten rounded operations on values no
+                // larger than |centre| + this scale) errs by well under 1e-6 of that sum; the
+                // screen allows 2e-5 of it.  A cone's closest-point parameter divides by the
+                // segment's squared length, which amplifies errors by scale / length.
+                double scale = std::fabs(ws.p[0]) + std::fabs(ws.p[1]) + std::fabs(ws.p[2]) + std::fabs(ws.r0) +
+                               std::fabs(ws.r1) + std::fabs(ws.z0) + std::fabs(ws.z1) + 1.0;
+                double cond = 1.0;
+                if (ws.type == WALL_CONE) {
+                    double len = std::sqrt((ws.r1 - ws.r0) * (ws.r1 - ws.r0) + (ws.z1 - ws.z0) * (ws.z1 - ws.z0));
+                    cond += scale / std::max(len, 1e-30);
+                }
+                w.tolf = (float)(2e-5 * scale * cond);
+            }
             m.walls.push_back(w);
         }
         m.scenes.push_back(g);
     }
-    m.n_cells_total = (uint32_t)cell_base;
+    {
+        dem_status ls = layout_cells(m, 1.0, err);
+        if (ls) return ls;
+    }
 
     // owners and sphere slots
     m.scene_owner_base.clear();

@@ -99,22 +99,27 @@ struct Wall {            // analytical wall (device copy); geometry in FP64
     double p[3], n[3];
     double r0, z0, r1, z1;
     double omega[3];
-    float pf[3], nf[3];  // FP32 copies for screening tests (never decide a contact)
-    float r0f, pad;
+    float pf[3], nf[3];  // FP32 copies for screening tests (decide only far from the
+    float r0f, r1f, z0f, z1f;   // threshold, see wall_gap_f)
+    float tolf;          // screening tolerance per unit of (|centre|_1 + 1), see wall_gap_f
 };
 
 struct Scene {           // per-scene constants (device copy)
     double lo[3];        // origin of the cell grid
+    float lof[3];        // the same rounded to FP32 (screening only)
     int nc[3];           // cells per axis
     uint32_t cell_base;  // first global cell index of this scene
     double h, g[3];
     float hf, gf[3];
     double v_err;        // <= 0: off
+    float v_errf;        // largest float not above v_err: a float speed s has s <= v_errf
+                         // exactly when s <= v_err
     int wall_begin, wall_count;
     int has_sink;
     double sink_p[3], sink_n[3];
     int mat_base, n_mat, pair_base;
-    int nb[3];           // schedule bins per axis (BIN_CELLS cells each)
+    int nb[3];           // schedule bins per axis (BIN_CELLS smallest cells each)
+    int nbc[3];          // smallest cells per axis (the bins' grid; detection cells may be larger)
     int bin_base;        // first global bin of this scene
 };
 
@@ -152,10 +157,17 @@ struct DevStatus {
     double disp_cur;             // displacement bound since the snapshot of the list in use
     double disp_next;            // ... since the snapshot of the list being built
     double beta_cur, beta_next;  // margins of those lists
+    float beta_next_f;           // beta_next rounded to FP32
     double vmax_last;            // max |v| after the last completed step
     double disp_slack;           // added per step: rounding of the position update
+    float disp_slack_f;          // the same (a power of two, exact in FP32)
     long long steps_done;
     long long rebuilds;
+    unsigned int cell_stamp;     // stamp of the cell table of the build in progress (from 1)
+    unsigned int list_pairs[2];  // sphere-sphere pairs of each list (each pair once)
+    unsigned int list_busy[2];   // slots of each list with listed partners
+    unsigned long long pair_steps;   // sum over completed steps of the pairs in use
+    unsigned long long busy_steps;   // sum over completed steps of the slots with partners
     long long stale_events;
 };
 

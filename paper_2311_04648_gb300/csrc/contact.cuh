@@ -139,6 +139,33 @@ __device__ __forceinline__ bool plane_may_reach(const Wall &w, float3 p, float r
     return g <= reach + 1e-5f * scale + 1e-9f;
 }
 
+// The signed gap of wall_gap evaluated in FP32 from an FP32 centre, for screening: it
+// differs from the FP64 gap by less than wall_gap_tol, so a comparison with a threshold
+// that clears the threshold by more than that is decided the same way as in FP64.
+__device__ __forceinline__ float wall_gap_f(const Wall &w, float3 c)
+{
+    const float dx = c.x - w.pf[0], dy = c.y - w.pf[1], dz = c.z - w.pf[2];
+    const float z = dx * w.nf[0] + dy * w.nf[1] + dz * w.nf[2];
+    if (w.type == WALL_PLANE) return z;
+    const float rx = dx - z * w.nf[0], ry = dy - z * w.nf[1], rz = dz - z * w.nf[2];
+    const float rho = sqrtf(rx * rx + ry * ry + rz * rz);
+    if (w.type == WALL_CYLINDER) return w.r0f - rho;
+    const float dr = w.r1f - w.r0f, dzz = w.z1f - w.z0f;
+    const float len2 = dr * dr + dzz * dzz;
+    float t = ((rho - w.r0f) * dr + (z - w.z0f) * dzz) / len2;
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    const float Dr = rho - (w.r0f + t * dr), Dz = z - (w.z0f + t * dzz);
+    const float dist = sqrtf(Dr * Dr + Dz * Dz);
+    float inr = -dzz, inz = dr;            // inward normal of the generator, unnormalised
+    if (inr > 0.0f) { inr = -inr; inz = -inz; }
+    return (Dr * inr + Dz * inz) >= 0.0f ? dist : -dist;
+}
+
+__device__ __forceinline__ float wall_gap_tol(const Wall &w, float3 c)
+{
+    return w.tolf * (fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + 1.0f) + 1e-9f;
+}
+
 // Signed gap of a sphere centre to a wall (positive on the domain side) and the unit
 // normal from the wall to the centre; FP64, every product and sum rounded in a fixed
 // order.  Returns false where the normal is undefined (centre on an axis).

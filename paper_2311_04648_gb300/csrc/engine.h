@@ -19,6 +19,10 @@ struct HostModel {
     double L = 0.0;                 // cell edge
     double Lv = 0.0;                // voxel edge (voxel form: a power of two, L = vpc * Lv)
     int vpc = 1;                    // voxels per cell edge
+    double L_min = 0.0;             // smallest usable cell edge (cell factor 1)
+    int vpc_min = 1;                // voxels per edge of that cell
+    double cell_factor = 1.0;       // L over L_min
+    std::vector<double> scene_ext;  // box extent per scene and axis (3 per scene)
     double margin = 0.0;            // margin of the lists (EVERY_STEP) / upper bound (delayed)
     double margin_max = 0.0;
     double r_max = 0.0;
@@ -55,6 +59,10 @@ struct ContactOut {
     int64_t i, j;                   // user sphere ids; j = -1 - wall for walls
     double force[3], point[3], overlap, hist[3];
 };
+
+// Detection cells of edge f * L_min (whole voxels in the voxel form) for every scene:
+// cells per axis, global cell bases and the total.  Schedule bins keep the f = 1 grid.
+dem_status layout_cells(HostModel &m, double factor, std::string &err);
 
 class EngineBase {
 public:

@@ -77,6 +77,8 @@ public:
         d_.Ld = F::voxel ? m_.Lv : m_.L;
         d_.invL = 1.0 / m_.L;
         d_.vpc = m_.vpc;
+        d_.bin_invL = 1.0 / m_.L_min;
+        d_.bin_vpc = m_.vpc_min;
         d_.gyro = m_.gyroscopic;
         d_.n_scenes = (int)m_.scenes.size();
         beta_ = m_.margin;
@@ -86,27 +88,28 @@ public:
             n_sm_ = std::max(1, sms);
         }
         const int64_t Np = d_.Np;
+        // owner arrays that the staged integration copies tile by tile hold whole tiles
+        const int64_t Mp = (M + ITILE - 1) / ITILE * ITILE;
+        Mp_ = Mp;
 
         dem_status s;
         // owner state, double-buffered
         for (int b = 0; b < 2; ++b) {
             if constexpr (F::voxel) {
-                if ((s = alloc(d_.st.pos[b].vox, M, err))) return s;
-                if ((s = alloc(d_.st.pos[b].om, M, err))) return s;
+                if ((s = alloc(d_.st.pos[b].vox, Mp, err))) return s;
+                if ((s = alloc(d_.st.pos[b].om, Mp, err))) return s;
             } else {
                 if ((s = alloc(d_.st.pos[b].xm, M, err))) return s;
             }
-            if ((s = alloc(d_.st.vel[b], M, err))) return s;
-            if ((s = alloc(d_.st.omg[b], M, err))) return s;
-            if ((s = alloc(d_.st.quat[b], M, err))) return s;
-            if ((s = alloc(d_.st.active[b], M, err))) return s;
+            if ((s = alloc(d_.st.vel[b], Mp, err))) return s;
+            if ((s = alloc(d_.st.omg[b], Mp, err))) return s;
+            if ((s = alloc(d_.st.quat[b], Mp, err))) return s;
+            if ((s = alloc(d_.st.active[b], Mp, err))) return s;
         }
-        if ((s = alloc(d_.inv_moi, M, err))) return s;
-        if ((s = alloc(d_.inv_mass, M, err))) return s;
-        if ((s = alloc(d_.owner_scene, M, err))) return s;
-        if ((s = alloc(d_.owner_iso, M, err))) return s;
-        if ((s = alloc(d_.acc[0], M, err))) return s;
-        if ((s = alloc(d_.acc[1], M, err))) return s;
+        if ((s = alloc(d_.inv_moi, Mp, err))) return s;
+        if ((s = alloc(d_.inv_mass, Mp, err))) return s;
+        if ((s = alloc(d_.owner_scene, Mp, err))) return s;
+        if ((s = alloc(d_.owner_iso, Mp, err))) return s;
         if ((s = alloc(d_.fo, M, err))) return s;
         if ((s = alloc(d_.to, M, err))) return s;
         if ((s = alloc(d_.owner_first, M, err))) return s;
@@ -117,6 +120,7 @@ public:
         if ((s = alloc(d_.sph_rlo, N, err))) return s;
         if ((s = alloc(d_.sph_mat, N, err))) return s;
         if ((s = alloc(d_.sph_rloc, N, err))) return s;
+        if ((s = alloc(d_.sph_pack, N, err))) return s;
         if ((s = alloc(d_.sph_head, N, err))) return s;
         if ((s = alloc(d_.sph_segend, N, err))) return s;
         Scene *scenes;
@@ -148,8 +152,7 @@ public:
         if ((s = alloc(db_.vals_alt, Nk, err))) return s;
         db_.hist_cap = radix_hist_entries(Nk);
         if ((s = alloc(db_.hist, db_.hist_cap, err))) return s;
-        if ((s = alloc(db_.cell_start, (int64_t)m_.n_cells_total + 1, err))) return s;
-        if ((s = alloc(db_.cell_end, (int64_t)m_.n_cells_total + 1, err))) return s;
+        if ((s = alloc(db_.cell_tab, (int64_t)m_.n_cells_total + 1, err))) return s;
         if (F::voxel) {
             int4 *a; float4 *b2; int4 *c; float4 *e;
             if ((s = alloc(a, Nk, err))) return s;
@@ -197,6 +200,21 @@ public:
         if ((s = up(d_.sph_rlo, rlo.data(), N, err))) return s;
         if ((s = up(d_.sph_mat, m_.sph_mat.data(), N, err))) return s;
         if ((s = up(d_.sph_rloc, rloc.data(), N, err))) return s;
+        {
+            using P = typename SphPack<R>::T;
+            std::vector<P> pk(N);
+            for (int64_t k = 0; k < N; ++k) {
+                if constexpr (F::voxel) {
+                    int mi = (int)m_.sph_mat[k];
+                    float mf;
+                    std::memcpy(&mf, &mi, sizeof(mf));
+                    pk[k] = make_float4((float)rad[k], rlo[k], mf, 0.0f);
+                } else {
+                    pk[k] = make_double2((double)rad[k], (double)m_.sph_mat[k]);
+                }
+            }
+            if ((s = up(d_.sph_pack, pk.data(), N, err))) return s;
+        }
         if ((s = up(d_.sph_head, m_.sph_head.data(), N, err))) return s;
         if ((s = up(d_.sph_segend, m_.sph_segend.data(), N, err))) return s;
         if ((s = up(scenes, m_.scenes.data(), m_.scenes.size(), err))) return s;
@@ -224,6 +242,7 @@ public:
         }
         DevStatus h{};
         h.disp_slack = F::voxel ? 4.0 * std::ldexp(1.0, std::ilogb(m_.Lv) - 23) : 0.0;
+        h.disp_slack_f = (float)h.disp_slack;
         h.beta_cur = h.beta_next = beta_;
         for (int64_t o = 0; o < M; ++o) {   // initial speed bound for the first cycle length
             double v2 = m_.v[3 * o] * m_.v[3 * o] + m_.v[3 * o + 1] * m_.v[3 * o + 1] + m_.v[3 * o + 2] * m_.v[3 * o + 2];
@@ -469,7 +488,9 @@ public:
         std::vector<uint8_t> cnt;
         if ((s = fetch_list(sth_->list_cur, partner, cnt, err))) return s;
         const int64_t ne = (int64_t)d_.K * d_.Np;
-        std::vector<R> hx(ne, R(0)), hy(ne, R(0)), hz(ne, R(0));
+        using H = typename HistVec<R>::T;
+        std::vector<H> hv(ne);
+        for (auto &v : hv) { v.x = R(0); v.y = R(0); v.z = R(0); v.w = R(0); }
         for (int64_t q = 0; q < nk; ++q) {
             if (ii[q] < 0 || ii[q] >= (int64_t)m_.slot_of_sphere.size()) continue;
             int64_t sl = m_.slot_of_sphere[ii[q]];
@@ -486,14 +507,12 @@ public:
             for (int k = 0; k < cnt[sl]; ++k) {
                 int64_t e = (int64_t)k * d_.Np + sl;
                 if (partner[e] == key) {
-                    hx[e] = (R)ut[3 * q]; hy[e] = (R)ut[3 * q + 1]; hz[e] = (R)ut[3 * q + 2];
+                    hv[e].x = (R)ut[3 * q]; hv[e].y = (R)ut[3 * q + 1]; hv[e].z = (R)ut[3 * q + 2];
                 }
             }
         }
         const int hp = sth_->hist_par;
-        DEM_CU(cudaMemcpyAsync(d_.lists.hx[hp], hx.data(), ne * sizeof(R), cudaMemcpyHostToDevice, sf_));
-        DEM_CU(cudaMemcpyAsync(d_.lists.hy[hp], hy.data(), ne * sizeof(R), cudaMemcpyHostToDevice, sf_));
-        DEM_CU(cudaMemcpyAsync(d_.lists.hz[hp], hz.data(), ne * sizeof(R), cudaMemcpyHostToDevice, sf_));
+        DEM_CU(cudaMemcpyAsync(d_.lists.hist[hp], hv.data(), ne * sizeof(H), cudaMemcpyHostToDevice, sf_));
         DEM_CU(cudaStreamSynchronize(sf_));
         return DEM_OK;
     }
@@ -526,6 +545,8 @@ public:
         o->ms_total = ms_total_;
         o->last_cycle = last_cycle_;
         o->schedule_samples = (int64_t)(ds_y_.size() / MLP_OUT);
+        o->pair_steps = (int64_t)sth_->pair_steps;
+        o->busy_steps = (int64_t)sth_->busy_steps;
         if (d_.N > 0) {
             double *buf;
             if ((s = scratch(buf, 4, err))) return s;
@@ -608,11 +629,7 @@ public:
         if ((s = dput(d_.lists.partner[lc], ne * 4))) return s;
         if ((s = dput(d_.lists.mirror[lc], ne))) return s;
         if ((s = dput(d_.lists.cnt[lc], d_.Np))) return s;
-        if ((s = dput(d_.lists.hx[hp], ne * sizeof(R)))) return s;
-        if ((s = dput(d_.lists.hy[hp], ne * sizeof(R)))) return s;
-        if ((s = dput(d_.lists.hz[hp], ne * sizeof(R)))) return s;
-        if ((s = dput(d_.acc[0], M * sizeof(float)))) return s;
-        if ((s = dput(d_.acc[1], M * sizeof(float)))) return s;
+        if ((s = dput(d_.lists.hist[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
         double extra[2] = {beta_, (double)fallbacks_};
         put(extra, sizeof(extra));
         return DEM_OK;
@@ -666,11 +683,7 @@ public:
         if ((s = dget(d_.lists.partner[lc], ne * 4))) return s;
         if ((s = dget(d_.lists.mirror[lc], ne))) return s;
         if ((s = dget(d_.lists.cnt[lc], d_.Np))) return s;
-        if ((s = dget(d_.lists.hx[hp], ne * sizeof(R)))) return s;
-        if ((s = dget(d_.lists.hy[hp], ne * sizeof(R)))) return s;
-        if ((s = dget(d_.lists.hz[hp], ne * sizeof(R)))) return s;
-        if ((s = dget(d_.acc[0], M * sizeof(float)))) return s;
-        if ((s = dget(d_.acc[1], M * sizeof(float)))) return s;
+        if ((s = dget(d_.lists.hist[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
         double extra[2];
         if (!get(extra, sizeof(extra))) { err = "truncated state blob"; return DEM_ERR_ARG; }
         beta_ = extra[0];
@@ -679,6 +692,13 @@ public:
         h.step_disp_bits = 0;
         h.vmax_bits = 0;
         h.diverged = 0;
+        {
+            // the cell table still holds entries stamped by builds after the checkpoint:
+            // the stamp only moves forward
+            unsigned int cur = 0;
+            DEM_CU(cudaMemcpy(&cur, &st_->cell_stamp, sizeof(cur), cudaMemcpyDeviceToHost));
+            h.cell_stamp = std::max(h.cell_stamp, cur);
+        }
         DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
         recompact_current();
         DEM_CU(cudaStreamSynchronize(sf_));
@@ -830,10 +850,8 @@ private:
         for (int b = 0; b < 2; ++b) {
             if ((s = alloc(d_.lists.partner[b], ne, err))) return s;
             if ((s = alloc(d_.lists.mirror[b], ne, err))) return s;
-            if ((s = alloc(d_.lists.cnt[b], d_.Np, err))) return s;
-            if ((s = alloc(d_.lists.hx[b], ne, err))) return s;
-            if ((s = alloc(d_.lists.hy[b], ne, err))) return s;
-            if ((s = alloc(d_.lists.hz[b], ne, err))) return s;
+            if ((s = alloc(d_.lists.cnt[b], std::max(d_.Np, Mp_), err))) return s;
+            if ((s = alloc(d_.lists.hist[b], ne, err))) return s;
             if (!act_alloc_) {
                 if ((s = alloc(d_.lists.act[b], d_.Np, err))) return s;
                 if ((s = alloc(d_.lists.n_act[b], 1, err))) return s;
@@ -860,15 +878,18 @@ private:
             DEM_CU(cudaMemcpy(d_.lists.partner[lc], old.partner[lc], ne * 4, cudaMemcpyDeviceToDevice));
             DEM_CU(cudaMemcpy(d_.lists.mirror[lc], old.mirror[lc], ne, cudaMemcpyDeviceToDevice));
             DEM_CU(cudaMemcpy(d_.lists.cnt[lc], old.cnt[lc], d_.Np, cudaMemcpyDeviceToDevice));
-            DEM_CU(cudaMemcpy(d_.lists.hx[hp], old.hx[hp], ne * sizeof(R), cudaMemcpyDeviceToDevice));
-            DEM_CU(cudaMemcpy(d_.lists.hy[hp], old.hy[hp], ne * sizeof(R), cudaMemcpyDeviceToDevice));
-            DEM_CU(cudaMemcpy(d_.lists.hz[hp], old.hz[hp], ne * sizeof(R), cudaMemcpyDeviceToDevice));
+            DEM_CU(cudaMemcpy(d_.lists.hist[hp], old.hist[hp], ne * sizeof(typename HistVec<R>::T),
+                              cudaMemcpyDeviceToDevice));
         }
         for (int b = 0; b < 2; ++b) {
             dfree(old.partner[b]); dfree(old.mirror[b]); dfree(old.cnt[b]);
-            dfree(old.hx[b]); dfree(old.hy[b]); dfree(old.hz[b]);
+            dfree(old.hist[b]);
         }
         if (keep) recompact_current();
+        if (tune_.integrate_staged) {               // new row-length arrays: check them again
+            staged_per_sm_ = 0;
+            tune_.integrate_staged = prepare_staged() ? 1 : 0;
+        }
         return DEM_OK;
     }
 
@@ -1005,10 +1026,87 @@ private:
             err = "block sizes must be multiples of 32 within the kernels' limits";
             return DEM_ERR_ARG;
         }
+        const double f = t->cell_factor == 0.0 ? 1.0 : t->cell_factor;
+        if (!(f >= 1.0 && f <= 4.0)) {
+            err = "cell_factor must be in [1, 4]";
+            return DEM_ERR_ARG;
+        }
         dem_status s;
         if ((s = sync(err))) return s;
-        tune_ = *t;
         drop_graphs();
+        if (f != m_.cell_factor) {
+            if ((s = relayout_cells(f, err))) return s;
+        }
+        tune_ = *t;
+        tune_.cell_factor = m_.cell_factor;
+        tune_.integrate_staged = (t->integrate_staged && prepare_staged()) ? 1 : 0;
+        tune_.contact_lean = t->contact_lean ? 1 : 0;
+        return DEM_OK;
+    }
+
+    // The staged integration needs its shared-memory size allowed once (outside any
+    // stream capture) and 16-byte aligned owner arrays (a user allocator might not give
+    // them); false where it cannot run.
+    bool prepare_staged()
+    {
+        if constexpr (!F::voxel) {
+            return false;
+        } else {
+            if (staged_per_sm_ > 0) return true;
+            const void *ptrs[] = {d_.st.pos[0].vox, d_.st.pos[1].vox, d_.st.pos[0].om, d_.st.pos[1].om,
+                                  d_.st.vel[0], d_.st.vel[1], d_.st.omg[0], d_.st.omg[1], d_.st.quat[0],
+                                  d_.st.quat[1], d_.st.active[0], d_.st.active[1], d_.inv_moi, d_.inv_mass,
+                                  d_.owner_scene, d_.owner_iso, d_.lists.cnt[0], d_.lists.cnt[1]};
+            for (const void *p : ptrs)
+                if ((uintptr_t)p % 16 != 0) return false;
+            const int smem = STAGES * StageLayout::bytes;
+            if (cudaFuncSetAttribute(k_integrate_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                    cudaSuccess ||
+                cudaFuncSetAttribute(k_integrate_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            int per_sm = 0;
+            cudaError_t e = m_.clumps
+                                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate_staged<true>, ITILE, smem)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate_staged<false>, ITILE, smem);
+            if (e != cudaSuccess || per_sm < 1) {
+                cudaGetLastError();
+                return false;
+            }
+            staged_per_sm_ = per_sm;
+            return true;
+        }
+    }
+
+    // New detection cells (nothing in flight: called after sync).  The list in use and
+    // the history do not depend on the cells; the next build uses the new ones.
+    dem_status relayout_cells(double f, std::string &err)
+    {
+        HostModel trial = m_;
+        dem_status s;
+        if ((s = layout_cells(trial, f, err))) return s;
+        uint4 *ct = nullptr;
+        if ((s = alloc(ct, (int64_t)trial.n_cells_total + 1, err))) return s;
+        dfree(db_.cell_tab);
+        db_.cell_tab = ct;
+        m_.L = trial.L;
+        m_.vpc = trial.vpc;
+        m_.cell_factor = trial.cell_factor;
+        m_.n_cells_total = trial.n_cells_total;
+        m_.scenes = trial.scenes;
+        if (!F::voxel) {
+            d_.L = (float)m_.L;
+            d_.Ld = m_.L;
+        }
+        d_.invL = 1.0 / m_.L;
+        d_.vpc = m_.vpc;
+        db_.n_cells_total = m_.n_cells_total;
+        db_.key_bits = 1;
+        while (db_.key_bits < 32 && ((uint64_t)1 << db_.key_bits) <= (uint64_t)m_.n_cells_total) ++db_.key_bits;
+        DEM_CU(cudaMemcpy(const_cast<Scene *>(d_.scenes), m_.scenes.data(), m_.scenes.size() * sizeof(Scene),
+                          cudaMemcpyHostToDevice));
         return DEM_OK;
     }
 
@@ -1050,9 +1148,10 @@ private:
                     char k[300];
                     dem_tuning t{};
                     if (std::sscanf(line, "{\"key\": \"%299[^\"]\", \"contact_block\": %d, \"integrate_block\": %d, "
-                                          "\"narrow_block\": %d, \"detect_inline\": %d, \"step_ms\": %lf}",
+                                          "\"narrow_block\": %d, \"detect_inline\": %d, \"cell_factor\": %lf, "
+                                          "\"integrate_staged\": %d, \"contact_lean\": %d, \"step_ms\": %lf}",
                                     k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
-                                    &t.step_ms) == 6 &&
+                                    &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.step_ms) == 9 &&
                         key == k) {
                         best = t;
                         found = true;
@@ -1088,15 +1187,32 @@ private:
             }
             return DEM_OK;
         };
-        // phase 1: contact block and detection placement; phase 2: the other two shapes
+        // phase 1: contact block and detection placement; phase 2: the other two shapes;
+        // phase 3: the detection cell size
+        const double f0 = m_.cell_factor;
         for (int cb : {32, 64, 128})
             for (int di = 0; di <= (delayed ? 1 : 0); ++di)
-                if ((s = trial(dem_tuning{cb, 256, 128, di, 0.0}))) return s;
+                if ((s = trial(dem_tuning{cb, 256, 128, di, 0.0, f0, 0, 0}))) return s;
         const dem_tuning b1 = best;
         for (int ib : {256, 512})
             for (int nb : {128, 256})
                 if (ib != b1.integrate_block || nb != b1.narrow_block)
-                    if ((s = trial(dem_tuning{b1.contact_block, ib, nb, b1.detect_inline, 0.0}))) return s;
+                    if ((s = trial(dem_tuning{b1.contact_block, ib, nb, b1.detect_inline, 0.0, f0, 0, 0}))) return s;
+        if (F::voxel)
+            if ((s = trial(dem_tuning{b1.contact_block, 256, best.narrow_block, b1.detect_inline, 0.0, f0, 1, 0})))
+                return s;
+        {
+            dem_tuning t = best;
+            t.contact_lean = 1;
+            t.step_ms = 0.0;
+            if ((s = trial(t))) return s;
+        }
+        const dem_tuning b2 = best;
+        for (double f : {1.0, 1.5, 2.0})
+            if (f != b2.cell_factor)
+                if ((s = trial(dem_tuning{b2.contact_block, b2.integrate_block, b2.narrow_block, b2.detect_inline,
+                                          0.0, f, b2.integrate_staged, b2.contact_lean})))
+                    return s;
         best.step_ms = best_ms / steps;
         if ((s = set_tuning(&best, err))) return s;
         if ((s = load(blob.data(), blob.size(), err))) return s;
@@ -1106,9 +1222,11 @@ private:
             if (f) {
                 std::fprintf(f,
                              "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
-                             "%d, \"detect_inline\": %d, \"step_ms\": %.6f}\n",
+                             "%d, \"detect_inline\": %d, \"cell_factor\": %.3f, \"integrate_staged\": %d, "
+                             "\"contact_lean\": %d, \"step_ms\": %.6f}\n",
                              key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
-                             best.detect_inline, best.step_ms);
+                             best.detect_inline, best.cell_factor, best.integrate_staged, best.contact_lean,
+                             best.step_ms);
                 std::fclose(f);
             }
         }
@@ -1294,8 +1412,8 @@ private:
 
     void launch_link(cudaStream_t st)
     {
-        k_link<F><<<grid(d_.N, 256), 256, 0, st>>>(d_);
         k_act_reset<F><<<1, 1, 0, st>>>(d_, 0);
+        k_link<F><<<grid(d_.N, 256), 256, 0, st>>>(d_);
         k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, 0, m_.clumps ? 1 : 0);
         k_commit<<<1, 1, 0, st>>>(st_);
     }
@@ -1356,21 +1474,51 @@ private:
             const unsigned cap = (unsigned)contact_per_sm(b) * (unsigned)n_sm_;
             g = std::min(g, std::max(1u, cap));
         }
-        if (m_.clumps) k_contact<F, true, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
-        else k_contact<F, false, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
+        const bool lean = MODE == MODE_STEP && tune_.contact_lean;
+        if (m_.clumps) {
+            if (lean) k_contact<F, true, MODE_STEP, 1><<<g, b, 0, sf_>>>(d_, eF, eT);
+            else k_contact<F, true, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
+        } else {
+            if (lean) k_contact<F, false, MODE_STEP, 1><<<g, b, 0, sf_>>>(d_, eF, eT);
+            else k_contact<F, false, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
+        }
     }
 
     int contact_per_sm(int b)
     {
-        if (b == occ_block_) return occ_per_sm_;
+        const int key = b * 2 + (tune_.contact_lean ? 1 : 0);
+        if (key == occ_block_) return occ_per_sm_;
         int per_sm = 0;
-        cudaError_t e = m_.clumps
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, true, MODE_STEP>, b, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, false, MODE_STEP>, b, 0);
+        cudaError_t e;
+        if (tune_.contact_lean)
+            e = m_.clumps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, true, MODE_STEP, 1>, b, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, false, MODE_STEP, 1>, b, 0);
+        else
+            e = m_.clumps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, true, MODE_STEP>, b, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, false, MODE_STEP>, b, 0);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-        occ_block_ = b;
+        occ_block_ = key;
         occ_per_sm_ = per_sm;
         return per_sm;
+    }
+
+    // Plain: one thread per owner.  Staged (voxel form): a persistent grid of as many
+    // blocks as the SMs hold streams tiles of owners through shared memory.
+    void launch_integrate()
+    {
+        if constexpr (F::voxel) {
+            if (tune_.integrate_staged && d_.M > 0 && staged_per_sm_ > 0) {
+                const int smem = STAGES * StageLayout::bytes;
+                const int64_t ntiles = (d_.M + ITILE - 1) / ITILE;
+                const unsigned g = (unsigned)std::min<int64_t>(ntiles, (int64_t)staged_per_sm_ * n_sm_);
+                if (m_.clumps) k_integrate_staged<true><<<g, ITILE, smem, sf_>>>(d_);
+                else k_integrate_staged<false><<<g, ITILE, smem, sf_>>>(d_);
+                return;
+            }
+        }
+        const int ib = tune_.integrate_block;
+        if (m_.clumps) k_integrate<F, true><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
+        else k_integrate<F, false><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
     }
 
     void force_step()
@@ -1380,9 +1528,7 @@ private:
         launch_force<MODE_STEP>(nullptr, nullptr);
         mark_end(sf_, m);
         mark_begin(P_INTEG, sf_, m2);
-        const int ib = tune_.integrate_block;
-        if (m_.clumps) k_integrate<F, true><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
-        else k_integrate<F, false><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
+        launch_integrate();
         mark_end(sf_, m2);
         k_audit<<<1, 1, 0, sf_>>>(st_);
         if (collect_ && d_.M > 0)
@@ -1447,8 +1593,10 @@ private:
     bool dirty_ = false;
     int64_t fallbacks_ = 0, regrows_ = 0;
     double ms_total_ = 0.0;
-    dem_tuning tune_{64, 256, 128, 0, 0.0};
+    dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0};   // contact_lean last
     int n_sm_ = 1, occ_block_ = 0, occ_per_sm_ = 1;
+    int64_t Mp_ = 0;                // owners rounded up to whole staging tiles
+    int staged_per_sm_ = 0;
     bool act_alloc_ = false;
     bool graphs_on_ = true;
     struct GraphEntry { long long c; cudaGraphExec_t exec; };

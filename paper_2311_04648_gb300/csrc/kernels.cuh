@@ -12,7 +12,10 @@ struct DetectBuffers {
     uint32_t *keys_alt, *vals_alt;
     uint32_t *hist;            // radix histogram / offsets
     int64_t hist_cap;          // entries
-    uint32_t *cell_start, *cell_end;
+    // per cell (start, stamp, end, 0): the sorted run [start, end) of the cell, valid only
+    // when stamp equals the build's stamp (the table is never cleared; one 16-byte load
+    // per cell)
+    uint4 *cell_tab;
     uint32_t n_cells_total;    // sentinel key (inactive / padding slots)
     int key_bits;
     // snapshot of sphere centres in slot order and the same gathered in sorted order
@@ -25,15 +28,28 @@ struct DetectBuffers {
 };
 
 // Two contact lists (ELL rows) plus two history buffers; DevStatus selects which.
+// Tangential history of one list entry as one vector (x, y, z, unused): a scattered
+// entry costs one memory sector to read or write instead of three.
+template <typename R> struct HistVec;
+template <> struct HistVec<float> { using T = float4; };
+template <> struct HistVec<double> { using T = double4_32a; };
+
+// A sphere's constants packed for the scattered loads of the contact kernel (one
+// memory sector): FP32 form (radius, radius low word, material as int bits, 0), FP64
+// form (radius, material).
+template <typename R> struct SphPack;
+template <> struct SphPack<float> { using T = float4; };
+template <> struct SphPack<double> { using T = double2; };
+
 template <typename R>
 struct ListBuffers {
     uint32_t *partner[2];
     uint8_t *mirror[2];
     uint8_t *cnt[2];
-    R *hx[2], *hy[2], *hz[2];
+    typename HistVec<R>::T *hist[2];
     // compacted work of each list: slots with listed partners (single spheres) or
     // 32-slot groups containing any (clumps), and their number
-    uint32_t *act[2];
+    uint4 *act[2];
     uint32_t *n_act[2];
 };
 

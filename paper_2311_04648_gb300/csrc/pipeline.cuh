@@ -2,8 +2,8 @@
 // position form (FormF64 / FormF32).  Included by engine_f64.cu and engine_f32.cu.
 //
 // Per step (arXiv 2311.04648 Sec. 2.1 and Sec. 4):
-//   [rebuild]  k_hash -> radix sort -> k_cellstart -> k_narrow -> k_link -> k_commit
-//   [advance]  k_force (contact forces, per-owner reduction, integration) -> k_audit
+//   [rebuild]  k_hash -> radix sort -> k_cellstart -> k_narrow -> k_link -> k_compact -> k_commit
+//   [advance]  k_contact (contact forces, per-owner sums) -> k_integrate -> k_audit
 // Contact lists are ELL rows: entry k of sphere s at k*Np + s, each row holds every
 // partner of s (both orientations) sorted by partner id, walls (WALL_BIT | id) last.
 // A pair (A, B) with A < B owns its tangential history in A's row; B finds it through
@@ -11,11 +11,27 @@
 // canonical orientation with identical inputs, so the force on B is exactly the negated
 // force on A and no force array or atomic is needed.
 #pragma once
+#include "stage.cuh"
 #include "common.cuh"
 #include "contact.cuh"
 #include "kernels.cuh"
 
 namespace dem {
+
+template <typename H, typename R>
+__device__ __forceinline__ V3<R> hist_get(const H *h, int64_t e)
+{
+    const H v = h[e];
+    return {(R)v.x, (R)v.y, (R)v.z};
+}
+template <typename H, typename R>
+__device__ __forceinline__ void hist_put(H *h, int64_t e, V3<R> u)
+{
+    H v;
+    v.x = u.x; v.y = u.y; v.z = u.z; v.w = 0;
+    h[e] = v;
+}
+
 
 enum : int { MODE_STEP = 0, MODE_EVAL = 1 };
 
@@ -30,6 +46,8 @@ struct Dev {
     int gyro;                       // gyroscopic term on
     int n_scenes;
     int vpc;                        // voxels per cell edge (voxel form)
+    double bin_invL;                // the smallest cells (schedule bins are made of them)
+    int bin_vpc;
     StateBuffers<F> st;
     ListBuffers<R> lists;
     R4 *inv_moi;                    // (1/I1, 1/I2, 1/I3, r_ext)
@@ -41,12 +59,15 @@ struct Dev {
     float *sph_rlo;                 // voxel form: radius minus its FP32 rounding (float-float)
     uint16_t *sph_mat;
     R4 *sph_rloc;                   // body-frame offset (x, y, z, 0); clumps only
+    typename SphPack<R>::T *sph_pack;   // radius, low word, material in one vector
     uint8_t *sph_head;              // first slot of its owner
     uint8_t *sph_segend;            // lane (within the warp) one past the owner's last slot
     int64_t *owner_first;           // first sphere slot of each owner
     uint8_t *owner_nsph;            // spheres of each owner
-    float *acc[2];                  // per owner: accumulated displacement bound since the
-                                    // snapshot of the list in use / the list being built
+    // Per owner, the accumulated displacement bounds since the snapshots of the two lists
+    // (acc[0] and acc[1]; acc[acc_par] belongs to the list in use) ride in the unused
+    // fourth lanes of the velocity (acc[0]) and angular velocity (acc[1]) vectors, so they
+    // are double-buffered with the state and cost no separate memory traffic.
     float *amag;                    // per owner |F|/m of the last step (schedule features)
     R4 *fo, *to;                    // per owner contact force and torque of the step
     const Scene *scenes;
@@ -63,8 +84,8 @@ template <class F>
 __device__ __forceinline__ float3 approx_pos(const typename F::Pos &p, const Scene &sc, float L)
 {
     if constexpr (F::voxel) {
-        return make_float3((float)sc.lo[0] + (float)p.cx * L + p.x, (float)sc.lo[1] + (float)p.cy * L + p.y,
-                           (float)sc.lo[2] + (float)p.cz * L + p.z);
+        return make_float3(sc.lof[0] + (float)p.cx * L + p.x, sc.lof[1] + (float)p.cy * L + p.y,
+                           sc.lof[2] + (float)p.cz * L + p.z);
     } else {
         return make_float3((float)p.x, (float)p.y, (float)p.z);
     }
@@ -89,7 +110,8 @@ __device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint3
 {
     using R = typename F::R;
     SphereK<F> k;
-    uint32_t o = d.sph_owner[s];
+    // a world of single spheres has one slot per owner, in owner order
+    uint32_t o = CLUMPS ? d.sph_owner[s] : s;
     k.owner = o;
     R mass;
     typename F::Pos po = F::load(d.st.pos[sp], o, mass);
@@ -98,9 +120,16 @@ __device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint3
     k.v = {v4.x, v4.y, v4.z};
     k.w = {w4.x, w4.y, w4.z};
     k.mass = mass;
-    k.rad = d.sph_rad[s];
-    k.rlo = F::voxel ? d.sph_rlo[s] : 0.0f;
-    k.mat = d.sph_mat[s];
+    const auto pk = d.sph_pack[s];
+    if constexpr (F::voxel) {
+        k.rad = pk.x;
+        k.rlo = pk.y;
+        k.mat = __float_as_int(pk.z);
+    } else {
+        k.rad = pk.x;
+        k.rlo = 0.0f;
+        k.mat = (int)pk.y;
+    }
     if (CLUMPS) {
         auto q = d.st.quat[sp][o];
         auto r4 = d.sph_rloc[s];
@@ -224,12 +253,18 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
     if (stp->halt) return;
     if (s == 0) {
         stp->disp_next = 0.0;
+        stp->cell_stamp += 1;            // a new cell table (the previous entries go stale)
         stp->beta_next = beta;
+        stp->beta_next_f = (float)beta;
     }
     if (s >= d.N) return;
     const int sp = stp->state_par;
     uint32_t o = d.sph_owner[s];
-    if (o != 0xffffffffu && d.sph_head[s]) d.acc[stp->acc_par ^ 1][o] = 0.0f;
+    if (o != 0xffffffffu && d.sph_head[s]) {
+        // the next list's bound starts at zero (the lane of the state the next step reads)
+        typename F::R4 *lane = (stp->acc_par ^ 1) == 0 ? &d.st.vel[sp][o] : &d.st.omg[sp][o];
+        lane->w = typename F::R(0);
+    }
     uint32_t key = b.n_cells_total;
     if (o != 0xffffffffu && d.st.active[sp][o]) {
         SphereK<F> k = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
@@ -251,8 +286,8 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
     b.vals[s] = (uint32_t)s;
 }
 
-// Cell start/end tables from the sorted keys (no clearing: an entry is valid only if
-// the sorted key at its start equals the cell) and the snapshot gathered in cell order.
+// Cell table from the sorted keys (no clearing: an entry is valid only if it carries this
+// build's stamp) and the snapshot gathered in cell order.
 template <class F>
 __global__ void __launch_bounds__(256) k_cellstart(Dev<F> d, DetectBuffers b, const uint32_t *keys,
                                                     const uint32_t *vals)
@@ -262,9 +297,11 @@ __global__ void __launch_bounds__(256) k_cellstart(Dev<F> d, DetectBuffers b, co
     if (t >= b.n) return;
     uint32_t k = keys[t];
     const uint32_t sent = b.n_cells_total;
+    const uint32_t stamp = d.status->cell_stamp;
     if (k != sent) {
-        if (t == 0 || keys[t - 1] != k) b.cell_start[k] = (uint32_t)t;
-        if (t == b.n - 1 || keys[t + 1] != k) b.cell_end[k] = (uint32_t)(t + 1);
+        // the first entry of a run writes (start, stamp), the last writes end: disjoint words
+        if (t == 0 || keys[t - 1] != k) reinterpret_cast<uint2 *>(&b.cell_tab[k])[0] = make_uint2((uint32_t)t, stamp);
+        if (t == b.n - 1 || keys[t + 1] != k) b.cell_tab[k].z = (uint32_t)(t + 1);
         if (t == b.n - 1 || keys[t + 1] == sent) *b.n_valid = (uint32_t)(t + 1);
     } else if (t == 0) {
         *b.n_valid = 0;
@@ -323,8 +360,10 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nvalid = *b.n_valid;
     if (t >= nvalid) return;
+    const uint32_t stamp = stp->cell_stamp;
     const int ln = stp->list_cur ^ 1;
     const double beta = stp->beta_next;
+    const float betaf = stp->beta_next_f;
     const uint32_t i = vals[t];
     const uint32_t key = keys[t];
     const uint32_t oi = b.sorted_owner[t];
@@ -344,7 +383,7 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
     } else {
         a64 = reinterpret_cast<const double4_32a *>(b.sorted)[t];
     }
-    const float b2f = 2.0f * (float)beta;
+    const float b2f = 2.0f * betaf;
     const double b2d = 2.0 * beta;
 
     uint32_t buf[KMAX];
@@ -359,11 +398,10 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             uint32_t rowbase = sc.cell_base + (uint32_t)((z * ny + y) * nx);
             uint32_t lo = 0xffffffffu, hi = 0;
             for (int x = x0; x <= x1; ++x) {
-                uint32_t c = rowbase + (uint32_t)x;
-                uint32_t st = b.cell_start[c];
-                if (st < nvalid && keys[st] == c) {
-                    if (lo == 0xffffffffu) lo = st;
-                    hi = b.cell_end[c];
+                const uint4 r = b.cell_tab[rowbase + (uint32_t)x];
+                if (r.y == stamp) {
+                    if (lo == 0xffffffffu) lo = r.x;
+                    hi = r.z;
                 }
             }
             if (lo == 0xffffffffu) continue;
@@ -382,30 +420,38 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             }
         }
     }
-    // walls: signed gap below R + beta; FP32 screens first (FP64 throughput is scarce on
-    // this part), the exact FP64 test only for walls that survive them
+    // walls: signed gap below R + beta (FP64).  An FP32 gap decides every wall that is
+    // clear of the threshold by more than its error bound; only the thin band around the
+    // threshold takes the FP64 test (FP64 throughput is scarce on this part)
     if (sc.wall_count > 0) {
+        float Rf;
         double R;
-        float3 pf;
         typename F::Pos pp;
         if constexpr (F::voxel) {
             pp = PosF32{ac.x, ac.y, ac.z, ao.x, ao.y, ao.z};
-            R = (double)ao.w;
+            Rf = ao.w;
         } else {
             pp = PosF64{a64.x, a64.y, a64.z};
-            R = a64.w;
+            Rf = (float)a64.w;
         }
-        pf = approx_pos<F>(pp, sc, d.L);
-        const float reach = (float)R + (float)beta;
-        const float scale = fabsf(pf.x) + fabsf(pf.y) + fabsf(pf.z) + 1.0f;
+        const float3 pf = approx_pos<F>(pp, sc, d.L);
+        const float reach = Rf + betaf;
         bool have64 = false;
         V3<double> pa;
         for (int wi = 0; wi < sc.wall_count; ++wi) {
-            int wg = sc.wall_begin + wi;
+            const int wg = sc.wall_begin + wi;
             const Wall &wl = d.walls[wg];
-            if (wl.type == WALL_PLANE && !plane_may_reach(wl, pf, reach, scale)) continue;
+            const float gf = wall_gap_f(wl, pf);
+            const float tol = wall_gap_tol(wl, pf) + 1e-6f * reach;
+            if (gf > reach + tol) continue;
+            if (gf < reach - tol) {
+                row_insert(buf, n, WALL_BIT | (uint32_t)wg);
+                continue;
+            }
             if (!have64) {
                 pa = F::absolute(pp, sc, d.Ld);
+                if constexpr (F::voxel) R = (double)ao.w;
+                else R = a64.w;
                 have64 = true;
             }
             double gap;
@@ -445,6 +491,8 @@ __global__ void k_act_reset(Dev<F> d, int which)
 {
     const int l = d.status->list_cur ^ (which ? 0 : 1);
     *d.lists.n_act[l] = 0;
+    d.status->list_busy[l] = 0;
+    if (!which) d.status->list_pairs[l] = 0;
 }
 
 // Compact the work of a list: slots with a non-empty row (single spheres) or 32-slot
@@ -458,12 +506,14 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int warp_l
     const int l = stp->list_cur ^ (which ? 0 : 1);
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const bool busy = s < d.N && d.lists.cnt[l][s] > 0;
+    const int nrow = s < d.N ? d.lists.cnt[l][s] : 0;
+    const bool busy = nrow > 0;
     const unsigned int ball = __ballot_sync(0xffffffffu, busy);
+    if (lane == 0 && ball) atomicAdd(&stp->list_busy[l], (unsigned int)__popc(ball));
     if (warp_level) {
         if (lane == 0 && ball) {
             unsigned int pos = atomicAdd(d.lists.n_act[l], 1u);
-            d.lists.act[l][pos] = (uint32_t)(s >> 5);
+            d.lists.act[l][pos] = make_uint4((uint32_t)(s >> 5), 0u, 0u, 0u);
         }
         // owners never span two groups: an idle group's owners get no contact force for as
         // long as this list is in use, and the steps of the previous list are done
@@ -479,7 +529,14 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int warp_l
         unsigned int base = 0;
         if (lane == 0 && ball) base = atomicAdd(d.lists.n_act[l], (unsigned int)__popc(ball));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (busy) d.lists.act[l][base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)s;
+        if (busy) {
+            // the first partner and its mirror index travel with the entry: the contact
+            // kernel starts on that pair without waiting for the row
+            const uint32_t j0 = d.lists.partner[l][s];
+            const uint32_t m0 = d.lists.mirror[l][s];
+            d.lists.act[l][base + __popc(ball & ((1u << lane) - 1u))] =
+                make_uint4((uint32_t)s, (uint32_t)nrow, j0, m0);
+        }
     }
 }
 
@@ -493,33 +550,30 @@ __global__ void __launch_bounds__(256) k_link(Dev<F> d)
     DevStatus *stp = d.status;
     if (stp->halt) return;
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.N) return;
+    const bool live = s < d.N;               // every lane stays for the warp sum below
     const int lo = stp->list_cur, ln = lo ^ 1;
     const int hs = stp->hist_par, hd = hs ^ 1;
     const uint32_t *pn = d.lists.partner[ln];
     const uint32_t *po = d.lists.partner[lo];
-    const int n = d.lists.cnt[ln][s];
-    const int nold = d.lists.cnt[lo][s];
+    const int n = live ? d.lists.cnt[ln][s] : 0;
+    const int nold = live ? d.lists.cnt[lo][s] : 0;
+    unsigned int owned = 0;                  // pairs this slot owns (partner id above its own)
     for (int k = 0; k < n; ++k) {
         int64_t e = (int64_t)k * d.Np + s;
         uint32_t j = pn[e];
+        if (!(j & WALL_BIT) && j > (uint32_t)s) ++owned;
         if (!(j & WALL_BIT) && j < (uint32_t)s) {
             int m = row_find(pn, d.Np, j, d.lists.cnt[ln][j], (uint32_t)s);
             d.lists.mirror[ln][e] = (uint8_t)(m < 0 ? 0 : m);
         } else {
             int ko = row_find(po, d.Np, s, nold, j);
-            R x = R(0), y = R(0), z = R(0);
-            if (ko >= 0) {
-                int64_t eo = (int64_t)ko * d.Np + s;
-                x = d.lists.hx[hs][eo];
-                y = d.lists.hy[hs][eo];
-                z = d.lists.hz[hs][eo];
-            }
-            d.lists.hx[hd][e] = x;
-            d.lists.hy[hd][e] = y;
-            d.lists.hz[hd][e] = z;
+            V3<R> u = {R(0), R(0), R(0)};
+            if (ko >= 0) u = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hs], (int64_t)ko * d.Np + s);
+            hist_put(d.lists.hist[hd], e, u);
         }
     }
+    const unsigned int tot = __reduce_add_sync(0xffffffffu, owned);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&stp->list_pairs[ln], tot);
 }
 
 // Switch to the new list (single thread, after k_link).
@@ -538,17 +592,63 @@ static __global__ void k_commit(DevStatus *stp)
 // ------------------------------------------------------------------ force + integration
 
 // Quaternion increment for a rotation vector th (angle |th|): (cos(|th|/2), sin(|th|/2) th/|th|).
+// Integration arithmetic with every product and sum rounded on its own (no fused
+// multiply-add): the same update compiled into different kernels (plain and staged
+// loads) gives the same bits, and the order is that of the written formulas.
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+template <typename R> __device__ __forceinline__ V3<R> vadd_rn(V3<R> a, V3<R> b)
+{
+    return {radd(a.x, b.x), radd(a.y, b.y), radd(a.z, b.z)};
+}
+template <typename R> __device__ __forceinline__ V3<R> vscale_rn(R k, V3<R> a)
+{
+    return {rmul(k, a.x), rmul(k, a.y), rmul(k, a.z)};
+}
+template <typename R> __device__ __forceinline__ R dot_rn(V3<R> a, V3<R> b)
+{
+    return radd(radd(rmul(a.x, b.x), rmul(a.y, b.y)), rmul(a.z, b.z));
+}
+template <typename R> __device__ __forceinline__ V3<R> cross_rn(V3<R> a, V3<R> b)
+{
+    return {rsub(rmul(a.y, b.z), rmul(a.z, b.y)), rsub(rmul(a.z, b.x), rmul(a.x, b.z)),
+            rsub(rmul(a.x, b.y), rmul(a.y, b.x))};
+}
+template <typename R> __device__ __forceinline__ void quat_mat_rn(R qw, R qx, R qy, R qz, R m[9])
+{
+    const R one = R(1), two = R(2);
+    R xx = rmul(qx, qx), yy = rmul(qy, qy), zz = rmul(qz, qz);
+    R xy = rmul(qx, qy), xz = rmul(qx, qz), yz = rmul(qy, qz);
+    R wx = rmul(qw, qx), wy = rmul(qw, qy), wz = rmul(qw, qz);
+    m[0] = rsub(one, rmul(two, radd(yy, zz))); m[1] = rmul(two, rsub(xy, wz)); m[2] = rmul(two, radd(xz, wy));
+    m[3] = rmul(two, radd(xy, wz)); m[4] = rsub(one, rmul(two, radd(xx, zz))); m[5] = rmul(two, rsub(yz, wx));
+    m[6] = rmul(two, rsub(xz, wy)); m[7] = rmul(two, radd(yz, wx)); m[8] = rsub(one, rmul(two, radd(xx, yy)));
+}
+template <typename R> __device__ __forceinline__ V3<R> mat_vec_rn(const R m[9], V3<R> a)
+{
+    return {radd(radd(rmul(m[0], a.x), rmul(m[1], a.y)), rmul(m[2], a.z)),
+            radd(radd(rmul(m[3], a.x), rmul(m[4], a.y)), rmul(m[5], a.z)),
+            radd(radd(rmul(m[6], a.x), rmul(m[7], a.y)), rmul(m[8], a.z))};
+}
+template <typename R> __device__ __forceinline__ V3<R> mat_tvec_rn(const R m[9], V3<R> a)
+{
+    return {radd(radd(rmul(m[0], a.x), rmul(m[3], a.y)), rmul(m[6], a.z)),
+            radd(radd(rmul(m[1], a.x), rmul(m[4], a.y)), rmul(m[7], a.z)),
+            radd(radd(rmul(m[2], a.x), rmul(m[5], a.y)), rmul(m[8], a.z))};
+}
+
+// Rotation increment [cos(h|w|/2), sin(h|w|/2) w/|w|] of angular velocity w over h.
 template <typename R>
 __device__ __forceinline__ void quat_increment(V3<R> w, R h, R &dw, R &dx, R &dy, R &dz)
 {
-    R wn = sqrt(dot(w, w));
+    R wn = sqrt(dot_rn(w, w));
     if (wn >= R(1e-30)) {
-        R half = R(0.5) * h * wn;
-        R sn = sin(half) / wn;
+        R half = rmul(rmul(R(0.5), h), wn);
+        R sn = rdiv(sin(half), wn);
         dw = cos(half);
-        dx = sn * w.x;
-        dy = sn * w.y;
-        dz = sn * w.z;
+        dx = rmul(sn, w.x);
+        dy = rmul(sn, w.y);
+        dz = rmul(sn, w.z);
     } else {
         dw = R(1); dx = R(0); dy = R(0); dz = R(0);
     }
@@ -557,10 +657,10 @@ __device__ __forceinline__ void quat_increment(V3<R> w, R h, R &dw, R &dx, R &dy
 template <typename R>
 __device__ __forceinline__ void quat_mul(R aw, R ax, R ay, R az, R bw, R bx, R by, R bz, R &w, R &x, R &y, R &z)
 {
-    w = ((aw * bw - ax * bx) - ay * by) - az * bz;
-    x = ((aw * bx + ax * bw) + ay * bz) - az * by;
-    y = ((aw * by - ax * bz) + ay * bw) + az * bx;
-    z = ((aw * bz + ax * by) - ay * bx) + az * bw;
+    w = rsub(rsub(rsub(rmul(aw, bw), rmul(ax, bx)), rmul(ay, by)), rmul(az, bz));
+    x = rsub(radd(radd(rmul(aw, bx), rmul(ax, bw)), rmul(ay, bz)), rmul(az, by));
+    y = radd(radd(rsub(rmul(aw, by), rmul(ax, bz)), rmul(ay, bw)), rmul(az, bx));
+    z = radd(rsub(radd(rmul(aw, bz), rmul(ax, by)), rmul(ay, bx)), rmul(az, bw));
 }
 
 // Contact forces of every listed pair of slot s and the per-owner sums (segmented warp
@@ -572,8 +672,8 @@ constexpr int CONTACT_BLOCK_MAX = 128;   // launch shapes are tuned at run time 
 constexpr int INTEGRATE_BLOCK_MAX = 512;
 
 template <class F, bool CLUMPS, int MODE>
-__device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int sp, int hp, int lc, double *eval_F,
-                                             double *eval_T)
+__device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_known, uint32_t j0_known,
+                                             uint32_t m0_known, int sp, int hp, int lc, double *eval_F, double *eval_T)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
@@ -582,7 +682,8 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int sp,
     // a world of single spheres has one slot per owner, in owner order
     uint32_t o = live ? (CLUMPS ? d.sph_owner[s] : (uint32_t)s) : 0xffffffffu;
     live = live && o != 0xffffffffu;
-    const int n = live ? d.lists.cnt[lc][s] : 0;
+    // the row length comes with the compacted work where it is known
+    const int n = !live ? 0 : (n_known >= 0 ? n_known : (int)d.lists.cnt[lc][s]);
     bool act = live && d.st.active[sp][o];
     if (!CLUMPS && MODE == MODE_STEP && (!act || n == 0)) return;
 
@@ -598,15 +699,19 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int sp,
         const R h = F::voxel ? (R)sc.hf : (R)sc.h;
         const uint32_t *prow = d.lists.partner[lc];
         const uint8_t *mrow = d.lists.mirror[lc];
-        const R *hxi = d.lists.hx[hp], *hyi = d.lists.hy[hp], *hzi = d.lists.hz[hp];
-        R *hxo = d.lists.hx[hp ^ 1], *hyo = d.lists.hy[hp ^ 1], *hzo = d.lists.hz[hp ^ 1];
+        using H = typename HistVec<R>::T;
+        const H *hin = d.lists.hist[hp];
+        H *hout = d.lists.hist[hp ^ 1];
+        const V3<R> zero = {R(0), R(0), R(0)};
+        uint32_t j_next = n_known >= 0 ? j0_known : (n > 0 ? prow[s] : 0u);
         for (int k = 0; k < n; ++k) {
             const int64_t e = (int64_t)k * d.Np + s;
-            const uint32_t j = prow[e];
+            const uint32_t j = j_next;
+            if (k + 1 < n) j_next = prow[e + d.Np];      // next partner's id in flight early
             ContactIn<R> c;
             V3<R> armA, armB;
             if (j & WALL_BIT) {
-                V3<R> ut = {hxi[e], hyi[e], hzi[e]};
+                V3<R> ut = hist_get<H, R>(hin, e);
                 V3<R> Fc;
                 bool on = wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA);
                 if (on) {
@@ -614,23 +719,20 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int sp,
                     Fs = Fs + Fc;
                     Ts = Ts + cross(armA, Fc);
                 }
-                if (MODE == MODE_STEP) {
-                    hxo[e] = on ? ut.x : R(0);
-                    hyo[e] = on ? ut.y : R(0);
-                    hzo[e] = on ? ut.z : R(0);
-                }
+                if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
                 continue;
             }
             SphereK<F> other = load_sphere<F, CLUMPS>(d, sp, j);
             const bool mine = (uint32_t)s < j;     // this slot owns the pair (A = lower id)
             if (!d.st.active[sp][other.owner]) {
-                if (MODE == MODE_STEP && mine) { hxo[e] = R(0); hyo[e] = R(0); hzo[e] = R(0); }
+                if (MODE == MODE_STEP && mine) hist_put(hout, e, zero);
                 continue;
             }
             // the pair is evaluated in this thread's own orientation; the history is
             // stored in the owner's orientation, so the other side negates it
-            const int64_t slot = mine ? e : (int64_t)mrow[e] * d.Np + j;
-            V3<R> ut = {hxi[slot], hyi[slot], hzi[slot]};
+            const uint32_t mk = (k == 0 && n_known >= 0) ? m0_known : (uint32_t)mrow[e];
+            const int64_t slot = mine ? e : (int64_t)mk * d.Np + j;
+            V3<R> ut = hist_get<H, R>(hin, slot);
             if (!mine) ut = -ut;
             V3<R> Fc;
             bool on = sphere_contact<F>(d, me, other, c, armA, armB);
@@ -639,11 +741,7 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int sp,
                 Fs = Fs + Fc;
                 Ts = Ts + cross(armA, Fc);
             }
-            if (MODE == MODE_STEP && mine) {
-                hxo[e] = on ? ut.x : R(0);
-                hyo[e] = on ? ut.y : R(0);
-                hzo[e] = on ? ut.z : R(0);
-            }
+            if (MODE == MODE_STEP && mine) hist_put(hout, e, on ? ut : zero);
         }
     }
     if (CLUMPS) {
@@ -680,54 +778,94 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int sp,
 // MODE_STEP: persistent grid-stride loop over the compacted work of the list in use
 // (every thread busy, whichever fraction of the spheres has listed partners); for clumps
 // a whole warp takes a 32-slot group.  MODE_EVAL: one thread per slot over all slots.
-template <class F, bool CLUMPS, int MODE>
-__global__ void __launch_bounds__(CONTACT_BLOCK_MAX, 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
+// LEAN = 1 compiles the kernel for 6 resident blocks of CONTACT_BLOCK_MAX threads per SM
+// (fewer registers, some spilled to the L1-cached local memory) instead of 4: more
+// warps to hide the latency of the gathers, chosen by the autotuner where it pays.
+template <class F, bool CLUMPS, int MODE, int LEAN = 0>
+__global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 6 : 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
 {
     DevStatus *stp = d.status;
     if (MODE == MODE_STEP && (stp->halt || stp->list_stale)) return;
     const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
     if (MODE == MODE_EVAL) {
-        contact_slot<F, CLUMPS, MODE>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, sp, hp, lc, eval_F, eval_T);
+        contact_slot<F, CLUMPS, MODE>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, -1, 0u, 0u, sp, hp, lc,
+                                      eval_F, eval_T);
         return;
     }
     // the counter never exceeds the slots (or 32-slot groups); the clamp keeps every
     // index in bounds whatever the counter holds
     const int64_t cap = CLUMPS ? (d.Np >> 5) : d.Np;
     const int64_t nw = min((int64_t)*d.lists.n_act[lc], cap);
-    const uint32_t *act = d.lists.act[lc];
+    const uint4 *act = d.lists.act[lc];
     if (CLUMPS) {
         const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
         for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps)
-            contact_slot<F, CLUMPS, MODE>(d, ((int64_t)act[w] << 5) + (threadIdx.x & 31), sp, hp, lc, eval_F, eval_T);
+            contact_slot<F, CLUMPS, MODE>(d, ((int64_t)act[w].x << 5) + (threadIdx.x & 31), -1, 0u, 0u, sp, hp, lc,
+                                          eval_F, eval_T);
     } else {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += stride)
-            contact_slot<F, CLUMPS, MODE>(d, (int64_t)act[t], sp, hp, lc, eval_F, eval_T);
+        {
+            const uint4 a = act[t];
+            contact_slot<F, CLUMPS, MODE>(d, (int64_t)a.x, (int)a.y, a.z, a.w, sp, hp, lc, eval_F, eval_T);
+        }
     }
 }
 
-// Semi-implicit Euler update of each owner (one thread per owner, streaming): v with the
-// contact force plus gravity, then the body-frame angular velocity (Euler's equations,
-// gyroscopic term switchable), then x with the new v, then the quaternion with the new
-// angular velocity; removal by the sink; the per-owner displacement bounds of the audit.
+// Warp max of the displacement bounds and the speed (non-negative floats order like
+// their bit patterns), one atomic per warp into one of 64 slots: no block barrier,
+// little contention; k_audit reduces the slots.
+__device__ __forceinline__ void audit_slots(DevStatus *stp, int64_t o, int lane, float disp, float disp2, float speed)
+{
+    unsigned int db = __reduce_max_sync(0xffffffffu, __float_as_uint(disp));
+    unsigned int db2 = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
+    unsigned int vb = __reduce_max_sync(0xffffffffu, __float_as_uint(speed));
+    if (lane == 0) {
+        const int slot = (int)((o >> 5) & 63);
+        if (db) atomicMax(&stp->disp_slots[slot], db);
+        if (db2) atomicMax(&stp->disp2_slots[slot], db2);
+        if (vb) atomicMax(&stp->vmax_slots[slot], vb);
+    }
+}
+
+// Where the per-owner inputs of the integration are read: the state arrays in global
+// memory (index = owner) or a tile of them staged in shared memory (index = position in
+// the tile).  Both paths run the same arithmetic (integrate_owner).
+template <class F>
+struct OwnerSrc {
+    typename F::PosStore pos;
+    const typename F::R4 *vel, *omg, *quat, *inv_moi;
+    const typename F::R *inv_mass;
+    const uint8_t *active, *cnt, *iso;
+    const uint16_t *scene;
+};
+
+// Semi-implicit Euler update of one owner: v with the contact force plus gravity, then
+// the body-frame angular velocity (Euler's equations, gyroscopic term switchable), then x
+// with the new v, then the quaternion with the new angular velocity; removal by the sink;
+// the per-owner displacement bounds of the audit.  Outputs go to the other state buffer.
 template <class F, bool CLUMPS>
-__global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
+__device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp, int64_t o, const OwnerSrc<F> &src,
+                                                int64_t i, int sp, float &disp, float &disp2, float &speed)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
-    DevStatus *stp = d.status;
-    if (stp->halt || stp->list_stale) return;
-    const int sp = stp->state_par, lc = stp->list_cur;
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
-    if (o < d.M) {
-        const bool act = d.st.active[sp][o];
-        const bool has = CLUMPS ? true : d.lists.cnt[lc][o] > 0;
+    {
+        // every load of this owner is issued before the first one is used: the thread
+        // waits for one memory round trip, not a chain of them
+        const bool act = src.active[i];
+        const bool has = CLUMPS ? true : src.cnt[i] > 0;
         R mass;
-        const typename F::Pos po = F::load(d.st.pos[sp], o, mass);
-        const R4 v4 = d.st.vel[sp][o], w4 = d.st.omg[sp][o], q4 = d.st.quat[sp][o];
-        const Scene &sc = d.scenes[d.owner_scene[o]];
+        const typename F::Pos po = F::load(src.pos, i, mass);
+        const R4 v4 = src.vel[i], w4 = src.omg[i], q4 = src.quat[i];
+        const R im = src.inv_mass[i];
+        const R4 ii = src.inv_moi[i];
+        const bool iso = CLUMPS ? (bool)src.iso[i] : true;     // a single sphere is isotropic
+        const int ap = stp->acc_par;
+        const float acc0 = (float)v4.w, acc1 = (float)w4.w;      // acc[0], acc[1]
+        const float acc_a = ap == 0 ? acc0 : acc1, acc_b = ap == 0 ? acc1 : acc0;
+        float a0 = acc_a, a1 = acc_b;
+        const Scene &sc = d.scenes[d.n_scenes > 1 ? src.scene[i] : 0];
         const int so = sp ^ 1;
         V3<R> vn = {v4.x, v4.y, v4.z}, wn = {w4.x, w4.y, w4.z};
         R qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
@@ -743,88 +881,207 @@ __global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
                 Fs = {f4.x, f4.y, f4.z};
                 Ts = {t4.x, t4.y, t4.z};
             }
-            const R im = d.inv_mass[o];
-            const R4 ii = d.inv_moi[o];
-            const V3<R> Ft = Fs + mass * g;
-            vn = vn + h * (im * Ft);
+            const V3<R> Ft = vadd_rn(Fs, vscale_rn(mass, g));
+            vn = vadd_rn(vn, vscale_rn(h, vscale_rn(im, Ft)));
             R nw, nx, ny, nz;
-            if (d.owner_iso[o]) {
+            if (iso) {
                 // isotropic inertia: the body-frame update equals a world-frame one
-                wn = wn + h * (ii.x * Ts);
+                wn = vadd_rn(wn, vscale_rn(h, vscale_rn(ii.x, Ts)));
                 R dw, dx, dy, dz;
                 quat_increment<R>(wn, h, dw, dx, dy, dz);
                 quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
             } else {
                 R m[9];
-                quat_mat<R>(qw, qx, qy, qz, m);
-                V3<R> wb = mat_tvec<R>(m, wn);
-                V3<R> Tb = mat_tvec<R>(m, Ts);
+                quat_mat_rn<R>(qw, qx, qy, qz, m);
+                V3<R> wb = mat_tvec_rn<R>(m, wn);
+                V3<R> Tb = mat_tvec_rn<R>(m, Ts);
                 V3<R> gyro = {R(0), R(0), R(0)};
                 if (d.gyro) {
-                    V3<R> Iw = {wb.x / ii.x, wb.y / ii.y, wb.z / ii.z};
-                    gyro = cross(wb, Iw);
+                    V3<R> Iw = {rdiv(wb.x, ii.x), rdiv(wb.y, ii.y), rdiv(wb.z, ii.z)};
+                    gyro = cross_rn(wb, Iw);
                 }
-                V3<R> dwb = {ii.x * (Tb.x - gyro.x), ii.y * (Tb.y - gyro.y), ii.z * (Tb.z - gyro.z)};
-                wb = wb + h * dwb;
+                V3<R> dwb = {rmul(ii.x, rsub(Tb.x, gyro.x)), rmul(ii.y, rsub(Tb.y, gyro.y)),
+                             rmul(ii.z, rsub(Tb.z, gyro.z))};
+                wb = vadd_rn(wb, vscale_rn(h, dwb));
                 R dw, dx, dy, dz;
                 quat_increment<R>(wb, h, dw, dx, dy, dz);
                 quat_mul<R>(qw, qx, qy, qz, dw, dx, dy, dz, nw, nx, ny, nz);
-                R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
+                R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
                 R m2[9];
-                quat_mat<R>(nw / qn, nx / qn, ny / qn, nz / qn, m2);
-                wn = mat_vec<R>(m2, wb);
+                quat_mat_rn<R>(rdiv(nw, qn), rdiv(nx, qn), rdiv(ny, qn), rdiv(nz, qn), m2);
+                wn = mat_vec_rn<R>(m2, wb);
             }
-            R qn = sqrt(((nw * nw + nx * nx) + ny * ny) + nz * nz);
-            qw = nw / qn; qx = nx / qn; qy = ny / qn; qz = nz / qn;
-            pn = F::advance(po, h * vn, d.L);
+            R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
+            qw = rdiv(nw, qn); qx = rdiv(nx, qn); qy = rdiv(ny, qn); qz = rdiv(nz, qn);
+            pn = F::advance(po, vscale_rn(h, vn), d.L);
             if (sc.has_sink) {
                 V3<double> pa = F::absolute(pn, sc, d.Ld);
-                double side = (pa.x - sc.sink_p[0]) * sc.sink_n[0] + (pa.y - sc.sink_p[1]) * sc.sink_n[1] +
-                              (pa.z - sc.sink_p[2]) * sc.sink_n[2];
+                double side = radd(radd(rmul(rsub(pa.x, sc.sink_p[0]), sc.sink_n[0]),
+                                        rmul(rsub(pa.y, sc.sink_p[1]), sc.sink_n[1])),
+                                   rmul(rsub(pa.z, sc.sink_p[2]), sc.sink_n[2]));
                 if (side < 0.0) {
                     active_out = 0;
                     vn = {R(0), R(0), R(0)};
                     wn = {R(0), R(0), R(0)};
                 }
             }
-            R sv = sqrt(dot(vn, vn));
-            R sw = sqrt(dot(wn, wn));
+            R sv = sqrt(dot_rn(vn, vn));
+            R sw = sqrt(dot_rn(wn, wn));
             speed = (float)sv;
             // displacement bound of this step (centre moves h|v|, a component centre at
             // most h|w| r_ext more) plus the rounding slack of the position update,
             // accumulated per owner since each list's snapshot
-            const float step_d = (float)(h * (sv + sw * ii.w)) * 1.0000005f + (float)stp->disp_slack;
-            const int ap = stp->acc_par;
-            const float a0 = d.acc[ap][o] + step_d;
-            const float a1 = d.acc[ap ^ 1][o] + step_d;
-            d.acc[ap][o] = a0;
-            d.acc[ap ^ 1][o] = a1;
+            const float step_d = radd(rmul((float)rmul(h, radd(sv, rmul(sw, ii.w))), 1.0000005f), stp->disp_slack_f);
+            a0 = acc_a + step_d;
+            a1 = acc_b + step_d;
             disp = a0;
             disp2 = a1;
-            if (d.amag) d.amag[o] = (float)(sqrt(dot(Ft, Ft)) * im);
-            if (sc.v_err > 0.0 && !((double)sv <= sc.v_err)) atomicOr(&stp->diverged, 1);
+            if (d.amag) d.amag[o] = (float)rmul(sqrt(dot_rn(Ft, Ft)), im);
+            if constexpr (F::voxel) {
+                if (sc.v_errf > 0.0f && !(sv <= sc.v_errf)) atomicOr(&stp->diverged, 1);
+            } else {
+                if (sc.v_err > 0.0 && !((double)sv <= sc.v_err)) atomicOr(&stp->diverged, 1);
+            }
             if (!(sv == sv) || !(sw == sw)) atomicOr(&stp->diverged, 1);
         } else {
             vn = {R(0), R(0), R(0)};
             wn = {R(0), R(0), R(0)};
         }
-        F::store(d.st.pos[so], o, pn, mass);
-        d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, R(0)};
-        d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, R(0)};
+        typename F::PosStore pos_out = d.st.pos[so];
+        F::store(pos_out, o, pn, mass);
+        d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, (R)(ap == 0 ? a0 : a1)};
+        d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, (R)(ap == 0 ? a1 : a0)};
         d.st.quat[so][o] = R4{qw, qx, qy, qz};
         d.st.active[so][o] = active_out;
     }
-    // warp max of the displacement bounds and the speed (non-negative floats order like
-    // their bit patterns), one atomic per warp into one of 64 slots: no block barrier,
-    // little contention; k_audit reduces the slots
-    unsigned int db = __reduce_max_sync(0xffffffffu, __float_as_uint(disp));
-    unsigned int db2 = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
-    unsigned int vb = __reduce_max_sync(0xffffffffu, __float_as_uint(speed));
-    if (lane == 0) {
-        const int slot = (int)((o >> 5) & 63);
-        if (db) atomicMax(&stp->disp_slots[slot], db);
-        if (db2) atomicMax(&stp->disp2_slots[slot], db2);
-        if (vb) atomicMax(&stp->vmax_slots[slot], vb);
+}
+
+// One thread per owner, reading its inputs straight from the state arrays.
+template <class F, bool CLUMPS>
+__global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
+{
+    DevStatus *stp = d.status;
+    if (stp->halt || stp->list_stale) return;
+    const int sp = stp->state_par, lc = stp->list_cur;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
+    if (o < d.M) {
+        OwnerSrc<F> src{d.st.pos[sp], d.st.vel[sp], d.st.omg[sp], d.st.quat[sp], d.inv_moi, d.inv_mass,
+                        d.st.active[sp], d.lists.cnt[lc], d.owner_iso, d.owner_scene};
+        integrate_owner<F, CLUMPS>(d, stp, o, src, o, sp, disp, disp2, speed);
+    }
+    audit_slots(stp, o, lane, disp, disp2, speed);
+}
+
+// ------------------------------------------------------------------ staged integration
+// The same update with the inputs streamed through shared memory: a persistent block
+// walks tiles of ITILE owners; one thread issues bulk asynchronous copies (TMA) of a
+// whole tile of every input array, completed on an mbarrier, two tiles ahead, so all of
+// a tile's bytes are in flight at once while the previous tile is computed.  Voxel form
+// only (its arrays are 16-byte vectors or packed scalars; owner arrays are allocated in
+// whole tiles so every copy is a full, 16-byte-aligned tile).
+constexpr int ITILE = 256;
+struct StageLayout {                                        // byte offsets within a stage
+    static constexpr int vox = 0;                           // u64 voxel index
+    static constexpr int om = vox + 8 * ITILE;              // float4 offset, mass
+    static constexpr int vel = om + 16 * ITILE;             // float4 v, acc[0]
+    static constexpr int omg = vel + 16 * ITILE;            // float4 w, acc[1]
+    static constexpr int quat = omg + 16 * ITILE;           // float4 q
+    static constexpr int moi = quat + 16 * ITILE;           // float4 1/I, r_ext
+    static constexpr int imass = moi + 16 * ITILE;          // float 1/m
+    static constexpr int active = imass + 4 * ITILE;        // u8
+    static constexpr int flags = active + ITILE;            // u8 row length (spheres) / isotropy (clumps)
+    static constexpr int scene = flags + ITILE;             // u16 scene (several scenes only)
+    static constexpr int bytes = scene + 2 * ITILE;
+};
+constexpr int STAGES = 2;
+constexpr uint64_t STAGE_WAIT_NS = 1000000000ull;           // a copy later than this is a fault
+
+template <bool CLUMPS>
+__global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
+{
+    using F = FormF32;
+    extern __shared__ __align__(128) unsigned char stage_mem[];
+    __shared__ uint64_t bar[STAGES];
+    __shared__ int skip;
+    DevStatus *stp = d.status;
+    // one reading of the flags for the whole block: its threads leave together or not at all
+    if (threadIdx.x == 0) skip = (stp->halt || stp->list_stale) ? 1 : 0;
+    __syncthreads();
+    if (skip) return;
+    const int sp = stp->state_par, lc = stp->list_cur;
+    const int64_t ntiles = (d.M + ITILE - 1) / ITILE;
+    const bool scenes = d.n_scenes > 1;
+    const uint32_t tile_bytes = (uint32_t)(StageLayout::scene + (scenes ? 2 * ITILE : 0));
+    const int lane = threadIdx.x & 31;
+    const uint64_t deadline = global_ns() + STAGE_WAIT_NS;
+
+    auto issue = [&](int64_t tile, int st) {
+        unsigned char *b = stage_mem + st * StageLayout::bytes;
+        const int64_t o0 = tile * ITILE;
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(&bar[st], tile_bytes);
+        bulk_g2s(b + StageLayout::vox, d.st.pos[sp].vox + o0, 8 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::om, d.st.pos[sp].om + o0, 16 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::vel, d.st.vel[sp] + o0, 16 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::omg, d.st.omg[sp] + o0, 16 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::quat, d.st.quat[sp] + o0, 16 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::moi, d.inv_moi + o0, 16 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::imass, d.inv_mass + o0, 4 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::active, d.st.active[sp] + o0, ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::flags, CLUMPS ? (const void *)(d.owner_iso + o0) : (const void *)(d.lists.cnt[lc] + o0),
+                 ITILE, &bar[st]);
+        if (scenes) bulk_g2s(b + StageLayout::scene, d.owner_scene + o0, 2 * ITILE, &bar[st]);
+    };
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) mbar_init(&bar[st], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st)
+            if (blockIdx.x + (int64_t)st * gridDim.x < ntiles) issue(blockIdx.x + (int64_t)st * gridDim.x, st);
+    }
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int st = k % STAGES;
+        const bool ok = mbar_wait(&bar[st], (uint32_t)((k / STAGES) & 1), deadline);
+        if (__syncthreads_or(!ok)) {
+            // a tile did not arrive in time: report it, let the copies still in flight
+            // land (bounded again) so that none writes into a finished block, and leave
+            if (threadIdx.x == 0) {
+                atomicCAS(&stp->halt, HALT_NONE, HALT_TIMEOUT);
+                const uint64_t late = global_ns() + STAGE_WAIT_NS;
+                for (int q = 0; q < STAGES; ++q) {
+                    const int64_t t = tile + (int64_t)q * gridDim.x;
+                    if (t < ntiles) mbar_wait(&bar[(k + q) % STAGES], (uint32_t)(((k + q) / STAGES) & 1), late);
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        unsigned char *b = stage_mem + st * StageLayout::bytes;
+        const int64_t o = tile * ITILE + threadIdx.x;
+        float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
+        if (o < d.M) {
+            const uint8_t *flags = b + StageLayout::flags;
+            OwnerSrc<F> src{F::PosStore{reinterpret_cast<uint64_t *>(b + StageLayout::vox),
+                                        reinterpret_cast<float4 *>(b + StageLayout::om)},
+                            reinterpret_cast<const float4 *>(b + StageLayout::vel),
+                            reinterpret_cast<const float4 *>(b + StageLayout::omg),
+                            reinterpret_cast<const float4 *>(b + StageLayout::quat),
+                            reinterpret_cast<const float4 *>(b + StageLayout::moi),
+                            reinterpret_cast<const float *>(b + StageLayout::imass),
+                            b + StageLayout::active, flags, flags,
+                            reinterpret_cast<const uint16_t *>(b + StageLayout::scene)};
+            integrate_owner<F, CLUMPS>(d, stp, o, src, threadIdx.x, sp, disp, disp2, speed);
+        }
+        audit_slots(stp, o, lane, disp, disp2, speed);
+        __syncthreads();                          // every thread has read this stage
+        const int64_t next = tile + (int64_t)STAGES * gridDim.x;
+        if (threadIdx.x == 0 && next < ntiles) issue(next, st);
     }
 }
 
@@ -854,6 +1111,8 @@ static __global__ void k_audit(DevStatus *stp)
         return;
     }
     stp->steps_done += 1;
+    stp->pair_steps += stp->list_pairs[stp->list_cur];
+    stp->busy_steps += stp->list_busy[stp->list_cur];
     stp->state_par ^= 1;
     stp->hist_par ^= 1;
     // largest per-owner accumulated bound of each list (owners accumulate on their own)
@@ -868,17 +1127,18 @@ static __global__ void k_audit(DevStatus *stp)
 
 // ------------------------------------------------------------------ learned schedule
 
-// Bin of an owner: its centre of mass's cell divided by BIN_CELLS per axis.
+// Bin of an owner: its centre of mass's cell of the smallest size divided by BIN_CELLS
+// per axis (independent of the detection cell size).
 template <class F>
 __device__ __forceinline__ int owner_bin(const Dev<F> &d, int sp, int64_t o, const Scene &sc)
 {
     typename F::R mass;
     typename F::Pos p = F::load(d.st.pos[sp], o, mass);
     int cx, cy, cz;
-    F::cell(p, sc, d.invL, d.vpc, cx, cy, cz);
-    cx = min(max(cx, 0), sc.nc[0] - 1) / BIN_CELLS;
-    cy = min(max(cy, 0), sc.nc[1] - 1) / BIN_CELLS;
-    cz = min(max(cz, 0), sc.nc[2] - 1) / BIN_CELLS;
+    F::cell(p, sc, d.bin_invL, d.bin_vpc, cx, cy, cz);
+    cx = min(max(cx, 0), sc.nbc[0] - 1) / BIN_CELLS;
+    cy = min(max(cy, 0), sc.nbc[1] - 1) / BIN_CELLS;
+    cz = min(max(cz, 0), sc.nbc[2] - 1) / BIN_CELLS;
     return sc.bin_base + (cz * sc.nb[1] + cy) * sc.nb[0] + cx;
 }
 
@@ -1027,7 +1287,7 @@ __global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *
         if (!act) continue;
         ContactIn<R> c;
         V3<R> armA, armB;
-        V3<R> ut = {d.lists.hx[hp][e], d.lists.hy[hp][e], d.lists.hz[hp][e]};
+        V3<R> ut = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hp], e);
         V3<R> Fc;
         V3<double> cp;
         if (j & WALL_BIT) {

@@ -48,7 +48,8 @@ class Stats(C.Structure):
                 ("ms_detect", C.c_double), ("ms_force", C.c_double), ("ms_hash", C.c_double),
                 ("ms_link", C.c_double), ("n_detect", C.c_int64), ("n_force", C.c_int64), ("ms_total", C.c_double),
                 ("last_cycle", C.c_int64), ("schedule_samples", C.c_int64), ("ms_integrate", C.c_double),
-                ("n_integrate", C.c_int64), ("spheres_with_entries", C.c_int64)]
+                ("n_integrate", C.c_int64), ("spheres_with_entries", C.c_int64),
+                ("pair_steps", C.c_int64), ("busy_steps", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -56,7 +57,8 @@ class Stats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("contact_block", C.c_int32), ("integrate_block", C.c_int32), ("narrow_block", C.c_int32),
-                ("detect_inline", C.c_int32), ("step_ms", C.c_double)]
+                ("detect_inline", C.c_int32), ("step_ms", C.c_double), ("cell_factor", C.c_double),
+                ("integrate_staged", C.c_int32), ("contact_lean", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

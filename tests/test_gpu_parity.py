@@ -374,3 +374,86 @@ def test_diagnostics_match_oracle():
         assert dg[k] == pytest.approx(do[k], rel=1e-8)
     assert np.allclose(dg["momentum"], do["momentum"], rtol=1e-8, atol=1e-14)
     assert np.allclose(dg["angmom"], do["angmom"], rtol=1e-8, atol=1e-16)
+
+
+# ----------------------------------------------------------------------------- wall screens
+
+_DELTAS = [-1e-4, -5e-5, -2e-5, -1e-6, -1e-9, -1e-12, 0.0, 1e-12, 1e-9, 1e-6, 2e-5, 5e-5, 1e-4]
+
+
+def _threshold_scene(kind, R=1e-3, beta=4e-5):
+    """Spheres whose gap to one wall is R + beta + delta for each delta above (from well
+    outside the FP32 screening band down to a picometre), spaced 4R apart."""
+    Em, num, corm, mum = W._single_material(1e7, 0.3, 0.5, 0.4)
+    T = R + beta
+    pts = []
+    if kind == "plane":
+        lo, hi = np.array([0.0, 0.0, 0.0]), np.array([0.2, 0.02, 0.05])
+        walls = [dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))]
+        for k, dl in enumerate(_DELTAS):
+            pts.append([0.004 + 4 * R * k, 0.01, T + dl])
+    elif kind == "cylinder":
+        r0 = 0.05
+        lo, hi = np.array([-0.1, -0.06, -0.06]), np.array([0.1, 0.06, 0.06])
+        walls = [dict(type=W.CYLINDER, mat=0, p=np.zeros(3), n=np.array([1.0, 0.0, 0.0]), r0=r0)]
+        for k, dl in enumerate(_DELTAS):
+            phi = 0.37 + 0.45 * k
+            rho = r0 - (T + dl)
+            pts.append([-0.05 + 4 * R * k, rho * np.cos(phi), rho * np.sin(phi)])
+    else:
+        r0, z0, r1, z1 = 0.01, 0.0, 0.04, 0.05
+        lo, hi = np.array([-0.05, -0.05, -0.01]), np.array([0.05, 0.05, 0.06])
+        walls = [dict(type=W.CONE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]), r0=r0, z0=z0, r1=r1, z1=z1)]
+        dr, dz = r1 - r0, z1 - z0
+        ln = np.hypot(dr, dz)
+        inr, inz = -dz / ln, dr / ln
+        if inr > 0:
+            inr, inz = -inr, -inz
+        for k, dl in enumerate(_DELTAS):
+            t = 0.2 + 0.05 * k
+            rho = r0 + t * dr + (T + dl) * inr
+            z = z0 + t * dz + (T + dl) * inz
+            phi = 0.3 + 0.47 * k
+            pts.append([rho * np.cos(phi), rho * np.sin(phi), z])
+    pts = np.array(pts)
+    n = len(pts)
+    return W.Scene(lo, hi, Em, num, corm, mum, walls, [W.sphere_template(R)], np.zeros(n, np.int64), None, pts,
+                   W._identity_quats(n), np.zeros((n, 3)), np.zeros((n, 3)), 1e-6, np.zeros(3), r_max=R)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "voxel_fp32"])
+@pytest.mark.parametrize("kind", ["plane", "cylinder", "cone"])
+def test_wall_sets_at_the_threshold_match_the_fp64_predicate(kind, precision):
+    beta = 4e-5
+    s = _threshold_scene(kind, beta=beta)
+    w = dem.World.from_scene(s, precision=precision, margin=beta, margin_max=beta)
+    ow = oracle.OracleWorld(s)
+    if precision == "fp64":
+        p, r = w.sphere_positions()
+        ow.rad[:] = r
+    else:
+        cell, off, L = w.sphere_voxels()
+        _, r = w.sphere_positions()
+        p = (np.asarray(s.box_lo) + cell.astype(np.float64) * L) + off.astype(np.float64)
+        ow.rad[:] = r.astype(np.float32).astype(np.float64)
+    si, wi = w.listed_wall_pairs()
+    osi, owi = ow.listed_wall_pairs(p, beta)
+    # the spheres inside the threshold are listed, those outside are not
+    assert 4 <= len(osi) <= len(_DELTAS) - 4
+    assert np.array_equal(si, osi) and np.array_equal(wi, owi)
+
+
+def test_pair_and_busy_step_counters_follow_the_lists():
+    # every-step detection: a read-back shows the list built from the current state, the
+    # one the next step uses
+    s = dense_scene(n=900, seed=8)
+    for precision in ("voxel_fp32", "fp64"):
+        w = dem.World.from_scene(s, precision=precision, schedule="every_step", margin_max=5e-5)
+        prev = w.stats()
+        for _ in range(12):
+            w.step(1)
+            st = w.stats()
+            assert st["pair_steps"] - prev["pair_steps"] == prev["listed_pairs"]
+            assert st["busy_steps"] - prev["busy_steps"] == prev["spheres_with_entries"]
+            prev = st
+        assert prev["listed_pairs"] > 100

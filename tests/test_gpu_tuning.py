@@ -1,5 +1,5 @@
-"""GPU: captured CUDA graphs, launch shapes, detection placement and the autotuner change
-timing only: every configuration gives bit-identical states."""
+"""GPU: captured CUDA graphs, launch shapes, detection cell size, detection placement and
+the autotuner change timing only: every configuration gives bit-identical states."""
 import os
 
 import numpy as np
@@ -28,12 +28,29 @@ def test_graphs_tunings_and_inline_detection_are_bit_identical():
     b.set_tuning(contact_block=32, integrate_block=512, narrow_block=256, detect_inline=1)
     runs.append(b)
     c = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
-    c.set_tuning(contact_block=128, integrate_block=128, narrow_block=64, detect_inline=0)
+    c.set_tuning(contact_block=128, integrate_block=128, narrow_block=64, detect_inline=0, cell_factor=2.0)
     runs.append(c)
+    e = dem.World.from_scene(s, precision="voxel_fp32", schedule="every_step", margin_max=beta)
+    e.set_tuning(cell_factor=1.5)
+    runs.append(e)
     for w in runs:
         w.step(150)
         for x, y in zip(_state(w), want):
             assert np.array_equal(x, y)
+    assert c.stats()["cell_size"] > 1.9 * ref.stats()["cell_size"]
+    # a cell size change in mid-run, in the FP64 form as well
+    for prec in ("voxel_fp32", "fp64"):
+        p = dem.World.from_scene(s, precision=prec, schedule="velocity_bound", margin=beta, margin_max=beta)
+        q = dem.World.from_scene(s, precision=prec, schedule="velocity_bound", margin=beta, margin_max=beta)
+        p.step(70)
+        p.set_tuning(cell_factor=3.0)
+        p.step(40)
+        p.set_tuning(cell_factor=1.0)
+        p.step(40)
+        q.step(150)
+        for x, y in zip(_state(p), _state(q)):
+            assert np.array_equal(x, y)
+        assert p.listed_pairs()[0].tolist() == q.listed_pairs()[0].tolist()
 
 
 def test_autotune_restores_the_state_and_reuses_its_cache(tmp_path):
@@ -57,6 +74,7 @@ def test_autotune_restores_the_state_and_reuses_its_cache(tmp_path):
     t2 = w2.autotune(steps=40, cache_path=cache)
     for k in ("contact_block", "integrate_block", "narrow_block", "detect_inline"):
         assert t2[k] == t[k]
+    assert t2["cell_factor"] == pytest.approx(t["cell_factor"], abs=1e-3)
     assert t2["step_ms"] == pytest.approx(t["step_ms"], abs=1e-6)
     assert len(open(cache).read().strip().splitlines()) == 1
     # tuned runs continue exactly like untuned ones
@@ -65,3 +83,49 @@ def test_autotune_restores_the_state_and_reuses_its_cache(tmp_path):
     u.step(80)
     for x, y in zip(_state(w), _state(u)):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("kind", ["spheres", "clumps"])
+def test_staged_integration_is_bit_identical(kind):
+    s = W.dense_lattice(n=700, seed=33, vel_sigma=0.3) if kind == "spheres" else W.packed_clumps(n=200, seed=34)
+    beta = 5e-5
+    a = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
+    b = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
+    b.set_tuning(integrate_staged=1)
+    assert b.tuning()["integrate_staged"] == 1
+    a.step(60)
+    b.step(60)
+    for x, y in zip(_state(a), _state(b)):
+        assert np.array_equal(x, y)
+    # switch back and forth in mid-run
+    b.set_tuning(integrate_staged=0)
+    a.step(20)
+    b.step(20)
+    b.set_tuning(integrate_staged=1)
+    a.step(20)
+    b.step(20)
+    for x, y in zip(_state(a), _state(b)):
+        assert np.array_equal(x, y)
+    assert a.stats()["audit_fallbacks"] == b.stats()["audit_fallbacks"]
+
+
+def test_staged_integration_in_a_batch_of_scenes():
+    scenes = [W.dense_lattice(n=150 + 97 * k, seed=40 + k, vel_sigma=0.3) for k in range(3)]
+    beta = 5e-5
+    p = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    q = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    p.initialize()
+    q.initialize()
+    q.worlds[0].set_tuning(integrate_staged=1)
+    p.step(50)
+    q.step(50)
+    for wp, wq in zip(p.worlds, q.worlds):
+        for x, y in zip(_state(wp), _state(wq)):
+            assert np.array_equal(x, y)
+
+
+def test_staged_integration_is_refused_by_the_fp64_form():
+    s = W.dense_lattice(n=200, seed=35)
+    w = dem.World.from_scene(s, precision="fp64", schedule="every_step")
+    w.set_tuning(integrate_staged=1)
+    assert w.tuning()["integrate_staged"] == 0
