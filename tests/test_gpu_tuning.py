@@ -30,6 +30,9 @@ def test_graphs_tunings_and_inline_detection_are_bit_identical():
     c = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
     c.set_tuning(contact_block=128, integrate_block=128, narrow_block=64, detect_inline=0, cell_factor=2.0)
     runs.append(c)
+    f = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
+    f.set_tuning(contact_block=32, contact_lean=1, integrate_staged=1)
+    runs.append(f)
     e = dem.World.from_scene(s, precision="voxel_fp32", schedule="every_step", margin_max=beta)
     e.set_tuning(cell_factor=1.5)
     runs.append(e)
