@@ -829,10 +829,7 @@ dem_status dem_set_owner_state(dem_world *w, int64_t first, int64_t n, const dou
 {
     CHECK_INIT(w);
     if (first < 0 || n < 0 || first + n > scene_owners(w)) return fail(w, DEM_ERR_ARG, "owner range out of bounds");
-    for (int64_t k = 0; k < n; ++k) {
-        if ((xyz && !finite3(xyz + 3 * k)) || (vel && !finite3(vel + 3 * k)) || (omega && !finite3(omega + 3 * k)))
-            return fail(w, DEM_ERR_ARG, "non-finite state");
-    }
+    // non-finite positions and velocities are rejected on the device before any is applied
     std::string err;
     dem_status s = w->impl->engine->set_owner_state(owner_base(w) + first, n, xyz, quat, vel, omega, err);
     return s ? fail(w, s, err) : DEM_OK;

@@ -335,13 +335,12 @@ public:
         if ((s = scratch(buf, 13 * n, err))) return s;
         k_owner_download<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, buf, buf + 3 * n, buf + 7 * n, buf + 10 * n);
         DEM_CU(cudaGetLastError());
-        std::vector<double> h(13 * n);
-        DEM_CU(cudaMemcpyAsync(h.data(), buf, 13 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        // straight into the caller's buffers (full link speed when they are pinned)
+        if (x) DEM_CU(cudaMemcpyAsync(x, buf, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        if (q) DEM_CU(cudaMemcpyAsync(q, buf + 3 * n, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        if (v) DEM_CU(cudaMemcpyAsync(v, buf + 7 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        if (w) DEM_CU(cudaMemcpyAsync(w, buf + 10 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
         DEM_CU(cudaStreamSynchronize(sf_));
-        if (x) std::memcpy(x, h.data(), 3 * n * sizeof(double));
-        if (q) std::memcpy(q, h.data() + 3 * n, 4 * n * sizeof(double));
-        if (v) std::memcpy(v, h.data() + 7 * n, 3 * n * sizeof(double));
-        if (w) std::memcpy(w, h.data() + 10 * n, 3 * n * sizeof(double));
         return DEM_OK;
     }
 
@@ -899,15 +898,30 @@ private:
         if (n <= 0) return DEM_OK;
         double *buf;
         dem_status s;
-        if ((s = scratch(buf, 13 * n + (n + 7) / 8, err))) return s;
+        if ((s = scratch(buf, 13 * n + (n + 7) / 8 + 1, err))) return s;
         double *dx = x ? buf : nullptr, *dq = q ? buf + 3 * n : nullptr, *dv = v ? buf + 7 * n : nullptr,
                *dw = w ? buf + 10 * n : nullptr;
         uint8_t *da = act ? reinterpret_cast<uint8_t *>(buf + 13 * n) : nullptr;
+        int *bad = reinterpret_cast<int *>(buf + 13 * n + (n + 7) / 8);
         if (x) DEM_CU(cudaMemcpyAsync(dx, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
         if (q) DEM_CU(cudaMemcpyAsync(dq, q, 4 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
         if (v) DEM_CU(cudaMemcpyAsync(dv, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
         if (w) DEM_CU(cudaMemcpyAsync(dw, w, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
         if (act) DEM_CU(cudaMemcpyAsync(da, act, n, cudaMemcpyHostToDevice, sf_));
+        // reject non-finite positions and velocities before anything is applied
+        if (x || v || w) {
+            DEM_CU(cudaMemsetAsync(bad, 0, sizeof(int), sf_));
+            const double *arr[3] = {dx, dv, dw};
+            for (const double *a : arr)
+                if (a) k_nonfinite<<<grid(3 * n, 256), 256, 0, sf_>>>(a, 3 * n, bad);
+            int hbad = 0;
+            DEM_CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, sf_));
+            DEM_CU(cudaStreamSynchronize(sf_));
+            if (hbad) {
+                err = "non-finite state";
+                return DEM_ERR_ARG;
+            }
+        }
         // the angular velocity conversion needs the new orientation: quaternion first
         if (q && w) {
             k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, nullptr, da);
@@ -1414,15 +1428,25 @@ private:
     {
         k_act_reset<F><<<1, 1, 0, st>>>(d_, 0);
         k_link<F><<<grid(d_.N, 256), 256, 0, st>>>(d_);
-        k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, 0, m_.clumps ? 1 : 0);
+        launch_compact(st, 0);
         k_commit<<<1, 1, 0, st>>>(st_);
+    }
+
+    // compacted work: clump groups, or single spheres ordered by row length per block
+    void launch_compact(cudaStream_t st, int which)
+    {
+        if (m_.clumps) {
+            k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, which, 0);
+        } else {
+            k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, which, 1);
+        }
     }
 
     // rebuild the compacted work of the list in use (after a restore or a regrow)
     void recompact_current()
     {
         k_act_reset<F><<<1, 1, 0, sf_>>>(d_, 1);
-        k_compact<F><<<grid(d_.Np, 256), 256, 0, sf_>>>(d_, 1, m_.clumps ? 1 : 0);
+        launch_compact(sf_, 1);
     }
 
     void rebuild_inline(cudaStream_t st)

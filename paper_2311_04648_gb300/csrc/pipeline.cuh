@@ -495,12 +495,24 @@ __global__ void k_act_reset(Dev<F> d, int which)
     if (!which) d.status->list_pairs[l] = 0;
 }
 
-// Compact the work of a list: slots with a non-empty row (single spheres) or 32-slot
-// groups with any (clumps: the segmented reduction needs whole warps).  The order of the
-// entries depends on scheduling; results do not (every slot's outputs are its own).
-template <class F>
-__global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int warp_level)
+// Flags any non-finite value of a[0, count).
+static __global__ void __launch_bounds__(256) k_nonfinite(const double *a, int64_t count, int *bad)
 {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count && !isfinite(a[i])) *bad = 1;
+}
+
+// Compact the work of a list: slots with a non-empty row (single spheres) or 32-slot
+// groups with any (clumps: the segmented reduction needs whole warps).  Single spheres
+// (phase 1) keep each block of 256 consecutive slots together, ordered by row length
+// within the block (a shared-memory counting sort): the contact kernel's warps then take
+// neighbouring spheres (shared memory sectors) with rows of equal length (no lanes idle
+// through longer rows).  The order of equal lengths and of the blocks depends on
+// scheduling; results do not (every slot's outputs are its own).
+template <class F>
+__global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase)
+{
+    const int warp_level = phase == 0;
     DevStatus *stp = d.status;
     if (stp->halt) return;
     const int l = stp->list_cur ^ (which ? 0 : 1);
@@ -510,6 +522,33 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int warp_l
     const bool busy = nrow > 0;
     const unsigned int ball = __ballot_sync(0xffffffffu, busy);
     if (lane == 0 && ball) atomicAdd(&stp->list_busy[l], (unsigned int)__popc(ball));
+    if (phase == 1) {
+        __shared__ unsigned int bins[KMAX + 1];
+        __shared__ unsigned int block_base;
+        for (int k = threadIdx.x; k <= KMAX; k += blockDim.x) bins[k] = 0;
+        __syncthreads();
+        if (busy) atomicAdd(&bins[nrow], 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int run = 0;
+            for (int k = 0; k <= KMAX; ++k) {
+                const unsigned int c = bins[k];
+                bins[k] = run;
+                run += c;
+            }
+            block_base = run ? atomicAdd(d.lists.n_act[l], run) : 0u;
+        }
+        __syncthreads();
+        if (busy) {
+            // the first partner and its mirror index travel with the entry: the contact
+            // kernel starts on that pair without waiting for the row
+            const unsigned int pos = block_base + atomicAdd(&bins[nrow], 1u);
+            const uint32_t j0 = d.lists.partner[l][s];
+            const uint32_t m0 = d.lists.mirror[l][s];
+            d.lists.act[l][pos] = make_uint4((uint32_t)s, (uint32_t)nrow, j0, m0);
+        }
+        return;
+    }
     if (warp_level) {
         if (lane == 0 && ball) {
             unsigned int pos = atomicAdd(d.lists.n_act[l], 1u);
