@@ -147,17 +147,17 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
     k_integrate (per owner): state read and written (16-byte vectors: mass kept beside
     the offset, the two audit accumulators in the fourth lanes of v and w; quaternion),
     constants, row length, flags, and the force/torque of owners with listed partners.  k_contact: per sphere with
-    listed partners its compacted work entry (slot, row length), active flag, state,
-    packed constants and the force/torque it writes; per listed pair both row entries,
-    one mirror byte, the history vector read by both sides and written once."""
+    listed partners its compacted work entry (slot, row length, first partner), active
+    flag, state, packed constants and the force/torque it writes; per listed pair both
+    row entries and both sides' history vectors read and written."""
     if precision == "voxel_fp32":
         integ = n * (1 + 1 + 24 + 16 + 16 + 16 + 4 + 16 + 2 + 1         # reads
                      + 24 + 16 + 16 + 16 + 1) + 32 * n_with_entries       # writes, force/torque read
-        contact = n_with_entries * (8 + 1 + 24 + 16 + 16 + 16 + 32) + pairs * (8 + 1 + 16 + 16)
+        contact = n_with_entries * (16 + 1 + 24 + 16 + 16 + 16 + 32) + pairs * (8 + 4 * 16)
     else:
         integ = n * (1 + 1 + 32 + 32 + 32 + 32 + 8 + 32 + 2 + 1
                      + 32 + 32 + 32 + 32 + 1) + 64 * n_with_entries
-        contact = n_with_entries * (8 + 1 + 32 + 32 + 32 + 16 + 64) + pairs * (8 + 1 + 32 + 32)
+        contact = n_with_entries * (16 + 1 + 32 + 32 + 32 + 16 + 64) + pairs * (8 + 4 * 32)
     if clumps:
         contact += n * (16 if precision == "voxel_fp32" else 32)
     return {"integrate": integ, "contact": contact}

@@ -499,6 +499,13 @@ public:
                 int64_t sj = m_.slot_of_sphere[jj[q]];
                 if (sj < sl) continue;
                 key = (uint32_t)sj;
+                // the partner's copy, in its own orientation
+                for (int k = 0; k < cnt[sj]; ++k) {
+                    int64_t e = (int64_t)k * d_.Np + sj;
+                    if (partner[e] == (uint32_t)sl) {
+                        hv[e].x = -(R)ut[3 * q]; hv[e].y = -(R)ut[3 * q + 1]; hv[e].z = -(R)ut[3 * q + 2];
+                    }
+                }
             } else {
                 int scene = m_.owner_scene[m_.sph_owner[sl]];
                 key = WALL_BIT | (uint32_t)(m_.scene_wall_base[scene] + (-1 - jj[q]));
@@ -626,7 +633,6 @@ public:
         if ((s = dput(d_.st.quat[sp], M * sizeof(R4)))) return s;
         if ((s = dput(d_.st.active[sp], M))) return s;
         if ((s = dput(d_.lists.partner[lc], ne * 4))) return s;
-        if ((s = dput(d_.lists.mirror[lc], ne))) return s;
         if ((s = dput(d_.lists.cnt[lc], d_.Np))) return s;
         if ((s = dput(d_.lists.hist[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
         double extra[2] = {beta_, (double)fallbacks_};
@@ -680,7 +686,6 @@ public:
         if ((s = dget(d_.st.quat[sp], M * sizeof(R4)))) return s;
         if ((s = dget(d_.st.active[sp], M))) return s;
         if ((s = dget(d_.lists.partner[lc], ne * 4))) return s;
-        if ((s = dget(d_.lists.mirror[lc], ne))) return s;
         if ((s = dget(d_.lists.cnt[lc], d_.Np))) return s;
         if ((s = dget(d_.lists.hist[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
         double extra[2];
@@ -848,7 +853,6 @@ private:
         dem_status s;
         for (int b = 0; b < 2; ++b) {
             if ((s = alloc(d_.lists.partner[b], ne, err))) return s;
-            if ((s = alloc(d_.lists.mirror[b], ne, err))) return s;
             if ((s = alloc(d_.lists.cnt[b], std::max(d_.Np, Mp_), err))) return s;
             if ((s = alloc(d_.lists.hist[b], ne, err))) return s;
             if (!act_alloc_) {
@@ -875,13 +879,12 @@ private:
         if (keep) {
             const int64_t ne = (int64_t)std::min(Kold, K) * d_.Np;
             DEM_CU(cudaMemcpy(d_.lists.partner[lc], old.partner[lc], ne * 4, cudaMemcpyDeviceToDevice));
-            DEM_CU(cudaMemcpy(d_.lists.mirror[lc], old.mirror[lc], ne, cudaMemcpyDeviceToDevice));
             DEM_CU(cudaMemcpy(d_.lists.cnt[lc], old.cnt[lc], d_.Np, cudaMemcpyDeviceToDevice));
             DEM_CU(cudaMemcpy(d_.lists.hist[hp], old.hist[hp], ne * sizeof(typename HistVec<R>::T),
                               cudaMemcpyDeviceToDevice));
         }
         for (int b = 0; b < 2; ++b) {
-            dfree(old.partner[b]); dfree(old.mirror[b]); dfree(old.cnt[b]);
+            dfree(old.partner[b]); dfree(old.cnt[b]);
             dfree(old.hist[b]);
         }
         if (keep) recompact_current();

@@ -44,7 +44,6 @@ template <> struct SphPack<double> { using T = double2; };
 template <typename R>
 struct ListBuffers {
     uint32_t *partner[2];
-    uint8_t *mirror[2];
     uint8_t *cnt[2];
     typename HistVec<R>::T *hist[2];
     // compacted work of each list: slots with listed partners (single spheres) or

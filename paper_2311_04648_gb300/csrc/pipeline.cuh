@@ -6,10 +6,10 @@
 //   [advance]  k_contact (contact forces, per-owner sums) -> k_integrate -> k_audit
 // Contact lists are ELL rows: entry k of sphere s at k*Np + s, each row holds every
 // partner of s (both orientations) sorted by partner id, walls (WALL_BIT | id) last.
-// A pair (A, B) with A < B owns its tangential history in A's row; B finds it through
-// mirror[] (the position of B in A's row).  Both threads evaluate the pair in the
-// canonical orientation with identical inputs, so the force on B is exactly the negated
-// force on A and no force array or atomic is needed.
+// Each side of a pair keeps the tangential history in its own row, in its own
+// orientation; both threads evaluate the pair from their own side, every term odd in the
+// orientation, so the two copies stay exact negations and the force on B is exactly the
+// negated force on A: no force array, no atomic, no lookup of the partner's row.
 #pragma once
 #include "stage.cuh"
 #include "common.cuh"
@@ -159,8 +159,8 @@ __device__ __forceinline__ V3<R> point_velocity(V3<R> v, V3<R> w, V3<R> r)
 
 // Sphere-sphere contact seen from A (the calling thread's sphere) against B.  Every term
 // is an odd function of the orientation and IEEE round-to-nearest is symmetric under
-// negation, so B's thread, calling with the roles exchanged (and the history negated),
-// obtains exactly the negated force: no canonical reordering is needed.  False if the
+// negation, so B's thread, calling with the roles exchanged (and its copy of the history,
+// the negation of A's), obtains exactly the negated force: no canonical reordering.  False if the
 // overlap is not positive.
 template <class F>
 __device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
@@ -540,12 +540,11 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase)
         }
         __syncthreads();
         if (busy) {
-            // the first partner and its mirror index travel with the entry: the contact
-            // kernel starts on that pair without waiting for the row
+            // the first partner travels with the entry: the contact kernel starts on that
+            // pair without waiting for the row
             const unsigned int pos = block_base + atomicAdd(&bins[nrow], 1u);
             const uint32_t j0 = d.lists.partner[l][s];
-            const uint32_t m0 = d.lists.mirror[l][s];
-            d.lists.act[l][pos] = make_uint4((uint32_t)s, (uint32_t)nrow, j0, m0);
+            d.lists.act[l][pos] = make_uint4((uint32_t)s, (uint32_t)nrow, j0, 0u);
         }
         return;
     }
@@ -564,24 +563,12 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase)
                 d.to[o] = typename F::R4{R(0), R(0), R(0), R(0)};
             }
         }
-    } else {
-        unsigned int base = 0;
-        if (lane == 0 && ball) base = atomicAdd(d.lists.n_act[l], (unsigned int)__popc(ball));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (busy) {
-            // the first partner and its mirror index travel with the entry: the contact
-            // kernel starts on that pair without waiting for the row
-            const uint32_t j0 = d.lists.partner[l][s];
-            const uint32_t m0 = d.lists.mirror[l][s];
-            d.lists.act[l][base + __popc(ball & ((1u << lane) - 1u))] =
-                make_uint4((uint32_t)s, (uint32_t)nrow, j0, m0);
-        }
     }
 }
 
-// Link the new list: mirror positions for entries whose partner owns the pair, and the
-// tangential history of owned entries carried over from the list in use (zero for a
-// pair that is new: Sec. 4.2, contact wildcards start at zero).
+// Link the new list: every entry carries its tangential history over from the same pair
+// in the list in use (zero for a pair that is new: Sec. 4.2, contact wildcards start at
+// zero); each side its own copy.
 template <class F>
 __global__ void __launch_bounds__(256) k_link(Dev<F> d)
 {
@@ -601,15 +588,10 @@ __global__ void __launch_bounds__(256) k_link(Dev<F> d)
         int64_t e = (int64_t)k * d.Np + s;
         uint32_t j = pn[e];
         if (!(j & WALL_BIT) && j > (uint32_t)s) ++owned;
-        if (!(j & WALL_BIT) && j < (uint32_t)s) {
-            int m = row_find(pn, d.Np, j, d.lists.cnt[ln][j], (uint32_t)s);
-            d.lists.mirror[ln][e] = (uint8_t)(m < 0 ? 0 : m);
-        } else {
-            int ko = row_find(po, d.Np, s, nold, j);
-            V3<R> u = {R(0), R(0), R(0)};
-            if (ko >= 0) u = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hs], (int64_t)ko * d.Np + s);
-            hist_put(d.lists.hist[hd], e, u);
-        }
+        const int ko = row_find(po, d.Np, s, nold, j);
+        V3<R> u = {R(0), R(0), R(0)};
+        if (ko >= 0) u = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hs], (int64_t)ko * d.Np + s);
+        hist_put(d.lists.hist[hd], e, u);
     }
     const unsigned int tot = __reduce_add_sync(0xffffffffu, owned);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&stp->list_pairs[ln], tot);
@@ -711,8 +693,8 @@ constexpr int CONTACT_BLOCK_MAX = 128;   // launch shapes are tuned at run time 
 constexpr int INTEGRATE_BLOCK_MAX = 512;
 
 template <class F, bool CLUMPS, int MODE>
-__device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_known, uint32_t j0_known,
-                                             uint32_t m0_known, int sp, int hp, int lc, double *eval_F, double *eval_T)
+__device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_known, uint32_t j0_known, int sp,
+                                             int hp, int lc, double *eval_F, double *eval_T)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
@@ -737,7 +719,6 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         const Scene &sc = d.scenes[scene];
         const R h = F::voxel ? (R)sc.hf : (R)sc.h;
         const uint32_t *prow = d.lists.partner[lc];
-        const uint8_t *mrow = d.lists.mirror[lc];
         using H = typename HistVec<R>::T;
         const H *hin = d.lists.hist[hp];
         H *hout = d.lists.hist[hp ^ 1];
@@ -762,17 +743,13 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
                 continue;
             }
             SphereK<F> other = load_sphere<F, CLUMPS>(d, sp, j);
-            const bool mine = (uint32_t)s < j;     // this slot owns the pair (A = lower id)
             if (!d.st.active[sp][other.owner]) {
-                if (MODE == MODE_STEP && mine) hist_put(hout, e, zero);
+                if (MODE == MODE_STEP) hist_put(hout, e, zero);
                 continue;
             }
-            // the pair is evaluated in this thread's own orientation; the history is
-            // stored in the owner's orientation, so the other side negates it
-            const uint32_t mk = (k == 0 && n_known >= 0) ? m0_known : (uint32_t)mrow[e];
-            const int64_t slot = mine ? e : (int64_t)mk * d.Np + j;
-            V3<R> ut = hist_get<H, R>(hin, slot);
-            if (!mine) ut = -ut;
+            // the pair is evaluated in this thread's own orientation with this side's copy
+            // of the history (the partner's copy is its exact negation)
+            V3<R> ut = hist_get<H, R>(hin, e);
             V3<R> Fc;
             bool on = sphere_contact<F>(d, me, other, c, armA, armB);
             if (on) {
@@ -780,7 +757,7 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
                 Fs = Fs + Fc;
                 Ts = Ts + cross(armA, Fc);
             }
-            if (MODE == MODE_STEP && mine) hist_put(hout, e, on ? ut : zero);
+            if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
         }
     }
     if (CLUMPS) {
@@ -817,17 +794,17 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
 // MODE_STEP: persistent grid-stride loop over the compacted work of the list in use
 // (every thread busy, whichever fraction of the spheres has listed partners); for clumps
 // a whole warp takes a 32-slot group.  MODE_EVAL: one thread per slot over all slots.
-// LEAN = 1 compiles the kernel for 6 resident blocks of CONTACT_BLOCK_MAX threads per SM
-// (fewer registers, some spilled to the L1-cached local memory) instead of 4: more
+// LEAN = 1 compiles the kernel for 5 resident blocks of CONTACT_BLOCK_MAX threads per SM
+// (96 registers, some spilled to the L1-cached local memory) instead of 4: more
 // warps to hide the latency of the gathers, chosen by the autotuner where it pays.
 template <class F, bool CLUMPS, int MODE, int LEAN = 0>
-__global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 6 : 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
+__global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
 {
     DevStatus *stp = d.status;
     if (MODE == MODE_STEP && (stp->halt || stp->list_stale)) return;
     const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
     if (MODE == MODE_EVAL) {
-        contact_slot<F, CLUMPS, MODE>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, -1, 0u, 0u, sp, hp, lc,
+        contact_slot<F, CLUMPS, MODE>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, -1, 0u, sp, hp, lc,
                                       eval_F, eval_T);
         return;
     }
@@ -839,14 +816,17 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 6 : 4) k_contact(Dev
     if (CLUMPS) {
         const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
         for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps)
-            contact_slot<F, CLUMPS, MODE>(d, ((int64_t)act[w].x << 5) + (threadIdx.x & 31), -1, 0u, 0u, sp, hp, lc,
+            contact_slot<F, CLUMPS, MODE>(d, ((int64_t)act[w].x << 5) + (threadIdx.x & 31), -1, 0u, sp, hp, lc,
                                           eval_F, eval_T);
     } else {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += stride)
-        {
-            const uint4 a = act[t];
-            contact_slot<F, CLUMPS, MODE>(d, (int64_t)a.x, (int)a.y, a.z, a.w, sp, hp, lc, eval_F, eval_T);
+        int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        uint4 a = t < nw ? act[t] : make_uint4(0u, 0u, 0u, 0u);
+        for (; t < nw; t += stride) {
+            // the next work entry is read while this one is evaluated
+            const uint4 next = t + stride < nw ? act[t + stride] : a;
+            contact_slot<F, CLUMPS, MODE>(d, (int64_t)a.x, (int)a.y, a.z, sp, hp, lc, eval_F, eval_T);
+            a = next;
         }
     }
 }
