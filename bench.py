@@ -163,14 +163,17 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
     return {"integrate": integ, "contact": contact}
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-# capture of the 4M-sphere bench workload (profiles/dram_traffic_settling_column_4M.md),
-# valid while the kernel's source text hashes to the recorded value.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one-pass
+# ncu captures of the 4M-sphere bench workload mid-run (profiles/dram_traffic_settling_
+# column_4M.md), valid while the kernels' source text hashes to the recorded values.
 MEASURED_TRAFFIC = {
-    "integrate": {"n": 4_000_000, "bytes": 745.1e6, "source": [("k_integrate(Dev<F> d)", "f9ed49db846000ab")]},
-    "contact": {"n": 4_000_000, "bytes": 244.3e6,
-                "source": [("k_contact(Dev<F> d, double *eval_F, double *eval_T)", "0d146a79dd095f7c"),
-                           ("contact_slot(const Dev<F> &d", "c8f2a259de1dbfb0")]},
+    "integrate": {"n": 4_000_000, "bytes": 757.6e6,
+                  "source": [("k_integrate(Dev<F> d)", "fe81e7fb942fa4af"),
+                             ("integrate_owner(const Dev<F> &d", "4996074ebb97ab14")]},
+    "contact": {"n": 4_000_000, "bytes": 811.9e6,
+                "source": [("k_contact(Dev<F> d, double *eval_F, double *eval_T)", "41586b578582277e"),
+                           ("contact_slot(const Dev<F> &d", "015946760ba8db1b"),
+                           ("wall_contact(const Dev<F> &d", "30f182659e6cbcd4")]},
 }
 
 
