@@ -207,6 +207,29 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def device_copy_gbs(device, nbytes=2 << 30, reps=5):
+    """This GPU's own device-to-device copy bandwidth (read + write bytes per second) with
+    a torch copy, for reading the run against the machine's measured peak: GPUs of a pool
+    differ."""
+    import torch
+    a = torch.empty(nbytes // 4, dtype=torch.float32, device=f"cuda:{device}")
+    b = torch.empty_like(a)
+    b.copy_(a)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    best = 0.0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * nbytes / (e0.elapsed_time(e1) / 1000.0) / 1e9)
+    del a, b
+    torch.cuda.empty_cache()
+    return best
+
+
 # ----------------------------------------------------------------------------- runs
 
 def make_scene(n):
@@ -299,7 +322,9 @@ def run_ours(args, device):
     s1 = w.stats()
     steps = s1["steps"] - s0["steps"]
     rebuilds = s1["rebuilds"] - s0["rebuilds"]
-    out["chosen"] = dict(ms=ms, steps=steps, rebuilds=rebuilds, clocks=clk.summary(), stats=s1)
+    out["chosen"] = dict(ms=ms, steps=steps, rebuilds=rebuilds, clocks=clk.summary(), stats=s1,
+                         fallbacks=s1["audit_fallbacks"] - s0["audit_fallbacks"])
+    out["copy_gbs"] = device_copy_gbs(device)
     # profiled pass over the same steps (restored from the checkpoint) for per-kernel
     # durations: events on each kernel's own stream
     end_state = w.save_state()
@@ -574,6 +599,8 @@ def main():
                    "schedule": "delayed detection on a second stream, velocity-bound cycle, audited every step",
                    "margin_m": res["chosen"]["stats"]["margin"],
                    "rebuilds_in_timed_region": res["chosen"]["rebuilds"],
+                   "audit_fallbacks_in_timed_region": res["chosen"]["fallbacks"],
+                   "device_copy_gbs_this_gpu": res["copy_gbs"],
                    "tuning": res["tuning"],
                    "l2": "inputs larger than L2 (owner state + contact lists > 0.5 GB)",
                    "parallelism": f"replica x{world}"},

@@ -316,6 +316,24 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
                 }
                 w.tolf = (float)(2e-5 * scale * cond);
             }
+            w.axis = -1;
+            if (ws.type == WALL_PLANE && ws.omega[0] == 0.0 && ws.omega[1] == 0.0 && ws.omega[2] == 0.0) {
+                for (int a = 0; a < 3; ++a) {
+                    const int b = (a + 1) % 3, c = (a + 2) % 3;
+                    if ((ws.n[a] == 1.0 || ws.n[a] == -1.0) && ws.n[b] == 0.0 && ws.n[c] == 0.0) {
+                        const double rel = ws.p[a] - g.lo[a];
+                        const double k = std::floor(rel / m.Lv);
+                        if (std::fabs(k) < 1e6 * (double)(1 << 20)) {
+                            w.axis = a;
+                            w.ax_c = (int)k;
+                            const double off = rel - k * m.Lv;
+                            w.ax_off = (float)off;
+                            w.ax_off_lo = (float)(off - (double)w.ax_off);
+                            w.ax_sign = (float)ws.n[a];
+                        }
+                    }
+                }
+            }
             m.walls.push_back(w);
         }
         m.scenes.push_back(g);

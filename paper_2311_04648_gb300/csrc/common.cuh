@@ -102,6 +102,11 @@ struct Wall {            // analytical wall (device copy); geometry in FP64
     float pf[3], nf[3];  // FP32 copies for screening tests (decide only far from the
     float r0f, r1f, z0f, z1f;   // threshold, see wall_gap_f)
     float tolf;          // screening tolerance per unit of (|centre|_1 + 1), see wall_gap_f
+    // a plane normal to a coordinate axis and not moving: axis (else -1), side (+1 / -1)
+    // and its position on the scene's voxel grid (voxel index, offset in [0, Lv) as a
+    // float-float pair), so that the voxel form measures gaps from voxel differences in FP32
+    int axis, ax_c;
+    float ax_sign, ax_off, ax_off_lo;
 };
 
 struct Scene {           // per-scene constants (device copy)

@@ -281,6 +281,7 @@ public:
             if (left <= 0) break;
             if (sth_->list_stale) {          // audit fallback: rebuild from the current state
                 fallbacks_ += 1;
+                cycle_scale_ = std::max(0.05, cycle_scale_ * 0.6);
                 rebuild_inline(sf_);
                 if ((s = settle(err))) return s;
                 continue;
@@ -1575,10 +1576,16 @@ private:
             long long lc = learned_cycle(err);
             if (lc > 0) c = lc;
         }
+        // a cycle cut short by the audit shrinks the next ones (x0.6); cycles that run to
+        // their end let the factor recover (x1.1 up to 1): fewer inline fallback rebuilds
+        // where the motion outgrows the bound, no change where it does not
+        c = (long long)std::floor((double)c * cycle_scale_);
+        cycle_scale_ = std::min(1.0, cycle_scale_ * 1.1);
         last_cycle_ = std::max<long long>(1, std::min<long long>(c, 2000));
         return last_cycle_;
     }
     long long last_cycle_ = 0;
+    double cycle_scale_ = 1.0;
 
     void release()
     {

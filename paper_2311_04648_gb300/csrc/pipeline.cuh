@@ -200,6 +200,42 @@ __device__ __forceinline__ bool wall_contact(const Dev<F> &d, const SphereK<F> &
                                              V3<double> *point = nullptr)
 {
     using R = typename F::R;
+    if constexpr (F::voxel) {
+        if (w.axis >= 0) {
+            // an axis-aligned resting plane: the signed distance of the centre is
+            // (voxel index - plane's) Lv (exact) plus the offset difference, kept in
+            // float-float, so the overlap is exact to a few ulps without FP64
+            const int a = w.axis;
+            const int ci = a == 0 ? A.p.cx : (a == 1 ? A.p.cy : A.p.cz);
+            const float oi = a == 0 ? A.p.x : (a == 1 ? A.p.y : A.p.z);
+            float bh, bl, gh, gl;
+            two_sum(oi, -w.ax_off, bh, bl);                      // exact offset difference
+            two_sum(__fmul_rn((float)(ci - w.ax_c), d.L), bh, gh, gl);
+            gl = __fadd_rn(gl, __fsub_rn(bl, w.ax_off_lo));
+            gh = __fmul_rn(gh, w.ax_sign);
+            gl = __fmul_rn(gl, w.ax_sign);
+            const float delta = __fadd_rn(__fsub_rn(A.rad, gh), __fsub_rn(A.rlo, gl));
+            if (!(delta > 0.0f)) return false;
+            const float arm = __fsub_rn(A.rad, __fmul_rn(0.5f, delta));
+            V3<float> n = {0.0f, 0.0f, 0.0f};
+            if (a == 0) n.x = w.ax_sign; else if (a == 1) n.y = w.ax_sign; else n.z = w.ax_sign;
+            c.n = n;
+            c.delta = delta;
+            armA = arm_of(A.rl, -arm, c.n);
+            c.uA = point_velocity(A.v, A.w, armA);
+            c.uB = {0.0f, 0.0f, 0.0f};
+            c.Rbar = A.rad;
+            c.mbar = A.mass;
+            load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
+            if (point) {
+                // read-backs: the contact point in FP64 (the force above is the step's)
+                const V3<double> pa = F::absolute(A.p, sc, d.Ld);
+                const double ad = (double)arm;
+                *point = {pa.x - ad * (double)n.x, pa.y - ad * (double)n.y, pa.z - ad * (double)n.z};
+            }
+            return true;
+        }
+    }
     if (w.type == WALL_PLANE) {
         const float3 pf = approx_pos<F>(A.p, sc, d.L);
         if (!plane_may_reach(w, pf, (float)A.rad, fabsf(pf.x) + fabsf(pf.y) + fabsf(pf.z) + 1.0f)) return false;

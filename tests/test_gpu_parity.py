@@ -457,3 +457,37 @@ def test_pair_and_busy_step_counters_follow_the_lists():
             assert st["busy_steps"] - prev["busy_steps"] == prev["spheres_with_entries"]
             prev = st
         assert prev["listed_pairs"] > 100
+
+
+def test_voxel_forces_on_axis_planes_match_fp64_at_every_overlap():
+    # one sphere against each face of a box, overlaps from a nanometre to 10 micrometres
+    R = 1e-3
+    Em, num, corm, mum = W._single_material(1e7, 0.3, 0.5, 0.4)
+    lo, hi = np.zeros(3), np.array([0.05, 0.04, 0.06])
+    pts = []
+    for i, dl in enumerate((1e-9, 1e-8, 1e-7, 1e-6, 1e-5)):
+        for a in range(3):
+            for side in (0, 1):
+                # the five spheres of a wall 6 mm apart along one in-plane axis
+                p = 0.5 * (lo + hi)
+                p[(a + 1) % 3] += 0.006 * (i - 2)
+                p[a] = lo[a] + (R - dl) if side == 0 else hi[a] - (R - dl)
+                pts.append(p)
+    pts = np.array(pts)
+    n = len(pts)
+    rng = np.random.default_rng(51)
+    s = W.Scene(lo, hi, Em, num, corm, mum, W.box_walls(lo, hi), [W.sphere_template(R)], np.zeros(n, np.int64),
+                None, pts, W._identity_quats(n), rng.normal(scale=0.05, size=(n, 3)),
+                rng.normal(scale=20.0, size=(n, 3)), 1e-6, np.zeros(3), r_max=R)
+    w = dem.World.from_scene(s, precision="voxel_fp32")
+    ow = oracle.OracleWorld(s)
+    cell, off, L = w.sphere_voxels()
+    # the oracle at the voxel form's own positions (the radius, kept as a float-float pair
+    # by the voxel form, is the scene's)
+    ow.x[:] = (np.asarray(s.box_lo) + cell.astype(np.float64) * L) + off.astype(np.float64)
+    F, T = w.owner_forces()
+    Fo, To, oc = ow.eval()
+    assert len(oc) == n
+    mag = np.linalg.norm(Fo, axis=1)
+    err = np.linalg.norm(F - Fo, axis=1) / mag
+    assert err.max() <= 1e-4, err.max()
