@@ -137,7 +137,8 @@ def algorithmic_bytes(precision, n, pairs, clumps=False):
     else:
         integ = 144 * n + (32 * n if clumps else 0)
         contact = 56 * pairs
-    return {"integrate": integ, "contact": contact}
+    # the fused step kernel does both: the whole force+integrate figure per launch
+    return {"integrate": integ, "contact": contact, "step": integ + contact}
 
 
 def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
@@ -154,13 +155,19 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
         integ = n * (1 + 1 + 24 + 16 + 16 + 16 + 4 + 16 + 2 + 1         # reads
                      + 24 + 16 + 16 + 16 + 1) + 32 * n_with_entries       # writes, force/torque read
         contact = n_with_entries * (16 + 1 + 24 + 16 + 16 + 16 + 32) + pairs * (8 + 4 * 16)
+        # fused step, per owner: permutation, row length, first entry, flag, state, packed
+        # constants, quaternion, inverse mass and inertia read; state and flag written
+        step = n * (1 + 1 + 4 + 1 + 24 + 16 + 16 + 16 + 16 + 4 + 16
+                    + 24 + 16 + 16 + 16 + 1) + pairs * (8 + 4 * 16)
     else:
         integ = n * (1 + 1 + 32 + 32 + 32 + 32 + 8 + 32 + 2 + 1
                      + 32 + 32 + 32 + 32 + 1) + 64 * n_with_entries
         contact = n_with_entries * (16 + 1 + 32 + 32 + 32 + 16 + 64) + pairs * (8 + 4 * 32)
+        step = n * (1 + 1 + 4 + 1 + 32 + 32 + 32 + 16 + 32 + 8 + 32
+                    + 32 + 32 + 32 + 32 + 1) + pairs * (8 + 4 * 32)
     if clumps:
         contact += n * (16 if precision == "voxel_fp32" else 32)
-    return {"integrate": integ, "contact": contact}
+    return {"integrate": integ, "contact": contact, "step": step}
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one-pass
@@ -254,19 +261,28 @@ def profile_delta(p0, p1):
                 active_contacts=p1["active_contacts"], list_capacity=p1["list_capacity"])
 
 
+KERNEL_NAMES = {"contact": "k_contact (pair forces + per-owner sums)",
+                "integrate": "k_integrate (owner update + audit)",
+                "step": "k_step_fused (pair forces summed in registers + owner update + audit)"}
+
+
+def fused_step(prof):
+    """True when the profiled steps ran the fused kernel (no separate integration)."""
+    return prof["n_integrate"] == 0 and prof["n_contact"] > 0
+
+
 def roofline(precision, n, prof, peak, peak_kind):
     ab = algorithmic_bytes(precision, n, prof["listed_pairs"])
     lb = layout_bytes(precision, n, prof["with_entries"], prof["listed_pairs"])
     per = {}
-    for k in ("contact", "integrate"):
-        ms = prof[f"{k}_ms"]
+    for k in (("step",) if fused_step(prof) else ("contact", "integrate")):
+        ms = prof["contact_ms" if k == "step" else f"{k}_ms"]
         sec = ms / 1000.0
         per[k] = {"ms": ms, "bytes": ab[k], "gbs": ab[k] / sec / 1e9 if ms > 0 else None,
                   "moved_bytes": lb[k], "moved_gbs": lb[k] / sec / 1e9 if ms > 0 else None}
     dom = max(per, key=lambda k: per[k]["ms"])
     a = per[dom]["gbs"]
-    return {"bound": "hbm", "kernel": {"contact": "k_contact (pair forces + per-owner sums)",
-                                       "integrate": "k_integrate (owner update + audit)"}[dom],
+    return {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
             "achieved": a, "peak": peak, "unit": "GB/s", "frac": (a / peak) if a else None,
             "traffic": measured_traffic(dom, n) if precision == "voxel_fp32" else None,
             "peak_kind": peak_kind, "bytes_per_launch": per[dom]["bytes"], "avg_launch_ms": per[dom]["ms"],
@@ -605,13 +621,14 @@ def main():
                    "l2": "inputs larger than L2 (owner state + contact lists > 0.5 GB)",
                    "parallelism": f"replica x{world}"},
         "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind),
-        "kernels_ms": {"contact": prof["contact_ms"], "integrate": prof["integrate_ms"],
-                       "detect": prof["detect_ms"], "hash": prof["hash_ms"], "link": prof["link_ms"]},
+        "kernels_ms": dict(({"step": prof["contact_ms"]} if fused_step(prof) else
+                            {"contact": prof["contact_ms"], "integrate": prof["integrate_ms"]}),
+                           detect=prof["detect_ms"], hash=prof["hash_ms"], link=prof["link_ms"]),
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": e2e["bytes_in"],
                 "d2h_bytes_per_step": e2e["bytes_out"],
                 "how": "dem_set_owner_state from pinned host buffers + dem_step(1) + dem_get_owner_state "
                        "to pinned host buffers, every step"},
-        "gpu_launches": int(3 * steps + 20 * res["chosen"]["rebuilds"]),
+        "gpu_launches": int((2 if fused_step(prof) else 3) * steps + 20 * res["chosen"]["rebuilds"]),
         "clocks": res["chosen"]["clocks"],
     }
     if plain:
@@ -619,8 +636,9 @@ def main():
         pp = plain["profile"]
         line["plain"] = {"value": pv, "unit": METRIC, "ms_per_step": plain["ms"] / max(plain["steps"], 1),
                          "dtype": "f64", "schedule": "every step",
-                         "kernels_ms": {"contact": pp["contact_ms"], "integrate": pp["integrate_ms"],
-                                        "detect": pp["detect_ms"]},
+                         "kernels_ms": dict(({"step": pp["contact_ms"]} if fused_step(pp) else
+                                             {"contact": pp["contact_ms"], "integrate": pp["integrate_ms"]}),
+                                            detect=pp["detect_ms"]),
                          "roofline": roofline("fp64", n_sph, pp, peak, peak_kind),
                          "chosen_over_plain": value / pv}
     if world == 1 and not args.no_cpu_baseline:

@@ -859,6 +859,7 @@ private:
             if (!act_alloc_) {
                 if ((s = alloc(d_.lists.act[b], d_.Np, err))) return s;
                 if ((s = alloc(d_.lists.n_act[b], 1, err))) return s;
+                if ((s = alloc(d_.lists.perm[b], d_.Np, err))) return s;
             }
         }
         act_alloc_ = true;
@@ -1044,6 +1045,10 @@ private:
             err = "block sizes must be multiples of 32 within the kernels' limits";
             return DEM_ERR_ARG;
         }
+        if (t->fused_block != 0 && t->fused_block != 64 && t->fused_block != 128 && t->fused_block != 256) {
+            err = "fused_block must be 0, 64, 128 or 256";
+            return DEM_ERR_ARG;
+        }
         const double f = t->cell_factor == 0.0 ? 1.0 : t->cell_factor;
         if (!(f >= 1.0 && f <= 4.0)) {
             err = "cell_factor must be in [1, 4]";
@@ -1059,6 +1064,7 @@ private:
         tune_.cell_factor = m_.cell_factor;
         tune_.integrate_staged = (t->integrate_staged && prepare_staged()) ? 1 : 0;
         tune_.contact_lean = t->contact_lean ? 1 : 0;
+        tune_.fused_block = m_.clumps ? 0 : t->fused_block;
         return DEM_OK;
     }
 
@@ -1167,9 +1173,11 @@ private:
                     dem_tuning t{};
                     if (std::sscanf(line, "{\"key\": \"%299[^\"]\", \"contact_block\": %d, \"integrate_block\": %d, "
                                           "\"narrow_block\": %d, \"detect_inline\": %d, \"cell_factor\": %lf, "
-                                          "\"integrate_staged\": %d, \"contact_lean\": %d, \"step_ms\": %lf}",
+                                          "\"integrate_staged\": %d, \"contact_lean\": %d, \"fused_block\": %d, "
+                                          "\"step_ms\": %lf}",
                                     k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
-                                    &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.step_ms) == 9 &&
+                                    &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.fused_block,
+                                    &t.step_ms) == 10 &&
                         key == k) {
                         best = t;
                         found = true;
@@ -1210,14 +1218,15 @@ private:
         const double f0 = m_.cell_factor;
         for (int cb : {32, 64, 128})
             for (int di = 0; di <= (delayed ? 1 : 0); ++di)
-                if ((s = trial(dem_tuning{cb, 256, 128, di, 0.0, f0, 0, 0}))) return s;
+                if ((s = trial(dem_tuning{cb, 256, 128, di, 0.0, f0, 0, 0, 0}))) return s;
         const dem_tuning b1 = best;
         for (int ib : {256, 512})
             for (int nb : {128, 256})
                 if (ib != b1.integrate_block || nb != b1.narrow_block)
-                    if ((s = trial(dem_tuning{b1.contact_block, ib, nb, b1.detect_inline, 0.0, f0, 0, 0}))) return s;
+                    if ((s = trial(dem_tuning{b1.contact_block, ib, nb, b1.detect_inline, 0.0, f0, 0, 0, 0})))
+                        return s;
         if (F::voxel)
-            if ((s = trial(dem_tuning{b1.contact_block, 256, best.narrow_block, b1.detect_inline, 0.0, f0, 1, 0})))
+            if ((s = trial(dem_tuning{b1.contact_block, 256, best.narrow_block, b1.detect_inline, 0.0, f0, 1, 0, 0})))
                 return s;
         {
             dem_tuning t = best;
@@ -1225,11 +1234,21 @@ private:
             t.step_ms = 0.0;
             if ((s = trial(t))) return s;
         }
+        // single spheres: forces and integration in one kernel, each of its block sizes
+        if (!m_.clumps) {
+            const dem_tuning b3 = best;
+            for (int fb : {64, 128, 256}) {
+                dem_tuning t = b3;
+                t.fused_block = fb;
+                t.step_ms = 0.0;
+                if ((s = trial(t))) return s;
+            }
+        }
         const dem_tuning b2 = best;
         for (double f : {1.0, 1.5, 2.0})
             if (f != b2.cell_factor)
                 if ((s = trial(dem_tuning{b2.contact_block, b2.integrate_block, b2.narrow_block, b2.detect_inline,
-                                          0.0, f, b2.integrate_staged, b2.contact_lean})))
+                                          0.0, f, b2.integrate_staged, b2.contact_lean, b2.fused_block})))
                     return s;
         best.step_ms = best_ms / steps;
         if ((s = set_tuning(&best, err))) return s;
@@ -1241,10 +1260,10 @@ private:
                 std::fprintf(f,
                              "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
                              "%d, \"detect_inline\": %d, \"cell_factor\": %.3f, \"integrate_staged\": %d, "
-                             "\"contact_lean\": %d, \"step_ms\": %.6f}\n",
+                             "\"contact_lean\": %d, \"fused_block\": %d, \"step_ms\": %.6f}\n",
                              key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
                              best.detect_inline, best.cell_factor, best.integrate_staged, best.contact_lean,
-                             best.step_ms);
+                             best.fused_block, best.step_ms);
                 std::fclose(f);
             }
         }
@@ -1549,15 +1568,26 @@ private:
         else k_integrate<F, false><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
     }
 
+    // Single spheres with the fused step chosen: one kernel for forces and integration.
+    bool fused() const { return !m_.clumps && tune_.fused_block > 0; }
+
     void force_step()
     {
-        Mark m, m2;
-        mark_begin(P_FORCE, sf_, m);
-        launch_force<MODE_STEP>(nullptr, nullptr);
-        mark_end(sf_, m);
-        mark_begin(P_INTEG, sf_, m2);
-        launch_integrate();
-        mark_end(sf_, m2);
+        if (fused()) {
+            Mark m;
+            mark_begin(P_FORCE, sf_, m);
+            const int b = tune_.fused_block;
+            k_step_fused<F><<<grid(d_.Np, b), b, 0, sf_>>>(d_);
+            mark_end(sf_, m);
+        } else {
+            Mark m, m2;
+            mark_begin(P_FORCE, sf_, m);
+            launch_force<MODE_STEP>(nullptr, nullptr);
+            mark_end(sf_, m);
+            mark_begin(P_INTEG, sf_, m2);
+            launch_integrate();
+            mark_end(sf_, m2);
+        }
         k_audit<<<1, 1, 0, sf_>>>(st_);
         if (collect_ && d_.M > 0)
             k_collect_step<F><<<grid(d_.M, 256), 256, 0, sf_>>>(d_, acc_lab_, obin_, cross_, win_start_, (float)beta_);
@@ -1627,7 +1657,7 @@ private:
     bool dirty_ = false;
     int64_t fallbacks_ = 0, regrows_ = 0;
     double ms_total_ = 0.0;
-    dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0};   // contact_lean last
+    dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0, 0};   // fused_block last
     int n_sm_ = 1, occ_block_ = 0, occ_per_sm_ = 1;
     int64_t Mp_ = 0;                // owners rounded up to whole staging tiles
     int staged_per_sm_ = 0;

@@ -50,6 +50,9 @@ struct ListBuffers {
     // 32-slot groups containing any (clumps), and their number
     uint4 *act[2];
     uint32_t *n_act[2];
+    // single spheres: per block of 256 slots, the slots' offsets within the block in
+    // order of row length (empty rows first), for the fused step kernel
+    uint8_t *perm[2];
 };
 
 // Owner-state double buffers.

@@ -560,21 +560,28 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase)
     if (lane == 0 && ball) atomicAdd(&stp->list_busy[l], (unsigned int)__popc(ball));
     if (phase == 1) {
         __shared__ unsigned int bins[KMAX + 1];
+        __shared__ unsigned int all[KMAX + 1];
         __shared__ unsigned int block_base;
-        for (int k = threadIdx.x; k <= KMAX; k += blockDim.x) bins[k] = 0;
+        for (int k = threadIdx.x; k <= KMAX; k += blockDim.x) bins[k] = all[k] = 0;
         __syncthreads();
         if (busy) atomicAdd(&bins[nrow], 1u);
+        if (s < d.Np) atomicAdd(&all[nrow], 1u);
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned int run = 0;
+            unsigned int run = 0, run_all = 0;
             for (int k = 0; k <= KMAX; ++k) {
-                const unsigned int c = bins[k];
+                const unsigned int c = bins[k], ca = all[k];
                 bins[k] = run;
+                all[k] = run_all;
                 run += c;
+                run_all += ca;
             }
             block_base = run ? atomicAdd(d.lists.n_act[l], run) : 0u;
         }
         __syncthreads();
+        // every slot of the block (empty rows first) by row length, for the fused step
+        // (the block is 256 slots: the position fits a byte)
+        if (s < d.Np) d.lists.perm[l][(s & ~(int64_t)255) + atomicAdd(&all[nrow], 1u)] = (uint8_t)(s & 255);
         if (busy) {
             // the first partner travels with the entry: the contact kernel starts on that
             // pair without waiting for the row
@@ -728,6 +735,59 @@ __device__ __forceinline__ void quat_mul(R aw, R ax, R ay, R az, R bw, R bx, R b
 constexpr int CONTACT_BLOCK_MAX = 128;   // launch shapes are tuned at run time up to these
 constexpr int INTEGRATE_BLOCK_MAX = 512;
 
+// The n listed entries of sphere s (first partner j_first) evaluated from s's side: the
+// sums of the contact forces on s and of their torques about its owner's centre, and
+// (MODE_STEP) each entry's updated history written to the other history buffer.
+template <class F, bool CLUMPS, int MODE>
+__device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me, const Scene &sc, int64_t s, int n,
+                                          uint32_t j_first, int sp, int hp, int lc, V3<typename F::R> &Fs,
+                                          V3<typename F::R> &Ts)
+{
+    using R = typename F::R;
+    const R h = F::voxel ? (R)sc.hf : (R)sc.h;
+    const uint32_t *prow = d.lists.partner[lc];
+    using H = typename HistVec<R>::T;
+    const H *hin = d.lists.hist[hp];
+    H *hout = d.lists.hist[hp ^ 1];
+    const V3<R> zero = {R(0), R(0), R(0)};
+    uint32_t j_next = j_first;
+    for (int k = 0; k < n; ++k) {
+        const int64_t e = (int64_t)k * d.Np + s;
+        const uint32_t j = j_next;
+        if (k + 1 < n) j_next = prow[e + d.Np];      // next partner's id in flight early
+        ContactIn<R> c;
+        V3<R> armA, armB;
+        if (j & WALL_BIT) {
+            V3<R> ut = hist_get<H, R>(hin, e);
+            V3<R> Fc;
+            bool on = wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA);
+            if (on) {
+                hertz_mindlin<R>(c, h, ut, Fc);
+                Fs = Fs + Fc;
+                Ts = Ts + cross(armA, Fc);
+            }
+            if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
+            continue;
+        }
+        SphereK<F> other = load_sphere<F, CLUMPS>(d, sp, j);
+        if (!d.st.active[sp][other.owner]) {
+            if (MODE == MODE_STEP) hist_put(hout, e, zero);
+            continue;
+        }
+        // the pair is evaluated in this thread's own orientation with this side's copy
+        // of the history (the partner's copy is its exact negation)
+        V3<R> ut = hist_get<H, R>(hin, e);
+        V3<R> Fc;
+        bool on = sphere_contact<F>(d, me, other, c, armA, armB);
+        if (on) {
+            hertz_mindlin<R>(c, h, ut, Fc);
+            Fs = Fs + Fc;
+            Ts = Ts + cross(armA, Fc);
+        }
+        if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
+    }
+}
+
 template <class F, bool CLUMPS, int MODE>
 __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_known, uint32_t j0_known, int sp,
                                              int hp, int lc, double *eval_F, double *eval_T)
@@ -751,51 +811,9 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
         scene = d.owner_scene[o];
     }
-    if (act) {
-        const Scene &sc = d.scenes[scene];
-        const R h = F::voxel ? (R)sc.hf : (R)sc.h;
-        const uint32_t *prow = d.lists.partner[lc];
-        using H = typename HistVec<R>::T;
-        const H *hin = d.lists.hist[hp];
-        H *hout = d.lists.hist[hp ^ 1];
-        const V3<R> zero = {R(0), R(0), R(0)};
-        uint32_t j_next = n_known >= 0 ? j0_known : (n > 0 ? prow[s] : 0u);
-        for (int k = 0; k < n; ++k) {
-            const int64_t e = (int64_t)k * d.Np + s;
-            const uint32_t j = j_next;
-            if (k + 1 < n) j_next = prow[e + d.Np];      // next partner's id in flight early
-            ContactIn<R> c;
-            V3<R> armA, armB;
-            if (j & WALL_BIT) {
-                V3<R> ut = hist_get<H, R>(hin, e);
-                V3<R> Fc;
-                bool on = wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA);
-                if (on) {
-                    hertz_mindlin<R>(c, h, ut, Fc);
-                    Fs = Fs + Fc;
-                    Ts = Ts + cross(armA, Fc);
-                }
-                if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
-                continue;
-            }
-            SphereK<F> other = load_sphere<F, CLUMPS>(d, sp, j);
-            if (!d.st.active[sp][other.owner]) {
-                if (MODE == MODE_STEP) hist_put(hout, e, zero);
-                continue;
-            }
-            // the pair is evaluated in this thread's own orientation with this side's copy
-            // of the history (the partner's copy is its exact negation)
-            V3<R> ut = hist_get<H, R>(hin, e);
-            V3<R> Fc;
-            bool on = sphere_contact<F>(d, me, other, c, armA, armB);
-            if (on) {
-                hertz_mindlin<R>(c, h, ut, Fc);
-                Fs = Fs + Fc;
-                Ts = Ts + cross(armA, Fc);
-            }
-            if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
-        }
-    }
+    if (act)
+        pair_sums<F, CLUMPS, MODE>(d, me, d.scenes[scene], s, n,
+                                   n_known >= 0 ? j0_known : (n > 0 ? d.lists.partner[lc][s] : 0u), sp, hp, lc, Fs, Ts);
     if (CLUMPS) {
         // segmented suffix sums over the owner's consecutive lanes; the head lane ends
         // with the owner's total (fixed tree order: deterministic)
@@ -895,120 +913,133 @@ struct OwnerSrc {
     const uint16_t *scene;
 };
 
-// Semi-implicit Euler update of one owner: v with the contact force plus gravity, then
-// the body-frame angular velocity (Euler's equations, gyroscopic term switchable), then x
-// with the new v, then the quaternion with the new angular velocity; removal by the sink;
-// the per-owner displacement bounds of the audit.  Outputs go to the other state buffer.
+// Semi-implicit Euler update of one owner from its loaded state and the contact force
+// and torque on it: v with the contact force plus gravity, then the body-frame angular
+// velocity (Euler's equations, gyroscopic term switchable), then x with the new v, then
+// the quaternion with the new angular velocity; removal by the sink; the per-owner
+// displacement bounds of the audit.  Outputs go to the other state buffer.
+template <class F, bool CLUMPS>
+__device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, int64_t o, int sp, bool act,
+                                               const typename F::Pos &po, typename F::R mass, typename F::R4 v4,
+                                               typename F::R4 w4, typename F::R4 q4, typename F::R im,
+                                               typename F::R4 ii, bool iso, const Scene &sc, V3<typename F::R> Fs,
+                                               V3<typename F::R> Ts, float &disp, float &disp2, float &speed)
+{
+    using R = typename F::R;
+    using R4 = typename F::R4;
+    const int ap = stp->acc_par;
+    const float acc0 = (float)v4.w, acc1 = (float)w4.w;      // acc[0], acc[1]
+    const float acc_a = ap == 0 ? acc0 : acc1, acc_b = ap == 0 ? acc1 : acc0;
+    float a0 = acc_a, a1 = acc_b;
+    const int so = sp ^ 1;
+    V3<R> vn = {v4.x, v4.y, v4.z}, wn = {w4.x, w4.y, w4.z};
+    R qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+    uint8_t active_out = act ? 1 : 0;
+    typename F::Pos pn = po;
+    if (act) {
+        const R h = F::voxel ? (R)sc.hf : (R)sc.h;
+        const V3<R> g = F::voxel ? V3<R>{(R)sc.gf[0], (R)sc.gf[1], (R)sc.gf[2]}
+                                 : V3<R>{(R)sc.g[0], (R)sc.g[1], (R)sc.g[2]};
+        const V3<R> Ft = vadd_rn(Fs, vscale_rn(mass, g));
+        vn = vadd_rn(vn, vscale_rn(h, vscale_rn(im, Ft)));
+        R nw, nx, ny, nz;
+        if (iso) {
+            // isotropic inertia: the body-frame update equals a world-frame one
+            wn = vadd_rn(wn, vscale_rn(h, vscale_rn(ii.x, Ts)));
+            R dw, dx, dy, dz;
+            quat_increment<R>(wn, h, dw, dx, dy, dz);
+            quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+        } else {
+            R m[9];
+            quat_mat_rn<R>(qw, qx, qy, qz, m);
+            V3<R> wb = mat_tvec_rn<R>(m, wn);
+            V3<R> Tb = mat_tvec_rn<R>(m, Ts);
+            V3<R> gyro = {R(0), R(0), R(0)};
+            if (d.gyro) {
+                V3<R> Iw = {rdiv(wb.x, ii.x), rdiv(wb.y, ii.y), rdiv(wb.z, ii.z)};
+                gyro = cross_rn(wb, Iw);
+            }
+            V3<R> dwb = {rmul(ii.x, rsub(Tb.x, gyro.x)), rmul(ii.y, rsub(Tb.y, gyro.y)),
+                         rmul(ii.z, rsub(Tb.z, gyro.z))};
+            wb = vadd_rn(wb, vscale_rn(h, dwb));
+            R dw, dx, dy, dz;
+            quat_increment<R>(wb, h, dw, dx, dy, dz);
+            quat_mul<R>(qw, qx, qy, qz, dw, dx, dy, dz, nw, nx, ny, nz);
+            R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
+            R m2[9];
+            quat_mat_rn<R>(rdiv(nw, qn), rdiv(nx, qn), rdiv(ny, qn), rdiv(nz, qn), m2);
+            wn = mat_vec_rn<R>(m2, wb);
+        }
+        R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
+        qw = rdiv(nw, qn); qx = rdiv(nx, qn); qy = rdiv(ny, qn); qz = rdiv(nz, qn);
+        pn = F::advance(po, vscale_rn(h, vn), d.L);
+        if (sc.has_sink) {
+            V3<double> pa = F::absolute(pn, sc, d.Ld);
+            double side = radd(radd(rmul(rsub(pa.x, sc.sink_p[0]), sc.sink_n[0]),
+                                    rmul(rsub(pa.y, sc.sink_p[1]), sc.sink_n[1])),
+                               rmul(rsub(pa.z, sc.sink_p[2]), sc.sink_n[2]));
+            if (side < 0.0) {
+                active_out = 0;
+                vn = {R(0), R(0), R(0)};
+                wn = {R(0), R(0), R(0)};
+            }
+        }
+        R sv = sqrt(dot_rn(vn, vn));
+        R sw = sqrt(dot_rn(wn, wn));
+        speed = (float)sv;
+        // displacement bound of this step (centre moves h|v|, a component centre at
+        // most h|w| r_ext more) plus the rounding slack of the position update,
+        // accumulated per owner since each list's snapshot
+        const float step_d = radd(rmul((float)rmul(h, radd(sv, rmul(sw, ii.w))), 1.0000005f), stp->disp_slack_f);
+        a0 = acc_a + step_d;
+        a1 = acc_b + step_d;
+        disp = a0;
+        disp2 = a1;
+        if (d.amag) d.amag[o] = (float)rmul(sqrt(dot_rn(Ft, Ft)), im);
+        if constexpr (F::voxel) {
+            if (sc.v_errf > 0.0f && !(sv <= sc.v_errf)) atomicOr(&stp->diverged, 1);
+        } else {
+            if (sc.v_err > 0.0 && !((double)sv <= sc.v_err)) atomicOr(&stp->diverged, 1);
+        }
+        if (!(sv == sv) || !(sw == sw)) atomicOr(&stp->diverged, 1);
+    } else {
+        vn = {R(0), R(0), R(0)};
+        wn = {R(0), R(0), R(0)};
+    }
+    typename F::PosStore pos_out = d.st.pos[so];
+    F::store(pos_out, o, pn, mass);
+    d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, (R)(ap == 0 ? a0 : a1)};
+    d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, (R)(ap == 0 ? a1 : a0)};
+    d.st.quat[so][o] = R4{qw, qx, qy, qz};
+    d.st.active[so][o] = active_out;
+}
+
+// integrate_core with the inputs read from src (global state arrays or a staged tile)
+// and the contact force and torque from the per-owner arrays written by k_contact.
 template <class F, bool CLUMPS>
 __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp, int64_t o, const OwnerSrc<F> &src,
                                                 int64_t i, int sp, float &disp, float &disp2, float &speed)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
-    {
-        // every load of this owner is issued before the first one is used: the thread
-        // waits for one memory round trip, not a chain of them
-        const bool act = src.active[i];
-        const bool has = CLUMPS ? true : src.cnt[i] > 0;
-        R mass;
-        const typename F::Pos po = F::load(src.pos, i, mass);
-        const R4 v4 = src.vel[i], w4 = src.omg[i], q4 = src.quat[i];
-        const R im = src.inv_mass[i];
-        const R4 ii = src.inv_moi[i];
-        const bool iso = CLUMPS ? (bool)src.iso[i] : true;     // a single sphere is isotropic
-        const int ap = stp->acc_par;
-        const float acc0 = (float)v4.w, acc1 = (float)w4.w;      // acc[0], acc[1]
-        const float acc_a = ap == 0 ? acc0 : acc1, acc_b = ap == 0 ? acc1 : acc0;
-        float a0 = acc_a, a1 = acc_b;
-        const Scene &sc = d.scenes[d.n_scenes > 1 ? src.scene[i] : 0];
-        const int so = sp ^ 1;
-        V3<R> vn = {v4.x, v4.y, v4.z}, wn = {w4.x, w4.y, w4.z};
-        R qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
-        uint8_t active_out = act ? 1 : 0;
-        typename F::Pos pn = po;
-        if (act) {
-            const R h = F::voxel ? (R)sc.hf : (R)sc.h;
-            const V3<R> g = F::voxel ? V3<R>{(R)sc.gf[0], (R)sc.gf[1], (R)sc.gf[2]}
-                                     : V3<R>{(R)sc.g[0], (R)sc.g[1], (R)sc.g[2]};
-            V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
-            if (has) {
-                const R4 f4 = d.fo[o], t4 = d.to[o];
-                Fs = {f4.x, f4.y, f4.z};
-                Ts = {t4.x, t4.y, t4.z};
-            }
-            const V3<R> Ft = vadd_rn(Fs, vscale_rn(mass, g));
-            vn = vadd_rn(vn, vscale_rn(h, vscale_rn(im, Ft)));
-            R nw, nx, ny, nz;
-            if (iso) {
-                // isotropic inertia: the body-frame update equals a world-frame one
-                wn = vadd_rn(wn, vscale_rn(h, vscale_rn(ii.x, Ts)));
-                R dw, dx, dy, dz;
-                quat_increment<R>(wn, h, dw, dx, dy, dz);
-                quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
-            } else {
-                R m[9];
-                quat_mat_rn<R>(qw, qx, qy, qz, m);
-                V3<R> wb = mat_tvec_rn<R>(m, wn);
-                V3<R> Tb = mat_tvec_rn<R>(m, Ts);
-                V3<R> gyro = {R(0), R(0), R(0)};
-                if (d.gyro) {
-                    V3<R> Iw = {rdiv(wb.x, ii.x), rdiv(wb.y, ii.y), rdiv(wb.z, ii.z)};
-                    gyro = cross_rn(wb, Iw);
-                }
-                V3<R> dwb = {rmul(ii.x, rsub(Tb.x, gyro.x)), rmul(ii.y, rsub(Tb.y, gyro.y)),
-                             rmul(ii.z, rsub(Tb.z, gyro.z))};
-                wb = vadd_rn(wb, vscale_rn(h, dwb));
-                R dw, dx, dy, dz;
-                quat_increment<R>(wb, h, dw, dx, dy, dz);
-                quat_mul<R>(qw, qx, qy, qz, dw, dx, dy, dz, nw, nx, ny, nz);
-                R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
-                R m2[9];
-                quat_mat_rn<R>(rdiv(nw, qn), rdiv(nx, qn), rdiv(ny, qn), rdiv(nz, qn), m2);
-                wn = mat_vec_rn<R>(m2, wb);
-            }
-            R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
-            qw = rdiv(nw, qn); qx = rdiv(nx, qn); qy = rdiv(ny, qn); qz = rdiv(nz, qn);
-            pn = F::advance(po, vscale_rn(h, vn), d.L);
-            if (sc.has_sink) {
-                V3<double> pa = F::absolute(pn, sc, d.Ld);
-                double side = radd(radd(rmul(rsub(pa.x, sc.sink_p[0]), sc.sink_n[0]),
-                                        rmul(rsub(pa.y, sc.sink_p[1]), sc.sink_n[1])),
-                                   rmul(rsub(pa.z, sc.sink_p[2]), sc.sink_n[2]));
-                if (side < 0.0) {
-                    active_out = 0;
-                    vn = {R(0), R(0), R(0)};
-                    wn = {R(0), R(0), R(0)};
-                }
-            }
-            R sv = sqrt(dot_rn(vn, vn));
-            R sw = sqrt(dot_rn(wn, wn));
-            speed = (float)sv;
-            // displacement bound of this step (centre moves h|v|, a component centre at
-            // most h|w| r_ext more) plus the rounding slack of the position update,
-            // accumulated per owner since each list's snapshot
-            const float step_d = radd(rmul((float)rmul(h, radd(sv, rmul(sw, ii.w))), 1.0000005f), stp->disp_slack_f);
-            a0 = acc_a + step_d;
-            a1 = acc_b + step_d;
-            disp = a0;
-            disp2 = a1;
-            if (d.amag) d.amag[o] = (float)rmul(sqrt(dot_rn(Ft, Ft)), im);
-            if constexpr (F::voxel) {
-                if (sc.v_errf > 0.0f && !(sv <= sc.v_errf)) atomicOr(&stp->diverged, 1);
-            } else {
-                if (sc.v_err > 0.0 && !((double)sv <= sc.v_err)) atomicOr(&stp->diverged, 1);
-            }
-            if (!(sv == sv) || !(sw == sw)) atomicOr(&stp->diverged, 1);
-        } else {
-            vn = {R(0), R(0), R(0)};
-            wn = {R(0), R(0), R(0)};
-        }
-        typename F::PosStore pos_out = d.st.pos[so];
-        F::store(pos_out, o, pn, mass);
-        d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, (R)(ap == 0 ? a0 : a1)};
-        d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, (R)(ap == 0 ? a1 : a0)};
-        d.st.quat[so][o] = R4{qw, qx, qy, qz};
-        d.st.active[so][o] = active_out;
+    // every load of this owner is issued before the first one is used: the thread waits
+    // for one memory round trip, not a chain of them
+    const bool act = src.active[i];
+    const bool has = CLUMPS ? true : src.cnt[i] > 0;
+    R mass;
+    const typename F::Pos po = F::load(src.pos, i, mass);
+    const R4 v4 = src.vel[i], w4 = src.omg[i], q4 = src.quat[i];
+    const R im = src.inv_mass[i];
+    const R4 ii = src.inv_moi[i];
+    const bool iso = CLUMPS ? (bool)src.iso[i] : true;     // a single sphere is isotropic
+    const Scene &sc = d.scenes[d.n_scenes > 1 ? src.scene[i] : 0];
+    V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
+    if (act && has) {
+        const R4 f4 = d.fo[o], t4 = d.to[o];
+        Fs = {f4.x, f4.y, f4.z};
+        Ts = {t4.x, t4.y, t4.z};
     }
+    integrate_core<F, CLUMPS>(d, stp, o, sp, act, po, mass, v4, w4, q4, im, ii, iso, sc, Fs, Ts, disp, disp2, speed);
 }
 
 // One thread per owner, reading its inputs straight from the state arrays.
@@ -1027,6 +1058,61 @@ __global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
         integrate_owner<F, CLUMPS>(d, stp, o, src, o, sp, disp, disp2, speed);
     }
     audit_slots(stp, o, lane, disp, disp2, speed);
+}
+
+// ------------------------------------------------------------------ fused step
+
+// One step of a world of single spheres in one kernel: a thread takes one sphere, sums
+// the contact forces of its listed entries in registers (pair_sums, as k_contact) and
+// integrates its owner at once (integrate_core, as k_integrate) into the other state
+// buffer.  The owner state is read once and no per-owner force array is written or
+// read.  Each block of 256 slots is taken in the order of the list's row-length
+// permutation of that block (written by k_compact), so the lanes of a warp loop over
+// rows of equal length.  Bit-identical to k_contact followed by k_integrate: the same
+// arithmetic in the same order for every sphere.
+constexpr int FUSED_BLOCK_MAX = 256;
+
+template <class F>
+__global__ void __launch_bounds__(FUSED_BLOCK_MAX, 2) k_step_fused(Dev<F> d)
+{
+    using R = typename F::R;
+    using R4 = typename F::R4;
+    DevStatus *stp = d.status;
+    if (stp->halt || stp->list_stale) return;
+    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
+    // perm holds positions within the slot's own 256-block: s stays below Np
+    const int64_t s = g < d.Np ? (g & ~(int64_t)255) + d.lists.perm[lc][g] : d.M;
+    if (s < d.M) {
+        const int n = d.lists.cnt[lc][s];
+        const uint32_t j0 = d.lists.partner[lc][s];      // entry 0 of the row (unused when n = 0)
+        const bool act = d.st.active[sp][s];
+        SphereK<F> me;
+        const typename F::Pos po = F::load(d.st.pos[sp], s, me.mass);
+        const R4 v4 = d.st.vel[sp][s], w4 = d.st.omg[sp][s];
+        const auto pk = d.sph_pack[s];
+        const Scene &sc = d.scenes[d.n_scenes > 1 ? d.owner_scene[s] : 0];
+        me.p = po;
+        me.rl = {R(0), R(0), R(0)};
+        me.v = {v4.x, v4.y, v4.z};
+        me.w = {w4.x, w4.y, w4.z};
+        me.rad = pk.x;
+        if constexpr (F::voxel) {
+            me.rlo = pk.y;
+            me.mat = __float_as_int(pk.z);
+        } else {
+            me.rlo = 0.0f;
+            me.mat = (int)pk.y;
+        }
+        me.owner = (uint32_t)s;
+        V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
+        if (act && n > 0) pair_sums<F, false, MODE_STEP>(d, me, sc, s, n, j0, sp, hp, lc, Fs, Ts);
+        integrate_core<F, false>(d, stp, s, sp, act, po, me.mass, v4, w4, d.st.quat[sp][s], d.inv_mass[s],
+                                 d.inv_moi[s], true, sc, Fs, Ts, disp, disp2, speed);
+    }
+    audit_slots(stp, g, lane, disp, disp2, speed);
 }
 
 // ------------------------------------------------------------------ staged integration
@@ -1199,41 +1285,67 @@ __device__ __forceinline__ int owner_bin(const Dev<F> &d, int sp, int64_t o, con
 
 // Per-bin motion statistics of the active owners: count, sum |v|, sum |v|^2, max |v|,
 // sum |a|, max |a|, sum |w| r_ext, max |w| r_ext, sum of list rows, max list row.  Also
-// records each owner's bin (for labels).  Float atomics: order-dependent last bits only
-// affect the schedule's choice, never the trajectory (lists are audited).
+// records each owner's bin (for labels).  Neighbouring owners mostly share a bin, so each
+// warp first reduces runs of consecutive lanes in the same bin (segmented shuffles) and
+// only the first lane of a run updates the bin: about one set of atomics per run instead
+// of one per owner.  Float atomics: order-dependent last bits only affect the schedule's
+// choice, never the trajectory (lists are audited).
 template <class F>
 __global__ void __launch_bounds__(256) k_bin_stats(Dev<F> d, float *stats, int *obin)
 {
     const int sp = d.status->state_par, lc = d.status->list_cur;
-    int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= d.M) return;
-    const Scene &sc = d.scenes[d.owner_scene[o]];
-    const int b = owner_bin(d, sp, o, sc);
-    obin[o] = b;
-    if (!d.st.active[sp][o]) return;
-    auto v4 = d.st.vel[sp][o];
-    auto w4 = d.st.omg[sp][o];
-    float v = sqrtf((float)(v4.x * v4.x + v4.y * v4.y + v4.z * v4.z));
-    float wr = sqrtf((float)(w4.x * w4.x + w4.y * w4.y + w4.z * w4.z)) * (float)d.inv_moi[o].w;
-    float a = d.amag ? d.amag[o] : 0.0f;
-    float rows = 0.0f, rmax = 0.0f;
-    const int64_t first = d.owner_first[o];
-    for (int c = 0; c < (int)d.owner_nsph[o]; ++c) {     // list rows of the owner's spheres
-        float r = (float)d.lists.cnt[lc][first + c];
-        rows += r;
-        rmax = fmaxf(rmax, r);
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int b = -1;                                   // -1: no contribution (past the end, inactive)
+    float x[NSTAT] = {};
+    if (o < d.M) {
+        const Scene &sc = d.scenes[d.owner_scene[o]];
+        const int bo = owner_bin(d, sp, o, sc);
+        obin[o] = bo;
+        if (d.st.active[sp][o]) {
+            b = bo;
+            auto v4 = d.st.vel[sp][o];
+            auto w4 = d.st.omg[sp][o];
+            float v = sqrtf((float)(v4.x * v4.x + v4.y * v4.y + v4.z * v4.z));
+            float wr = sqrtf((float)(w4.x * w4.x + w4.y * w4.y + w4.z * w4.z)) * (float)d.inv_moi[o].w;
+            float a = d.amag ? d.amag[o] : 0.0f;
+            float rows = 0.0f, rmax = 0.0f;
+            const int64_t first = d.owner_first[o];
+            for (int c = 0; c < (int)d.owner_nsph[o]; ++c) {     // list rows of the owner's spheres
+                float r = (float)d.lists.cnt[lc][first + c];
+                rows += r;
+                rmax = fmaxf(rmax, r);
+            }
+            x[0] = 1.0f; x[1] = v; x[2] = v * v; x[3] = v; x[4] = a; x[5] = a; x[6] = wr; x[7] = wr;
+            x[8] = rows; x[9] = rmax;
+        }
     }
+    // runs of equal bins within the warp: a lane heads a run when its bin differs from the
+    // previous lane's; each lane reduces towards the head over the lanes of its run
+    const int prev = __shfl_up_sync(0xffffffffu, b, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != b);
+    const unsigned above = heads & ~((2u << lane) - 1u);
+    const int end = above ? __ffs(above) - 1 : 32;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int k = 0; k < NSTAT; ++k) {
+            const float y = __shfl_down_sync(0xffffffffu, x[k], off);
+            if (lane + off < end) x[k] = (k == 3 || k == 5 || k == 7 || k == 9) ? fmaxf(x[k], y) : x[k] + y;
+        }
+    }
+    if (b < 0 || !((heads >> lane) & 1u)) return;
     float *st = stats + (int64_t)b * NSTAT;
-    atomicAdd(&st[0], 1.0f);
-    atomicAdd(&st[1], v);
-    atomicAdd(&st[2], v * v);
-    atomicMax(reinterpret_cast<unsigned int *>(&st[3]), __float_as_uint(v));
-    atomicAdd(&st[4], a);
-    atomicMax(reinterpret_cast<unsigned int *>(&st[5]), __float_as_uint(a));
-    atomicAdd(&st[6], wr);
-    atomicMax(reinterpret_cast<unsigned int *>(&st[7]), __float_as_uint(wr));
-    atomicAdd(&st[8], rows);
-    atomicMax(reinterpret_cast<unsigned int *>(&st[9]), __float_as_uint(rmax));
+    atomicAdd(&st[0], x[0]);
+    atomicAdd(&st[1], x[1]);
+    atomicAdd(&st[2], x[2]);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[3]), __float_as_uint(x[3]));
+    atomicAdd(&st[4], x[4]);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[5]), __float_as_uint(x[5]));
+    atomicAdd(&st[6], x[6]);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[7]), __float_as_uint(x[7]));
+    atomicAdd(&st[8], x[8]);
+    atomicMax(reinterpret_cast<unsigned int *>(&st[9]), __float_as_uint(x[9]));
 }
 
 // The 16 features of each bin, made dimensionless with the step h and the margin beta

@@ -132,3 +132,76 @@ def test_staged_integration_is_refused_by_the_fp64_form():
     w = dem.World.from_scene(s, precision="fp64", schedule="every_step")
     w.set_tuning(integrate_staged=1)
     assert w.tuning()["integrate_staged"] == 0
+
+
+@pytest.mark.parametrize("prec", ["voxel_fp32", "fp64"])
+def test_fused_step_is_bit_identical(prec):
+    # one kernel summing each sphere's contact forces in registers and integrating it
+    # against contact forces and integration as two kernels; every block size, switched
+    # in mid-run, both schedules
+    s = W.dense_lattice(n=900, seed=36, vel_sigma=0.3)
+    beta = 5e-5
+    for sched in ("every_step", "velocity_bound"):
+        kw = dict(precision=prec, schedule=sched, margin_max=beta)
+        if sched != "every_step":
+            kw["margin"] = beta
+        a = dem.World.from_scene(s, **kw)
+        a.set_tuning(fused_block=0)
+        for k in (50, 20, 50):              # the same calls as below: the same cycles
+            a.step(k)
+        want = _state(a)
+        # read in the same order for every world: stats() rebuilds a stale list
+        want_pairs = a.listed_pairs()[0].tolist()
+        want_fallbacks = a.stats()["audit_fallbacks"]
+        for fb in (64, 128, 256):
+            b = dem.World.from_scene(s, **kw)
+            b.set_tuning(fused_block=fb)
+            assert b.tuning()["fused_block"] == fb
+            b.step(50)
+            b.set_tuning(fused_block=0)
+            b.step(20)
+            b.set_tuning(fused_block=fb)
+            b.step(50)
+            for x, y in zip(_state(b), want):
+                assert np.array_equal(x, y)
+            assert b.listed_pairs()[0].tolist() == want_pairs
+            assert b.stats()["audit_fallbacks"] == want_fallbacks
+
+
+def test_fused_step_with_a_sink_and_walls_is_bit_identical():
+    s = W.cone_bed(n=300, seed=13)        # some spheres pass the sink within 900 steps
+    a = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    b = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    a.set_tuning(fused_block=0)
+    b.set_tuning(fused_block=128)
+    a.step(900)
+    b.step(900)
+    sa, sb = _state(a), _state(b)
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+    removed = np.all(sa[2] == 0.0, axis=1) & np.all(sa[3] == 0.0, axis=1)
+    assert removed.sum() > 0                # removed spheres keep zero velocities
+    ca, cb = a.contacts(), b.contacts()
+    for k in ("i", "j", "force"):
+        assert np.array_equal(ca[k], cb[k])
+
+
+def test_fused_step_in_a_batch_and_ignored_for_clumps():
+    scenes = [W.dense_lattice(n=150 + 97 * k, seed=45 + k, vel_sigma=0.3) for k in range(3)]
+    beta = 5e-5
+    p = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    q = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    p.initialize()
+    q.initialize()
+    p.worlds[0].set_tuning(fused_block=0)
+    q.worlds[0].set_tuning(fused_block=256)
+    p.step(60)
+    q.step(60)
+    for wp, wq in zip(p.worlds, q.worlds):
+        for x, y in zip(_state(wp), _state(wq)):
+            assert np.array_equal(x, y)
+    c = dem.World.from_scene(W.packed_clumps(n=100, seed=38), precision="voxel_fp32", schedule="every_step")
+    c.set_tuning(fused_block=128)
+    assert c.tuning()["fused_block"] == 0
+    with pytest.raises(Exception):
+        c.set_tuning(fused_block=96)
