@@ -201,6 +201,7 @@ struct FormF64 {
     static constexpr bool voxel = false;
     // owner position storage: double4_32a (x, y, z, mass)
     struct PosStore { double4_32a *xm; };
+    struct Aux {};              // nothing rides along with the position in this form
 
     __device__ static Pos load(const PosStore &s, int64_t o, R &mass)
     {
@@ -208,7 +209,11 @@ struct FormF64 {
         mass = a.w;
         return Pos{a.x, a.y, a.z};
     }
-    __device__ static void store(PosStore &s, int64_t o, Pos p, R mass) { s.xm[o] = make_double4_32a(p.x, p.y, p.z, mass); }
+    __device__ static Pos load(const PosStore &s, int64_t o, R &mass, Aux &) { return load(s, o, mass); }
+    __device__ static void store(PosStore &s, int64_t o, Pos p, R mass, const Aux & = Aux{})
+    {
+        s.xm[o] = make_double4_32a(p.x, p.y, p.z, mass);
+    }
     // a - b, exactly rounded component-wise
     __device__ static V3<R> diff(const Pos &a, const Pos &b, float /*L*/)
     {
@@ -230,23 +235,40 @@ struct FormF32 {
     using R4 = float4;
     using Pos = PosF32;
     static constexpr bool voxel = true;
-    // owner position storage: packed voxel + float4 (offset, mass)
-    struct PosStore { uint64_t *vox; float4 *om; };
+    // owner position storage: one 32-byte record per owner (one DRAM sector): offset and
+    // mass, the packed voxel index, and for a single sphere its radius as a float-float
+    // pair (the sphere's constants travel with its position, so a partner's gather reads
+    // one sector; for clumps the two words are unused)
+    struct PosRec {
+        float4 om;              // offset x, y, z, mass
+        uint4 vr;               // voxel index (low, high word), radius, radius low word (bits)
+    };
+    struct PosStore { PosRec *rec; };
+    struct Aux { float rad, rlo; };
 
-    __device__ static Pos load(const PosStore &s, int64_t o, R &mass)
+    __device__ static Pos load(const PosStore &s, int64_t o, R &mass, Aux &aux)
     {
-        uint64_t v = s.vox[o];
-        float4 a = s.om[o];
+        const float4 a = s.rec[o].om;
+        const uint4 b = s.rec[o].vr;
         Pos p;
-        unpack_vox(v, p.cx, p.cy, p.cz);
+        unpack_vox((uint64_t)b.x | ((uint64_t)b.y << 32), p.cx, p.cy, p.cz);
         p.x = a.x; p.y = a.y; p.z = a.z;
         mass = a.w;
+        aux.rad = __uint_as_float(b.z);
+        aux.rlo = __uint_as_float(b.w);
         return p;
     }
-    __device__ static void store(PosStore &s, int64_t o, Pos p, R mass)
+    __device__ static Pos load(const PosStore &s, int64_t o, R &mass)
     {
-        s.vox[o] = pack_vox(p.cx, p.cy, p.cz);
-        s.om[o] = make_float4(p.x, p.y, p.z, mass);
+        Aux aux;
+        return load(s, o, mass, aux);
+    }
+    // the whole record is written (no partially written sector)
+    __device__ static void store(PosStore &s, int64_t o, Pos p, R mass, const Aux &aux)
+    {
+        const uint64_t v = pack_vox(p.cx, p.cy, p.cz);
+        s.rec[o].om = make_float4(p.x, p.y, p.z, mass);
+        s.rec[o].vr = make_uint4((uint32_t)v, (uint32_t)(v >> 32), __float_as_uint(aux.rad), __float_as_uint(aux.rlo));
     }
     // (ca - cb) * L + (oa - ob): the integer part is exact, then two rounded operations
     __device__ static V3<R> diff(const Pos &a, const Pos &b, float L)

@@ -96,13 +96,11 @@ public:
         // owner state, double-buffered
         for (int b = 0; b < 2; ++b) {
             if constexpr (F::voxel) {
-                if ((s = alloc(d_.st.pos[b].vox, Mp, err))) return s;
-                if ((s = alloc(d_.st.pos[b].om, Mp, err))) return s;
+                if ((s = alloc(d_.st.pos[b].rec, Mp, err))) return s;
             } else {
                 if ((s = alloc(d_.st.pos[b].xm, M, err))) return s;
             }
-            if ((s = alloc(d_.st.vel[b], Mp, err))) return s;
-            if ((s = alloc(d_.st.omg[b], Mp, err))) return s;
+            if ((s = alloc(d_.st.kv[b], 2 * Mp, err))) return s;
             if ((s = alloc(d_.st.quat[b], Mp, err))) return s;
             if ((s = alloc(d_.st.active[b], Mp, err))) return s;
         }
@@ -230,11 +228,24 @@ public:
         if ((s = up(ms, m_.mat_scene.data(), m_.mat_scene.size(), err))) return s;
         if ((s = up(ml, m_.mat_local.data(), m_.mat_local.size(), err))) return s;
 
-        // mass into the position store of buffer 0, then the state through the upload kernel
+        // mass into the position store of buffer 0, then the state through the upload kernel;
+        // in the voxel form a single sphere's radius (float-float) rides in both buffers'
+        // records from here on
         if constexpr (F::voxel) {
-            std::vector<float4> om(M);
-            for (int64_t o = 0; o < M; ++o) om[o] = make_float4(0.f, 0.f, 0.f, (float)m_.mass[o]);
-            if ((s = up(d_.st.pos[0].om, om.data(), M, err))) return s;
+            using PR = typename F::PosRec;
+            std::vector<PR> rec(M);
+            for (int64_t o = 0; o < M; ++o) {
+                uint32_t rb = 0, lb = 0;
+                if (!m_.clumps) {
+                    const float r = (float)rad[o], l = rlo[o];
+                    std::memcpy(&rb, &r, 4);
+                    std::memcpy(&lb, &l, 4);
+                }
+                rec[o].om = make_float4(0.f, 0.f, 0.f, (float)m_.mass[o]);
+                rec[o].vr = make_uint4(0u, 0u, rb, lb);
+            }
+            if ((s = up(d_.st.pos[0].rec, rec.data(), M, err))) return s;
+            if ((s = up(d_.st.pos[1].rec, rec.data(), M, err))) return s;
         } else {
             std::vector<double4_32a> xm(M);
             for (int64_t o = 0; o < M; ++o) xm[o] = make_double4_32a(0.0, 0.0, 0.0, m_.mass[o]);
@@ -612,7 +623,7 @@ public:
             blob.resize(o + n);
             std::memcpy(blob.data() + o, p, n);
         };
-        uint64_t magic = 0x44454d4742333030ull;   // "DEMGB300"
+        uint64_t magic = 0x44454d4742333031ull;   // "DEMGB301": 32-byte position records
         put(&magic, 8);
         int64_t hdr[6] = {M, d_.N, d_.Np, d_.K, (int64_t)F::voxel, (int64_t)sizeof(R)};
         put(hdr, sizeof(hdr));
@@ -624,13 +635,11 @@ public:
             return DEM_OK;
         };
         if constexpr (F::voxel) {
-            if ((s = dput(d_.st.pos[sp].vox, M * 8))) return s;
-            if ((s = dput(d_.st.pos[sp].om, M * 16))) return s;
+            if ((s = dput(d_.st.pos[sp].rec, M * 32))) return s;
         } else {
             if ((s = dput(d_.st.pos[sp].xm, M * 32))) return s;
         }
-        if ((s = dput(d_.st.vel[sp], M * sizeof(R4)))) return s;
-        if ((s = dput(d_.st.omg[sp], M * sizeof(R4)))) return s;
+        if ((s = dput(d_.st.kv[sp], 2 * M * sizeof(R4)))) return s;
         if ((s = dput(d_.st.quat[sp], M * sizeof(R4)))) return s;
         if ((s = dput(d_.st.active[sp], M))) return s;
         if ((s = dput(d_.lists.partner[lc], ne * 4))) return s;
@@ -653,7 +662,7 @@ public:
         uint64_t magic;
         int64_t hdr[6];
         DevStatus h;
-        if (!get(&magic, 8) || magic != 0x44454d4742333030ull || !get(hdr, sizeof(hdr)) || !get(&h, sizeof(h))) {
+        if (!get(&magic, 8) || magic != 0x44454d4742333031ull || !get(hdr, sizeof(hdr)) || !get(&h, sizeof(h))) {
             err = "not a state blob";
             return DEM_ERR_ARG;
         }
@@ -677,13 +686,11 @@ public:
             return DEM_OK;
         };
         if constexpr (F::voxel) {
-            if ((s = dget(d_.st.pos[sp].vox, M * 8))) return s;
-            if ((s = dget(d_.st.pos[sp].om, M * 16))) return s;
+            if ((s = dget(d_.st.pos[sp].rec, M * 32))) return s;
         } else {
             if ((s = dget(d_.st.pos[sp].xm, M * 32))) return s;
         }
-        if ((s = dget(d_.st.vel[sp], M * sizeof(R4)))) return s;
-        if ((s = dget(d_.st.omg[sp], M * sizeof(R4)))) return s;
+        if ((s = dget(d_.st.kv[sp], 2 * M * sizeof(R4)))) return s;
         if ((s = dget(d_.st.quat[sp], M * sizeof(R4)))) return s;
         if ((s = dget(d_.st.active[sp], M))) return s;
         if ((s = dget(d_.lists.partner[lc], ne * 4))) return s;
@@ -1077,8 +1084,7 @@ private:
             return false;
         } else {
             if (staged_per_sm_ > 0) return true;
-            const void *ptrs[] = {d_.st.pos[0].vox, d_.st.pos[1].vox, d_.st.pos[0].om, d_.st.pos[1].om,
-                                  d_.st.vel[0], d_.st.vel[1], d_.st.omg[0], d_.st.omg[1], d_.st.quat[0],
+            const void *ptrs[] = {d_.st.pos[0].rec, d_.st.pos[1].rec, d_.st.kv[0], d_.st.kv[1], d_.st.quat[0],
                                   d_.st.quat[1], d_.st.active[0], d_.st.active[1], d_.inv_moi, d_.inv_mass,
                                   d_.owner_scene, d_.owner_iso, d_.lists.cnt[0], d_.lists.cnt[1]};
             for (const void *p : ptrs)

@@ -59,7 +59,9 @@ struct ListBuffers {
 template <class F>
 struct StateBuffers {
     typename F::PosStore pos[2];
-    typename F::R4 *vel[2], *omg[2], *quat[2];
+    // linear and angular velocity of owner o side by side, kv[2o] = (v, acc[0]) and
+    // kv[2o + 1] = (w, acc[1]): one 32-byte sector per owner in the voxel form
+    typename F::R4 *kv[2], *quat[2];
     uint8_t *active[2];
 };
 

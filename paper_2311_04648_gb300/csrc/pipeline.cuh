@@ -105,7 +105,10 @@ struct SphereK {
     uint32_t owner;
 };
 
-template <class F, bool CLUMPS>
+// MAT false: the material is left at -1 where it would need a load of its own (a single
+// sphere in the voxel form, whose other constants ride in its position record); the
+// caller reads it only if the scene has several materials.
+template <class F, bool CLUMPS, bool MAT = true>
 __device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint32_t s)
 {
     using R = typename F::R;
@@ -114,21 +117,28 @@ __device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint3
     uint32_t o = CLUMPS ? d.sph_owner[s] : s;
     k.owner = o;
     R mass;
-    typename F::Pos po = F::load(d.st.pos[sp], o, mass);
-    auto v4 = d.st.vel[sp][o];
-    auto w4 = d.st.omg[sp][o];
+    typename F::Aux aux;
+    typename F::Pos po = F::load(d.st.pos[sp], o, mass, aux);
+    auto v4 = d.st.kv[sp][2 * o];
+    auto w4 = d.st.kv[sp][2 * o + 1];
     k.v = {v4.x, v4.y, v4.z};
     k.w = {w4.x, w4.y, w4.z};
     k.mass = mass;
-    const auto pk = d.sph_pack[s];
-    if constexpr (F::voxel) {
-        k.rad = pk.x;
-        k.rlo = pk.y;
-        k.mat = __float_as_int(pk.z);
+    if constexpr (F::voxel && !CLUMPS) {
+        k.rad = aux.rad;
+        k.rlo = aux.rlo;
+        k.mat = MAT ? (int)d.sph_mat[s] : -1;
     } else {
-        k.rad = pk.x;
-        k.rlo = 0.0f;
-        k.mat = (int)pk.y;
+        const auto pk = d.sph_pack[s];
+        if constexpr (F::voxel) {
+            k.rad = pk.x;
+            k.rlo = pk.y;
+            k.mat = __float_as_int(pk.z);
+        } else {
+            k.rad = pk.x;
+            k.rlo = 0.0f;
+            k.mat = (int)pk.y;
+        }
     }
     if (CLUMPS) {
         auto q = d.st.quat[sp][o];
@@ -162,7 +172,7 @@ __device__ __forceinline__ V3<R> point_velocity(V3<R> v, V3<R> w, V3<R> r)
 // negation, so B's thread, calling with the roles exchanged (and its copy of the history,
 // the negation of A's), obtains exactly the negated force: no canonical reordering.  False if the
 // overlap is not positive.
-template <class F>
+template <class F, bool PARAMS = true>
 __device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
                                                ContactIn<typename F::R> &c, V3<typename F::R> &armA,
                                                V3<typename F::R> &armB)
@@ -189,12 +199,13 @@ __device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F>
     c.uB = point_velocity(B.v, B.w, armB);
     c.Rbar = (A.rad * B.rad) / (A.rad + B.rad);
     c.mbar = (A.mass * B.mass) / (A.mass + B.mass);
-    load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, B.mat, c);
+    if constexpr (PARAMS) load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, B.mat, c);
     return true;
 }
 
-// Sphere-wall contact (B = wall of infinite radius and mass), geometry in FP64.
-template <class F>
+// Sphere-wall contact (B = wall of infinite radius and mass), geometry in FP64.  With
+// PARAMS false the caller fills the material constants of c.
+template <class F, bool PARAMS = true>
 __device__ __forceinline__ bool wall_contact(const Dev<F> &d, const SphereK<F> &A, const Scene &sc, const Wall &w,
                                              ContactIn<typename F::R> &c, V3<typename F::R> &armA,
                                              V3<double> *point = nullptr)
@@ -226,7 +237,7 @@ __device__ __forceinline__ bool wall_contact(const Dev<F> &d, const SphereK<F> &
             c.uB = {0.0f, 0.0f, 0.0f};
             c.Rbar = A.rad;
             c.mbar = A.mass;
-            load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
+            if constexpr (PARAMS) load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
             if (point) {
                 // read-backs: the contact point in FP64 (the force above is the step's)
                 const V3<double> pa = F::absolute(A.p, sc, d.Ld);
@@ -259,7 +270,7 @@ __device__ __forceinline__ bool wall_contact(const Dev<F> &d, const SphereK<F> &
     c.uB = {(R)vw.x, (R)vw.y, (R)vw.z};
     c.Rbar = A.rad;
     c.mbar = A.mass;
-    load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
+    if constexpr (PARAMS) load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, w.mat, c);
     return true;
 }
 
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
     uint32_t o = d.sph_owner[s];
     if (o != 0xffffffffu && d.sph_head[s]) {
         // the next list's bound starts at zero (the lane of the state the next step reads)
-        typename F::R4 *lane = (stp->acc_par ^ 1) == 0 ? &d.st.vel[sp][o] : &d.st.omg[sp][o];
+        typename F::R4 *lane = (stp->acc_par ^ 1) == 0 ? &d.st.kv[sp][2 * o] : &d.st.kv[sp][2 * o + 1];
         lane->w = typename F::R(0);
     }
     uint32_t key = b.n_cells_total;
@@ -735,9 +746,25 @@ __device__ __forceinline__ void quat_mul(R aw, R ax, R ay, R az, R bw, R bx, R b
 constexpr int CONTACT_BLOCK_MAX = 128;   // launch shapes are tuned at run time up to these
 constexpr int INTEGRATE_BLOCK_MAX = 512;
 
+// Pairwise material constants of the form's precision.
+template <class F>
+__device__ __forceinline__ const PairParamF *pair_table(const Dev<F> &d, float)
+{
+    return d.pairs_f;
+}
+template <class F>
+__device__ __forceinline__ const PairParam *pair_table(const Dev<F> &d, double)
+{
+    return d.pairs;
+}
+
 // The n listed entries of sphere s (first partner j_first) evaluated from s's side: the
 // sums of the contact forces on s and of their torques about its owner's centre, and
-// (MODE_STEP) each entry's updated history written to the other history buffer.
+// (MODE_STEP) each entry's updated history written to the other history buffer.  Every
+// load of an entry (history, partner state, the partner's flag) is issued before any is
+// used, so an entry costs one memory round trip; the material constants come from the
+// sphere's own scene (both bodies of a contact belong to it), without a lookup of the
+// partner's material where the scene has only one.
 template <class F, bool CLUMPS, int MODE>
 __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me, const Scene &sc, int64_t s, int n,
                                           uint32_t j_first, int sp, int hp, int lc, V3<typename F::R> &Fs,
@@ -750,36 +777,41 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
     const H *hin = d.lists.hist[hp];
     H *hout = d.lists.hist[hp ^ 1];
     const V3<R> zero = {R(0), R(0), R(0)};
+    const auto *tab = pair_table(d, R(0));
+    const bool one = sc.n_mat == 1;
+    const int row = sc.pair_base + (me.mat - sc.mat_base) * sc.n_mat - sc.mat_base;
     uint32_t j_next = j_first;
     for (int k = 0; k < n; ++k) {
         const int64_t e = (int64_t)k * d.Np + s;
         const uint32_t j = j_next;
         if (k + 1 < n) j_next = prow[e + d.Np];      // next partner's id in flight early
+        V3<R> ut = hist_get<H, R>(hin, e);
         ContactIn<R> c;
         V3<R> armA, armB;
+        bool on;
+        int mb;
         if (j & WALL_BIT) {
-            V3<R> ut = hist_get<H, R>(hin, e);
-            V3<R> Fc;
-            bool on = wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA);
-            if (on) {
-                hertz_mindlin<R>(c, h, ut, Fc);
-                Fs = Fs + Fc;
-                Ts = Ts + cross(armA, Fc);
+            const Wall &w = d.walls[j & ~WALL_BIT];
+            mb = w.mat;
+            on = wall_contact<F, false>(d, me, sc, w, c, armA);
+        } else {
+            SphereK<F> other = load_sphere<F, CLUMPS, false>(d, sp, j);
+            if (!d.st.active[sp][other.owner]) {
+                if (MODE == MODE_STEP) hist_put(hout, e, zero);
+                continue;
             }
-            if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
-            continue;
+            // the pair is evaluated in this thread's own orientation with this side's
+            // copy of the history (the partner's copy is its exact negation)
+            mb = other.mat >= 0 || one ? other.mat : (int)d.sph_mat[j];
+            on = sphere_contact<F, false>(d, me, other, c, armA, armB);
         }
-        SphereK<F> other = load_sphere<F, CLUMPS>(d, sp, j);
-        if (!d.st.active[sp][other.owner]) {
-            if (MODE == MODE_STEP) hist_put(hout, e, zero);
-            continue;
-        }
-        // the pair is evaluated in this thread's own orientation with this side's copy
-        // of the history (the partner's copy is its exact negation)
-        V3<R> ut = hist_get<H, R>(hin, e);
-        V3<R> Fc;
-        bool on = sphere_contact<F>(d, me, other, c, armA, armB);
         if (on) {
+            const auto p = tab[one ? sc.pair_base : row + mb];
+            c.Estar = p.Estar;
+            c.Gstar = p.Gstar;
+            c.beta = p.beta;
+            c.mu = p.mu;
+            V3<R> Fc;
             hertz_mindlin<R>(c, h, ut, Fc);
             Fs = Fs + Fc;
             Ts = Ts + cross(armA, Fc);
@@ -907,7 +939,7 @@ __device__ __forceinline__ void audit_slots(DevStatus *stp, int64_t o, int lane,
 template <class F>
 struct OwnerSrc {
     typename F::PosStore pos;
-    const typename F::R4 *vel, *omg, *quat, *inv_moi;
+    const typename F::R4 *kv, *quat, *inv_moi;      // kv: v and w of owner i at 2i, 2i + 1
     const typename F::R *inv_mass;
     const uint8_t *active, *cnt, *iso;
     const uint16_t *scene;
@@ -923,7 +955,8 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
                                                const typename F::Pos &po, typename F::R mass, typename F::R4 v4,
                                                typename F::R4 w4, typename F::R4 q4, typename F::R im,
                                                typename F::R4 ii, bool iso, const Scene &sc, V3<typename F::R> Fs,
-                                               V3<typename F::R> Ts, float &disp, float &disp2, float &speed)
+                                               V3<typename F::R> Ts, const typename F::Aux &aux, float &disp,
+                                               float &disp2, float &speed)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
@@ -1007,9 +1040,9 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
         wn = {R(0), R(0), R(0)};
     }
     typename F::PosStore pos_out = d.st.pos[so];
-    F::store(pos_out, o, pn, mass);
-    d.st.vel[so][o] = R4{vn.x, vn.y, vn.z, (R)(ap == 0 ? a0 : a1)};
-    d.st.omg[so][o] = R4{wn.x, wn.y, wn.z, (R)(ap == 0 ? a1 : a0)};
+    F::store(pos_out, o, pn, mass, aux);
+    d.st.kv[so][2 * o] = R4{vn.x, vn.y, vn.z, (R)(ap == 0 ? a0 : a1)};
+    d.st.kv[so][2 * o + 1] = R4{wn.x, wn.y, wn.z, (R)(ap == 0 ? a1 : a0)};
     d.st.quat[so][o] = R4{qw, qx, qy, qz};
     d.st.active[so][o] = active_out;
 }
@@ -1027,8 +1060,9 @@ __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp,
     const bool act = src.active[i];
     const bool has = CLUMPS ? true : src.cnt[i] > 0;
     R mass;
-    const typename F::Pos po = F::load(src.pos, i, mass);
-    const R4 v4 = src.vel[i], w4 = src.omg[i], q4 = src.quat[i];
+    typename F::Aux aux;
+    const typename F::Pos po = F::load(src.pos, i, mass, aux);
+    const R4 v4 = src.kv[2 * i], w4 = src.kv[2 * i + 1], q4 = src.quat[i];
     const R im = src.inv_mass[i];
     const R4 ii = src.inv_moi[i];
     const bool iso = CLUMPS ? (bool)src.iso[i] : true;     // a single sphere is isotropic
@@ -1039,7 +1073,8 @@ __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp,
         Fs = {f4.x, f4.y, f4.z};
         Ts = {t4.x, t4.y, t4.z};
     }
-    integrate_core<F, CLUMPS>(d, stp, o, sp, act, po, mass, v4, w4, q4, im, ii, iso, sc, Fs, Ts, disp, disp2, speed);
+    integrate_core<F, CLUMPS>(d, stp, o, sp, act, po, mass, v4, w4, q4, im, ii, iso, sc, Fs, Ts, aux, disp, disp2,
+                              speed);
 }
 
 // One thread per owner, reading its inputs straight from the state arrays.
@@ -1053,7 +1088,7 @@ __global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
     const int lane = threadIdx.x & 31;
     float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
     if (o < d.M) {
-        OwnerSrc<F> src{d.st.pos[sp], d.st.vel[sp], d.st.omg[sp], d.st.quat[sp], d.inv_moi, d.inv_mass,
+        OwnerSrc<F> src{d.st.pos[sp], d.st.kv[sp], d.st.quat[sp], d.inv_moi, d.inv_mass,
                         d.st.active[sp], d.lists.cnt[lc], d.owner_iso, d.owner_scene};
         integrate_owner<F, CLUMPS>(d, stp, o, src, o, sp, disp, disp2, speed);
     }
@@ -1090,19 +1125,23 @@ __global__ void __launch_bounds__(FUSED_BLOCK_MAX, 2) k_step_fused(Dev<F> d)
         const uint32_t j0 = d.lists.partner[lc][s];      // entry 0 of the row (unused when n = 0)
         const bool act = d.st.active[sp][s];
         SphereK<F> me;
-        const typename F::Pos po = F::load(d.st.pos[sp], s, me.mass);
-        const R4 v4 = d.st.vel[sp][s], w4 = d.st.omg[sp][s];
-        const auto pk = d.sph_pack[s];
+        typename F::Aux aux;
+        const typename F::Pos po = F::load(d.st.pos[sp], s, me.mass, aux);
+        const R4 v4 = d.st.kv[sp][2 * s], w4 = d.st.kv[sp][2 * s + 1];
         const Scene &sc = d.scenes[d.n_scenes > 1 ? d.owner_scene[s] : 0];
         me.p = po;
         me.rl = {R(0), R(0), R(0)};
         me.v = {v4.x, v4.y, v4.z};
         me.w = {w4.x, w4.y, w4.z};
-        me.rad = pk.x;
         if constexpr (F::voxel) {
-            me.rlo = pk.y;
-            me.mat = __float_as_int(pk.z);
+            // the radius rides in the position record; the material is needed only
+            // where the scene has several
+            me.rad = aux.rad;
+            me.rlo = aux.rlo;
+            me.mat = sc.n_mat == 1 ? sc.mat_base : (int)d.sph_mat[s];
         } else {
+            const auto pk = d.sph_pack[s];
+            me.rad = pk.x;
             me.rlo = 0.0f;
             me.mat = (int)pk.y;
         }
@@ -1110,7 +1149,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK_MAX, 2) k_step_fused(Dev<F> d)
         V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
         if (act && n > 0) pair_sums<F, false, MODE_STEP>(d, me, sc, s, n, j0, sp, hp, lc, Fs, Ts);
         integrate_core<F, false>(d, stp, s, sp, act, po, me.mass, v4, w4, d.st.quat[sp][s], d.inv_mass[s],
-                                 d.inv_moi[s], true, sc, Fs, Ts, disp, disp2, speed);
+                                 d.inv_moi[s], true, sc, Fs, Ts, aux, disp, disp2, speed);
     }
     audit_slots(stp, g, lane, disp, disp2, speed);
 }
@@ -1124,11 +1163,9 @@ __global__ void __launch_bounds__(FUSED_BLOCK_MAX, 2) k_step_fused(Dev<F> d)
 // whole tiles so every copy is a full, 16-byte-aligned tile).
 constexpr int ITILE = 256;
 struct StageLayout {                                        // byte offsets within a stage
-    static constexpr int vox = 0;                           // u64 voxel index
-    static constexpr int om = vox + 8 * ITILE;              // float4 offset, mass
-    static constexpr int vel = om + 16 * ITILE;             // float4 v, acc[0]
-    static constexpr int omg = vel + 16 * ITILE;            // float4 w, acc[1]
-    static constexpr int quat = omg + 16 * ITILE;           // float4 q
+    static constexpr int rec = 0;                           // 32-byte position records
+    static constexpr int kv = rec + 32 * ITILE;             // float4 (v, acc[0]), (w, acc[1])
+    static constexpr int quat = kv + 32 * ITILE;            // float4 q
     static constexpr int moi = quat + 16 * ITILE;           // float4 1/I, r_ext
     static constexpr int imass = moi + 16 * ITILE;          // float 1/m
     static constexpr int active = imass + 4 * ITILE;        // u8
@@ -1163,10 +1200,8 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
         const int64_t o0 = tile * ITILE;
         fence_proxy_async_shared();
         mbar_arrive_expect_tx(&bar[st], tile_bytes);
-        bulk_g2s(b + StageLayout::vox, d.st.pos[sp].vox + o0, 8 * ITILE, &bar[st]);
-        bulk_g2s(b + StageLayout::om, d.st.pos[sp].om + o0, 16 * ITILE, &bar[st]);
-        bulk_g2s(b + StageLayout::vel, d.st.vel[sp] + o0, 16 * ITILE, &bar[st]);
-        bulk_g2s(b + StageLayout::omg, d.st.omg[sp] + o0, 16 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::rec, d.st.pos[sp].rec + o0, 32 * ITILE, &bar[st]);
+        bulk_g2s(b + StageLayout::kv, d.st.kv[sp] + 2 * o0, 32 * ITILE, &bar[st]);
         bulk_g2s(b + StageLayout::quat, d.st.quat[sp] + o0, 16 * ITILE, &bar[st]);
         bulk_g2s(b + StageLayout::moi, d.inv_moi + o0, 16 * ITILE, &bar[st]);
         bulk_g2s(b + StageLayout::imass, d.inv_mass + o0, 4 * ITILE, &bar[st]);
@@ -1208,10 +1243,8 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
         float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
         if (o < d.M) {
             const uint8_t *flags = b + StageLayout::flags;
-            OwnerSrc<F> src{F::PosStore{reinterpret_cast<uint64_t *>(b + StageLayout::vox),
-                                        reinterpret_cast<float4 *>(b + StageLayout::om)},
-                            reinterpret_cast<const float4 *>(b + StageLayout::vel),
-                            reinterpret_cast<const float4 *>(b + StageLayout::omg),
+            OwnerSrc<F> src{F::PosStore{reinterpret_cast<F::PosRec *>(b + StageLayout::rec)},
+                            reinterpret_cast<const float4 *>(b + StageLayout::kv),
                             reinterpret_cast<const float4 *>(b + StageLayout::quat),
                             reinterpret_cast<const float4 *>(b + StageLayout::moi),
                             reinterpret_cast<const float *>(b + StageLayout::imass),
@@ -1304,8 +1337,8 @@ __global__ void __launch_bounds__(256) k_bin_stats(Dev<F> d, float *stats, int *
         obin[o] = bo;
         if (d.st.active[sp][o]) {
             b = bo;
-            auto v4 = d.st.vel[sp][o];
-            auto w4 = d.st.omg[sp][o];
+            auto v4 = d.st.kv[sp][2 * o];
+            auto w4 = d.st.kv[sp][2 * o + 1];
             float v = sqrtf((float)(v4.x * v4.x + v4.y * v4.y + v4.z * v4.z));
             float wr = sqrtf((float)(w4.x * w4.x + w4.y * w4.y + w4.z * w4.z)) * (float)d.inv_moi[o].w;
             float a = d.amag ? d.amag[o] : 0.0f;
@@ -1396,8 +1429,8 @@ __global__ void __launch_bounds__(256) k_collect_step(Dev<F> d, float *acc_lab, 
     const int sp = stp->state_par;
     if (!d.st.active[sp][o]) return;
     const Scene &sc = d.scenes[d.owner_scene[o]];
-    auto v4 = d.st.vel[sp][o];
-    auto w4 = d.st.omg[sp][o];
+    auto v4 = d.st.kv[sp][2 * o];
+    auto w4 = d.st.kv[sp][2 * o + 1];
     float v = sqrtf((float)(v4.x * v4.x + v4.y * v4.y + v4.z * v4.z));
     float w = sqrtf((float)(w4.x * w4.x + w4.y * w4.y + w4.z * w4.z));
     float a0 = acc_lab[o];
@@ -1539,9 +1572,9 @@ __global__ void k_owner_download(Dev<F> d, int64_t first, int64_t n, double *x, 
     x[3 * k] = pa.x; x[3 * k + 1] = pa.y; x[3 * k + 2] = pa.z;
     auto q4 = d.st.quat[sp][o];
     q[4 * k] = q4.x; q[4 * k + 1] = q4.y; q[4 * k + 2] = q4.z; q[4 * k + 3] = q4.w;
-    auto v4 = d.st.vel[sp][o];
+    auto v4 = d.st.kv[sp][2 * o];
     v[3 * k] = v4.x; v[3 * k + 1] = v4.y; v[3 * k + 2] = v4.z;
-    auto w4 = d.st.omg[sp][o];
+    auto w4 = d.st.kv[sp][2 * o + 1];
     R m[9];
     quat_mat<R>(q4.x, q4.y, q4.z, q4.w, m);
     V3<R> wb = mat_tvec<R>(m, V3<R>{w4.x, w4.y, w4.z});
@@ -1562,7 +1595,8 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
     int64_t o = first + k;
     const int sp = d.status->state_par;
     R mass;
-    typename F::Pos p = F::load(d.st.pos[sp], o, mass);
+    typename F::Aux aux;
+    typename F::Pos p = F::load(d.st.pos[sp], o, mass, aux);
     const Scene &sc = d.scenes[d.owner_scene[o]];
     if (x) {
         if constexpr (F::voxel) {
@@ -1579,19 +1613,19 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
         } else {
             p.x = x[3 * k]; p.y = x[3 * k + 1]; p.z = x[3 * k + 2];
         }
-        F::store(d.st.pos[sp], o, p, mass);
+        F::store(d.st.pos[sp], o, p, mass, aux);
     }
     R4 q4 = d.st.quat[sp][o];
     if (q) {
         q4 = R4{(R)q[4 * k], (R)q[4 * k + 1], (R)q[4 * k + 2], (R)q[4 * k + 3]};
         d.st.quat[sp][o] = q4;
     }
-    if (v) d.st.vel[sp][o] = R4{(R)v[3 * k], (R)v[3 * k + 1], (R)v[3 * k + 2], R(0)};
+    if (v) d.st.kv[sp][2 * o] = R4{(R)v[3 * k], (R)v[3 * k + 1], (R)v[3 * k + 2], R(0)};
     if (w) {
         double m[9];
         quat_mat<double>((double)q4.x, (double)q4.y, (double)q4.z, (double)q4.w, m);
         V3<double> wg = mat_vec<double>(m, V3<double>{w[3 * k], w[3 * k + 1], w[3 * k + 2]});
-        d.st.omg[sp][o] = R4{(R)wg.x, (R)wg.y, (R)wg.z, R(0)};
+        d.st.kv[sp][2 * o + 1] = R4{(R)wg.x, (R)wg.y, (R)wg.z, R(0)};
     }
     if (act) d.st.active[sp][o] = act[k];
 }
@@ -1633,8 +1667,8 @@ __global__ void __launch_bounds__(256) k_diag(Dev<F> d, double *partials)
         typename F::Pos p = F::load(d.st.pos[sp], o, mass);
         const Scene &sc = d.scenes[d.owner_scene[o]];
         V3<double> x = F::absolute(p, sc, d.Ld);
-        auto v4 = d.st.vel[sp][o];
-        auto w4 = d.st.omg[sp][o];
+        auto v4 = d.st.kv[sp][2 * o];
+        auto w4 = d.st.kv[sp][2 * o + 1];
         auto q4 = d.st.quat[sp][o];
         auto ii = d.inv_moi[o];
         double m = (double)mass;
