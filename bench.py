@@ -145,20 +145,24 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
     """Bytes the kernels actually move in this implementation's layout, each distinct
     array element counted once per launch (context for the algorithmic figure).
 
-    k_integrate (per owner): state read and written (16-byte vectors: mass kept beside
-    the offset, the two audit accumulators in the fourth lanes of v and w; quaternion),
-    constants, row length, flags, and the force/torque of owners with listed partners.  k_contact: per sphere with
-    listed partners its compacted work entry (slot, row length, first partner), active
-    flag, state, packed constants and the force/torque it writes; per listed pair both
-    row entries and both sides' history vectors read and written."""
+    k_integrate (per owner): state read and written (voxel form: a 32-byte position record
+    with mass and radius, a 32-byte velocity pair with the two audit accumulators in the
+    fourth lanes; quaternion), constants, row length, flags, and the force/torque of
+    owners with listed partners.  k_contact: per sphere with listed partners its compacted
+    work entry (slot, row length, first partner), active flag, state and the force/torque
+    it writes; per listed pair both row entries and both sides' history vectors read and
+    written.  k_step_fused: both, without the force/torque array."""
     if precision == "voxel_fp32":
-        integ = n * (1 + 1 + 24 + 16 + 16 + 16 + 4 + 16 + 2 + 1         # reads
-                     + 24 + 16 + 16 + 16 + 1) + 32 * n_with_entries       # writes, force/torque read
-        contact = n_with_entries * (16 + 1 + 24 + 16 + 16 + 16 + 32) + pairs * (8 + 4 * 16)
-        # fused step, per owner: permutation, row length, first entry, flag, state, packed
-        # constants, quaternion, inverse mass and inertia read; state and flag written
-        step = n * (1 + 1 + 4 + 1 + 24 + 16 + 16 + 16 + 16 + 4 + 16
-                    + 24 + 16 + 16 + 16 + 1) + pairs * (8 + 4 * 16)
+        # 32-byte position record (offset, mass, voxel index, radius pair) and 32-byte
+        # velocity pair (v, w with the audit accumulators) per owner
+        integ = n * (1 + 1 + 32 + 32 + 16 + 4 + 16 + 2 + 1              # reads
+                     + 32 + 32 + 16 + 1) + 32 * n_with_entries            # writes, force/torque read
+        contact = n_with_entries * (16 + 1 + 32 + 32 + 32) + pairs * (8 + 4 * 16)
+        # fused step, per owner: permutation, row length, first entry, flag, position
+        # record, velocity pair, quaternion, inverse mass and inertia read; record,
+        # velocity pair, quaternion and flag written
+        step = n * (1 + 1 + 4 + 1 + 32 + 32 + 16 + 4 + 16
+                    + 32 + 32 + 16 + 1) + pairs * (8 + 4 * 16)
     else:
         integ = n * (1 + 1 + 32 + 32 + 32 + 32 + 8 + 32 + 2 + 1
                      + 32 + 32 + 32 + 32 + 1) + 64 * n_with_entries
