@@ -243,10 +243,10 @@ typedef struct {
                                       with every value in registers                         */
     int32_t fused_block;           /* worlds of single spheres: 0 = contact forces and
                                       integration as two kernels (with a per-owner force
-                                      array between them); 64, 128 or 256 = one fused
-                                      kernel of that block size (a thread sums its sphere's
-                                      contact forces in registers and integrates it);
-                                      ignored for clumps                                    */
+                                      array between them); 64 (the default), 128 or 256 =
+                                      one fused kernel of that block size (a thread sums
+                                      its sphere's contact forces in registers and
+                                      integrates it); always 0 for clumps                   */
 } dem_tuning;
 
 dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);

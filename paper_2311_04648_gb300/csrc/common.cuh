@@ -141,6 +141,13 @@ struct PairParamF {      // the same rounded to FP32 once, for the voxel form
 // Device-resident control block (one per world).  Kernels read the selectors and flags
 // here, so the host can queue work (or replay a CUDA graph) without knowing in advance
 // which buffers hold the current state, whether a list went stale or a step diverged.
+// Per-warp maxima of a step (float bits: displacement bound of the list in use, of the
+// list being built, speed) land in AUDIT_SLOTS slots of their own array, one 128-byte
+// line per slot (AUDIT_STRIDE words), so the atomics spread over the L2 instead of
+// sharing lines with each other or with the control block that every thread reads.
+constexpr int AUDIT_SLOTS = 64;
+constexpr int AUDIT_STRIDE = 32;
+
 struct DevStatus {
     int halt;                    // HALT_*: every kernel returns immediately
     int list_stale;              // list in use no longer covers every contact: force skips
@@ -155,10 +162,6 @@ struct DevStatus {
     unsigned int step_disp_bits; // max over owners of this step's displacement bound (float bits)
     unsigned int vmax_bits;      // max |v| over owners this step (float bits)
     int pad0, pad1;
-    // per-warp maxima land in AUDIT_SLOTS spread slots (float bits), reduced by k_audit
-    unsigned int disp_slots[64];
-    unsigned int disp2_slots[64];
-    unsigned int vmax_slots[64];
     double disp_cur;             // displacement bound since the snapshot of the list in use
     double disp_next;            // ... since the snapshot of the list being built
     double beta_cur, beta_next;  // margins of those lists

@@ -81,6 +81,7 @@ public:
         d_.bin_vpc = m_.vpc_min;
         d_.gyro = m_.gyroscopic;
         d_.n_scenes = (int)m_.scenes.size();
+        if (m_.clumps) tune_.fused_block = 0;          // the fused step serves single spheres
         beta_ = m_.margin;
         {
             int sms = 0;
@@ -135,6 +136,7 @@ public:
         d_.scenes = scenes; d_.walls = walls; d_.pairs = pairs; d_.pairs_f = pairs_f;
         d_.mat_scene = ms; d_.mat_local = ml;
         if ((s = alloc(st_, 1, err))) return s;
+        if ((s = alloc(d_.audit, AUDIT_SLOTS * AUDIT_STRIDE, err))) return s;
         DEM_CU(cudaMallocHost((void **)&sth_, sizeof(DevStatus)));
         if ((s = alloc_lists(d_.K, err))) return s;
 
@@ -623,7 +625,7 @@ public:
             blob.resize(o + n);
             std::memcpy(blob.data() + o, p, n);
         };
-        uint64_t magic = 0x44454d4742333031ull;   // "DEMGB301": 32-byte position records
+        uint64_t magic = 0x44454d4742333032ull;   // "DEMGB302": 32-byte position records, audit slots outside the status
         put(&magic, 8);
         int64_t hdr[6] = {M, d_.N, d_.Np, d_.K, (int64_t)F::voxel, (int64_t)sizeof(R)};
         put(hdr, sizeof(hdr));
@@ -662,7 +664,7 @@ public:
         uint64_t magic;
         int64_t hdr[6];
         DevStatus h;
-        if (!get(&magic, 8) || magic != 0x44454d4742333031ull || !get(hdr, sizeof(hdr)) || !get(&h, sizeof(h))) {
+        if (!get(&magic, 8) || magic != 0x44454d4742333032ull || !get(hdr, sizeof(hdr)) || !get(&h, sizeof(h))) {
             err = "not a state blob";
             return DEM_ERR_ARG;
         }
@@ -712,6 +714,7 @@ public:
             h.cell_stamp = std::max(h.cell_stamp, cur);
         }
         DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
+        DEM_CU(cudaMemset(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int)));   // no maxima of an unfinished step
         recompact_current();
         DEM_CU(cudaStreamSynchronize(sf_));
         dirty_ = false;
@@ -1422,6 +1425,7 @@ private:
             h.step_disp_bits = 0;
             h.vmax_bits = 0;
             DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
+            DEM_CU(cudaMemset(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int)));   // no maxima of an unfinished step
             rebuild_inline(sf_);
             return settle(err);
         }
@@ -1594,7 +1598,7 @@ private:
             launch_integrate();
             mark_end(sf_, m2);
         }
-        k_audit<<<1, 1, 0, sf_>>>(st_);
+        k_audit<<<1, 1, 0, sf_>>>(st_, d_.audit);
         if (collect_ && d_.M > 0)
             k_collect_step<F><<<grid(d_.M, 256), 256, 0, sf_>>>(d_, acc_lab_, obin_, cross_, win_start_, (float)beta_);
     }
@@ -1663,7 +1667,7 @@ private:
     bool dirty_ = false;
     int64_t fallbacks_ = 0, regrows_ = 0;
     double ms_total_ = 0.0;
-    dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0, 0};   // fused_block last
+    dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0, 64};   // fused_block last (ignored for clumps)
     int n_sm_ = 1, occ_block_ = 0, occ_per_sm_ = 1;
     int64_t Mp_ = 0;                // owners rounded up to whole staging tiles
     int staged_per_sm_ = 0;

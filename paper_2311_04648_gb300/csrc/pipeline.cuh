@@ -76,6 +76,7 @@ struct Dev {
     const PairParamF *pairs_f;
     const uint16_t *mat_scene, *mat_local;
     DevStatus *status;
+    unsigned int *audit;            // AUDIT_SLOTS x AUDIT_STRIDE words (per-warp maxima of a step)
 };
 
 // FP32 position of a sphere centre for screening tests (FP64 form: rounded absolute;
@@ -918,18 +919,19 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
 }
 
 // Warp max of the displacement bounds and the speed (non-negative floats order like
-// their bit patterns), one atomic per warp into one of 64 slots: no block barrier,
-// little contention; k_audit reduces the slots.
-__device__ __forceinline__ void audit_slots(DevStatus *stp, int64_t o, int lane, float disp, float disp2, float speed)
+// their bit patterns), one atomic per warp and value into one of AUDIT_SLOTS slots: no
+// block barrier, little contention; k_audit reduces the slots.
+__device__ __forceinline__ void audit_slots(unsigned int *audit, int64_t o, int lane, float disp, float disp2,
+                                            float speed)
 {
     unsigned int db = __reduce_max_sync(0xffffffffu, __float_as_uint(disp));
     unsigned int db2 = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
     unsigned int vb = __reduce_max_sync(0xffffffffu, __float_as_uint(speed));
     if (lane == 0) {
-        const int slot = (int)((o >> 5) & 63);
-        if (db) atomicMax(&stp->disp_slots[slot], db);
-        if (db2) atomicMax(&stp->disp2_slots[slot], db2);
-        if (vb) atomicMax(&stp->vmax_slots[slot], vb);
+        unsigned int *slot = audit + ((o >> 5) & (AUDIT_SLOTS - 1)) * AUDIT_STRIDE;
+        if (db) atomicMax(&slot[0], db);
+        if (db2) atomicMax(&slot[1], db2);
+        if (vb) atomicMax(&slot[2], vb);
     }
 }
 
@@ -1092,7 +1094,7 @@ __global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
                         d.st.active[sp], d.lists.cnt[lc], d.owner_iso, d.owner_scene};
         integrate_owner<F, CLUMPS>(d, stp, o, src, o, sp, disp, disp2, speed);
     }
-    audit_slots(stp, o, lane, disp, disp2, speed);
+    audit_slots(d.audit, o, lane, disp, disp2, speed);
 }
 
 // ------------------------------------------------------------------ fused step
@@ -1151,7 +1153,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK_MAX, 2) k_step_fused(Dev<F> d)
         integrate_core<F, false>(d, stp, s, sp, act, po, me.mass, v4, w4, d.st.quat[sp][s], d.inv_mass[s],
                                  d.inv_moi[s], true, sc, Fs, Ts, aux, disp, disp2, speed);
     }
-    audit_slots(stp, g, lane, disp, disp2, speed);
+    audit_slots(d.audit, g, lane, disp, disp2, speed);
 }
 
 // ------------------------------------------------------------------ staged integration
@@ -1252,7 +1254,7 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
                             reinterpret_cast<const uint16_t *>(b + StageLayout::scene)};
             integrate_owner<F, CLUMPS>(d, stp, o, src, threadIdx.x, sp, disp, disp2, speed);
         }
-        audit_slots(stp, o, lane, disp, disp2, speed);
+        audit_slots(d.audit, o, lane, disp, disp2, speed);
         __syncthreads();                          // every thread has read this stage
         const int64_t next = tile + (int64_t)STAGES * gridDim.x;
         if (threadIdx.x == 0 && next < ntiles) issue(next, st);
@@ -1265,17 +1267,18 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
 // motion between list updates); turns a divergence into a halt, leaving the last good
 // state.  A pair touching now was, at the snapshot, at most R_i + R_j + acc_i + acc_j
 // apart, so every touching pair is listed while the largest acc stays below the margin.
-static __global__ void k_audit(DevStatus *stp)
+static __global__ void k_audit(DevStatus *stp, unsigned int *audit)
 {
     if (stp->halt || stp->list_stale) return;
     unsigned int md = 0, md2 = 0, mv = 0;
-    for (int k = 0; k < 64; ++k) {
-        md = max(md, stp->disp_slots[k]);
-        md2 = max(md2, stp->disp2_slots[k]);
-        mv = max(mv, stp->vmax_slots[k]);
-        stp->disp_slots[k] = 0;
-        stp->disp2_slots[k] = 0;
-        stp->vmax_slots[k] = 0;
+    for (int k = 0; k < AUDIT_SLOTS; ++k) {
+        unsigned int *slot = audit + k * AUDIT_STRIDE;
+        md = max(md, slot[0]);
+        md2 = max(md2, slot[1]);
+        mv = max(mv, slot[2]);
+        slot[0] = 0;
+        slot[1] = 0;
+        slot[2] = 0;
     }
     float sd = __uint_as_float(md);
     float sd2 = __uint_as_float(md2);

@@ -25,13 +25,14 @@ def test_graphs_tunings_and_inline_detection_are_bit_identical():
     a.set_graphs(False)
     runs.append(a)
     b = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
-    b.set_tuning(contact_block=32, integrate_block=512, narrow_block=256, detect_inline=1)
+    b.set_tuning(contact_block=32, integrate_block=512, narrow_block=256, detect_inline=1, fused_block=0)
     runs.append(b)
     c = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
-    c.set_tuning(contact_block=128, integrate_block=128, narrow_block=64, detect_inline=0, cell_factor=2.0)
+    c.set_tuning(contact_block=128, integrate_block=128, narrow_block=64, detect_inline=0, cell_factor=2.0,
+                 fused_block=256)
     runs.append(c)
     f = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
-    f.set_tuning(contact_block=32, contact_lean=1, integrate_staged=1)
+    f.set_tuning(contact_block=32, contact_lean=1, integrate_staged=1, fused_block=0)
     runs.append(f)
     e = dem.World.from_scene(s, precision="voxel_fp32", schedule="every_step", margin_max=beta)
     e.set_tuning(cell_factor=1.5)
@@ -94,7 +95,9 @@ def test_staged_integration_is_bit_identical(kind):
     beta = 5e-5
     a = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
     b = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
-    b.set_tuning(integrate_staged=1)
+    # the two-kernel path (the staged integration is not part of the fused step)
+    a.set_tuning(fused_block=0)
+    b.set_tuning(integrate_staged=1, fused_block=0)
     assert b.tuning()["integrate_staged"] == 1
     a.step(60)
     b.step(60)
@@ -119,7 +122,8 @@ def test_staged_integration_in_a_batch_of_scenes():
     q = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
     p.initialize()
     q.initialize()
-    q.worlds[0].set_tuning(integrate_staged=1)
+    p.worlds[0].set_tuning(fused_block=0)
+    q.worlds[0].set_tuning(integrate_staged=1, fused_block=0)
     p.step(50)
     q.step(50)
     for wp, wq in zip(p.worlds, q.worlds):
