@@ -149,19 +149,15 @@ constexpr int AUDIT_SLOTS = 64;
 constexpr int AUDIT_STRIDE = 32;
 
 struct DevStatus {
+    // read by every thread of the step kernels; written by single threads between kernels
     int halt;                    // HALT_*: every kernel returns immediately
     int list_stale;              // list in use no longer covers every contact: force skips
-    int overflow;                // a row exceeded the list capacity in the last narrow phase
-    int max_row;                 // longest row of the last narrow phase
     int state_par;               // owner-state buffer holding the current state
     int hist_par;                // history buffer holding the current history
     int list_cur;                // contact list in use
     int acc_par;                 // displacement accumulator of the list in use (the other: next)
-    int pad2;
-    int diverged;                // set by the force kernel, turned into a halt by the audit
     unsigned int step_disp_bits; // max over owners of this step's displacement bound (float bits)
     unsigned int vmax_bits;      // max |v| over owners this step (float bits)
-    int pad0, pad1;
     double disp_cur;             // displacement bound since the snapshot of the list in use
     double disp_next;            // ... since the snapshot of the list being built
     double beta_cur, beta_next;  // margins of those lists
@@ -172,11 +168,16 @@ struct DevStatus {
     long long steps_done;
     long long rebuilds;
     unsigned int cell_stamp;     // stamp of the cell table of the build in progress (from 1)
-    unsigned int list_pairs[2];  // sphere-sphere pairs of each list (each pair once)
-    unsigned int list_busy[2];   // slots of each list with listed partners
     unsigned long long pair_steps;   // sum over completed steps of the pairs in use
     unsigned long long busy_steps;   // sum over completed steps of the slots with partners
     long long stale_events;
+    // updated by atomics of many threads (narrow phase, compaction, link, divergence): a
+    // line of their own, away from the fields above
+    alignas(128) int overflow;   // a row exceeded the list capacity in the last narrow phase
+    int max_row;                 // longest row of the last narrow phase
+    int diverged;                // set by the force kernel, turned into a halt by the audit
+    unsigned int list_pairs[2];  // sphere-sphere pairs of each list (each pair once)
+    unsigned int list_busy[2];   // slots of each list with listed partners
 };
 
 // ------------------------------------------------------------------ position forms

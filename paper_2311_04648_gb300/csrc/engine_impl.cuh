@@ -625,7 +625,7 @@ public:
             blob.resize(o + n);
             std::memcpy(blob.data() + o, p, n);
         };
-        uint64_t magic = 0x44454d4742333032ull;   // "DEMGB302": 32-byte position records, audit slots outside the status
+        uint64_t magic = 0x44454d4742333033ull;   // "DEMGB303": 32-byte position records, status lines split
         put(&magic, 8);
         int64_t hdr[6] = {M, d_.N, d_.Np, d_.K, (int64_t)F::voxel, (int64_t)sizeof(R)};
         put(hdr, sizeof(hdr));
@@ -664,7 +664,7 @@ public:
         uint64_t magic;
         int64_t hdr[6];
         DevStatus h;
-        if (!get(&magic, 8) || magic != 0x44454d4742333032ull || !get(hdr, sizeof(hdr)) || !get(&h, sizeof(h))) {
+        if (!get(&magic, 8) || magic != 0x44454d4742333033ull || !get(hdr, sizeof(hdr)) || !get(&h, sizeof(h))) {
             err = "not a state blob";
             return DEM_ERR_ARG;
         }
