@@ -241,10 +241,10 @@ typedef struct {
     int32_t contact_lean;          /* 1 = the contact kernel compiled for more resident
                                       warps (fewer registers, some spilled), 0 = fewer warps
                                       with every value in registers                         */
-    int32_t fused_block;           /* worlds of single spheres: 0 = contact forces and
-                                      integration as two kernels (with a per-owner force
-                                      array between them); 64 (the default), 128 or 256 =
-                                      one fused kernel of that block size (a thread sums
+    int32_t fused_block;           /* worlds of single spheres: 0 (the default) = contact
+                                      forces and integration as two kernels (with a
+                                      per-owner force array between them); 64, 128 or 256
+                                      = one fused kernel of that block size (a thread sums
                                       its sphere's contact forces in registers and
                                       integrates it); always 0 for clumps                   */
 } dem_tuning;

@@ -81,7 +81,6 @@ public:
         d_.bin_vpc = m_.vpc_min;
         d_.gyro = m_.gyroscopic;
         d_.n_scenes = (int)m_.scenes.size();
-        if (m_.clumps) tune_.fused_block = 0;          // the fused step serves single spheres
         beta_ = m_.margin;
         {
             int sms = 0;
@@ -1667,7 +1666,7 @@ private:
     bool dirty_ = false;
     int64_t fallbacks_ = 0, regrows_ = 0;
     double ms_total_ = 0.0;
-    dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0, 64};   // fused_block last (ignored for clumps)
+    dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0, 0};   // fused_block last: the two-kernel step
     int n_sm_ = 1, occ_block_ = 0, occ_per_sm_ = 1;
     int64_t Mp_ = 0;                // owners rounded up to whole staging tiles
     int staged_per_sm_ = 0;
