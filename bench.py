@@ -556,7 +556,9 @@ def main():
                 "warmup": w, "ms_per_step": 1000.0 * args.cpu_sample_n / cb["value"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "impl": "reference",
-                "config": {"workload": "settling_column (bounded sample)", "sample": cb["sample"]},
+                "config": {"workload": "settling_column", "n_spheres": args.n, "radius_mm": [0.8, 1.2],
+                           "box_m": [0.3, 0.3, 1.2], "dt_s": 2e-6, "precision": "FP64 (the oracle)",
+                           "sample": cb["sample"]},
                 "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))

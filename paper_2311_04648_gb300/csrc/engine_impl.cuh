@@ -294,6 +294,7 @@ public:
             if (sth_->list_stale) {          // audit fallback: rebuild from the current state
                 fallbacks_ += 1;
                 cycle_scale_ = std::max(0.05, cycle_scale_ * 0.6);
+                learned_left_ = 0;           // a fresh prediction from the current state
                 rebuild_inline(sf_);
                 if ((s = settle(err))) return s;
                 continue;
@@ -653,6 +654,7 @@ public:
 
     dem_status load(const uint8_t *blob, size_t nb, std::string &err) override
     {
+        learned_left_ = 0;                   // the next cycle asks the network again
         size_t off = 0;
         auto get = [&](void *p, size_t n) -> bool {
             if (off + n > nb) return false;
@@ -780,6 +782,7 @@ public:
 
     dem_status schedule_load(const uint8_t *w, size_t n, std::string &err) override
     {
+        learned_left_ = 0;                   // the next cycle asks the network again
         uint32_t np = 0;
         if (n < 12 || std::memcmp(w, "DEMSCHD1", 8) != 0 || (std::memcpy(&np, w + 8, 4), np != (uint32_t)MLP_NPARAM) ||
             n != 12 + MLP_NPARAM * sizeof(float)) {
@@ -909,6 +912,7 @@ private:
     dem_status upload_state(int64_t first, int64_t n, const double *x, const double *q, const double *v,
                             const double *w, const uint8_t *act, std::string &err)
     {
+        learned_left_ = 0;
         if (n <= 0) return DEM_OK;
         double *buf;
         dem_status s;
@@ -1371,7 +1375,24 @@ private:
     // Learned cycle length: the smallest predicted log2(steps until a bin passes beta) over
     // the occupied bins; a list is used from c to 2c steps after its snapshot, so c is
     // half of it, with a 20% allowance.
+    // The network runs at every LEARNED_REUSE-th cycle boundary (and after any audit
+    // fallback); the cycles between reuse its last answer: the features move little over a
+    // few cycles, and each evaluation (a pass over all owners, the network, a read-back)
+    // sits on the critical path at the boundary.  Any answer is audited.
+    static constexpr int LEARNED_REUSE = 4;
+    long long learned_c_ = 0;
+    int learned_left_ = 0;
     long long learned_cycle(std::string &err)
+    {
+        if (learned_left_ > 0 && learned_c_ > 0) {
+            --learned_left_;
+            return learned_c_;
+        }
+        learned_c_ = learned_eval(err);
+        learned_left_ = LEARNED_REUSE - 1;
+        return learned_c_;
+    }
+    long long learned_eval(std::string &err)
     {
         if (sched_buffers(err) || !mlp_->ready()) return 0;
         const int nb = std::max(1, m_.n_bins);
