@@ -399,7 +399,7 @@ __device__ __forceinline__ void row_insert(uint32_t *buf, int &n, uint32_t e)
 // Narrow phase: one thread per sorted entry scans the 27 neighbour cells (as 9 runs of
 // three x-consecutive cells, each contiguous in the sorted order) and the walls of its
 // scene, and writes its full, sorted row into the list that is not in use.
-template <class F>
+template <class F, bool CLUMPS>
 __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const uint32_t *keys,
                                                  const uint32_t *vals)
 {
@@ -454,17 +454,24 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             }
             if (lo == 0xffffffffu) continue;
             for (uint32_t u = lo; u < hi; ++u) {
-                uint32_t j = vals[u];
-                if (j == i) continue;
-                if (b.sorted_owner[u] == oi) continue;
                 bool hit;
                 if constexpr (F::voxel) {
-                    hit = listed_f32(ac, ao, reinterpret_cast<const int4 *>(b.sorted)[u],
-                                     reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
+                    // whole voxels first: |dx| >= (|di| - 1) L after any rounding, so a
+                    // difference of reject_vox voxels along an axis is out of reach of the
+                    // exact test (three integer compares instead of the float test)
+                    const int4 cb = reinterpret_cast<const int4 *>(b.sorted)[u];
+                    if (abs(ac.x - cb.x) >= b.reject_vox || abs(ac.y - cb.y) >= b.reject_vox ||
+                        abs(ac.z - cb.z) >= b.reject_vox)
+                        continue;
+                    if (vals[u] == i) continue;
+                    if (CLUMPS && b.sorted_owner[u] == oi) continue;
+                    hit = listed_f32(ac, ao, cb, reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
                 } else {
+                    if (vals[u] == i) continue;
+                    if (CLUMPS && b.sorted_owner[u] == oi) continue;
                     hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
                 }
-                if (hit) row_insert(buf, n, j);
+                if (hit) row_insert(buf, n, vals[u]);
             }
         }
     }
