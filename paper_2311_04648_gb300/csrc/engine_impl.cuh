@@ -166,13 +166,6 @@ public:
             db_.snap = a; db_.sorted = c; db_.snap_aux = nullptr; db_.sorted_aux = nullptr;
         }
         if ((s = alloc(db_.sorted_owner, Nk, err))) return s;
-        db_.reject_vox = 0;
-        if (F::voxel) {
-            // the largest listing distance 2 r_max + 2 margin_max, rounded up generously, in
-            // voxels, plus one voxel for the offsets and one for safety
-            const double reach = (2.0 * m_.r_max + 2.0 * m_.margin_max) * (1.0 + 1e-5);
-            db_.reject_vox = (int)std::ceil(reach / m_.Lv) + 2;
-        }
         if ((s = alloc(db_.n_valid, 1, err))) return s;
 
         // constants

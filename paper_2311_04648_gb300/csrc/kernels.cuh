@@ -25,10 +25,6 @@ struct DetectBuffers {
     void *sorted_aux;
     uint32_t *sorted_owner;    // owner of each sorted entry
     uint32_t *n_valid;         // device counter: active entries at the front of the order
-    // voxel form: a candidate whose voxel index differs by at least this along any axis is
-    // farther than the largest listing distance (2 r_max + 2 margin_max) and cannot pass
-    // the exact test; 0 in the FP64 form
-    int reject_vox;
 };
 
 // Two contact lists (ELL rows) plus two history buffers; DevStatus selects which.

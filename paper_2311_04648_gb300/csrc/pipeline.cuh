@@ -456,16 +456,10 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             for (uint32_t u = lo; u < hi; ++u) {
                 bool hit;
                 if constexpr (F::voxel) {
-                    // whole voxels first: |dx| >= (|di| - 1) L after any rounding, so a
-                    // difference of reject_vox voxels along an axis is out of reach of the
-                    // exact test (three integer compares instead of the float test)
-                    const int4 cb = reinterpret_cast<const int4 *>(b.sorted)[u];
-                    if (abs(ac.x - cb.x) >= b.reject_vox || abs(ac.y - cb.y) >= b.reject_vox ||
-                        abs(ac.z - cb.z) >= b.reject_vox)
-                        continue;
                     if (vals[u] == i) continue;
                     if (CLUMPS && b.sorted_owner[u] == oi) continue;
-                    hit = listed_f32(ac, ao, cb, reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
+                    hit = listed_f32(ac, ao, reinterpret_cast<const int4 *>(b.sorted)[u],
+                                     reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
                 } else {
                     if (vals[u] == i) continue;
                     if (CLUMPS && b.sorted_owner[u] == oi) continue;

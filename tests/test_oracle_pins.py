@@ -616,35 +616,3 @@ def test_hertz_headon_unlike_materials_and_radii():
     assert best == pytest.approx(dmax, rel=2e-3)
     assert ow.v[1, 0] - ow.v[0, 0] == pytest.approx(v0, rel=2e-3)   # elastic: speed of separation = v0
 
-
-def test_whole_voxel_reject_never_drops_a_listed_pair():
-    # The narrow phase rejects a candidate whose voxel index differs by at least
-    # ceil(reach / Lv) + 2 along an axis (reach = 2 r_max + 2 margin_max, rounded up)
-    # before the exact FP32 test.  Pairs at that voxel distance, with the offsets and radii
-    # at their extremes, fail the exact test; a touching pair (well inside the bound)
-    # passes it.
-    rng = np.random.default_rng(13)
-    Lv = np.float32(2.0 ** -13)                        # voxel edge (a power of two)
-    r_max, beta = 1.2e-3, 6e-5
-    reach = (2 * r_max + 2 * beta) * (1 + 1e-5)
-    thr = int(np.ceil(reach / float(Lv))) + 2
-    top = np.nextafter(Lv, np.float32(0))              # largest offset below Lv
-    for axis in range(3):
-        for sign in (1, -1):
-            for _ in range(40):
-                cell = np.zeros((2, 3), np.int32)
-                cell[1, axis] = sign * thr
-                cell[1, (axis + 1) % 3] = rng.integers(-thr, thr + 1)
-                off = (rng.random((2, 3)) * float(Lv)).astype(np.float32)
-                off[0, axis] = top if sign > 0 else 0
-                off[1, axis] = 0 if sign > 0 else top
-                rad = np.full(2, r_max, np.float32)
-                pi, _ = oracle.listed_pairs_voxel_f32(cell, off, Lv, rad, np.arange(2), np.float32(beta))
-                assert len(pi) == 0
-    # overlapping spheres along one axis, aligned on the others: listed
-    near = int(np.floor((2 * r_max) / float(Lv))) - 1
-    cell = np.array([[0, 0, 0], [near, 0, 0]], np.int32)
-    off = np.zeros((2, 3), np.float32)
-    pi, _ = oracle.listed_pairs_voxel_f32(cell, off, Lv, np.full(2, r_max, np.float32), np.arange(2),
-                                          np.float32(beta))
-    assert len(pi) == 1 and near < thr
