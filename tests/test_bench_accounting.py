@@ -1,0 +1,63 @@
+"""Host-side accounting of bench.py: the per-unit algorithmic bytes, the layout bytes, the
+kernel choice of the roofline and the source-hash guard on recorded DRAM traffic."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_algorithmic_bytes_follow_the_per_unit_figures(bench):
+    # owner state 44 B each way (voxel form), 32 B per listed pair; FP64 144 B and 56 B
+    a = bench.algorithmic_bytes("voxel_fp32", 1000, 250)
+    assert a == {"integrate": 88000, "contact": 8000, "step": 96000}
+    f = bench.algorithmic_bytes("fp64", 1000, 250)
+    assert f["integrate"] == 144000 and f["contact"] == 14000
+    assert bench.algorithmic_bytes("voxel_fp32", 10, 0, clumps=True)["integrate"] == 10 * (88 + 32)
+
+
+def test_layout_bytes_exceed_the_algorithmic_figure(bench):
+    for prec in ("voxel_fp32", "fp64"):
+        a = bench.algorithmic_bytes(prec, 4_000_000, 1_590_000)
+        lb = bench.layout_bytes(prec, 4_000_000, 2_090_000, 1_590_000)
+        for k in ("integrate", "contact", "step"):
+            assert lb[k] > a[k]
+        # the fused step drops the force array and the second pass over busy owners
+        assert lb["step"] < lb["integrate"] + lb["contact"]
+
+
+def _prof(n_integrate, contact_ms=0.2, integrate_ms=0.15):
+    return {"n_integrate": n_integrate, "n_contact": 100, "contact_ms": contact_ms, "integrate_ms": integrate_ms,
+            "listed_pairs": 1.0e6, "with_entries": 1.5e6}
+
+
+def test_roofline_picks_the_dominant_kernel(bench):
+    r = bench.roofline("voxel_fp32", 4_000_000, _prof(100), 6768.8, "measured")
+    assert r["kernel"].startswith("k_contact") and set(r["kernels"]) == {"contact", "integrate"}
+    assert r["achieved"] == pytest.approx(32e6 / 0.2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6768.8)
+    r = bench.roofline("voxel_fp32", 4_000_000, _prof(100, 0.1, 0.15), 6768.8, "measured")
+    assert r["kernel"].startswith("k_integrate")
+    # no integration launches: the fused step, whole force+integrate figure per launch
+    r = bench.roofline("voxel_fp32", 4_000_000, _prof(0), 6768.8, "measured")
+    assert r["kernel"].startswith("k_step_fused") and r["bytes_per_launch"] == 88 * 4_000_000 + 32e6
+
+
+def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(bench, monkeypatch):
+    t = bench.MEASURED_TRAFFIC["contact"]
+    same = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in t["source"])
+    assert bench.measured_traffic("contact", t["n"]) == (t["bytes"] if same else None)
+    assert bench.measured_traffic("contact", t["n"] + 1) is None          # another size
+    fn, sig, hv = t["source"][0]
+    changed = dict(t, source=[(fn, sig, "0" * 16)] + t["source"][1:])
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, "contact", changed)
+    assert bench.measured_traffic("contact", t["n"]) is None
