@@ -1619,7 +1619,7 @@ private:
             launch_integrate();
             mark_end(sf_, m2);
         }
-        k_audit<<<1, 1, 0, sf_>>>(st_, d_.audit);
+        k_audit<<<1, 32, 0, sf_>>>(st_, d_.audit);
         if (collect_ && d_.M > 0)
             k_collect_step<F><<<grid(d_.M, 256), 256, 0, sf_>>>(d_, acc_lab_, obin_, cross_, win_start_, (float)beta_);
     }

@@ -1270,9 +1270,11 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
 // apart, so every touching pair is listed while the largest acc stays below the margin.
 static __global__ void k_audit(DevStatus *stp, unsigned int *audit)
 {
+    // one warp: each lane reads and clears AUDIT_SLOTS / 32 slots, a warp max combines them
     if (stp->halt || stp->list_stale) return;
+    const int lane = threadIdx.x & 31;
     unsigned int md = 0, md2 = 0, mv = 0;
-    for (int k = 0; k < AUDIT_SLOTS; ++k) {
+    for (int k = lane; k < AUDIT_SLOTS; k += 32) {
         unsigned int *slot = audit + k * AUDIT_STRIDE;
         md = max(md, slot[0]);
         md2 = max(md2, slot[1]);
@@ -1281,6 +1283,10 @@ static __global__ void k_audit(DevStatus *stp, unsigned int *audit)
         slot[1] = 0;
         slot[2] = 0;
     }
+    md = __reduce_max_sync(0xffffffffu, md);
+    md2 = __reduce_max_sync(0xffffffffu, md2);
+    mv = __reduce_max_sync(0xffffffffu, mv);
+    if (lane != 0) return;
     float sd = __uint_as_float(md);
     float sd2 = __uint_as_float(md2);
     float vm = __uint_as_float(mv);
