@@ -633,8 +633,7 @@ public:
         auto dput = [&](const void *dp, size_t n) -> dem_status {
             size_t o = blob.size();
             blob.resize(o + n);
-            if (n) DEM_CU(cudaMemcpy(blob.data() + o, dp, n, cudaMemcpyDeviceToHost));
-            return DEM_OK;
+            return copy_sync(blob.data() + o, dp, n, cudaMemcpyDeviceToHost, err);
         };
         if constexpr (F::voxel) {
             if ((s = dput(d_.st.pos[sp].rec, M * 32))) return s;
@@ -684,9 +683,9 @@ public:
         const int sp = h.state_par, hp = h.hist_par, lc = h.list_cur;
         auto dget = [&](void *dp, size_t n) -> dem_status {
             if (off + n > nb) { err = "truncated state blob"; return DEM_ERR_ARG; }
-            if (n) DEM_CU(cudaMemcpy(dp, blob + off, n, cudaMemcpyHostToDevice));
+            const size_t o = off;
             off += n;
-            return DEM_OK;
+            return copy_sync(dp, blob + o, n, cudaMemcpyHostToDevice, err);
         };
         if constexpr (F::voxel) {
             if ((s = dget(d_.st.pos[sp].rec, M * 32))) return s;
@@ -711,11 +710,11 @@ public:
             // the cell table still holds entries stamped by builds after the checkpoint:
             // the stamp only moves forward
             unsigned int cur = 0;
-            DEM_CU(cudaMemcpy(&cur, &st_->cell_stamp, sizeof(cur), cudaMemcpyDeviceToHost));
+            if ((s = copy_sync(&cur, &st_->cell_stamp, sizeof(cur), cudaMemcpyDeviceToHost, err))) return s;
             h.cell_stamp = std::max(h.cell_stamp, cur);
         }
-        DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
-        DEM_CU(cudaMemset(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int)));   // no maxima of an unfinished step
+        if ((s = copy_sync(st_, &h, sizeof(h), cudaMemcpyHostToDevice, err))) return s;
+        DEM_CU(cudaMemsetAsync(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int), sf_));   // no maxima of an unfinished step
         recompact_current();
         DEM_CU(cudaStreamSynchronize(sf_));
         dirty_ = false;
@@ -821,8 +820,12 @@ private:
             cudaError_t e = cudaMalloc(&ptr, bytes);
             if (e != cudaSuccess) { err = std::string("cudaMalloc: ") + cudaGetErrorString(e); return DEM_ERR_NOMEM; }
         }
-        cudaError_t e = cudaMemset(ptr, 0, bytes);
-        if (e != cudaSuccess) { err = std::string("cudaMemset: ") + cudaGetErrorString(e); return DEM_ERR_CUDA; }
+        // zeroed on the force stream and waited for: the library's streams do not
+        // synchronise with the legacy default stream, so a plain cudaMemset could still be
+        // clearing the buffer when the next kernel on the force stream writes it
+        cudaError_t e = cudaMemsetAsync(ptr, 0, bytes, sf_);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sf_);
+        if (e != cudaSuccess) { err = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e); return DEM_ERR_CUDA; }
         allocs_.push_back(ptr);
         p = reinterpret_cast<T *>(ptr);
         return DEM_OK;
@@ -841,11 +844,20 @@ private:
     dem_status up(T *dst, const T *src, int64_t count, std::string &err)
     {
         if (count <= 0) return DEM_OK;
-        DEM_CU(cudaMemcpy(dst, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
-        return DEM_OK;
+        return copy_sync(dst, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice, err);
     }
 
     // grow-only scratch buffer for read-back kernels
+    // A copy outside the step, on the force stream and waited for (ordered after the work
+    // queued there, complete before anything queued later on either stream).
+    dem_status copy_sync(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, std::string &err)
+    {
+        if (bytes == 0) return DEM_OK;
+        DEM_CU(cudaMemcpyAsync(dst, src, bytes, kind, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        return DEM_OK;
+    }
+
     dem_status scratch(double *&p, int64_t count, std::string &err)
     {
         if (count > scratch_n_) {
@@ -892,10 +904,11 @@ private:
         if ((s = alloc_lists(K, err))) return s;
         if (keep) {
             const int64_t ne = (int64_t)std::min(Kold, K) * d_.Np;
-            DEM_CU(cudaMemcpy(d_.lists.partner[lc], old.partner[lc], ne * 4, cudaMemcpyDeviceToDevice));
-            DEM_CU(cudaMemcpy(d_.lists.cnt[lc], old.cnt[lc], d_.Np, cudaMemcpyDeviceToDevice));
-            DEM_CU(cudaMemcpy(d_.lists.hist[hp], old.hist[hp], ne * sizeof(typename HistVec<R>::T),
-                              cudaMemcpyDeviceToDevice));
+            if ((s = copy_sync(d_.lists.partner[lc], old.partner[lc], ne * 4, cudaMemcpyDeviceToDevice, err))) return s;
+            if ((s = copy_sync(d_.lists.cnt[lc], old.cnt[lc], d_.Np, cudaMemcpyDeviceToDevice, err))) return s;
+            if ((s = copy_sync(d_.lists.hist[hp], old.hist[hp], ne * sizeof(typename HistVec<R>::T),
+                               cudaMemcpyDeviceToDevice, err)))
+                return s;
         }
         for (int b = 0; b < 2; ++b) {
             dfree(old.partner[b]); dfree(old.cnt[b]);
@@ -1141,9 +1154,8 @@ private:
         db_.n_cells_total = m_.n_cells_total;
         db_.key_bits = 1;
         while (db_.key_bits < 32 && ((uint64_t)1 << db_.key_bits) <= (uint64_t)m_.n_cells_total) ++db_.key_bits;
-        DEM_CU(cudaMemcpy(const_cast<Scene *>(d_.scenes), m_.scenes.data(), m_.scenes.size() * sizeof(Scene),
-                          cudaMemcpyHostToDevice));
-        return DEM_OK;
+        return copy_sync(const_cast<Scene *>(d_.scenes), m_.scenes.data(), m_.scenes.size() * sizeof(Scene),
+                         cudaMemcpyHostToDevice, err);
     }
 
     dem_status get_tuning(dem_tuning *t, std::string &err) override
@@ -1444,8 +1456,8 @@ private:
             h.max_row = 0;
             h.step_disp_bits = 0;
             h.vmax_bits = 0;
-            DEM_CU(cudaMemcpy(st_, &h, sizeof(h), cudaMemcpyHostToDevice));
-            DEM_CU(cudaMemset(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int)));   // no maxima of an unfinished step
+            if ((s = copy_sync(st_, &h, sizeof(h), cudaMemcpyHostToDevice, err))) return s;
+            DEM_CU(cudaMemsetAsync(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int), sf_));   // no maxima of an unfinished step
             rebuild_inline(sf_);
             return settle(err);
         }
