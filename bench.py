@@ -339,7 +339,7 @@ def run_ours(args, device):
         kw = {}
         for item in args.set_tuning.split(","):
             k, v = item.split("=")
-            kw[k.strip()] = float(v) if k.strip() == "cell_factor" else int(v)
+            kw[k.strip()] = float(v) if k.strip() in ("cell_factor", "margin") else int(v)
         w.set_tuning(**kw)
         out["tuning"] = w.tuning()
     w.step(args.warmup)

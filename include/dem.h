@@ -247,6 +247,13 @@ typedef struct {
                                       = one fused kernel of that block size (a thread sums
                                       its sphere's contact forces in registers and
                                       integrates it); always 0 for clumps                   */
+    double margin;                 /* delayed schedules: the detection margin beta in m,
+                                      0 < beta <= the world's margin_max (0 = keep the
+                                      current one).  A smaller margin lists fewer pairs
+                                      that do not touch and rebuilds more often.  Every
+                                      touching pair is listed either way, so results are
+                                      the same bits.  dem_get_tuning reports the margin in
+                                      use.  Ignored by the every-step schedule.            */
 } dem_tuning;
 
 dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);

@@ -700,7 +700,9 @@ public:
         if ((s = dget(d_.lists.hist[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
         double extra[2];
         if (!get(extra, sizeof(extra))) { err = "truncated state blob"; return DEM_ERR_ARG; }
-        beta_ = extra[0];
+        // the margin is a tuning choice (results are the same bits for every margin) and
+        // stays as it is; a list built for another margin is rebuilt before the next step
+        const double beta_blob = extra[0];
         fallbacks_ = (int64_t)extra[1];
         h.halt = 0;
         h.step_disp_bits = 0;
@@ -717,7 +719,7 @@ public:
         DEM_CU(cudaMemsetAsync(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int), sf_));   // no maxima of an unfinished step
         recompact_current();
         DEM_CU(cudaStreamSynchronize(sf_));
-        dirty_ = false;
+        dirty_ = beta_blob != beta_;
         return DEM_OK;
     }
 
@@ -1080,6 +1082,10 @@ private:
             err = "cell_factor must be in [1, 4]";
             return DEM_ERR_ARG;
         }
+        if (!(t->margin >= 0.0) || t->margin > m_.margin_max) {
+            err = "margin must be in [0, margin_max]";
+            return DEM_ERR_ARG;
+        }
         dem_status s;
         if ((s = sync(err))) return s;
         drop_graphs();
@@ -1091,7 +1097,20 @@ private:
         tune_.integrate_staged = (t->integrate_staged && prepare_staged()) ? 1 : 0;
         tune_.contact_lean = t->contact_lean ? 1 : 0;
         tune_.fused_block = m_.clumps ? 0 : t->fused_block;
+        tune_.margin = 0.0;
+        apply_margin(t->margin);
         return DEM_OK;
+    }
+
+    // A new detection margin for the delayed schedules (0: keep the current one).  The
+    // list in use was built for the old margin, so the next step rebuilds it first.
+    void apply_margin(double beta)
+    {
+        if (beta > 0.0 && m_.schedule != DEM_SCHEDULE_EVERY_STEP && beta != beta_) {
+            beta_ = beta;
+            dirty_ = true;
+            drop_graphs();
+        }
     }
 
     // The staged integration needs its shared-memory size allowed once (outside any
@@ -1162,6 +1181,7 @@ private:
     {
         (void)err;
         *t = tune_;
+        t->margin = beta_;
         return DEM_OK;
     }
 
@@ -1198,10 +1218,10 @@ private:
                     if (std::sscanf(line, "{\"key\": \"%299[^\"]\", \"contact_block\": %d, \"integrate_block\": %d, "
                                           "\"narrow_block\": %d, \"detect_inline\": %d, \"cell_factor\": %lf, "
                                           "\"integrate_staged\": %d, \"contact_lean\": %d, \"fused_block\": %d, "
-                                          "\"step_ms\": %lf}",
+                                          "\"margin\": %lf, \"step_ms\": %lf}",
                                     k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
                                     &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.fused_block,
-                                    &t.step_ms) == 10 &&
+                                    &t.margin, &t.step_ms) == 11 &&
                         key == k) {
                         best = t;
                         found = true;
@@ -1218,10 +1238,14 @@ private:
         std::vector<uint8_t> blob;
         if ((s = save(blob, err))) return s;
         const bool delayed = m_.schedule != DEM_SCHEDULE_EVERY_STEP;
+        const double beta0 = beta_;                   // the margin of candidates that leave it
         dem_tuning best = tune_;
+        best.margin = 0.0;
         double best_ms = 1e300;
-        auto trial = [&](const dem_tuning &t) -> dem_status {
+        auto trial = [&](const dem_tuning &t0) -> dem_status {
             dem_status st;
+            dem_tuning t = t0;
+            if (t.margin <= 0.0) t.margin = beta0;
             if ((st = set_tuning(&t, err))) return st;
             if ((st = load(blob.data(), blob.size(), err))) return st;
             if ((st = step(std::max(2, steps / 4), err))) return st;     // warm-up, graph capture
@@ -1274,9 +1298,22 @@ private:
                 if ((s = trial(dem_tuning{b2.contact_block, b2.integrate_block, b2.narrow_block, b2.detect_inline,
                                           0.0, f, b2.integrate_staged, b2.contact_lean, b2.fused_block})))
                     return s;
+        // phase 4 (delayed schedules): smaller detection margins list fewer pairs that do
+        // not touch, at the price of more rebuilds; the results are the same bits
+        if (delayed) {
+            const dem_tuning b4 = best;
+            for (double fm : {0.75, 0.5, 0.35}) {
+                dem_tuning t = b4;
+                t.margin = fm * m_.margin_max;
+                t.step_ms = 0.0;
+                if ((s = trial(t))) return s;
+            }
+        }
         best.step_ms = best_ms / steps;
+        if (best.margin <= 0.0) best.margin = beta0;
         if ((s = set_tuning(&best, err))) return s;
         if ((s = load(blob.data(), blob.size(), err))) return s;
+        best.margin = beta_;
         if (chosen) *chosen = best;
         if (cache_path) {
             FILE *f = std::fopen(cache_path, "a");
@@ -1284,10 +1321,10 @@ private:
                 std::fprintf(f,
                              "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
                              "%d, \"detect_inline\": %d, \"cell_factor\": %.3f, \"integrate_staged\": %d, "
-                             "\"contact_lean\": %d, \"fused_block\": %d, \"step_ms\": %.6f}\n",
+                             "\"contact_lean\": %d, \"fused_block\": %d, \"margin\": %.17g, \"step_ms\": %.6f}\n",
                              key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
                              best.detect_inline, best.cell_factor, best.integrate_staged, best.contact_lean,
-                             best.fused_block, best.step_ms);
+                             best.fused_block, best.margin, best.step_ms);
                 std::fclose(f);
             }
         }

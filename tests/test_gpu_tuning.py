@@ -37,10 +37,24 @@ def test_graphs_tunings_and_inline_detection_are_bit_identical():
     e = dem.World.from_scene(s, precision="voxel_fp32", schedule="every_step", margin_max=beta)
     e.set_tuning(cell_factor=1.5)
     runs.append(e)
+    g = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
+    g.set_tuning(margin=0.35 * beta)             # fewer listed pairs, more rebuilds
+    assert g.tuning()["margin"] == 0.35 * beta
+    with pytest.raises(Exception):
+        g.set_tuning(margin=2.0 * beta)          # above margin_max
+    runs.append(g)
     for w in runs:
         w.step(150)
         for x, y in zip(_state(w), want):
             assert np.array_equal(x, y)
+    assert g.stats()["rebuilds"] > b.stats()["rebuilds"]
+    # margins changed in mid-run
+    m = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound", margin=beta, margin_max=beta)
+    for k, fm in ((40, 0.5), (50, 1.0), (60, 0.35)):
+        m.set_tuning(margin=fm * beta)
+        m.step(k)
+    for x, y in zip(_state(m), want):
+        assert np.array_equal(x, y)
     assert c.stats()["cell_size"] > 1.9 * ref.stats()["cell_size"]
     # a cell size change in mid-run, in the FP64 form as well
     for prec in ("voxel_fp32", "fp64"):
@@ -80,6 +94,8 @@ def test_autotune_restores_the_state_and_reuses_its_cache(tmp_path):
         assert t2[k] == t[k]
     assert t2["cell_factor"] == pytest.approx(t["cell_factor"], abs=1e-3)
     assert t2["step_ms"] == pytest.approx(t["step_ms"], abs=1e-6)
+    assert 0.0 < t["margin"] <= beta and w.tuning()["margin"] == t["margin"]
+    assert t2["margin"] == t["margin"] and w2.tuning()["margin"] == t["margin"]
     assert len(open(cache).read().strip().splitlines()) == 1
     # tuned runs continue exactly like untuned ones
     w.step(60)
