@@ -587,6 +587,40 @@ def test_tangential_to_normal_stiffness_is_mindlins_ratio(nu):
     assert kt / kn_incr == pytest.approx(2 * (1 - nu) / (2 - nu), rel=1e-9)
 
 
+def _contact_stiffness(mats, E, nu, R=1e-3, delta=2e-5, h=1e-7):
+    """Normal (F_n / delta^(3/2)) and tangential (|F_t| / |u_t|) stiffness of one undamped,
+    frictionally locked contact between spheres of materials mats[0] and mats[1], from one
+    step of tangential sliding."""
+    tpls = [W.sphere_template(R, mat=0), W.sphere_template(R, mat=1)]
+    x = np.array([[0.0, 0.0, 0.0], [2 * R - delta, 0.0, 0.0]])
+    mat = (np.asarray(E, np.float64), np.asarray(nu, np.float64), np.ones((2, 2)), np.full((2, 2), 10.0))
+    s = make_scene(x, v=[[0.0, 0.01, 0.0], [0.0, 0.0, 0.0]], templates=tpls, owner_t=list(mats), h=h, mat=mat)
+    cs = oracle.OracleWorld(s).eval()[2]
+    assert len(cs) == 1
+    n = np.array(cs[0]["normal"])
+    f = np.array(cs[0]["force"])
+    fn = abs(np.dot(f, n))
+    ft = f - np.dot(f, n) * n
+    return fn / cs[0]["overlap"] ** 1.5, np.linalg.norm(ft) / np.linalg.norm(cs[0]["ut"])
+
+
+def test_unlike_material_stiffnesses_are_the_two_half_space_compliances_in_series():
+    """Hertz and Mindlin: each body of a contact deforms as an elastic half-space, so at a
+    given contact radius the contact's normal and tangential compliances are the sums of
+    the two bodies' compliances ((1 - nu^2)/E and (2 - nu)/G per body, G = E/(2(1 + nu))).
+    With the geometry fixed, a like-material contact has twice one body's compliance, so
+    1/k(A, B) = (1/k(A, A) + 1/k(B, B)) / 2 for both stiffnesses."""
+    E, nu = [1e7, 4.5e7], [0.22, 0.41]
+    kn_aa, kt_aa = _contact_stiffness((0, 0), E, nu)
+    kn_bb, kt_bb = _contact_stiffness((1, 1), E, nu)
+    kn_ab, kt_ab = _contact_stiffness((0, 1), E, nu)
+    assert 1.0 / kn_ab == pytest.approx(0.5 * (1.0 / kn_aa + 1.0 / kn_bb), rel=1e-9)
+    assert 1.0 / kt_ab == pytest.approx(0.5 * (1.0 / kt_aa + 1.0 / kt_bb), rel=1e-9)
+    # and the pair is symmetric in its two bodies
+    kn_ba, kt_ba = _contact_stiffness((1, 0), E, nu)
+    assert kn_ba == pytest.approx(kn_ab, rel=1e-12) and kt_ba == pytest.approx(kt_ab, rel=1e-12)
+
+
 def test_hertz_headon_unlike_materials_and_radii():
     """Hertz impact of unlike spheres: delta_max = (15 mbar v^2 / (16 E* sqrt(Rbar)))^(2/5)
     with 1/E* = sum (1 - nu_i^2)/E_i, Rbar = R1 R2/(R1 + R2), mbar = m1 m2/(m1 + m2)."""
