@@ -318,7 +318,9 @@ dem_status dem_get_diagnostics(dem_world *w, dem_diagnostics *d);
 /* Serialise owner state, contact list with history and schedule state into buf.
  * *used receives the size; DEM_ERR_CAPACITY (with *used set) if cap is too small. */
 dem_status dem_save_state(dem_world *w, void *buf, size_t cap, size_t *used);
-/* Restore a blob written by dem_save_state of a world with identical set-up. */
+/* Restore a blob written by dem_save_state of a world with identical set-up.  Tuning
+ * choices, the detection margin among them, stay as they are; a contact list saved
+ * under another margin is rebuilt before the next step. */
 dem_status dem_load_state(dem_world *w, const void *buf, size_t bytes);
 
 /* ---------------------------------------------------------------- batched scenes */
