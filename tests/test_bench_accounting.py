@@ -55,9 +55,45 @@ def test_roofline_picks_the_dominant_kernel(bench):
 def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(bench, monkeypatch):
     t = bench.MEASURED_TRAFFIC["contact"]
     same = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in t["source"])
-    assert bench.measured_traffic("contact", t["n"]) == (t["bytes"] if same else None)
-    assert bench.measured_traffic("contact", t["n"] + 1) is None          # another size
+    m = t["margin"]
+    assert bench.measured_traffic("contact", t["n"], m) == (t["bytes"] if same else None)
+    assert bench.measured_traffic("contact", t["n"] + 1, m) is None       # another size
+    assert bench.measured_traffic("contact", t["n"], 0.35 * m) is None    # another margin
+    assert bench.measured_traffic("contact", t["n"]) is None              # margin unknown
+    ti = bench.MEASURED_TRAFFIC["integrate"]                             # margin-free
+    same_i = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in ti["source"])
+    assert bench.measured_traffic("integrate", ti["n"], 0.35 * m) == (ti["bytes"] if same_i else None)
     fn, sig, hv = t["source"][0]
     changed = dict(t, source=[(fn, sig, "0" * 16)] + t["source"][1:])
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, "contact", changed)
-    assert bench.measured_traffic("contact", t["n"]) is None
+    assert bench.measured_traffic("contact", t["n"], m) is None
+
+
+def test_bench_line_carries_the_contract_keys(bench, monkeypatch, capsys):
+    """main() on a stand-in for the GPU run: one JSON line with the contract's keys, the
+    roofline of the dominant kernel and the traffic guard keyed by the run's margin."""
+    import json
+    import sys
+    prof = dict(_prof(100, 0.15, 0.152), n_detect=10, detect_ms=3.0, hash_ms=0.09, link_ms=0.2)
+    stats = {"margin": 2.1e-5}
+    res = {"chosen": {"ms": 1825.0, "steps": 5000, "rebuilds": 488, "fallbacks": 0, "stats": stats,
+                      "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 30}},
+           "profile": prof, "copy_gbs": 6700.0, "tuning": {"fused_block": 0, "margin": 2.1e-5},
+           "e2e": {"seconds": 0.08, "steps": 8, "bytes_in": 416_000_000, "bytes_out": 416_000_000},
+           "n_spheres": 4_000_000, "clumps": False,
+           "plain": {"ms": 229.0, "steps": 40, "profile": dict(prof, n_integrate=5)}}
+    monkeypatch.setattr(bench, "run_ours", lambda args, device: res)
+    monkeypatch.setattr(bench, "cpu_baseline", lambda args: {"value": 8e4, "unit": "sphere-steps/s", "cores": 1,
+                                                             "kind": "oracle", "sample": "stand-in"})
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    assert bench.main() == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        assert k in line, k
+    assert line["value"] == pytest.approx(4_000_000 * 5000 / 1.825)
+    assert line["gpu_launches"] == 3 * 5000 + 20 * 488
+    r = line["roofline"]
+    assert r["kernel"].startswith("k_integrate") and r["unit"] == "GB/s"
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert line["e2e"]["h2d_bytes_per_step"] == 416_000_000
