@@ -565,6 +565,42 @@ def test_gyroscopic_angular_momentum_drift_is_first_order_in_h():
     assert 1.8 < drift[0] / drift[1] < 2.2
 
 
+def stack_run(mu, gap_frac, m2, t_end=3.0, h=5e-5):
+    """The three-sphere stack of Sec. 4.3.2 with C_r = 0, run to t_end; returns the top
+    sphere's height, the largest speed and the statics threshold tan(theta/2)."""
+    g = read_golden("stacking_sec4_3_2.txt")
+    R, m1 = g["radius_m"], g["bottom_mass_kg"]
+    a = R + 0.5 * gap_frac * R                      # bottom centres at x = -a, +a
+    sin_t = a / (2 * R)                             # theta: contact normal from vertical
+    x = np.array([[-a, 0.0, R], [a, 0.0, R], [0.0, 0.0, R + 2 * R * math.sqrt(1 - sin_t ** 2)]])
+    vol = 4.0 / 3.0 * math.pi * R ** 3
+    tpls = [W.sphere_template(R, rho=m1 / vol), W.sphere_template(R, rho=m2 / vol)]
+    floor = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    s = make_scene(x, templates=tpls, owner_t=[0, 0, 1], walls=[floor], g=(0, 0, -9.81), h=h,
+                   mat=one_material(E=1e7, nu=0.3, e=0.5, mu=mu))
+    ow = oracle.OracleWorld(s)
+    assert ow.step(int(round(t_end / h))) == 0
+    return ow.x[2, 2], float(np.max(np.abs(ow.v))), math.tan(0.5 * math.asin(sin_t)), R
+
+
+@pytest.mark.parametrize("gap_frac,m2", [(0.2, 1.0), (0.2, 3.0), (0.5, 0.3)])
+def test_three_sphere_stack_stands_iff_friction_exceeds_tan_half_angle(gap_frac, m2):
+    """Statics of the stack without rolling resistance.  On a bottom sphere, torques about
+    its centre make the floor's friction equal the friction T at the top contact, and the
+    horizontal balance gives T = N tan(theta/2), N being the normal force there.  The top
+    sphere's vertical balance gives N = m2 g / 2, because cos(theta) + tan(theta/2)
+    sin(theta) = 1.  The floor then carries more than N, so its friction limit holds
+    whenever the top contact's does.  The stack can stand iff mu >= tan(theta/2),
+    whatever the masses.  It stands 4% above the threshold and collapses 4% below."""
+    R = read_golden("stacking_sec4_3_2.txt")["radius_m"]
+    thr = math.tan(0.5 * math.asin((R + 0.5 * gap_frac * R) / (2 * R)))
+    z_hi, v_hi, thr_run, _ = stack_run(1.04 * thr, gap_frac, m2)
+    z_lo, v_lo, _, _ = stack_run(0.96 * thr, gap_frac, m2)
+    assert thr_run == thr
+    assert z_hi > 2.0 * R and v_hi < 1e-9            # standing, at rest
+    assert z_lo < 1.01 * R                           # the top sphere reached the floor
+
+
 @pytest.mark.parametrize("nu", [0.2, 0.3, 0.45])
 def test_tangential_to_normal_stiffness_is_mindlins_ratio(nu):
     """Mindlin: for like materials the tangential stiffness of a Hertzian contact is
