@@ -565,6 +565,36 @@ def test_gyroscopic_angular_momentum_drift_is_first_order_in_h():
     assert 1.8 < drift[0] / drift[1] < 2.2
 
 
+@pytest.mark.parametrize("mu,vn,vt", [(0.1, 1.0, 2.0), (0.3, 0.5, 3.0)])
+def test_oblique_impact_in_gross_sliding_follows_the_coulomb_impulse(mu, vn, vt):
+    """A sphere hits a plane obliquely, elastic (e = 1) and fast enough along the plane
+    that its contact point slides for the whole impact (vt > 7 mu vn for a solid sphere).
+    Coulomb friction then transmits a tangential impulse of exactly mu times the normal
+    one, so the tangential velocity changes by mu times the normal velocity change.  The
+    spin gained is that impulse times the lever arm over I = (2/5) m R^2.  The arm runs
+    from R down to R - delta_max/2, the contact point being the middle of the overlap, so
+    the spin lies between 2.5 mu dv_n (R - delta_max/2)/R^2 and 2.5 mu dv_n / R."""
+    R, E, nu, h = 1e-3, 1e9, 0.3, 1e-8
+    assert vt > 7 * mu * vn
+    floor = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    s = make_scene([[0.0, 0.0, R + 1e-7]], v=[[vt, 0.0, -vn]], walls=[floor], h=h,
+                   mat=one_material(E=E, nu=nu, e=1.0, mu=mu))
+    ow = oracle.OracleWorld(s)
+    m = ow.mass[0]
+    Es = E / (2 * (1 - nu ** 2))                     # the plane is of the same material
+    dmax = (15 * m * vn ** 2 / (16 * Es * math.sqrt(R))) ** 0.4
+    tc = 2 * dmax / vn * 0.4 * math.gamma(0.4) * math.gamma(0.5) / math.gamma(0.9)
+    assert ow.step(int((1e-7 / vn + 1.5 * tc) / h)) == 0
+    assert len(ow.eval()[2]) == 0                    # the impact is over
+    dvn = ow.v[0, 2] + vn
+    dvt = ow.v[0, 0] - vt
+    assert dvn == pytest.approx(2 * vn, rel=1e-6)    # elastic
+    assert -dvt / dvn == pytest.approx(mu, rel=1e-9)
+    spin = ow.wb[0, 1]
+    hi = 2.5 * mu * dvn / R
+    assert hi * (1 - dmax / (2 * R)) < spin < hi
+
+
 def stack_run(mu, gap_frac, m2, t_end=3.0, h=5e-5):
     """The three-sphere stack of Sec. 4.3.2 with C_r = 0, run to t_end; returns the top
     sphere's height, the largest speed and the statics threshold tan(theta/2)."""
