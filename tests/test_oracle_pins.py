@@ -565,6 +565,30 @@ def test_gyroscopic_angular_momentum_drift_is_first_order_in_h():
     assert 1.8 < drift[0] / drift[1] < 2.2
 
 
+def test_sphere_launched_on_a_floor_slides_then_rolls_at_five_sevenths():
+    """A sphere resting on a floor at its static overlap, launched at v0 without spin:
+    it slides with deceleration mu g while friction spins it up, w R = (5/2) mu g t, until
+    the contact point stops slipping at t = 2 v0 / (7 mu g).  From then on it rolls at
+    (5/7) v0, its angular momentum about the contact line being conserved."""
+    R, E, nu, mu, v0, g, h = 1e-3, 1e9, 0.3, 0.3, 0.1, 9.81, 1e-6
+    m = W.sphere_template(R).mass
+    ds = (3 * m * g / (4 * (E / (2 * (1 - nu ** 2))) * math.sqrt(R))) ** (2 / 3)
+    floor = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    s = make_scene([[0.0, 0.0, R - ds]], v=[[v0, 0.0, 0.0]], walls=[floor], g=(0, 0, -g), h=h,
+                   mat=one_material(E=E, nu=nu, e=0.5, mu=mu))
+    ow = oracle.OracleWorld(s)
+    t_roll = 2 * v0 / (7 * mu * g)
+    n = int(0.25 * t_roll / h)
+    for k in (1, 2, 3):                              # sliding
+        assert ow.step(n) == 0
+        t = k * n * h
+        assert ow.v[0, 0] == pytest.approx(v0 - mu * g * t, rel=1e-6)
+        assert ow.wb[0, 1] * R == pytest.approx(2.5 * mu * g * t, rel=1e-4)
+    assert ow.step(int(1.5 * t_roll / h)) == 0      # rolling
+    assert ow.v[0, 0] == pytest.approx(5.0 / 7.0 * v0, rel=1e-4)
+    assert ow.wb[0, 1] * R == pytest.approx(ow.v[0, 0], rel=1e-4)
+
+
 @pytest.mark.parametrize("mu,vn,vt", [(0.1, 1.0, 2.0), (0.3, 0.5, 3.0)])
 def test_oblique_impact_in_gross_sliding_follows_the_coulomb_impulse(mu, vn, vt):
     """A sphere hits a plane obliquely, elastic (e = 1) and fast enough along the plane
