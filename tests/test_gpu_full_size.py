@@ -2,8 +2,9 @@
 
 The 4,000,000-sphere settling column (R ~ U[0.8, 1.2] mm, 0.3 x 0.3 x 1.2 m box, dt = 2e-6 s)
 runs in the launch configuration the bench times: voxel positions with FP32 arithmetic,
-velocity-bound delayed detection on the second stream, audited every step, the default
-tuning (the two-kernel force step, which the autotuner keeps at this size).  The oracle
+velocity-bound delayed detection on the second stream, audited every step, and the
+tuning the bench's autotuner picks at this size on a GB300 (the two-kernel force step,
+128-thread contact blocks, a detection margin of 0.35 of margin_max).  The oracle
 cannot step four million spheres, so it evaluates sampled windows of the GPU's own state
 one by one: every owner whose centre lies in a cube around a sampled sphere, with the
 tangential history the GPU carried into the step.  A sphere in the inner core of a
@@ -170,6 +171,7 @@ def test_full_size_bench_workload_matches_oracle_on_sampled_windows():
     s = W.settling_column(n=N_FULL)
     w = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
     try:
+        w.set_tuning(contact_block=128, fused_block=0, margin=0.35 * w.tuning()["margin"])
         w.step(STEPS)
         c0 = w.contacts()                      # the first read-back allocates its buffer
         again = w.contacts()
