@@ -76,3 +76,31 @@ def test_smoke_scene_builds_and_has_contacts():
     o = oracle.OracleWorld(s)
     assert o.step(5) == 0
     assert len(o.eval()[2]) > 100
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of the header's structs have the C sizes and field offsets (the
+    header compiled as C99 by gcc prints them)."""
+    import ctypes
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2311_04648_gb300 import dem
+    mirrors = {"dem_world_desc": dem.WorldDesc, "dem_stats": dem.Stats, "dem_tuning": dem.Tuning,
+               "dem_diagnostics": dem.Diagnostics}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dem.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
