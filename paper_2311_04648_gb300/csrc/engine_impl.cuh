@@ -849,7 +849,6 @@ private:
         return copy_sync(dst, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice, err);
     }
 
-    // grow-only scratch buffer for read-back kernels
     // A copy outside the step, on the force stream and waited for (ordered after the work
     // queued there, complete before anything queued later on either stream).
     dem_status copy_sync(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, std::string &err)
@@ -860,6 +859,7 @@ private:
         return DEM_OK;
     }
 
+    // grow-only scratch buffer for read-back kernels
     dem_status scratch(double *&p, int64_t count, std::string &err)
     {
         if (count > scratch_n_) {
