@@ -42,12 +42,15 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=40, help="timed steps of the plain FP64 every-step form")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-n", type=int, default=4000)
-    ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-sample-n", type=int, default=20000, help="spheres of the oracle's sub-box sample")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
     ap.add_argument("--tune-steps", type=int, default=60, help="steps per autotuner trial (0: no tuning)")
     ap.add_argument("--tune-at", type=int, default=2500,
-                    help="the autotuner times its candidates from the state after this many steps "
-                         "(then the initial state is restored)")
+                    help="the autotuner times its candidates from the state after this many steps")
+    ap.add_argument("--config-steps", type=int, default=5000, help="steps of the configuration (5,000)")
+    ap.add_argument("--window-start", type=int, default=-1,
+                    help="step at which the warm-up starts (-1: the tuning step when the warm-up and "
+                         "timed steps fit in the configuration's steps after it, else as late as they fit)")
     ap.add_argument("--workload", default="column", choices=["column", "drum", "hopper", "batch"],
                     help="column: the headline settling column; the others run one configuration at full size")
     ap.add_argument("--set-tuning", default="",
@@ -139,6 +142,18 @@ def algorithmic_bytes(precision, n, pairs, clumps=False):
         contact = 56 * pairs
     # the fused step kernel does both: the whole force+integrate figure per launch
     return {"integrate": integ, "contact": contact, "step": integ + contact}
+
+
+def detection_bytes(precision, n, pairs):
+    """Algorithmic bytes of one list rebuild (per-unit figures of the method's detection):
+    per sphere its position read (voxel form: voxel index 8 + offset 12 = 20 B; FP64 form
+    24 B), the cell key and id written and read back (12 B each way), two sort passes over
+    them (2 x 24 B) and its share of the cell table (4 B); per listed pair its two ids
+    written (8 B) and the history remap, which reads the old ids and history and writes
+    the new (2 x (8 + 12) B; FP64 form 2 x (8 + 24) B)."""
+    if precision == "voxel_fp32":
+        return 96 * n + 48 * pairs
+    return 100 * n + 72 * pairs
 
 
 def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
@@ -281,7 +296,8 @@ def profile_delta(p0, p1):
 
 KERNEL_NAMES = {"contact": "k_contact (pair forces + per-owner sums)",
                 "integrate": "k_integrate (owner update + audit)",
-                "step": "k_step_fused (pair forces summed in registers + owner update + audit)"}
+                "step": "k_step_fused (pair forces summed in registers + owner update + audit)",
+                "detect": "detection phase (k_hash, radix sort, k_cellstart, k_narrow, k_link)"}
 
 
 def fused_step(prof):
@@ -289,20 +305,35 @@ def fused_step(prof):
     return prof["n_integrate"] == 0 and prof["n_contact"] > 0
 
 
-def roofline(precision, n, prof, peak, peak_kind, margin=None):
+def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step=0.0):
+    """Roofline of the dominant kernel of a step (largest share of the step's time) and of
+    each per-step kernel and the detection phase on its own: algorithmic bytes per
+    launch over the average launch duration (CUDA events on the kernel's own stream)."""
     ab = algorithmic_bytes(precision, n, prof["listed_pairs"])
     lb = layout_bytes(precision, n, prof["with_entries"], prof["listed_pairs"])
     per = {}
     for k in (("step",) if fused_step(prof) else ("contact", "integrate")):
         ms = prof["contact_ms" if k == "step" else f"{k}_ms"]
         sec = ms / 1000.0
-        per[k] = {"ms": ms, "bytes": ab[k], "gbs": ab[k] / sec / 1e9 if ms > 0 else None,
+        per[k] = {"ms": ms, "ms_per_step": ms, "bytes": ab[k], "gbs": ab[k] / sec / 1e9 if ms > 0 else None,
                   "moved_bytes": lb[k], "moved_gbs": lb[k] / sec / 1e9 if ms > 0 else None}
-    dom = max(per, key=lambda k: per[k]["ms"])
+    if prof["n_detect"] > 0 and prof["detect_ms"] > 0:
+        db = detection_bytes(precision, n, prof["listed_pairs"])
+        dms = prof["detect_ms"]
+        per["detect"] = {"ms": dms, "ms_per_step": dms * rebuilds_per_step, "bytes": db,
+                         "gbs": db / (dms / 1000.0) / 1e9, "moved_bytes": None, "moved_gbs": None,
+                         "what": "one list rebuild: hash, sort passes, cell table, narrow phase, history link"}
+    for k, v in per.items():
+        v["frac"] = (v["gbs"] / peak) if v["gbs"] else None
+        v["traffic"] = (measured_traffic(k, n, margin) if precision == "voxel_fp32" and k in MEASURED_TRAFFIC
+                        else None)
+    # the dominant kernel among the per-step kernels (the detection phase is several
+    # kernels on the second stream, reported beside them)
+    dom = max((k for k in per if k != "detect"), key=lambda k: per[k]["ms_per_step"])
     a = per[dom]["gbs"]
     return {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
             "achieved": a, "peak": peak, "unit": "GB/s", "frac": (a / peak) if a else None,
-            "traffic": measured_traffic(dom, n, margin) if precision == "voxel_fp32" else None,
+            "traffic": per[dom]["traffic"],
             "peak_kind": peak_kind, "bytes_per_launch": per[dom]["bytes"], "avg_launch_ms": per[dom]["ms"],
             "moved_frac": (per[dom]["moved_gbs"] / peak) if per[dom]["moved_gbs"] else None,
             "kernels": per, "listed_pairs": prof["listed_pairs"], "spheres_with_entries": prof["with_entries"]}
@@ -330,16 +361,29 @@ def run_ours(args, device):
         torch.cuda.nvtx.range_pop()
         return e0.elapsed_time(e1)
 
-    # chosen form: voxel + FP32, delayed detection on the second stream, audited; tuned on
-    # a mid-run state (contacts grow as the column settles), then started from step 0
+    # chosen form: voxel + FP32, delayed detection on the second stream, audited.  The
+    # timed window lies inside the configuration's steps: it starts where the autotuner
+    # tunes (mid-run, after the column has closed many lattice gaps) when the warm-up and
+    # the timed steps fit after it, else as late as they fit, so that a short run times a
+    # state in contact, not the contact-free initial lattice
     w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
+    start_at = args.window_start
+    if start_at < 0:
+        start_at = min(args.tune_at, max(0, args.config_steps - args.steps - args.warmup))
+    out["window_start"] = start_at
     if args.tune_steps > 0:
-        start = w.save_state()
-        w.step(args.tune_at)
-        out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache)
-        w.load_state(start)
-        del start
+        if start_at == args.tune_at:
+            w.step(args.tune_at)
+            out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache)
+        else:
+            start = w.save_state()
+            w.step(args.tune_at)
+            out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache)
+            w.load_state(start)
+            del start
+            w.step(start_at)
     else:
+        w.step(start_at)
         out["tuning"] = w.tuning()
     if args.set_tuning:
         kw = {}
@@ -348,29 +392,38 @@ def run_ours(args, device):
             kw[k.strip()] = float(v) if k.strip() in ("cell_factor", "margin") else int(v)
         w.set_tuning(**kw)
         out["tuning"] = w.tuning()
-    w.step(args.warmup)
-    after_warmup = w.save_state()
-    s0 = w.stats()
+    # the state at the start of the warm-up, for the plain form's run from the same state
+    window_state = w.owner_state()
+    window_contacts = w.contacts()
+    # the clock sampler covers the warm-up, the timed steps and the profiled pass over
+    # the same steps (nvidia-smi samples every 50 ms: a short timed region alone may fall
+    # between two samples)
     with ClockSampler(device) as clk:
+        time.sleep(0.2)
+        w.step(args.warmup)
+        after_warmup = w.save_state()
+        s0 = w.stats()
         ms = timed(w, args.steps, "timed_chosen")
-    s1 = w.stats()
-    steps = s1["steps"] - s0["steps"]
-    rebuilds = s1["rebuilds"] - s0["rebuilds"]
+        s1 = w.stats()
+        steps = s1["steps"] - s0["steps"]
+        rebuilds = s1["rebuilds"] - s0["rebuilds"]
+        # profiled pass over the same steps (restored from the checkpoint) for per-kernel
+        # durations: events on each kernel's own stream
+        end_state = w.save_state()
+        w.load_state(after_warmup)
+        w.set_profiling(True)
+        p0 = w.stats()
+        w.step(args.steps)
+        p1 = w.stats()
+        w.set_profiling(False)
+        time.sleep(0.2)
     out["chosen"] = dict(ms=ms, steps=steps, rebuilds=rebuilds, clocks=clk.summary(), stats=s1,
-                         fallbacks=s1["audit_fallbacks"] - s0["audit_fallbacks"])
-    out["copy_gbs"] = device_copy_gbs(device)
-    # profiled pass over the same steps (restored from the checkpoint) for per-kernel
-    # durations: events on each kernel's own stream
-    end_state = w.save_state()
-    w.load_state(after_warmup)
-    w.set_profiling(True)
-    p0 = w.stats()
-    w.step(args.steps)
-    p1 = w.stats()
-    w.set_profiling(False)
+                         fallbacks=s1["audit_fallbacks"] - s0["audit_fallbacks"],
+                         first_step=s0["steps"], contacts=(s0["active_contacts"], s1["active_contacts"]))
     out["profile"] = profile_delta(p0, p1)
     w.load_state(end_state)
     del after_warmup, end_state
+    out["copy_gbs"] = device_copy_gbs(device)
     # e2e through the C ABI with host buffers: state in from pinned memory, one step,
     # state out to pinned memory, every step
     n_own = scene.n_owner
@@ -402,6 +455,13 @@ def run_ours(args, device):
     # plain form: FP64, detection every step, same workload
     if args.plain_steps > 0:
         wp = dem.World.from_scene(scene, precision="fp64", schedule="every_step", device=device)
+        # the same state as the chosen form's window (positions, orientations, velocities
+        # and the tangential history of its contacts)
+        x, q, v, wb = window_state
+        wp.set_owner_state(0, xyz=x, quat=q, vel=v, omega=wb)
+        wp.step(0)
+        wp.set_history(window_contacts["i"], window_contacts["j"], window_contacts["history"])
+        del window_state, window_contacts
         wp.step(3)
         p0 = wp.stats()
         msp = timed(wp, args.plain_steps, "timed_plain")
@@ -522,31 +582,58 @@ def run_scale(args, device, rank=0, world=1):
     return out
 
 
-def cpu_baseline(args):
-    """The oracle as it stands (single thread, O(N^2) detection) on a bounded sample of
-    the same workload: the central column of the same generator with ~args.cpu_sample_n
-    spheres, stepped until ~args.cpu_sample_seconds of CPU time."""
-    import math
+def cpu_baseline(args, max_steps=None):
+    """The oracle as it stands on the host cores, on bounded samples of the workload:
+
+    value  -- the oracle's own O(N^2) contact search (the default mode), OpenMP over
+              spheres on every host core, on the 20,000-sphere sub-box of the settling
+              column (the same generator restricted to a 0.03 m central column), stepped
+              from the lattice until ~args.cpu_sample_seconds have passed;
+    cell_list      -- the same sub-box with the oracle's grid candidate enumeration (the
+                      faster variant: the same contacts in the same order), all cores,
+                      up to 500 steps;
+    single_thread  -- the grid variant on one thread;
+    c1_full        -- the 2,000-sphere box (seed 1, from rest) for its full 2,000 steps,
+                      O(N^2) search on all cores.
+    The oracle's threads find contacts in parallel and reduce them serially in the
+    serial order, so every variant computes the same trajectory bits."""
     import oracle
     from paper_2311_04648_gb300 import workloads as W
 
-    n = args.cpu_sample_n
-    # a square column holding ~n spheres over the first few hundred lattice layers
-    per_layer = max(1, int(round((n / 28) ** 0.5)) ** 2)
-    side = int(round(per_layer ** 0.5))
-    width = side * 2.45e-3 + 2 * 1.2e-3 + 1e-6
-    s = W.settling_column(n=n, column_width=width)
-    ow = oracle.OracleWorld(s)
-    ow.step(1)
-    t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < args.cpu_sample_seconds:
-        ow.step(5)
-        steps += 5
-    dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{n}-sphere central column of the settling-column generator ({width * 1e3:.1f} mm wide), "
-                      f"{steps} steps in {dt:.1f} s, single thread, brute-force O(N^2) contacts"}
+    threads = max(1, os.cpu_count() or 1)
+    sub = W.settling_column(n=args.cpu_sample_n, column_width=0.03)
+
+    def rate(scene, cell_list, th, steps_cap, seconds):
+        ow = oracle.OracleWorld(scene, cell_list=cell_list, threads=th)
+        assert ow.step(1) == 0
+        t0 = time.perf_counter()
+        k = 0
+        while k < steps_cap and (k == 0 or time.perf_counter() - t0 < seconds):
+            assert ow.step(1) == 0
+            k += 1
+        dt = time.perf_counter() - t0
+        return {"value": scene.n_sphere * k / dt, "steps": k, "seconds": dt, "threads": th}
+
+    cap = 10 ** 9 if max_steps is None else max_steps
+    brute = rate(sub, False, threads, cap, args.cpu_sample_seconds)
+    out = {"value": brute["value"], "unit": METRIC, "cores": threads, "kind": "oracle",
+           "sample": f"{sub.n_sphere}-sphere sub-box of the settling column (0.03 m central column), "
+                     f"{brute['steps']} steps in {brute['seconds']:.1f} s from the lattice, O(N^2) contacts, "
+                     f"{threads} OpenMP threads"}
+    if max_steps is None:
+        grid = rate(sub, True, threads, 500, 30.0)
+        one = rate(sub, True, 1, 500, 4.0)
+        c1 = W.settle_box(n=2000, seed=1)
+        ow = oracle.OracleWorld(c1, threads=threads)
+        t0 = time.perf_counter()
+        assert ow.step(2000) == 0
+        dt = time.perf_counter() - t0
+        out.update(cell_list=grid, single_thread=one,
+                   c1_full={"value": 2000 * 2000 / dt, "steps": 2000, "seconds": dt, "threads": threads,
+                            "what": "2,000 spheres from rest in the 40x40x80 mm box, dt = 1e-6 s, FP64, "
+                                    "O(N^2) contacts every step"},
+                   max_threads_openmp=oracle.max_threads())
+    return out
 
 
 def main():
@@ -555,18 +642,34 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        w = args.warmup
-        args.cpu_sample_seconds = max(3.0, args.cpu_sample_seconds)
-        cb = cpu_baseline(args)
-        line = {"metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": w, "ms_per_step": 1000.0 * args.cpu_sample_n / cb["value"], "higher_is_better": True,
+        # the oracle on the host cores, one oracle step per step of the sub-box sample;
+        # the warm-up and the timed steps are capped so that the run ends within minutes
+        import oracle
+        from paper_2311_04648_gb300 import workloads as W
+        threads = max(1, os.cpu_count() or 1)
+        sub = W.settling_column(n=args.cpu_sample_n, column_width=0.03)
+        ow = oracle.OracleWorld(sub, threads=threads)
+        for _ in range(min(args.warmup, 3)):
+            assert ow.step(1) == 0
+        t0 = time.perf_counter()
+        k = 0
+        while k < args.steps and (k == 0 or time.perf_counter() - t0 < 90.0):
+            assert ow.step(1) == 0
+            k += 1
+        dt = time.perf_counter() - t0
+        value = sub.n_sphere * k / dt
+        sample = (f"{sub.n_sphere}-sphere sub-box of the settling column (0.03 m central column), {k} of "
+                  f"{args.steps} steps timed in {dt:.1f} s, O(N^2) contacts, {threads} OpenMP threads")
+        cb = {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample}
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(k, 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "impl": "reference",
                 "config": {"workload": "settling_column", "n_spheres": args.n, "radius_mm": [0.8, 1.2],
                            "box_m": [0.3, 0.3, 1.2], "dt_s": 2e-6, "precision": "FP64 (the oracle)",
-                           "sample": cb["sample"]},
+                           "sample": sample},
                 "cpu_baseline": cb,
-                "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
 
@@ -634,16 +737,23 @@ def main():
                    "box_m": [0.3, 0.3, 1.2], "dt_s": 2e-6, "precision": "voxel index + FP32 offset, FP32 forces",
                    "schedule": "delayed detection on a second stream, velocity-bound cycle, audited every step",
                    "margin_m": res["chosen"]["stats"]["margin"],
+                   "timed_window": f"steps {res['chosen']['first_step']}-{res['chosen']['first_step'] + steps} "
+                                   f"of the configuration's {args.config_steps} (warm-up from step "
+                                   f"{res['window_start']})",
+                   "listed_pairs_per_sphere": prof["listed_pairs"] / n_sph,
+                   "spheres_with_partners_per_sphere": prof["with_entries"] / n_sph,
+                   "contacts_per_sphere": [c / n_sph for c in res["chosen"]["contacts"]],
                    "rebuilds_in_timed_region": res["chosen"]["rebuilds"],
                    "audit_fallbacks_in_timed_region": res["chosen"]["fallbacks"],
                    "device_copy_gbs_this_gpu": res["copy_gbs"],
                    "tuning": res["tuning"],
                    "l2": "inputs larger than L2 (owner state + contact lists > 0.5 GB)",
                    "parallelism": f"replica x{world}"},
-        "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind, margin=res["chosen"]["stats"]["margin"]),
+        "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind, margin=res["chosen"]["stats"]["margin"],
+                             rebuilds_per_step=res["chosen"]["rebuilds"] / max(steps, 1)),
         "kernels_ms": dict(({"step": prof["contact_ms"]} if fused_step(prof) else
                             {"contact": prof["contact_ms"], "integrate": prof["integrate_ms"]}),
-                           detect=prof["detect_ms"], hash=prof["hash_ms"], link=prof["link_ms"]),
+                           detect_per_rebuild=prof["detect_ms"], hash=prof["hash_ms"], link=prof["link_ms"]),
         "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": e2e["bytes_in"],
                 "d2h_bytes_per_step": e2e["bytes_out"],
                 "how": "dem_set_owner_state from pinned host buffers + dem_step(1) + dem_get_owner_state "
@@ -659,7 +769,7 @@ def main():
                          "kernels_ms": dict(({"step": pp["contact_ms"]} if fused_step(pp) else
                                              {"contact": pp["contact_ms"], "integrate": pp["integrate_ms"]}),
                                             detect=pp["detect_ms"]),
-                         "roofline": roofline("fp64", n_sph, pp, peak, peak_kind),
+                         "roofline": roofline("fp64", n_sph, pp, peak, peak_kind, rebuilds_per_step=1.0),
                          "chosen_over_plain": value / pv}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)

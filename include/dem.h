@@ -140,7 +140,10 @@ const char *dem_last_error(const dem_world *w);
 /* Register a material (Sec. 3.1: LoadMaterial with E, nu, CoR, mu, Crr).  E > 0,
  * 0 <= nu < 0.5, 0 <= CoR <= 1, mu >= 0.  Crr must be 0: rolling resistance is not
  * implemented (DEM_ERR_UNSUPPORTED otherwise).  *mat_id receives the dense id.
- * Pairwise CoR and mu default to the mean of the two materials' values. */
+ * A pair of materials takes the CoR and mu set for it with dem_set_material_pair; a
+ * pair left unset takes its two materials' common value where they agree, and
+ * dem_initialize returns DEM_ERR_STATE where they differ (the paper sets pairwise
+ * properties explicitly and gives no rule for combining two materials). */
 dem_status dem_add_material(dem_world *w, double E, double nu, double CoR, double mu, double Crr,
                             int32_t *mat_id);
 /* Override a pairwise property for materials (a, b), symmetric (Sec. 3.1:
@@ -375,17 +378,22 @@ dem_status dem_util_radix_sort_u32(int64_t n, const uint32_t *keys, const uint32
  * cudaMalloc (code running while a CUDA graph is captured, frameworks that own device
  * memory through their own pools, loops where an allocation could synchronise the
  * device).  Same stable LSD radix sort as dem_util_radix_sort_u32, but on DEVICE
- * buffers owned by the caller: keys[n], vals[n] in, keys_out[n], vals_out[n] out (the
- * outputs must not alias the inputs or each other), queued on `stream` (a cudaStream_t;
+ * buffers owned by the caller: keys[n], vals[n] in, keys_out[n], vals_out[n] out (an
+ * output that shares any byte with an input or with the other output is rejected with
+ * DEM_ERR_ARG), queued on `stream` (a cudaStream_t;
  * NULL = legacy default stream) and returning once queued.  It allocates nothing: its
  * temporary storage is one array of device memory inside the library, sized for
  * DEM_NOALLOC_SORT_MAX keys (about 8.7 MB), which every GPU that loads the library keeps
  * until the process exits.  n above the maximum returns DEM_ERR_CAPACITY before any work.
  * The first call on each device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.  Every
+ * with that device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process, so a device reset (cudaDeviceReset, or
+ * anything else that destroys the primary context) while the library is loaded is not
+ * supported: later calls would use the stale address.  Every
  * call shares the array, so calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller; nothing in it needs clearing
- * between calls.  Errors are described by dem_util_noalloc_error(). */
+ * between calls.  Errors are described by dem_util_noalloc_error(), which describes the
+ * calling thread's last call ("" after a call that succeeded). */
 #define DEM_NOALLOC_SORT_MAX (1 << 20)
 dem_status dem_util_radix_sort_u32_noalloc(int64_t n, const uint32_t *keys, const uint32_t *vals, int32_t bits,
                                            uint32_t *keys_out, uint32_t *vals_out, void *stream);

@@ -41,7 +41,10 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
                "-Wall", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP where the toolchain has it (the parallel loops give the serial results)
+        r = subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -61,7 +64,7 @@ class _World(C.Structure):
                 ("owner", C.c_void_p), ("rloc", C.c_void_p), ("rad", C.c_void_p), ("mat", C.c_void_p),
                 ("h", C.c_double), ("g", C.c_double * 3), ("gyroscopic", C.c_int32), ("has_sink", C.c_int32),
                 ("sink_p", C.c_double * 3), ("sink_n", C.c_double * 3), ("v_err", C.c_double),
-                ("hist", C.c_void_p), ("cell_list", C.c_int32)]
+                ("hist", C.c_void_p), ("cell_list", C.c_int32), ("n_threads", C.c_int32)]
 
 
 class Contact(C.Structure):
@@ -91,11 +94,18 @@ def lib():
             L.orc_step.argtypes = [P, C.c_int64]
             L.orc_diagnostics.argtypes = [P, P, P, P, P, P]
             L.orc_effective_moduli.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, P, P]
+            L.orc_max_threads.restype = C.c_int
+            L.orc_max_threads.argtypes = []
     return _LIB
 
 
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def max_threads() -> int:
+    """Threads the oracle's parallel loops can use (1 without OpenMP)."""
+    return int(lib().orc_max_threads())
 
 
 def effective_moduli(E_a, nu_a, E_b, nu_b):
@@ -151,7 +161,7 @@ class OracleWorld:
     """A world for the oracle, built from a scene description (duck-typed; see
     paper_2311_04648_gb300.workloads.Scene for the fields read here)."""
 
-    def __init__(self, scene, cell_list: bool = False):
+    def __init__(self, scene, cell_list: bool = False, threads: int = 1):
         s = scene
         self.n_mat = len(s.E)
         self.E = np.ascontiguousarray(s.E, np.float64)
@@ -215,6 +225,7 @@ class OracleWorld:
         w.v_err = float(getattr(s, "v_err", 0.0) or 0.0)
         w.hist = lib().orc_history_new()
         w.cell_list = 1 if cell_list else 0
+        w.n_threads = int(threads)
 
     def __del__(self):
         try:

@@ -11,6 +11,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PI 3.14159265358979323846
 
@@ -153,24 +156,32 @@ static int64_t hist_find(const orc_hist *h, int64_t i, int64_t j)
     return -1;
 }
 
+typedef struct { int64_t i, j, k; } hist_ref;
+
+static int hist_ref_cmp(const void *a, const void *b)
+{
+    const hist_ref *x = (const hist_ref *)a, *y = (const hist_ref *)b;
+    if (key_less(x->i, x->j, y->i, y->j)) return -1;
+    if (key_less(y->i, y->j, x->i, x->j)) return 1;
+    return x->k < y->k ? -1 : (x->k > y->k ? 1 : 0);
+}
+
 int orc_history_set(void *hp, int64_t n, const int64_t *i, const int64_t *j, const double *ut)
 {
     orc_hist *h = (orc_hist *)hp;
     if (!h || n < 0) return ORC_ERR_ARG;
     if (hist_reserve(h, n)) return ORC_ERR_NOMEM;
-    /* insertion sort into place (test inputs are small) */
-    h->n = 0;
+    /* entries sorted by (i, partner) for hist_find */
+    hist_ref *r = (hist_ref *)malloc((size_t)(n > 0 ? n : 1) * sizeof(hist_ref));
+    if (!r) return ORC_ERR_NOMEM;
+    for (int64_t k = 0; k < n; ++k) { r[k].i = i[k]; r[k].j = j[k]; r[k].k = k; }
+    qsort(r, (size_t)n, sizeof(hist_ref), hist_ref_cmp);
     for (int64_t k = 0; k < n; ++k) {
-        int64_t pos = h->n;
-        while (pos > 0 && key_less(i[k], j[k], h->i[pos - 1], h->j[pos - 1])) {
-            h->i[pos] = h->i[pos - 1]; h->j[pos] = h->j[pos - 1];
-            memcpy(&h->ut[3 * pos], &h->ut[3 * (pos - 1)], 3 * sizeof(double));
-            --pos;
-        }
-        h->i[pos] = i[k]; h->j[pos] = j[k];
-        memcpy(&h->ut[3 * pos], &ut[3 * k], 3 * sizeof(double));
-        h->n++;
+        h->i[k] = r[k].i; h->j[k] = r[k].j;
+        memcpy(&h->ut[3 * k], &ut[3 * r[k].k], 3 * sizeof(double));
     }
+    h->n = n;
+    free(r);
     return 0;
 }
 
@@ -191,6 +202,9 @@ int orc_history_get(const void *hp, int64_t cap, int64_t *n, int64_t *i, int64_t
 
 int orc_sphere_positions(const orc_world *w, double *p)
 {
+    const int nt = w->n_threads > 1 ? w->n_threads : 1;
+    (void)nt;
+#pragma omp parallel for num_threads(nt) if (nt > 1) schedule(static)
     for (int64_t s = 0; s < w->n_sphere; ++s) {
         int64_t o = w->owner[s];
         double R[9], r[3];
@@ -250,6 +264,18 @@ static int wall_gap(const orc_wall *wl, const double c[3], double *gap, double n
 }
 
 static int owner_is_active(const orc_world *w, int64_t o) { return w->active ? w->active[o] != 0 : 1; }
+
+/* Threads of the parallel loops (1 = serial). */
+static int n_threads(const orc_world *w) { return w->n_threads > 1 ? w->n_threads : 1; }
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 int orc_listed_pairs_f64(int64_t n, const double *p, const double *rad, const int64_t *owner,
                          const uint8_t *sphere_active, double beta, int64_t cap,
@@ -478,17 +504,17 @@ static int cbuf_push(contact_buf *b, const orc_contact *c)
 }
 
 /* One candidate partner jj of sphere i (a sphere when jj < N, else wall jj - N): if the
- * two touch, the contact's force with its updated history, added to the owners' sums. */
-static int visit_partner(const orc_world *w, const double *p, const orc_hist *h, int64_t i, int64_t jj,
-                         double *F, double *T, contact_buf *out)
+ * two touch, the contact with its force and updated history in *rec; returns 1 then. */
+static int contact_of(const orc_world *w, const double *p, const orc_hist *h, int64_t i, int64_t jj,
+                      orc_contact *rec)
 {
     int64_t N = w->n_sphere;
     int64_t oa = w->owner[i];
     contact_in ci;
-    int64_t j, ob = -1;
+    int64_t j;
     if (jj < N) {
         j = jj;
-        ob = w->owner[j];
+        int64_t ob = w->owner[j];
         if (ob == oa || !owner_is_active(w, ob)) return 0;
         if (!sphere_pair_contact(w, p, i, j, &ci)) return 0;
     } else {
@@ -496,29 +522,34 @@ static int visit_partner(const orc_world *w, const double *p, const orc_hist *h,
         j = -1 - (int64_t)k;
         if (!sphere_wall_contact(w, p, i, k, &ci)) return 0;
     }
-    orc_contact rec;
-    memset(&rec, 0, sizeof(rec));
-    rec.i = i; rec.j = j;
+    memset(rec, 0, sizeof(*rec));
+    rec->i = i; rec->j = j;
     int64_t hk = h ? hist_find(h, i, j) : -1;
-    if (hk >= 0) { rec.ut[0] = h->ut[3 * hk]; rec.ut[1] = h->ut[3 * hk + 1]; rec.ut[2] = h->ut[3 * hk + 2]; }
-    hertz_mindlin(&ci, w->h, rec.ut, rec.force);
-    memcpy(rec.point, ci.c, sizeof(ci.c));
-    memcpy(rec.normal, ci.n, sizeof(ci.n));
-    rec.overlap = ci.delta;
-    /* reduction onto the owners: F on A, -F on B; torques about the centres of mass */
-    double rA[3] = {ci.c[0] - w->x[3 * oa], ci.c[1] - w->x[3 * oa + 1], ci.c[2] - w->x[3 * oa + 2]};
+    if (hk >= 0) { rec->ut[0] = h->ut[3 * hk]; rec->ut[1] = h->ut[3 * hk + 1]; rec->ut[2] = h->ut[3 * hk + 2]; }
+    hertz_mindlin(&ci, w->h, rec->ut, rec->force);
+    memcpy(rec->point, ci.c, sizeof(ci.c));
+    memcpy(rec->normal, ci.n, sizeof(ci.n));
+    rec->overlap = ci.delta;
+    return 1;
+}
+
+/* Reduction of one contact onto the owners (Eqs. 5a-5b): F on A's owner, -F on B's;
+ * torques about the centres of mass. */
+static void add_to_owners(const orc_world *w, const orc_contact *rec, double *F, double *T)
+{
+    int64_t oa = w->owner[rec->i];
+    double rA[3] = {rec->point[0] - w->x[3 * oa], rec->point[1] - w->x[3 * oa + 1], rec->point[2] - w->x[3 * oa + 2]};
     double tA[3];
-    cross3(rA, rec.force, tA);
-    for (int k = 0; k < 3; ++k) { F[3 * oa + k] += rec.force[k]; T[3 * oa + k] += tA[k]; }
-    if (ob >= 0) {
-        double rB[3] = {ci.c[0] - w->x[3 * ob], ci.c[1] - w->x[3 * ob + 1], ci.c[2] - w->x[3 * ob + 2]};
-        double mf[3] = {-rec.force[0], -rec.force[1], -rec.force[2]};
+    cross3(rA, rec->force, tA);
+    for (int k = 0; k < 3; ++k) { F[3 * oa + k] += rec->force[k]; T[3 * oa + k] += tA[k]; }
+    if (rec->j >= 0) {
+        int64_t ob = w->owner[rec->j];
+        double rB[3] = {rec->point[0] - w->x[3 * ob], rec->point[1] - w->x[3 * ob + 1], rec->point[2] - w->x[3 * ob + 2]};
+        double mf[3] = {-rec->force[0], -rec->force[1], -rec->force[2]};
         double tB[3];
         cross3(rB, mf, tB);
         for (int k = 0; k < 3; ++k) { F[3 * ob + k] += mf[k]; T[3 * ob + k] += tB[k]; }
     }
-    if (out) return cbuf_push(out, &rec);
-    return 0;
 }
 
 /* ------------------------------------------------------------------ optional grid
@@ -657,7 +688,12 @@ static int64_t grid_candidates(const grid_ent *e, int64_t n, const int64_t *star
 }
 
 /* Every contact with delta > 0 in (i, partner) order, each with its force and updated
- * history; per-owner force (gravity first, then contacts) and torque sums. */
+ * history; per-owner force (gravity first, then contacts) and torque sums.
+ * The contacts of each block of spheres are found independently (in parallel when
+ * w->n_threads > 1); the reduction onto the owners then runs serially in (i, partner)
+ * order, so every sum, and the result, is the same whatever the thread count. */
+#define ORC_BLOCK 64
+
 static int evaluate(const orc_world *w, const double *p, double *F, double *T, contact_buf *out)
 {
     const orc_hist *h = (const orc_hist *)w->hist;
@@ -671,32 +707,56 @@ static int evaluate(const orc_world *w, const double *p, double *F, double *T, c
         T[3 * o + 0] = 0.0; T[3 * o + 1] = 0.0; T[3 * o + 2] = 0.0;
     }
     grid_ent *ge = NULL;
-    int64_t ng = 0, *home = NULL, *cand = NULL, *start = NULL, dims[3] = {0, 0, 0};
+    int64_t ng = 0, *home = NULL, *start = NULL, dims[3] = {0, 0, 0};
     int use_grid = 0;
     if (w->cell_list) {
         use_grid = grid_build(w, p, &ge, &ng, &home);
         if (use_grid < 0) return use_grid;
-        if (use_grid) {
-            cand = (int64_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
-            if (!cand) { free(ge); free(home); return ORC_ERR_NOMEM; }
-            start = grid_starts(ge, ng, dims);
-        }
+        if (use_grid) start = grid_starts(ge, ng, dims);
     }
+    int64_t nblk = (N + ORC_BLOCK - 1) / ORC_BLOCK;
+    contact_buf *blk = (contact_buf *)calloc((size_t)(nblk > 0 ? nblk : 1), sizeof(contact_buf));
+    if (!blk) { free(start); free(home); free(ge); return ORC_ERR_NOMEM; }
     int err = 0;
-    for (int64_t i = 0; i < N && !err; ++i) {
-        if (!owner_is_active(w, w->owner[i])) continue;
-        /* sphere partners j > i first, then walls in ascending id */
-        if (use_grid) {
-            int64_t nc = grid_candidates(ge, ng, start, dims, &home[3 * i], i, cand);
-            for (int64_t a = 0; a < nc && !err; ++a) err = visit_partner(w, p, h, i, cand[a], F, T, out);
-            for (int64_t jj = N; jj < N + w->n_wall && !err; ++jj) err = visit_partner(w, p, h, i, jj, F, T, out);
-        } else {
-            for (int64_t jj = i + 1; jj < N + w->n_wall && !err; ++jj)
-                err = visit_partner(w, p, h, i, jj, F, T, out);
+    const int nt = n_threads(w);
+    (void)nt;
+#pragma omp parallel num_threads(nt) if (nt > 1)
+    {
+        int64_t *cand = use_grid ? (int64_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t)) : NULL;
+        int my_err = (use_grid && !cand) ? ORC_ERR_NOMEM : 0;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t b = 0; b < nblk; ++b) {
+            int64_t i_end = (b + 1) * ORC_BLOCK < N ? (b + 1) * ORC_BLOCK : N;
+            for (int64_t i = b * ORC_BLOCK; i < i_end && !my_err; ++i) {
+                if (!owner_is_active(w, w->owner[i])) continue;
+                orc_contact rec;
+                /* sphere partners j > i first, then walls in ascending id */
+                if (use_grid) {
+                    int64_t nc = grid_candidates(ge, ng, start, dims, &home[3 * i], i, cand);
+                    for (int64_t a = 0; a < nc && !my_err; ++a)
+                        if (contact_of(w, p, h, i, cand[a], &rec)) my_err = cbuf_push(&blk[b], &rec);
+                    for (int64_t jj = N; jj < N + w->n_wall && !my_err; ++jj)
+                        if (contact_of(w, p, h, i, jj, &rec)) my_err = cbuf_push(&blk[b], &rec);
+                } else {
+                    for (int64_t jj = i + 1; jj < N + w->n_wall && !my_err; ++jj)
+                        if (contact_of(w, p, h, i, jj, &rec)) my_err = cbuf_push(&blk[b], &rec);
+                }
+            }
+        }
+        free(cand);
+        if (my_err) {
+#pragma omp critical
+            err = my_err;
         }
     }
+    for (int64_t b = 0; b < nblk && !err; ++b)
+        for (int64_t k = 0; k < blk[b].n && !err; ++k) {
+            add_to_owners(w, &blk[b].c[k], F, T);
+            if (out) err = cbuf_push(out, &blk[b].c[k]);
+        }
+    for (int64_t b = 0; b < nblk; ++b) free(blk[b].c);
+    free(blk);
     free(start);
-    free(cand);
     free(home);
     free(ge);
     return err;
@@ -786,6 +846,9 @@ int orc_step(orc_world *w, int64_t nsteps)
         if (err) goto done;
         err = replace_history(w, &buf);
         if (err) goto done;
+        const int nt = n_threads(w);
+        (void)nt;
+#pragma omp parallel for num_threads(nt) if (nt > 1) schedule(static)
         for (int64_t o = 0; o < M; ++o)
             if (owner_is_active(w, o)) integrate_owner(w, o, &F[3 * o], &T[3 * o]);
         if (w->has_sink && w->active) {
@@ -813,24 +876,40 @@ done:
 
 /* ------------------------------------------------------------------ diagnostics */
 
+/* Neumaier's compensated sum: the running sum and the lost low-order parts. */
+typedef struct { double s, c; } csum;
+
+static void csum_add(csum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double csum_get(const csum *a) { return a->s + a->c; }
+
 int orc_diagnostics(const orc_world *w, double *ke, double *pe, double *elastic, double *mom, double *angmom)
 {
     int64_t M = w->n_owner, N = w->n_sphere;
-    double k = 0.0, u = 0.0, el = 0.0;
-    double P[3] = {0.0, 0.0, 0.0}, L[3] = {0.0, 0.0, 0.0};
+    csum k = {0.0, 0.0}, u = {0.0, 0.0}, el = {0.0, 0.0};
+    csum P[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}}, L[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
     for (int64_t o = 0; o < M; ++o) {
         const double *v = &w->v[3 * o], *x = &w->x[3 * o], *wb = &w->wb[3 * o], *I = &w->moi[3 * o];
         double m = w->mass[o];
-        k += 0.5 * m * dot3(v, v);
-        k += 0.5 * ((I[0] * wb[0] * wb[0] + I[1] * wb[1] * wb[1]) + I[2] * wb[2] * wb[2]);
-        u -= m * dot3(w->g, x);
+        csum_add(&k, 0.5 * m * dot3(v, v));
+        csum_add(&k, 0.5 * ((I[0] * wb[0] * wb[0] + I[1] * wb[1] * wb[1]) + I[2] * wb[2] * wb[2]));
+        csum_add(&u, -(m * dot3(w->g, x)));
         double mv[3] = {m * v[0], m * v[1], m * v[2]};
-        P[0] += mv[0]; P[1] += mv[1]; P[2] += mv[2];
         double orb[3], R[9], Iw[3] = {I[0] * wb[0], I[1] * wb[1], I[2] * wb[2]}, spin[3];
         cross3(x, mv, orb);
         quat_matrix(&w->q[4 * o], R);
         mat_vec(R, Iw, spin);
-        L[0] += orb[0] + spin[0]; L[1] += orb[1] + spin[1]; L[2] += orb[2] + spin[2];
+        for (int a = 0; a < 3; ++a) {
+            csum_add(&P[a], mv[a]);
+            csum_add(&L[a], orb[a]);
+            csum_add(&L[a], spin[a]);
+        }
     }
     double *p = (double *)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(double));
     if (!p) return ORC_ERR_NOMEM;
@@ -845,14 +924,14 @@ int orc_diagnostics(const orc_world *w, double *ke, double *pe, double *elastic,
             } else {
                 if (!sphere_wall_contact(w, p, i, (int32_t)(jj - N), &ci)) continue;
             }
-            el += (8.0 / 15.0) * ci.Estar * sqrt(ci.Rbar) * ci.delta * ci.delta * sqrt(ci.delta);
+            csum_add(&el, (8.0 / 15.0) * ci.Estar * sqrt(ci.Rbar) * ci.delta * ci.delta * sqrt(ci.delta));
         }
     }
     free(p);
-    if (ke) *ke = k;
-    if (pe) *pe = u;
-    if (elastic) *elastic = el;
-    if (mom) { mom[0] = P[0]; mom[1] = P[1]; mom[2] = P[2]; }
-    if (angmom) { angmom[0] = L[0]; angmom[1] = L[1]; angmom[2] = L[2]; }
+    if (ke) *ke = csum_get(&k);
+    if (pe) *pe = csum_get(&u);
+    if (elastic) *elastic = csum_get(&el);
+    if (mom) { for (int a = 0; a < 3; ++a) mom[a] = csum_get(&P[a]); }
+    if (angmom) { for (int a = 0; a < 3; ++a) angmom[a] = csum_get(&L[a]); }
     return 0;
 }

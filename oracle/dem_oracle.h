@@ -76,6 +76,10 @@ typedef struct {
     int32_t cell_list;              /* 1: enumerate candidates from a uniform grid instead
                                        of all j > i; the same contacts in the same order,
                                        so results are bit-identical (a faster variant)   */
+    int32_t n_threads;              /* > 1: find contacts and integrate owners on that
+                                       many OpenMP threads; the reduction onto owners stays
+                                       serial in (i, partner) order, so results are
+                                       bit-identical to one thread                        */
 } orc_world;
 
 /* One resolved contact.  j >= 0 is a sphere, j < 0 is wall (-1 - j).  force acts on
@@ -135,9 +139,14 @@ int orc_step(orc_world *w, int64_t nsteps);
 
 /* Diagnostics in FP64: kinetic (translational + rotational), gravitational potential
  * -sum m g.x, Hertz elastic energy sum (8/15) E* sqrt(Rbar) delta^(5/2) over contacts,
- * linear momentum, angular momentum about the origin (orbital + spin). */
+ * linear momentum, angular momentum about the origin (orbital + spin).  Every sum is
+ * compensated (Neumaier's variant of Kahan summation), so it is accurate to a few ulps
+ * of the sum of the magnitudes of its terms whatever their number. */
 int orc_diagnostics(const orc_world *w, double *ke, double *pe, double *elastic,
                     double *mom, double *angmom);
+
+/* Threads OpenMP would use (1 when built without OpenMP). */
+int orc_max_threads(void);
 
 /* Material combination used for E* and G* (readings of the unstated formula). */
 void orc_effective_moduli(double E_a, double nu_a, double E_b, double nu_b,

@@ -77,3 +77,28 @@ def loss_grad(p, X, Y, bf=True):
     g["b1"] = d_h1.sum(axis=0)
     grad = np.concatenate([g[name].ravel() for name, _ in SHAPES])
     return L, grad
+
+
+def blocks():
+    """(name, slice) of each parameter block in the flat layout."""
+    out, k = [], 0
+    for name, shp in SHAPES:
+        m = int(np.prod(shp))
+        out.append((name, slice(k, k + m)))
+        k += m
+    return out
+
+
+def gradient_tolerance(g_ref):
+    """Per-element tolerance of a BF16-operand gradient against g_ref (this oracle with
+    bf=True): one BF16 ulp of the element (2^-7 of it), plus 2^-14 of the largest entry
+    of its block for entries that cancel to near zero.  Both sides round the same
+    operands to BF16; they differ only in the precision of the sums and intermediates
+    (FP32 against FP64), which moves an operand across a BF16 rounding boundary only
+    rarely, and then changes one term of a sum by one BF16 ulp."""
+    g_ref = np.asarray(g_ref, np.float64)
+    tol = np.empty_like(g_ref)
+    for _, sl in blocks():
+        tol[sl] = 2.0 ** -7 * np.abs(g_ref[sl]) + 2.0 ** -14 * np.max(np.abs(g_ref[sl]))
+    return tol
+

@@ -284,11 +284,21 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
             m.mat_scene.push_back((uint16_t)si);
             m.mat_local.push_back((uint16_t)a);
         }
+        // Pairwise restitution and friction (Sec. 3.1 sets them per pair and states no
+        // rule for combining two materials): a pair takes the value set for it, or the
+        // common value of its two materials where they agree; two materials that differ
+        // and have no value set for the pair are an error.
         for (int a = 0; a < nm; ++a)
             for (int b = 0; b < nm; ++b) {
                 auto key = std::make_pair(std::min(a, b), std::max(a, b));
-                double cor = sc.cor_pair.count(key) ? sc.cor_pair[key] : 0.5 * (sc.cor[a] + sc.cor[b]);
-                double mu = sc.mu_pair.count(key) ? sc.mu_pair[key] : 0.5 * (sc.mu[a] + sc.mu[b]);
+                if ((!sc.cor_pair.count(key) && sc.cor[a] != sc.cor[b]) ||
+                    (!sc.mu_pair.count(key) && sc.mu[a] != sc.mu[b])) {
+                    err = "materials " + std::to_string(key.first) + " and " + std::to_string(key.second) +
+                          " differ in CoR or mu: set the pair's value with dem_set_material_pair";
+                    return DEM_ERR_STATE;
+                }
+                double cor = sc.cor_pair.count(key) ? sc.cor_pair[key] : sc.cor[a];
+                double mu = sc.mu_pair.count(key) ? sc.mu_pair[key] : sc.mu[a];
                 m.pairs.push_back(pair_param(sc.E[a], sc.nu[a], sc.E[b], sc.nu[b], cor, mu));
             }
         mat_base += nm;

@@ -37,6 +37,9 @@ void *g_ptr[MAX_DEV] = {};
 
 thread_local const char *g_msg = "";
 
+// [a, a + len) and [b, b + len) share a byte
+bool ranges_overlap(uint64_t a, uint64_t b, uint64_t len) { return a < b + len && b < a + len; }
+
 }  // namespace
 }  // namespace dem
 
@@ -48,12 +51,19 @@ extern "C" dem_status dem_util_radix_sort_u32_noalloc(int64_t n, const uint32_t 
                                                        int32_t bits, uint32_t *keys_out, uint32_t *vals_out,
                                                        void *stream)
 {
+    g_msg = "";                          // a message describes the last call only
     if (n < 0 || bits < 1 || bits > 32) { g_msg = "need n >= 0 and 1 <= bits <= 32"; return DEM_ERR_ARG; }
     if (n > MAXN) { g_msg = "n exceeds DEM_NOALLOC_SORT_MAX keys"; return DEM_ERR_CAPACITY; }
     if (n == 0) return DEM_OK;
     if (!keys || !vals || !keys_out || !vals_out) { g_msg = "null buffer"; return DEM_ERR_ARG; }
-    if (keys_out == keys || vals_out == vals || keys_out == vals_out) {
-        g_msg = "output buffers must differ from the inputs and from each other";
+    // a pass reads its whole input while other blocks write its output: neither output
+    // may share a byte with an input or with the other output
+    const uint64_t bytes = 4ull * (uint64_t)n;
+    const uint64_t ko = (uint64_t)(uintptr_t)keys_out, vo = (uint64_t)(uintptr_t)vals_out;
+    const uint64_t ki = (uint64_t)(uintptr_t)keys, vi = (uint64_t)(uintptr_t)vals;
+    if (ranges_overlap(ko, ki, bytes) || ranges_overlap(ko, vi, bytes) || ranges_overlap(vo, ki, bytes) ||
+        ranges_overlap(vo, vi, bytes) || ranges_overlap(ko, vo, bytes)) {
+        g_msg = "output buffers must not overlap the inputs or each other";
         return DEM_ERR_ARG;
     }
     int dev = 0;

@@ -173,13 +173,25 @@ def mlp_loss_grad(params, X, Y):
     return loss.value, grad
 
 
+# device allocator callbacks of dem_world_desc: void *alloc(size_t, void *ctx), void free(void *, void *ctx)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class World:
-    """One simulated world (or, with ``_handle``, one scene of a :class:`Batch`)."""
+    """One simulated world (or, with ``_handle``, one scene of a :class:`Batch`).
+
+    ``stream`` / ``detect_stream``: cudaStream_t handles (ints) the library runs on
+    instead of its own.  ``alloc(nbytes) -> device pointer`` and ``free(pointer)``: a
+    device allocator the library takes all its memory from (both or neither); they must
+    stay callable until the world is closed."""
 
     def __init__(self, box_lo=(0, 0, 0), box_hi=(1, 1, 1), precision="fp64", schedule="every_step", device=0,
-                 gyroscopic=True, margin_max=0.0, _handle=None, _batch=None):
+                 gyroscopic=True, margin_max=0.0, stream=None, detect_stream=None, alloc=None, free=None,
+                 _handle=None, _batch=None):
         self.L = load()
         self._batch = _batch
+        self._callbacks = None
         if _handle is not None:
             self.h = _handle
             return
@@ -192,6 +204,16 @@ class World:
         d.device = device
         d.gyroscopic = 1 if gyroscopic else 0
         d.margin_max = margin_max
+        d.stream = stream
+        d.detect_stream = detect_stream
+        if (alloc is None) != (free is None):
+            raise ValueError("alloc and free go together")
+        if alloc is not None:
+            cb_a = ALLOC_FN(lambda nbytes, ctx: alloc(int(nbytes)) or None)
+            cb_f = FREE_FN(lambda ptr, ctx: free(ptr))
+            self._callbacks = (cb_a, cb_f)            # alive until the world is destroyed
+            d.alloc = C.cast(cb_a, C.c_void_p)
+            d.free = C.cast(cb_f, C.c_void_p)
         h = C.c_void_p()
         _check(self.L.dem_world_create(C.byref(d), C.byref(h)))
         self.h = h
@@ -200,6 +222,7 @@ class World:
         if getattr(self, "h", None) is not None and self._batch is None:
             self.L.dem_world_destroy(self.h)
         self.h = None
+        self._callbacks = None
 
     def __del__(self):
         try:
@@ -443,10 +466,8 @@ class World:
             self.add_material(float(scene.E[a]), float(scene.nu[a]), float(cor[a, a]), float(mu[a, a]))
         for a in range(nm):
             for b in range(a + 1, nm):
-                if cor[a, b] != 0.5 * (cor[a, a] + cor[b, b]):
-                    self.set_material_pair(PROP_COR, a, b, float(cor[a, b]))
-                if mu[a, b] != 0.5 * (mu[a, a] + mu[b, b]):
-                    self.set_material_pair(PROP_MU, a, b, float(mu[a, b]))
+                self.set_material_pair(PROP_COR, a, b, float(cor[a, b]))
+                self.set_material_pair(PROP_MU, a, b, float(mu[a, b]))
         for wd in scene.walls:
             t = int(wd["type"])
             om = np.asarray(wd.get("omega", (0.0, 0.0, 0.0)), np.float64)
@@ -479,10 +500,10 @@ class World:
 
     @classmethod
     def from_scene(cls, scene, precision="fp64", schedule="every_step", margin=None, margin_max=0.0, device=0,
-                   gyroscopic=None, initialize=True):
+                   gyroscopic=None, initialize=True, **hooks):
         g = scene.gyroscopic if gyroscopic is None else gyroscopic
         w = cls(scene.box_lo, scene.box_hi, precision=precision, schedule=schedule, device=device, gyroscopic=g,
-                margin_max=margin_max)
+                margin_max=margin_max, **hooks)
         w.setup_scene(scene, margin=margin)
         if initialize:
             w.initialize()

@@ -37,7 +37,25 @@ def test_layout_bytes_exceed_the_algorithmic_figure(bench):
 
 def _prof(n_integrate, contact_ms=0.2, integrate_ms=0.15):
     return {"n_integrate": n_integrate, "n_contact": 100, "contact_ms": contact_ms, "integrate_ms": integrate_ms,
-            "listed_pairs": 1.0e6, "with_entries": 1.5e6}
+            "listed_pairs": 1.0e6, "with_entries": 1.5e6, "n_detect": 0, "detect_ms": 0.0}
+
+
+def test_detection_bytes_follow_the_per_unit_figures(bench):
+    # per sphere 20 + 24 + 48 + 4 B (voxel form; FP64 24 + 24 + 48 + 4), per listed pair
+    # 8 B written plus the remap 2 (8 + 12) B (FP64 2 (8 + 24) B)
+    assert bench.detection_bytes("voxel_fp32", 1000, 250) == 96 * 1000 + 48 * 250
+    assert bench.detection_bytes("fp64", 1000, 250) == 100 * 1000 + 72 * 250
+
+
+def test_roofline_reports_the_detection_phase_beside_the_kernels(bench):
+    prof = dict(_prof(100, 0.15, 0.152), n_detect=10, detect_ms=3.0)
+    r = bench.roofline("voxel_fp32", 4_000_000, prof, 6768.8, "measured", rebuilds_per_step=0.1)
+    d = r["kernels"]["detect"]
+    assert d["bytes"] == 96 * 4_000_000 + 48 * 1.0e6
+    assert d["gbs"] == pytest.approx(d["bytes"] / 3.0e-3 / 1e9)
+    assert d["ms_per_step"] == pytest.approx(0.3)
+    # the detection phase is not a kernel: the dominant kernel stays a per-step kernel
+    assert r["kernel"].startswith("k_integrate")
 
 
 def test_roofline_picks_the_dominant_kernel(bench):
@@ -77,7 +95,9 @@ def test_bench_line_carries_the_contract_keys(bench, monkeypatch, capsys):
     prof = dict(_prof(100, 0.15, 0.152), n_detect=10, detect_ms=3.0, hash_ms=0.09, link_ms=0.2)
     stats = {"margin": 2.1e-5}
     res = {"chosen": {"ms": 1825.0, "steps": 5000, "rebuilds": 488, "fallbacks": 0, "stats": stats,
-                      "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 30}},
+                      "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 30},
+                      "first_step": 50, "contacts": (600_000, 700_000)},
+           "window_start": 0,
            "profile": prof, "copy_gbs": 6700.0, "tuning": {"fused_block": 0, "margin": 2.1e-5},
            "e2e": {"seconds": 0.08, "steps": 8, "bytes_in": 416_000_000, "bytes_out": 416_000_000},
            "n_spheres": 4_000_000, "clumps": False,
@@ -97,3 +117,5 @@ def test_bench_line_carries_the_contract_keys(bench, monkeypatch, capsys):
     assert r["kernel"].startswith("k_integrate") and r["unit"] == "GB/s"
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert line["e2e"]["h2d_bytes_per_step"] == 416_000_000
+    assert line["config"]["listed_pairs_per_sphere"] == pytest.approx(0.25)
+    assert "detect" in r["kernels"]

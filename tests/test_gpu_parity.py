@@ -6,6 +6,7 @@ voxel + FP32 form within 1e-4 on per-contact forces (error normalised by
 max(|F64|, 1e-3 median |F64|)); schedules and batching bit-identical to the plain run.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -16,6 +17,11 @@ from paper_2311_04648_gb300 import dem, workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-9
+# free-running trajectories of dense packings over hundreds of steps: neighbouring
+# trajectories separate (each collision amplifies the last-bit differences of the two
+# evaluation orders), so these compare at the measured separation bound; the 1e-9 bar is
+# held step by step from the GPU's own states (test_fp64_one_step_parity_from_gpu_states)
+TOL64_FREE = 1e-8
 
 
 def dense_scene(n=1200, seed=3, vel=0.2, e=0.5, mu=0.4, h=1e-6):
@@ -148,6 +154,108 @@ def state_close(w, ow, tol):
     return errs, max(errs.values()) < tol
 
 
+def oracle_threads():
+    return max(1, os.cpu_count() or 1)
+
+
+def sync_oracle_to_gpu(w, ow, stored):
+    """Put the oracle at the GPU's current state: the owner state, and as the stored
+    tangential history the updated history the GPU reported one step earlier
+    (``stored``: ``dem.World.contacts`` of the previous state, None at the start).
+    Owners the sink removed stay removed on both sides (the oracle's own flags; the GPU
+    reports zero velocities for them)."""
+    x, q, v, wb = w.owner_state()
+    gone = ow.active == 0
+    assert np.all(v[gone] == 0.0) and np.all(wb[gone] == 0.0)
+    ow.x[:] = x
+    ow.q[:] = q
+    ow.v[:] = v
+    ow.wb[:] = wb
+    if stored is None:
+        ow.set_history(np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros((0, 3)))
+    else:
+        ow.set_history(stored["i"], stored["j"], stored["history"])
+
+
+def one_step_parity(w, ow, stored, tol=TOL64):
+    """From the GPU's own state: every contact's force, overlap, point and updated
+    history, the per-owner force and torque sums, and the state after one step, against
+    the oracle at 1e-9 (forces per contact relative to its largest component; overlaps
+    relative to the largest radius; histories relative to the largest history; sums
+    relative to the summed magnitudes).  Returns the largest errors and the contacts."""
+    sync_oracle_to_gpu(w, ow, stored)
+    gc = w.contacts()
+    Fo, To, oc = ow.eval()
+    assert np.array_equal(gc["i"], oc["i"]) and np.array_equal(gc["j"], oc["j"])
+    fs = np.abs(oc["force"]).max(axis=1, keepdims=True) + 1e-300
+    hs = max(float(np.max(np.abs(oc["ut"]))) if len(oc) else 0.0, 1e-300)
+    Fg, Tg = w.owner_forces()
+    errs = dict(force=rel_err(gc["force"], oc["force"], fs) if len(oc) else 0.0,
+                overlap=rel_err(gc["overlap"], oc["overlap"], float(np.max(ow.rad))) if len(oc) else 0.0,
+                point=rel_err(gc["point"], oc["point"], 1e-3) if len(oc) else 0.0,
+                history=rel_err(gc["history"], oc["ut"], hs) if len(oc) else 0.0,
+                F=rel_err(Fg, Fo, owner_scale(ow, oc, Fo)), T=rel_err(Tg, To, torque_scale(ow, oc)))
+    assert max(errs.values()) < tol, errs
+    w.step(1)
+    assert ow.step(1) == 0
+    st, ok = state_close(w, ow, tol)
+    assert ok, st
+    errs.update(st)
+    return errs, len(oc)
+
+
+ONE_STEP_SCENES = {
+    # name: (scene, free-running steps between the one-step checks)
+    "dense_polydisperse": (lambda: dense_scene(n=600, seed=8, vel=0.5), (50, 100, 200)),
+    "clumps_walls_gravity": (lambda: W.packed_clumps(n=150, seed=10), (100, 200)),
+    "spinning_drum": (lambda: W.drum_bed(n=120, seed=1), (300, 700)),
+    "cone_hopper_sink": (lambda: W.cone_bed(n=300, seed=13), (300, 600)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ONE_STEP_SCENES))
+def test_fp64_one_step_parity_from_gpu_states(name):
+    """One-step parity (contact forces, sums, state, history) at 1e-9 from the GPU's own
+    state at several steps of a run: the binding check where the free-running comparison
+    is limited by the separation of nearby trajectories in dense packings."""
+    make, chunks = ONE_STEP_SCENES[name]
+    s = make()
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    report = []
+    errs, n = one_step_parity(w, ow, None)
+    report.append((0, n, errs))
+    for k in chunks:
+        w.step(k - 1)
+        assert ow.step(k - 1) == 0
+        stored = w.contacts()          # the history the next step stores
+        w.step(1)
+        assert ow.step(1) == 0
+        errs, n = one_step_parity(w, ow, stored)
+        report.append((w.stats()["steps"] - 1, n, errs))
+    print(name, [(d, n, {k: f"{v:.2g}" for k, v in e.items()}) for d, n, e in report])
+    assert sum(n for _, n, _ in report) > 20
+
+
+@pytest.mark.parametrize("seed,vel", [(1, 0.0), (2, 0.3)], ids=["C1_from_rest", "C1b_random_velocities"])
+def test_fp64_full_c1_run_matches_oracle(seed, vel):
+    """The 2,000-sphere box (R = 1 mm, 40 x 40 x 80 mm, dt = 1e-6 s, FP64, detection every
+    step) for its full 2,000 steps, free-running, compared every 500 steps at 1e-9."""
+    s = W.settle_box(n=2000, seed=seed, vel_sigma=vel)
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    worst = {}
+    for _ in range(4):
+        w.step(500)
+        assert ow.step(500) == 0
+        errs, ok = state_close(w, ow, TOL64)
+        assert ok, errs
+        worst = {k: max(worst.get(k, 0.0), v) for k, v in errs.items()}
+    st = w.stats()
+    assert st["steps"] == 2000 and st["rebuilds"] >= 2000
+    print("C1", seed, {k: f"{v:.2g}" for k, v in worst.items()}, "contacts", len(ow.eval()[2]))
+
+
 def test_fp64_trajectory_matches_oracle_random_spheres_in_a_box():
     s = W.settle_box(n=2000, seed=2, vel_sigma=0.3)       # 2,000 spheres, 40x40x80 mm box
     w = dem.World.from_scene(s, precision="fp64")
@@ -161,25 +269,29 @@ def test_fp64_trajectory_matches_oracle_random_spheres_in_a_box():
     assert st["steps"] == 300 and st["rebuilds"] >= 300
 
 
-def test_fp64_trajectory_matches_oracle_dense_polydisperse():
-    s = dense_scene(n=600, seed=8, vel=0.5)
+def _free_running(s, chunks):
     w = dem.World.from_scene(s, precision="fp64")
-    ow = oracle.OracleWorld(s)
-    w.step(200)
-    ow.step(200)
-    errs, ok = state_close(w, ow, 1e-8)
-    assert ok, errs
-    compare_contacts(w, ow, 1e-8)
+    ow = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    worst = {}
+    for k in chunks:
+        w.step(k)
+        assert ow.step(k) == 0
+        errs, _ = state_close(w, ow, TOL64)
+        worst = {a: max(worst.get(a, 0.0), b) for a, b in errs.items()}
+    return w, ow, worst
+
+
+def test_fp64_trajectory_matches_oracle_dense_polydisperse():
+    w, ow, worst = _free_running(dense_scene(n=600, seed=8, vel=0.5), (100, 100))
+    print("dense free-running", worst)
+    assert max(worst.values()) < TOL64_FREE, worst
+    compare_contacts(w, ow, TOL64_FREE)
 
 
 def test_fp64_trajectory_matches_oracle_clumps_with_walls_and_gravity():
-    s = W.packed_clumps(n=150, seed=10)
-    w = dem.World.from_scene(s, precision="fp64")
-    ow = oracle.OracleWorld(s)
-    w.step(300)
-    ow.step(300)
-    errs, ok = state_close(w, ow, 1e-8)
-    assert ok, errs
+    w, ow, worst = _free_running(W.packed_clumps(n=150, seed=10), (150, 150))
+    print("clumps free-running", worst)
+    assert max(worst.values()) < TOL64_FREE, worst
 
 
 def test_fp64_trajectory_matches_oracle_in_a_spinning_drum():
@@ -187,24 +299,24 @@ def test_fp64_trajectory_matches_oracle_in_a_spinning_drum():
     w = dem.World.from_scene(s, precision="fp64")
     ow = oracle.OracleWorld(s)
     wall_contacts = 0
+    worst = {}
     for _ in range(10):
         w.step(100)
         ow.step(100)
         cs = ow.eval()[2]
         wall_contacts += int(np.sum(cs["j"] < 0))
-    errs, ok = state_close(w, ow, 1e-8)
-    assert ok, errs
+        errs, _ = state_close(w, ow, TOL64)
+        worst = {a: max(worst.get(a, 0.0), b) for a, b in errs.items()}
+    print("drum free-running", worst)
+    assert max(worst.values()) < TOL64_FREE, worst
     assert wall_contacts > 3
 
 
 def test_fp64_trajectory_matches_oracle_in_a_cone_hopper_with_sink():
     s = W.cone_bed(n=300, seed=13)
-    w = dem.World.from_scene(s, precision="fp64")
-    ow = oracle.OracleWorld(s)
-    w.step(900)
-    ow.step(900)
-    errs, ok = state_close(w, ow, 1e-8)
-    assert ok, errs
+    w, ow, worst = _free_running(s, (300, 300, 300))
+    print("cone free-running", worst)
+    assert max(worst.values()) < TOL64_FREE, worst
     assert ow.active.sum() < len(ow.active)          # some spheres went through the sink
 
 
@@ -363,17 +475,25 @@ def test_set_owner_state_forces_a_rebuild_and_keeps_history():
 
 
 def test_diagnostics_match_oracle():
-    s = dense_scene(n=700, seed=22)
-    w = dem.World.from_scene(s, precision="fp64")
-    ow = oracle.OracleWorld(s)
-    w.step(20)
-    ow.step(20)
-    dg = w.diagnostics()
-    do = ow.diagnostics()
-    for k in ("ke", "pe", "elastic"):
-        assert dg[k] == pytest.approx(do[k], rel=1e-8)
-    assert np.allclose(dg["momentum"], do["momentum"], rtol=1e-8, atol=1e-14)
-    assert np.allclose(dg["angmom"], do["angmom"], rtol=1e-8, atol=1e-16)
+    """The GPU's fixed-order FP64 sums against the oracle's compensated sums of the same
+    state, at 1e-9 of the summed magnitudes (energies: the sums themselves, every term
+    of one sign; momenta: the sum of the terms' magnitudes)."""
+    for s, steps in ((dense_scene(n=700, seed=22), 20), (W.packed_clumps(n=150, seed=10), 150)):
+        w = dem.World.from_scene(s, precision="fp64")
+        ow = oracle.OracleWorld(s)
+        w.step(steps)
+        sync_oracle_to_gpu(w, ow, None)
+        dg = w.diagnostics()
+        do = ow.diagnostics()
+        for k in ("ke", "pe", "elastic"):
+            assert dg[k] == pytest.approx(do[k], rel=TOL64, abs=1e-300), k
+        m = ow.mass[:, None]
+        p_scale = np.sum(np.abs(m * ow.v), axis=0)
+        assert np.all(np.abs(dg["momentum"] - do["momentum"]) <= TOL64 * p_scale + 1e-300)
+        L_orb = np.abs(np.cross(ow.x, m * ow.v)).sum(axis=0)
+        L_spin = np.sum(np.abs(ow.moi * ow.wb), axis=0).max()
+        assert np.all(np.abs(dg["angmom"] - do["angmom"]) <= TOL64 * (L_orb + L_spin) + 1e-300)
+        assert do["elastic"] > 0.0
 
 
 # ----------------------------------------------------------------------------- wall screens
@@ -491,3 +611,34 @@ def test_voxel_forces_on_axis_planes_match_fp64_at_every_overlap():
     mag = np.linalg.norm(Fo, axis=1)
     err = np.linalg.norm(F - Fo, axis=1) / mag
     assert err.max() <= 1e-4, err.max()
+
+
+def test_unset_pairs_of_differing_materials_are_rejected():
+    """Sec. 3.1 sets restitution and friction per material pair and gives no rule for
+    combining two materials: a pair of materials that differ needs its value set."""
+    def world(cor_b, mu_b, set_pair):
+        w = dem.World((0, 0, 0), (0.02, 0.02, 0.02), precision="fp64")
+        a = w.add_material(1e7, 0.3, 0.5, 0.4)
+        b = w.add_material(2e7, 0.25, cor_b, mu_b)
+        if set_pair:
+            w.set_material_pair(dem.PROP_COR, a, b, 0.45)
+            w.set_material_pair(dem.PROP_MU, a, b, 0.35)
+        w.add_box_walls(a)
+        t = w.add_clump_template([[0, 0, 0]], [1e-3], [b], 1e-5, [4e-12] * 3)
+        w.add_clumps(t, [[0.005, 0.005, 0.005], [0.0075, 0.005, 0.005]])
+        return w
+    for cor_b, mu_b in ((0.7, 0.4), (0.5, 0.6)):
+        w = world(cor_b, mu_b, False)
+        with pytest.raises(dem.DemError) as e:
+            w.initialize()
+        assert e.value.status == dem.ERR_STATE and "dem_set_material_pair" in str(e.value)
+        w.close()
+        w = world(cor_b, mu_b, True)
+        w.initialize()
+        w.step(2)
+        w.close()
+    # equal CoR and mu need no pair value (E and nu combine by the Hertz-Mindlin rule)
+    w = world(0.5, 0.4, False)
+    w.initialize()
+    w.step(2)
+    w.close()

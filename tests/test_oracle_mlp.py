@@ -48,3 +48,33 @@ def test_bf16_rounding_is_round_to_nearest_even():
     assert r[2] == 1.0 + 2 ** -6               # tie to even (upwards)
     assert abs(r[3] - (-3.0e-5)) <= 2 ** -8 * 3.0e-5
     assert r[4] == 65536.0
+
+
+def test_gradient_tolerance_catches_planted_mistakes():
+    """The per-element tolerance the GPU gradient is held to is tight enough to see a
+    wrong row, a dropped batch row or a sign error of any block in the oracle's own
+    BF16-operand gradient."""
+    rng = np.random.default_rng(4)
+    p = random_params(rng).astype(np.float32).astype(np.float64)
+    X = rng.normal(size=(257, 16)).astype(np.float32).astype(np.float64)
+    Y = rng.normal(size=(257, 2)).astype(np.float32).astype(np.float64)
+    _, g = mlp.loss_grad(p, X, Y, bf=True)
+    tol = mlp.gradient_tolerance(g)
+    assert np.all(np.abs(g - g) <= tol)
+    blocks = dict(mlp.blocks())
+    # two rows of dW1 exchanged
+    bad = g.copy()
+    w1 = bad[blocks["W1"]].reshape(64, 16)
+    w1[[3, 4]] = w1[[4, 3]]
+    bad[blocks["W1"]] = w1.ravel()
+    assert np.any(np.abs(bad - g) > tol)
+    # one batch row left out of the gradient
+    _, g_drop = mlp.loss_grad(p, X[1:], Y[1:], bf=True)
+    g_drop = g_drop * (X.shape[0] - 1) / X.shape[0]       # same normalisation (mean over 257 rows)
+    for name, sl in mlp.blocks():
+        assert np.any(np.abs(g_drop[sl] - g[sl]) > tol[sl]), name
+    # a sign error in each bias
+    for name in ("b1", "b2", "b3"):
+        bad = g.copy()
+        bad[blocks[name]] *= -1.0
+        assert np.any(np.abs(bad - g) > tol), name

@@ -153,3 +153,48 @@ def test_grid_enumeration_is_bit_identical_with_a_sink():
     assert a.step(1000) == 0 and b.step(1000) == 0
     assert (a.active == 0).sum() > 0          # the sink has removed owners
     assert np.array_equal(a.x, b.x) and np.array_equal(a.v, b.v) and np.array_equal(a.active, b.active)
+
+
+# ------------------------------------------------------------------ oracle threads
+
+def _same_run_threads(scene, steps, cell_list):
+    a = oracle.OracleWorld(scene, cell_list=cell_list, threads=4)
+    b = oracle.OracleWorld(scene, cell_list=cell_list)
+    assert a.step(steps) == 0 and b.step(steps) == 0
+    for f in ("x", "v", "wb", "q", "active"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    ha, hb = a.history(), b.history()
+    for u, w in zip(ha, hb):
+        assert np.array_equal(u, w)
+    Fa, Ta, ca = a.eval()
+    Fb, Tb, cb = b.eval()
+    assert np.array_equal(Fa, Fb) and np.array_equal(Ta, Tb) and np.array_equal(ca, cb)
+    return len(ha[0])
+
+
+@pytest.mark.parametrize("cell_list", [False, True])
+def test_threaded_oracle_is_bit_identical_for_clumps_and_walls(cell_list):
+    """Contacts found on four threads, reduced serially: the one-thread results."""
+    assert _same_run_threads(W.packed_clumps(n=300, seed=22), 120, cell_list) > 20
+
+
+def test_threaded_oracle_is_bit_identical_with_a_sink():
+    sc = W.cone_bed(n=600, seed=23)
+    a = oracle.OracleWorld(sc, cell_list=True, threads=4)
+    b = oracle.OracleWorld(sc, cell_list=True)
+    assert a.step(1000) == 0 and b.step(1000) == 0
+    assert (a.active == 0).sum() > 0
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.v, b.v) and np.array_equal(a.active, b.active)
+
+
+def test_history_set_sorts_unsorted_entries():
+    sc = W.packed_clumps(n=100, seed=24)
+    ow = oracle.OracleWorld(sc)
+    assert ow.step(60) == 0
+    i, j, ut = ow.history()
+    assert len(i) > 5
+    perm = np.random.default_rng(1).permutation(len(i))
+    ow2 = oracle.OracleWorld(sc)
+    ow2.set_history(i[perm], j[perm], ut[perm])
+    i2, j2, ut2 = ow2.history()
+    assert np.array_equal(i, i2) and np.array_equal(j, j2) and np.array_equal(ut, ut2)
