@@ -17,11 +17,6 @@ from paper_2311_04648_gb300 import dem, workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-9
-# free-running trajectories of dense packings over hundreds of steps: neighbouring
-# trajectories separate (each collision amplifies the last-bit differences of the two
-# evaluation orders), so these compare at the measured separation bound; the 1e-9 bar is
-# held step by step from the GPU's own states (test_fp64_one_step_parity_from_gpu_states)
-TOL64_FREE = 1e-8
 
 
 def dense_scene(n=1200, seed=3, vel=0.2, e=0.5, mu=0.4, h=1e-6):
@@ -216,8 +211,8 @@ ONE_STEP_SCENES = {
 @pytest.mark.parametrize("name", sorted(ONE_STEP_SCENES))
 def test_fp64_one_step_parity_from_gpu_states(name):
     """One-step parity (contact forces, sums, state, history) at 1e-9 from the GPU's own
-    state at several steps of a run: the binding check where the free-running comparison
-    is limited by the separation of nearby trajectories in dense packings."""
+    state at several steps of a run, so that every step is checked against the oracle
+    from identical inputs, whatever the separation of the free-running trajectories."""
     make, chunks = ONE_STEP_SCENES[name]
     s = make()
     w = dem.World.from_scene(s, precision="fp64")
@@ -284,14 +279,14 @@ def _free_running(s, chunks):
 def test_fp64_trajectory_matches_oracle_dense_polydisperse():
     w, ow, worst = _free_running(dense_scene(n=600, seed=8, vel=0.5), (100, 100))
     print("dense free-running", worst)
-    assert max(worst.values()) < TOL64_FREE, worst
-    compare_contacts(w, ow, TOL64_FREE)
+    assert max(worst.values()) < TOL64, worst
+    compare_contacts(w, ow, TOL64)
 
 
 def test_fp64_trajectory_matches_oracle_clumps_with_walls_and_gravity():
     w, ow, worst = _free_running(W.packed_clumps(n=150, seed=10), (150, 150))
     print("clumps free-running", worst)
-    assert max(worst.values()) < TOL64_FREE, worst
+    assert max(worst.values()) < TOL64, worst
 
 
 def test_fp64_trajectory_matches_oracle_in_a_spinning_drum():
@@ -308,7 +303,7 @@ def test_fp64_trajectory_matches_oracle_in_a_spinning_drum():
         errs, _ = state_close(w, ow, TOL64)
         worst = {a: max(worst.get(a, 0.0), b) for a, b in errs.items()}
     print("drum free-running", worst)
-    assert max(worst.values()) < TOL64_FREE, worst
+    assert max(worst.values()) < TOL64, worst
     assert wall_contacts > 3
 
 
@@ -316,7 +311,7 @@ def test_fp64_trajectory_matches_oracle_in_a_cone_hopper_with_sink():
     s = W.cone_bed(n=300, seed=13)
     w, ow, worst = _free_running(s, (300, 300, 300))
     print("cone free-running", worst)
-    assert max(worst.values()) < TOL64_FREE, worst
+    assert max(worst.values()) < TOL64, worst
     assert ow.active.sum() < len(ow.active)          # some spheres went through the sink
 
 
