@@ -138,16 +138,18 @@ const char *dem_last_error(const dem_world *w);
 /* ---------------------------------------------------------------- set-up (before init) */
 
 /* Register a material (Sec. 3.1: LoadMaterial with E, nu, CoR, mu, Crr).  E > 0,
- * 0 <= nu < 0.5, 0 <= CoR <= 1, mu >= 0.  Crr must be 0: rolling resistance is not
- * implemented (DEM_ERR_UNSUPPORTED otherwise).  *mat_id receives the dense id.
- * A pair of materials takes the CoR and mu set for it with dem_set_material_pair; a
+ * 0 <= nu < 0.5, 0 <= CoR <= 1, mu >= 0, Crr >= 0 (the rolling resistance coefficient
+ * of Sec. 4.1: after a contact has outlasted its collision time, a force of Crr |F_n|
+ * along the rolling part of the contact point's relative velocity, applied as an
+ * action-reaction pair that changes only the torques).  *mat_id receives the dense id.
+ * A pair of materials takes the CoR, mu and Crr set for it with dem_set_material_pair; a
  * pair left unset takes its two materials' common value where they agree, and
  * dem_initialize returns DEM_ERR_STATE where they differ (the paper sets pairwise
  * properties explicitly and gives no rule for combining two materials). */
 dem_status dem_add_material(dem_world *w, double E, double nu, double CoR, double mu, double Crr,
                             int32_t *mat_id);
 /* Override a pairwise property for materials (a, b), symmetric (Sec. 3.1:
- * SetMaterialPropertyPair).  prop is dem_prop; CRR accepts only 0. */
+ * SetMaterialPropertyPair).  prop is dem_prop: CoR in [0, 1], mu >= 0, Crr >= 0. */
 dem_status dem_set_material_pair(dem_world *w, int32_t prop, int32_t a, int32_t b, double value);
 
 /* Six planes on the faces of the domain box, normals pointing inwards
@@ -312,6 +314,40 @@ dem_status dem_get_owner_forces(dem_world *w, int64_t first, int64_t n, double *
 /* Set the tangential history of the listed contacts (i, j, ut[3k]); unlisted entries
  * are ignored and all other history is zeroed.  For exact replays in tests. */
 dem_status dem_set_history(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *ut);
+/* The same with each contact's age age[k] (time in contact, seconds; NULL: zero), the
+ * history the rolling-resistance gate of Sec. 4.2.1 reads. */
+dem_status dem_set_history_age(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *ut,
+                               const double *age);
+/* ---------------------------------------------------------------- family tags */
+
+/* Family tags (Sec. 2.2.2): every owner carries a family in [0, 255] (0 by default).
+ * Owners [first, first + n) of this scene (insertion order) take family[n].  Before
+ * dem_initialize for owners added so far; after it, the contact list is rebuilt before
+ * the next step.  The first use of any family call turns on family lookups in the step
+ * kernels (a few bytes per owner and per detection candidate). */
+dem_status dem_set_family(dem_world *w, int64_t first, int64_t n, const uint8_t *family);
+/* Prescribed motion of a family (Sec. 2.2.2, SetFamilyPrescribedLinVel / AngVel): where
+ * v (omega) is non-NULL, every owner of the family moves with that linear (angular,
+ * global-frame) velocity instead of the one its forces give; it still exerts contact
+ * forces on others.  v = omega = {0, 0, 0} holds the family fixed; both NULL frees it.
+ * Valid before and after dem_initialize; applies to every scene of a batch. */
+dem_status dem_set_family_motion(dem_world *w, int32_t family, const double *v, const double *omega);
+/* Resolve (on = 1, the default) or ignore (on = 0) contacts between owners of families
+ * fa and fb (fa == fb: within one family).  Walls meet every family. */
+dem_status dem_set_family_contacts(dem_world *w, int32_t fa, int32_t fb, int32_t on);
+/* Active box (Sec. 6.4): every owner of this scene whose centre lies inside the
+ * axis-aligned box [lo, hi] takes family_inside, every other family_outside (typically
+ * a family held fixed with its contacts to itself off: dormant, it costs next to
+ * nothing).  After dem_initialize; call it again as the region of interest moves. */
+dem_status dem_set_active_box(dem_world *w, const double lo[3], const double hi[3], int32_t family_inside,
+                              int32_t family_outside);
+
+/* Per contact, in the order and count of dem_get_contacts: age[count] (time in contact
+ * after this step's update; kept only in worlds where some material pair has Crr > 0,
+ * else 0) and torque_force[3 count] (the rolling-resistance force on sphere i, global
+ * frame; -it acts on j; it changes only the torques, Sec. 4.1 F_r / tau_r).  Outputs
+ * nullable; DEM_ERR_CAPACITY if cap < count (count is always written). */
+dem_status dem_get_contact_rolling(dem_world *w, int64_t cap, int64_t *count, double *age, double *torque_force);
 dem_status dem_get_stats(dem_world *w, dem_stats *s);
 /* FP64 diagnostics computed on the GPU with a fixed-order reduction. */
 dem_status dem_get_diagnostics(dem_world *w, dem_diagnostics *d);

@@ -64,12 +64,18 @@ class _World(C.Structure):
                 ("owner", C.c_void_p), ("rloc", C.c_void_p), ("rad", C.c_void_p), ("mat", C.c_void_p),
                 ("h", C.c_double), ("g", C.c_double * 3), ("gyroscopic", C.c_int32), ("has_sink", C.c_int32),
                 ("sink_p", C.c_double * 3), ("sink_n", C.c_double * 3), ("v_err", C.c_double),
-                ("hist", C.c_void_p), ("cell_list", C.c_int32), ("n_threads", C.c_int32)]
+                ("hist", C.c_void_p), ("cell_list", C.c_int32), ("n_threads", C.c_int32), ("crr", C.c_void_p),
+                ("family", C.c_void_p), ("contact_mask", C.c_void_p), ("motion", C.c_void_p)]
+
+
+class FamilyMotion(C.Structure):
+    _fields_ = [("fix_v", C.c_int32), ("fix_w", C.c_int32), ("v", C.c_double * 3), ("w", C.c_double * 3)]
 
 
 class Contact(C.Structure):
     _fields_ = [("i", C.c_int64), ("j", C.c_int64), ("force", C.c_double * 3), ("point", C.c_double * 3),
-                ("normal", C.c_double * 3), ("overlap", C.c_double), ("ut", C.c_double * 3)]
+                ("normal", C.c_double * 3), ("overlap", C.c_double), ("ut", C.c_double * 3), ("age", C.c_double),
+                ("torque_force", C.c_double * 3)]
 
 
 def lib():
@@ -83,8 +89,8 @@ def lib():
             L.orc_history_free.argtypes = [P]
             L.orc_history_size.restype = C.c_int64
             L.orc_history_size.argtypes = [P]
-            L.orc_history_set.argtypes = [P, C.c_int64, P, P, P]
-            L.orc_history_get.argtypes = [P, C.c_int64, P, P, P, P]
+            L.orc_history_set.argtypes = [P, C.c_int64, P, P, P, P]
+            L.orc_history_get.argtypes = [P, C.c_int64, P, P, P, P, P]
             L.orc_sphere_positions.argtypes = [P, P]
             L.orc_listed_pairs_f64.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_int64, P, P, P]
             L.orc_listed_pairs_voxel_f32.argtypes = [C.c_int64, P, P, C.c_float, P, P, P, C.c_float,
@@ -168,6 +174,9 @@ class OracleWorld:
         self.nu = np.ascontiguousarray(s.nu, np.float64)
         self.cor = np.ascontiguousarray(s.cor, np.float64).reshape(self.n_mat, self.n_mat)
         self.mu = np.ascontiguousarray(s.mu, np.float64).reshape(self.n_mat, self.n_mat)
+        crr = getattr(s, "crr", None)
+        self.crr = (np.zeros((self.n_mat, self.n_mat)) if crr is None
+                    else np.ascontiguousarray(crr, np.float64).reshape(self.n_mat, self.n_mat))
         walls = list(s.walls)
         self.walls = (Wall * max(1, len(walls)))()
         for k, wd in enumerate(walls):
@@ -209,6 +218,7 @@ class OracleWorld:
         w = self._w
         w.n_owner = M; w.n_sphere = len(self.rad); w.n_mat = self.n_mat; w.n_wall = self.n_wall
         w.E = _ptr(self.E); w.nu = _ptr(self.nu); w.cor = _ptr(self.cor); w.mu = _ptr(self.mu)
+        w.crr = _ptr(self.crr)
         w.walls = C.cast(self.walls, C.c_void_p)
         w.x = _ptr(self.x); w.v = _ptr(self.v); w.wb = _ptr(self.wb); w.q = _ptr(self.q)
         w.mass = _ptr(self.mass); w.moi = _ptr(self.moi); w.active = _ptr(self.active)
@@ -223,6 +233,33 @@ class OracleWorld:
             for a in range(3):
                 w.sink_p[a] = float(sink[0][a]); w.sink_n[a] = float(sink[1][a])
         w.v_err = float(getattr(s, "v_err", 0.0) or 0.0)
+        # family tags: per-owner family, contact mask between families, prescribed motion
+        fam = getattr(s, "family", None)
+        self.family = None if fam is None else np.ascontiguousarray(fam, np.uint8).reshape(M)
+        masked = getattr(s, "family_masked", None)
+        self.contact_mask = None
+        if masked:
+            self.contact_mask = np.ones((256, 256), np.uint8)
+            for a, b in masked:
+                self.contact_mask[a, b] = 0
+                self.contact_mask[b, a] = 0
+        motion = getattr(s, "family_motion", None)
+        self.motion = None
+        if motion:
+            self.motion = (FamilyMotion * 256)()
+            for f, (vel, om) in motion.items():
+                fm = self.motion[int(f)]
+                if vel is not None:
+                    fm.fix_v = 1
+                    for a in range(3):
+                        fm.v[a] = float(vel[a])
+                if om is not None:
+                    fm.fix_w = 1
+                    for a in range(3):
+                        fm.w[a] = float(om[a])
+        w.family = _ptr(self.family)
+        w.contact_mask = _ptr(self.contact_mask)
+        w.motion = C.cast(self.motion, C.c_void_p) if self.motion is not None else None
         w.hist = lib().orc_history_new()
         w.cell_list = 1 if cell_list else 0
         w.n_threads = int(threads)
@@ -290,22 +327,27 @@ class OracleWorld:
             arr = np.ctypeslib.as_array(buf)[:n].copy() if n else np.zeros(0, dtype=np.ctypeslib.as_array(buf).dtype)
             return F, T, arr
 
-    def history(self):
+    def history(self, with_age=False):
+        """Stored tangential history (i, j, ut[n, 3]) and, with_age, the contacts' ages."""
         h = self._w.hist
         n = lib().orc_history_size(h)
         i = np.empty(max(n, 1), np.int64)
         j = np.empty(max(n, 1), np.int64)
         ut = np.empty((max(n, 1), 3))
+        age = np.empty(max(n, 1))
         cnt = C.c_int64()
-        rc = lib().orc_history_get(h, max(n, 1), C.byref(cnt), _ptr(i), _ptr(j), _ptr(ut))
+        rc = lib().orc_history_get(h, max(n, 1), C.byref(cnt), _ptr(i), _ptr(j), _ptr(ut), _ptr(age))
         assert rc == 0
+        if with_age:
+            return i[:n].copy(), j[:n].copy(), ut[:n].copy(), age[:n].copy()
         return i[:n].copy(), j[:n].copy(), ut[:n].copy()
 
-    def set_history(self, i, j, ut):
+    def set_history(self, i, j, ut, age=None):
         i = np.ascontiguousarray(i, np.int64)
         j = np.ascontiguousarray(j, np.int64)
         ut = np.ascontiguousarray(ut, np.float64).reshape(-1, 3)
-        rc = lib().orc_history_set(self._w.hist, len(i), _ptr(i), _ptr(j), _ptr(ut))
+        age = None if age is None else np.ascontiguousarray(age, np.float64).reshape(-1)
+        rc = lib().orc_history_set(self._w.hist, len(i), _ptr(i), _ptr(j), _ptr(ut), _ptr(age))
         assert rc == 0
 
     def diagnostics(self):

@@ -99,6 +99,7 @@ typedef struct {
     int64_t n, cap;
     int64_t *i, *j;      /* j >= 0 sphere, j < 0 wall -1-j */
     double *ut;          /* 3 per entry */
+    double *age;         /* time in contact, 1 per entry */
 } orc_hist;
 
 /* Sort key of the partner: spheres first by id, then walls by wall id. */
@@ -120,7 +121,7 @@ void orc_history_free(void *hp)
 {
     orc_hist *h = (orc_hist *)hp;
     if (!h) return;
-    free(h->i); free(h->j); free(h->ut); free(h);
+    free(h->i); free(h->j); free(h->ut); free(h->age); free(h);
 }
 
 int64_t orc_history_size(const void *hp) { return hp ? ((const orc_hist *)hp)->n : 0; }
@@ -139,6 +140,9 @@ static int hist_reserve(orc_hist *h, int64_t n)
     double *nu = (double *)realloc(h->ut, (size_t)c * 3 * sizeof(double));
     if (!nu) return ORC_ERR_NOMEM;
     h->ut = nu;
+    double *na = (double *)realloc(h->age, (size_t)c * sizeof(double));
+    if (!na) return ORC_ERR_NOMEM;
+    h->age = na;
     h->cap = c;
     return 0;
 }
@@ -166,7 +170,7 @@ static int hist_ref_cmp(const void *a, const void *b)
     return x->k < y->k ? -1 : (x->k > y->k ? 1 : 0);
 }
 
-int orc_history_set(void *hp, int64_t n, const int64_t *i, const int64_t *j, const double *ut)
+int orc_history_set(void *hp, int64_t n, const int64_t *i, const int64_t *j, const double *ut, const double *age)
 {
     orc_hist *h = (orc_hist *)hp;
     if (!h || n < 0) return ORC_ERR_ARG;
@@ -179,13 +183,14 @@ int orc_history_set(void *hp, int64_t n, const int64_t *i, const int64_t *j, con
     for (int64_t k = 0; k < n; ++k) {
         h->i[k] = r[k].i; h->j[k] = r[k].j;
         memcpy(&h->ut[3 * k], &ut[3 * r[k].k], 3 * sizeof(double));
+        h->age[k] = age ? age[r[k].k] : 0.0;
     }
     h->n = n;
     free(r);
     return 0;
 }
 
-int orc_history_get(const void *hp, int64_t cap, int64_t *n, int64_t *i, int64_t *j, double *ut)
+int orc_history_get(const void *hp, int64_t cap, int64_t *n, int64_t *i, int64_t *j, double *ut, double *age)
 {
     const orc_hist *h = (const orc_hist *)hp;
     if (!h) return ORC_ERR_ARG;
@@ -194,6 +199,7 @@ int orc_history_get(const void *hp, int64_t cap, int64_t *n, int64_t *i, int64_t
     for (int64_t k = 0; k < h->n; ++k) {
         i[k] = h->i[k]; j[k] = h->j[k];
         ut[3 * k] = h->ut[3 * k]; ut[3 * k + 1] = h->ut[3 * k + 1]; ut[3 * k + 2] = h->ut[3 * k + 2];
+        if (age) age[k] = h->age[k];
     }
     return 0;
 }
@@ -264,6 +270,15 @@ static int wall_gap(const orc_wall *wl, const double c[3], double *gap, double n
 }
 
 static int owner_is_active(const orc_world *w, int64_t o) { return w->active ? w->active[o] != 0 : 1; }
+
+static int owner_family(const orc_world *w, int64_t o) { return w->family ? (int)w->family[o] : 0; }
+
+/* Contacts between owners a and b are resolved (the families' contact mask). */
+static int families_meet(const orc_world *w, int64_t a, int64_t b)
+{
+    if (!w->contact_mask) return 1;
+    return w->contact_mask[owner_family(w, a) * 256 + owner_family(w, b)] != 0;
+}
 
 /* Threads of the parallel loops (1 = serial). */
 static int n_threads(const orc_world *w) { return w->n_threads > 1 ? w->n_threads : 1; }
@@ -362,20 +377,45 @@ typedef struct {
     double c[3];       /* contact point */
     double uA[3];      /* velocity of the contact point as a point of A */
     double uB[3];      /* ... as a point of B */
+    double rotA[3];    /* the rotational part of uA: (angular velocity of A) x (c - x_A) */
+    double rotB[3];    /* ... of uB (for a wall its whole surface velocity) */
     double Rbar, mbar;
-    double Estar, Gstar, beta, mu;
+    double Estar, Gstar, beta, mu, crr;
 } contact_in;
 
+/* Whether a contact that has lasted `age` is still inside its first collision: the
+ * default model of Sec. 4.2.1 applies rolling resistance only after a collision time of
+ * a damped linear oscillator, whose stiffness and damping it forms from E*, the damping
+ * ratio and the effective mass and radius in a simplified way.  This follows that
+ * reading term by term: with s = sqrt(Rbar), k = (4/3) E* sqrt(s) and
+ * g = -2 sqrt((5/3) mbar E*) beta s^(1/4), the damping ratio is z = g / (2 sqrt(k mbar))
+ * and, where z < 1 and 1 - z^2 > 0, the collision time is pi sqrt(mbar / (k (1 - z^2))). */
+static int within_collision_time(const contact_in *ci, double age)
+{
+    double s = sqrt(ci->Rbar);
+    double k = (4.0 / 3.0) * ci->Estar * sqrt(s);
+    double g = -2.0 * sqrt((5.0 / 3.0) * ci->mbar * ci->Estar) * ci->beta * sqrt(sqrt(s));
+    double z = g / (2.0 * sqrt(k * ci->mbar));
+    if (!(z < 1.0)) return 0;
+    double d = 1.0 - z * z;
+    if (!(d > 0.0)) return 0;
+    double tc = ORC_PI * sqrt(ci->mbar / (k * d));
+    return age <= tc;
+}
+
 /* The default history-based Hertz-Mindlin model (Sec. 4.1 Eqs. 1-4 as the listing of
- * Sec. 4.2.1 computes them).  ut is updated in place; F is the force on A. */
-static void hertz_mindlin(const contact_in *ci, double h, double ut[3], double F[3])
+ * Sec. 4.2.1 computes it), with rolling resistance.  ut and age (time in contact) are
+ * updated in place; F is the force on A; Fr the rolling-resistance force on A, which
+ * acts only through the contact torque (B receives -Fr). */
+static void hertz_mindlin(const contact_in *ci, double h, double ut[3], double *age, double F[3], double Fr[3])
 {
     const double *n = ci->n;
     double u[3] = {ci->uA[0] - ci->uB[0], ci->uA[1] - ci->uB[1], ci->uA[2] - ci->uB[2]};
     double proj = dot3(u, n);
     double vt[3] = {u[0] - proj * n[0], u[1] - proj * n[1], u[2] - proj * n[2]};
 
-    /* history update precedes the force: accumulate h*vt, then remove the normal part */
+    /* history update precedes the force: accumulate h*vt, then remove the normal part;
+     * the contact's age grows by h */
     ut[0] = ut[0] + h * vt[0];
     ut[1] = ut[1] + h * vt[1];
     ut[2] = ut[2] + h * vt[2];
@@ -383,6 +423,7 @@ static void hertz_mindlin(const contact_in *ci, double h, double ut[3], double F
     ut[0] = ut[0] - up * n[0];
     ut[1] = ut[1] - up * n[1];
     ut[2] = ut[2] - up * n[2];
+    *age = *age + h;
 
     double c56 = sqrt(5.0 / 6.0);
     double sqrtRd = sqrt(ci->delta * ci->Rbar);
@@ -391,6 +432,19 @@ static void hertz_mindlin(const contact_in *ci, double h, double ut[3], double F
     double gn = 2.0 * c56 * ci->beta * sqrt(Sn * ci->mbar);
     double fn = kn * ci->delta + gn * proj;
     F[0] = fn * n[0]; F[1] = fn * n[1]; F[2] = fn * n[2];
+
+    /* rolling resistance: C_r times the normal force (damping included), along the
+     * rolling part of B's contact-point velocity relative to A's, once the contact has
+     * outlasted its collision time */
+    Fr[0] = 0.0; Fr[1] = 0.0; Fr[2] = 0.0;
+    if (ci->crr > 0.0 && !within_collision_time(ci, *age)) {
+        double vr[3] = {ci->rotB[0] - ci->rotA[0], ci->rotB[1] - ci->rotA[1], ci->rotB[2] - ci->rotA[2]};
+        double vm = norm3(vr);
+        if (vm > 1e-12) {
+            double sc = ci->crr * norm3(F) / vm;
+            Fr[0] = sc * vr[0]; Fr[1] = sc * vr[1]; Fr[2] = sc * vr[2];
+        }
+    }
 
     if (ci->mu > 0.0) {
         double kt = 8.0 * ci->Gstar * sqrtRd;
@@ -413,17 +467,18 @@ static void hertz_mindlin(const contact_in *ci, double h, double ut[3], double F
     }
 }
 
-/* Velocity of a point `c` carried by owner o: v + (R(q) wb) x (c - x). */
-static void owner_point_velocity(const orc_world *w, int64_t o, const double c[3], double out[3])
+/* Velocity of a point `c` carried by owner o: v + (R(q) wb) x (c - x); rot receives
+ * the rotational part (R(q) wb) x (c - x). */
+static void owner_point_velocity(const orc_world *w, int64_t o, const double c[3], double out[3], double rot[3])
 {
-    double R[9], wg[3], r[3], vr[3];
+    double R[9], wg[3], r[3];
     quat_matrix(&w->q[4 * o], R);
     mat_vec(R, &w->wb[3 * o], wg);
     r[0] = c[0] - w->x[3 * o + 0]; r[1] = c[1] - w->x[3 * o + 1]; r[2] = c[2] - w->x[3 * o + 2];
-    cross3(wg, r, vr);
-    out[0] = w->v[3 * o + 0] + vr[0];
-    out[1] = w->v[3 * o + 1] + vr[1];
-    out[2] = w->v[3 * o + 2] + vr[2];
+    cross3(wg, r, rot);
+    out[0] = w->v[3 * o + 0] + rot[0];
+    out[1] = w->v[3 * o + 1] + rot[1];
+    out[2] = w->v[3 * o + 2] + rot[2];
 }
 
 /* Fill the pair-dependent material part of a contact. */
@@ -432,6 +487,7 @@ static void contact_material(const orc_world *w, int32_t ma, int32_t mb, contact
     orc_effective_moduli(w->E[ma], w->nu[ma], w->E[mb], w->nu[mb], &ci->Estar, &ci->Gstar);
     ci->beta = damping_beta(w->cor[ma * w->n_mat + mb]);
     ci->mu = w->mu[ma * w->n_mat + mb];
+    ci->crr = w->crr ? w->crr[ma * w->n_mat + mb] : 0.0;
 }
 
 /* Geometry of the sphere pair (A = i, B = j).  Returns 1 if delta > 0. */
@@ -451,8 +507,8 @@ static int sphere_pair_contact(const orc_world *w, const double *p, int64_t i, i
     ci->c[1] = p[3 * i + 1] - a * ci->n[1];
     ci->c[2] = p[3 * i + 2] - a * ci->n[2];
     int64_t oa = w->owner[i], ob = w->owner[j];
-    owner_point_velocity(w, oa, ci->c, ci->uA);
-    owner_point_velocity(w, ob, ci->c, ci->uB);
+    owner_point_velocity(w, oa, ci->c, ci->uA, ci->rotA);
+    owner_point_velocity(w, ob, ci->c, ci->uB, ci->rotB);
     ci->Rbar = (RA * RB) / (RA + RB);
     ci->mbar = (w->mass[oa] * w->mass[ob]) / (w->mass[oa] + w->mass[ob]);
     contact_material(w, w->mat[i], w->mat[j], ci);
@@ -475,9 +531,10 @@ static int sphere_wall_contact(const orc_world *w, const double *p, int64_t i, i
     ci->c[1] = p[3 * i + 1] - a * nrm[1];
     ci->c[2] = p[3 * i + 2] - a * nrm[2];
     int64_t oa = w->owner[i];
-    owner_point_velocity(w, oa, ci->c, ci->uA);
+    owner_point_velocity(w, oa, ci->c, ci->uA, ci->rotA);
     double r[3] = {ci->c[0] - wl->p[0], ci->c[1] - wl->p[1], ci->c[2] - wl->p[2]};
     cross3(wl->omega, r, ci->uB);
+    memcpy(ci->rotB, ci->uB, sizeof(ci->uB));   /* a wall moves by rotation only */
     ci->Rbar = RA;
     ci->mbar = w->mass[oa];
     contact_material(w, w->mat[i], wl->mat, ci);
@@ -515,7 +572,7 @@ static int contact_of(const orc_world *w, const double *p, const orc_hist *h, in
     if (jj < N) {
         j = jj;
         int64_t ob = w->owner[j];
-        if (ob == oa || !owner_is_active(w, ob)) return 0;
+        if (ob == oa || !owner_is_active(w, ob) || !families_meet(w, oa, ob)) return 0;
         if (!sphere_pair_contact(w, p, i, j, &ci)) return 0;
     } else {
         int32_t k = (int32_t)(jj - N);
@@ -525,8 +582,11 @@ static int contact_of(const orc_world *w, const double *p, const orc_hist *h, in
     memset(rec, 0, sizeof(*rec));
     rec->i = i; rec->j = j;
     int64_t hk = h ? hist_find(h, i, j) : -1;
-    if (hk >= 0) { rec->ut[0] = h->ut[3 * hk]; rec->ut[1] = h->ut[3 * hk + 1]; rec->ut[2] = h->ut[3 * hk + 2]; }
-    hertz_mindlin(&ci, w->h, rec->ut, rec->force);
+    if (hk >= 0) {
+        rec->ut[0] = h->ut[3 * hk]; rec->ut[1] = h->ut[3 * hk + 1]; rec->ut[2] = h->ut[3 * hk + 2];
+        rec->age = h->age[hk];
+    }
+    hertz_mindlin(&ci, w->h, rec->ut, &rec->age, rec->force, rec->torque_force);
     memcpy(rec->point, ci.c, sizeof(ci.c));
     memcpy(rec->normal, ci.n, sizeof(ci.n));
     rec->overlap = ci.delta;
@@ -539,16 +599,27 @@ static void add_to_owners(const orc_world *w, const orc_contact *rec, double *F,
 {
     int64_t oa = w->owner[rec->i];
     double rA[3] = {rec->point[0] - w->x[3 * oa], rec->point[1] - w->x[3 * oa + 1], rec->point[2] - w->x[3 * oa + 2]};
-    double tA[3];
+    double tA[3], rrA[3];
     cross3(rA, rec->force, tA);
-    for (int k = 0; k < 3; ++k) { F[3 * oa + k] += rec->force[k]; T[3 * oa + k] += tA[k]; }
+    cross3(rA, rec->torque_force, rrA);
+    for (int k = 0; k < 3; ++k) {
+        F[3 * oa + k] += rec->force[k];
+        T[3 * oa + k] += tA[k];
+        T[3 * oa + k] += rrA[k];
+    }
     if (rec->j >= 0) {
         int64_t ob = w->owner[rec->j];
         double rB[3] = {rec->point[0] - w->x[3 * ob], rec->point[1] - w->x[3 * ob + 1], rec->point[2] - w->x[3 * ob + 2]};
         double mf[3] = {-rec->force[0], -rec->force[1], -rec->force[2]};
-        double tB[3];
+        double mr[3] = {-rec->torque_force[0], -rec->torque_force[1], -rec->torque_force[2]};
+        double tB[3], rrB[3];
         cross3(rB, mf, tB);
-        for (int k = 0; k < 3; ++k) { F[3 * ob + k] += mf[k]; T[3 * ob + k] += tB[k]; }
+        cross3(rB, mr, rrB);
+        for (int k = 0; k < 3; ++k) {
+            F[3 * ob + k] += mf[k];
+            T[3 * ob + k] += tB[k];
+            T[3 * ob + k] += rrB[k];
+        }
     }
 }
 
@@ -790,9 +861,29 @@ static void integrate_owner(orc_world *w, int64_t o, const double Fo[3], const d
     double h = w->h, m = w->mass[o];
     double *v = &w->v[3 * o], *x = &w->x[3 * o], *wb = &w->wb[3 * o], *q = &w->q[4 * o];
     const double *I = &w->moi[3 * o];
+    const orc_family_motion *pm = w->motion ? &w->motion[owner_family(w, o)] : NULL;
     for (int k = 0; k < 3; ++k) {
         double a = Fo[k] / m;
         v[k] = v[k] + h * a;
+    }
+    if (pm && pm->fix_v) { v[0] = pm->v[0]; v[1] = pm->v[1]; v[2] = pm->v[2]; }
+    if (pm && pm->fix_w) {
+        /* prescribed angular velocity (global frame): the orientation turns by it */
+        for (int k = 0; k < 3; ++k) x[k] = x[k] + h * v[k];
+        double wn = norm3(pm->w);
+        if (wn >= 1e-30) {
+            double half = 0.5 * h * wn;
+            double s = sin(half) / wn;
+            double dq[4] = {cos(half), s * pm->w[0], s * pm->w[1], s * pm->w[2]};
+            double nq[4];
+            quat_mul(dq, q, nq);
+            double qn = sqrt(((nq[0] * nq[0] + nq[1] * nq[1]) + nq[2] * nq[2]) + nq[3] * nq[3]);
+            q[0] = nq[0] / qn; q[1] = nq[1] / qn; q[2] = nq[2] / qn; q[3] = nq[3] / qn;
+        }
+        double R[9];
+        quat_matrix(q, R);
+        mat_tvec(R, pm->w, wb);
+        return;
     }
     double R[9], Tb[3];
     quat_matrix(q, R);
@@ -825,6 +916,7 @@ static int replace_history(orc_world *w, const contact_buf *b)
     for (int64_t k = 0; k < b->n; ++k) {
         h->i[k] = b->c[k].i; h->j[k] = b->c[k].j;
         h->ut[3 * k] = b->c[k].ut[0]; h->ut[3 * k + 1] = b->c[k].ut[1]; h->ut[3 * k + 2] = b->c[k].ut[2];
+        h->age[k] = b->c[k].age;
     }
     h->n = b->n;
     return 0;

@@ -13,7 +13,13 @@
  *     capping with the damping term included and the history back-solved);
  *   - tangential history that is created at zero when a contact appears and dropped when
  *     it disappears (Sec. 4.2, contact wildcards);
- *   - per-owner force/torque sums (Eqs. 5a-5b, rolling resistance excluded: C_r = 0);
+ *   - rolling resistance (the F_r, tau_r equations of Sec. 4.1 as the default model of
+ *     Sec. 4.2.1): after a contact has lasted longer than a collision time, a force of
+ *     magnitude C_r |F_n| along the rolling part of the relative velocity of the contact
+ *     point, applied as an action-reaction pair that changes only the torques;
+ *   - per-owner force/torque sums (Eqs. 5a-5b);
+ *   - family tags (Sec. 2.2.2): prescribed linear / angular velocities per family and
+ *     contact masks between families;
  *   - a semi-implicit Euler step of velocity, body-frame angular velocity (with the
  *     gyroscopic term, switchable), position and quaternion.  The paper does not state
  *     the integrator; this is the reading adopted for the whole project.
@@ -50,6 +56,15 @@ typedef struct {
     double omega[3];
 } orc_wall;
 
+/* Prescribed motion of a family (Sec. 2.2.2, family tags): where fix_v (fix_w) is set,
+ * every owner of the family moves with linear velocity v (angular velocity w, global
+ * frame) instead of the one its forces would give; fix_v = fix_w = 1 with zero
+ * velocities holds the family fixed. */
+typedef struct {
+    int32_t fix_v, fix_w;
+    double v[3], w[3];
+} orc_family_motion;
+
 typedef struct {
     int64_t n_owner, n_sphere;
     int32_t n_mat, n_wall;
@@ -80,6 +95,15 @@ typedef struct {
                                        many OpenMP threads; the reduction onto owners stays
                                        serial in (i, partner) order, so results are
                                        bit-identical to one thread                        */
+    const double *crr;              /* rolling resistance coefficient per ordered material
+                                       pair, row-major; NULL: zero for every pair         */
+    /* family tags (Sec. 2.2.2): family[M] (NULL: every owner in family 0); contact_mask
+     * [256 * 256], 0 where contacts between two families are not resolved (NULL: all
+     * resolved; walls belong to no family and meet every sphere); motion[256] (NULL: no
+     * prescribed motion) */
+    const uint8_t *family;
+    const uint8_t *contact_mask;
+    const orc_family_motion *motion;
 } orc_world;
 
 /* One resolved contact.  j >= 0 is a sphere, j < 0 is wall (-1 - j).  force acts on
@@ -91,15 +115,19 @@ typedef struct {
     double normal[3];
     double overlap;
     double ut[3];                   /* tangential history after this step's update       */
+    double age;                     /* time in contact after this step's update (the
+                                       delta_time wildcard of Sec. 4.2.1)                 */
+    double torque_force[3];         /* rolling resistance: a force on i (-it on j) that
+                                       acts through the contact torque only (Sec. 4.1) */
 } orc_contact;
 
 void *orc_history_new(void);
 void  orc_history_free(void *h);
 int64_t orc_history_size(const void *h);
-/* Replace the history by n entries (i, j, ut[3n]); j < 0 denotes wall -1-j.  Entries
- * need not be sorted. */
-int orc_history_set(void *h, int64_t n, const int64_t *i, const int64_t *j, const double *ut);
-int orc_history_get(const void *h, int64_t cap, int64_t *n, int64_t *i, int64_t *j, double *ut);
+/* Replace the history by n entries (i, j, ut[3n], age[n]); j < 0 denotes wall -1-j;
+ * age NULL: zero.  Entries need not be sorted.  get: age may be NULL. */
+int orc_history_set(void *h, int64_t n, const int64_t *i, const int64_t *j, const double *ut, const double *age);
+int orc_history_get(const void *h, int64_t cap, int64_t *n, int64_t *i, int64_t *j, double *ut, double *age);
 
 /* Sphere centres in the global frame: p_s = x_o + R(q_o) rloc_s. */
 int orc_sphere_positions(const orc_world *w, double *p);

@@ -32,8 +32,8 @@ struct TemplateSetup {
 
 struct SceneSetup {
     dem_world_desc desc{};
-    std::vector<double> E, nu, cor, mu;
-    std::map<std::pair<int, int>, double> cor_pair, mu_pair;
+    std::vector<double> E, nu, cor, mu, crr;
+    std::map<std::pair<int, int>, double> cor_pair, mu_pair, crr_pair;
     std::vector<WallSetup> walls;
     std::vector<TemplateSetup> templates;
     std::vector<int32_t> inst_tid;
@@ -44,6 +44,7 @@ struct SceneSetup {
     double margin = -1.0;          // unset
     bool has_sink = false;
     double sink_p[3] = {0, 0, 0}, sink_n[3] = {0, 0, 1};
+    std::vector<uint8_t> inst_family;   // family tag per owner (shorter: the rest are 0)
 };
 
 struct WorldImpl {
@@ -54,6 +55,10 @@ struct WorldImpl {
     HostModel model;
     std::string err;
     std::vector<uint8_t> schedule_model;
+    // family tags of the world (all its scenes): prescribed motion and contact mask
+    std::vector<FamilyMotion> fam_motion;
+    std::vector<uint32_t> fam_mask;
+    bool families_used = false;
 };
 
 }  // namespace
@@ -111,6 +116,34 @@ dem_status layout_cells(HostModel &m, double factor, std::string &err)
     m.n_cells_total = (uint32_t)cell_base;
     m.cell_factor = factor;
     return DEM_OK;
+}
+
+void family_defaults(std::vector<FamilyMotion> &motion, std::vector<uint32_t> &mask)
+{
+    motion.assign(N_FAMILY, FamilyMotion{});
+    mask.assign(FAMILY_MASK_WORDS, 0xffffffffu);
+}
+
+void family_set_motion(FamilyMotion &m, const double *v, const double *w)
+{
+    m.fix_v = v ? 1 : 0;
+    m.fix_w = w ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        m.v[a] = v ? v[a] : 0.0;
+        m.w[a] = w ? w[a] : 0.0;
+        m.vf[a] = (float)m.v[a];
+        m.wf[a] = (float)m.w[a];
+    }
+}
+
+void family_set_contacts(std::vector<uint32_t> &mask, int fa, int fb, int on)
+{
+    for (int k = 0; k < 2; ++k) {
+        const int a = k ? fb : fa, b = k ? fa : fb;
+        uint32_t &word = mask[(a << 3) | (b >> 5)];
+        const uint32_t bit = 1u << (b & 31);
+        word = on ? (word | bit) : (word & ~bit);
+    }
 }
 
 }  // namespace dem
@@ -190,6 +223,11 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
     m.free = d0.free;
     m.alloc_ctx = d0.alloc_ctx;
     m.schedule_model = W.schedule_model;
+    if (W.families_used) {
+        m.fam_motion = W.fam_motion;
+        m.fam_mask = W.fam_mask;
+        m.families_used = true;
+    }
 
     // largest radius over all instances
     double rmax = 0.0;
@@ -288,18 +326,26 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
         // rule for combining two materials): a pair takes the value set for it, or the
         // common value of its two materials where they agree; two materials that differ
         // and have no value set for the pair are an error.
+        g.has_rolling = 0;
         for (int a = 0; a < nm; ++a)
             for (int b = 0; b < nm; ++b) {
                 auto key = std::make_pair(std::min(a, b), std::max(a, b));
                 if ((!sc.cor_pair.count(key) && sc.cor[a] != sc.cor[b]) ||
-                    (!sc.mu_pair.count(key) && sc.mu[a] != sc.mu[b])) {
+                    (!sc.mu_pair.count(key) && sc.mu[a] != sc.mu[b]) ||
+                    (!sc.crr_pair.count(key) && sc.crr[a] != sc.crr[b])) {
                     err = "materials " + std::to_string(key.first) + " and " + std::to_string(key.second) +
-                          " differ in CoR or mu: set the pair's value with dem_set_material_pair";
+                          " differ in CoR, mu or Crr: set the pair's value with dem_set_material_pair";
                     return DEM_ERR_STATE;
                 }
                 double cor = sc.cor_pair.count(key) ? sc.cor_pair[key] : sc.cor[a];
                 double mu = sc.mu_pair.count(key) ? sc.mu_pair[key] : sc.mu[a];
+                double crr = sc.crr_pair.count(key) ? sc.crr_pair[key] : sc.crr[a];
                 m.pairs.push_back(pair_param(sc.E[a], sc.nu[a], sc.E[b], sc.nu[b], cor, mu));
+                m.pair_crr.push_back(crr);
+                if (crr > 0.0) {
+                    g.has_rolling = 1;
+                    m.rolling = true;
+                }
             }
         mat_base += nm;
         pair_base += nm * nm;
@@ -378,6 +424,7 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
             for (int a = 0; a < 3; ++a) m.moi.push_back(t.moi[a] * s5);
             m.owner_scene.push_back((uint16_t)si);
             m.owner_iso.push_back((t.moi[0] == t.moi[1] && t.moi[1] == t.moi[2]) ? 1 : 0);
+            m.owner_family.push_back(k < sc.inst_family.size() ? sc.inst_family[k] : (uint8_t)0);
             // keep an owner's slots inside one warp (segmented reduction)
             if (clumps && (slot % 32) + nsph > 32) {
                 while (slot % 32 != 0) {
@@ -504,15 +551,15 @@ dem_status dem_add_material(dem_world *w, double E, double nu, double CoR, doubl
 {
     CHECK_SETUP(w);
     if (!(E > 0) || !(nu >= 0 && nu < 0.5) || !(CoR >= 0 && CoR <= 1) || !(mu >= 0) || !std::isfinite(E) ||
-        !std::isfinite(mu))
-        return fail(w, DEM_ERR_ARG, "material needs E > 0, 0 <= nu < 0.5, 0 <= CoR <= 1, mu >= 0");
-    if (Crr != 0.0) return fail(w, DEM_ERR_UNSUPPORTED, "rolling resistance (Crr != 0) is not implemented");
+        !std::isfinite(mu) || !(Crr >= 0) || !std::isfinite(Crr))
+        return fail(w, DEM_ERR_ARG, "material needs E > 0, 0 <= nu < 0.5, 0 <= CoR <= 1, mu >= 0, Crr >= 0");
     SceneSetup &sc = S(w);
     if (sc.E.size() >= 256) return fail(w, DEM_ERR_ARG, "at most 256 materials per scene");
     sc.E.push_back(E);
     sc.nu.push_back(nu);
     sc.cor.push_back(CoR);
     sc.mu.push_back(mu);
+    sc.crr.push_back(Crr);
     if (mat_id) *mat_id = (int32_t)sc.E.size() - 1;
     return DEM_OK;
 }
@@ -530,7 +577,8 @@ dem_status dem_set_material_pair(dem_world *w, int32_t prop, int32_t a, int32_t 
         if (!(value >= 0) || !std::isfinite(value)) return fail(w, DEM_ERR_ARG, "mu must be >= 0");
         sc.mu_pair[key] = value;
     } else if (prop == DEM_PROP_CRR) {
-        if (value != 0.0) return fail(w, DEM_ERR_UNSUPPORTED, "rolling resistance is not implemented");
+        if (!(value >= 0) || !std::isfinite(value)) return fail(w, DEM_ERR_ARG, "Crr must be >= 0");
+        sc.crr_pair[key] = value;
     } else {
         return fail(w, DEM_ERR_ARG, "unknown property");
     }
@@ -973,7 +1021,109 @@ dem_status dem_get_owner_forces(dem_world *w, int64_t first, int64_t n, double *
     return DEM_OK;
 }
 
+// ---------------------------------------------------------------- family tags (Sec. 2.2.2)
+
+static void families_on(WorldImpl &W)
+{
+    if (!W.families_used) {
+        family_defaults(W.fam_motion, W.fam_mask);
+        W.families_used = true;
+    }
+}
+
+dem_status dem_set_family(dem_world *w, int64_t first, int64_t n, const uint8_t *family)
+{
+    CHECK_W(w);
+    if (n < 0 || first < 0 || (n > 0 && !family)) return fail(w, DEM_ERR_ARG, "bad family range");
+    WorldImpl &W = *w->impl;
+    if (W.initialized) {
+        if (first + n > scene_owners(w)) return fail(w, DEM_ERR_ARG, "owner range out of bounds");
+        std::string err;
+        dem_status s = W.engine->set_family(owner_base(w) + first, n, family, err);
+        return s ? fail(w, s, err) : DEM_OK;
+    }
+    SceneSetup &sc = S(w);
+    if (first + n > (int64_t)sc.inst_tid.size()) return fail(w, DEM_ERR_ARG, "owner range out of bounds");
+    if ((int64_t)sc.inst_family.size() < first + n) sc.inst_family.resize((size_t)(first + n), 0);
+    std::copy(family, family + n, sc.inst_family.begin() + first);
+    families_on(W);
+    return DEM_OK;
+}
+
+dem_status dem_set_family_motion(dem_world *w, int32_t family, const double *v, const double *omega)
+{
+    CHECK_W(w);
+    if (family < 0 || family >= N_FAMILY) return fail(w, DEM_ERR_ARG, "family must be in [0, 255]");
+    if ((v && !finite3(v)) || (omega && !finite3(omega))) return fail(w, DEM_ERR_ARG, "non-finite velocity");
+    WorldImpl &W = *w->impl;
+    families_on(W);
+    family_set_motion(W.fam_motion[family], v, omega);
+    if (W.initialized) {
+        std::string err;
+        dem_status s = W.engine->set_family_motion(family, v, omega, err);
+        return s ? fail(w, s, err) : DEM_OK;
+    }
+    return DEM_OK;
+}
+
+dem_status dem_set_family_contacts(dem_world *w, int32_t fa, int32_t fb, int32_t on)
+{
+    CHECK_W(w);
+    if (fa < 0 || fa >= N_FAMILY || fb < 0 || fb >= N_FAMILY) return fail(w, DEM_ERR_ARG, "family must be in [0, 255]");
+    WorldImpl &W = *w->impl;
+    families_on(W);
+    family_set_contacts(W.fam_mask, fa, fb, on);
+    if (W.initialized) {
+        std::string err;
+        dem_status s = W.engine->set_family_contacts(fa, fb, on, err);
+        return s ? fail(w, s, err) : DEM_OK;
+    }
+    return DEM_OK;
+}
+
+dem_status dem_set_active_box(dem_world *w, const double lo[3], const double hi[3], int32_t family_inside,
+                              int32_t family_outside)
+{
+    CHECK_INIT(w);
+    if (!lo || !hi || !finite3(lo) || !finite3(hi)) return fail(w, DEM_ERR_ARG, "bad box");
+    if (family_inside < 0 || family_inside >= N_FAMILY || family_outside < 0 || family_outside >= N_FAMILY)
+        return fail(w, DEM_ERR_ARG, "family must be in [0, 255]");
+    std::string err;
+    dem_status s = w->impl->engine->set_active_box(owner_base(w), scene_owners(w), lo, hi, family_inside,
+                                                   family_outside, err);
+    return s ? fail(w, s, err) : DEM_OK;
+}
+
+dem_status dem_get_contact_rolling(dem_world *w, int64_t cap, int64_t *count, double *age, double *torque_force)
+{
+    CHECK_INIT(w);
+    if (!count) return fail(w, DEM_ERR_ARG, "null count");
+    std::vector<ContactOut> cs;
+    std::string err;
+    dem_status s = w->impl->engine->contacts(cs, err);
+    if (s) return fail(w, s, err);
+    const int64_t b = sphere_base(w), e = b + scene_spheres(w);
+    int64_t c = 0;
+    for (auto &x : cs) {
+        if (x.i < b || x.i >= e) continue;
+        if (c < cap) {
+            if (age) age[c] = x.age;
+            for (int a = 0; a < 3; ++a)
+                if (torque_force) torque_force[3 * c + a] = x.trf[a];
+        }
+        ++c;
+    }
+    *count = c;
+    return c > cap ? fail(w, DEM_ERR_CAPACITY, "contact buffer too small") : DEM_OK;
+}
+
 dem_status dem_set_history(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *ut)
+{
+    return dem_set_history_age(w, k, i, j, ut, nullptr);
+}
+
+dem_status dem_set_history_age(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *ut,
+                               const double *age)
 {
     CHECK_INIT(w);
     if (k < 0 || (k > 0 && (!i || !j || !ut))) return fail(w, DEM_ERR_ARG, "bad history arrays");
@@ -984,7 +1134,7 @@ dem_status dem_set_history(dem_world *w, int64_t k, const int64_t *i, const int6
         gj[q] = j[q] >= 0 ? j[q] + b : j[q];
     }
     std::string err;
-    dem_status s = w->impl->engine->set_history(k, gi.data(), gj.data(), ut, err);
+    dem_status s = w->impl->engine->set_history(k, gi.data(), gj.data(), ut, age, err);
     return s ? fail(w, s, err) : DEM_OK;
 }
 

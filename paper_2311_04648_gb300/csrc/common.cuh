@@ -126,10 +126,27 @@ struct Scene {           // per-scene constants (device copy)
     int nb[3];           // schedule bins per axis (BIN_CELLS smallest cells each)
     int nbc[3];          // smallest cells per axis (the bins' grid; detection cells may be larger)
     int bin_base;        // first global bin of this scene
+    int has_rolling;     // a material pair of this scene has C_r > 0
 };
 
 constexpr int BIN_CELLS = 8;     // cells per schedule-bin edge
 constexpr int NSTAT = 10;        // per-bin motion statistics
+
+// Family tags (Sec. 2.2.2): every owner carries a family (0..255).  A family may have a
+// prescribed linear and/or angular velocity (global frame) that replaces the one its
+// forces would give; pairs of families may have their contacts left unresolved.
+constexpr int N_FAMILY = 256;
+struct FamilyMotion {
+    int fix_v, fix_w;
+    double v[3], w[3];
+    float vf[3], wf[3];  // the same rounded to FP32
+};
+// contact mask: bit b of word (a * 8 + b / 32) set = contacts of families a and b resolved
+constexpr int FAMILY_MASK_WORDS = N_FAMILY * N_FAMILY / 32;
+DEM_HD bool families_meet(const uint32_t *mask, int a, int b)
+{
+    return (mask[(a << 3) | (b >> 5)] >> (b & 31)) & 1u;
+}
 
 struct PairParam {       // pairwise contact constants, precomputed on the host in FP64
     double Estar, Gstar, beta, mu;

@@ -10,7 +10,9 @@
 //   F_t = -k_t ut - g_t v_t; if |F_t| > mu |F| (and |F_t| > 1e-12): F_t scaled to mu |F|
 //   and ut back-solved as (F_t + g_t v_t) / (-k_t); |F_t| <= 1e-12 gives F_t = 0.
 // beta = ln e / sqrt(ln^2 e + pi^2) (e clamped at 1e-12) is precomputed on the host per
-// material pair.  Rolling resistance (C_r) is not part of this model build.
+// material pair.  Rolling resistance (rolling_force) follows the same listing: once a
+// contact has lasted longer than a collision time, a force of C_r |F_n| along the
+// rolling part of the contact point's relative velocity, acting only through torques.
 #pragma once
 #include "common.cuh"
 
@@ -26,7 +28,7 @@ struct ContactIn {
 };
 
 template <typename R>
-__device__ __forceinline__ void hertz_mindlin(const ContactIn<R> &c, R h, V3<R> &ut, V3<R> &F)
+__device__ __forceinline__ void hertz_mindlin(const ContactIn<R> &c, R h, V3<R> &ut, V3<R> &F, R *fn_abs = nullptr)
 {
     const R c56 = R(0.91287092917527690);   // sqrt(5/6)
     V3<R> u = c.uA - c.uB;
@@ -42,6 +44,7 @@ __device__ __forceinline__ void hertz_mindlin(const ContactIn<R> &c, R h, V3<R> 
     R gn = R(2) * c56 * c.beta * sqrt(Sn * c.mbar);
     R fn = kn * c.delta + gn * proj;
     F = fn * c.n;
+    if (fn_abs) *fn_abs = sqrt(radd(radd(rmul(F.x, F.x), rmul(F.y, F.y)), rmul(F.z, F.z)));
     if (c.mu > R(0)) {
         R kt = R(8) * c.Gstar * sqrtRd;
         R gt = R(-2) * c56 * c.beta * sqrt(c.mbar * kt);
@@ -58,6 +61,42 @@ __device__ __forceinline__ void hertz_mindlin(const ContactIn<R> &c, R h, V3<R> 
         }
         F = F + Ft;
     }
+}
+
+// Whether a contact that has lasted `age` is still inside its first collision.  The
+// default model of Sec. 4.2.1 forms a damped linear oscillator from E*, the damping
+// ratio beta, mbar and Rbar in a simplified way and applies rolling resistance only
+// after its collision time: with s = sqrt(Rbar), k = (4/3) E* sqrt(s) and
+// g = -2 sqrt((5/3) mbar E*) beta s^(1/4), the damping ratio is z = g / (2 sqrt(k mbar))
+// and, where z < 1 and 1 - z^2 > 0, the collision time is pi sqrt(mbar / (k (1 - z^2))).
+// Every operation is rounded on its own in this order (the FP64 form decides exactly as
+// an FP64 evaluation without fused multiply-adds), and the inputs are symmetric in the
+// two bodies, so both sides of a pair decide alike.
+template <typename R>
+__device__ __forceinline__ bool within_collision_time(const ContactIn<R> &c, R age)
+{
+    const R s = sqrt(c.Rbar);
+    const R k = rmul(rmul(R(4.0 / 3.0), c.Estar), sqrt(s));
+    const R g = rmul(rmul(R(-2.0) * sqrt(rmul(rmul(R(5.0 / 3.0), c.mbar), c.Estar)), c.beta), sqrt(sqrt(s)));
+    const R z = g / rmul(R(2), sqrt(rmul(k, c.mbar)));
+    if (!(z < R(1))) return false;
+    const R dz = rsub(R(1), rmul(z, z));
+    if (!(dz > R(0))) return false;
+    const R tc = rmul(R(3.14159265358979323846), sqrt(c.mbar / rmul(k, dz)));
+    return age <= tc;
+}
+
+// Rolling-resistance force on A (Sec. 4.1, F_r and tau_r; Sec. 4.2.1): C_r |F_n| along
+// vr = (rolling part of B's contact-point velocity) - (A's), i.e. w_B x r_B - w_A x r_A,
+// where |vr| > 1e-12; zero otherwise.  It enters only A's torque (r_A x F_r); B's side,
+// evaluated with the roles exchanged, obtains exactly -F_r.
+template <typename R>
+__device__ __forceinline__ V3<R> rolling_force(R crr, R fn_abs, V3<R> vr)
+{
+    const R vm = sqrt(radd(radd(rmul(vr.x, vr.x), rmul(vr.y, vr.y)), rmul(vr.z, vr.z)));
+    if (!(vm > R(1e-12))) return V3<R>{R(0), R(0), R(0)};
+    const R sc = rmul(crr, fn_abs) / vm;
+    return V3<R>{rmul(sc, vr.x), rmul(sc, vr.y), rmul(sc, vr.z)};
 }
 
 // Error-free transformations in FP32 (Knuth's TwoSum; the product error from an FMA).

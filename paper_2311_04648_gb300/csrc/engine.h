@@ -29,6 +29,14 @@ struct HostModel {
     std::vector<Scene> scenes;
     std::vector<Wall> walls;
     std::vector<PairParam> pairs;
+    std::vector<double> pair_crr;   // rolling resistance per material pair (pairs' indexing)
+    bool rolling = false;           // some pair has C_r > 0
+    // family tags: per-owner family (empty: all 0), prescribed motion per family, contact
+    // mask; families_used once any of them departs from the default
+    std::vector<uint8_t> owner_family;
+    std::vector<FamilyMotion> fam_motion;       // N_FAMILY entries
+    std::vector<uint32_t> fam_mask;             // FAMILY_MASK_WORDS words
+    bool families_used = false;
     std::vector<uint16_t> mat_scene, mat_local;
     // owners, M
     std::vector<double> x, q, v, wb, mass, moi, r_ext;
@@ -58,6 +66,7 @@ struct HostModel {
 struct ContactOut {
     int64_t i, j;                   // user sphere ids; j = -1 - wall for walls
     double force[3], point[3], overlap, hist[3];
+    double age, trf[3];             // time in contact; rolling-resistance force on i (torque only)
 };
 
 // Detection cells of edge f * L_min (whole voxels in the voxel form) for every scene:
@@ -82,7 +91,7 @@ public:
                               std::vector<int64_t> &wi, std::string &err) = 0;
     virtual dem_status owner_forces(std::vector<double> &F, std::vector<double> &T, std::string &err) = 0;
     virtual dem_status set_history(int64_t k, const int64_t *i, const int64_t *j, const double *ut,
-                                   std::string &err) = 0;
+                                   const double *age, std::string &err) = 0;
     virtual dem_status stats(dem_stats *s, std::string &err) = 0;
     virtual dem_status diagnostics(dem_diagnostics *d, std::string &err) = 0;
     virtual dem_status save(std::vector<uint8_t> &blob, std::string &err) = 0;
@@ -98,7 +107,18 @@ public:
     virtual dem_status schedule_train(int epochs, float lr, uint64_t seed, float *loss, std::string &err) = 0;
     virtual dem_status schedule_export(std::vector<uint8_t> &w, std::string &err) = 0;
     virtual dem_status schedule_load(const uint8_t *w, size_t n, std::string &err) = 0;
+    // family tags after initialisation (owner ids global)
+    virtual dem_status set_family(int64_t first, int64_t n, const uint8_t *fam, std::string &err) = 0;
+    virtual dem_status set_family_motion(int f, const double *v, const double *w, std::string &err) = 0;
+    virtual dem_status set_family_contacts(int fa, int fb, int on, std::string &err) = 0;
+    virtual dem_status set_active_box(int64_t first, int64_t n, const double lo[3], const double hi[3], int fin,
+                                      int fout, std::string &err) = 0;
 };
+
+// Host-side family tables in their default state: no prescribed motion, all contacts.
+void family_defaults(std::vector<FamilyMotion> &motion, std::vector<uint32_t> &mask);
+void family_set_motion(FamilyMotion &m, const double *v, const double *w);
+void family_set_contacts(std::vector<uint32_t> &mask, int fa, int fb, int on);
 
 EngineBase *make_engine_f64();
 EngineBase *make_engine_f32();

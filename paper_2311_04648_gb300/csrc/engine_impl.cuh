@@ -134,6 +134,19 @@ public:
         if ((s = alloc(ml, m_.mat_local.size(), err))) return s;
         d_.scenes = scenes; d_.walls = walls; d_.pairs = pairs; d_.pairs_f = pairs_f;
         d_.mat_scene = ms; d_.mat_local = ml;
+        {
+            double *crr;
+            float *crr_f;
+            if ((s = alloc(crr, m_.pairs.size(), err))) return s;
+            if ((s = alloc(crr_f, m_.pairs.size(), err))) return s;
+            std::vector<double> cd(m_.pairs.size(), 0.0);
+            for (size_t k = 0; k < cd.size() && k < m_.pair_crr.size(); ++k) cd[k] = m_.pair_crr[k];
+            std::vector<float> cf(cd.begin(), cd.end());
+            if ((s = up(crr, cd.data(), (int64_t)cd.size(), err))) return s;
+            if ((s = up(crr_f, cf.data(), (int64_t)cf.size(), err))) return s;
+            d_.crr = crr;
+            d_.crr_f = crr_f;
+        }
         if ((s = alloc(st_, 1, err))) return s;
         if ((s = alloc(d_.audit, AUDIT_SLOTS * AUDIT_STRIDE, err))) return s;
         DEM_CU(cudaMallocHost((void **)&sth_, sizeof(DevStatus)));
@@ -228,6 +241,10 @@ public:
         }
         if ((s = up(ms, m_.mat_scene.data(), m_.mat_scene.size(), err))) return s;
         if ((s = up(ml, m_.mat_local.data(), m_.mat_local.size(), err))) return s;
+
+        if (m_.families_used) {
+            if ((s = alloc_families(err))) return s;
+        }
 
         // mass into the position store of buffer 0, then the state through the upload kernel;
         // in the voxel form a single sphere's radius (float-float) rides in both buffers'
@@ -414,14 +431,16 @@ public:
         if (N == 0) return DEM_OK;
         double *buf;
         const int64_t ne = K * Np;
-        if ((s = scratch(buf, 10 * ne, err))) return s;
+        if ((s = scratch(buf, 14 * ne, err))) return s;
         if (m_.clumps)
-            k_contacts<F, true><<<grid(N, 128), 128, 0, sf_>>>(d_, buf, buf + ne, buf + 4 * ne, buf + 7 * ne);
+            k_contacts<F, true><<<grid(N, 128), 128, 0, sf_>>>(d_, buf, buf + ne, buf + 4 * ne, buf + 7 * ne,
+                                                               buf + 10 * ne, buf + 11 * ne);
         else
-            k_contacts<F, false><<<grid(N, 128), 128, 0, sf_>>>(d_, buf, buf + ne, buf + 4 * ne, buf + 7 * ne);
+            k_contacts<F, false><<<grid(N, 128), 128, 0, sf_>>>(d_, buf, buf + ne, buf + 4 * ne, buf + 7 * ne,
+                                                                buf + 10 * ne, buf + 11 * ne);
         DEM_CU(cudaGetLastError());
-        std::vector<double> h(10 * ne);
-        DEM_CU(cudaMemcpyAsync(h.data(), buf, 10 * ne * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        std::vector<double> h(14 * ne);
+        DEM_CU(cudaMemcpyAsync(h.data(), buf, 14 * ne * sizeof(double), cudaMemcpyDeviceToHost, sf_));
         std::vector<uint32_t> partner;
         std::vector<uint8_t> cnt;
         if ((s = fetch_list(sth_->list_cur, partner, cnt, err))) return s;
@@ -440,8 +459,10 @@ public:
                     c.force[a] = h[ne + 3 * e + a];
                     c.point[a] = h[4 * ne + 3 * e + a];
                     c.hist[a] = h[7 * ne + 3 * e + a];
+                    c.trf[a] = h[11 * ne + 3 * e + a];
                 }
                 c.overlap = h[e];
+                c.age = h[10 * ne + e];
                 out.push_back(c);
             }
         }
@@ -492,7 +513,7 @@ public:
         return DEM_OK;
     }
 
-    dem_status set_history(int64_t nk, const int64_t *ii, const int64_t *jj, const double *ut,
+    dem_status set_history(int64_t nk, const int64_t *ii, const int64_t *jj, const double *ut, const double *age,
                            std::string &err) override
     {
         dem_status s;
@@ -507,6 +528,12 @@ public:
         for (int64_t q = 0; q < nk; ++q) {
             if (ii[q] < 0 || ii[q] >= (int64_t)m_.slot_of_sphere.size()) continue;
             int64_t sl = m_.slot_of_sphere[ii[q]];
+            // the age lane: seconds (FP64 form) or whole steps (voxel form)
+            R lane = R(0);
+            if (age) {
+                const double hs = m_.scenes[m_.owner_scene[m_.sph_owner[sl]]].h;
+                lane = F::voxel ? (R)std::nearbyint(age[q] / hs) : (R)age[q];
+            }
             uint32_t key;
             if (jj[q] >= 0) {
                 if (jj[q] >= (int64_t)m_.slot_of_sphere.size()) continue;
@@ -518,6 +545,7 @@ public:
                     int64_t e = (int64_t)k * d_.Np + sj;
                     if (partner[e] == (uint32_t)sl) {
                         hv[e].x = -(R)ut[3 * q]; hv[e].y = -(R)ut[3 * q + 1]; hv[e].z = -(R)ut[3 * q + 2];
+                        hv[e].w = lane;
                     }
                 }
             } else {
@@ -528,12 +556,93 @@ public:
                 int64_t e = (int64_t)k * d_.Np + sl;
                 if (partner[e] == key) {
                     hv[e].x = (R)ut[3 * q]; hv[e].y = (R)ut[3 * q + 1]; hv[e].z = (R)ut[3 * q + 2];
+                    hv[e].w = lane;
                 }
             }
         }
         const int hp = sth_->hist_par;
         DEM_CU(cudaMemcpyAsync(d_.lists.hist[hp], hv.data(), ne * sizeof(H), cudaMemcpyHostToDevice, sf_));
         DEM_CU(cudaStreamSynchronize(sf_));
+        return DEM_OK;
+    }
+
+    // ---- family tags (Sec. 2.2.2)
+
+    // Device family arrays, made when families are first used; from then on the kernels
+    // look the family up for every owner (and the narrow phase for every candidate).
+    dem_status alloc_families(std::string &err)
+    {
+        dem_status s;
+        if (!d_.owner_family) {
+            uint8_t *of, *sf;
+            FamilyMotion *fm;
+            uint32_t *mk;
+            if ((s = alloc(of, Mp_, err))) return s;
+            if ((s = alloc(fm, N_FAMILY, err))) return s;
+            if ((s = alloc(mk, FAMILY_MASK_WORDS, err))) return s;
+            if ((s = alloc(sf, std::max<int64_t>(d_.N, 1), err))) return s;
+            if (m_.owner_family.size() != (size_t)d_.M) m_.owner_family.assign((size_t)d_.M, 0);
+            if (m_.fam_motion.size() != (size_t)N_FAMILY || m_.fam_mask.size() != (size_t)FAMILY_MASK_WORDS)
+                family_defaults(m_.fam_motion, m_.fam_mask);
+            if ((s = up(of, m_.owner_family.data(), d_.M, err))) return s;
+            d_.owner_family = of;
+            d_.fam_motion = fm;
+            d_.fam_mask = mk;
+            db_.sorted_family = sf;
+            m_.families_used = true;
+            drop_graphs();                // captured launches hold the old parameters
+        }
+        if ((s = up(const_cast<FamilyMotion *>(d_.fam_motion), m_.fam_motion.data(), N_FAMILY, err))) return s;
+        if ((s = up(const_cast<uint32_t *>(d_.fam_mask), m_.fam_mask.data(), FAMILY_MASK_WORDS, err))) return s;
+        return DEM_OK;
+    }
+
+    dem_status set_family(int64_t first, int64_t n, const uint8_t *fam, std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        if ((s = alloc_families(err))) return s;
+        std::copy(fam, fam + n, m_.owner_family.begin() + first);
+        if ((s = up(const_cast<uint8_t *>(d_.owner_family) + first, fam, n, err))) return s;
+        dirty_ = true;                    // masked contacts may change: rebuild before the next step
+        return DEM_OK;
+    }
+
+    dem_status set_family_motion(int f, const double *v, const double *w, std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        if ((s = alloc_families(err))) return s;
+        family_set_motion(m_.fam_motion[f], v, w);
+        return alloc_families(err);
+    }
+
+    dem_status set_family_contacts(int fa, int fb, int on, std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        if ((s = alloc_families(err))) return s;
+        family_set_contacts(m_.fam_mask, fa, fb, on);
+        if ((s = alloc_families(err))) return s;
+        dirty_ = true;
+        return DEM_OK;
+    }
+
+    dem_status set_active_box(int64_t first, int64_t n, const double lo[3], const double hi[3], int fin, int fout,
+                              std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        if ((s = alloc_families(err))) return s;
+        if (n > 0) {
+            uint8_t *fam = const_cast<uint8_t *>(d_.owner_family);
+            k_active_box<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, make_double3(lo[0], lo[1], lo[2]),
+                                                           make_double3(hi[0], hi[1], hi[2]), fin, fout, fam);
+            DEM_CU(cudaGetLastError());
+            DEM_CU(cudaMemcpyAsync(m_.owner_family.data() + first, fam + first, n, cudaMemcpyDeviceToHost, sf_));
+            DEM_CU(cudaStreamSynchronize(sf_));
+        }
+        dirty_ = true;
         return DEM_OK;
     }
 
@@ -1602,6 +1711,12 @@ private:
             g = std::min(g, std::max(1u, cap));
         }
         const bool lean = MODE == MODE_STEP && tune_.contact_lean;
+        if (m_.rolling) {
+            // rolling resistance: its own build of the kernel (the others carry none of it)
+            if (m_.clumps) k_contact<F, true, MODE, 0, true><<<g, b, 0, sf_>>>(d_, eF, eT);
+            else k_contact<F, false, MODE, 0, true><<<g, b, 0, sf_>>>(d_, eF, eT);
+            return;
+        }
         if (m_.clumps) {
             if (lean) k_contact<F, true, MODE_STEP, 1><<<g, b, 0, sf_>>>(d_, eF, eT);
             else k_contact<F, true, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
@@ -1617,7 +1732,11 @@ private:
         if (key == occ_block_) return occ_per_sm_;
         int per_sm = 0;
         cudaError_t e;
-        if (tune_.contact_lean)
+        if (m_.rolling)
+            e = m_.clumps
+                    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, true, MODE_STEP, 0, true>, b, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, false, MODE_STEP, 0, true>, b, 0);
+        else if (tune_.contact_lean)
             e = m_.clumps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, true, MODE_STEP, 1>, b, 0)
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, false, MODE_STEP, 1>, b, 0);
         else
@@ -1649,7 +1768,7 @@ private:
     }
 
     // Single spheres with the fused step chosen: one kernel for forces and integration.
-    bool fused() const { return !m_.clumps && tune_.fused_block > 0; }
+    bool fused() const { return !m_.clumps && !m_.rolling && tune_.fused_block > 0; }
 
     void force_step()
     {

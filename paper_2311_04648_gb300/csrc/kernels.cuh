@@ -24,6 +24,7 @@ struct DetectBuffers {
     void *sorted;              // gathered snapshot in cell order
     void *sorted_aux;
     uint32_t *sorted_owner;    // owner of each sorted entry
+    uint8_t *sorted_family;    // family of each sorted entry (only where families mask contacts)
     uint32_t *n_valid;         // device counter: active entries at the front of the order
 };
 

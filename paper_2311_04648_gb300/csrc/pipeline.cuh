@@ -18,6 +18,8 @@
 
 namespace dem {
 
+// One history entry: the tangential displacement (x, y, z) and, in the fourth lane, the
+// time the contact has lasted (kept where a scene has rolling resistance, else zero).
 template <typename H, typename R>
 __device__ __forceinline__ V3<R> hist_get(const H *h, int64_t e)
 {
@@ -25,10 +27,17 @@ __device__ __forceinline__ V3<R> hist_get(const H *h, int64_t e)
     return {(R)v.x, (R)v.y, (R)v.z};
 }
 template <typename H, typename R>
-__device__ __forceinline__ void hist_put(H *h, int64_t e, V3<R> u)
+__device__ __forceinline__ V3<R> hist_get(const H *h, int64_t e, R &age)
+{
+    const H v = h[e];
+    age = (R)v.w;
+    return {(R)v.x, (R)v.y, (R)v.z};
+}
+template <typename H, typename R>
+__device__ __forceinline__ void hist_put(H *h, int64_t e, V3<R> u, R age = R(0))
 {
     H v;
-    v.x = u.x; v.y = u.y; v.z = u.z; v.w = 0;
+    v.x = u.x; v.y = u.y; v.z = u.z; v.w = age;
     h[e] = v;
 }
 
@@ -74,6 +83,13 @@ struct Dev {
     const Wall *walls;
     const PairParam *pairs;
     const PairParamF *pairs_f;
+    const double *crr;              // rolling resistance per material pair (pairs' indexing)
+    const float *crr_f;             // the same rounded to FP32
+    // family tags; owner_family is null while no family has prescribed motion or masked
+    // contacts (the kernels then skip every family lookup)
+    const uint8_t *owner_family;
+    const FamilyMotion *fam_motion; // [N_FAMILY]
+    const uint32_t *fam_mask;       // [FAMILY_MASK_WORDS]
     const uint16_t *mat_scene, *mat_local;
     DevStatus *status;
     unsigned int *audit;            // AUDIT_SLOTS x AUDIT_STRIDE words (per-warp maxima of a step)
@@ -362,6 +378,10 @@ __global__ void __launch_bounds__(256) k_cellstart(Dev<F> d, DetectBuffers b, co
         reinterpret_cast<double4_32a *>(b.sorted)[t] = reinterpret_cast<const double4_32a *>(b.snap)[id];
     }
     b.sorted_owner[t] = d.sph_owner[id];
+    if (d.owner_family) {
+        const uint32_t o = d.sph_owner[id];
+        b.sorted_family[t] = o != 0xffffffffu ? d.owner_family[o] : (uint8_t)0;
+    }
 }
 
 // Listed-pair predicate on snapshot entries: squared distance below
@@ -416,6 +436,9 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
     const uint32_t key = keys[t];
     const uint32_t oi = b.sorted_owner[t];
     const Scene &sc = d.scenes[d.owner_scene[oi]];
+    // families: candidates of a family whose contacts with this one are masked are skipped
+    const bool fam = d.owner_family != nullptr;
+    const int fi = fam ? (int)b.sorted_family[t] : 0;
     const uint32_t local = key - sc.cell_base;
     const int nx = sc.nc[0], ny = sc.nc[1], nz = sc.nc[2];
     const int cx = (int)(local % (uint32_t)nx);
@@ -458,11 +481,13 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
                 if constexpr (F::voxel) {
                     if (vals[u] == i) continue;
                     if (CLUMPS && b.sorted_owner[u] == oi) continue;
+                    if (fam && !families_meet(d.fam_mask, fi, b.sorted_family[u])) continue;
                     hit = listed_f32(ac, ao, reinterpret_cast<const int4 *>(b.sorted)[u],
                                      reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
                 } else {
                     if (vals[u] == i) continue;
                     if (CLUMPS && b.sorted_owner[u] == oi) continue;
+                    if (fam && !families_meet(d.fam_mask, fi, b.sorted_family[u])) continue;
                     hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
                 }
                 if (hit) row_insert(buf, n, vals[u]);
@@ -646,8 +671,9 @@ __global__ void __launch_bounds__(256) k_link(Dev<F> d)
         if (!(j & WALL_BIT) && j > (uint32_t)s) ++owned;
         const int ko = row_find(po, d.Np, s, nold, j);
         V3<R> u = {R(0), R(0), R(0)};
-        if (ko >= 0) u = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hs], (int64_t)ko * d.Np + s);
-        hist_put(d.lists.hist[hd], e, u);
+        R age = R(0);
+        if (ko >= 0) u = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hs], (int64_t)ko * d.Np + s, age);
+        hist_put(d.lists.hist[hd], e, u, age);
     }
     const unsigned int tot = __reduce_add_sync(0xffffffffu, owned);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&stp->list_pairs[ln], tot);
@@ -760,6 +786,34 @@ __device__ __forceinline__ const PairParam *pair_table(const Dev<F> &d, double)
     return d.pairs;
 }
 
+// The fourth lane of a history vector counts a contact's duration: in the FP64 form its
+// age in seconds, accumulated as age + h every step (the wildcard of Sec. 4.2.1); in the
+// voxel form the number of steps it has lasted, an integer held exactly in FP32 up to
+// 2^24 steps, whose age count * h has one rounding instead of one per step.
+template <class F>
+__device__ __forceinline__ typename F::R advance_age(typename F::R lane, typename F::R h)
+{
+    if constexpr (F::voxel) return radd(lane, typename F::R(1));
+    else return radd(lane, h);
+}
+template <class F>
+__device__ __forceinline__ typename F::R age_seconds(typename F::R lane, typename F::R h)
+{
+    if constexpr (F::voxel) return rmul(lane, h);
+    else return lane;
+}
+
+template <class F>
+__device__ __forceinline__ const float *crr_table(const Dev<F> &d, float)
+{
+    return d.crr_f;
+}
+template <class F>
+__device__ __forceinline__ const double *crr_table(const Dev<F> &d, double)
+{
+    return d.crr;
+}
+
 // The n listed entries of sphere s (first partner j_first) evaluated from s's side: the
 // sums of the contact forces on s and of their torques about its owner's centre, and
 // (MODE_STEP) each entry's updated history written to the other history buffer.  Every
@@ -767,7 +821,10 @@ __device__ __forceinline__ const PairParam *pair_table(const Dev<F> &d, double)
 // used, so an entry costs one memory round trip; the material constants come from the
 // sphere's own scene (both bodies of a contact belong to it), without a lookup of the
 // partner's material where the scene has only one.
-template <class F, bool CLUMPS, int MODE>
+// ROLL compiles in rolling resistance (worlds where a material pair has C_r > 0): each
+// entry's age is kept in its history vector, and past the collision time the rolling
+// force's torque is added after the contact force's.
+template <class F, bool CLUMPS, int MODE, bool ROLL = false>
 __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me, const Scene &sc, int64_t s, int n,
                                           uint32_t j_first, int sp, int hp, int lc, V3<typename F::R> &Fs,
                                           V3<typename F::R> &Ts)
@@ -787,9 +844,11 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
         const int64_t e = (int64_t)k * d.Np + s;
         const uint32_t j = j_next;
         if (k + 1 < n) j_next = prow[e + d.Np];      // next partner's id in flight early
-        V3<R> ut = hist_get<H, R>(hin, e);
+        R age = R(0);
+        V3<R> ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
         ContactIn<R> c;
         V3<R> armA, armB;
+        V3<R> wB = zero;                 // the partner's angular velocity (ROLL only)
         bool on;
         int mb;
         if (j & WALL_BIT) {
@@ -806,23 +865,42 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
             // copy of the history (the partner's copy is its exact negation)
             mb = other.mat >= 0 || one ? other.mat : (int)d.sph_mat[j];
             on = sphere_contact<F, false>(d, me, other, c, armA, armB);
+            if constexpr (ROLL) wB = other.w;
         }
         if (on) {
-            const auto p = tab[one ? sc.pair_base : row + mb];
+            const int pk = one ? sc.pair_base : row + mb;
+            const auto p = tab[pk];
             c.Estar = p.Estar;
             c.Gstar = p.Gstar;
             c.beta = p.beta;
             c.mu = p.mu;
             V3<R> Fc;
-            hertz_mindlin<R>(c, h, ut, Fc);
-            Fs = Fs + Fc;
-            Ts = Ts + cross(armA, Fc);
+            if constexpr (ROLL) {
+                R fn_abs;
+                hertz_mindlin<R>(c, h, ut, Fc, &fn_abs);
+                age = advance_age<F>(age, h);
+                Fs = Fs + Fc;
+                Ts = Ts + cross(armA, Fc);
+                const R crr = crr_table(d, R(0))[pk];
+                if (crr > R(0) && !within_collision_time<R>(c, age_seconds<F>(age, h))) {
+                    // rolling parts of the contact-point velocities; a wall moves by
+                    // rotation only, so its part is its whole surface velocity
+                    const V3<R> rotA = cross_rn(me.w, armA);
+                    const V3<R> rotB = (j & WALL_BIT) ? c.uB : cross_rn(wB, armB);
+                    const V3<R> vr = {rsub(rotB.x, rotA.x), rsub(rotB.y, rotA.y), rsub(rotB.z, rotA.z)};
+                    Ts = Ts + cross(armA, rolling_force<R>(crr, fn_abs, vr));
+                }
+            } else {
+                hertz_mindlin<R>(c, h, ut, Fc);
+                Fs = Fs + Fc;
+                Ts = Ts + cross(armA, Fc);
+            }
         }
-        if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero);
+        if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero, on ? age : R(0));
     }
 }
 
-template <class F, bool CLUMPS, int MODE>
+template <class F, bool CLUMPS, int MODE, bool ROLL = false>
 __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_known, uint32_t j0_known, int sp,
                                              int hp, int lc, double *eval_F, double *eval_T)
 {
@@ -846,7 +924,7 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         scene = d.owner_scene[o];
     }
     if (act)
-        pair_sums<F, CLUMPS, MODE>(d, me, d.scenes[scene], s, n,
+        pair_sums<F, CLUMPS, MODE, ROLL>(d, me, d.scenes[scene], s, n,
                                    n_known >= 0 ? j0_known : (n > 0 ? d.lists.partner[lc][s] : 0u), sp, hp, lc, Fs, Ts);
     if (CLUMPS) {
         // segmented suffix sums over the owner's consecutive lanes; the head lane ends
@@ -885,15 +963,15 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
 // LEAN = 1 compiles the kernel for 5 resident blocks of CONTACT_BLOCK_MAX threads per SM
 // (96 registers, some spilled to the L1-cached local memory) instead of 4: more
 // warps to hide the latency of the gathers, chosen by the autotuner where it pays.
-template <class F, bool CLUMPS, int MODE, int LEAN = 0>
+template <class F, bool CLUMPS, int MODE, int LEAN = 0, bool ROLL = false>
 __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
 {
     DevStatus *stp = d.status;
     if (MODE == MODE_STEP && (stp->halt || stp->list_stale)) return;
     const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
     if (MODE == MODE_EVAL) {
-        contact_slot<F, CLUMPS, MODE>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, -1, 0u, sp, hp, lc,
-                                      eval_F, eval_T);
+        contact_slot<F, CLUMPS, MODE, ROLL>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, -1, 0u, sp, hp, lc,
+                                            eval_F, eval_T);
         return;
     }
     // the counter never exceeds the slots (or 32-slot groups); the clamp keeps every
@@ -904,8 +982,8 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
     if (CLUMPS) {
         const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
         for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps)
-            contact_slot<F, CLUMPS, MODE>(d, ((int64_t)act[w].x << 5) + (threadIdx.x & 31), -1, 0u, sp, hp, lc,
-                                          eval_F, eval_T);
+            contact_slot<F, CLUMPS, MODE, ROLL>(d, ((int64_t)act[w].x << 5) + (threadIdx.x & 31), -1, 0u, sp, hp,
+                                                lc, eval_F, eval_T);
     } else {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -913,7 +991,7 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
         for (; t < nw; t += stride) {
             // the next work entry is read while this one is evaluated
             const uint4 next = t + stride < nw ? act[t + stride] : a;
-            contact_slot<F, CLUMPS, MODE>(d, (int64_t)a.x, (int)a.y, a.z, sp, hp, lc, eval_F, eval_T);
+            contact_slot<F, CLUMPS, MODE, ROLL>(d, (int64_t)a.x, (int)a.y, a.z, sp, hp, lc, eval_F, eval_T);
             a = next;
         }
     }
@@ -978,8 +1056,21 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
                                  : V3<R>{(R)sc.g[0], (R)sc.g[1], (R)sc.g[2]};
         const V3<R> Ft = vadd_rn(Fs, vscale_rn(mass, g));
         vn = vadd_rn(vn, vscale_rn(h, vscale_rn(im, Ft)));
+        // prescribed motion of the owner's family replaces what the forces give
+        const FamilyMotion *pm = d.owner_family ? &d.fam_motion[d.owner_family[o]] : nullptr;
+        if (pm && pm->fix_v) {
+            if constexpr (F::voxel) vn = {pm->vf[0], pm->vf[1], pm->vf[2]};
+            else vn = {(R)pm->v[0], (R)pm->v[1], (R)pm->v[2]};
+        }
         R nw, nx, ny, nz;
-        if (iso) {
+        if (pm && pm->fix_w) {
+            // turn by the prescribed (global-frame) angular velocity: q <- dq(h w) q
+            if constexpr (F::voxel) wn = {pm->wf[0], pm->wf[1], pm->wf[2]};
+            else wn = {(R)pm->w[0], (R)pm->w[1], (R)pm->w[2]};
+            R dw, dx, dy, dz;
+            quat_increment<R>(wn, h, dw, dx, dy, dz);
+            quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+        } else if (iso) {
             // isotropic inertia: the body-frame update equals a world-frame one
             wn = vadd_rn(wn, vscale_rn(h, vscale_rn(ii.x, Ts)));
             R dw, dx, dy, dz;
@@ -1476,7 +1567,8 @@ static __global__ void __launch_bounds__(256) k_min_pred(const float *out, const
 // Evaluate every owned entry (canonical sphere pairs and wall entries) at the current
 // state: overlap (<= 0 if not in contact), force on A, contact point and updated history.
 template <class F, bool CLUMPS>
-__global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *fo, double *pt, double *hi)
+__global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *fo, double *pt, double *hi,
+                                                  double *ag, double *rf)
 {
     using R = typename F::R;
     DevStatus *stp = d.status;
@@ -1497,11 +1589,16 @@ __global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *
         if (!act) continue;
         ContactIn<R> c;
         V3<R> armA, armB;
-        V3<R> ut = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hp], e);
+        R age;
+        V3<R> ut = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hp], e, age);
         V3<R> Fc;
         V3<double> cp;
+        V3<R> wB = {R(0), R(0), R(0)};
+        int mb;
         if (j & WALL_BIT) {
-            if (!wall_contact<F>(d, me, sc, d.walls[j & ~WALL_BIT], c, armA, &cp)) continue;
+            const Wall &wl = d.walls[j & ~WALL_BIT];
+            if (!wall_contact<F>(d, me, sc, wl, c, armA, &cp)) continue;
+            mb = wl.mat;
         } else {
             if (j < (uint32_t)s) continue;
             SphereK<F> B = load_sphere<F, CLUMPS>(d, sp, j);
@@ -1510,12 +1607,32 @@ __global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *
             V3<double> pa = F::absolute(me.p, sc, d.Ld);
             double a = ((double)me.rad + (double)me.rlo) - 0.5 * (double)c.delta;
             cp = {pa.x - a * (double)c.n.x, pa.y - a * (double)c.n.y, pa.z - a * (double)c.n.z};
+            wB = B.w;
+            mb = B.mat;
         }
-        hertz_mindlin<R>(c, h, ut, Fc);
+        R fn_abs;
+        hertz_mindlin<R>(c, h, ut, Fc, &fn_abs);
+        V3<R> Fr = {R(0), R(0), R(0)};
+        if (sc.has_rolling) {
+            age = advance_age<F>(age, h);
+            const int pk = sc.pair_base + (me.mat - sc.mat_base) * sc.n_mat + (mb - sc.mat_base);
+            const R crr = crr_table(d, R(0))[pk];
+            if (crr > R(0) && !within_collision_time<R>(c, age_seconds<F>(age, h))) {
+                const V3<R> rotA = cross_rn(me.w, armA);
+                const V3<R> rotB = (j & WALL_BIT) ? c.uB : cross_rn(wB, armB);
+                Fr = rolling_force<R>(crr, fn_abs, V3<R>{rsub(rotB.x, rotA.x), rsub(rotB.y, rotA.y),
+                                                          rsub(rotB.z, rotA.z)});
+            }
+            age = age_seconds<F>(age, h);
+        } else {
+            age = R(0);
+        }
         ov[e] = (double)c.delta;
         fo[3 * e + 0] = (double)Fc.x; fo[3 * e + 1] = (double)Fc.y; fo[3 * e + 2] = (double)Fc.z;
         pt[3 * e + 0] = cp.x; pt[3 * e + 1] = cp.y; pt[3 * e + 2] = cp.z;
         hi[3 * e + 0] = (double)ut.x; hi[3 * e + 1] = (double)ut.y; hi[3 * e + 2] = (double)ut.z;
+        ag[e] = (double)age;
+        rf[3 * e + 0] = (double)Fr.x; rf[3 * e + 1] = (double)Fr.y; rf[3 * e + 2] = (double)Fr.z;
     }
 }
 
@@ -1567,6 +1684,23 @@ __global__ void __launch_bounds__(256) k_count(Dev<F> d, unsigned long long *out
 }
 
 // Owner state to FP64 host layout (quaternion (w,x,y,z); angular velocity to body frame).
+// Active box (Sec. 6.4): owners [first, first + n) whose centre lies inside [lo, hi]
+// take family fin, the others fout.
+template <class F>
+__global__ void __launch_bounds__(256) k_active_box(Dev<F> d, int64_t first, int64_t n, double3 lo, double3 hi,
+                                                    int fin, int fout, uint8_t *family)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t o = first + k;
+    const int sp = d.status->state_par;
+    typename F::R mass;
+    const typename F::Pos p = F::load(d.st.pos[sp], o, mass);
+    const V3<double> x = F::absolute(p, d.scenes[d.owner_scene[o]], d.Ld);
+    const bool in = x.x >= lo.x && x.x <= hi.x && x.y >= lo.y && x.y <= hi.y && x.z >= lo.z && x.z <= hi.z;
+    family[o] = (uint8_t)(in ? fin : fout);
+}
+
 template <class F>
 __global__ void k_owner_download(Dev<F> d, int64_t first, int64_t n, double *x, double *q, double *v, double *w)
 {

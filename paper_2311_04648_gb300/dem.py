@@ -88,7 +88,10 @@ def _sigs(L):
         "dem_get_sphere_positions": [P, I64, I64, P, P], "dem_get_sphere_voxels": [P, I64, I64, P, P, P],
         "dem_get_contacts": [P, I64, P, P, P, P, P, P, P], "dem_get_listed_pairs": [P, I64, P, P, P],
         "dem_get_listed_wall_pairs": [P, I64, P, P, P], "dem_get_owner_forces": [P, I64, I64, P, P],
-        "dem_set_history": [P, I64, P, P, P], "dem_get_stats": [P, P], "dem_get_diagnostics": [P, P],
+        "dem_set_history": [P, I64, P, P, P], "dem_set_history_age": [P, I64, P, P, P, P],
+        "dem_get_contact_rolling": [P, I64, P, P, P],
+        "dem_set_family": [P, I64, I64, P], "dem_set_family_motion": [P, I32, P, P],
+        "dem_set_family_contacts": [P, I32, I32, I32], "dem_set_active_box": [P, P, P, I32, I32], "dem_get_stats": [P, P], "dem_get_diagnostics": [P, P],
         "dem_save_state": [P, P, SZ, P], "dem_load_state": [P, P, SZ],
         "dem_batch_create": [I32, P, P], "dem_batch_world": [P, I32, P], "dem_batch_initialize": [P],
         "dem_batch_step": [P, I64], "dem_batch_destroy": [P],
@@ -428,10 +431,40 @@ class World:
         self._c(self.L.dem_get_owner_forces(self.h, first, n, _p(F), _p(T)))
         return F, T
 
-    def set_history(self, i, j, ut):
+    def set_history(self, i, j, ut, age=None):
         i = np.ascontiguousarray(i, np.int64); j = np.ascontiguousarray(j, np.int64)
         ut = _f64(ut).reshape(-1, 3)
-        self._c(self.L.dem_set_history(self.h, len(i), _p(i), _p(j), _p(ut)))
+        if age is None:
+            self._c(self.L.dem_set_history(self.h, len(i), _p(i), _p(j), _p(ut)))
+        else:
+            self._c(self.L.dem_set_history_age(self.h, len(i), _p(i), _p(j), _p(ut), _p(_f64(age))))
+
+    # ---- family tags
+    def set_family(self, first, family):
+        f = np.ascontiguousarray(family, np.uint8)
+        self._c(self.L.dem_set_family(self.h, int(first), len(f), _p(f)))
+
+    def set_family_motion(self, family, v=None, omega=None):
+        self._c(self.L.dem_set_family_motion(self.h, int(family), _p(_f64(v)) if v is not None else None,
+                                             _p(_f64(omega)) if omega is not None else None))
+
+    def set_family_contacts(self, fa, fb, on):
+        self._c(self.L.dem_set_family_contacts(self.h, int(fa), int(fb), 1 if on else 0))
+
+    def set_active_box(self, lo, hi, family_inside, family_outside):
+        self._c(self.L.dem_set_active_box(self.h, _p(_f64(lo)), _p(_f64(hi)), int(family_inside),
+                                          int(family_outside)))
+
+    def contact_rolling(self):
+        """Per contact (dem_get_contacts order): its age and the rolling-resistance force on i."""
+        cnt = C.c_int64()
+        st = self.L.dem_get_contact_rolling(self.h, 0, C.byref(cnt), None, None)
+        if st not in (OK, ERR_CAPACITY):
+            self._c(st)
+        n = cnt.value
+        age = np.empty(n); trf = np.empty((n, 3))
+        self._c(self.L.dem_get_contact_rolling(self.h, n, C.byref(cnt), _p(age), _p(trf)))
+        return age, trf
 
     def stats(self):
         s = Stats()
@@ -462,12 +495,16 @@ class World:
         nm = len(scene.E)
         cor = np.asarray(scene.cor).reshape(nm, nm)
         mu = np.asarray(scene.mu).reshape(nm, nm)
+        crr = (np.zeros((nm, nm)) if getattr(scene, "crr", None) is None
+               else np.asarray(scene.crr, np.float64).reshape(nm, nm))
         for a in range(nm):
-            self.add_material(float(scene.E[a]), float(scene.nu[a]), float(cor[a, a]), float(mu[a, a]))
+            self.add_material(float(scene.E[a]), float(scene.nu[a]), float(cor[a, a]), float(mu[a, a]),
+                              float(crr[a, a]))
         for a in range(nm):
             for b in range(a + 1, nm):
                 self.set_material_pair(PROP_COR, a, b, float(cor[a, b]))
                 self.set_material_pair(PROP_MU, a, b, float(mu[a, b]))
+                self.set_material_pair(PROP_CRR, a, b, float(crr[a, b]))
         for wd in scene.walls:
             t = int(wd["type"])
             om = np.asarray(wd.get("omega", (0.0, 0.0, 0.0)), np.float64)
@@ -482,6 +519,11 @@ class World:
                 self.set_wall_spin(wid, om)
         for t in scene.templates:
             self.add_clump_template(t.rel_xyz, t.radii, t.mats, float(t.mass), t.moi)
+        fm = getattr(scene, "family_motion", None) or {}
+        for f, (vel, om) in fm.items():
+            self.set_family_motion(f, vel, om)
+        for fa, fb in getattr(scene, "family_masked", None) or []:
+            self.set_family_contacts(fa, fb, False)
         ot = np.asarray(scene.owner_template)
         tid = int(ot[0]) if len(ot) and np.all(ot == ot[0]) else ot
         if len(ot):
@@ -494,6 +536,8 @@ class World:
             self.set_sink(scene.sink[0], scene.sink[1])
         if margin is not None:
             self.set_margin(margin)
+        if getattr(scene, "family", None) is not None:
+            self.set_family(0, scene.family)
         self.n_owner = len(ot)
         self.n_sphere = scene.n_sphere
         return self

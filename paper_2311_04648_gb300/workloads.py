@@ -63,6 +63,10 @@ class Scene:
     r_max: float = 0.0
     name: str = ""
     meta: dict = field(default_factory=dict)
+    crr: np.ndarray | None = None    # (nm, nm) rolling resistance coefficients; None: zero
+    family: np.ndarray | None = None  # (M,) family tag per owner (0..255); None: all 0
+    family_motion: dict | None = None  # family -> (v or None, w or None): prescribed velocities
+    family_masked: list | None = None  # (a, b) family pairs whose contacts are not resolved
 
     @property
     def n_owner(self):

@@ -5,6 +5,7 @@ Bars: contact sets bit-exact (same predicate, same positions); FP64 plain form w
 voxel + FP32 form within 1e-4 on per-contact forces (error normalised by
 max(|F64|, 1e-3 median |F64|)); schedules and batching bit-identical to the plain run.
 """
+import dataclasses
 import math
 import os
 
@@ -169,10 +170,10 @@ def sync_oracle_to_gpu(w, ow, stored):
     if stored is None:
         ow.set_history(np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros((0, 3)))
     else:
-        ow.set_history(stored["i"], stored["j"], stored["history"])
+        ow.set_history(stored["i"], stored["j"], stored["history"], age=stored.get("age"))
 
 
-def one_step_parity(w, ow, stored, tol=TOL64):
+def one_step_parity(w, ow, stored, tol=TOL64, rolling=False):
     """From the GPU's own state: every contact's force, overlap, point and updated
     history, the per-owner force and torque sums, and the state after one step, against
     the oracle at 1e-9 (forces per contact relative to its largest component; overlaps
@@ -185,6 +186,12 @@ def one_step_parity(w, ow, stored, tol=TOL64):
     fs = np.abs(oc["force"]).max(axis=1, keepdims=True) + 1e-300
     hs = max(float(np.max(np.abs(oc["ut"]))) if len(oc) else 0.0, 1e-300)
     Fg, Tg = w.owner_forces()
+    if rolling:
+        age, trf = w.contact_rolling()
+        # the contact's age after this step's update: the same FP64 additions on both sides
+        assert np.array_equal(age, oc["age"])
+        assert rel_err(trf, oc["torque_force"], fs) < tol if len(oc) else True
+        one_step_parity.rolling_on = int(np.sum(np.any(oc["torque_force"] != 0, axis=1))) if len(oc) else 0
     errs = dict(force=rel_err(gc["force"], oc["force"], fs) if len(oc) else 0.0,
                 overlap=rel_err(gc["overlap"], oc["overlap"], float(np.max(ow.rad))) if len(oc) else 0.0,
                 point=rel_err(gc["point"], oc["point"], 1e-3) if len(oc) else 0.0,
@@ -637,3 +644,185 @@ def test_unset_pairs_of_differing_materials_are_rejected():
     w.initialize()
     w.step(2)
     w.close()
+
+
+# ----------------------------------------------------------------------------- rolling resistance
+
+def with_rolling(scene, crr):
+    nm = len(scene.E)
+    return dataclasses.replace(scene, crr=np.full((nm, nm), crr))
+
+
+def stored_contacts(w):
+    c = w.contacts()
+    c["age"] = w.contact_rolling()[0]
+    return c
+
+
+ROLLING_SCENES = {
+    "dense_polydisperse": (lambda: with_rolling(dense_scene(n=600, seed=8, vel=0.5), 0.08), (100, 300)),
+    "clumps_walls_gravity": (lambda: with_rolling(W.packed_clumps(n=150, seed=10), 0.05), (150, 300)),
+    "spinning_drum": (lambda: with_rolling(W.drum_bed(n=120, seed=1), 0.1), (400, 800)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ROLLING_SCENES))
+def test_fp64_rolling_resistance_matches_oracle(name):
+    """Rolling resistance (Sec. 4.1, F_r / tau_r, with the collision-time gate of the
+    default model of Sec. 4.2.1): one-step parity at 1e-9 from the GPU's own states,
+    contact ages included (they must agree bit for bit), and the free-running trajectory
+    within 1e-9."""
+    make, chunks = ROLLING_SCENES[name]
+    s = make()
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    free = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    errs, n = one_step_parity(w, ow, None, rolling=True)
+    assert one_step_parity.rolling_on == 0             # every contact is younger than its collision time
+    assert free.step(1) == 0
+    worst = {}
+    rolling_on = 0
+    for k in chunks:
+        w.step(k - 1)
+        assert ow.step(k - 1) == 0
+        assert free.step(k) == 0
+        stored = stored_contacts(w)
+        w.step(1)
+        assert ow.step(1) == 0
+        st, _ = state_close(w, free, TOL64)
+        worst = {a: max(worst.get(a, 0.0), b) for a, b in st.items()}
+        errs, n = one_step_parity(w, ow, stored, rolling=True)
+        rolling_on += one_step_parity.rolling_on
+        assert free.step(1) == 0
+        assert n > 0
+    print(name, "rolling free-running", worst, "contacts with rolling resistance", rolling_on)
+    assert max(worst.values()) < TOL64, worst
+    assert rolling_on > 0
+
+
+def test_voxel_fp32_rolling_resistance_within_1e4_of_fp64():
+    """The voxel + FP32 form with rolling resistance: per-contact forces and rolling
+    forces within 1e-4 of the FP64 oracle on the GPU's own state (the precision form's
+    metric, normalised by max(|F64|, 1e-3 median |F64|))."""
+    s = with_rolling(dense_scene(n=1200, seed=14, vel=0.3), 0.08)
+    w = dem.World.from_scene(s, precision="voxel_fp32")
+    ow = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    w.step(299)
+    stored = stored_contacts(w)
+    w.step(1)
+    sync_oracle_to_gpu(w, ow, stored)
+    gc = w.contacts()
+    age, trf = w.contact_rolling()
+    _, _, oc = ow.eval()
+    key_g = {(int(a), int(b)): k for k, (a, b) in enumerate(zip(gc["i"], gc["j"]))}
+    key_o = {(int(a), int(b)): k for k, (a, b) in enumerate(zip(oc["i"], oc["j"]))}
+    common = sorted(set(key_g) & set(key_o))
+    assert len(common) > 300
+    fo = np.array([oc["force"][key_o[k]] for k in common])
+    mag = np.linalg.norm(fo, axis=1)
+    floor = 1e-3 * np.median(mag)
+    for got, want in ((gc["force"], oc["force"]), (trf, oc["torque_force"])):
+        g = np.array([got[key_g[k]] for k in common])
+        o = np.array([want[key_o[k]] for k in common])
+        err = np.linalg.norm(g - o, axis=1) / np.maximum(mag, floor)
+        assert err.max() <= 1e-4, err.max()
+    assert np.sum(np.linalg.norm(np.array([oc["torque_force"][key_o[k]] for k in common]), axis=1) > 0) > 100
+
+
+
+# ----------------------------------------------------------------------------- family tags
+
+def family_scene(n=800, seed=33):
+    """A dense lattice with families: the bottom fifth held fixed, the top tenth pushed
+    down at a prescribed 5 cm/s with a prescribed spin, a middle slab whose contacts with
+    family 0 are not resolved."""
+    s = dense_scene(n=n, seed=seed, vel=0.2)
+    z = np.asarray(s.x)[:, 2]
+    fam = np.zeros(len(z), np.uint8)
+    fam[z < np.quantile(z, 0.2)] = 1
+    fam[z > np.quantile(z, 0.9)] = 2
+    fam[(z > np.quantile(z, 0.45)) & (z < np.quantile(z, 0.55))] = 3
+    return dataclasses.replace(s, family=fam,
+                               family_motion={1: ((0, 0, 0), (0, 0, 0)), 2: ((0, 0, -0.05), (0.0, 0.0, 20.0))},
+                               family_masked=[(3, 0)])
+
+
+def test_fp64_families_match_oracle():
+    """Family tags (Sec. 2.2.2): fixed and prescribed families move exactly as prescribed,
+    masked contacts are never listed, and everything matches the oracle at 1e-9 (one step
+    from the GPU's own states, and free-running)."""
+    s = family_scene()
+    w = dem.World.from_scene(s, precision="fp64")
+    ow = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    free = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    x0 = np.asarray(s.x)
+    one_step_parity(w, ow, None)
+    assert free.step(1) == 0
+    worst = {}
+    for k in (100, 200):
+        w.step(k - 1)
+        assert ow.step(k - 1) == 0 and free.step(k) == 0
+        stored = w.contacts()
+        w.step(1)
+        assert ow.step(1) == 0
+        st, _ = state_close(w, free, TOL64)
+        worst = {a: max(worst.get(a, 0.0), b) for a, b in st.items()}
+        one_step_parity(w, ow, stored)
+        assert free.step(1) == 0
+    assert max(worst.values()) < TOL64, worst
+    x, q, v, wb = w.owner_state()
+    fam = s.family
+    assert np.array_equal(x[fam == 1], x0[fam == 1]) and np.all(v[fam == 1] == 0.0)
+    assert np.all(v[fam == 2] == np.array([0.0, 0.0, -0.05]))
+    # no listed pair joins family 3 to family 0
+    gi, gj = w.listed_pairs()
+    o = ow.owner
+    fi, fj = fam[o[gi]], fam[o[gj]]
+    assert not np.any(((fi == 3) & (fj == 0)) | ((fi == 0) & (fj == 3)))
+    assert np.any((fi == 3) & (fj == 3)) and np.any((fi == 1) & (fj == 0))
+
+
+def test_voxel_fp32_families_hold_the_prescribed_motion():
+    """The voxel form: a fixed family's positions stay bit for bit, a prescribed one moves
+    at its velocity, and the rest stays within the precision form's error of FP64."""
+    s = family_scene()
+    w = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    ow = oracle.OracleWorld(s, cell_list=True, threads=oracle_threads())
+    x_start = w.owner_state()[0]
+    w.step(300)
+    assert ow.step(300) == 0
+    x, q, v, wb = w.owner_state()
+    fam = s.family
+    assert np.array_equal(x[fam == 1], x_start[fam == 1]) and np.all(v[fam == 1] == 0.0)
+    assert np.allclose(v[fam == 2], [0.0, 0.0, np.float32(-0.05)], rtol=0, atol=1e-9)
+    assert np.max(np.abs(x - ow.x)) < 1e-6
+
+
+def test_active_box_leaves_the_active_region_bit_identical():
+    """Sec. 6.4: owners outside the active box are held fixed and their contacts with each
+    other are dropped.  Contacts between two fixed owners move nothing, so the run equals,
+    bit for bit, one where the same owners are fixed with every contact resolved; the box
+    tags owners by their centres."""
+    s = dense_scene(n=1500, seed=41, vel=0.3)
+    lo, hi = np.asarray(s.box_lo), np.asarray(s.box_hi)
+    blo = lo + 0.25 * (hi - lo)
+    bhi = hi - 0.25 * (hi - lo)
+    worlds = []
+    for dormant_masked in (True, False):
+        w = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+        w.set_family_motion(7, (0, 0, 0), (0, 0, 0))
+        if dormant_masked:
+            w.set_family_contacts(7, 7, False)
+        w.set_active_box(blo, bhi, 0, 7)
+        worlds.append(w)
+    x0 = worlds[0].owner_state()[0]
+    inside = np.all((x0 >= blo) & (x0 <= bhi), axis=1)
+    for w in worlds:
+        w.step(400)
+    a, b = worlds
+    for xa, xb in zip(a.owner_state(), b.owner_state()):
+        assert np.array_equal(xa, xb)
+    assert a.stats()["listed_pairs"] < b.stats()["listed_pairs"]
+    x = a.owner_state()[0]
+    assert np.array_equal(x[~inside], x0[~inside])
+    assert np.any(x[inside] != x0[inside])

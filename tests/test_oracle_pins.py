@@ -4,6 +4,7 @@ None of these tests compares the oracle with itself: each checks a closed form, 
 invariant, a special case or a brute-force enumeration that a plausible mistake in the
 oracle (dropped term, wrong sign or index, transposed operand) would break.
 """
+import dataclasses
 import math
 import os
 
@@ -740,3 +741,261 @@ def test_hertz_headon_unlike_materials_and_radii():
     assert best == pytest.approx(dmax, rel=2e-3)
     assert ow.v[1, 0] - ow.v[0, 0] == pytest.approx(v0, rel=2e-3)   # elastic: speed of separation = v0
 
+
+
+# ----------------------------------------------------------------------------- rolling resistance
+
+def rolling_incline_run(alpha_deg, crr, v0, t_end, mu=None):
+    """A sphere (the Sec. 4.3.1 incline parameters) set rolling without slip at v0 along
+    the incline (negative: down-slope), rolling resistance C_r = crr."""
+    gd = read_golden("incline_sec4_3_1.txt")
+    r, m = gd["radius_m"], gd["mass_kg"]
+    mu = gd["mu"] if mu is None else mu
+    rho = m / (4 / 3 * math.pi * r ** 3)
+    a = math.radians(alpha_deg)
+    g = 9.81 * np.array([-math.sin(a), 0.0, -math.cos(a)])
+    Es = gd["E_pa"] / (2 * (1 - gd["nu"] ** 2))
+    d0 = (3 * m * 9.81 * math.cos(a) / (4 * Es * math.sqrt(r))) ** (2 / 3)
+    arm0 = r - 0.5 * d0
+    plane = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    h = 2e-5
+    s = make_scene([[0.0, 0.0, r - d0]], v=[[v0, 0, 0]], wb=[[0, v0 / arm0, 0]],
+                   templates=[W.sphere_template(r, rho=rho)], walls=[plane], g=g, h=h,
+                   mat=one_material(E=gd["E_pa"], nu=gd["nu"], e=gd["cor"], mu=mu), crr=np.array([[crr]]))
+    ow = oracle.OracleWorld(s)
+    ts, vs, xs, slips, arms = [], [], [], [], []
+    for k in range(0, int(t_end / h), 50):
+        assert ow.step(50) == 0
+        qw, qx, qy, qz = ow.q[0]
+        Rm = np.array([[1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)],
+                       [2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)],
+                       [2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)]])
+        F, T, cs = ow.eval()
+        arm = np.array(cs["point"][0]) - ow.x[0]
+        ts.append((k + 50) * h)
+        vs.append(ow.v[0, 0])
+        xs.append(ow.x[0, 0])
+        slips.append(ow.v[0, 0] + np.cross(Rm @ ow.wb[0], arm)[0])
+        arms.append(np.linalg.norm(arm))
+    return np.array(ts), np.array(vs), np.array(xs), np.array(slips), a, float(np.mean(arms)), r
+
+
+@pytest.mark.parametrize("alpha", [7.0, 15.0, 25.0, 30.0])
+def test_rolling_resistance_on_an_incline_rolls_at_the_closed_form_rate(alpha):
+    """Sec. 4.3.1 with C_r = 0.1, mu = 0.25: between tan(alpha) = C_r and 3.5 mu - 2.5 C_r
+    the sphere rolls without slip.  Rolling resistance C_r N acts at the contact arm a, so
+    the friction F_t and the rolling equations m dv/dt = m g sin(alpha) - F_t and
+    I dw/dt = a (F_t - C_r N), with v = a w and N = m g cos(alpha), give
+    dv/dt = g (sin(alpha) - C_r cos(alpha)) / (1 + I / (m a^2)), I = (2/5) m r^2."""
+    crr, mu = 0.1, 0.25
+    ts, vs, xs, slips, a, arm, r = rolling_incline_run(alpha, crr, -0.2 if alpha > 7 else 0.0, 1.5)
+    assert crr < math.tan(a) < 3.5 * mu - 2.5 * crr
+    late = ts > ts[-1] * 0.4
+    assert np.max(np.abs(slips[late])) < 1e-6 * np.max(np.abs(vs[late]))
+    acc = np.polyfit(ts[late], vs[late], 1)[0]
+    assert acc == pytest.approx(-9.81 * (math.sin(a) - crr * math.cos(a)) / (1 + 0.4 * r * r / arm ** 2), rel=1e-6)
+
+
+def test_rolling_resistance_stops_a_sphere_below_tan_alpha_equal_to_cr():
+    """Sec. 4.3.1: stationary iff tan(alpha) <= (mu_s / mu_k) C_r (here mu_s = mu_k): a
+    sphere rolling down a 4 degree incline with C_r = 0.1 decelerates at
+    g (C_r cos - sin) / (1 + I / (m a^2)) and then stays put."""
+    crr = 0.1
+    ts, vs, xs, slips, a, arm, r = rolling_incline_run(4.0, crr, -0.2, 2.0)
+    assert math.tan(a) < crr
+    early = (ts > 0.1) & (ts < 0.4)            # after the first contact's transient, before it stops
+    acc = np.polyfit(ts[early], vs[early], 1)[0]
+    assert acc == pytest.approx(9.81 * (crr * math.cos(a) - math.sin(a)) / (1 + 0.4 * r * r / arm ** 2), rel=1e-6)
+    last = ts > 1.5
+    assert np.max(np.abs(vs[last])) < 1e-3 * 0.2
+    assert np.ptp(xs[last]) < 1e-4 * r
+
+
+def test_rolling_resistance_slips_above_the_mixed_threshold():
+    """Sec. 4.3.1: pure rolling only while tan(alpha) <= 3.5 mu_s - 2.5 C_r (0.625 for
+    mu = 0.25, C_r = 0.1); at 35 degrees the contact point slides."""
+    ts, vs, xs, slips, a, arm, r = rolling_incline_run(35.0, 0.1, -0.2, 1.0)
+    assert math.tan(a) > 3.5 * 0.25 - 2.5 * 0.1
+    late = ts > ts[-1] * 0.5
+    assert np.max(np.abs(slips[late])) > 0.1 * np.max(np.abs(vs[late]))
+
+
+def stack_statics_critical_mass(mu, crr, gap_frac, R, m1, g=9.81):
+    """Largest top mass m2 for which the three-sphere stack can stand with friction mu and
+    rolling resistance C_r, by the statics of a bottom sphere (rolling resistance acting
+    as a torque limit C_r N R at each of its two contacts).  With theta the angle of the
+    top contact normal from vertical and N = m2 g / 2 + x its normal force, the top
+    sphere's balance fixes the tangential force there, f = (x cos + (m2 g / 2)(cos - 1))
+    / sin, the bottom sphere's horizontal balance the floor friction
+    F = (-x - (m2 g / 2)(1 - cos)) / sin, its torque balance the rolling torque needed,
+    R x / tan(theta/2), and the floor carries m1 g + m2 g / 2.  The stack stands iff some
+    x >= 0 meets |f| <= mu N, |F| <= mu (m1 g + m2 g / 2) and the rolling torque limit
+    C_r R (N + m1 g + m2 g / 2).  (C_r = 0 leaves x = 0: mu >= tan(theta/2).)"""
+    st = (R + 0.5 * gap_frac * R) / (2 * R)
+    ct = math.sqrt(1 - st * st)
+    cot2 = 1.0 / math.tan(0.5 * math.asin(st))
+
+    def stands(m2):
+        W2 = 0.5 * m2 * g
+        x_min = W2 * (1 - ct - mu * st) / (ct + mu * st)            # |f| <= mu N
+        x_max = crr * (2 * W2 + m1 * g) / (cot2 - crr) if cot2 > crr else math.inf
+        x_f = mu * st * (m1 * g + W2) - W2 * (1 - ct)                # floor friction
+        return max(x_min, 0.0) <= min(x_max, x_f)
+
+    lo, hi = 1e-4, 1e3
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if stands(mid) else (lo, mid)
+    return lo
+
+
+def stack_run_rolling(mu, crr, gap_frac, m2, t_end=3.0, h=5e-5):
+    g = read_golden("stacking_sec4_3_2.txt")
+    R, m1 = g["radius_m"], g["bottom_mass_kg"]
+    a = R + 0.5 * gap_frac * R
+    sin_t = a / (2 * R)
+    x = np.array([[-a, 0.0, R], [a, 0.0, R], [0.0, 0.0, R + 2 * R * math.sqrt(1 - sin_t ** 2)]])
+    vol = 4.0 / 3.0 * math.pi * R ** 3
+    tpls = [W.sphere_template(R, rho=m1 / vol), W.sphere_template(R, rho=m2 / vol)]
+    floor = dict(type=W.PLANE, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]))
+    s = make_scene(x, templates=tpls, owner_t=[0, 0, 1], walls=[floor], g=(0, 0, -9.81), h=h,
+                   mat=one_material(E=1e7, nu=0.3, e=0.5, mu=mu), crr=np.array([[crr]]))
+    ow = oracle.OracleWorld(s)
+    assert ow.step(int(round(t_end / h))) == 0
+    return ow.x[2, 2], R
+
+
+@pytest.mark.parametrize("gap_frac,mu,crr", [(0.2, 0.2, 0.05), (0.2, 0.2, 0.03), (0.5, 0.25, 0.05)])
+def test_three_sphere_stack_with_rolling_resistance_follows_its_statics(gap_frac, mu, crr):
+    """Sec. 4.3.2: with rolling resistance the stack carries a top mass up to a critical
+    value that grows with C_r (here mu < tan(theta/2), so friction alone cannot hold it).
+    The run stands at 0.85 of the statics' critical mass and collapses at 1.15 of it."""
+    g = read_golden("stacking_sec4_3_2.txt")
+    R, m1 = g["radius_m"], g["bottom_mass_kg"]
+    assert mu < math.tan(0.5 * math.asin((R + 0.5 * gap_frac * R) / (2 * R)))
+    mc = stack_statics_critical_mass(mu, crr, gap_frac, R, m1)
+    assert mc > stack_statics_critical_mass(mu, 0.5 * crr, gap_frac, R, m1) > 0.0
+    z_lo, _ = stack_run_rolling(mu, crr, gap_frac, 0.85 * mc)
+    z_hi, _ = stack_run_rolling(mu, crr, gap_frac, 1.15 * mc)
+    assert z_lo > 2.0 * R                  # standing
+    assert z_hi < 1.01 * R                 # the top sphere reached the floor
+
+
+def test_rolling_resistance_waits_for_the_collision_time_and_acts_on_torques_only():
+    """The default model of Sec. 4.2.1: no rolling resistance during a contact's first
+    collision time; after it, a force of C_r |F_n| along w_B x r_B - w_A x r_A that enters
+    the torques only (the contact force and the owners' force sums are unchanged)."""
+    R, crr = 1e-3, 0.2
+    x = np.array([[0.0, 0.0, 0.0], [2 * R - 2e-5, 0.0, 0.0]])
+    wb = np.array([[0.0, 0.0, 30.0], [0.0, 0.0, 0.0]])
+    s = make_scene(x, wb=wb, h=1e-7, mat=one_material(e=0.5, mu=0.4), crr=np.array([[crr]]))
+    s0 = make_scene(x, wb=wb, h=1e-7, mat=one_material(e=0.5, mu=0.4))
+    ow, ow0 = oracle.OracleWorld(s), oracle.OracleWorld(s0)
+    F, T, cs = ow.eval()
+    F0, T0, cs0 = ow0.eval()
+    assert len(cs) == 1 and cs["age"][0] == pytest.approx(1e-7)
+    assert np.all(np.array(cs["torque_force"][0]) == 0.0) and np.array_equal(T, T0)
+    # a contact that has lasted a long time: the rolling force is on
+    ow.set_history([0], [1], [[0.0, 0.0, 0.0]], age=[1.0])
+    F, T, cs = ow.eval()
+    fr = np.array(cs["torque_force"][0])
+    fn = abs(np.dot(np.array(cs["force"][0]), np.array(cs["normal"][0])))
+    assert np.linalg.norm(fr) == pytest.approx(crr * fn, rel=1e-9)
+    # along w_B x r_B - w_A x r_A: A spins about +z, its contact point (r_A = +a x) moves
+    # along +y, so the force on A points along -y
+    assert fr[1] / np.linalg.norm(fr) == pytest.approx(-1.0, abs=1e-12)
+    assert np.array_equal(F, F0)
+    arm = np.array(cs["point"][0]) - x[0]
+    assert T[0] - T0[0] == pytest.approx(np.cross(arm, fr), rel=1e-9, abs=1e-18)
+    assert T[1] - T0[1] == pytest.approx(np.cross(np.array(cs["point"][0]) - x[1], -fr), rel=1e-9, abs=1e-18)
+
+
+# ----------------------------------------------------------------------------- family tags
+
+def test_a_fixed_family_holds_still_and_carries_a_sphere_at_the_hertz_overlap():
+    """Sec. 2.2.2: a family prescribed to zero velocity stays put; a sphere resting on a
+    fixed sphere settles to the static Hertz overlap delta = (3 W / (4 E* sqrt(Rbar)))^(2/3)
+    with W = m g and Rbar = R / 2."""
+    R, E, nu = 1e-3, 1e7, 0.3
+    x = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 2 * R]])
+    s = make_scene(x, g=(0, 0, -9.81), h=2e-6, mat=one_material(E=E, nu=nu, e=0.3, mu=0.3),
+                   family=np.array([1, 0]), family_motion={1: ((0, 0, 0), (0, 0, 0))})
+    ow = oracle.OracleWorld(s)
+    assert ow.step(150000) == 0
+    assert np.array_equal(ow.x[0], x[0]) and np.all(ow.v[0] == 0.0)
+    m = ow.mass[1]
+    Es = E / (2 * (1 - nu * nu))
+    want = (3 * m * 9.81 / (4 * Es * math.sqrt(R / 2))) ** (2 / 3)
+    assert (2 * R - (ow.x[1, 2] - ow.x[0, 2])) == pytest.approx(want, rel=1e-6)
+
+
+def test_a_prescribed_velocity_bounces_a_sphere_off_at_twice_its_speed():
+    """A family prescribed to move at V does not respond to forces: an elastic,
+    frictionless head-on hit on a free sphere at rest sends it off at 2 V (the relative
+    motion of an elastic Hertz contact is reversed; the prescribed body is not slowed)."""
+    R = 1e-3
+    V = 0.3
+    x = np.array([[0.0, 0.0, 0.0], [2 * R + 1e-5, 0.0, 0.0]])
+    s = make_scene(x, v=[[V, 0, 0], [0, 0, 0]], h=1e-8, mat=one_material(e=1.0, mu=0.0),
+                   family=np.array([2, 0]), family_motion={2: ((V, 0, 0), None)})
+    ow = oracle.OracleWorld(s)
+    n = 40000
+    assert ow.step(n) == 0
+    assert len(ow.eval()[2]) == 0                       # the contact is over
+    assert ow.v[0, 0] == V
+    assert ow.x[0, 0] == pytest.approx(n * 1e-8 * V, rel=1e-12)
+    assert ow.v[1, 0] == pytest.approx(2 * V, rel=1e-4)
+    assert np.all(np.abs(ow.v[1, 1:]) < 1e-12)
+
+
+def test_a_prescribed_spin_turns_the_owner_at_that_rate():
+    """A family prescribed to spin at w (global frame) turns by h |w| per step about w
+    whatever torque acts, and reads back its body-frame angular velocity R(q)^T w."""
+    R = 1e-3
+    w = np.array([0.0, 3.0, 4.0])
+    s = make_scene([[0.0, 0.0, 0.0]], h=1e-5, family=np.array([5]), family_motion={5: (None, w)})
+    ow = oracle.OracleWorld(s)
+    n = 2000
+    assert ow.step(n) == 0
+    ang = n * 1e-5 * 5.0
+    ax = w / 5.0
+    want = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * ax])
+    assert np.allclose(ow.q[0], want, atol=1e-12)
+    qw, qx, qy, qz = ow.q[0]
+    Rm = np.array([[1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)],
+                   [2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)],
+                   [2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)]])
+    assert np.allclose(Rm @ ow.wb[0], w, atol=1e-12)
+
+
+def test_masked_families_pass_through_each_other():
+    """Sec. 2.2.2: contacts between masked families are not resolved; the same spheres in
+    unmasked families collide."""
+    R = 1e-3
+    x = np.array([[0.0, 0.0, 0.0], [2 * R + 1e-5, 0.0, 0.0]])
+    v = [[0.5, 0, 0], [-0.5, 0, 0]]
+    base = dict(v=v, h=1e-7, mat=one_material(e=0.5, mu=0.3), family=np.array([3, 4]))
+    through = oracle.OracleWorld(make_scene(x, family_masked=[(3, 4)], **base))
+    hit = oracle.OracleWorld(make_scene(x, **base))
+    assert through.step(40000) == 0 and hit.step(40000) == 0
+    assert np.array_equal(through.v, np.array(v, np.float64))
+    assert through.x[0, 0] > through.x[1, 0]           # they have crossed
+    assert hit.v[0, 0] < 0 and hit.v[1, 0] > 0          # they bounced
+
+
+def test_contacts_among_fixed_owners_change_nothing():
+    """The active-box reading (Sec. 6.4): owners outside the box are fixed and their
+    mutual contacts are not resolved.  Contacts between two fixed owners move nothing, so
+    masking them leaves every trajectory bit-identical."""
+    sc = W.dense_lattice(n=600, seed=31, vel_sigma=0.3)
+    z = np.asarray(sc.x)[:, 2]
+    fam = np.where(z < np.median(z), 1, 0).astype(np.uint8)
+    fixed = {1: ((0, 0, 0), (0, 0, 0))}
+    a = oracle.OracleWorld(dataclasses.replace(sc, family=fam, family_motion=fixed, family_masked=[(1, 1)]))
+    b = oracle.OracleWorld(dataclasses.replace(sc, family=fam, family_motion=fixed))
+    assert a.step(200) == 0 and b.step(200) == 0
+    for f in ("x", "v", "wb", "q"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    assert len(a.eval()[2]) < len(b.eval()[2])          # fewer contacts resolved
+    moved = np.any(a.x != np.asarray(sc.x), axis=1)
+    assert not np.any(moved[fam == 1]) and np.any(moved[fam == 0])
