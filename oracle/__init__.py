@@ -65,7 +65,11 @@ class _World(C.Structure):
                 ("h", C.c_double), ("g", C.c_double * 3), ("gyroscopic", C.c_int32), ("has_sink", C.c_int32),
                 ("sink_p", C.c_double * 3), ("sink_n", C.c_double * 3), ("v_err", C.c_double),
                 ("hist", C.c_void_p), ("cell_list", C.c_int32), ("n_threads", C.c_int32), ("crr", C.c_void_p),
-                ("family", C.c_void_p), ("contact_mask", C.c_void_p), ("motion", C.c_void_p)]
+                ("family", C.c_void_p), ("contact_mask", C.c_void_p), ("motion", C.c_void_p),
+                ("model", C.c_int32), ("model_params", C.c_void_p)]
+
+MODEL_HERTZ_MINDLIN, MODEL_BONDED_BREAKAGE = 0, 1
+BREAKAGE_PARAMS = ("tension", "cohesion", "eta", "damping")
 
 
 class FamilyMotion(C.Structure):
@@ -75,7 +79,7 @@ class FamilyMotion(C.Structure):
 class Contact(C.Structure):
     _fields_ = [("i", C.c_int64), ("j", C.c_int64), ("force", C.c_double * 3), ("point", C.c_double * 3),
                 ("normal", C.c_double * 3), ("overlap", C.c_double), ("ut", C.c_double * 3), ("age", C.c_double),
-                ("torque_force", C.c_double * 3)]
+                ("torque_force", C.c_double * 3), ("wc", C.c_double * 4)]
 
 
 def lib():
@@ -100,6 +104,8 @@ def lib():
             L.orc_step.argtypes = [P, C.c_int64]
             L.orc_diagnostics.argtypes = [P, P, P, P, P, P]
             L.orc_effective_moduli.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, P, P]
+            L.orc_history_set_wildcards.argtypes = [P, C.c_int64, P, P, P]
+            L.orc_history_get_wildcards.argtypes = [P, C.c_int64, P, P]
             L.orc_max_threads.restype = C.c_int
             L.orc_max_threads.argtypes = []
     return _LIB
@@ -257,6 +263,15 @@ class OracleWorld:
                     fm.fix_w = 1
                     for a in range(3):
                         fm.w[a] = float(om[a])
+        model = getattr(s, "force_model", None)
+        self.model_params = None
+        if model == "bonded_breakage":
+            w.model = MODEL_BONDED_BREAKAGE
+            par = s.model_params
+            self.model_params = np.array([float(par[k]) for k in BREAKAGE_PARAMS], np.float64)
+            w.model_params = _ptr(self.model_params)
+        elif model not in (None, "hertz_mindlin"):
+            raise ValueError(f"unknown force model {model!r}")
         w.family = _ptr(self.family)
         w.contact_mask = _ptr(self.contact_mask)
         w.motion = C.cast(self.motion, C.c_void_p) if self.motion is not None else None
@@ -349,6 +364,21 @@ class OracleWorld:
         age = None if age is None else np.ascontiguousarray(age, np.float64).reshape(-1)
         rc = lib().orc_history_set(self._w.hist, len(i), _ptr(i), _ptr(j), _ptr(ut), _ptr(age))
         assert rc == 0
+
+    def set_wildcards(self, i, j, wc):
+        """Model wildcards wc[n, 4] of the contacts (i, j) (bonded breakage: bond state,
+        bond length); entries not in the history are added with zero history."""
+        i = np.ascontiguousarray(i, np.int64)
+        j = np.ascontiguousarray(j, np.int64)
+        wc = np.ascontiguousarray(wc, np.float64).reshape(-1, 4)
+        assert lib().orc_history_set_wildcards(self._w.hist, len(i), _ptr(i), _ptr(j), _ptr(wc)) == 0
+
+    def wildcards(self):
+        n = lib().orc_history_size(self._w.hist)
+        wc = np.empty((max(n, 1), 4))
+        cnt = C.c_int64()
+        assert lib().orc_history_get_wildcards(self._w.hist, max(n, 1), C.byref(cnt), _ptr(wc)) == 0
+        return wc[:n].copy()
 
     def diagnostics(self):
         ke, pe, el = C.c_double(), C.c_double(), C.c_double()

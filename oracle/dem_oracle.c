@@ -100,6 +100,7 @@ typedef struct {
     int64_t *i, *j;      /* j >= 0 sphere, j < 0 wall -1-j */
     double *ut;          /* 3 per entry */
     double *age;         /* time in contact, 1 per entry */
+    double *wc;          /* further model wildcards, 4 per entry */
 } orc_hist;
 
 /* Sort key of the partner: spheres first by id, then walls by wall id. */
@@ -121,7 +122,7 @@ void orc_history_free(void *hp)
 {
     orc_hist *h = (orc_hist *)hp;
     if (!h) return;
-    free(h->i); free(h->j); free(h->ut); free(h->age); free(h);
+    free(h->i); free(h->j); free(h->ut); free(h->age); free(h->wc); free(h);
 }
 
 int64_t orc_history_size(const void *hp) { return hp ? ((const orc_hist *)hp)->n : 0; }
@@ -143,6 +144,9 @@ static int hist_reserve(orc_hist *h, int64_t n)
     double *na = (double *)realloc(h->age, (size_t)c * sizeof(double));
     if (!na) return ORC_ERR_NOMEM;
     h->age = na;
+    double *nw = (double *)realloc(h->wc, (size_t)c * 4 * sizeof(double));
+    if (!nw) return ORC_ERR_NOMEM;
+    h->wc = nw;
     h->cap = c;
     return 0;
 }
@@ -184,9 +188,66 @@ int orc_history_set(void *hp, int64_t n, const int64_t *i, const int64_t *j, con
         h->i[k] = r[k].i; h->j[k] = r[k].j;
         memcpy(&h->ut[3 * k], &ut[3 * r[k].k], 3 * sizeof(double));
         h->age[k] = age ? age[r[k].k] : 0.0;
+        h->wc[4 * k] = h->wc[4 * k + 1] = h->wc[4 * k + 2] = h->wc[4 * k + 3] = 0.0;
     }
     h->n = n;
     free(r);
+    return 0;
+}
+
+int orc_history_set_wildcards(void *hp, int64_t n, const int64_t *i, const int64_t *j, const double *wc)
+{
+    orc_hist *h = (orc_hist *)hp;
+    if (!h || n < 0) return ORC_ERR_ARG;
+    /* entries not present are added with zero history, then the whole set re-sorted */
+    int64_t n0 = h->n, add = 0;
+    for (int64_t k = 0; k < n; ++k)
+        if (hist_find(h, i[k], j[k]) < 0) ++add;
+    if (add) {
+        int64_t tot = n0 + add;
+        int64_t *ni = (int64_t *)malloc((size_t)tot * sizeof(int64_t));
+        int64_t *nj = (int64_t *)malloc((size_t)tot * sizeof(int64_t));
+        double *nu = (double *)malloc((size_t)tot * 3 * sizeof(double));
+        double *na = (double *)malloc((size_t)tot * sizeof(double));
+        double *nw = (double *)malloc((size_t)tot * 4 * sizeof(double));
+        if (!ni || !nj || !nu || !na || !nw) { free(ni); free(nj); free(nu); free(na); free(nw); return ORC_ERR_NOMEM; }
+        memcpy(ni, h->i, (size_t)n0 * sizeof(int64_t));
+        memcpy(nj, h->j, (size_t)n0 * sizeof(int64_t));
+        memcpy(nu, h->ut, (size_t)n0 * 3 * sizeof(double));
+        memcpy(na, h->age, (size_t)n0 * sizeof(double));
+        memcpy(nw, h->wc, (size_t)n0 * 4 * sizeof(double));
+        int64_t m = n0;
+        for (int64_t k = 0; k < n; ++k) {
+            if (hist_find(h, i[k], j[k]) >= 0) continue;
+            ni[m] = i[k]; nj[m] = j[k];
+            nu[3 * m] = nu[3 * m + 1] = nu[3 * m + 2] = 0.0;
+            na[m] = 0.0;
+            nw[4 * m] = nw[4 * m + 1] = nw[4 * m + 2] = nw[4 * m + 3] = 0.0;
+            ++m;
+        }
+        int e = orc_history_set(h, tot, ni, nj, nu, na);
+        /* orc_history_set cleared the wildcards: put the kept ones back */
+        for (int64_t k = 0; k < tot && !e; ++k) {
+            int64_t q = hist_find(h, ni[k], nj[k]);
+            memcpy(&h->wc[4 * q], &nw[4 * k], 4 * sizeof(double));
+        }
+        free(ni); free(nj); free(nu); free(na); free(nw);
+        if (e) return e;
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t q = hist_find(h, i[k], j[k]);
+        memcpy(&h->wc[4 * q], &wc[4 * k], 4 * sizeof(double));
+    }
+    return 0;
+}
+
+int orc_history_get_wildcards(const void *hp, int64_t cap, int64_t *n, double *wc)
+{
+    const orc_hist *h = (const orc_hist *)hp;
+    if (!h) return ORC_ERR_ARG;
+    *n = h->n;
+    if (h->n > cap) return ORC_ERR_CAPACITY;
+    memcpy(wc, h->wc, (size_t)h->n * 4 * sizeof(double));
     return 0;
 }
 
@@ -381,6 +442,8 @@ typedef struct {
     double rotB[3];    /* ... of uB (for a wall its whole surface velocity) */
     double Rbar, mbar;
     double Estar, Gstar, beta, mu, crr;
+    double RA, RB;     /* radii of the two geometries (a wall: 0) */
+    double nu;         /* mean of the two materials' Poisson ratios */
 } contact_in;
 
 /* Whether a contact that has lasted `age` is still inside its first collision: the
@@ -467,6 +530,70 @@ static void hertz_mindlin(const contact_in *ci, double h, double ut[3], double *
     }
 }
 
+/* The bonded, breakable contact of Sec. 6.3 (the paper's worked custom model, after the
+ * constitutive laws it cites), for a bonded pair (wc[0] > 1e-12; wc[1] is the overlap at
+ * which the bond carries no load).  The readings of the partial listing are those of the
+ * equations printed beside it:
+ *   D = delta - wc[1], k_n = E* Rbar, area A = pi max(R_A, R_B)^2, bond strength
+ *   F_b = sigma_t A (sigma_t < 0: tension), D_y = F_b / k_n, D_u = 3 D_y;
+ *   normal force k_n D above D_y, softening linearly to zero at D_u below it (the
+ *   printed equation's slope -k_n / xi with xi = 2, continuous at D_y), damped by
+ *   0.01 sqrt(mbar k_n) times the normal relative velocity; the bond breaks
+ *   (wc[0] = -1) once D < D_u;
+ *   tangential: the history update of the default model, k_t = nu k_n (nu the mean of
+ *   the two materials'), damping g_t = -2 sqrt(5/6) beta sqrt(mbar k_t) opposing sliding
+ *   as in the default model, F_t = -k_t ut - g_t v_t; the bond breaks once |F_t|
+ *   exceeds mu |F| + c A (c the cohesion; c A only while D > D_y);
+ *   bending: a torque-only force of magnitude min(h R_A R_B k_t / R_A, eta |F|) along the
+ *   rolling part of B's contact-point velocity relative to A's (as rolling resistance).
+ * A is the lower sphere id (the bending term is not symmetric in A and B). */
+static void bonded_breakage(const contact_in *ci, const double *par, double h, double ut[3], double *age,
+                            double wc[4], double F[3], double Fr[3])
+{
+    const double *n = ci->n;
+    double u[3] = {ci->uA[0] - ci->uB[0], ci->uA[1] - ci->uB[1], ci->uA[2] - ci->uB[2]};
+    double proj = dot3(u, n);
+    double vt[3] = {u[0] - proj * n[0], u[1] - proj * n[1], u[2] - proj * n[2]};
+    ut[0] = ut[0] + h * vt[0];
+    ut[1] = ut[1] + h * vt[1];
+    ut[2] = ut[2] + h * vt[2];
+    double up = dot3(ut, n);
+    ut[0] = ut[0] - up * n[0];
+    ut[1] = ut[1] - up * n[1];
+    ut[2] = ut[2] - up * n[2];
+    *age = *age + h;
+
+    double D = ci->delta - wc[1];
+    double kn = ci->Estar * ci->Rbar;
+    double Rm = ci->RA > ci->RB ? ci->RA : ci->RB;
+    double area = ORC_PI * (Rm * Rm);
+    double Dy = (par[ORC_BRK_TENSION] * area) / kn;
+    double Du = 3.0 * Dy;
+    double fn = D > Dy ? kn * D : 0.5 * kn * (Du - D);
+    double gn = par[ORC_BRK_DAMPING] * sqrt(ci->mbar * kn);
+    double fnd = fn - gn * proj;
+    F[0] = fnd * n[0]; F[1] = fnd * n[1]; F[2] = fnd * n[2];
+    if (D < Du) wc[0] = -1.0;
+
+    double kt = ci->nu * kn;
+    double c56 = sqrt(5.0 / 6.0);
+    double gt = -2.0 * c56 * ci->beta * sqrt(ci->mbar * kt);
+    double fs_max = norm3(F) * ci->mu + (D > Dy ? par[ORC_BRK_COHESION] * area : 0.0);
+    double Ft[3] = {-kt * ut[0] - gt * vt[0], -kt * ut[1] - gt * vt[1], -kt * ut[2] - gt * vt[2]};
+    if (norm3(Ft) > fs_max) wc[0] = -1.0;
+    F[0] = F[0] + Ft[0]; F[1] = F[1] + Ft[1]; F[2] = F[2] + Ft[2];
+
+    Fr[0] = 0.0; Fr[1] = 0.0; Fr[2] = 0.0;
+    double vr[3] = {ci->rotB[0] - ci->rotA[0], ci->rotB[1] - ci->rotA[1], ci->rotB[2] - ci->rotA[2]};
+    double vm = norm3(vr);
+    if (vm > 1e-12) {
+        double kr = (ci->RA * ci->RB) * kt;
+        double m1 = (h * kr) / ci->RA, m2 = par[ORC_BRK_ETA] * norm3(F);
+        double sc = (m1 < m2 ? m1 : m2) / vm;
+        Fr[0] = sc * vr[0]; Fr[1] = sc * vr[1]; Fr[2] = sc * vr[2];
+    }
+}
+
 /* Velocity of a point `c` carried by owner o: v + (R(q) wb) x (c - x); rot receives
  * the rotational part (R(q) wb) x (c - x). */
 static void owner_point_velocity(const orc_world *w, int64_t o, const double c[3], double out[3], double rot[3])
@@ -488,16 +615,19 @@ static void contact_material(const orc_world *w, int32_t ma, int32_t mb, contact
     ci->beta = damping_beta(w->cor[ma * w->n_mat + mb]);
     ci->mu = w->mu[ma * w->n_mat + mb];
     ci->crr = w->crr ? w->crr[ma * w->n_mat + mb] : 0.0;
+    ci->nu = 0.5 * (w->nu[ma] + w->nu[mb]);
 }
 
-/* Geometry of the sphere pair (A = i, B = j).  Returns 1 if delta > 0. */
-static int sphere_pair_contact(const orc_world *w, const double *p, int64_t i, int64_t j, contact_in *ci)
+/* Geometry of the sphere pair (A = i, B = j) whatever the sign of the overlap (a bonded
+ * contact acts in tension too).  Returns 0 only where the centres coincide. */
+static int sphere_pair_geometry(const orc_world *w, const double *p, int64_t i, int64_t j, contact_in *ci)
 {
     double dx[3] = {p[3 * i + 0] - p[3 * j + 0], p[3 * i + 1] - p[3 * j + 1], p[3 * i + 2] - p[3 * j + 2]};
     double d = sqrt((dx[0] * dx[0] + dx[1] * dx[1]) + dx[2] * dx[2]);
     double RA = w->rad[i], RB = w->rad[j];
     double delta = (RA + RB) - d;
-    if (!(delta > 0.0) || !(d > 0.0)) return 0;
+    if (!(d > 0.0)) return 0;
+    ci->RA = RA; ci->RB = RB;
     double inv = 1.0 / d;
     ci->n[0] = dx[0] * inv; ci->n[1] = dx[1] * inv; ci->n[2] = dx[2] * inv;
     ci->delta = delta;
@@ -513,6 +643,12 @@ static int sphere_pair_contact(const orc_world *w, const double *p, int64_t i, i
     ci->mbar = (w->mass[oa] * w->mass[ob]) / (w->mass[oa] + w->mass[ob]);
     contact_material(w, w->mat[i], w->mat[j], ci);
     return 1;
+}
+
+/* The same where the spheres touch: returns 1 iff delta > 0. */
+static int sphere_pair_contact(const orc_world *w, const double *p, int64_t i, int64_t j, contact_in *ci)
+{
+    return sphere_pair_geometry(w, p, i, j, ci) && ci->delta > 0.0;
 }
 
 /* Geometry of sphere i against wall k (A = sphere, B = wall: infinite radius and mass). */
@@ -537,6 +673,7 @@ static int sphere_wall_contact(const orc_world *w, const double *p, int64_t i, i
     memcpy(ci->rotB, ci->uB, sizeof(ci->uB));   /* a wall moves by rotation only */
     ci->Rbar = RA;
     ci->mbar = w->mass[oa];
+    ci->RA = RA; ci->RB = 0.0;
     contact_material(w, w->mat[i], wl->mat, ci);
     return 1;
 }
@@ -569,11 +706,17 @@ static int contact_of(const orc_world *w, const double *p, const orc_hist *h, in
     int64_t oa = w->owner[i];
     contact_in ci;
     int64_t j;
+    int bonded = 0;
     if (jj < N) {
         j = jj;
         int64_t ob = w->owner[j];
         if (ob == oa || !owner_is_active(w, ob) || !families_meet(w, oa, ob)) return 0;
-        if (!sphere_pair_contact(w, p, i, j, &ci)) return 0;
+        if (w->model == ORC_MODEL_BONDED_BREAKAGE) {
+            /* a bonded pair acts whatever the sign of its overlap */
+            int64_t hb = h ? hist_find(h, i, j) : -1;
+            bonded = hb >= 0 && h->wc[4 * hb] > 1e-12;
+        }
+        if (bonded ? !sphere_pair_geometry(w, p, i, j, &ci) : !sphere_pair_contact(w, p, i, j, &ci)) return 0;
     } else {
         int32_t k = (int32_t)(jj - N);
         j = -1 - (int64_t)k;
@@ -585,8 +728,12 @@ static int contact_of(const orc_world *w, const double *p, const orc_hist *h, in
     if (hk >= 0) {
         rec->ut[0] = h->ut[3 * hk]; rec->ut[1] = h->ut[3 * hk + 1]; rec->ut[2] = h->ut[3 * hk + 2];
         rec->age = h->age[hk];
+        memcpy(rec->wc, &h->wc[4 * hk], sizeof(rec->wc));
     }
-    hertz_mindlin(&ci, w->h, rec->ut, &rec->age, rec->force, rec->torque_force);
+    if (bonded)
+        bonded_breakage(&ci, w->model_params, w->h, rec->ut, &rec->age, rec->wc, rec->force, rec->torque_force);
+    else
+        hertz_mindlin(&ci, w->h, rec->ut, &rec->age, rec->force, rec->torque_force);
     memcpy(rec->point, ci.c, sizeof(ci.c));
     memcpy(rec->normal, ci.n, sizeof(ci.n));
     rec->overlap = ci.delta;
@@ -780,7 +927,9 @@ static int evaluate(const orc_world *w, const double *p, double *F, double *T, c
     grid_ent *ge = NULL;
     int64_t ng = 0, *home = NULL, *start = NULL, dims[3] = {0, 0, 0};
     int use_grid = 0;
-    if (w->cell_list) {
+    /* the grid finds pairs that can touch; a bond also acts across a gap, so the bonded
+     * model takes the plain loop */
+    if (w->cell_list && w->model == ORC_MODEL_HERTZ_MINDLIN) {
         use_grid = grid_build(w, p, &ge, &ng, &home);
         if (use_grid < 0) return use_grid;
         if (use_grid) start = grid_starts(ge, ng, dims);
@@ -917,6 +1066,7 @@ static int replace_history(orc_world *w, const contact_buf *b)
         h->i[k] = b->c[k].i; h->j[k] = b->c[k].j;
         h->ut[3 * k] = b->c[k].ut[0]; h->ut[3 * k + 1] = b->c[k].ut[1]; h->ut[3 * k + 2] = b->c[k].ut[2];
         h->age[k] = b->c[k].age;
+        memcpy(&h->wc[4 * k], b->c[k].wc, 4 * sizeof(double));
     }
     h->n = b->n;
     return 0;

@@ -20,6 +20,8 @@
  *   - per-owner force/torque sums (Eqs. 5a-5b);
  *   - family tags (Sec. 2.2.2): prescribed linear / angular velocities per family and
  *     contact masks between families;
+ *   - a second contact model, the bonded breakable contact of Sec. 6.3 (the paper's
+ *     worked custom model), see orc_world.model;
  *   - a semi-implicit Euler step of velocity, body-frame angular velocity (with the
  *     gyroscopic term, switchable), position and quaternion.  The paper does not state
  *     the integrator; this is the reading adopted for the whole project.
@@ -38,6 +40,11 @@ extern "C" {
 #endif
 
 enum { ORC_WALL_PLANE = 0, ORC_WALL_CYLINDER = 1, ORC_WALL_CONE = 2 };
+/* contact force models (Sec. 4.2: the default model; Sec. 6.3: a bonded, breakable
+ * contact for brittle solids, the paper's worked example of a custom model) */
+enum { ORC_MODEL_HERTZ_MINDLIN = 0, ORC_MODEL_BONDED_BREAKAGE = 1 };
+/* parameters of ORC_MODEL_BONDED_BREAKAGE (model_params[k]) */
+enum { ORC_BRK_TENSION = 0, ORC_BRK_COHESION = 1, ORC_BRK_ETA = 2, ORC_BRK_DAMPING = 3, ORC_BRK_NPARAM = 4 };
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_CAPACITY = -2, ORC_ERR_DIVERGED = -3, ORC_ERR_NOMEM = -4 };
 
 /* One analytical wall.  All walls move rigidly with angular velocity `omega` about the
@@ -104,6 +111,9 @@ typedef struct {
     const uint8_t *family;
     const uint8_t *contact_mask;
     const orc_family_motion *motion;
+    /* contact force model (ORC_MODEL_*) and its parameters (NULL for the default) */
+    int32_t model;
+    const double *model_params;
 } orc_world;
 
 /* One resolved contact.  j >= 0 is a sphere, j < 0 is wall (-1 - j).  force acts on
@@ -119,6 +129,8 @@ typedef struct {
                                        delta_time wildcard of Sec. 4.2.1)                 */
     double torque_force[3];         /* rolling resistance: a force on i (-it on j) that
                                        acts through the contact torque only (Sec. 4.1) */
+    double wc[4];                   /* the model's further contact wildcards after this
+                                       step (bonded breakage: bond state, bond length)    */
 } orc_contact;
 
 void *orc_history_new(void);
@@ -128,6 +140,10 @@ int64_t orc_history_size(const void *h);
  * age NULL: zero.  Entries need not be sorted.  get: age may be NULL. */
 int orc_history_set(void *h, int64_t n, const int64_t *i, const int64_t *j, const double *ut, const double *age);
 int orc_history_get(const void *h, int64_t cap, int64_t *n, int64_t *i, int64_t *j, double *ut, double *age);
+/* The further wildcards wc[4n] of the entries (i, j) (model wildcards; entries that are
+ * not in the history are added with zero ut and age).  get: wc[4 * count]. */
+int orc_history_set_wildcards(void *h, int64_t n, const int64_t *i, const int64_t *j, const double *wc);
+int orc_history_get_wildcards(const void *h, int64_t cap, int64_t *n, double *wc);
 
 /* Sphere centres in the global frame: p_s = x_o + R(q_o) rloc_s. */
 int orc_sphere_positions(const orc_world *w, double *p);

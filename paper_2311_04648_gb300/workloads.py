@@ -67,6 +67,8 @@ class Scene:
     family: np.ndarray | None = None  # (M,) family tag per owner (0..255); None: all 0
     family_motion: dict | None = None  # family -> (v or None, w or None): prescribed velocities
     family_masked: list | None = None  # (a, b) family pairs whose contacts are not resolved
+    force_model: str | None = None     # None / "hertz_mindlin" or "bonded_breakage"
+    model_params: dict | None = None   # bonded_breakage: tension, cohesion, eta, damping
 
     @property
     def n_owner(self):

@@ -999,3 +999,113 @@ def test_contacts_among_fixed_owners_change_nothing():
     assert len(a.eval()[2]) < len(b.eval()[2])          # fewer contacts resolved
     moved = np.any(a.x != np.asarray(sc.x), axis=1)
     assert not np.any(moved[fam == 1]) and np.any(moved[fam == 0])
+
+
+# ----------------------------------------------------------------------------- bonded breakage
+
+BRK = dict(tension=-1e5, cohesion=2e5, eta=0.1, damping=0.01)
+
+
+def bonded_pair_run(v_b, steps, R=1e-3, E=1e7, nu=0.3, mu=0.4, h=1e-6, sample=50, params=BRK):
+    """Two touching spheres bonded at zero load (Sec. 6.3 model): A held fixed, B moved
+    at the prescribed velocity v_b; returns per sample the centre distance, the contact
+    force on A and whether the pair still interacts."""
+    x = np.array([[0.0, 0.0, 0.0], [2 * R, 0.0, 0.0]])
+    s = make_scene(x, h=h, mat=one_material(E=E, nu=nu, e=0.5, mu=mu), family=np.array([1, 2]),
+                   family_motion={1: ((0, 0, 0), (0, 0, 0)), 2: (v_b, (0, 0, 0))},
+                   force_model="bonded_breakage", model_params=params)
+    ow = oracle.OracleWorld(s)
+    ow.set_wildcards([0], [1], [[1.0, 0.0, 0.0, 0.0]])
+    out = []
+    for k in range(steps // sample):
+        assert ow.step(sample) == 0
+        F, T, cs = ow.eval()
+        d = float(np.linalg.norm(ow.x[1] - ow.x[0]))
+        if len(cs):
+            out.append((d, np.array(cs["force"][0]), float(cs["wc"][0][0])))
+        else:
+            out.append((d, np.zeros(3), 0.0))
+    return out, ow
+
+
+def test_bonded_contact_in_tension_peaks_at_its_strength_and_breaks_at_three_times_yield():
+    """Sec. 6.3 (Eq. of k_n): a bond pulled apart carries k_n D up to its strength
+    F_b = sigma_t A (A = pi R^2, k_n = E* Rbar), softens linearly to zero at three times
+    the yield separation D_y = F_b / k_n, and breaks there."""
+    R, E, nu = 1e-3, 1e7, 0.3
+    V = 0.01
+    out, ow = bonded_pair_run((V, 0, 0), 40000, R=R, E=E, nu=nu)
+    Es = E / (2 * (1 - nu * nu))
+    kn = Es * R / 2
+    Fb = BRK["tension"] * math.pi * R * R
+    Dy = Fb / kn
+    sep = np.array([d - 2 * R for d, _, _ in out])
+    fx = np.array([f[0] for _, f, _ in out])             # pull on A towards B (+x)
+    damp = BRK["damping"] * math.sqrt(0.5 * ow.mass[0] * kn) * V
+    alive = fx > 0
+    assert fx.max() == pytest.approx(-Fb + damp, rel=2e-3)
+    k_peak = int(np.argmax(fx))
+    assert sep[k_peak] == pytest.approx(-Dy, rel=2e-2)
+    # halfway down the softening branch at twice the yield separation
+    mid = int(np.argmin(np.abs(sep - 2 * (-Dy))))
+    assert fx[mid] == pytest.approx(-0.5 * Fb + damp, rel=2e-2)
+    # the bond is gone once the separation passes 3 D_y, and nothing pulls afterwards
+    last_alive = int(np.flatnonzero(alive)[-1])
+    step_sep = V * 1e-6 * 50
+    assert sep[last_alive] <= 3 * (-Dy) + step_sep and sep[last_alive + 1] >= 3 * (-Dy) - step_sep
+    assert np.all(fx[last_alive + 1:] == 0.0)
+
+
+def test_bonded_contact_in_shear_breaks_at_its_cohesion():
+    """Sec. 6.3: the tangential spring k_t = nu k_n carries the shear until it exceeds
+    mu |F| + c A (c the cohesion).  Sheared sideways by u at speed V, the pair's centre
+    distance grows to sqrt(4 R^2 + u^2), so the bond also carries a tension
+    k_n (sqrt(4 R^2 + u^2) - 2 R); it breaks where k_t u + g_t V (the spring plus its
+    damping) first exceeds mu times that tension plus c A."""
+    R, E, nu = 1e-3, 1e7, 0.3
+    V = 0.01
+    par = dict(BRK, cohesion=2e4)          # breaks in shear long before the normal gap matters
+    out, ow = bonded_pair_run((0, V, 0), 12000, R=R, E=E, nu=nu, sample=10, params=par)
+    kn = E / (2 * (1 - nu * nu)) * R / 2
+    kt = nu * kn
+    m = ow.mass[0]
+    beta = math.log(0.5) / math.sqrt(math.log(0.5) ** 2 + math.pi ** 2)
+    gt = -2 * math.sqrt(5 / 6) * beta * math.sqrt(0.5 * m * kt)
+    cA = par["cohesion"] * math.pi * R * R
+
+    def excess(u):
+        return kt * u + gt * V - (0.4 * kn * (math.sqrt(4 * R * R + u * u) - 2 * R) + cA)
+    lo, hi = 0.0, 1e-3
+    for _ in range(100):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (lo, mid) if excess(mid) > 0 else (mid, hi)
+    u_break = hi
+    state = np.array([st for _, _, st in out])
+    k = int(np.flatnonzero(state <= 0.0)[0])            # first sample without the bond
+    assert k * 10 * 1e-6 * V <= u_break <= (k + 1) * 10 * 1e-6 * V + 1e-12
+    # the tangential part of the force just before the break: the spring and its damping
+    u = k * 10 * 1e-6 * V
+    n = np.array([-2 * R, -u, 0.0]) / math.sqrt(4 * R * R + u * u)
+    f = out[k - 1][1]
+    ft = np.linalg.norm(f - np.dot(f, n) * n)
+    assert ft == pytest.approx(kt * (u + 1e-6 * V) + gt * V, rel=1e-3)
+
+
+def test_bonded_cluster_conserves_linear_momentum():
+    """Action and reaction: a free cluster of bonded spheres of unequal radii (no walls, no
+    gravity) keeps its total linear momentum to rounding while bonds stretch and break."""
+    rng = np.random.default_rng(5)
+    R = 1e-3
+    x = np.array([[0.0, 0.0, 0.0], [1.95 * R, 0.0, 0.0], [0.9 * R, 1.7 * R, 0.0], [0.9 * R, 0.6 * R, 1.6 * R]])
+    v = rng.normal(scale=0.2, size=(4, 3))
+    scale = np.array([1.0, 0.9, 1.1, 0.95])
+    s = make_scene(x, v=v, scale=scale, h=1e-6, mat=one_material(e=0.5, mu=0.4),
+                   force_model="bonded_breakage", model_params=BRK)
+    ow = oracle.OracleWorld(s)
+    pairs = [(0, 1), (0, 2), (1, 2), (0, 3), (1, 3), (2, 3)]
+    ow.set_wildcards([a for a, _ in pairs], [b for _, b in pairs], [[1.0, 0.0, 0.0, 0.0]] * len(pairs))
+    p0 = (ow.mass[:, None] * ow.v).sum(axis=0)
+    assert ow.step(3000) == 0
+    p1 = (ow.mass[:, None] * ow.v).sum(axis=0)
+    scale_p = (ow.mass[:, None] * np.abs(v)).sum()
+    assert np.all(np.abs(p1 - p0) <= 1e-12 * scale_p)
