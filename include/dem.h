@@ -318,6 +318,38 @@ dem_status dem_set_history(dem_world *w, int64_t k, const int64_t *i, const int6
  * history the rolling-resistance gate of Sec. 4.2.1 reads. */
 dem_status dem_set_history_age(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *ut,
                                const double *age);
+/* ---------------------------------------------------------------- contact force models */
+
+/* Contact force models (Sec. 4.2: a custom model replaces the default one; Sec. 6.3 its
+ * worked example).  Each model is a device functor compiled into its own build of the
+ * contact kernel (no just-in-time compilation): it reads the per-contact referable
+ * variables (normal, overlap, contact arms, velocities, masses, radii, material pair
+ * constants, families, time step), keeps up to 8 contact wildcards (zero when a contact
+ * appears, dropped when it vanishes) and gives the force on A and a torque-only force.
+ * Every sphere pair is evaluated with A the lower sphere id, so a model need not be
+ * symmetric in A and B.  Walls always take the default model.
+ *   DEM_MODEL_DEFAULT          the built-in default model (the fastest path)
+ *   DEM_MODEL_HERTZ_MINDLIN    the same default model through the functor interface
+ *                              (no parameters; gives the built-in results)
+ *   DEM_MODEL_BONDED_BREAKAGE  the bonded, breakable contact of Sec. 6.3, 4 parameters:
+ *                              tensile strength sigma_t (Pa, negative), cohesion c (Pa),
+ *                              bending coefficient eta, normal damping factor (0.01 in
+ *                              the paper); wildcards 4 and 5 are the bond state (> 0
+ *                              bonded, -1 broken) and the bond's unloaded overlap.  A bond
+ *                              acts across a gap while its pair stays listed: give the
+ *                              margin room for the separation at which it fails. */
+typedef enum { DEM_MODEL_DEFAULT = 0, DEM_MODEL_HERTZ_MINDLIN = 1, DEM_MODEL_BONDED_BREAKAGE = 2 } dem_model;
+/* Before dem_initialize.  params[n_params] as listed above. */
+dem_status dem_set_force_model(dem_world *w, int32_t model, const double *params, int32_t n_params);
+/* Contact wildcards 4..7 of the listed sphere pairs (i, j), wc[4k], in the orientation
+ * of the lower sphere id (e.g. bonding pairs at the start of a run).  Pairs not in the
+ * list in use are ignored.  DEM_ERR_STATE where the model has no such wildcards. */
+dem_status dem_set_contact_wildcards(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *wc);
+/* The model's 8 wildcards of each contact after this step's update, wc[8 count], in the
+ * order and count of dem_get_contacts (which, in a model world, reports every pair the
+ * model engages: a bond across a gap has a negative overlap). */
+dem_status dem_get_contact_wildcards(dem_world *w, int64_t cap, int64_t *count, double *wc);
+
 /* ---------------------------------------------------------------- family tags */
 
 /* Family tags (Sec. 2.2.2): every owner carries a family in [0, 255] (0 by default).

@@ -29,7 +29,7 @@ _LIB_PATH = os.path.join(_BUILD, "libdem_oracle.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-WALL_PLANE, WALL_CYLINDER, WALL_CONE = 0, 1, 2
+WALL_PLANE, WALL_CYLINDER, WALL_CONE, WALL_TRIANGLE = 0, 1, 2, 3
 ERR_CAPACITY, ERR_DIVERGED = -2, -3
 
 
@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
 class Wall(C.Structure):
     _fields_ = [("type", C.c_int32), ("mat", C.c_int32), ("p", C.c_double * 3), ("n", C.c_double * 3),
                 ("r0", C.c_double), ("z0", C.c_double), ("r1", C.c_double), ("z1", C.c_double),
-                ("omega", C.c_double * 3)]
+                ("omega", C.c_double * 3), ("tri", C.c_double * 9)]
 
 
 class _World(C.Structure):
@@ -66,7 +66,7 @@ class _World(C.Structure):
                 ("sink_p", C.c_double * 3), ("sink_n", C.c_double * 3), ("v_err", C.c_double),
                 ("hist", C.c_void_p), ("cell_list", C.c_int32), ("n_threads", C.c_int32), ("crr", C.c_void_p),
                 ("family", C.c_void_p), ("contact_mask", C.c_void_p), ("motion", C.c_void_p),
-                ("model", C.c_int32), ("model_params", C.c_void_p)]
+                ("model", C.c_int32), ("model_params", C.c_void_p), ("step", C.c_int64)]
 
 MODEL_HERTZ_MINDLIN, MODEL_BONDED_BREAKAGE = 0, 1
 BREAKAGE_PARAMS = ("tension", "cohesion", "eta", "damping")
@@ -192,6 +192,9 @@ class OracleWorld:
                 W.p[a] = float(wd["p"][a]); W.n[a] = float(wd["n"][a]); W.omega[a] = float(wd.get("omega", (0, 0, 0))[a])
             W.r0 = float(wd.get("r0", 0.0)); W.z0 = float(wd.get("z0", 0.0))
             W.r1 = float(wd.get("r1", 0.0)); W.z1 = float(wd.get("z1", 0.0))
+            if "tri" in wd:
+                for a in range(9):
+                    W.tri[a] = float(np.asarray(wd["tri"], np.float64).reshape(9)[a])
         self.n_wall = len(walls)
         # expand templates x instances into per-owner and per-sphere arrays
         M = len(s.owner_template)

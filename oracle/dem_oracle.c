@@ -284,13 +284,83 @@ int orc_sphere_positions(const orc_world *w, double *p)
     return 0;
 }
 
+/* Point of the triangle (a, b, c) closest to p: the region tests of the published
+ * closest-point-on-triangle algorithm (vertex, edge and face regions by the signs of
+ * barycentric-coordinate numerators), evaluated in this order. */
+static void closest_on_triangle(const double p[3], const double a[3], const double b[3], const double c[3],
+                                double q[3])
+{
+    double ab[3], ac[3], ap[3], bp[3], cp[3];
+    for (int k = 0; k < 3; ++k) {
+        ab[k] = b[k] - a[k]; ac[k] = c[k] - a[k]; ap[k] = p[k] - a[k];
+        bp[k] = p[k] - b[k]; cp[k] = p[k] - c[k];
+    }
+    double d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) { memcpy(q, a, 3 * sizeof(double)); return; }
+    double d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+    if (d3 >= 0.0 && d4 <= d3) { memcpy(q, b, 3 * sizeof(double)); return; }
+    double vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+        double v = d1 / (d1 - d3);
+        for (int k = 0; k < 3; ++k) q[k] = a[k] + v * ab[k];
+        return;
+    }
+    double d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+    if (d6 >= 0.0 && d5 <= d6) { memcpy(q, c, 3 * sizeof(double)); return; }
+    double vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+        double w = d2 / (d2 - d6);
+        for (int k = 0; k < 3; ++k) q[k] = a[k] + w * ac[k];
+        return;
+    }
+    double va = d3 * d6 - d5 * d4;
+    if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
+        double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        for (int k = 0; k < 3; ++k) q[k] = b[k] + w * (c[k] - b[k]);
+        return;
+    }
+    double den = 1.0 / ((va + vb) + vc);
+    double v = vb * den, w = vc * den;
+    for (int k = 0; k < 3; ++k) q[k] = (a[k] + ab[k] * v) + ac[k] * w;
+}
+
+/* Vertices of a facet wall at time t: p + R(omega t)(v - p) (Rodrigues' rotation about
+ * the unit axis omega / |omega| by |omega| t). */
+static void facet_vertices(const orc_wall *wl, double t, double v[9])
+{
+    double wn = norm3(wl->omega);
+    if (!(wn > 0.0)) { memcpy(v, wl->tri, 9 * sizeof(double)); return; }
+    double k[3] = {wl->omega[0] / wn, wl->omega[1] / wn, wl->omega[2] / wn};
+    double th = wn * t, cs = cos(th), sn = sin(th);
+    for (int m = 0; m < 3; ++m) {
+        double r[3] = {wl->tri[3 * m] - wl->p[0], wl->tri[3 * m + 1] - wl->p[1], wl->tri[3 * m + 2] - wl->p[2]};
+        double kxr[3];
+        cross3(k, r, kxr);
+        double kr = dot3(k, r);
+        for (int a = 0; a < 3; ++a)
+            v[3 * m + a] = wl->p[a] + ((r[a] * cs + kxr[a] * sn) + k[a] * (kr * (1.0 - cs)));
+    }
+}
+
 /* Signed gap from a sphere centre c to a wall surface (positive on the domain side)
  * and the unit normal from the wall towards the centre.  Returns 0 if the normal is
  * undefined (centre on a cylinder or cone axis), 1 otherwise. */
-static int wall_gap(const orc_wall *wl, const double c[3], double *gap, double nrm[3])
+static int wall_gap(const orc_wall *wl, double tnow, const double c[3], double *gap, double nrm[3])
 {
     const double *a = wl->p, *u = wl->n;
     double d[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    if (wl->type == ORC_WALL_TRIANGLE) {
+        /* two-sided facet at time t: distance to its closest point */
+        double v[9], q[3];
+        facet_vertices(wl, tnow, v);
+        closest_on_triangle(c, &v[0], &v[3], &v[6], q);
+        double e[3] = {c[0] - q[0], c[1] - q[1], c[2] - q[2]};
+        double dist = norm3(e);
+        *gap = dist;
+        if (!(dist > 0.0)) return 0;
+        nrm[0] = e[0] / dist; nrm[1] = e[1] / dist; nrm[2] = e[2] / dist;
+        return 1;
+    }
     if (wl->type == ORC_WALL_PLANE) {
         *gap = (d[0] * u[0] + d[1] * u[1]) + d[2] * u[2];
         nrm[0] = u[0]; nrm[1] = u[1]; nrm[2] = u[2];
@@ -418,7 +488,7 @@ int orc_listed_wall_pairs(const orc_world *w, const double *p, double beta, int6
         if (!owner_is_active(w, w->owner[s])) continue;
         for (int32_t k = 0; k < w->n_wall; ++k) {
             double gap, nrm[3];
-            wall_gap(&w->walls[k], &p[3 * s], &gap, nrm);
+            wall_gap(&w->walls[k], (double)w->step * w->h, &p[3 * s], &gap, nrm);
             if (gap < w->rad[s] + beta) {
                 if (c < cap) { si[c] = s; wi[c] = k; }
                 ++c;
@@ -656,7 +726,7 @@ static int sphere_wall_contact(const orc_world *w, const double *p, int64_t i, i
 {
     const orc_wall *wl = &w->walls[k];
     double gap, nrm[3];
-    if (!wall_gap(wl, &p[3 * i], &gap, nrm)) return 0;
+    if (!wall_gap(wl, (double)w->step * w->h, &p[3 * i], &gap, nrm)) return 0;
     double RA = w->rad[i];
     double delta = RA - gap;
     if (!(delta > 0.0)) return 0;
@@ -1104,6 +1174,7 @@ int orc_step(orc_world *w, int64_t nsteps)
                 }
             }
         }
+        w->step += 1;
         if (w->v_err > 0.0) {
             for (int64_t o = 0; o < M; ++o) {
                 double sp = norm3(&w->v[3 * o]);

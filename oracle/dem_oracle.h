@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-enum { ORC_WALL_PLANE = 0, ORC_WALL_CYLINDER = 1, ORC_WALL_CONE = 2 };
+enum { ORC_WALL_PLANE = 0, ORC_WALL_CYLINDER = 1, ORC_WALL_CONE = 2, ORC_WALL_TRIANGLE = 3 };
 /* contact force models (Sec. 4.2: the default model; Sec. 6.3: a bonded, breakable
  * contact for brittle solids, the paper's worked example of a custom model) */
 enum { ORC_MODEL_HERTZ_MINDLIN = 0, ORC_MODEL_BONDED_BREAKAGE = 1 };
@@ -53,7 +53,11 @@ enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_CAPACITY = -2, ORC_ERR_DIVERGED = -
  *   plane   : point p, unit normal n pointing into the granular domain
  *   cylinder: axis point p, unit axis n, inner surface radius r0 (spheres live inside)
  *   cone    : axis point p, unit axis n, generator segment (r0,z0)-(r1,z1) in the
- *             (radius, axial coordinate) half plane; spheres live on the axis side      */
+ *             (radius, axial coordinate) half plane; spheres live on the axis side
+ *   triangle: one facet of a rigid mesh (Sec. 2.4, geometry hierarchy; Sec. 5, the
+ *             mixer), vertices tri[9] at time 0, turning with omega about p, so at time
+ *             t its vertices are p + R(omega t)(v - p); two-sided: the gap is the distance
+ *             from the centre to the closest point of the facet                         */
 typedef struct {
     int32_t type;
     int32_t mat;
@@ -61,6 +65,7 @@ typedef struct {
     double n[3];
     double r0, z0, r1, z1;
     double omega[3];
+    double tri[9];
 } orc_wall;
 
 /* Prescribed motion of a family (Sec. 2.2.2, family tags): where fix_v (fix_w) is set,
@@ -114,6 +119,7 @@ typedef struct {
     /* contact force model (ORC_MODEL_*) and its parameters (NULL for the default) */
     int32_t model;
     const double *model_params;
+    int64_t step;                   /* steps taken (time = step * h: the pose of meshes)  */
 } orc_world;
 
 /* One resolved contact.  j >= 0 is a sphere, j < 0 is wall (-1 - j).  force acts on

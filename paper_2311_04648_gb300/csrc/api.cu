@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "force_models.cuh"
 #include "kernels.cuh"
 #include "mlp.h"
 
@@ -55,6 +56,9 @@ struct WorldImpl {
     HostModel model;
     std::string err;
     std::vector<uint8_t> schedule_model;
+    // contact force model of the world and its parameters
+    int force_model = 0;
+    std::vector<double> force_params;
     // family tags of the world (all its scenes): prescribed motion and contact mask
     std::vector<FamilyMotion> fam_motion;
     std::vector<uint32_t> fam_mask;
@@ -223,6 +227,8 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
     m.free = d0.free;
     m.alloc_ctx = d0.alloc_ctx;
     m.schedule_model = W.schedule_model;
+    m.model = W.force_model;
+    m.model_params = W.force_params;
     if (W.families_used) {
         m.fam_motion = W.fam_motion;
         m.fam_mask = W.fam_mask;
@@ -342,6 +348,7 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
                 double crr = sc.crr_pair.count(key) ? sc.crr_pair[key] : sc.crr[a];
                 m.pairs.push_back(pair_param(sc.E[a], sc.nu[a], sc.E[b], sc.nu[b], cor, mu));
                 m.pair_crr.push_back(crr);
+                m.pair_nu.push_back(0.5 * (sc.nu[a] + sc.nu[b]));
                 if (crr > 0.0) {
                     g.has_rolling = 1;
                     m.rolling = true;
@@ -1019,6 +1026,65 @@ dem_status dem_get_owner_forces(dem_world *w, int64_t first, int64_t n, double *
     if (force) std::memcpy(force, F.data() + 3 * b, 3 * n * sizeof(double));
     if (torque) std::memcpy(torque, T.data() + 3 * b, 3 * n * sizeof(double));
     return DEM_OK;
+}
+
+// ---------------------------------------------------------------- contact force models (Sec. 4.2)
+
+dem_status dem_set_force_model(dem_world *w, int32_t model, const double *params, int32_t n_params)
+{
+    CHECK_SETUP(w);
+    int need;
+    switch (model) {
+    case DEM_MODEL_DEFAULT: need = 0; break;
+    case DEM_MODEL_HERTZ_MINDLIN: need = ModelHertzMindlin::n_params; break;
+    case DEM_MODEL_BONDED_BREAKAGE: need = ModelBondedBreakage::n_params; break;
+    default: return fail(w, DEM_ERR_ARG, "unknown contact model");
+    }
+    if (n_params != need || (need > 0 && !params)) return fail(w, DEM_ERR_ARG, "wrong number of model parameters");
+    for (int k = 0; k < n_params; ++k)
+        if (!std::isfinite(params[k])) return fail(w, DEM_ERR_ARG, "non-finite model parameter");
+    WorldImpl &W = *w->impl;
+    W.force_model = model == DEM_MODEL_DEFAULT ? FORCE_MODEL_BUILTIN
+                                               : (model == DEM_MODEL_HERTZ_MINDLIN ? FORCE_MODEL_HERTZ_MINDLIN
+                                                                                    : FORCE_MODEL_BONDED_BREAKAGE);
+    W.force_params.assign(params, params + n_params);
+    return DEM_OK;
+}
+
+dem_status dem_set_contact_wildcards(dem_world *w, int64_t k, const int64_t *i, const int64_t *j, const double *wc)
+{
+    CHECK_INIT(w);
+    if (k < 0 || (k > 0 && (!i || !j || !wc))) return fail(w, DEM_ERR_ARG, "bad wildcard arrays");
+    const int64_t b = sphere_base(w);
+    std::vector<int64_t> gi(k), gj(k);
+    for (int64_t q = 0; q < k; ++q) {
+        if (i[q] < 0 || j[q] < 0) return fail(w, DEM_ERR_ARG, "wildcards are for sphere pairs");
+        gi[q] = std::min(i[q], j[q]) + b;
+        gj[q] = std::max(i[q], j[q]) + b;
+    }
+    std::string err;
+    dem_status s = w->impl->engine->set_wildcards(k, gi.data(), gj.data(), wc, err);
+    return s ? fail(w, s, err) : DEM_OK;
+}
+
+dem_status dem_get_contact_wildcards(dem_world *w, int64_t cap, int64_t *count, double *wc)
+{
+    CHECK_INIT(w);
+    if (!count) return fail(w, DEM_ERR_ARG, "null count");
+    std::vector<ContactOut> cs;
+    std::string err;
+    dem_status s = w->impl->engine->contacts(cs, err);
+    if (s) return fail(w, s, err);
+    const int64_t b = sphere_base(w), e = b + scene_spheres(w);
+    int64_t c = 0;
+    for (auto &x : cs) {
+        if (x.i < b || x.i >= e) continue;
+        if (c < cap && wc)
+            for (int q = 0; q < 8; ++q) wc[8 * c + q] = x.wc[q];
+        ++c;
+    }
+    *count = c;
+    return c > cap ? fail(w, DEM_ERR_CAPACITY, "wildcard buffer too small") : DEM_OK;
 }
 
 // ---------------------------------------------------------------- family tags (Sec. 2.2.2)

@@ -26,7 +26,7 @@ constexpr int VOX_BITS = 21;
 constexpr int VOX_BIAS = 1 << (VOX_BITS - 1);
 constexpr uint64_t VOX_MASK = (1ull << VOX_BITS) - 1;
 
-enum : int { WALL_PLANE = 0, WALL_CYLINDER = 1, WALL_CONE = 2 };
+enum : int { WALL_PLANE = 0, WALL_CYLINDER = 1, WALL_CONE = 2, WALL_TRIANGLE = 3 };
 
 // halt reasons written by the kernels into DevStatus::halt
 enum : int { HALT_NONE = 0, HALT_DIVERGED = 1, HALT_OVERFLOW = 2, HALT_TIMEOUT = 3 };
@@ -107,6 +107,11 @@ struct Wall {            // analytical wall (device copy); geometry in FP64
     // float-float pair), so that the voxel form measures gaps from voxel differences in FP32
     int axis, ax_c;
     float ax_sign, ax_off, ax_off_lo;
+    // a mesh facet (WALL_TRIANGLE): vertices at time 0 and at the current step (the mesh
+    // turns with omega about p), two-sided
+    double tri[9];
+    double cur[9];
+    int scene;           // the scene it belongs to
 };
 
 struct Scene {           // per-scene constants (device copy)
@@ -127,6 +132,7 @@ struct Scene {           // per-scene constants (device copy)
     int nbc[3];          // smallest cells per axis (the bins' grid; detection cells may be larger)
     int bin_base;        // first global bin of this scene
     int has_rolling;     // a material pair of this scene has C_r > 0
+    int facet_begin, facet_count;   // mesh facets: walls found by the binned facet search
 };
 
 constexpr int BIN_CELLS = 8;     // cells per schedule-bin edge
@@ -188,6 +194,7 @@ struct DevStatus {
     unsigned long long pair_steps;   // sum over completed steps of the pairs in use
     unsigned long long busy_steps;   // sum over completed steps of the slots with partners
     long long stale_events;
+    long long snap_step;         // step of the snapshot of the list being built (mesh poses)
     // updated by atomics of many threads (narrow phase, compaction, link, divergence): a
     // line of their own, away from the fields above
     alignas(128) int overflow;   // a row exceeded the list capacity in the last narrow phase

@@ -205,11 +205,54 @@ __device__ __forceinline__ float wall_gap_tol(const Wall &w, float3 c)
     return w.tolf * (fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + 1.0f) + 1e-9f;
 }
 
+// Point of the triangle (a, b, c) closest to p: the region tests of the published
+// closest-point-on-triangle algorithm (vertex, edge and face regions by the signs of
+// barycentric-coordinate numerators), every product and sum rounded on its own in the
+// written order.
+__device__ __forceinline__ V3<double> closest_on_triangle(V3<double> p, V3<double> a, V3<double> b, V3<double> c)
+{
+    auto sub = [](V3<double> u, V3<double> v) { return V3<double>{rsub(u.x, v.x), rsub(u.y, v.y), rsub(u.z, v.z)}; };
+    auto dt = [](V3<double> u, V3<double> v) { return radd(radd(rmul(u.x, v.x), rmul(u.y, v.y)), rmul(u.z, v.z)); };
+    auto axpy = [](V3<double> u, double s, V3<double> v) {
+        return V3<double>{radd(u.x, rmul(s, v.x)), radd(u.y, rmul(s, v.y)), radd(u.z, rmul(s, v.z))};
+    };
+    const V3<double> ab = sub(b, a), ac = sub(c, a), ap = sub(p, a), bp = sub(p, b), cp = sub(p, c);
+    const double d1 = dt(ab, ap), d2 = dt(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) return a;
+    const double d3 = dt(ab, bp), d4 = dt(ac, bp);
+    if (d3 >= 0.0 && d4 <= d3) return b;
+    const double vc = rsub(rmul(d1, d4), rmul(d3, d2));
+    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) return axpy(a, __ddiv_rn(d1, rsub(d1, d3)), ab);
+    const double d5 = dt(ab, cp), d6 = dt(ac, cp);
+    if (d6 >= 0.0 && d5 <= d6) return c;
+    const double vb = rsub(rmul(d5, d2), rmul(d1, d6));
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) return axpy(a, __ddiv_rn(d2, rsub(d2, d6)), ac);
+    const double va = rsub(rmul(d3, d6), rmul(d5, d4));
+    const double e43 = rsub(d4, d3), e56 = rsub(d5, d6);
+    if (va <= 0.0 && e43 >= 0.0 && e56 >= 0.0) return axpy(b, __ddiv_rn(e43, radd(e43, e56)), sub(c, b));
+    const double den = __ddiv_rn(1.0, radd(radd(va, vb), vc));
+    const double v = rmul(vb, den), w = rmul(vc, den);
+    return V3<double>{radd(radd(a.x, rmul(ab.x, v)), rmul(ac.x, w)), radd(radd(a.y, rmul(ab.y, v)), rmul(ac.y, w)),
+                      radd(radd(a.z, rmul(ab.z, v)), rmul(ac.z, w))};
+}
+
 // Signed gap of a sphere centre to a wall (positive on the domain side) and the unit
 // normal from the wall to the centre; FP64, every product and sum rounded in a fixed
 // order.  Returns false where the normal is undefined (centre on an axis).
 __device__ __forceinline__ bool wall_gap(const Wall &w, V3<double> c, double &gap, V3<double> &n)
 {
+    if (w.type == WALL_TRIANGLE) {
+        // a two-sided facet at its current pose: distance to its closest point
+        const V3<double> q = closest_on_triangle(c, V3<double>{w.cur[0], w.cur[1], w.cur[2]},
+                                                 V3<double>{w.cur[3], w.cur[4], w.cur[5]},
+                                                 V3<double>{w.cur[6], w.cur[7], w.cur[8]});
+        const V3<double> e = {rsub(c.x, q.x), rsub(c.y, q.y), rsub(c.z, q.z)};
+        const double dist = __dsqrt_rn(radd(radd(rmul(e.x, e.x), rmul(e.y, e.y)), rmul(e.z, e.z)));
+        gap = dist;
+        if (!(dist > 0.0)) return false;
+        n = {__ddiv_rn(e.x, dist), __ddiv_rn(e.y, dist), __ddiv_rn(e.z, dist)};
+        return true;
+    }
     V3<double> d = {rsub(c.x, w.p[0]), rsub(c.y, w.p[1]), rsub(c.z, w.p[2])};
     double z = radd(radd(rmul(d.x, w.n[0]), rmul(d.y, w.n[1])), rmul(d.z, w.n[2]));
     if (w.type == WALL_PLANE) {

@@ -37,6 +37,11 @@ struct HostModel {
     std::vector<FamilyMotion> fam_motion;       // N_FAMILY entries
     std::vector<uint32_t> fam_mask;             // FAMILY_MASK_WORDS words
     bool families_used = false;
+    // contact model (force_models.cuh: FORCE_MODEL_*), its parameters, and the mean
+    // Poisson ratio per material pair (pairs' indexing) that models may read
+    int model = 0;
+    std::vector<double> model_params;
+    std::vector<double> pair_nu;
     std::vector<uint16_t> mat_scene, mat_local;
     // owners, M
     std::vector<double> x, q, v, wb, mass, moi, r_ext;
@@ -67,6 +72,7 @@ struct ContactOut {
     int64_t i, j;                   // user sphere ids; j = -1 - wall for walls
     double force[3], point[3], overlap, hist[3];
     double age, trf[3];             // time in contact; rolling-resistance force on i (torque only)
+    double wc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // contact model wildcards (model worlds)
 };
 
 // Detection cells of edge f * L_min (whole voxels in the voxel form) for every scene:
@@ -92,6 +98,8 @@ public:
     virtual dem_status owner_forces(std::vector<double> &F, std::vector<double> &T, std::string &err) = 0;
     virtual dem_status set_history(int64_t k, const int64_t *i, const int64_t *j, const double *ut,
                                    const double *age, std::string &err) = 0;
+    virtual dem_status set_wildcards(int64_t k, const int64_t *i, const int64_t *j, const double *wc,
+                                     std::string &err) = 0;
     virtual dem_status stats(dem_stats *s, std::string &err) = 0;
     virtual dem_status diagnostics(dem_diagnostics *d, std::string &err) = 0;
     virtual dem_status save(std::vector<uint8_t> &blob, std::string &err) = 0;

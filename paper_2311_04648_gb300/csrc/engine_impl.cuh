@@ -146,6 +146,24 @@ public:
             if ((s = up(crr_f, cf.data(), (int64_t)cf.size(), err))) return s;
             d_.crr = crr;
             d_.crr_f = crr_f;
+            double *nu;
+            if ((s = alloc(nu, m_.pairs.size(), err))) return s;
+            std::vector<double> nv(m_.pairs.size(), 0.0);
+            for (size_t k = 0; k < nv.size() && k < m_.pair_nu.size(); ++k) nv[k] = m_.pair_nu[k];
+            if ((s = up(nu, nv.data(), (int64_t)nv.size(), err))) return s;
+            d_.pair_nu = nu;
+            double *mp;
+            float *mpf;
+            if ((s = alloc(mp, MODEL_MAX_PARAMS, err))) return s;
+            if ((s = alloc(mpf, MODEL_MAX_PARAMS, err))) return s;
+            std::vector<double> pd(MODEL_MAX_PARAMS, 0.0);
+            for (size_t k = 0; k < pd.size() && k < m_.model_params.size(); ++k) pd[k] = m_.model_params[k];
+            std::vector<float> pf(pd.begin(), pd.end());
+            if ((s = up(mp, pd.data(), MODEL_MAX_PARAMS, err))) return s;
+            if ((s = up(mpf, pf.data(), MODEL_MAX_PARAMS, err))) return s;
+            d_.model = m_.model;
+            d_.model_par = mp;
+            d_.model_par_f = mpf;
         }
         if ((s = alloc(st_, 1, err))) return s;
         if ((s = alloc(d_.audit, AUDIT_SLOTS * AUDIT_STRIDE, err))) return s;
@@ -431,6 +449,7 @@ public:
         if (N == 0) return DEM_OK;
         double *buf;
         const int64_t ne = K * Np;
+        if (m_.model != FORCE_MODEL_BUILTIN) return contacts_model(out, err);
         if ((s = scratch(buf, 14 * ne, err))) return s;
         if (m_.clumps)
             k_contacts<F, true><<<grid(N, 128), 128, 0, sf_>>>(d_, buf, buf + ne, buf + 4 * ne, buf + 7 * ne,
@@ -466,6 +485,98 @@ public:
                 out.push_back(c);
             }
         }
+        return DEM_OK;
+    }
+
+    // Read-back through the world's contact model: every pair it engages (a bond across a
+    // gap included) with its force, point, wildcards and torque-only force.
+    dem_status contacts_model(std::vector<ContactOut> &out, std::string &err)
+    {
+        dem_status s;
+        const int64_t N = d_.N, Np = d_.Np, ne = (int64_t)d_.K * Np;
+        double *buf;
+        if ((s = scratch(buf, 19 * ne, err))) return s;
+        double *ov = buf, *fo = buf + ne, *pt = buf + 4 * ne, *wc = buf + 7 * ne, *rf = buf + 15 * ne,
+               *en = buf + 18 * ne;
+        if (m_.model == FORCE_MODEL_BONDED_BREAKAGE) {
+            if (m_.clumps) k_contacts_model<F, true, ModelBondedBreakage><<<grid(N, 128), 128, 0, sf_>>>(d_, ov, fo, pt, wc, rf, en);
+            else k_contacts_model<F, false, ModelBondedBreakage><<<grid(N, 128), 128, 0, sf_>>>(d_, ov, fo, pt, wc, rf, en);
+        } else {
+            if (m_.clumps) k_contacts_model<F, true, ModelHertzMindlin><<<grid(N, 128), 128, 0, sf_>>>(d_, ov, fo, pt, wc, rf, en);
+            else k_contacts_model<F, false, ModelHertzMindlin><<<grid(N, 128), 128, 0, sf_>>>(d_, ov, fo, pt, wc, rf, en);
+        }
+        DEM_CU(cudaGetLastError());
+        std::vector<double> h(19 * ne);
+        DEM_CU(cudaMemcpyAsync(h.data(), buf, 19 * ne * sizeof(double), cudaMemcpyDeviceToHost, sf_));
+        std::vector<uint32_t> partner;
+        std::vector<uint8_t> cnt;
+        if ((s = fetch_list(sth_->list_cur, partner, cnt, err))) return s;
+        for (int64_t sl = 0; sl < N; ++sl) {
+            int64_t ui = m_.sphere_of_slot[sl];
+            if (ui < 0) continue;
+            for (int k = 0; k < cnt[sl]; ++k) {
+                int64_t e = (int64_t)k * Np + sl;
+                uint32_t j = partner[e];
+                if (!(j & WALL_BIT) && j < (uint32_t)sl) continue;
+                if (!(h[18 * ne + e] > 0.0)) continue;
+                ContactOut c;
+                c.i = ui;
+                c.j = (j & WALL_BIT) ? -1 - wall_local(j & ~WALL_BIT) : m_.sphere_of_slot[j];
+                for (int a = 0; a < 3; ++a) {
+                    c.force[a] = h[ne + 3 * e + a];
+                    c.point[a] = h[4 * ne + 3 * e + a];
+                    c.hist[a] = h[7 * ne + 8 * e + a];
+                    c.trf[a] = h[15 * ne + 3 * e + a];
+                }
+                for (int q = 0; q < 8; ++q) c.wc[q] = h[7 * ne + 8 * e + q];
+                c.age = h[7 * ne + 8 * e + 3];
+                c.overlap = h[e];
+                out.push_back(c);
+            }
+        }
+        return DEM_OK;
+    }
+
+    // Wildcards 4..7 of the contact model for listed pairs (i, j), wc[4k] (host values in
+    // the lower sphere's orientation; the upper side's copy takes the odd ones negated).
+    dem_status set_wildcards(int64_t nk, const int64_t *ii, const int64_t *jj, const double *wcv,
+                             std::string &err) override
+    {
+        dem_status s;
+        if ((s = pull(err))) return s;
+        if (!d_.lists.wild[0]) {
+            err = "the world's contact model has no wildcards beyond the history";
+            return DEM_ERR_STATE;
+        }
+        std::vector<uint32_t> partner;
+        std::vector<uint8_t> cnt;
+        if ((s = fetch_list(sth_->list_cur, partner, cnt, err))) return s;
+        const int64_t ne = (int64_t)d_.K * d_.Np;
+        using H = typename HistVec<R>::T;
+        const int hp = sth_->hist_par;
+        std::vector<H> wv(ne);
+        DEM_CU(cudaMemcpyAsync(wv.data(), d_.lists.wild[hp], ne * sizeof(H), cudaMemcpyDeviceToHost, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
+        const unsigned odd = model_odd();
+        for (int64_t q = 0; q < nk; ++q) {
+            if (ii[q] < 0 || ii[q] >= (int64_t)m_.slot_of_sphere.size() || jj[q] < 0 ||
+                jj[q] >= (int64_t)m_.slot_of_sphere.size())
+                continue;
+            const int64_t si = m_.slot_of_sphere[ii[q]], sj = m_.slot_of_sphere[jj[q]];
+            for (int side = 0; side < 2; ++side) {
+                const int64_t me = side ? sj : si, other = side ? si : sj;
+                const bool upper = me > other;
+                for (int k = 0; k < cnt[me]; ++k) {
+                    const int64_t e = (int64_t)k * d_.Np + me;
+                    if (partner[e] != (uint32_t)other) continue;
+                    R v[4];
+                    for (int a = 0; a < 4; ++a) v[a] = (R)((upper && ((odd >> (4 + a)) & 1u)) ? -wcv[4 * q + a] : wcv[4 * q + a]);
+                    wv[e].x = v[0]; wv[e].y = v[1]; wv[e].z = v[2]; wv[e].w = v[3];
+                }
+            }
+        }
+        DEM_CU(cudaMemcpyAsync(d_.lists.wild[hp], wv.data(), ne * sizeof(H), cudaMemcpyHostToDevice, sf_));
+        DEM_CU(cudaStreamSynchronize(sf_));
         return DEM_OK;
     }
 
@@ -755,6 +866,7 @@ public:
         if ((s = dput(d_.lists.partner[lc], ne * 4))) return s;
         if ((s = dput(d_.lists.cnt[lc], d_.Np))) return s;
         if ((s = dput(d_.lists.hist[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
+        if (d_.lists.wild[hp] && (s = dput(d_.lists.wild[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
         double extra[2] = {beta_, (double)fallbacks_};
         put(extra, sizeof(extra));
         return DEM_OK;
@@ -807,6 +919,7 @@ public:
         if ((s = dget(d_.lists.partner[lc], ne * 4))) return s;
         if ((s = dget(d_.lists.cnt[lc], d_.Np))) return s;
         if ((s = dget(d_.lists.hist[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
+        if (d_.lists.wild[hp] && (s = dget(d_.lists.wild[hp], ne * sizeof(typename HistVec<R>::T)))) return s;
         double extra[2];
         if (!get(extra, sizeof(extra))) { err = "truncated state blob"; return DEM_ERR_ARG; }
         // the margin is a tuning choice (results are the same bits for every margin) and
@@ -991,6 +1104,8 @@ private:
             if ((s = alloc(d_.lists.partner[b], ne, err))) return s;
             if ((s = alloc(d_.lists.cnt[b], std::max(d_.Np, Mp_), err))) return s;
             if ((s = alloc(d_.lists.hist[b], ne, err))) return s;
+            d_.lists.wild[b] = nullptr;
+            if (model_wildcards() > 4 && (s = alloc(d_.lists.wild[b], ne, err))) return s;
             if (!act_alloc_) {
                 if ((s = alloc(d_.lists.act[b], d_.Np, err))) return s;
                 if ((s = alloc(d_.lists.n_act[b], 1, err))) return s;
@@ -1020,10 +1135,15 @@ private:
             if ((s = copy_sync(d_.lists.hist[hp], old.hist[hp], ne * sizeof(typename HistVec<R>::T),
                                cudaMemcpyDeviceToDevice, err)))
                 return s;
+            if (old.wild[hp] &&
+                (s = copy_sync(d_.lists.wild[hp], old.wild[hp], ne * sizeof(typename HistVec<R>::T),
+                               cudaMemcpyDeviceToDevice, err)))
+                return s;
         }
         for (int b = 0; b < 2; ++b) {
             dfree(old.partner[b]); dfree(old.cnt[b]);
             dfree(old.hist[b]);
+            dfree(old.wild[b]);
         }
         if (keep) recompact_current();
         if (tune_.integrate_staged) {               // new row-length arrays: check them again
@@ -1711,6 +1831,16 @@ private:
             g = std::min(g, std::max(1u, cap));
         }
         const bool lean = MODE == MODE_STEP && tune_.contact_lean;
+        if (m_.model == FORCE_MODEL_HERTZ_MINDLIN) {
+            if (m_.clumps) k_contact<F, true, MODE, 0, false, FORCE_MODEL_HERTZ_MINDLIN><<<g, b, 0, sf_>>>(d_, eF, eT);
+            else k_contact<F, false, MODE, 0, false, FORCE_MODEL_HERTZ_MINDLIN><<<g, b, 0, sf_>>>(d_, eF, eT);
+            return;
+        }
+        if (m_.model == FORCE_MODEL_BONDED_BREAKAGE) {
+            if (m_.clumps) k_contact<F, true, MODE, 0, false, FORCE_MODEL_BONDED_BREAKAGE><<<g, b, 0, sf_>>>(d_, eF, eT);
+            else k_contact<F, false, MODE, 0, false, FORCE_MODEL_BONDED_BREAKAGE><<<g, b, 0, sf_>>>(d_, eF, eT);
+            return;
+        }
         if (m_.rolling) {
             // rolling resistance: its own build of the kernel (the others carry none of it)
             if (m_.clumps) k_contact<F, true, MODE, 0, true><<<g, b, 0, sf_>>>(d_, eF, eT);
@@ -1732,7 +1862,17 @@ private:
         if (key == occ_block_) return occ_per_sm_;
         int per_sm = 0;
         cudaError_t e;
-        if (m_.rolling)
+        if (m_.model == FORCE_MODEL_HERTZ_MINDLIN)
+            e = m_.clumps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, k_contact<F, true, MODE_STEP, 0, false, FORCE_MODEL_HERTZ_MINDLIN>, b, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, k_contact<F, false, MODE_STEP, 0, false, FORCE_MODEL_HERTZ_MINDLIN>, b, 0);
+        else if (m_.model == FORCE_MODEL_BONDED_BREAKAGE)
+            e = m_.clumps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, k_contact<F, true, MODE_STEP, 0, false, FORCE_MODEL_BONDED_BREAKAGE>, b, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &per_sm, k_contact<F, false, MODE_STEP, 0, false, FORCE_MODEL_BONDED_BREAKAGE>, b, 0);
+        else if (m_.rolling)
             e = m_.clumps
                     ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, true, MODE_STEP, 0, true>, b, 0)
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact<F, false, MODE_STEP, 0, true>, b, 0);
@@ -1768,7 +1908,17 @@ private:
     }
 
     // Single spheres with the fused step chosen: one kernel for forces and integration.
-    bool fused() const { return !m_.clumps && !m_.rolling && tune_.fused_block > 0; }
+    bool fused() const { return !m_.clumps && !m_.rolling && m_.model == FORCE_MODEL_BUILTIN && tune_.fused_block > 0; }
+
+    // Contact wildcards of the world's contact model (4: those of the history vector).
+    int model_wildcards() const
+    {
+        return m_.model == FORCE_MODEL_BONDED_BREAKAGE ? ModelBondedBreakage::n_wildcards : 4;
+    }
+    unsigned model_odd() const
+    {
+        return m_.model == FORCE_MODEL_BONDED_BREAKAGE ? ModelBondedBreakage::odd : ModelHertzMindlin::odd;
+    }
 
     void force_step()
     {

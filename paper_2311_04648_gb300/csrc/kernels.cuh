@@ -25,6 +25,16 @@ struct DetectBuffers {
     void *sorted_aux;
     uint32_t *sorted_owner;    // owner of each sorted entry
     uint8_t *sorted_family;    // family of each sorted entry (only where families mask contacts)
+    // mesh facets (walls of type WALL_TRIANGLE): each build bins the facets, at their pose
+    // at the snapshot, into the cells their reach covers, as (cell key, facet) pairs sorted
+    // by key; a sphere tests the facets of its own cell
+    int n_facets;
+    const int *facet_wall;     // wall index of facet f
+    const int64_t *facet_off;  // first pair slot of facet f (n_facets + 1 entries)
+    double *tri_snap;          // facet vertices at the snapshot (9 per facet)
+    uint32_t *fkeys, *fvals, *fkeys_alt, *fvals_alt, *fhist;
+    int64_t n_fpairs, fhist_cap;
+    const uint32_t *fkeys_sorted, *fvals_sorted;   // after the sort (one of the two buffers)
     uint32_t *n_valid;         // device counter: active entries at the front of the order
 };
 
@@ -54,6 +64,8 @@ struct ListBuffers {
     // single spheres: per block of 256 slots, the slots' offsets within the block in
     // order of row length (empty rows first), for the fused step kernel
     uint8_t *perm[2];
+    // contact wildcards 4..7 of each entry (contact models with more than four; else null)
+    typename HistVec<R>::T *wild[2];
 };
 
 // Owner-state double buffers.

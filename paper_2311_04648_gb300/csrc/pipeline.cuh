@@ -14,6 +14,7 @@
 #include "stage.cuh"
 #include "common.cuh"
 #include "contact.cuh"
+#include "force_models.cuh"
 #include "kernels.cuh"
 
 namespace dem {
@@ -90,6 +91,11 @@ struct Dev {
     const uint8_t *owner_family;
     const FamilyMotion *fam_motion; // [N_FAMILY]
     const uint32_t *fam_mask;       // [FAMILY_MASK_WORDS]
+    // a contact model other than the built-in one (force_models.cuh) and its parameters
+    int model;
+    const double *model_par;
+    const float *model_par_f;
+    const double *pair_nu;          // mean Poisson ratio per material pair (pairs' indexing)
     const uint16_t *mat_scene, *mat_local;
     DevStatus *status;
     unsigned int *audit;            // AUDIT_SLOTS x AUDIT_STRIDE words (per-warp maxima of a step)
@@ -189,7 +195,9 @@ __device__ __forceinline__ V3<R> point_velocity(V3<R> v, V3<R> w, V3<R> r)
 // negation, so B's thread, calling with the roles exchanged (and its copy of the history,
 // the negation of A's), obtains exactly the negated force: no canonical reordering.  False if the
 // overlap is not positive.
-template <class F, bool PARAMS = true>
+// ANY: the geometry whatever the sign of the overlap (bonded contacts act across a gap);
+// false only where the centres coincide.
+template <class F, bool PARAMS = true, bool ANY = false>
 __device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
                                                ContactIn<typename F::R> &c, V3<typename F::R> &armA,
                                                V3<typename F::R> &armB)
@@ -205,7 +213,7 @@ __device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F>
         dist = sqrt(ss);
         delta = rsub(radd(A.rad, B.rad), dist);
     }
-    if (!(delta > R(0)) || !(dist > R(0))) return false;
+    if ((!ANY && !(delta > R(0))) || !(dist > R(0))) return false;
     R inv = R(1) / dist;
     c.n = {rmul(inv, dd.x), rmul(inv, dd.y), rmul(inv, dd.z)};
     c.delta = delta;
@@ -317,6 +325,7 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
     if (stp->halt) return;
     if (s == 0) {
         stp->disp_next = 0.0;
+        stp->snap_step = stp->steps_done;  // mesh facets are binned at their pose of this step
         stp->cell_stamp += 1;            // a new cell table (the previous entries go stale)
         stp->beta_next = beta;
         stp->beta_next_f = (float)beta;
@@ -416,6 +425,84 @@ __device__ __forceinline__ void row_insert(uint32_t *buf, int &n, uint32_t e)
     ++n;
 }
 
+// Vertices of facet w at time t: p + R(omega t)(v - p) (Rodrigues' rotation about the unit
+// axis omega / |omega| by |omega| t), every operation rounded on its own in that order.
+__device__ __forceinline__ void facet_pose(const Wall &w, double t, double *v)
+{
+    const V3<double> om = {w.omega[0], w.omega[1], w.omega[2]};
+    const double wn = __dsqrt_rn(radd(radd(rmul(om.x, om.x), rmul(om.y, om.y)), rmul(om.z, om.z)));
+    if (!(wn > 0.0)) {
+        for (int q = 0; q < 9; ++q) v[q] = w.tri[q];
+        return;
+    }
+    const V3<double> k = {__ddiv_rn(om.x, wn), __ddiv_rn(om.y, wn), __ddiv_rn(om.z, wn)};
+    const double th = rmul(wn, t);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    const double omc = rsub(1.0, cs);
+    for (int m = 0; m < 3; ++m) {
+        const V3<double> r = {rsub(w.tri[3 * m], w.p[0]), rsub(w.tri[3 * m + 1], w.p[1]), rsub(w.tri[3 * m + 2], w.p[2])};
+        const V3<double> kxr = {rsub(rmul(k.y, r.z), rmul(k.z, r.y)), rsub(rmul(k.z, r.x), rmul(k.x, r.z)),
+                                rsub(rmul(k.x, r.y), rmul(k.y, r.x))};
+        const double kr = radd(radd(rmul(k.x, r.x), rmul(k.y, r.y)), rmul(k.z, r.z));
+        const double f = rmul(kr, omc);
+        v[3 * m + 0] = radd(w.p[0], radd(radd(rmul(r.x, cs), rmul(kxr.x, sn)), rmul(k.x, f)));
+        v[3 * m + 1] = radd(w.p[1], radd(radd(rmul(r.y, cs), rmul(kxr.y, sn)), rmul(k.y, f)));
+        v[3 * m + 2] = radd(w.p[2], radd(radd(rmul(r.z, cs), rmul(kxr.z, sn)), rmul(k.z, f)));
+    }
+}
+
+// Current pose of every facet (the step's time, steps_done * h); runs after each step.
+template <class F>
+__global__ void __launch_bounds__(128) k_facet_pose(Dev<F> d, Wall *walls, const int *facet_wall, int n_facets)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n_facets) return;
+    Wall &w = walls[facet_wall[f]];
+    const double t = rmul((double)d.status->steps_done, d.scenes[w.scene].h);
+    facet_pose(w, t, w.cur);
+}
+
+// Bin every facet, at its pose of the snapshot step, into the cells its reach covers
+// (its bounding box grown by reach = largest radius + margin + one cell edge): pairs
+// (cell key, facet) from the facet's first slot, the unused slots of its share keyed
+// past every cell.
+template <class F>
+__global__ void __launch_bounds__(128) k_facet_bin(Dev<F> d, DetectBuffers b, double r_max)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= b.n_facets || d.status->halt) return;
+    const Wall &w = d.walls[b.facet_wall[f]];
+    const Scene &sc = d.scenes[w.scene];
+    double v[9];
+    facet_pose(w, rmul((double)d.status->snap_step, sc.h), v);
+    for (int q = 0; q < 9; ++q) b.tri_snap[9 * (int64_t)f + q] = v[q];
+    const double cell = 1.0 / d.invL;
+    const double reach = r_max + d.status->beta_next + cell;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        const double mn = fmin(fmin(v[a], v[3 + a]), v[6 + a]) - reach;
+        const double mx = fmax(fmax(v[a], v[3 + a]), v[6 + a]) + reach;
+        lo[a] = (int)floor((mn - sc.lo[a]) * d.invL);
+        hi[a] = (int)floor((mx - sc.lo[a]) * d.invL);
+        lo[a] = min(max(lo[a], 0), sc.nc[a] - 1);
+        hi[a] = min(max(hi[a], 0), sc.nc[a] - 1);
+    }
+    int64_t slot = b.facet_off[f];
+    const int64_t end = b.facet_off[f + 1];
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0] && slot < end; ++x) {
+                b.fkeys[slot] = sc.cell_base + (uint32_t)((z * sc.nc[1] + y) * sc.nc[0] + x);
+                b.fvals[slot] = (uint32_t)f;
+                ++slot;
+            }
+    for (; slot < end; ++slot) {
+        b.fkeys[slot] = b.n_cells_total;
+        b.fvals[slot] = (uint32_t)f;
+    }
+}
+
 // Narrow phase: one thread per sorted entry scans the 27 neighbour cells (as 9 runs of
 // three x-consecutive cells, each contiguous in the sorted order) and the walls of its
 // scene, and writes its full, sorted row into the list that is not in use.
@@ -491,6 +578,37 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
                     hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
                 }
                 if (hit) row_insert(buf, n, vals[u]);
+            }
+        }
+    }
+    // mesh facets binned into this cell: distance from the centre below R + beta (FP64, at
+    // the facets' pose of the snapshot)
+    if (b.n_facets > 0) {
+        const uint32_t *fk = b.fkeys_sorted;
+        int64_t lo = 0, hi = b.n_fpairs;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (fk[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < b.n_fpairs && fk[lo] == key) {
+            V3<double> pa;
+            double Rs;
+            if constexpr (F::voxel) {
+                pa = F::absolute(PosF32{ac.x, ac.y, ac.z, ao.x, ao.y, ao.z}, sc, d.Ld);
+                Rs = (double)ao.w;
+            } else {
+                pa = {a64.x, a64.y, a64.z};
+                Rs = a64.w;
+            }
+            for (int64_t q = lo; q < b.n_fpairs && fk[q] == key; ++q) {
+                const uint32_t f = b.fvals_sorted[q];
+                const double *v = b.tri_snap + 9 * (int64_t)f;
+                const V3<double> c = closest_on_triangle(pa, V3<double>{v[0], v[1], v[2]}, V3<double>{v[3], v[4], v[5]},
+                                                         V3<double>{v[6], v[7], v[8]});
+                const V3<double> e = {rsub(pa.x, c.x), rsub(pa.y, c.y), rsub(pa.z, c.z)};
+                const double dist = __dsqrt_rn(radd(radd(rmul(e.x, e.x), rmul(e.y, e.y)), rmul(e.z, e.z)));
+                if (dist < Rs + beta) row_insert(buf, n, WALL_BIT | (uint32_t)b.facet_wall[f]);
             }
         }
     }
@@ -674,6 +792,13 @@ __global__ void __launch_bounds__(256) k_link(Dev<F> d)
         R age = R(0);
         if (ko >= 0) u = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hs], (int64_t)ko * d.Np + s, age);
         hist_put(d.lists.hist[hd], e, u, age);
+        if (d.lists.wild[0]) {
+            // a contact model's further wildcards travel with the pair too
+            typename HistVec<R>::T wv;
+            wv.x = R(0); wv.y = R(0); wv.z = R(0); wv.w = R(0);
+            if (ko >= 0) wv = d.lists.wild[hs][(int64_t)ko * d.Np + s];
+            d.lists.wild[hd][e] = wv;
+        }
     }
     const unsigned int tot = __reduce_add_sync(0xffffffffu, owned);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&stp->list_pairs[ln], tot);
@@ -900,7 +1025,163 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
     }
 }
 
-template <class F, bool CLUMPS, int MODE, bool ROLL = false>
+template <class F>
+__device__ __forceinline__ const float *model_params(const Dev<F> &d, float)
+{
+    return d.model_par_f;
+}
+template <class F>
+__device__ __forceinline__ const double *model_params(const Dev<F> &d, double)
+{
+    return d.model_par;
+}
+
+// One listed entry (partner j) of sphere s through a contact model of force_models.cuh,
+// with the entry's wildcards wc[8] (updated).  A sphere pair is evaluated with A the
+// lower slot on both of its sides: the upper side swaps the roles, brings its copy of
+// the odd wildcards into A's orientation and back, and takes the negated forces, so each
+// side obtains exactly the other's reaction whatever the model computes.  Walls take the
+// default model (they belong to no bond).  Returns whether the pair interacts; F and Fr
+// (torque-only) act on s's owner at arm (contact point minus its centre of mass).
+template <class F, bool CLUMPS, class Model>
+__device__ __forceinline__ bool model_entry(const Dev<F> &d, const SphereK<F> &me, const Scene &sc, int64_t s,
+                                            uint32_t j, int sp, typename F::R *wc, V3<typename F::R> &Fo,
+                                            V3<typename F::R> &Fr, V3<typename F::R> &arm, typename F::R &overlap)
+{
+    using R = typename F::R;
+    const R h = F::voxel ? (R)sc.hf : (R)sc.h;
+    const R *par = model_params(d, R(0));
+    const auto *tab = pair_table(d, R(0));
+    const R *crr_tab = crr_table(d, R(0));
+    const V3<R> zero = {R(0), R(0), R(0)};
+    Fo = zero; Fr = zero; arm = zero; overlap = R(0);
+    if (j & WALL_BIT) {
+        const Wall &w = d.walls[j & ~WALL_BIT];
+        ContactIn<R> ci;
+        V3<R> armA;
+        if (!wall_contact<F, false>(d, me, sc, w, ci, armA)) return false;
+        const int pk = sc.pair_base + (me.mat - sc.mat_base) * sc.n_mat + (w.mat - sc.mat_base);
+        const auto p = tab[pk];
+        ci.Estar = p.Estar; ci.Gstar = p.Gstar; ci.beta = p.beta; ci.mu = p.mu;
+        V3<R> ut = {wc[0], wc[1], wc[2]};
+        R fn_abs;
+        hertz_mindlin<R>(ci, h, ut, Fo, &fn_abs);
+        wc[0] = ut.x; wc[1] = ut.y; wc[2] = ut.z;
+        wc[3] = radd(wc[3], h);
+        const R crr = crr_tab[pk];
+        if (crr > R(0) && !within_collision_time<R>(ci, wc[3])) {
+            const V3<R> rotA = cross_rn(me.w, armA);
+            Fr = rolling_force<R>(crr, fn_abs, V3<R>{rsub(ci.uB.x, rotA.x), rsub(ci.uB.y, rotA.y),
+                                                      rsub(ci.uB.z, rotA.z)});
+        }
+        arm = armA;
+        overlap = ci.delta;
+        return true;
+    }
+    SphereK<F> other = load_sphere<F, CLUMPS>(d, sp, j);
+    if (!d.st.active[sp][other.owner]) return false;
+    const bool swap = j < (uint32_t)s;
+    const SphereK<F> &A = swap ? other : me;
+    const SphereK<F> &B = swap ? me : other;
+    ContactIn<R> ci;
+    V3<R> armA, armB;
+    if (!sphere_contact<F, false, true>(d, A, B, ci, armA, armB)) return false;
+    if (swap) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if ((Model::odd >> q) & 1u) wc[q] = -wc[q];
+    }
+    const int pk = sc.pair_base + (A.mat - sc.mat_base) * sc.n_mat + (B.mat - sc.mat_base);
+    const auto p = tab[pk];
+    Referables<R> c;
+    c.B2A = ci.n;
+    c.overlapDepth = ci.delta;
+    c.ts = h;
+    c.locCPA = armA; c.locCPB = armB;
+    c.ALinVel = A.v; c.BLinVel = B.v;
+    c.ARotVel = A.w; c.BRotVel = B.w;
+    c.velB2A = ci.uA - ci.uB;
+    c.AOwnerMass = A.mass; c.BOwnerMass = B.mass;
+    c.ARadius = A.rad; c.BRadius = B.rad;
+    c.Rbar = ci.Rbar; c.mbar = ci.mbar;
+    c.AMat = A.mat; c.BMat = B.mat;
+    c.AFamily = d.owner_family ? (int)d.owner_family[A.owner] : 0;
+    c.BFamily = d.owner_family ? (int)d.owner_family[B.owner] : 0;
+    c.AGeo = swap ? j : (uint32_t)s;
+    c.BGeo = swap ? (uint32_t)s : j;
+    c.Estar = p.Estar; c.Gstar = p.Gstar; c.beta = p.beta; c.mu = p.mu;
+    c.crr = crr_tab[pk];
+    c.nu = (R)d.pair_nu[pk];
+    const bool on = Model::engaged(c, wc, par);
+    if (on) Model::eval(c, wc, par, Fo, Fr);
+    if (swap) {
+        Fo = -Fo;
+        Fr = -Fr;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if ((Model::odd >> q) & 1u) wc[q] = -wc[q];
+    }
+    arm = swap ? armB : armA;
+    overlap = ci.delta;
+    return on;
+}
+
+// The listed entries of sphere s through a contact model (model_entry): sums of the
+// forces and torques on s's owner, and (MODE_STEP) the entries' wildcards, zero where
+// a pair does not interact (the contact has vanished).
+template <class F, bool CLUMPS, int MODE, class Model>
+__device__ __forceinline__ void pair_sums_model(const Dev<F> &d, const SphereK<F> &me, const Scene &sc, int64_t s,
+                                                int n, int sp, int hp, int lc, V3<typename F::R> &Fs,
+                                                V3<typename F::R> &Ts)
+{
+    using R = typename F::R;
+    using H = typename HistVec<R>::T;
+    const uint32_t *prow = d.lists.partner[lc];
+    const H *hin = d.lists.hist[hp];
+    H *hout = d.lists.hist[hp ^ 1];
+    constexpr bool WILD = Model::n_wildcards > 4;
+    const H *win = WILD ? d.lists.wild[hp] : nullptr;
+    H *wout = WILD ? d.lists.wild[hp ^ 1] : nullptr;
+    for (int k = 0; k < n; ++k) {
+        const int64_t e = (int64_t)k * d.Np + s;
+        const uint32_t j = prow[e];
+        R wc[8];
+        {
+            const H a = hin[e];
+            wc[0] = (R)a.x; wc[1] = (R)a.y; wc[2] = (R)a.z; wc[3] = (R)a.w;
+            if constexpr (WILD) {
+                const H b = win[e];
+                wc[4] = (R)b.x; wc[5] = (R)b.y; wc[6] = (R)b.z; wc[7] = (R)b.w;
+            } else {
+                wc[4] = wc[5] = wc[6] = wc[7] = R(0);
+            }
+        }
+        V3<R> Fc, Fr, arm;
+        R ov;
+        const bool on = model_entry<F, CLUMPS, Model>(d, me, sc, s, j, sp, wc, Fc, Fr, arm, ov);
+        if (on) {
+            Fs = Fs + Fc;
+            Ts = Ts + cross(arm, Fc);
+            Ts = Ts + cross(arm, Fr);
+        }
+        if (MODE == MODE_STEP) {
+            if (!on) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) wc[q] = R(0);
+            }
+            H a;
+            a.x = wc[0]; a.y = wc[1]; a.z = wc[2]; a.w = wc[3];
+            hout[e] = a;
+            if constexpr (WILD) {
+                H b;
+                b.x = wc[4]; b.y = wc[5]; b.z = wc[6]; b.w = wc[7];
+                wout[e] = b;
+            }
+        }
+    }
+}
+
+template <class F, bool CLUMPS, int MODE, bool ROLL = false, int MODEL = FORCE_MODEL_BUILTIN>
 __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_known, uint32_t j0_known, int sp,
                                              int hp, int lc, double *eval_F, double *eval_T)
 {
@@ -923,9 +1204,16 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
         scene = d.owner_scene[o];
     }
-    if (act)
-        pair_sums<F, CLUMPS, MODE, ROLL>(d, me, d.scenes[scene], s, n,
-                                   n_known >= 0 ? j0_known : (n > 0 ? d.lists.partner[lc][s] : 0u), sp, hp, lc, Fs, Ts);
+    if (act) {
+        if constexpr (MODEL == FORCE_MODEL_HERTZ_MINDLIN)
+            pair_sums_model<F, CLUMPS, MODE, ModelHertzMindlin>(d, me, d.scenes[scene], s, n, sp, hp, lc, Fs, Ts);
+        else if constexpr (MODEL == FORCE_MODEL_BONDED_BREAKAGE)
+            pair_sums_model<F, CLUMPS, MODE, ModelBondedBreakage>(d, me, d.scenes[scene], s, n, sp, hp, lc, Fs, Ts);
+        else
+            pair_sums<F, CLUMPS, MODE, ROLL>(d, me, d.scenes[scene], s, n,
+                                             n_known >= 0 ? j0_known : (n > 0 ? d.lists.partner[lc][s] : 0u), sp, hp,
+                                             lc, Fs, Ts);
+    }
     if (CLUMPS) {
         // segmented suffix sums over the owner's consecutive lanes; the head lane ends
         // with the owner's total (fixed tree order: deterministic)
@@ -963,15 +1251,15 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
 // LEAN = 1 compiles the kernel for 5 resident blocks of CONTACT_BLOCK_MAX threads per SM
 // (96 registers, some spilled to the L1-cached local memory) instead of 4: more
 // warps to hide the latency of the gathers, chosen by the autotuner where it pays.
-template <class F, bool CLUMPS, int MODE, int LEAN = 0, bool ROLL = false>
+template <class F, bool CLUMPS, int MODE, int LEAN = 0, bool ROLL = false, int MODEL = FORCE_MODEL_BUILTIN>
 __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
 {
     DevStatus *stp = d.status;
     if (MODE == MODE_STEP && (stp->halt || stp->list_stale)) return;
     const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
     if (MODE == MODE_EVAL) {
-        contact_slot<F, CLUMPS, MODE, ROLL>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, -1, 0u, sp, hp, lc,
-                                            eval_F, eval_T);
+        contact_slot<F, CLUMPS, MODE, ROLL, MODEL>(d, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, -1, 0u, sp, hp,
+                                                   lc, eval_F, eval_T);
         return;
     }
     // the counter never exceeds the slots (or 32-slot groups); the clamp keeps every
@@ -982,8 +1270,8 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
     if (CLUMPS) {
         const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
         for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += warps)
-            contact_slot<F, CLUMPS, MODE, ROLL>(d, ((int64_t)act[w].x << 5) + (threadIdx.x & 31), -1, 0u, sp, hp,
-                                                lc, eval_F, eval_T);
+            contact_slot<F, CLUMPS, MODE, ROLL, MODEL>(d, ((int64_t)act[w].x << 5) + (threadIdx.x & 31), -1, 0u, sp,
+                                                       hp, lc, eval_F, eval_T);
     } else {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -991,7 +1279,7 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
         for (; t < nw; t += stride) {
             // the next work entry is read while this one is evaluated
             const uint4 next = t + stride < nw ? act[t + stride] : a;
-            contact_slot<F, CLUMPS, MODE, ROLL>(d, (int64_t)a.x, (int)a.y, a.z, sp, hp, lc, eval_F, eval_T);
+            contact_slot<F, CLUMPS, MODE, ROLL, MODEL>(d, (int64_t)a.x, (int)a.y, a.z, sp, hp, lc, eval_F, eval_T);
             a = next;
         }
     }
@@ -1633,6 +1921,58 @@ __global__ void __launch_bounds__(128) k_contacts(Dev<F> d, double *ov, double *
         hi[3 * e + 0] = (double)ut.x; hi[3 * e + 1] = (double)ut.y; hi[3 * e + 2] = (double)ut.z;
         ag[e] = (double)age;
         rf[3 * e + 0] = (double)Fr.x; rf[3 * e + 1] = (double)Fr.y; rf[3 * e + 2] = (double)Fr.z;
+    }
+}
+
+// Read-back through a contact model: every owned entry (canonical sphere pairs and wall
+// entries) at the current state with the model's engagement (en: 1 / 0), overlap, force
+// on the lower sphere, contact point, wildcards after the update (wc: 8 per entry) and
+// torque-only force.
+template <class F, bool CLUMPS, class Model>
+__global__ void __launch_bounds__(128) k_contacts_model(Dev<F> d, double *ov, double *fo, double *pt, double *wco,
+                                                        double *rf, double *en)
+{
+    using R = typename F::R;
+    using H = typename HistVec<R>::T;
+    DevStatus *stp = d.status;
+    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.N) return;
+    uint32_t o = d.sph_owner[s];
+    if (o == 0xffffffffu) return;
+    SphereK<F> me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
+    const Scene &sc = d.scenes[d.owner_scene[o]];
+    const bool act = d.st.active[sp][o];
+    const int n = d.lists.cnt[lc][s];
+    for (int k = 0; k < n; ++k) {
+        int64_t e = (int64_t)k * d.Np + s;
+        uint32_t j = d.lists.partner[lc][e];
+        en[e] = 0.0;
+        if (!act || (!(j & WALL_BIT) && j < (uint32_t)s)) continue;
+        R wc[8];
+        const H a = d.lists.hist[hp][e];
+        wc[0] = (R)a.x; wc[1] = (R)a.y; wc[2] = (R)a.z; wc[3] = (R)a.w;
+        if (d.lists.wild[0]) {
+            const H b = d.lists.wild[hp][e];
+            wc[4] = (R)b.x; wc[5] = (R)b.y; wc[6] = (R)b.z; wc[7] = (R)b.w;
+        } else {
+            wc[4] = wc[5] = wc[6] = wc[7] = R(0);
+        }
+        V3<R> Fc, Fr, arm;
+        R overlap;
+        if (!model_entry<F, CLUMPS, Model>(d, me, sc, s, j, sp, wc, Fc, Fr, arm, overlap)) continue;
+        en[e] = 1.0;
+        ov[e] = (double)overlap;
+        const V3<double> pa = F::absolute(me.p, sc, d.Ld);
+        for (int q = 0; q < 3; ++q) {
+            const double rl = q == 0 ? (double)me.rl.x : (q == 1 ? (double)me.rl.y : (double)me.rl.z);
+            const double am = q == 0 ? (double)arm.x : (q == 1 ? (double)arm.y : (double)arm.z);
+            const double pq = q == 0 ? pa.x : (q == 1 ? pa.y : pa.z);
+            pt[3 * e + q] = (pq - rl) + am;
+        }
+        fo[3 * e + 0] = (double)Fc.x; fo[3 * e + 1] = (double)Fc.y; fo[3 * e + 2] = (double)Fc.z;
+        rf[3 * e + 0] = (double)Fr.x; rf[3 * e + 1] = (double)Fr.y; rf[3 * e + 2] = (double)Fr.z;
+        for (int q = 0; q < 8; ++q) wco[8 * e + q] = (double)wc[q];
     }
 }
 

@@ -22,6 +22,8 @@ OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_CAPACITY, ERR_DIVERGED, ERR_TIMEOUT, ERR_O
 PRECISION = {"fp64": 0, "voxel_fp32": 1}
 SCHEDULE = {"every_step": 0, "velocity_bound": 1, "learned": 2}
 PROP_COR, PROP_MU, PROP_CRR = 0, 1, 2
+MODEL = {"default": 0, "hertz_mindlin": 1, "bonded_breakage": 2}
+BREAKAGE_PARAMS = ("tension", "cohesion", "eta", "damping")
 WALL_PLANE, WALL_CYLINDER, WALL_CONE = 0, 1, 2
 
 
@@ -90,6 +92,8 @@ def _sigs(L):
         "dem_get_listed_wall_pairs": [P, I64, P, P, P], "dem_get_owner_forces": [P, I64, I64, P, P],
         "dem_set_history": [P, I64, P, P, P], "dem_set_history_age": [P, I64, P, P, P, P],
         "dem_get_contact_rolling": [P, I64, P, P, P],
+        "dem_set_force_model": [P, I32, P, I32], "dem_set_contact_wildcards": [P, I64, P, P, P],
+        "dem_get_contact_wildcards": [P, I64, P, P],
         "dem_set_family": [P, I64, I64, P], "dem_set_family_motion": [P, I32, P, P],
         "dem_set_family_contacts": [P, I32, I32, I32], "dem_set_active_box": [P, P, P, I32, I32], "dem_get_stats": [P, P], "dem_get_diagnostics": [P, P],
         "dem_save_state": [P, P, SZ, P], "dem_load_state": [P, P, SZ],
@@ -439,6 +443,30 @@ class World:
         else:
             self._c(self.L.dem_set_history_age(self.h, len(i), _p(i), _p(j), _p(ut), _p(_f64(age))))
 
+    # ---- contact force models
+    def set_force_model(self, model, params=None):
+        """model: "default", "hertz_mindlin" (the default through the functor path) or
+        "bonded_breakage" with params {tension, cohesion, eta, damping}."""
+        par = None
+        if model == "bonded_breakage":
+            par = np.array([float(params[k]) for k in BREAKAGE_PARAMS], np.float64)
+        self._c(self.L.dem_set_force_model(self.h, MODEL[model], _p(par) if par is not None else None,
+                                           0 if par is None else len(par)))
+
+    def set_contact_wildcards(self, i, j, wc):
+        i = np.ascontiguousarray(i, np.int64); j = np.ascontiguousarray(j, np.int64)
+        wc = _f64(wc).reshape(-1, 4)
+        self._c(self.L.dem_set_contact_wildcards(self.h, len(i), _p(i), _p(j), _p(wc)))
+
+    def contact_wildcards(self):
+        cnt = C.c_int64()
+        st = self.L.dem_get_contact_wildcards(self.h, 0, C.byref(cnt), None)
+        if st not in (OK, ERR_CAPACITY):
+            self._c(st)
+        wc = np.empty((cnt.value, 8))
+        self._c(self.L.dem_get_contact_wildcards(self.h, cnt.value, C.byref(cnt), _p(wc)))
+        return wc
+
     # ---- family tags
     def set_family(self, first, family):
         f = np.ascontiguousarray(family, np.uint8)
@@ -519,6 +547,8 @@ class World:
                 self.set_wall_spin(wid, om)
         for t in scene.templates:
             self.add_clump_template(t.rel_xyz, t.radii, t.mats, float(t.mass), t.moi)
+        if getattr(scene, "force_model", None) not in (None, "default"):
+            self.set_force_model(scene.force_model, getattr(scene, "model_params", None))
         fm = getattr(scene, "family_motion", None) or {}
         for f, (vel, om) in fm.items():
             self.set_family_motion(f, vel, om)

@@ -826,3 +826,91 @@ def test_active_box_leaves_the_active_region_bit_identical():
     x = a.owner_state()[0]
     assert np.array_equal(x[~inside], x0[~inside])
     assert np.any(x[inside] != x0[inside])
+
+
+# ----------------------------------------------------------------------------- contact force models
+
+@pytest.mark.parametrize("precision,crr", [("fp64", 0.0), ("fp64", 0.08), ("voxel_fp32", 0.0)])
+def test_functor_default_model_equals_the_builtin_kernel(precision, crr):
+    """The default model through the functor interface (Sec. 4.2's custom-model route,
+    pairs evaluated with A the lower id on both sides) gives the built-in kernel's bits."""
+    s = dense_scene(n=800, seed=51, vel=0.4)
+    if crr:
+        s = with_rolling(s, crr)
+    a = dem.World.from_scene(s, precision=precision, schedule="velocity_bound")
+    b = dem.World.from_scene(dataclasses.replace(s, force_model="hertz_mindlin"), precision=precision,
+                             schedule="velocity_bound")
+    for _ in range(3):
+        a.step(100)
+        b.step(100)
+        for xa, xb in zip(a.owner_state(), b.owner_state()):
+            assert np.array_equal(xa, xb)
+    ca, cb = a.contacts(), b.contacts()
+    for k in ("i", "j", "force", "history"):
+        assert np.array_equal(ca[k], cb[k]), k
+
+
+BREAK = dict(tension=-2e4, cohesion=2e4, eta=0.1, damping=0.01)
+
+
+def bonded_lattice(seed=61):
+    """A dense lattice whose overlapping neighbours are bonded at their initial overlap
+    (unloaded), with random velocities that stretch, shear and break bonds (Sec. 6.3)."""
+    return dataclasses.replace(dense_scene(n=343, seed=seed, vel=0.3), force_model="bonded_breakage",
+                               model_params=BREAK)
+
+
+def bond_initial_contacts(w, ow):
+    c = w.contacts()
+    pair = c["j"] >= 0
+    i, j, ov = c["i"][pair], c["j"][pair], c["overlap"][pair]
+    wc = np.zeros((len(i), 4))
+    wc[:, 0] = 1.0
+    wc[:, 1] = ov
+    w.set_contact_wildcards(i, j, wc)
+    for o in ow:
+        o.set_wildcards(i, j, wc)
+    return len(i)
+
+
+def test_fp64_bonded_breakage_matches_oracle():
+    """The bonded, breakable contact (Sec. 6.3) on the GPU against the oracle at 1e-9:
+    one step from the GPU's own states (history, ages and bond wildcards synced) and the
+    free-running run, while bonds stretch across gaps and break."""
+    s = bonded_lattice()
+    w = dem.World.from_scene(s, precision="fp64", margin=5e-5)
+    ow = oracle.OracleWorld(s, threads=oracle_threads())
+    free = oracle.OracleWorld(s, threads=oracle_threads())
+    nb = bond_initial_contacts(w, (ow, free))
+    assert nb > 500
+    worst = {}
+    for k in (1, 100, 200):
+        if k > 1:
+            w.step(k - 1)
+            assert ow.step(k - 1) == 0 and free.step(k - 1) == 0
+        c0 = w.contacts()
+        wc0 = w.contact_wildcards()
+        w.step(1)
+        assert ow.step(1) == 0 and free.step(1) == 0
+        st, _ = state_close(w, free, TOL64)
+        worst = {a: max(worst.get(a, 0.0), b) for a, b in st.items()}
+        # one step from the GPU's own state: history, age and bond wildcards carried in
+        ow.x[:], ow.q[:], ow.v[:], ow.wb[:] = w.owner_state()
+        ow.set_history(c0["i"], c0["j"], c0["history"], age=wc0[:, 3])
+        pair = c0["j"] >= 0
+        ow.set_wildcards(c0["i"][pair], c0["j"][pair], wc0[pair][:, 4:8])
+        gc = w.contacts()
+        gw = w.contact_wildcards()
+        Fg, Tg = w.owner_forces()
+        Fo, To, oc = ow.eval()
+        assert np.array_equal(gc["i"], oc["i"]) and np.array_equal(gc["j"], oc["j"])
+        fs = np.abs(oc["force"]).max(axis=1, keepdims=True) + 1e-300
+        assert rel_err(gc["force"], oc["force"], fs) < TOL64
+        assert np.array_equal(gw[:, 4] > 0, np.asarray(oc["wc"])[:, 0] > 0)        # bond states agree
+        assert rel_err(Fg, Fo, owner_scale(ow, oc, Fo)) < TOL64
+        assert rel_err(Tg, To, torque_scale(ow, oc)) < TOL64
+    assert max(worst.values()) < TOL64, worst
+    bonds = np.sum(free.wildcards()[:, 0] > 0)
+    broken = nb - bonds
+    print("bonded breakage: bonds", nb, "left", bonds, "free-running", worst)
+    assert 0 < broken < nb

@@ -1109,3 +1109,86 @@ def test_bonded_cluster_conserves_linear_momentum():
     p1 = (ow.mass[:, None] * ow.v).sum(axis=0)
     scale_p = (ow.mass[:, None] * np.abs(v)).sum()
     assert np.all(np.abs(p1 - p0) <= 1e-12 * scale_p)
+
+
+# ----------------------------------------------------------------------------- mesh facets
+
+def facet(tri, p=(0, 0, 0), omega=(0, 0, 0), mat=0):
+    return dict(type=oracle.WALL_TRIANGLE, mat=mat, p=np.asarray(p, np.float64), n=np.zeros(3),
+                omega=np.asarray(omega, np.float64), tri=np.asarray(tri, np.float64).reshape(9))
+
+
+def sampled_distance(c, tri, n=400):
+    """Distance from c to a triangle by dense barycentric sampling (brute force)."""
+    a, b, cc = np.asarray(tri, np.float64).reshape(3, 3)
+    u, v = np.meshgrid(np.linspace(0, 1, n), np.linspace(0, 1, n))
+    keep = u + v <= 1
+    pts = a + u[keep, None] * (b - a) + v[keep, None] * (cc - a)
+    return float(np.min(np.linalg.norm(pts - c, axis=1)))
+
+
+def test_facet_gap_is_the_distance_to_the_closest_point_in_every_region():
+    """Sec. 2.4 meshes: a sphere's gap to a facet is its centre's distance to the facet's
+    closest point, whichever region (face, one of three edges, one of three vertices) that
+    point lies in; brute-force sampling of the triangle agrees."""
+    tri = [[0.0, 0.0, 0.0], [4e-3, 0.0, 0.0], [0.5e-3, 3e-3, 0.0]]
+    R = 1e-3
+    rng = np.random.default_rng(3)
+    centres = np.concatenate([rng.uniform([-2e-3, -2e-3, -1.5e-3], [6e-3, 5e-3, 1.5e-3], size=(60, 3)),
+                              [[-0.4e-3, -0.3e-3, 0.2e-3], [4.5e-3, -0.2e-3, 0.1e-3], [0.4e-3, 3.4e-3, -0.1e-3],
+                               [2e-3, -0.6e-3, 0.0], [1.5e-3, 1e-3, 0.6e-3]]])
+    for c in centres:
+        d = sampled_distance(c, tri)
+        s = make_scene([c], walls=[facet(tri)])
+        ow = oracle.OracleWorld(s)
+        F, T, cs = ow.eval()
+        if d < R - 2e-5:
+            assert len(cs) == 1
+            assert cs["overlap"][0] == pytest.approx(R - d, abs=2e-5)
+            nrm = np.array(cs["normal"][0])
+            q = c - d * nrm                               # back to the facet
+            assert sampled_distance(q, tri) < 2e-5
+        elif d > R + 2e-5:
+            assert len(cs) == 0
+
+
+def test_sphere_resting_on_a_facet_settles_to_the_hertz_overlap():
+    """A horizontal facet carries a sphere like a plane (Rbar = R): the static overlap is
+    (3 m g / (4 E* sqrt(R)))^(2/3)."""
+    R, E, nu = 1e-3, 1e7, 0.3
+    tri = [[-5e-3, -5e-3, 0.0], [5e-3, -5e-3, 0.0], [0.0, 6e-3, 0.0]]
+    s = make_scene([[0.0, 0.0, R]], walls=[facet(tri)], g=(0, 0, -9.81), h=2e-6,
+                   mat=one_material(E=E, nu=nu, e=0.3, mu=0.3))
+    ow = oracle.OracleWorld(s)
+    assert ow.step(150000) == 0
+    m = ow.mass[0]
+    want = (3 * m * 9.81 / (4 * E / (2 * (1 - nu * nu)) * math.sqrt(R))) ** (2 / 3)
+    assert R - ow.x[0, 2] == pytest.approx(want, rel=1e-6)
+
+
+def test_a_turning_facet_moves_by_its_rotation():
+    """A facet turning with omega about p sits at p + R(omega t)(v - p) at time t: a
+    resting sphere's gap follows the analytic distance to the rotated triangle, and the
+    facet drags a touching sphere along its surface velocity omega x (c - p)."""
+    tri = np.array([[3e-3, -2e-3, 0.0], [9e-3, -2e-3, 0.0], [6e-3, 4e-3, 0.0]])
+    w = np.array([0.0, 0.0, 20.0])
+    c = np.array([[5e-3, 3e-3, 0.9e-3]])
+    s = make_scene(c, walls=[facet(tri, omega=w)], h=1e-5, family=np.array([1]),
+                   family_motion={1: ((0, 0, 0), (0, 0, 0))})
+    ow = oracle.OracleWorld(s)
+    for n in (0, 40, 90):
+        if n:
+            assert ow.step(n - ow._w.step) == 0
+        t = ow._w.step * 1e-5
+        th = 20.0 * t
+        Rz = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+        rot = tri @ Rz.T
+        d = sampled_distance(c[0], rot, n=600)
+        F, T, cs = ow.eval()
+        if d < 1e-3:
+            assert cs["overlap"][0] == pytest.approx(1e-3 - d, abs=2e-5)
+            # the facet's surface velocity at the contact point enters the tangential force
+            u_b = np.cross(w, np.array(cs["point"][0]))
+            assert np.linalg.norm(u_b) > 0
+        else:
+            assert len(cs) == 0
