@@ -51,8 +51,10 @@ def parse():
     ap.add_argument("--window-start", type=int, default=-1,
                     help="step at which the warm-up starts (-1: the tuning step when the warm-up and "
                          "timed steps fit in the configuration's steps after it, else as late as they fit)")
-    ap.add_argument("--workload", default="column", choices=["column", "drum", "hopper", "batch"],
+    ap.add_argument("--workload", default="column", choices=["column", "drum", "hopper", "batch", "mixer"],
                     help="column: the headline settling column; the others run one configuration at full size")
+    ap.add_argument("--clump", default="sphere", choices=["sphere", "rod3", "six"],
+                    help="mixer elements: single spheres, three-sphere or six-sphere clumps")
     ap.add_argument("--set-tuning", default="",
                     help="tuning fields applied after the autotuner, e.g. integrate_staged=1,contact_block=64")
     ap.add_argument("--tune-cache", default=None,
@@ -559,6 +561,25 @@ def run_scale(args, device, rank=0, world=1):
             w.close()
         out.update(n_spheres=n_sph, steps=steps, schedules=res, value=res["learned"]["value"],
                    ms=res["learned"]["ms"])
+    elif args.workload == "mixer":
+        # Sec. 5's bladed mixer: 2,892 facets turning at 2 pi rad/s, elements released from
+        # rest above it, dt = 5e-7 s
+        scene = W.mixer(n=args.n if args.n != 4_000_000 else 2_000_000, clump=args.clump)
+        w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
+        out["setup_s"] = time.perf_counter() - t0
+        out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache) if args.tune_steps > 0 else w.tuning()
+        w.step(args.warmup)
+        s0 = w.stats()
+        with ClockSampler(device) as clk:
+            ms = timed(w.step, w.stream(), steps, "timed_mixer")
+        s1 = w.stats()
+        n_sph = scene.n_sphere
+        out.update(n_spheres=n_sph, n_elements=scene.n_owner, clump=args.clump, facets=2892, ms=ms, steps=steps,
+                   clocks=clk.summary(), rebuilds=s1["rebuilds"] - s0["rebuilds"],
+                   fallbacks=s1["audit_fallbacks"] - s0["audit_fallbacks"], listed_pairs=s1["listed_pairs"],
+                   wall_pairs=s1["wall_pairs"], contacts=s1["active_contacts"],
+                   value=n_sph * steps / (ms / 1000.0), element_radius_m=scene.meta["element_radius"])
+        w.close()
     elif args.workload == "batch":
         from paper_2311_04648_gb300 import shard
         all_scenes = W.batch_scenes(512)

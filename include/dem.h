@@ -168,6 +168,20 @@ dem_status dem_add_cylinder(dem_world *w, const double c[3], const double axis[3
  * side (the conical hopper wall). */
 dem_status dem_add_cone_segment(dem_world *w, const double p[3], const double axis[3], double r0,
                                 double z0, double r1, double z1, int32_t mat, int32_t *id);
+/* A rigid triangle mesh (Sec. 2.4: meshes in the geometry hierarchy; Sec. 5: the bladed
+ * mixer): n_facets two-sided facets, vertices[9 n] (three xyz points per facet, global
+ * frame, SI units, at time 0), one material, turning with the prescribed angular
+ * velocity omega[3] (world frame; zero: static) about axis_point[3], so that at time t a
+ * vertex v sits at axis_point + R(omega t)(v - axis_point).  Each facet is a wall
+ * (ids first_id .. first_id + n_facets - 1; contacts report j = -1 - id); a sphere's
+ * gap to it is its centre's distance to the facet's closest point, and the facet's
+ * surface velocity omega x (c - axis_point) enters the contact.  Facets are found by
+ * binning them into the detection cells at every list build (not by the per-sphere wall
+ * loop), and their motion is added to the audited displacement bound.  Add a scene's
+ * meshes after its other walls (DEM_ERR_STATE otherwise).  Degenerate facets:
+ * DEM_ERR_ARG. */
+dem_status dem_add_mesh(dem_world *w, int64_t n_facets, const double *vertices, int32_t mat,
+                        const double axis_point[3], const double omega[3], int32_t *first_id);
 /* Prescribed rigid spin of wall `id` about its own point p with angular velocity
  * omega[3] (world frame); only walls whose geometry is invariant under the spin are
  * accepted (planes about their normal, cylinders and cones about their axis). */
@@ -259,6 +273,13 @@ typedef struct {
                                       touching pair is listed either way, so results are
                                       the same bits.  dem_get_tuning reports the margin in
                                       use.  Ignored by the every-step schedule.            */
+    int32_t contact_integrates;    /* worlds of single spheres with the two-kernel step
+                                      (fused_block 0), no rolling resistance and the
+                                      built-in contact model: 1 = the contact kernel also
+                                      integrates the owners with listed partners (no
+                                      per-owner force array), the integration kernel the
+                                      others; 0 = the integration kernel integrates every
+                                      owner.  The same bits either way; ignored elsewhere  */
 } dem_tuning;
 
 dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);

@@ -23,6 +23,7 @@ thread_local std::string g_err;
 struct WallSetup {
     int type, mat;
     double p[3], n[3], r0, z0, r1, z1, omega[3];
+    double tri[9];
 };
 
 struct TemplateSetup {
@@ -310,7 +311,12 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
         g.v_errf = (float)sc.v_err;
         if ((double)g.v_errf > sc.v_err) g.v_errf = std::nextafter(g.v_errf, -INFINITY);
         g.wall_begin = (int)m.walls.size();
-        g.wall_count = (int)sc.walls.size();
+        // mesh facets come after the scene's other walls: the narrow phase's wall loop
+        // covers the others, the facets are found through their cell bins
+        g.wall_count = 0;
+        for (auto &ws : sc.walls) g.wall_count += ws.type != WALL_TRIANGLE ? 1 : 0;
+        g.facet_begin = g.wall_begin + g.wall_count;
+        g.facet_count = (int)sc.walls.size() - g.wall_count;
         g.has_sink = sc.has_sink ? 1 : 0;
         for (int a = 0; a < 3; ++a) { g.sink_p[a] = sc.sink_p[a]; g.sink_n[a] = sc.sink_n[a]; }
         const int nm = (int)sc.E.size();
@@ -363,6 +369,8 @@ dem_status build_model(WorldImpl &W, HostModel &m, std::string &err)
             w.mat = g.mat_base + ws.mat;
             for (int a = 0; a < 3; ++a) { w.p[a] = ws.p[a]; w.n[a] = ws.n[a]; w.omega[a] = ws.omega[a]; }
             w.r0 = ws.r0; w.z0 = ws.z0; w.r1 = ws.r1; w.z1 = ws.z1;
+            w.scene = (int)si;
+            for (int q = 0; q < 9; ++q) { w.tri[q] = ws.tri[q]; w.cur[q] = ws.tri[q]; }
             for (int a = 0; a < 3; ++a) { w.pf[a] = (float)ws.p[a]; w.nf[a] = (float)ws.n[a]; }
             w.r0f = (float)ws.r0; w.r1f = (float)ws.r1; w.z0f = (float)ws.z0; w.z1f = (float)ws.z1;
             {
@@ -596,6 +604,8 @@ static dem_status add_wall(dem_world *w, const WallSetup &ws, int32_t *id)
 {
     SceneSetup &sc = S(w);
     if (ws.mat < 0 || ws.mat >= (int)sc.E.size()) return fail(w, DEM_ERR_ARG, "bad material id");
+    if (ws.type != WALL_TRIANGLE && !sc.walls.empty() && sc.walls.back().type == WALL_TRIANGLE)
+        return fail(w, DEM_ERR_STATE, "add a scene's meshes after its other walls");
     sc.walls.push_back(ws);
     if (id) *id = (int32_t)sc.walls.size() - 1;
     return DEM_OK;
@@ -1025,6 +1035,37 @@ dem_status dem_get_owner_forces(dem_world *w, int64_t first, int64_t n, double *
     const int64_t b = owner_base(w) + first;
     if (force) std::memcpy(force, F.data() + 3 * b, 3 * n * sizeof(double));
     if (torque) std::memcpy(torque, T.data() + 3 * b, 3 * n * sizeof(double));
+    return DEM_OK;
+}
+
+// ---------------------------------------------------------------- meshes (Sec. 2.4)
+
+dem_status dem_add_mesh(dem_world *w, int64_t n_facets, const double *vertices, int32_t mat, const double axis_point[3],
+                        const double omega[3], int32_t *first_id)
+{
+    CHECK_SETUP(w);
+    if (n_facets <= 0 || !vertices || !axis_point || !omega) return fail(w, DEM_ERR_ARG, "bad mesh arrays");
+    if (!finite3(axis_point) || !finite3(omega)) return fail(w, DEM_ERR_ARG, "non-finite axis point or omega");
+    SceneSetup &sc = S(w);
+    if (mat < 0 || mat >= (int)sc.E.size()) return fail(w, DEM_ERR_ARG, "bad material id");
+    for (int64_t f = 0; f < n_facets; ++f) {
+        const double *v = vertices + 9 * f;
+        for (int q = 0; q < 9; ++q)
+            if (!std::isfinite(v[q])) return fail(w, DEM_ERR_ARG, "non-finite facet vertex");
+        const double e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+        const double e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+        const double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        if (!((c[0] * c[0] + c[1] * c[1] + c[2] * c[2]) > 0.0)) return fail(w, DEM_ERR_ARG, "degenerate facet");
+    }
+    if (first_id) *first_id = (int32_t)sc.walls.size();
+    for (int64_t f = 0; f < n_facets; ++f) {
+        WallSetup ws{};
+        ws.type = WALL_TRIANGLE;
+        ws.mat = mat;
+        for (int a = 0; a < 3; ++a) { ws.p[a] = axis_point[a]; ws.omega[a] = omega[a]; }
+        for (int q = 0; q < 9; ++q) ws.tri[q] = vertices[9 * f + q];
+        sc.walls.push_back(ws);
+    }
     return DEM_OK;
 }
 

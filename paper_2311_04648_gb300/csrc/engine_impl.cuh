@@ -133,6 +133,7 @@ public:
         if ((s = alloc(ms, m_.mat_scene.size(), err))) return s;
         if ((s = alloc(ml, m_.mat_local.size(), err))) return s;
         d_.scenes = scenes; d_.walls = walls; d_.pairs = pairs; d_.pairs_f = pairs_f;
+        walls_dev_ = walls;
         d_.mat_scene = ms; d_.mat_local = ml;
         {
             double *crr;
@@ -198,6 +199,7 @@ public:
         }
         if ((s = alloc(db_.sorted_owner, Nk, err))) return s;
         if ((s = alloc(db_.n_valid, 1, err))) return s;
+        if ((s = setup_facets(err))) return s;
 
         // constants
         std::vector<R4> inv_moi(M);
@@ -289,7 +291,12 @@ public:
         }
         DevStatus h{};
         h.disp_slack = F::voxel ? 4.0 * std::ldexp(1.0, std::ilogb(m_.Lv) - 23) : 0.0;
+        // a turning mesh moves the facets between a list's snapshot and its use: its
+        // largest surface displacement per step counts against the margin like the
+        // owners' own
+        h.disp_slack += mesh_slack_;
         h.disp_slack_f = (float)h.disp_slack;
+        if ((double)h.disp_slack_f < h.disp_slack) h.disp_slack_f = std::nextafter(h.disp_slack_f, INFINITY);
         h.beta_cur = h.beta_next = beta_;
         for (int64_t o = 0; o < M; ++o) {   // initial speed bound for the first cycle length
             double v2 = m_.v[3 * o] * m_.v[3 * o] + m_.v[3 * o + 1] * m_.v[3 * o + 1] + m_.v[3 * o + 2] * m_.v[3 * o + 2];
@@ -303,11 +310,75 @@ public:
             if ((s = upload_state(0, M, m_.x.data(), m_.q.data(), m_.v.data(), m_.wb.data(), act.data(), err)))
                 return s;
         }
+        pose_facets(sf_);
         if (N > 0) {
             rebuild_inline(sf_);
             if ((s = settle(err))) return s;
         }
         return DEM_OK;
+    }
+
+    // Mesh facets: their wall indices, a share of (cell, facet) pair slots each (enough
+    // for any pose: the facet's extent at most twice its largest vertex distance from its
+    // centroid, grown by the reach on both sides, in cells of the smallest edge), the
+    // snapshot vertices and the sort buffers; the largest surface displacement per step.
+    dem_status setup_facets(std::string &err)
+    {
+        std::vector<int> fw;
+        for (size_t k = 0; k < m_.walls.size(); ++k)
+            if (m_.walls[k].type == WALL_TRIANGLE) fw.push_back((int)k);
+        db_.n_facets = (int)fw.size();
+        mesh_slack_ = 0.0;
+        if (fw.empty()) return DEM_OK;
+        const double cell = m_.L_min;
+        const double reach = m_.r_max + m_.margin_max + 4.0 * cell;
+        std::vector<int64_t> off(fw.size() + 1, 0);
+        for (size_t f = 0; f < fw.size(); ++f) {
+            const Wall &w = m_.walls[fw[f]];
+            double c[3] = {0, 0, 0}, rho = 0.0, rp = 0.0;
+            for (int a = 0; a < 3; ++a) c[a] = (w.tri[a] + w.tri[3 + a] + w.tri[6 + a]) / 3.0;
+            for (int v = 0; v < 3; ++v) {
+                double dc = 0.0, dp = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    dc += (w.tri[3 * v + a] - c[a]) * (w.tri[3 * v + a] - c[a]);
+                    dp += (w.tri[3 * v + a] - w.p[a]) * (w.tri[3 * v + a] - w.p[a]);
+                }
+                rho = std::max(rho, std::sqrt(dc));
+                rp = std::max(rp, std::sqrt(dp));
+            }
+            const int64_t per = (int64_t)std::floor((2.0 * rho + 2.0 * reach) / cell) + 2;
+            off[f + 1] = off[f] + per * per * per;
+            const double wn = std::sqrt(w.omega[0] * w.omega[0] + w.omega[1] * w.omega[1] + w.omega[2] * w.omega[2]);
+            mesh_slack_ = std::max(mesh_slack_, 1.000001 * wn * rp * m_.scenes[w.scene].h);
+        }
+        const int64_t P = off.back();
+        dem_status s;
+        int *fwd;
+        int64_t *offd;
+        if ((s = alloc(fwd, (int64_t)fw.size(), err))) return s;
+        if ((s = alloc(offd, (int64_t)off.size(), err))) return s;
+        if ((s = up(fwd, fw.data(), (int64_t)fw.size(), err))) return s;
+        if ((s = up(offd, off.data(), (int64_t)off.size(), err))) return s;
+        db_.facet_wall = fwd;
+        db_.facet_off = offd;
+        if ((s = alloc(db_.tri_snap, 9 * (int64_t)fw.size(), err))) return s;
+        if ((s = alloc(db_.fkeys, P, err))) return s;
+        if ((s = alloc(db_.fvals, P, err))) return s;
+        if ((s = alloc(db_.fkeys_alt, P, err))) return s;
+        if ((s = alloc(db_.fvals_alt, P, err))) return s;
+        db_.fhist_cap = radix_hist_entries(P);
+        if ((s = alloc(db_.fhist, db_.fhist_cap, err))) return s;
+        db_.n_fpairs = P;
+        db_.fkeys_sorted = db_.fkeys;
+        db_.fvals_sorted = db_.fvals;
+        return DEM_OK;
+    }
+
+    // Current pose of the mesh facets (the state's step).
+    void pose_facets(cudaStream_t st)
+    {
+        if (db_.n_facets > 0)
+            k_facet_pose<F><<<grid(db_.n_facets, 128), 128, 0, st>>>(d_, walls_dev_, db_.facet_wall, db_.n_facets);
     }
 
     dem_status step(int64_t n, std::string &err) override
@@ -940,6 +1011,7 @@ public:
         if ((s = copy_sync(st_, &h, sizeof(h), cudaMemcpyHostToDevice, err))) return s;
         DEM_CU(cudaMemsetAsync(d_.audit, 0, AUDIT_SLOTS * AUDIT_STRIDE * sizeof(unsigned int), sf_));   // no maxima of an unfinished step
         recompact_current();
+        pose_facets(sf_);                    // the facets at the restored step
         DEM_CU(cudaStreamSynchronize(sf_));
         dirty_ = beta_blob != beta_;
         return DEM_OK;
@@ -1326,6 +1398,7 @@ private:
         tune_.integrate_staged = (t->integrate_staged && prepare_staged()) ? 1 : 0;
         tune_.contact_lean = t->contact_lean ? 1 : 0;
         tune_.fused_block = m_.clumps ? 0 : t->fused_block;
+        tune_.contact_integrates = (!m_.clumps && t->contact_integrates) ? 1 : 0;
         tune_.margin = 0.0;
         apply_margin(t->margin);
         return DEM_OK;
@@ -1447,10 +1520,10 @@ private:
                     if (std::sscanf(line, "{\"key\": \"%299[^\"]\", \"contact_block\": %d, \"integrate_block\": %d, "
                                           "\"narrow_block\": %d, \"detect_inline\": %d, \"cell_factor\": %lf, "
                                           "\"integrate_staged\": %d, \"contact_lean\": %d, \"fused_block\": %d, "
-                                          "\"margin\": %lf, \"step_ms\": %lf}",
+                                          "\"contact_integrates\": %d, \"margin\": %lf, \"step_ms\": %lf}",
                                     k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
                                     &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.fused_block,
-                                    &t.margin, &t.step_ms) == 11 &&
+                                    &t.contact_integrates, &t.margin, &t.step_ms) == 12 &&
                         key == k) {
                         best = t;
                         found = true;
@@ -1511,12 +1584,21 @@ private:
             t.step_ms = 0.0;
             if ((s = trial(t))) return s;
         }
-        // single spheres: forces and integration in one kernel, each of its block sizes
+        // single spheres: the contact kernel integrating the owners with partners (each
+        // contact build), then forces and integration in one kernel, each block size
         if (!m_.clumps) {
             const dem_tuning b3 = best;
+            for (int lean = 0; lean <= 1; ++lean) {
+                dem_tuning t = b3;
+                t.contact_integrates = 1;
+                t.contact_lean = lean;
+                t.step_ms = 0.0;
+                if ((s = trial(t))) return s;
+            }
             for (int fb : {64, 128, 256}) {
                 dem_tuning t = b3;
                 t.fused_block = fb;
+                t.contact_integrates = 0;
                 t.step_ms = 0.0;
                 if ((s = trial(t))) return s;
             }
@@ -1525,7 +1607,8 @@ private:
         for (double f : {1.0, 1.5, 2.0})
             if (f != b2.cell_factor)
                 if ((s = trial(dem_tuning{b2.contact_block, b2.integrate_block, b2.narrow_block, b2.detect_inline,
-                                          0.0, f, b2.integrate_staged, b2.contact_lean, b2.fused_block})))
+                                          0.0, f, b2.integrate_staged, b2.contact_lean, b2.fused_block, 0.0,
+                                          b2.contact_integrates})))
                     return s;
         // phase 4 (delayed schedules): smaller detection margins list fewer pairs that do
         // not touch, at the price of more rebuilds; the results are the same bits
@@ -1550,10 +1633,11 @@ private:
                 std::fprintf(f,
                              "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
                              "%d, \"detect_inline\": %d, \"cell_factor\": %.3f, \"integrate_staged\": %d, "
-                             "\"contact_lean\": %d, \"fused_block\": %d, \"margin\": %.17g, \"step_ms\": %.6f}\n",
+                             "\"contact_lean\": %d, \"fused_block\": %d, \"contact_integrates\": %d, "
+                             "\"margin\": %.17g, \"step_ms\": %.6f}\n",
                              key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
                              best.detect_inline, best.cell_factor, best.integrate_staged, best.contact_lean,
-                             best.fused_block, best.margin, best.step_ms);
+                             best.fused_block, best.contact_integrates, best.margin, best.step_ms);
                 std::fclose(f);
             }
         }
@@ -1752,6 +1836,15 @@ private:
                        st, &ks, &vs);
         k_clear_rows<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_);
         k_cellstart<F><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, ks, vs);
+        if (db_.n_facets > 0) {
+            // bin the facets at their pose of the snapshot and sort the pairs by cell
+            k_facet_bin<F><<<grid(db_.n_facets, 128), 128, 0, st>>>(d_, db_, m_.r_max);
+            uint32_t *fk, *fv;
+            radix_sort_u32(db_.fkeys, db_.fvals, db_.fkeys_alt, db_.fvals_alt, db_.n_fpairs, db_.key_bits, db_.fhist,
+                           db_.fhist_cap, st, &fk, &fv);
+            db_.fkeys_sorted = fk;
+            db_.fvals_sorted = fv;
+        }
         if (m_.clumps) k_narrow<F, true><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
         else k_narrow<F, false><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
     }
@@ -1850,6 +1943,9 @@ private:
         if (m_.clumps) {
             if (lean) k_contact<F, true, MODE_STEP, 1><<<g, b, 0, sf_>>>(d_, eF, eT);
             else k_contact<F, true, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
+        } else if (MODE == MODE_STEP && integ()) {
+            if (lean) k_contact<F, false, MODE_STEP, 1, false, FORCE_MODEL_BUILTIN, true><<<g, b, 0, sf_>>>(d_, eF, eT);
+            else k_contact<F, false, MODE_STEP, 0, false, FORCE_MODEL_BUILTIN, true><<<g, b, 0, sf_>>>(d_, eF, eT);
         } else {
             if (lean) k_contact<F, false, MODE_STEP, 1><<<g, b, 0, sf_>>>(d_, eF, eT);
             else k_contact<F, false, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
@@ -1858,11 +1954,17 @@ private:
 
     int contact_per_sm(int b)
     {
-        const int key = b * 2 + (tune_.contact_lean ? 1 : 0);
+        const int key = b * 4 + (tune_.contact_lean ? 1 : 0) + (integ() ? 2 : 0);
         if (key == occ_block_) return occ_per_sm_;
         int per_sm = 0;
         cudaError_t e;
-        if (m_.model == FORCE_MODEL_HERTZ_MINDLIN)
+        if (integ())
+            e = tune_.contact_lean
+                    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &per_sm, k_contact<F, false, MODE_STEP, 1, false, FORCE_MODEL_BUILTIN, true>, b, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &per_sm, k_contact<F, false, MODE_STEP, 0, false, FORCE_MODEL_BUILTIN, true>, b, 0);
+        else if (m_.model == FORCE_MODEL_HERTZ_MINDLIN)
             e = m_.clumps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                 &per_sm, k_contact<F, true, MODE_STEP, 0, false, FORCE_MODEL_HERTZ_MINDLIN>, b, 0)
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1892,6 +1994,12 @@ private:
     // blocks as the SMs hold streams tiles of owners through shared memory.
     void launch_integrate()
     {
+        const int ib = tune_.integrate_block;
+        if (integ()) {
+            // owners with listed partners were integrated by the contact kernel
+            k_integrate<F, false, true><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
+            return;
+        }
         if constexpr (F::voxel) {
             if (tune_.integrate_staged && d_.M > 0 && staged_per_sm_ > 0) {
                 const int smem = STAGES * StageLayout::bytes;
@@ -1902,13 +2010,18 @@ private:
                 return;
             }
         }
-        const int ib = tune_.integrate_block;
         if (m_.clumps) k_integrate<F, true><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
         else k_integrate<F, false><<<grid(d_.M, ib), ib, 0, sf_>>>(d_);
     }
 
     // Single spheres with the fused step chosen: one kernel for forces and integration.
     bool fused() const { return !m_.clumps && !m_.rolling && m_.model == FORCE_MODEL_BUILTIN && tune_.fused_block > 0; }
+    // Single spheres, two-kernel step: the contact kernel integrates the owners it holds.
+    bool integ() const
+    {
+        return !m_.clumps && !m_.rolling && m_.model == FORCE_MODEL_BUILTIN && tune_.fused_block == 0 &&
+               tune_.contact_integrates;
+    }
 
     // Contact wildcards of the world's contact model (4: those of the history vector).
     int model_wildcards() const
@@ -1938,6 +2051,7 @@ private:
             mark_end(sf_, m2);
         }
         k_audit<<<1, 32, 0, sf_>>>(st_, d_.audit);
+        pose_facets(sf_);
         if (collect_ && d_.M > 0)
             k_collect_step<F><<<grid(d_.M, 256), 256, 0, sf_>>>(d_, acc_lab_, obin_, cross_, win_start_, (float)beta_);
     }
@@ -1993,6 +2107,8 @@ private:
 
     HostModel m_;
     Dev<F> d_{};
+    Wall *walls_dev_ = nullptr;     // the walls (mesh facets' current pose written each step)
+    double mesh_slack_ = 0.0;       // largest facet displacement per step
     DetectBuffers db_{};
     DevStatus *st_ = nullptr;
     DevStatus *sth_ = nullptr;

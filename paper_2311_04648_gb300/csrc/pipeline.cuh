@@ -122,6 +122,7 @@ struct SphereK {
     typename F::Pos p;   // sphere centre
     V3<R> rl;            // centre minus owner centre of mass, world frame
     V3<R> v, w;          // owner linear velocity and world-frame angular velocity
+    R acc0, acc1;        // the fourth lanes of v and w (the audit accumulators)
     R rad, mass;
     float rlo;           // low word of the radius (voxel form)
     int mat;
@@ -146,6 +147,8 @@ __device__ __forceinline__ SphereK<F> load_sphere(const Dev<F> &d, int sp, uint3
     auto w4 = d.st.kv[sp][2 * o + 1];
     k.v = {v4.x, v4.y, v4.z};
     k.w = {w4.x, w4.y, w4.z};
+    k.acc0 = v4.w;
+    k.acc1 = w4.w;
     k.mass = mass;
     if constexpr (F::voxel && !CLUMPS) {
         k.rad = aux.rad;
@@ -1181,10 +1184,26 @@ __device__ __forceinline__ void pair_sums_model(const Dev<F> &d, const SphereK<F
     }
 }
 
-template <class F, bool CLUMPS, int MODE, bool ROLL = false, int MODEL = FORCE_MODEL_BUILTIN>
+template <class F, bool CLUMPS>
+__device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, int64_t o, int sp, bool act,
+                                               const typename F::Pos &po, typename F::R mass, typename F::R4 v4,
+                                               typename F::R4 w4, typename F::R4 q4, typename F::R im,
+                                               typename F::R4 ii, bool iso, const Scene &sc, V3<typename F::R> Fs,
+                                               V3<typename F::R> Ts, const typename F::Aux &aux, float &disp,
+                                               float &disp2, float &speed);
+__device__ __forceinline__ void audit_slots(unsigned int *audit, int64_t o, int lane, float disp, float disp2,
+                                            float speed);
+
+// INTEG (single spheres, MODE_STEP): the contact kernel also integrates the owner of the
+// slot, from the state it has already loaded and the force it has just summed, and
+// keeps the running maxima of the audit values in aud[3]; the integration kernel then
+// leaves owners with listed partners alone (k_integrate<..., SKIP_LISTED>).  No
+// per-owner force array is written or read, and such an owner's state is read once.
+template <class F, bool CLUMPS, int MODE, bool ROLL = false, int MODEL = FORCE_MODEL_BUILTIN, bool INTEG = false>
 __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_known, uint32_t j0_known, int sp,
-                                             int hp, int lc, double *eval_F, double *eval_T)
+                                             int hp, int lc, double *eval_F, double *eval_T, float *aud = nullptr)
 {
+    static_assert(!INTEG || (!CLUMPS && MODE == MODE_STEP), "the contact kernel integrates only single spheres");
     using R = typename F::R;
     using R4 = typename F::R4;
     const int lane = threadIdx.x & 31;
@@ -1200,9 +1219,17 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
     V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
     SphereK<F> me;
     int scene = 0;
+    R4 q4 = {}, ii = {};
+    R im = R(0);
     if (live) {
         me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
         scene = d.owner_scene[o];
+        if constexpr (INTEG) {
+            // the rest of the owner's inputs are in flight while the pairs are summed
+            q4 = d.st.quat[sp][o];
+            im = d.inv_mass[o];
+            ii = d.inv_moi[o];
+        }
     }
     if (act) {
         if constexpr (MODEL == FORCE_MODEL_HERTZ_MINDLIN)
@@ -1239,6 +1266,21 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         V3<R> Ft = act ? Fs + me.mass * g : V3<R>{R(0), R(0), R(0)};
         eval_F[3 * o + 0] = (double)Ft.x; eval_F[3 * o + 1] = (double)Ft.y; eval_F[3 * o + 2] = (double)Ft.z;
         eval_T[3 * o + 0] = (double)Ts.x; eval_T[3 * o + 1] = (double)Ts.y; eval_T[3 * o + 2] = (double)Ts.z;
+    } else if constexpr (INTEG) {
+        // the same update as k_integrate from the same inputs (the force it would read
+        // back is the one summed here): the same bits
+        typename F::Aux aux{};
+        if constexpr (F::voxel) {
+            aux.rad = me.rad;
+            aux.rlo = me.rlo;
+        }
+        float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
+        integrate_core<F, false>(d, d.status, o, sp, true, me.p, me.mass, R4{me.v.x, me.v.y, me.v.z, me.acc0},
+                                 R4{me.w.x, me.w.y, me.w.z, me.acc1}, q4, im, ii, true, d.scenes[scene], Fs, Ts, aux,
+                                 disp, disp2, speed);
+        aud[0] = fmaxf(aud[0], disp);
+        aud[1] = fmaxf(aud[1], disp2);
+        aud[2] = fmaxf(aud[2], speed);
     } else {
         d.fo[o] = R4{Fs.x, Fs.y, Fs.z, R(0)};
         d.to[o] = R4{Ts.x, Ts.y, Ts.z, R(0)};
@@ -1251,7 +1293,8 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
 // LEAN = 1 compiles the kernel for 5 resident blocks of CONTACT_BLOCK_MAX threads per SM
 // (96 registers, some spilled to the L1-cached local memory) instead of 4: more
 // warps to hide the latency of the gathers, chosen by the autotuner where it pays.
-template <class F, bool CLUMPS, int MODE, int LEAN = 0, bool ROLL = false, int MODEL = FORCE_MODEL_BUILTIN>
+template <class F, bool CLUMPS, int MODE, int LEAN = 0, bool ROLL = false, int MODEL = FORCE_MODEL_BUILTIN,
+          bool INTEG = false>
 __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev<F> d, double *eval_F, double *eval_T)
 {
     DevStatus *stp = d.status;
@@ -1274,14 +1317,19 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
                                                        hp, lc, eval_F, eval_T);
     } else {
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        int64_t t = t0;
         uint4 a = t < nw ? act[t] : make_uint4(0u, 0u, 0u, 0u);
+        float aud[3] = {0.0f, 0.0f, 0.0f};
         for (; t < nw; t += stride) {
             // the next work entry is read while this one is evaluated
             const uint4 next = t + stride < nw ? act[t + stride] : a;
-            contact_slot<F, CLUMPS, MODE, ROLL, MODEL>(d, (int64_t)a.x, (int)a.y, a.z, sp, hp, lc, eval_F, eval_T);
+            contact_slot<F, CLUMPS, MODE, ROLL, MODEL, INTEG>(d, (int64_t)a.x, (int)a.y, a.z, sp, hp, lc, eval_F,
+                                                              eval_T, aud);
             a = next;
         }
+        // every lane of the warp gets here (the loop's exit is the only divergence)
+        if constexpr (INTEG) audit_slots(d.audit, t0, threadIdx.x & 31, aud[0], aud[1], aud[2]);
     }
 }
 
@@ -1431,22 +1479,27 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
 
 // integrate_core with the inputs read from src (global state arrays or a staged tile)
 // and the contact force and torque from the per-owner arrays written by k_contact.
-template <class F, bool CLUMPS>
+// FREE (single spheres whose owners with listed partners the contact kernel integrates):
+// every owner here has zero contact force and torque, so neither the force array nor the
+// inverse inertia is read; a single sphere's r_ext is 0 and the torque term adds exactly
+// zero whatever its inverse inertia, so the results are the same bits.
+template <class F, bool CLUMPS, bool FREE = false>
 __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp, int64_t o, const OwnerSrc<F> &src,
                                                 int64_t i, int sp, float &disp, float &disp2, float &speed)
 {
+    static_assert(!FREE || !CLUMPS, "FREE is for single spheres");
     using R = typename F::R;
     using R4 = typename F::R4;
     // every load of this owner is issued before the first one is used: the thread waits
     // for one memory round trip, not a chain of them
     const bool act = src.active[i];
-    const bool has = CLUMPS ? true : src.cnt[i] > 0;
+    const bool has = FREE ? false : (CLUMPS ? true : src.cnt[i] > 0);
     R mass;
     typename F::Aux aux;
     const typename F::Pos po = F::load(src.pos, i, mass, aux);
     const R4 v4 = src.kv[2 * i], w4 = src.kv[2 * i + 1], q4 = src.quat[i];
     const R im = src.inv_mass[i];
-    const R4 ii = src.inv_moi[i];
+    const R4 ii = FREE ? R4{R(0), R(0), R(0), R(0)} : src.inv_moi[i];
     const bool iso = CLUMPS ? (bool)src.iso[i] : true;     // a single sphere is isotropic
     const Scene &sc = d.scenes[d.n_scenes > 1 ? src.scene[i] : 0];
     V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
@@ -1460,19 +1513,22 @@ __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp,
 }
 
 // One thread per owner, reading its inputs straight from the state arrays.
-template <class F, bool CLUMPS>
+// SKIP_LISTED (single spheres): owners that are active with listed partners are left to
+// the contact kernel, which integrates them (k_contact<..., INTEG>).
+template <class F, bool CLUMPS, bool SKIP_LISTED = false>
 __global__ void __launch_bounds__(INTEGRATE_BLOCK_MAX) k_integrate(Dev<F> d)
 {
+    static_assert(!SKIP_LISTED || !CLUMPS, "only single spheres are integrated by the contact kernel");
     DevStatus *stp = d.status;
     if (stp->halt || stp->list_stale) return;
     const int sp = stp->state_par, lc = stp->list_cur;
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
-    if (o < d.M) {
+    if (o < d.M && !(SKIP_LISTED && d.st.active[sp][o] && d.lists.cnt[lc][o] > 0)) {
         OwnerSrc<F> src{d.st.pos[sp], d.st.kv[sp], d.st.quat[sp], d.inv_moi, d.inv_mass,
                         d.st.active[sp], d.lists.cnt[lc], d.owner_iso, d.owner_scene};
-        integrate_owner<F, CLUMPS>(d, stp, o, src, o, sp, disp, disp2, speed);
+        integrate_owner<F, CLUMPS, SKIP_LISTED>(d, stp, o, src, o, sp, disp, disp2, speed);
     }
     audit_slots(d.audit, o, lane, disp, disp2, speed);
 }

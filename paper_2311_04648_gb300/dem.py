@@ -24,7 +24,7 @@ SCHEDULE = {"every_step": 0, "velocity_bound": 1, "learned": 2}
 PROP_COR, PROP_MU, PROP_CRR = 0, 1, 2
 MODEL = {"default": 0, "hertz_mindlin": 1, "bonded_breakage": 2}
 BREAKAGE_PARAMS = ("tension", "cohesion", "eta", "damping")
-WALL_PLANE, WALL_CYLINDER, WALL_CONE = 0, 1, 2
+WALL_PLANE, WALL_CYLINDER, WALL_CONE, WALL_TRIANGLE = 0, 1, 2, 3
 
 
 class DemError(RuntimeError):
@@ -61,7 +61,7 @@ class Tuning(C.Structure):
     _fields_ = [("contact_block", C.c_int32), ("integrate_block", C.c_int32), ("narrow_block", C.c_int32),
                 ("detect_inline", C.c_int32), ("step_ms", C.c_double), ("cell_factor", C.c_double),
                 ("integrate_staged", C.c_int32), ("contact_lean", C.c_int32), ("fused_block", C.c_int32),
-                ("margin", C.c_double)]
+                ("margin", C.c_double), ("contact_integrates", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +92,7 @@ def _sigs(L):
         "dem_get_listed_wall_pairs": [P, I64, P, P, P], "dem_get_owner_forces": [P, I64, I64, P, P],
         "dem_set_history": [P, I64, P, P, P], "dem_set_history_age": [P, I64, P, P, P, P],
         "dem_get_contact_rolling": [P, I64, P, P, P],
+        "dem_add_mesh": [P, I64, P, I32, P, P, P],
         "dem_set_force_model": [P, I32, P, I32], "dem_set_contact_wildcards": [P, I64, P, P, P],
         "dem_get_contact_wildcards": [P, I64, P, P],
         "dem_set_family": [P, I64, I64, P], "dem_set_family_motion": [P, I32, P, P],
@@ -262,6 +263,15 @@ class World:
     def add_cylinder(self, c, axis, radius, mat, omega=0.0):
         i = C.c_int32()
         self._c(self.L.dem_add_cylinder(self.h, _p(_f64(c)), _p(_f64(axis)), radius, mat, omega, C.byref(i)))
+        return i.value
+
+    def add_mesh(self, vertices, mat, axis_point=(0, 0, 0), omega=(0, 0, 0)):
+        """A rigid triangle mesh (facets vertices[n, 3, 3]) turning with omega about
+        axis_point; returns the first facet's wall id."""
+        v = _f64(vertices).reshape(-1, 9)
+        i = C.c_int32()
+        self._c(self.L.dem_add_mesh(self.h, len(v), _p(v), int(mat), _p(_f64(axis_point)), _p(_f64(omega)),
+                                    C.byref(i)))
         return i.value
 
     def add_cone_segment(self, p, axis, r0, z0, r1, z1, mat):
@@ -533,9 +543,24 @@ class World:
                 self.set_material_pair(PROP_COR, a, b, float(cor[a, b]))
                 self.set_material_pair(PROP_MU, a, b, float(mu[a, b]))
                 self.set_material_pair(PROP_CRR, a, b, float(crr[a, b]))
-        for wd in scene.walls:
+        walls = list(scene.walls)
+        k = 0
+        while k < len(walls):
+            wd = walls[k]
             t = int(wd["type"])
             om = np.asarray(wd.get("omega", (0.0, 0.0, 0.0)), np.float64)
+            if t == WALL_TRIANGLE:
+                # consecutive facets of one material, axis point and spin form one mesh
+                run = [wd]
+                while (k + len(run) < len(walls) and int(walls[k + len(run)]["type"]) == WALL_TRIANGLE
+                       and int(walls[k + len(run)]["mat"]) == int(wd["mat"])
+                       and np.array_equal(walls[k + len(run)]["p"], wd["p"])
+                       and np.array_equal(walls[k + len(run)].get("omega", om), om)):
+                    run.append(walls[k + len(run)])
+                self.add_mesh(np.array([r["tri"] for r in run]), int(wd["mat"]), wd["p"], om)
+                k += len(run)
+                continue
+            k += 1
             if t == WALL_PLANE:
                 wid = self.add_plane(wd["p"], wd["n"], int(wd["mat"]))
             elif t == WALL_CYLINDER:

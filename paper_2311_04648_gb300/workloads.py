@@ -27,7 +27,7 @@ import math
 import numpy as np
 
 RHO = 2600.0
-PLANE, CYLINDER, CONE = 0, 1, 2
+PLANE, CYLINDER, CONE, TRIANGLE = 0, 1, 2, 3
 
 
 @dataclass
@@ -575,3 +575,142 @@ def cone_bed(n=300, R=1e-3, half_angle_deg=30.0, r_orifice=0.01, e=0.5, mu=0.4, 
                  [sphere_template(R)], np.zeros(m, np.int64), None, pts, _identity_quats(m), v,
                  rng.normal(scale=50.0, size=(m, 3)), h, np.array([0.0, 0.0, -9.81]),
                  sink=(np.array([0.0, 0.0, sink_z]), axis.copy()), r_max=R, name=f"cone_bed_n{m}_seed{seed}")
+
+
+# ----------------------------------------------------------------------------- meshes
+
+def box_facets(lo, hi, n=(1, 1, 1)):
+    """Triangles (k, 3, 3) of the surface of the axis-aligned box [lo, hi], each face split
+    into a grid of quads (n[a] divisions along axis a), two triangles per quad."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    tris = []
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        for side in (lo[a], hi[a]):
+            us = np.linspace(lo[b], hi[b], n[b] + 1)
+            vs = np.linspace(lo[c], hi[c], n[c] + 1)
+            for i in range(n[b]):
+                for j in range(n[c]):
+                    q = []
+                    for u, v in ((us[i], vs[j]), (us[i + 1], vs[j]), (us[i + 1], vs[j + 1]), (us[i], vs[j + 1])):
+                        p = np.empty(3)
+                        p[a], p[b], p[c] = side, u, v
+                        q.append(p)
+                    tris.append([q[0], q[1], q[2]])
+                    tris.append([q[0], q[2], q[3]])
+    return np.array(tris)
+
+
+def rotated_z(tris, angle):
+    c, s = math.cos(angle), math.sin(angle)
+    Rz = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    return np.asarray(tris) @ Rz.T
+
+
+def facet_walls(tris, mat=0, p=(0.0, 0.0, 0.0), omega=(0.0, 0.0, 0.0)):
+    return [dict(type=TRIANGLE, mat=mat, p=np.asarray(p, np.float64), n=np.zeros(3),
+                 omega=np.asarray(omega, np.float64), tri=np.asarray(t, np.float64).reshape(9)) for t in tris]
+
+
+def mixer_mesh(r_in=0.05, r_out=0.45, z0=0.02, z1=0.12, thickness=0.02, hub_r=0.05, hub_h=0.15):
+    """The bladed mixer: four blades (boxes from r_in to r_out, z0 to z1, each face split
+    into quads: 716 facets a blade) around a heptagonal hub prism (28 facets), 2,892
+    facets in all, about the z axis."""
+    blade = box_facets([r_in, -thickness / 2, z0], [r_out, thickness / 2, z1], n=(29, 1, 5))
+    tris = [rotated_z(blade, k * math.pi / 2) for k in range(4)]
+    ang = np.linspace(0, 2 * math.pi, 8)[:7]
+    ring = np.stack([hub_r * np.cos(ang), hub_r * np.sin(ang)], axis=1)
+    hub = []
+    for k in range(7):
+        a, b = ring[k], ring[(k + 1) % 7]
+        pa0, pb0 = [a[0], a[1], 0.0], [b[0], b[1], 0.0]
+        pa1, pb1 = [a[0], a[1], hub_h], [b[0], b[1], hub_h]
+        hub += [[pa0, pb0, pb1], [pa0, pb1, pa1], [[0, 0, hub_h], pa1, pb1], [[0, 0, 0.0], pb0, pa0]]
+    return np.concatenate(tris + [np.array(hub)])
+
+
+def paddle_bed(n=300, R=1e-3, omega=150.0, e=0.5, mu=0.4, E=1e7, nu=0.3, seed=0, h=1e-6, vel_sigma=0.02) -> Scene:
+    """Layers of spheres in a walled box around a paddle mesh (a tessellated thin box, 20
+    facets) turning about the vertical axis through the box centre, over a static facet
+    floor (8 facets) lying on the box floor: the bottom layer starts overlapping the floor
+    facets by 0.001 R and spheres inside the paddle's sweep are struck by its faces,
+    edges and corners."""
+    rng = np.random.default_rng(seed)
+    side = 0.024
+    lo = np.zeros(3)
+    hi = np.array([side, side, 0.02])
+    cx = side / 2
+    pl = np.array([cx - 0.008, cx - 0.001, 0.0015])
+    ph = np.array([cx + 0.008, cx + 0.001, 0.009])
+    paddle = box_facets(pl, ph, n=(2, 1, 1))
+    floor = box_facets([0.0005, 0.0005, 0.0], [side - 0.0005, side - 0.0005, 0.0005], n=(2, 2, 1))
+    floor = floor[np.abs(floor[:, :, 2] - 0.0005).max(axis=1) < 1e-12]      # its top face only
+    pts = []
+    z = 0.0005 + R - 0.001 * R
+    while len(pts) < n and z < 0.018:
+        tries = 0
+        layer = []
+        while tries < 4000 and len(pts) + len(layer) < n:
+            tries += 1
+            p = np.array([rng.uniform(R + 1e-4, side - R - 1e-4), rng.uniform(R + 1e-4, side - R - 1e-4), z])
+            if np.all(p[:2] > pl[:2] - R - 1e-4) and np.all(p[:2] < ph[:2] + R + 1e-4) and p[2] < ph[2] + R + 1e-4:
+                continue                              # clear of the paddle at time 0
+            if all(np.linalg.norm(p - q) > 2 * R + 1e-5 for q in layer):
+                layer.append(p)
+        pts += layer
+        z += 2 * R + 1e-4
+    x = np.array(pts[:n])
+    m = len(x)
+    Em, num, corm, mum = _single_material(E, nu, e, mu)
+    walls = box_walls(lo, hi) + facet_walls(floor) + facet_walls(paddle, p=(cx, cx, 0.0), omega=(0.0, 0.0, omega))
+    return Scene(lo, hi, Em, num, corm, mum, walls, [sphere_template(R)], np.zeros(m, np.int64), None, x,
+                 _identity_quats(m), rng.normal(scale=vel_sigma, size=(m, 3)), np.zeros((m, 3)), h,
+                 np.array([0.0, 0.0, -9.81]), r_max=R, name=f"paddle_bed_n{m}")
+
+
+def six_template(R: float, mat: int = 0, rho: float = RHO) -> Template:
+    """Six tangent spheres on the vertices of a regular octahedron (centres at +-a on each
+    axis, neighbours 2R apart)."""
+    m1 = rho * 4.0 / 3.0 * math.pi * R ** 3
+    i1 = 0.4 * m1 * R * R
+    a = 2 * R / math.sqrt(2)
+    xs = np.array([[a, 0, 0], [-a, 0, 0], [0, a, 0], [0, -a, 0], [0, 0, a], [0, 0, -a]], np.float64)
+    I = 6 * i1 + 4 * m1 * a * a      # four of the six centres lie at distance a from each axis
+    return Template(xs, np.full(6, R), np.full(6, mat, np.int32), 6 * m1, np.array([I, I, I]))
+
+
+def mixer(n=4_000_000, clump="sphere", omega=2 * math.pi, mu=0.5, seed=7, R=None, vel_sigma=0.0) -> Scene:
+    """The mixer of Sec. 5: elements released at rest from a cylindrical region of radius
+    0.5 m and height 1/3 m above a bladed mixer mesh (2,892 facets) that turns at
+    omega = 2 pi rad/s inside a cylindrical container with a floor; material and step of
+    Sec. 5's table (rho 2600, E 1e9, nu 0.3, CoR 0.2, dt 5e-7 s; mu is not printed:
+    0.5).  clump: "sphere", "rod3" (three tangent spheres) or "six" (six on an
+    octahedron); the element size follows from n (lattice of the region), as the paper
+    sizes elements to set the count."""
+    rng = np.random.default_rng(seed)
+    Rc, h_mix, H = 0.5, 0.15, 1.0 / 3.0
+    ext = {"sphere": 1.0, "rod3": 3.0, "six": 1.0 + math.sqrt(2)}[clump]
+    vol = math.pi * (Rc - 0.01) ** 2 * H
+    pitch = (vol / n) ** (1.0 / 3.0)
+    if R is None:
+        R = pitch / (2.0 * ext * 1.05)
+    tpl = {"sphere": sphere_template, "rod3": rod_template, "six": six_template}[clump](R, rho=2600.0)
+    span = ext * R * 1.05
+    g = np.arange(-Rc + span, Rc - span + 1e-12, pitch)
+    zs = np.arange(h_mix + span, h_mix + H - span + 1e-12, pitch)
+    X, Y, Z = np.meshgrid(g, g, zs, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    pts = pts[np.hypot(pts[:, 0], pts[:, 1]) < Rc - span]
+    pts = pts[np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))][:n]
+    m = len(pts)
+    q = _identity_quats(m) if clump == "sphere" else _random_quats(rng, m)
+    Em, num, corm, mum = _single_material(1e9, 0.3, 0.2, mu)
+    lo = np.array([-Rc - 0.02, -Rc - 0.02, -0.01])
+    hi = np.array([Rc + 0.02, Rc + 0.02, h_mix + H + 0.05])
+    walls = [dict(type=PLANE, mat=0, p=np.array([0.0, 0.0, 0.0]), n=np.array([0.0, 0.0, 1.0])),
+             dict(type=CYLINDER, mat=0, p=np.zeros(3), n=np.array([0.0, 0.0, 1.0]), r0=Rc)]
+    walls += facet_walls(mixer_mesh(), p=(0.0, 0.0, 0.0), omega=(0.0, 0.0, omega))
+    return Scene(lo, hi, Em, num, corm, mum, walls, [tpl], np.zeros(m, np.int64), None, pts, q,
+                 rng.normal(scale=vel_sigma, size=(m, 3)), np.zeros((m, 3)), 5e-7, np.array([0.0, 0.0, -9.81]),
+                 r_max=R, name=f"mixer_{clump}_n{m}", meta=dict(element_radius=R, facets=2892))

@@ -914,3 +914,52 @@ def test_fp64_bonded_breakage_matches_oracle():
     broken = nb - bonds
     print("bonded breakage: bonds", nb, "left", bonds, "free-running", worst)
     assert 0 < broken < nb
+
+
+# ----------------------------------------------------------------------------- mesh facets
+
+def test_fp64_mesh_facets_match_oracle():
+    """Sphere-facet contacts with a static facet floor and a turning paddle mesh (Sec. 2.4,
+    Sec. 5): the listed sets (facets found through their cell bins) equal the oracle's
+    brute-force set, and forces and states match at 1e-9, one step from the GPU's own
+    states and free-running."""
+    s = W.paddle_bed(n=300, seed=3)
+    beta = 4e-5
+    w = dem.World.from_scene(s, precision="fp64", margin=beta)
+    ow = oracle.OracleWorld(s, threads=oracle_threads())
+    free = oracle.OracleWorld(s, threads=oracle_threads())
+    n_regular = 6
+    facet_hits = 0
+    worst = {}
+    one_step_parity(w, ow, None)
+    assert free.step(1) == 0
+    for k in (300, 600, 900):
+        w.step(k - 1)
+        assert ow.step(k - 1) == 0 and free.step(k - 1) == 0
+        p, r = w.sphere_positions()
+        si, wi = w.listed_wall_pairs()
+        osi, owi = ow.listed_wall_pairs(p, beta)
+        assert np.array_equal(si, osi) and np.array_equal(wi, owi)
+        stored = w.contacts()
+        w.step(1)
+        assert ow.step(1) == 0 and free.step(1) == 0
+        st, _ = state_close(w, free, TOL64)
+        worst = {a: max(worst.get(a, 0.0), b) for a, b in st.items()}
+        facet_hits += int(np.sum(w.contacts()["j"] <= -1 - n_regular))
+        one_step_parity(w, ow, stored)
+        assert free.step(1) == 0
+    print("paddle bed free-running", worst, "facet contacts", facet_hits)
+    assert max(worst.values()) < TOL64, worst
+    assert facet_hits > 10
+
+
+def test_voxel_fp32_mesh_facets_stay_close_to_fp64():
+    s = W.paddle_bed(n=300, seed=3)
+    w = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    ow = oracle.OracleWorld(s, threads=oracle_threads())
+    w.step(400)
+    assert ow.step(400) == 0
+    x = w.owner_state()[0]
+    assert np.max(np.abs(x - ow.x)) < 1e-6
+    c = w.contacts()
+    assert np.sum(c["j"] <= -7) > 10

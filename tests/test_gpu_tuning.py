@@ -188,6 +188,67 @@ def test_fused_step_is_bit_identical(prec):
             assert b.stats()["audit_fallbacks"] == want_fallbacks
 
 
+@pytest.mark.parametrize("prec", ["voxel_fp32", "fp64"])
+def test_contact_kernel_integration_is_bit_identical(prec):
+    # the contact kernel integrating the owners with listed partners (the integration
+    # kernel the rest) against every owner integrated by the integration kernel: both
+    # contact builds, switched in mid-run, both schedules
+    s = W.dense_lattice(n=900, seed=37, vel_sigma=0.3)
+    beta = 5e-5
+    for sched in ("every_step", "velocity_bound"):
+        kw = dict(precision=prec, schedule=sched, margin_max=beta)
+        if sched != "every_step":
+            kw["margin"] = beta
+        a = dem.World.from_scene(s, **kw)
+        a.set_tuning(fused_block=0, contact_integrates=0)
+        for k in (50, 20, 50):
+            a.step(k)
+        want = _state(a)
+        want_pairs = a.listed_pairs()[0].tolist()
+        want_fallbacks = a.stats()["audit_fallbacks"]
+        for lean in (0, 1):
+            b = dem.World.from_scene(s, **kw)
+            b.set_tuning(fused_block=0, contact_integrates=1, contact_lean=lean)
+            assert b.tuning()["contact_integrates"] == 1
+            b.step(50)
+            b.set_tuning(fused_block=0, contact_integrates=0, contact_lean=lean)
+            b.step(20)
+            b.set_tuning(fused_block=0, contact_integrates=1, contact_lean=lean)
+            b.step(50)
+            for x, y in zip(_state(b), want):
+                assert np.array_equal(x, y)
+            assert b.listed_pairs()[0].tolist() == want_pairs
+            assert b.stats()["audit_fallbacks"] == want_fallbacks
+
+
+def test_contact_kernel_integration_with_a_sink_in_a_batch_and_ignored_for_clumps():
+    s = W.cone_bed(n=300, seed=13)
+    a = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    b = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    a.set_tuning(fused_block=0, contact_integrates=0)
+    b.set_tuning(fused_block=0, contact_integrates=1)
+    a.step(900)
+    b.step(900)
+    for x, y in zip(_state(a), _state(b)):
+        assert np.array_equal(x, y)
+    scenes = [W.dense_lattice(n=150 + 97 * k, seed=45 + k, vel_sigma=0.3) for k in range(3)]
+    beta = 5e-5
+    p = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    q = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    p.initialize()
+    q.initialize()
+    p.worlds[0].set_tuning(fused_block=0, contact_integrates=0)
+    q.worlds[0].set_tuning(fused_block=0, contact_integrates=1)
+    p.step(60)
+    q.step(60)
+    for wp, wq in zip(p.worlds, q.worlds):
+        for x, y in zip(_state(wp), _state(wq)):
+            assert np.array_equal(x, y)
+    c = dem.World.from_scene(W.packed_clumps(n=100, seed=38), precision="voxel_fp32", schedule="every_step")
+    c.set_tuning(contact_integrates=1)
+    assert c.tuning()["contact_integrates"] == 0
+
+
 def test_fused_step_with_a_sink_and_walls_is_bit_identical():
     s = W.cone_bed(n=300, seed=13)        # some spheres pass the sink within 900 steps
     a = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
