@@ -129,21 +129,24 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- algorithmic bytes
 
-def algorithmic_bytes(precision, n, pairs, clumps=False):
+def algorithmic_bytes(precision, n, pairs, clumps=False, n_with_entries=0.0, contact_integrates=False):
     """Algorithmic bytes per launch of the two per-step kernels, from the per-unit figures
     of the method's force+integrate step: the owner state read and written once (voxel
     form: voxel 8 + offset 12 + v 12 + w 12 = 44 B each way, 88 B; FP64 form: 3 x 24 B each
     way, 144 B), clumps adding the quaternion (16 B each way), and per listed pair the two
     ids (8 B) with the tangential history read and written (voxel form 12 + 12 B; FP64
-    24 + 24 B)."""
-    if precision == "voxel_fp32":
-        integ = 88 * n + (32 * n if clumps else 0)
-        contact = 32 * pairs
-    else:
-        integ = 144 * n + (32 * n if clumps else 0)
-        contact = 56 * pairs
+    24 + 24 B).  With contact_integrates the contact kernel also updates the owners with
+    listed partners (n_with_entries of them) and the integration kernel the others."""
+    per_owner = (88 if precision == "voxel_fp32" else 144) + (32 if clumps else 0)
+    per_pair = 32 if precision == "voxel_fp32" else 56
+    integ = per_owner * n
+    contact = per_pair * pairs
+    step = integ + contact
+    if contact_integrates:
+        contact += per_owner * n_with_entries
+        integ = per_owner * (n - n_with_entries)
     # the fused step kernel does both: the whole force+integrate figure per launch
-    return {"integrate": integ, "contact": contact, "step": integ + contact}
+    return {"integrate": integ, "contact": contact, "step": step}
 
 
 def detection_bytes(precision, n, pairs):
@@ -158,7 +161,7 @@ def detection_bytes(precision, n, pairs):
     return 100 * n + 72 * pairs
 
 
-def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
+def layout_bytes(precision, n, n_with_entries, pairs, clumps=False, contact_integrates=False, derived=False):
     """Bytes the kernels actually move in this implementation's layout, each distinct
     array element counted once per launch (context for the algorithmic figure).
 
@@ -168,7 +171,12 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
     owners with listed partners.  k_contact: per sphere with listed partners its compacted
     work entry (slot, row length, first partner), active flag, state and the force/torque
     it writes; per listed pair both row entries and both sides' history vectors read and
-    written.  k_step_fused: both, without the force/torque array."""
+    written.  k_step_fused: both, without the force/torque array.  With contact_integrates
+    (single spheres) the contact kernel also reads the quaternion and constants of its
+    owners and writes their state instead of the force/torque, and the integration kernel
+    reads every owner's flag and row length but the state of the others only, without
+    constants or forces.  With derived constants (voxel form, single spheres of one
+    inertia coefficient) no kernel reads 1/m or 1/I (20 B per owner)."""
     if precision == "voxel_fp32":
         # 32-byte position record (offset, mass, voxel index, radius pair) and 32-byte
         # velocity pair (v, w with the audit accumulators) per owner
@@ -188,6 +196,22 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False):
                     + 32 + 32 + 32 + 32 + 1) + pairs * (8 + 4 * 32)
     if clumps:
         contact += n * (16 if precision == "voxel_fp32" else 32)
+    if derived and precision == "voxel_fp32" and not clumps and not contact_integrates:
+        integ -= n * (4 + 16)
+        step -= n * (4 + 16)
+    if contact_integrates and not clumps:
+        free = n - n_with_entries
+        if precision == "voxel_fp32":
+            # reads: quaternion, inverse mass and inertia; writes: record, velocity pair,
+            # quaternion and flag, instead of the force/torque
+            contact += n_with_entries * (16 + 4 + 16 + 32 + 32 + 16 + 1 - 32)
+            integ = n * (1 + 1) + free * (32 + 32 + 16 + 4 + 32 + 32 + 16 + 1)
+            if derived:
+                contact -= n_with_entries * (4 + 16)
+                integ -= free * 4
+        else:
+            contact += n_with_entries * (32 + 8 + 32 + 32 + 32 + 32 + 32 + 1 - 64)
+            integ = n * (1 + 1) + free * (32 + 32 + 32 + 8 + 32 + 32 + 32 + 32 + 1)
     return {"integrate": integ, "contact": contact, "step": step}
 
 
@@ -307,12 +331,16 @@ def fused_step(prof):
     return prof["n_integrate"] == 0 and prof["n_contact"] > 0
 
 
-def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step=0.0):
+def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step=0.0, contact_integrates=False,
+             derived=False):
     """Roofline of the dominant kernel of a step (largest share of the step's time) and of
     each per-step kernel and the detection phase on its own: algorithmic bytes per
     launch over the average launch duration (CUDA events on the kernel's own stream)."""
-    ab = algorithmic_bytes(precision, n, prof["listed_pairs"])
-    lb = layout_bytes(precision, n, prof["with_entries"], prof["listed_pairs"])
+    ci = bool(contact_integrates) and not fused_step(prof)
+    ab = algorithmic_bytes(precision, n, prof["listed_pairs"], n_with_entries=prof["with_entries"],
+                           contact_integrates=ci)
+    lb = layout_bytes(precision, n, prof["with_entries"], prof["listed_pairs"], contact_integrates=ci,
+                      derived=derived)
     per = {}
     for k in (("step",) if fused_step(prof) else ("contact", "integrate")):
         ms = prof["contact_ms" if k == "step" else f"{k}_ms"]
@@ -328,12 +356,16 @@ def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step
     for k, v in per.items():
         v["frac"] = (v["gbs"] / peak) if v["gbs"] else None
         v["traffic"] = (measured_traffic(k, n, margin) if precision == "voxel_fp32" and k in MEASURED_TRAFFIC
-                        else None)
+                        and not ci else None)
     # the dominant kernel among the per-step kernels (the detection phase is several
     # kernels on the second stream, reported beside them)
     dom = max((k for k in per if k != "detect"), key=lambda k: per[k]["ms_per_step"])
     a = per[dom]["gbs"]
-    return {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
+    name = KERNEL_NAMES[dom]
+    if ci:
+        name = {"contact": "k_contact (pair forces + per-owner sums + update of the owners with partners)",
+                "integrate": "k_integrate (update of the owners without partners + audit)"}.get(dom, name)
+    return {"bound": "hbm", "kernel": name, "contact_integrates": ci,
             "achieved": a, "peak": peak, "unit": "GB/s", "frac": (a / peak) if a else None,
             "traffic": per[dom]["traffic"],
             "peak_kind": peak_kind, "bytes_per_launch": per[dom]["bytes"], "avg_launch_ms": per[dom]["ms"],
@@ -771,7 +803,9 @@ def main():
                    "l2": "inputs larger than L2 (owner state + contact lists > 0.5 GB)",
                    "parallelism": f"replica x{world}"},
         "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind, margin=res["chosen"]["stats"]["margin"],
-                             rebuilds_per_step=res["chosen"]["rebuilds"] / max(steps, 1)),
+                             rebuilds_per_step=res["chosen"]["rebuilds"] / max(steps, 1),
+                             contact_integrates=res["tuning"].get("contact_integrates", 0),
+                             derived=bool(res["chosen"]["stats"].get("derived_constants", 0))),
         "kernels_ms": dict(({"step": prof["contact_ms"]} if fused_step(prof) else
                             {"contact": prof["contact_ms"], "integrate": prof["integrate_ms"]}),
                            detect_per_rebuild=prof["detect_ms"], hash=prof["hash_ms"], link=prof["link_ms"]),

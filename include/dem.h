@@ -115,6 +115,11 @@ typedef struct {
                                       pairs in use (each pair once): per-step averages     */
     int64_t busy_steps;            /* sum over completed steps of the spheres with listed
                                       partners                                              */
+    int32_t derived_constants;     /* 1: the voxel-form kernels derive 1/m and 1/I from
+                                      each sphere's mass and radius (single spheres whose
+                                      inertia is c m R^2 for one c) instead of reading them */
+    int32_t counting_sort;         /* 1: detection orders spheres by cell with the counting
+                                      sort, 0: with the radix sort                         */
 } dem_stats;
 
 typedef struct {
@@ -280,6 +285,11 @@ typedef struct {
                                       per-owner force array), the integration kernel the
                                       others; 0 = the integration kernel integrates every
                                       owner.  The same bits either way; ignored elsewhere  */
+    int32_t binning;               /* how detection orders the spheres by cell: 0 = automatic
+                                      (counting sort where the cells number at most 8 per
+                                      sphere slot, else radix sort), 1 = radix sort of the
+                                      cell keys, 2 = counting sort (per-cell counts, a scan,
+                                      a scatter).  The same contact lists either way       */
 } dem_tuning;
 
 dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);

@@ -199,6 +199,10 @@ public:
         }
         if ((s = alloc(db_.sorted_owner, Nk, err))) return s;
         if ((s = alloc(db_.n_valid, 1, err))) return s;
+        if ((s = alloc(db_.rowcnt, Np, err))) return s;
+        if ((s = alloc(db_.crank, Nk, err))) return s;
+        if ((s = alloc_cell_counts(m_.n_cells_total, err))) return s;
+        choose_binning();
         if ((s = setup_facets(err))) return s;
 
         // constants
@@ -219,6 +223,26 @@ public:
         }
         if ((s = up(d_.inv_moi, inv_moi.data(), M, err))) return s;
         if ((s = up(d_.inv_mass, inv_mass.data(), M, err))) return s;
+        // voxel form, single spheres: if every owner is isotropic with I = c m R^2 for one
+        // c, the kernels derive 1/m and 1/I from the position record (20 bytes less per
+        // owner and step)
+        d_.solid = 0;
+        if (F::voxel && !m_.clumps && M > 0) {
+            bool ok = true;
+            double c0 = 0.0;
+            for (int64_t o = 0; o < M && ok; ++o) {
+                const double r = m_.sph_rad[m_.owner_first_slot[o]], mass = m_.mass[o];
+                const double *I = &m_.moi[3 * o];
+                const double c = I[0] / (mass * r * r);
+                if (o == 0) c0 = c;
+                ok = I[1] == I[0] && I[2] == I[0] && m_.r_ext[o] == 0.0 && std::isfinite(c) && c > 0.0 &&
+                     std::fabs(c - c0) <= 1e-12 * c0;
+            }
+            if (ok) {
+                d_.solid = 1;
+                d_.moi_coef = (float)c0;
+            }
+        }
         if ((s = up(d_.owner_scene, m_.owner_scene.data(), M, err))) return s;
         if ((s = up(d_.owner_iso, m_.owner_iso.data(), M, err))) return s;
         if ((s = up(d_.owner_first, m_.owner_first_slot.data(), M, err))) return s;
@@ -845,6 +869,8 @@ public:
         o->mean_steps_per_build = sth_->rebuilds > 0 ? (double)sth_->steps_done / (double)sth_->rebuilds : 0.0;
         o->cell_size = m_.L;
         o->n_cells = m_.n_cells_total;
+        o->derived_constants = d_.solid;
+        o->counting_sort = db_.counting;
         o->ms_force = prof_ms_[P_FORCE];
         o->ms_detect = prof_ms_[P_DETECT];
         o->ms_hash = prof_ms_[P_HASH];
@@ -1378,6 +1404,10 @@ private:
             err = "fused_block must be 0, 64, 128 or 256";
             return DEM_ERR_ARG;
         }
+        if (t->binning < 0 || t->binning > 2) {
+            err = "binning must be 0 (automatic), 1 (radix sort) or 2 (counting sort)";
+            return DEM_ERR_ARG;
+        }
         const double f = t->cell_factor == 0.0 ? 1.0 : t->cell_factor;
         if (!(f >= 1.0 && f <= 4.0)) {
             err = "cell_factor must be in [1, 4]";
@@ -1399,6 +1429,7 @@ private:
         tune_.contact_lean = t->contact_lean ? 1 : 0;
         tune_.fused_block = m_.clumps ? 0 : t->fused_block;
         tune_.contact_integrates = (!m_.clumps && t->contact_integrates) ? 1 : 0;
+        choose_binning();
         tune_.margin = 0.0;
         apply_margin(t->margin);
         return DEM_OK;
@@ -1450,6 +1481,34 @@ private:
         }
     }
 
+    // Per-cell counts of the counting-sort binning (zeroed; a whole number of scan tiles)
+    // and the scan's per-tile sums.
+    dem_status alloc_cell_counts(int64_t n_cells, std::string &err)
+    {
+        const int64_t len = std::max<int64_t>((n_cells + CS_TILE - 1) / CS_TILE, 1) * CS_TILE;
+        uint32_t *cc = nullptr, *ct = nullptr;
+        dem_status s;
+        if ((s = alloc(cc, len, err))) return s;
+        if ((s = alloc(ct, len / CS_TILE, err))) {
+            dfree(cc);
+            return s;
+        }
+        if (db_.ccount) dfree(db_.ccount);
+        if (db_.ctile) dfree(db_.ctile);
+        db_.ccount = cc;
+        db_.ctile = ct;
+        db_.ccount_len = len;
+        return DEM_OK;
+    }
+
+    // Counting sort where the cells are not much more numerous than the sphere slots
+    // (its scan reads every cell), else the radix sort; the tuning may force either.
+    void choose_binning()
+    {
+        const int b = tune_.binning;
+        db_.counting = b == 2 || (b == 0 && (int64_t)m_.n_cells_total <= 8 * std::max<int64_t>(d_.N, 1)) ? 1 : 0;
+    }
+
     // New detection cells (nothing in flight: called after sync).  The list in use and
     // the history do not depend on the cells; the next build uses the new ones.
     dem_status relayout_cells(double f, std::string &err)
@@ -1459,6 +1518,10 @@ private:
         if ((s = layout_cells(trial, f, err))) return s;
         uint4 *ct = nullptr;
         if ((s = alloc(ct, (int64_t)trial.n_cells_total + 1, err))) return s;
+        if ((s = alloc_cell_counts(trial.n_cells_total, err))) {
+            dfree(ct);
+            return s;
+        }
         dfree(db_.cell_tab);
         db_.cell_tab = ct;
         m_.L = trial.L;
@@ -1475,6 +1538,7 @@ private:
         db_.n_cells_total = m_.n_cells_total;
         db_.key_bits = 1;
         while (db_.key_bits < 32 && ((uint64_t)1 << db_.key_bits) <= (uint64_t)m_.n_cells_total) ++db_.key_bits;
+        choose_binning();
         return copy_sync(const_cast<Scene *>(d_.scenes), m_.scenes.data(), m_.scenes.size() * sizeof(Scene),
                          cudaMemcpyHostToDevice, err);
     }
@@ -1520,10 +1584,11 @@ private:
                     if (std::sscanf(line, "{\"key\": \"%299[^\"]\", \"contact_block\": %d, \"integrate_block\": %d, "
                                           "\"narrow_block\": %d, \"detect_inline\": %d, \"cell_factor\": %lf, "
                                           "\"integrate_staged\": %d, \"contact_lean\": %d, \"fused_block\": %d, "
-                                          "\"contact_integrates\": %d, \"margin\": %lf, \"step_ms\": %lf}",
+                                          "\"contact_integrates\": %d, \"binning\": %d, \"margin\": %lf, "
+                                          "\"step_ms\": %lf}",
                                     k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
                                     &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.fused_block,
-                                    &t.contact_integrates, &t.margin, &t.step_ms) == 12 &&
+                                    &t.contact_integrates, &t.binning, &t.margin, &t.step_ms) == 13 &&
                         key == k) {
                         best = t;
                         found = true;
@@ -1608,8 +1673,18 @@ private:
             if (f != b2.cell_factor)
                 if ((s = trial(dem_tuning{b2.contact_block, b2.integrate_block, b2.narrow_block, b2.detect_inline,
                                           0.0, f, b2.integrate_staged, b2.contact_lean, b2.fused_block, 0.0,
-                                          b2.contact_integrates})))
+                                          b2.contact_integrates, b2.binning})))
                     return s;
+        // the binning: radix sort against counting sort (the automatic choice is one of them)
+        {
+            const dem_tuning b5 = best;
+            for (int bn : {1, 2}) {
+                dem_tuning t = b5;
+                t.binning = bn;
+                t.step_ms = 0.0;
+                if ((s = trial(t))) return s;
+            }
+        }
         // phase 4 (delayed schedules): smaller detection margins list fewer pairs that do
         // not touch, at the price of more rebuilds; the results are the same bits
         if (delayed) {
@@ -1634,10 +1709,10 @@ private:
                              "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
                              "%d, \"detect_inline\": %d, \"cell_factor\": %.3f, \"integrate_staged\": %d, "
                              "\"contact_lean\": %d, \"fused_block\": %d, \"contact_integrates\": %d, "
-                             "\"margin\": %.17g, \"step_ms\": %.6f}\n",
+                             "\"binning\": %d, \"margin\": %.17g, \"step_ms\": %.6f}\n",
                              key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
                              best.detect_inline, best.cell_factor, best.integrate_staged, best.contact_lean,
-                             best.fused_block, best.contact_integrates, best.margin, best.step_ms);
+                             best.fused_block, best.contact_integrates, best.binning, best.margin, best.step_ms);
                 std::fclose(f);
             }
         }
@@ -1832,10 +1907,24 @@ private:
     void launch_detect(cudaStream_t st)
     {
         uint32_t *ks, *vs;
-        radix_sort_u32(db_.keys, db_.vals, db_.keys_alt, db_.vals_alt, d_.N, db_.key_bits, db_.hist, db_.hist_cap,
-                       st, &ks, &vs);
-        k_clear_rows<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_);
-        k_cellstart<F><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, ks, vs);
+        if (db_.counting) {
+            const unsigned nt = (unsigned)(db_.ccount_len / CS_TILE);
+            k_ccount<F><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_);
+            k_cscan_reduce<<<nt, CS_THREADS, 0, st>>>(st_, db_.ccount, db_.ctile);
+            k_cscan_tiles<<<1, 1024, 0, st>>>(st_, db_.ctile, (int64_t)nt, db_.n_valid);
+            k_cscan_write<F><<<nt, CS_THREADS, 0, st>>>(d_, db_, db_.ctile);
+            k_clear_rows<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, db_);
+            k_cscatter<F><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, db_.keys_alt, db_.vals_alt);
+            // the counts start at zero for the next build, whether or not this one halted
+            cudaMemsetAsync(db_.ccount, 0, (size_t)db_.ccount_len * sizeof(uint32_t), st);
+            ks = db_.keys_alt;
+            vs = db_.vals_alt;
+        } else {
+            radix_sort_u32(db_.keys, db_.vals, db_.keys_alt, db_.vals_alt, d_.N, db_.key_bits, db_.hist,
+                           db_.hist_cap, st, &ks, &vs);
+            k_clear_rows<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, db_);
+            k_cellstart<F><<<grid(d_.N, 256), 256, 0, st>>>(d_, db_, ks, vs);
+        }
         if (db_.n_facets > 0) {
             // bin the facets at their pose of the snapshot and sort the pairs by cell
             k_facet_bin<F><<<grid(db_.n_facets, 128), 128, 0, st>>>(d_, db_, m_.r_max);
@@ -1847,6 +1936,7 @@ private:
         }
         if (m_.clumps) k_narrow<F, true><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
         else k_narrow<F, false><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
+        k_rows_finish<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, db_);
     }
 
     void launch_link(cudaStream_t st)

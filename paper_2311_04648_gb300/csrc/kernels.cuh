@@ -36,6 +36,12 @@ struct DetectBuffers {
     int64_t n_fpairs, fhist_cap;
     const uint32_t *fkeys_sorted, *fvals_sorted;   // after the sort (one of the two buffers)
     uint32_t *n_valid;         // device counter: active entries at the front of the order
+    uint32_t *rowcnt;          // per slot: entries appended to its row by the narrow phase
+    // counting-sort binning: per-cell counts (a whole number of scan tiles, zero between
+    // builds), each slot's rank in its cell, the scan's per-tile sums
+    uint32_t *ccount, *crank, *ctile;
+    int64_t ccount_len;
+    int counting;              // 1: this build bins by counting sort, 0: by radix sort
 };
 
 // Two contact lists (ELL rows) plus two history buffers; DevStatus selects which.

@@ -54,6 +54,11 @@ struct Dev {
     float L;                        // cell (= voxel) edge
     double Ld, invL;
     int gyro;                       // gyroscopic term on
+    // voxel form, single spheres, every owner with I = moi_coef m R^2 (one coefficient):
+    // 1/m and 1/I are derived from the mass and radius in the position record instead of
+    // read from inv_mass / inv_moi
+    int solid;
+    float moi_coef;
     int n_scenes;
     int vpc;                        // voxels per cell edge (voxel form)
     double bin_invL;                // the smallest cells (schedule bins are made of them)
@@ -396,6 +401,161 @@ __global__ void __launch_bounds__(256) k_cellstart(Dev<F> d, DetectBuffers b, co
     }
 }
 
+// ---- counting sort of the snapshot by cell (the binning where cells are not much more
+// numerous than spheres): each sphere takes its rank in its cell with an atomic, an
+// exclusive scan of the per-cell counts gives each cell's start and writes the cell
+// table, and each sphere is placed at start + rank.  The order within a cell is the
+// order of the atomics; nothing downstream depends on it (the narrow phase tests each
+// pair once whatever the order, and rows are sorted by partner).
+constexpr int CS_THREADS = 256;
+constexpr int CS_ITEMS = 16;
+constexpr int CS_TILE = CS_THREADS * CS_ITEMS;
+
+template <class F>
+__global__ void __launch_bounds__(256) k_ccount(Dev<F> d, DetectBuffers b)
+{
+    if (d.status->halt) return;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.n) return;
+    const uint32_t key = b.keys[s];
+    if (key != b.n_cells_total) b.crank[s] = atomicAdd(&b.ccount[key], 1u);
+}
+
+// Sum of a block's value over the block (every thread gets it).
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
+    __syncthreads();
+    return t;
+}
+
+// Per tile of CS_TILE cells: the sum of the counts.
+static __global__ void __launch_bounds__(CS_THREADS) k_cscan_reduce(const DevStatus *stp, const uint32_t *count,
+                                                                     uint32_t *tile_sum)
+{
+    __shared__ uint32_t wsum[CS_THREADS / 32];
+    if (stp->halt) return;
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(count + (int64_t)blockIdx.x * CS_TILE);
+    uint32_t v = 0;
+#pragma unroll
+    for (int r = 0; r < CS_ITEMS / 4; ++r) {
+        const uint4 q = c4[r * CS_THREADS + threadIdx.x];
+        v += q.x + q.y + q.z + q.w;
+    }
+    v = block_sum_u32(v, wsum);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = v;
+}
+
+// Exclusive scan of the tile sums in place (one block, 1024-wide chunks with a carry);
+// the total is the number of spheres in cells (the valid entries of the order).
+static __global__ void __launch_bounds__(1024) k_cscan_tiles(const DevStatus *stp, uint32_t *tile_sum, int64_t n_tiles,
+                                                             uint32_t *n_valid)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    if (stp->halt) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n_tiles; base += 1024) {
+        const int64_t i = base + t;
+        const uint32_t v = i < n_tiles ? tile_sum[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t incl = x + (warp > 0 ? wsum[warp - 1] : 0u) + carry;
+        if (i < n_tiles) tile_sum[i] = incl - v;
+        __syncthreads();
+        if (t == 1023) carry = incl;
+        __syncthreads();
+    }
+    if (t == 0) *n_valid = carry;
+}
+
+// Per tile: each thread takes CS_ITEMS consecutive cells, the block scans the threads'
+// sums, and every cell with spheres gets its table entry (start, stamp, end).
+template <class F>
+__global__ void __launch_bounds__(CS_THREADS) k_cscan_write(Dev<F> d, DetectBuffers b, const uint32_t *tile_start)
+{
+    __shared__ uint32_t wsum[CS_THREADS / 32];
+    const DevStatus *stp = d.status;
+    if (stp->halt) return;
+    const uint32_t stamp = stp->cell_stamp;
+    const int64_t c0 = (int64_t)blockIdx.x * CS_TILE + (int64_t)threadIdx.x * CS_ITEMS;
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(b.ccount + c0);
+    uint32_t cnt[CS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < CS_ITEMS / 4; ++r) {
+        const uint4 q = c4[r];
+        cnt[4 * r] = q.x; cnt[4 * r + 1] = q.y; cnt[4 * r + 2] = q.z; cnt[4 * r + 3] = q.w;
+    }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < CS_ITEMS; ++k) mine += cnt[k];
+    // exclusive scan of the threads' sums over the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int k = 0; k < warp; ++k) before += wsum[k];
+    uint32_t start = tile_start[blockIdx.x] + before + x - mine;
+#pragma unroll
+    for (int k = 0; k < CS_ITEMS; ++k) {
+        if (cnt[k]) b.cell_tab[c0 + k] = make_uint4(start, stamp, start + cnt[k], 0u);
+        start += cnt[k];
+    }
+}
+
+// Each sphere of a cell to its place in the order, with its key, slot, snapshot, owner and
+// family (what the radix path's sort and k_cellstart produce).
+template <class F>
+__global__ void __launch_bounds__(256) k_cscatter(Dev<F> d, DetectBuffers b, uint32_t *keys_out, uint32_t *vals_out)
+{
+    if (d.status->halt) return;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.n) return;
+    const uint32_t key = b.keys[s];
+    if (key == b.n_cells_total) return;
+    const uint32_t pos = b.cell_tab[key].x + b.crank[s];
+    keys_out[pos] = key;
+    vals_out[pos] = (uint32_t)s;
+    if constexpr (F::voxel) {
+        reinterpret_cast<int4 *>(b.sorted)[pos] = reinterpret_cast<const int4 *>(b.snap)[s];
+        reinterpret_cast<float4 *>(b.sorted_aux)[pos] = reinterpret_cast<const float4 *>(b.snap_aux)[s];
+    } else {
+        reinterpret_cast<double4_32a *>(b.sorted)[pos] = reinterpret_cast<const double4_32a *>(b.snap)[s];
+    }
+    const uint32_t o = d.sph_owner[s];
+    b.sorted_owner[pos] = o;
+    if (d.owner_family) b.sorted_family[pos] = o != 0xffffffffu ? d.owner_family[o] : (uint8_t)0;
+}
+
 // Listed-pair predicate on snapshot entries: squared distance below
 // ((Ri + Rj) + 2 beta)^2, rounded in a fixed order (FP64 or voxel + FP32).
 __device__ __forceinline__ bool listed_f64(double4_32a a, double4_32a b, double b2)
@@ -506,9 +666,15 @@ __global__ void __launch_bounds__(128) k_facet_bin(Dev<F> d, DetectBuffers b, do
     }
 }
 
-// Narrow phase: one thread per sorted entry scans the 27 neighbour cells (as 9 runs of
-// three x-consecutive cells, each contiguous in the sorted order) and the walls of its
-// scene, and writes its full, sorted row into the list that is not in use.
+// Narrow phase, first pass: one thread per sorted entry t tests the candidates after it
+// in the sorted order within its 27 neighbour cells (the half shell: the rest of its own
+// x-run of three cells, from t + 1, and the four full x-runs of cells with larger keys,
+// each run contiguous in the sorted order), so each pair is tested once, by its first
+// entry.  A listed pair is appended to both rows of the list that is not in use, at
+// slots reserved by per-row atomic counters (b.rowcnt, zeroed before the pass); the
+// thread also appends its sphere's walls and facets.  The listed predicate is symmetric
+// in its two spheres, so the rows hold what each sphere's own full scan would list; the
+// second pass (k_rows_finish) sorts them.
 template <class F, bool CLUMPS>
 __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const uint32_t *keys,
                                                  const uint32_t *vals)
@@ -547,40 +713,48 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
     const float b2f = 2.0f * betaf;
     const double b2d = 2.0 * beta;
 
-    uint32_t buf[KMAX];
-    int n = 0;
+    // append e to the row of slot r (entries beyond K are counted, not stored: the second
+    // pass reports the overflow)
+    const uint32_t K = (uint32_t)d.K;
+    uint32_t *prow = d.lists.partner[ln];
+    uint32_t *rc = b.rowcnt;
+    auto put = [&](uint32_t r, uint32_t e) {
+        const uint32_t pos = atomicAdd(&rc[r], 1u);
+        if (pos < K) prow[(int64_t)pos * d.Np + r] = e;
+    };
     const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        if (z < 0 || z >= nz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= ny) continue;
-            uint32_t rowbase = sc.cell_base + (uint32_t)((z * ny + y) * nx);
-            uint32_t lo = 0xffffffffu, hi = 0;
-            for (int x = x0; x <= x1; ++x) {
-                const uint4 r = b.cell_tab[rowbase + (uint32_t)x];
-                if (r.y == stamp) {
-                    if (lo == 0xffffffffu) lo = r.x;
-                    hi = r.z;
-                }
+    // runs (dz, dy): (0, 0) from t + 1, then (0, +1), (+1, -1), (+1, 0), (+1, +1)
+#pragma unroll 1
+    for (int run = 0; run < 5; ++run) {
+        const int dz = run < 2 ? 0 : 1;
+        const int dy = run == 0 ? 0 : (run == 1 ? 1 : run - 3);
+        const int z = cz + dz, y = cy + dy;
+        if (z >= nz || y < 0 || y >= ny) continue;
+        const uint32_t rowbase = sc.cell_base + (uint32_t)((z * ny + y) * nx);
+        uint32_t lo = 0xffffffffu, hi = 0;
+        for (int x = x0; x <= x1; ++x) {
+            const uint4 r = b.cell_tab[rowbase + (uint32_t)x];
+            if (r.y == stamp) {
+                if (lo == 0xffffffffu) lo = r.x;
+                hi = r.z;
             }
-            if (lo == 0xffffffffu) continue;
-            for (uint32_t u = lo; u < hi; ++u) {
-                bool hit;
-                if constexpr (F::voxel) {
-                    if (vals[u] == i) continue;
-                    if (CLUMPS && b.sorted_owner[u] == oi) continue;
-                    if (fam && !families_meet(d.fam_mask, fi, b.sorted_family[u])) continue;
-                    hit = listed_f32(ac, ao, reinterpret_cast<const int4 *>(b.sorted)[u],
-                                     reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
-                } else {
-                    if (vals[u] == i) continue;
-                    if (CLUMPS && b.sorted_owner[u] == oi) continue;
-                    if (fam && !families_meet(d.fam_mask, fi, b.sorted_family[u])) continue;
-                    hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
-                }
-                if (hit) row_insert(buf, n, vals[u]);
+        }
+        if (lo == 0xffffffffu) continue;
+        // the own run holds this entry's cell: only the entries after it
+        if (run == 0) lo = (uint32_t)t + 1u;
+        for (uint32_t u = lo; u < hi; ++u) {
+            if (CLUMPS && b.sorted_owner[u] == oi) continue;
+            if (fam && !families_meet(d.fam_mask, fi, b.sorted_family[u])) continue;
+            bool hit;
+            if constexpr (F::voxel)
+                hit = listed_f32(ac, ao, reinterpret_cast<const int4 *>(b.sorted)[u],
+                                 reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
+            else
+                hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
+            if (hit) {
+                const uint32_t j = vals[u];
+                put(i, j);
+                put(j, i);
             }
         }
     }
@@ -611,7 +785,7 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
                                                          V3<double>{v[6], v[7], v[8]});
                 const V3<double> e = {rsub(pa.x, c.x), rsub(pa.y, c.y), rsub(pa.z, c.z)};
                 const double dist = __dsqrt_rn(radd(radd(rmul(e.x, e.x), rmul(e.y, e.y)), rmul(e.z, e.z)));
-                if (dist < Rs + beta) row_insert(buf, n, WALL_BIT | (uint32_t)b.facet_wall[f]);
+                if (dist < Rs + beta) put(i, WALL_BIT | (uint32_t)b.facet_wall[f]);
             }
         }
     }
@@ -640,7 +814,7 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             const float tol = wall_gap_tol(wl, pf) + 1e-6f * reach;
             if (gf > reach + tol) continue;
             if (gf < reach - tol) {
-                row_insert(buf, n, WALL_BIT | (uint32_t)wg);
+                put(i, WALL_BIT | (uint32_t)wg);
                 continue;
             }
             if (!have64) {
@@ -652,32 +826,53 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             double gap;
             V3<double> nn;
             wall_gap(wl, pa, gap, nn);
-            if (gap < R + beta) row_insert(buf, n, WALL_BIT | (uint32_t)wg);
+            if (gap < R + beta) put(i, WALL_BIT | (uint32_t)wg);
         }
     }
+}
+
+// Narrow phase, second pass: one thread per slot sorts its row of the new list by
+// partner (spheres by id, then walls: their ids carry the top bit) and writes its length;
+// a row longer than K stops the step for a larger K, as a full scan would.  Slots that
+// are inactive or padding get empty rows.
+template <class F>
+__global__ void __launch_bounds__(256) k_rows_finish(Dev<F> d, DetectBuffers b)
+{
+    DevStatus *stp = d.status;
+    if (stp->halt) return;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.Np) return;
+    const int ln = stp->list_cur ^ 1;
     const int K = d.K;
+    const uint32_t total = b.rowcnt[s];
+    int n = (int)min(total, 0x7fffffffu);
+    const unsigned am = __activemask();
+    const int mx = (int)__reduce_max_sync(am, (unsigned)n);
+    if ((threadIdx.x & 31) == (__ffs(am) - 1) && mx > 0) atomicMax(&stp->max_row, mx);
     if (n > K) {
-        atomicMax(&stp->max_row, n);
         stp->overflow = 1;
         stp->halt = HALT_OVERFLOW;
         n = K;
-    } else {
-        atomicMax(&stp->max_row, n);
     }
     uint32_t *prow = d.lists.partner[ln];
-    for (int k = 0; k < n; ++k) prow[(int64_t)k * d.Np + i] = buf[k];
-    d.lists.cnt[ln][i] = (uint8_t)n;
+    if (n > 1) {
+        uint32_t buf[KMAX];
+        int m = 0;
+        for (int k = 0; k < n; ++k) row_insert(buf, m, prow[(int64_t)k * d.Np + s]);
+        for (int k = 0; k < n; ++k) prow[(int64_t)k * d.Np + s] = buf[k];
+    }
+    d.lists.cnt[ln][s] = (uint8_t)n;
 }
 
-// Rows of spheres that are inactive or padding are empty in the new list.
+// The row counters of the list being built start at zero.
 template <class F>
-__global__ void __launch_bounds__(256) k_clear_rows(Dev<F> d)
+__global__ void __launch_bounds__(256) k_clear_rows(Dev<F> d, DetectBuffers b)
 {
     DevStatus *stp = d.status;
     if (stp->halt) return;
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= d.Np) return;
-    d.lists.cnt[stp->list_cur ^ 1][s] = 0;
+    b.rowcnt[s] = 0u;
 }
 
 // Reset the work counter of the new list (which = 0) or of the list in use (which = 1).
@@ -1194,6 +1389,18 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
 __device__ __forceinline__ void audit_slots(unsigned int *audit, int64_t o, int lane, float disp, float disp2,
                                             float speed);
 
+// 1/m and 1/I (isotropic, r_ext 0) of a single sphere from its mass and radius, where the
+// world derives them (Dev::solid): every kernel that integrates rounds them the same way.
+template <class F>
+__device__ __forceinline__ void solid_consts(const Dev<F> &d, typename F::R mass, float rad, typename F::R &im,
+                                             typename F::R4 &ii)
+{
+    using R = typename F::R;
+    im = rdiv(R(1), mass);
+    const R iI = rdiv(R(1), rmul(rmul((R)d.moi_coef, mass), rmul((R)rad, (R)rad)));
+    ii = typename F::R4{iI, iI, iI, R(0)};
+}
+
 // INTEG (single spheres, MODE_STEP): the contact kernel also integrates the owner of the
 // slot, from the state it has already loaded and the force it has just summed, and
 // keeps the running maxima of the audit values in aud[3]; the integration kernel then
@@ -1227,8 +1434,12 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         if constexpr (INTEG) {
             // the rest of the owner's inputs are in flight while the pairs are summed
             q4 = d.st.quat[sp][o];
-            im = d.inv_mass[o];
-            ii = d.inv_moi[o];
+            if (F::voxel && d.solid) {
+                solid_consts<F>(d, me.mass, (float)me.rad, im, ii);
+            } else {
+                im = d.inv_mass[o];
+                ii = d.inv_moi[o];
+            }
         }
     }
     if (act) {
@@ -1498,8 +1709,17 @@ __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp,
     typename F::Aux aux;
     const typename F::Pos po = F::load(src.pos, i, mass, aux);
     const R4 v4 = src.kv[2 * i], w4 = src.kv[2 * i + 1], q4 = src.quat[i];
-    const R im = src.inv_mass[i];
-    const R4 ii = FREE ? R4{R(0), R(0), R(0), R(0)} : src.inv_moi[i];
+    R im;
+    R4 ii;
+    if (!CLUMPS && F::voxel && d.solid) {
+        float rad = 0.0f;
+        if constexpr (F::voxel) rad = aux.rad;
+        solid_consts<F>(d, mass, rad, im, ii);
+        if (FREE) ii = R4{R(0), R(0), R(0), R(0)};
+    } else {
+        im = src.inv_mass[i];
+        ii = FREE ? R4{R(0), R(0), R(0), R(0)} : src.inv_moi[i];
+    }
     const bool iso = CLUMPS ? (bool)src.iso[i] : true;     // a single sphere is isotropic
     const Scene &sc = d.scenes[d.n_scenes > 1 ? src.scene[i] : 0];
     V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
@@ -1586,8 +1806,16 @@ __global__ void __launch_bounds__(FUSED_BLOCK_MAX, 2) k_step_fused(Dev<F> d)
         me.owner = (uint32_t)s;
         V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
         if (act && n > 0) pair_sums<F, false, MODE_STEP>(d, me, sc, s, n, j0, sp, hp, lc, Fs, Ts);
-        integrate_core<F, false>(d, stp, s, sp, act, po, me.mass, v4, w4, d.st.quat[sp][s], d.inv_mass[s],
-                                 d.inv_moi[s], true, sc, Fs, Ts, aux, disp, disp2, speed);
+        R im;
+        R4 ii;
+        if (F::voxel && d.solid) {
+            solid_consts<F>(d, me.mass, (float)me.rad, im, ii);
+        } else {
+            im = d.inv_mass[s];
+            ii = d.inv_moi[s];
+        }
+        integrate_core<F, false>(d, stp, s, sp, act, po, me.mass, v4, w4, d.st.quat[sp][s], im, ii, true, sc, Fs,
+                                 Ts, aux, disp, disp2, speed);
     }
     audit_slots(d.audit, g, lane, disp, disp2, speed);
 }
@@ -1629,7 +1857,10 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
     const int sp = stp->state_par, lc = stp->list_cur;
     const int64_t ntiles = (d.M + ITILE - 1) / ITILE;
     const bool scenes = d.n_scenes > 1;
-    const uint32_t tile_bytes = (uint32_t)(StageLayout::scene + (scenes ? 2 * ITILE : 0));
+    // derived constants (Dev::solid): the 1/I and 1/m arrays are not copied
+    const bool solid = !CLUMPS && d.solid;
+    const uint32_t tile_bytes =
+        (uint32_t)(StageLayout::scene + (scenes ? 2 * ITILE : 0) - (solid ? (16 + 4) * ITILE : 0));
     const int lane = threadIdx.x & 31;
     const uint64_t deadline = global_ns() + STAGE_WAIT_NS;
 
@@ -1641,8 +1872,10 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
         bulk_g2s(b + StageLayout::rec, d.st.pos[sp].rec + o0, 32 * ITILE, &bar[st]);
         bulk_g2s(b + StageLayout::kv, d.st.kv[sp] + 2 * o0, 32 * ITILE, &bar[st]);
         bulk_g2s(b + StageLayout::quat, d.st.quat[sp] + o0, 16 * ITILE, &bar[st]);
-        bulk_g2s(b + StageLayout::moi, d.inv_moi + o0, 16 * ITILE, &bar[st]);
-        bulk_g2s(b + StageLayout::imass, d.inv_mass + o0, 4 * ITILE, &bar[st]);
+        if (!solid) {
+            bulk_g2s(b + StageLayout::moi, d.inv_moi + o0, 16 * ITILE, &bar[st]);
+            bulk_g2s(b + StageLayout::imass, d.inv_mass + o0, 4 * ITILE, &bar[st]);
+        }
         bulk_g2s(b + StageLayout::active, d.st.active[sp] + o0, ITILE, &bar[st]);
         bulk_g2s(b + StageLayout::flags, CLUMPS ? (const void *)(d.owner_iso + o0) : (const void *)(d.lists.cnt[lc] + o0),
                  ITILE, &bar[st]);

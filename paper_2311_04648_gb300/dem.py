@@ -51,7 +51,8 @@ class Stats(C.Structure):
                 ("ms_link", C.c_double), ("n_detect", C.c_int64), ("n_force", C.c_int64), ("ms_total", C.c_double),
                 ("last_cycle", C.c_int64), ("schedule_samples", C.c_int64), ("ms_integrate", C.c_double),
                 ("n_integrate", C.c_int64), ("spheres_with_entries", C.c_int64),
-                ("pair_steps", C.c_int64), ("busy_steps", C.c_int64)]
+                ("pair_steps", C.c_int64), ("busy_steps", C.c_int64), ("derived_constants", C.c_int32),
+                ("counting_sort", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,7 +62,7 @@ class Tuning(C.Structure):
     _fields_ = [("contact_block", C.c_int32), ("integrate_block", C.c_int32), ("narrow_block", C.c_int32),
                 ("detect_inline", C.c_int32), ("step_ms", C.c_double), ("cell_factor", C.c_double),
                 ("integrate_staged", C.c_int32), ("contact_lean", C.c_int32), ("fused_block", C.c_int32),
-                ("margin", C.c_double), ("contact_integrates", C.c_int32)]
+                ("margin", C.c_double), ("contact_integrates", C.c_int32), ("binning", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -70,6 +70,20 @@ def test_roofline_picks_the_dominant_kernel(bench):
     assert r["kernel"].startswith("k_step_fused") and r["bytes_per_launch"] == 88 * 4_000_000 + 32e6
 
 
+def test_contact_kernel_integration_moves_the_busy_owners_bytes(bench):
+    # the owners with listed partners move from the integration kernel's figure to the
+    # contact kernel's; the sum is the step's figure
+    a = bench.algorithmic_bytes("voxel_fp32", 1000, 250, n_with_entries=300, contact_integrates=True)
+    assert a == {"integrate": 88 * 700, "contact": 32 * 250 + 88 * 300, "step": 88 * 1000 + 32 * 250}
+    lb0 = bench.layout_bytes("voxel_fp32", 4_000_000, 1_160_000, 710_000)
+    lb1 = bench.layout_bytes("voxel_fp32", 4_000_000, 1_160_000, 710_000, contact_integrates=True)
+    assert lb1["integrate"] + lb1["contact"] < lb0["integrate"] + lb0["contact"]
+    r = bench.roofline("voxel_fp32", 4_000_000, _prof(100, 0.2, 0.1), 6768.8, "measured", contact_integrates=1)
+    assert r["contact_integrates"] and r["kernel"].startswith("k_contact")
+    assert r["bytes_per_launch"] == 32 * 1.0e6 + 88 * 1.5e6
+    assert r["kernels"]["integrate"]["bytes"] == 88 * 2.5e6 and r["traffic"] is None
+
+
 def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(bench, monkeypatch):
     t = bench.MEASURED_TRAFFIC["contact"]
     same = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in t["source"])

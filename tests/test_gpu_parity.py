@@ -357,6 +357,28 @@ def test_voxel_fp32_trajectory_close_to_oracle_over_short_run():
     assert rel_err(v, ow.v, float(np.max(np.abs(ow.v)))) < 1e-3
 
 
+def test_voxel_fp32_derived_owner_constants_stay_close_to_oracle():
+    # single spheres with I = 0.4 m R^2 throughout: the voxel-form kernels derive 1/m and
+    # 1/I from the mass and radius; one sphere with another inertia makes the world read
+    # them instead.  Both runs follow the oracle, with torques from contacts
+    s = dense_scene(n=500, seed=16, vel=0.2)
+    s2 = dataclasses.replace(s, templates=s.templates + [dataclasses.replace(
+        s.templates[0], moi=s.templates[0].moi * 1.25)],
+        owner_template=np.where(np.arange(s.n_owner) == 7, len(s.templates), s.owner_template))
+    for sc, derived in ((s, 1), (s2, 0)):
+        w = dem.World.from_scene(sc, precision="voxel_fp32")
+        assert w.stats()["derived_constants"] == derived
+        ow = oracle.OracleWorld(sc)
+        w.step(50)
+        ow.step(50)
+        x, q, v, wb = w.owner_state()
+        assert np.max(np.abs(x - ow.x)) < 1e-8
+        assert rel_err(v, ow.v, float(np.max(np.abs(ow.v)))) < 1e-3
+        assert rel_err(wb, ow.wb, float(np.max(np.abs(ow.wb)))) < 1e-3
+        assert np.max(np.abs(ow.wb)) > 0.0
+    assert dem.World.from_scene(s, precision="fp64").stats()["derived_constants"] == 0
+
+
 # ----------------------------------------------------------------------------- schedules, determinism
 
 @pytest.mark.parametrize("precision", ["fp64", "voxel_fp32"])

@@ -286,3 +286,59 @@ def test_fused_step_in_a_batch_and_ignored_for_clumps():
     assert c.tuning()["fused_block"] == 0
     with pytest.raises(Exception):
         c.set_tuning(fused_block=96)
+
+
+@pytest.mark.parametrize("prec", ["voxel_fp32", "fp64"])
+@pytest.mark.parametrize("scene", ["dense", "clumps", "drum", "cone", "paddle"])
+def test_counting_sort_binning_equals_radix_sort_binning(prec, scene):
+    # the detection's two ways of ordering spheres by cell build the same contact lists
+    # (rows sorted by partner), so the runs are the same bits: single spheres, clumps,
+    # walls, a sink and turning facets, both schedules
+    s = {"dense": lambda: W.dense_lattice(n=900, seed=39, vel_sigma=0.3),
+         "clumps": lambda: W.packed_clumps(n=120, seed=40),
+         "drum": lambda: W.drum_bed(n=150, seed=41),
+         "cone": lambda: W.cone_bed(n=300, seed=13),
+         "paddle": lambda: W.paddle_bed(n=300, seed=3)}[scene]()
+    for sched in ("every_step", "velocity_bound"):
+        runs = []
+        for bn in (1, 2):
+            w = dem.World.from_scene(s, precision=prec, schedule=sched)
+            w.set_tuning(binning=bn)
+            assert w.tuning()["binning"] == bn
+            w.step(150)
+            runs.append((_state(w), w.listed_pairs()[0].tolist(), w.listed_wall_pairs()[0].tolist(),
+                         w.stats()["rebuilds"]))
+        (sa, pa, wa, ra), (sb, pb, wb, rb) = runs
+        for x, y in zip(sa, sb):
+            assert np.array_equal(x, y)
+        assert pa == pb and wa == wb and ra == rb
+
+
+def test_counting_sort_binning_with_families_in_a_batch():
+    scenes = [W.dense_lattice(n=150 + 97 * k, seed=45 + k, vel_sigma=0.3) for k in range(3)]
+    beta = 5e-5
+    out = []
+    for bn in (1, 2):
+        b = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+        b.initialize()
+        b.worlds[0].set_tuning(binning=bn)
+        b.step(80)
+        out.append([_state(w) for w in b.worlds])
+    for wa, wb in zip(*out):
+        for x, y in zip(wa, wb):
+            assert np.array_equal(x, y)
+    s = W.dense_lattice(n=400, seed=47, vel_sigma=0.3)
+    fam = np.arange(s.n_owner) % 3
+    res = []
+    for bn in (1, 2):
+        w = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+        w.set_family(0, fam)
+        w.set_family_contacts(1, 2, False)
+        w.set_tuning(binning=bn)
+        w.step(100)
+        res.append((_state(w), w.listed_pairs()[0].tolist()))
+    for x, y in zip(res[0][0], res[1][0]):
+        assert np.array_equal(x, y)
+    assert res[0][1] == res[1][1]
+    with pytest.raises(Exception):
+        w.set_tuning(binning=3)
