@@ -800,6 +800,9 @@ def main():
                    "audit_fallbacks_in_timed_region": res["chosen"]["fallbacks"],
                    "device_copy_gbs_this_gpu": res["copy_gbs"],
                    "tuning": res["tuning"],
+                   "binning": "counting sort" if res["chosen"]["stats"].get("counting_sort") else "radix sort",
+                   "owner_constants": ("1/m and 1/I derived from mass and radius"
+                                       if res["chosen"]["stats"].get("derived_constants") else "read per owner"),
                    "l2": "inputs larger than L2 (owner state + contact lists > 0.5 GB)",
                    "parallelism": f"replica x{world}"},
         "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind, margin=res["chosen"]["stats"]["margin"],

@@ -335,11 +335,20 @@ public:
                 return s;
         }
         pose_facets(sf_);
+        flag_wall_cells(sf_);
         if (N > 0) {
             rebuild_inline(sf_);
             if ((s = settle(err))) return s;
         }
         return DEM_OK;
+    }
+
+    // Which cells a wall may reach (walls keep their shape: computed per cell layout).
+    void flag_wall_cells(cudaStream_t st)
+    {
+        if (m_.n_cells_total == 0) return;
+        k_cell_walls<F><<<grid((int64_t)m_.n_cells_total, 256), 256, 0, st>>>(d_, db_, m_.L,
+                                                                             m_.r_max + m_.margin_max);
     }
 
     // Mesh facets: their wall indices, a share of (cell, facet) pair slots each (enough
@@ -1208,6 +1217,7 @@ private:
                 if ((s = alloc(d_.lists.act[b], d_.Np, err))) return s;
                 if ((s = alloc(d_.lists.n_act[b], 1, err))) return s;
                 if ((s = alloc(d_.lists.perm[b], d_.Np, err))) return s;
+                if ((s = alloc(d_.lists.bcount[b], (d_.Np + 255) / 256 + 1, err))) return s;
             }
         }
         act_alloc_ = true;
@@ -1487,16 +1497,20 @@ private:
     {
         const int64_t len = std::max<int64_t>((n_cells + CS_TILE - 1) / CS_TILE, 1) * CS_TILE;
         uint32_t *cc = nullptr, *ct = nullptr;
+        uint8_t *cw = nullptr;
         dem_status s;
         if ((s = alloc(cc, len, err))) return s;
-        if ((s = alloc(ct, len / CS_TILE, err))) {
+        if ((s = alloc(ct, len / CS_TILE, err)) || (s = alloc(cw, std::max<int64_t>(n_cells, 1), err))) {
             dfree(cc);
+            dfree(ct);
             return s;
         }
         if (db_.ccount) dfree(db_.ccount);
         if (db_.ctile) dfree(db_.ctile);
+        if (db_.cell_wall) dfree(db_.cell_wall);
         db_.ccount = cc;
         db_.ctile = ct;
+        db_.cell_wall = cw;
         db_.ccount_len = len;
         return DEM_OK;
     }
@@ -1539,8 +1553,11 @@ private:
         db_.key_bits = 1;
         while (db_.key_bits < 32 && ((uint64_t)1 << db_.key_bits) <= (uint64_t)m_.n_cells_total) ++db_.key_bits;
         choose_binning();
-        return copy_sync(const_cast<Scene *>(d_.scenes), m_.scenes.data(), m_.scenes.size() * sizeof(Scene),
-                         cudaMemcpyHostToDevice, err);
+        if ((s = copy_sync(const_cast<Scene *>(d_.scenes), m_.scenes.data(), m_.scenes.size() * sizeof(Scene),
+                           cudaMemcpyHostToDevice, err)))
+            return s;
+        flag_wall_cells(sf_);
+        return DEM_OK;
     }
 
     dem_status get_tuning(dem_tuning *t, std::string &err) override
@@ -1936,7 +1953,10 @@ private:
         }
         if (m_.clumps) k_narrow<F, true><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
         else k_narrow<F, false><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
-        k_rows_finish<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, db_);
+        const unsigned nb = grid(d_.Np, 256);
+        k_rows_finish<F><<<nb, 256, 0, st>>>(d_, db_, d_.lists.bcount[0]);
+        // the offsets of the new list's compacted work, ahead of the switch
+        if (!m_.clumps) k_cscan_tiles<<<1, 1024, 0, st>>>(st_, d_.lists.bcount[0], (int64_t)nb, d_.lists.bcount[0] + nb);
     }
 
     void launch_link(cudaStream_t st)
@@ -1951,9 +1971,18 @@ private:
     void launch_compact(cudaStream_t st, int which)
     {
         if (m_.clumps) {
-            k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, which, 0);
+            k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, which, 0, nullptr, 0);
         } else {
-            k_compact<F><<<grid(d_.Np, 256), 256, 0, st>>>(d_, which, 1);
+            // per-block counts and their scan (total last; for a new list both ran on the
+            // detection stream after its rows), then each block writes its entries at its
+            // offset: the work follows slot order
+            const unsigned nb = grid(d_.Np, 256);
+            uint32_t *bc = d_.lists.bcount[which];
+            if (which) {
+                k_compact_count<F><<<nb, 256, 0, st>>>(d_, which, bc);
+                k_cscan_tiles<<<1, 1024, 0, st>>>(st_, bc, (int64_t)nb, bc + nb);
+            }
+            k_compact<F><<<nb, 256, 0, st>>>(d_, which, 1, bc, (int64_t)nb);
         }
     }
 

@@ -42,6 +42,7 @@ struct DetectBuffers {
     uint32_t *ccount, *crank, *ctile;
     int64_t ccount_len;
     int counting;              // 1: this build bins by counting sort, 0: by radix sort
+    uint8_t *cell_wall;        // per cell: 1 if a (non-facet) wall may be in reach from it
 };
 
 // Two contact lists (ELL rows) plus two history buffers; DevStatus selects which.
@@ -72,6 +73,10 @@ struct ListBuffers {
     uint8_t *perm[2];
     // contact wildcards 4..7 of each entry (contact models with more than four; else null)
     typename HistVec<R>::T *wild[2];
+    // single spheres: busy slots per block of 256, scanned into each block's offset in the
+    // compacted work (so that the work follows slot order), the total last; one array for
+    // the compaction of the new list and one for that of the list in use
+    uint32_t *bcount[2];
 };
 
 // Owner-state double buffers.

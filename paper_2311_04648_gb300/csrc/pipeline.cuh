@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
         cz = min(max(cz, 0), sc.nc[2] - 1);
         key = sc.cell_base + (uint32_t)((cz * sc.nc[1] + cy) * sc.nc[0] + cx);
         if constexpr (F::voxel) {
-            reinterpret_cast<int4 *>(b.snap)[s] = make_int4(k.p.cx, k.p.cy, k.p.cz, 0);
+            // voxel indices as floats (exact below 2^24): the listed predicate's
+            // (float)(ia - ib) is then the exact difference fa - fb, with no conversions
+            reinterpret_cast<float4 *>(b.snap)[s] = make_float4((float)k.p.cx, (float)k.p.cy, (float)k.p.cz, 0.0f);
             reinterpret_cast<float4 *>(b.snap_aux)[s] = make_float4(k.p.x, k.p.y, k.p.z, (float)k.rad);
         } else {
             reinterpret_cast<double4_32a *>(b.snap)[s] = make_double4_32a(k.p.x, k.p.y, k.p.z, (double)k.rad);
@@ -565,11 +567,13 @@ __device__ __forceinline__ bool listed_f64(double4_32a a, double4_32a b, double 
     double t = radd(radd(a.w, b.w), b2);
     return s < rmul(t, t);
 }
-__device__ __forceinline__ bool listed_f32(int4 ca, float4 oa, int4 cb, float4 ob, float L, float b2)
+// ca, cb: voxel indices held as floats (integers below 2^21 in magnitude, so their float
+// difference is exactly the converted integer difference)
+__device__ __forceinline__ bool listed_f32(float4 ca, float4 oa, float4 cb, float4 ob, float L, float b2)
 {
-    float dx = radd(rmul((float)(ca.x - cb.x), L), rsub(oa.x, ob.x));
-    float dy = radd(rmul((float)(ca.y - cb.y), L), rsub(oa.y, ob.y));
-    float dz = radd(rmul((float)(ca.z - cb.z), L), rsub(oa.z, ob.z));
+    float dx = radd(rmul(rsub(ca.x, cb.x), L), rsub(oa.x, ob.x));
+    float dy = radd(rmul(rsub(ca.y, cb.y), L), rsub(oa.y, ob.y));
+    float dz = radd(rmul(rsub(ca.z, cb.z), L), rsub(oa.z, ob.z));
     float s = radd(radd(rmul(dx, dx), rmul(dy, dy)), rmul(dz, dz));
     float t = radd(radd(oa.w, ob.w), b2);
     return s < rmul(t, t);
@@ -666,6 +670,47 @@ __global__ void __launch_bounds__(128) k_facet_bin(Dev<F> d, DetectBuffers b, do
     }
 }
 
+// Per cell: 1 if a wall of its scene (facets excepted: they are binned) may be within
+// reach_max = largest radius + largest margin of a sphere centred anywhere in the cell.
+// Plane and cylinder gaps are 1-Lipschitz signed distances, so a cell whose FP64 gap at
+// the centre, less half its diagonal, exceeds reach_max by a rounding allowance is out of
+// every listed sphere's reach; cones and the cells on the grid's boundary (where centres
+// outside the grid are clamped) are always flagged.
+template <class F>
+__global__ void __launch_bounds__(256) k_cell_walls(Dev<F> d, DetectBuffers b, double cell, double reach_max)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (int64_t)b.n_cells_total) return;
+    int lo = 0, hi = d.n_scenes - 1;     // the scene whose cells hold c: last base <= c
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)d.scenes[mid].cell_base <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    const Scene &sc = d.scenes[lo];
+    const uint32_t local = (uint32_t)(c - (int64_t)sc.cell_base);
+    const int nx = sc.nc[0], ny = sc.nc[1], nz = sc.nc[2];
+    const int cx = (int)(local % (uint32_t)nx), cy = (int)((local / (uint32_t)nx) % (uint32_t)ny),
+              cz = (int)(local / (uint32_t)(nx * ny));
+    uint8_t near = 0;
+    if (cx == 0 || cy == 0 || cz == 0 || cx == nx - 1 || cy == ny - 1 || cz == nz - 1) near = 1;
+    const V3<double> ctr = {sc.lo[0] + (cx + 0.5) * cell, sc.lo[1] + (cy + 0.5) * cell, sc.lo[2] + (cz + 0.5) * cell};
+    const double half_diag = 0.8660254037844387 * cell * (1.0 + 1e-6);
+    const double allow = 1e-9 * (fabs(ctr.x) + fabs(ctr.y) + fabs(ctr.z) + 1.0) + 1e-12;
+    for (int wi = 0; wi < sc.wall_count && !near; ++wi) {
+        const Wall &wl = d.walls[sc.wall_begin + wi];
+        if (wl.type != WALL_PLANE && wl.type != WALL_CYLINDER) {
+            near = 1;
+            break;
+        }
+        double gap;
+        V3<double> nn;
+        wall_gap(wl, ctr, gap, nn);
+        if (!(gap - half_diag > reach_max + allow)) near = 1;
+    }
+    b.cell_wall[c] = near;
+}
+
 // Narrow phase, first pass: one thread per sorted entry t tests the candidates after it
 // in the sorted order within its 27 neighbour cells (the half shell: the rest of its own
 // x-run of three cells, from t + 1, and the four full x-runs of cells with larger keys,
@@ -702,10 +747,12 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
     const int cz = (int)(local / (uint32_t)(nx * ny));
 
     double4_32a a64 = make_double4_32a(0, 0, 0, 0);
+    float4 acf = make_float4(0, 0, 0, 0);
     int4 ac = make_int4(0, 0, 0, 0);
     float4 ao = make_float4(0, 0, 0, 0);
     if constexpr (F::voxel) {
-        ac = reinterpret_cast<const int4 *>(b.sorted)[t];
+        acf = reinterpret_cast<const float4 *>(b.sorted)[t];
+        ac = make_int4((int)acf.x, (int)acf.y, (int)acf.z, 0);
         ao = reinterpret_cast<const float4 *>(b.sorted_aux)[t];
     } else {
         a64 = reinterpret_cast<const double4_32a *>(b.sorted)[t];
@@ -747,7 +794,7 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
             if (fam && !families_meet(d.fam_mask, fi, b.sorted_family[u])) continue;
             bool hit;
             if constexpr (F::voxel)
-                hit = listed_f32(ac, ao, reinterpret_cast<const int4 *>(b.sorted)[u],
+                hit = listed_f32(acf, ao, reinterpret_cast<const float4 *>(b.sorted)[u],
                                  reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
             else
                 hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
@@ -791,8 +838,9 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
     }
     // walls: signed gap below R + beta (FP64).  An FP32 gap decides every wall that is
     // clear of the threshold by more than its error bound; only the thin band around the
-    // threshold takes the FP64 test (FP64 throughput is scarce on this part)
-    if (sc.wall_count > 0) {
+    // threshold takes the FP64 test (FP64 throughput is scarce on this part).  Cells that
+    // no wall can reach from any point inside skip the loop (b.cell_wall).
+    if (sc.wall_count > 0 && b.cell_wall[key]) {
         float Rf;
         double R;
         typename F::Pos pp;
@@ -835,20 +883,21 @@ __global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const
 // partner (spheres by id, then walls: their ids carry the top bit) and writes its length;
 // a row longer than K stops the step for a larger K, as a full scan would.  Slots that
 // are inactive or padding get empty rows.
+// Single spheres: the number of rows with entries in each block of 256 slots goes to
+// bcount[block] (the blocks of the compaction), for the scan that orders the compacted work.
 template <class F>
-__global__ void __launch_bounds__(256) k_rows_finish(Dev<F> d, DetectBuffers b)
+__global__ void __launch_bounds__(256) k_rows_finish(Dev<F> d, DetectBuffers b, uint32_t *bcount)
 {
+    __shared__ uint32_t wsum[8];
     DevStatus *stp = d.status;
     if (stp->halt) return;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.Np) return;
+    const bool live = s < d.Np;               // every thread stays for the block sum
     const int ln = stp->list_cur ^ 1;
     const int K = d.K;
-    const uint32_t total = b.rowcnt[s];
-    int n = (int)min(total, 0x7fffffffu);
-    const unsigned am = __activemask();
-    const int mx = (int)__reduce_max_sync(am, (unsigned)n);
-    if ((threadIdx.x & 31) == (__ffs(am) - 1) && mx > 0) atomicMax(&stp->max_row, mx);
+    int n = live ? (int)min(b.rowcnt[s], 0x7fffffffu) : 0;
+    const int mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(&stp->max_row, mx);
     if (n > K) {
         stp->overflow = 1;
         stp->halt = HALT_OVERFLOW;
@@ -861,7 +910,9 @@ __global__ void __launch_bounds__(256) k_rows_finish(Dev<F> d, DetectBuffers b)
         for (int k = 0; k < n; ++k) row_insert(buf, m, prow[(int64_t)k * d.Np + s]);
         for (int k = 0; k < n; ++k) prow[(int64_t)k * d.Np + s] = buf[k];
     }
-    d.lists.cnt[ln][s] = (uint8_t)n;
+    if (live) d.lists.cnt[ln][s] = (uint8_t)n;
+    const uint32_t busy = block_sum_u32((live && s < d.N && n > 0) ? 1u : 0u, wsum);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = busy;
 }
 
 // The row counters of the list being built start at zero.
@@ -899,8 +950,26 @@ static __global__ void __launch_bounds__(256) k_nonfinite(const double *a, int64
 // neighbouring spheres (shared memory sectors) with rows of equal length (no lanes idle
 // through longer rows).  The order of equal lengths and of the blocks depends on
 // scheduling; results do not (every slot's outputs are its own).
+// Single spheres, before phase 1: the busy slots of each block of 256 (bcount[block]); a
+// scan of bcount then gives each block its offset, so the compacted work lists the blocks
+// in slot order (the contact kernel's concurrent threads then cover a narrow window of
+// slots, whose partners' records stay in L2).  For a new list k_rows_finish counts them.
 template <class F>
-__global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase)
+__global__ void __launch_bounds__(256) k_compact_count(Dev<F> d, int which, uint32_t *bcount)
+{
+    __shared__ uint32_t wsum[8];
+    DevStatus *stp = d.status;
+    if (stp->halt) return;
+    const int l = stp->list_cur ^ (which ? 0 : 1);
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool busy = s < d.N && d.lists.cnt[l][s] > 0;
+    const uint32_t tot = block_sum_u32(busy ? 1u : 0u, wsum);
+    if (threadIdx.x == 0) bcount[blockIdx.x] = tot;
+}
+
+template <class F>
+__global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase, const uint32_t *bstart,
+                                                 int64_t nblocks)
 {
     const int warp_level = phase == 0;
     DevStatus *stp = d.status;
@@ -911,7 +980,7 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase)
     const int nrow = s < d.N ? d.lists.cnt[l][s] : 0;
     const bool busy = nrow > 0;
     const unsigned int ball = __ballot_sync(0xffffffffu, busy);
-    if (lane == 0 && ball) atomicAdd(&stp->list_busy[l], (unsigned int)__popc(ball));
+    if (phase == 0 && lane == 0 && ball) atomicAdd(&stp->list_busy[l], (unsigned int)__popc(ball));
     if (phase == 1) {
         __shared__ unsigned int bins[KMAX + 1];
         __shared__ unsigned int all[KMAX + 1];
@@ -930,7 +999,12 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase)
                 run += c;
                 run_all += ca;
             }
-            block_base = run ? atomicAdd(d.lists.n_act[l], run) : 0u;
+            // the block's offset from the scan of the per-block counts (total last)
+            block_base = bstart[blockIdx.x];
+            if (blockIdx.x == 0) {
+                *d.lists.n_act[l] = bstart[nblocks];
+                stp->list_busy[l] = bstart[nblocks];
+            }
         }
         __syncthreads();
         // every slot of the block (empty rows first) by row length, for the fused step
@@ -981,11 +1055,25 @@ __global__ void __launch_bounds__(256) k_link(Dev<F> d)
     const int n = live ? d.lists.cnt[ln][s] : 0;
     const int nold = live ? d.lists.cnt[lo][s] : 0;
     unsigned int owned = 0;                  // pairs this slot owns (partner id above its own)
+    // the first LINK_REG entries of the old row in one batch of independent loads; a new
+    // entry is matched against them by compares in registers (longer rows search the
+    // rest), not by a chain of dependent loads
+    constexpr int LINK_REG = 8;
+    uint32_t oldr[LINK_REG];
+#pragma unroll
+    for (int q = 0; q < LINK_REG; ++q) oldr[q] = q < nold ? po[(int64_t)q * d.Np + s] : 0xffffffffu;
     for (int k = 0; k < n; ++k) {
         int64_t e = (int64_t)k * d.Np + s;
         uint32_t j = pn[e];
         if (!(j & WALL_BIT) && j > (uint32_t)s) ++owned;
-        const int ko = row_find(po, d.Np, s, nold, j);
+        int ko = -1;
+#pragma unroll
+        for (int q = 0; q < LINK_REG; ++q)
+            if (q < nold && oldr[q] == j) ko = q;
+        if (ko < 0 && nold > LINK_REG && j > oldr[LINK_REG - 1]) {
+            const int kr = row_find(po + (int64_t)LINK_REG * d.Np, d.Np, s, nold - LINK_REG, j);
+            if (kr >= 0) ko = kr + LINK_REG;
+        }
         V3<R> u = {R(0), R(0), R(0)};
         R age = R(0);
         if (ko >= 0) u = hist_get<typename HistVec<R>::T, R>(d.lists.hist[hs], (int64_t)ko * d.Np + s, age);
