@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--window-start", type=int, default=-1,
                     help="step at which the warm-up starts (-1: the tuning step when the warm-up and "
                          "timed steps fit in the configuration's steps after it, else as late as they fit)")
+    ap.add_argument("--mixer-start", default="bed", choices=["bed", "above"],
+                    help="mixer: elements start as a bed around the blades (mixing from the first step) or "
+                         "above them (the paper's release)")
     ap.add_argument("--workload", default="column", choices=["column", "drum", "hopper", "batch", "mixer"],
                     help="column: the headline settling column; the others run one configuration at full size")
     ap.add_argument("--clump", default="sphere", choices=["sphere", "rod3", "six"],
@@ -224,37 +227,46 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False, contact_inte
 # read of the force array (32 B per owner with listed partners, under 5% of its bytes
 # here) depends on the margin, so its figure carries no margin.
 MEASURED_TRAFFIC = {
-    "integrate": {"n": 4_000_000, "margin": None, "bytes": 818.1e6,
-                  "source": [("pipeline.cuh", "k_integrate(Dev<F> d)", "271877dcdfc79d92"),
-                             ("pipeline.cuh", "integrate_owner(const Dev<F> &d", "9612bdf5e98a8480"),
-                             ("pipeline.cuh", "integrate_core(const Dev<F> &d", "9233be729e01299e"),
+    "integrate": {"n": 4_000_000, "margin": None, "bytes": 730.4e6, "tuning": {"integrate_staged": 0},
+                  "source": [("pipeline.cuh", "k_integrate(Dev<F> d)", "2a86d66be349aff5"),
+                             ("pipeline.cuh", "integrate_owner(const Dev<F> &d", "00969198b29d2bf1"),
+                             ("pipeline.cuh", "integrate_core(const Dev<F> &d", "b006b33b4402c18e"),
                              ("pipeline.cuh", "audit_slots(unsigned int *audit", "bbac98b73df81d9c"),
                              ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]},
-    "contact": {"n": 4_000_000, "margin": 6e-5, "bytes": 799.8e6,
-                "source": [("pipeline.cuh", "k_contact(Dev<F> d, double *eval_F, double *eval_T)", "41586b578582277e"),
-                           ("pipeline.cuh", "contact_slot(const Dev<F> &d", "1906008c3a9811fb"),
-                           ("pipeline.cuh", "pair_sums(const Dev<F> &d", "c4189f32d1f7e12c"),
+    "contact": {"n": 4_000_000, "margin": 2.1e-5, "bytes": 595.4e6, "tuning": {"contact_lean": 0},
+                "source": [("pipeline.cuh", "k_contact(Dev<F> d, double *eval_F, double *eval_T)", "36e10c0e4e38a6ea"),
+                           ("pipeline.cuh", "contact_slot(const Dev<F> &d", "957e0acb822aecf6"),
+                           ("pipeline.cuh", "pair_sums(const Dev<F> &d", "1d7fda8702d98777"),
                            ("pipeline.cuh", "wall_contact(const Dev<F> &d", "54458541bf779dd2"),
-                           ("pipeline.cuh", "sphere_contact(const Dev<F> &d", "261302666ffedbe3"),
-                           ("pipeline.cuh", "load_sphere(const Dev<F> &d", "1a845165f8f091c6"),
+                           ("pipeline.cuh", "sphere_contact(const Dev<F> &d", "d3359c7f3fec3d02"),
+                           ("pipeline.cuh", "load_sphere(const Dev<F> &d", "e464faf6f6eeda0b"),
                            ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]},
 }
 
 
 def kernel_source_hash(signature, fname="pipeline.cuh"):
+    """Hash of the definition of the function whose text starts with signature (forward
+    declarations, which end at a semicolon before any brace, are skipped)."""
     import hashlib
     with open(os.path.join(ROOT, "paper_2311_04648_gb300", "csrc", fname)) as f:
         src = f.read()
     i = src.find(signature)
-    if i < 0:
-        return None
-    j = src.index("\n}", i)
-    return hashlib.sha1(src[i:j].encode()).hexdigest()[:16]
+    while i >= 0:
+        semi, brace = src.find(";", i), src.find("{", i)
+        if brace >= 0 and (semi < 0 or brace < semi):
+            j = src.index("\n}", i)
+            return hashlib.sha1(src[i:j].encode()).hexdigest()[:16]
+        i = src.find(signature, i + 1)
+    return None
 
 
-def measured_traffic(kernel, n, margin=None):
+def measured_traffic(kernel, n, margin=None, tuning=None):
     t = MEASURED_TRAFFIC.get(kernel)
     if not t or t["n"] != n:
+        return None
+    # the capture's kernel build: a run that chose another (staged integration, lean
+    # contact kernel) has no recorded figure
+    if any((tuning or {}).get(k, v) != v for k, v in t.get("tuning", {}).items()):
         return None
     if t["margin"] is not None and (margin is None or abs(margin - t["margin"]) > 1e-6 * t["margin"]):
         return None
@@ -332,7 +344,7 @@ def fused_step(prof):
 
 
 def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step=0.0, contact_integrates=False,
-             derived=False):
+             derived=False, tuning=None):
     """Roofline of the dominant kernel of a step (largest share of the step's time) and of
     each per-step kernel and the detection phase on its own: algorithmic bytes per
     launch over the average launch duration (CUDA events on the kernel's own stream)."""
@@ -355,7 +367,7 @@ def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step
                          "what": "one list rebuild: hash, sort passes, cell table, narrow phase, history link"}
     for k, v in per.items():
         v["frac"] = (v["gbs"] / peak) if v["gbs"] else None
-        v["traffic"] = (measured_traffic(k, n, margin) if precision == "voxel_fp32" and k in MEASURED_TRAFFIC
+        v["traffic"] = (measured_traffic(k, n, margin, tuning) if precision == "voxel_fp32" and k in MEASURED_TRAFFIC
                         and not ci else None)
     # the dominant kernel among the per-step kernels (the detection phase is several
     # kernels on the second stream, reported beside them)
@@ -596,7 +608,7 @@ def run_scale(args, device, rank=0, world=1):
     elif args.workload == "mixer":
         # Sec. 5's bladed mixer: 2,892 facets turning at 2 pi rad/s, elements released from
         # rest above it, dt = 5e-7 s
-        scene = W.mixer(n=args.n if args.n != 4_000_000 else 2_000_000, clump=args.clump)
+        scene = W.mixer(n=args.n if args.n != 4_000_000 else 2_000_000, clump=args.clump, start=args.mixer_start)
         w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
         out["setup_s"] = time.perf_counter() - t0
         out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache) if args.tune_steps > 0 else w.tuning()
@@ -606,7 +618,8 @@ def run_scale(args, device, rank=0, world=1):
             ms = timed(w.step, w.stream(), steps, "timed_mixer")
         s1 = w.stats()
         n_sph = scene.n_sphere
-        out.update(n_spheres=n_sph, n_elements=scene.n_owner, clump=args.clump, facets=2892, ms=ms, steps=steps,
+        out.update(n_spheres=n_sph, n_elements=scene.n_owner, clump=args.clump, start=args.mixer_start, facets=2892,
+                   ms=ms, steps=steps,
                    clocks=clk.summary(), rebuilds=s1["rebuilds"] - s0["rebuilds"],
                    fallbacks=s1["audit_fallbacks"] - s0["audit_fallbacks"], listed_pairs=s1["listed_pairs"],
                    wall_pairs=s1["wall_pairs"], contacts=s1["active_contacts"],
@@ -808,7 +821,7 @@ def main():
         "roofline": roofline("voxel_fp32", n_sph, prof, peak, peak_kind, margin=res["chosen"]["stats"]["margin"],
                              rebuilds_per_step=res["chosen"]["rebuilds"] / max(steps, 1),
                              contact_integrates=res["tuning"].get("contact_integrates", 0),
-                             derived=bool(res["chosen"]["stats"].get("derived_constants", 0))),
+                             derived=bool(res["chosen"]["stats"].get("derived_constants", 0)), tuning=res["tuning"]),
         "kernels_ms": dict(({"step": prof["contact_ms"]} if fused_step(prof) else
                             {"contact": prof["contact_ms"], "integrate": prof["integrate_ms"]}),
                            detect_per_rebuild=prof["detect_ms"], hash=prof["hash_ms"], link=prof["link_ms"]),

@@ -1706,7 +1706,7 @@ private:
         // not touch, at the price of more rebuilds; the results are the same bits
         if (delayed) {
             const dem_tuning b4 = best;
-            for (double fm : {0.75, 0.5, 0.35}) {
+            for (double fm : {0.75, 0.5, 0.35, 0.25, 0.18}) {
                 dem_tuning t = b4;
                 t.margin = fm * m_.margin_max;
                 t.step_ms = 0.0;

@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(256) k_cell_walls(Dev<F> d, DetectBuffers b, d
 // in its two spheres, so the rows hold what each sphere's own full scan would list; the
 // second pass (k_rows_finish) sorts them.
 template <class F, bool CLUMPS>
-__global__ void __launch_bounds__(256) k_narrow(Dev<F> d, DetectBuffers b, const uint32_t *keys,
+__global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, const uint32_t *keys,
                                                  const uint32_t *vals)
 {
     DevStatus *stp = d.status;

@@ -680,14 +680,18 @@ def six_template(R: float, mat: int = 0, rho: float = RHO) -> Template:
     return Template(xs, np.full(6, R), np.full(6, mat, np.int32), 6 * m1, np.array([I, I, I]))
 
 
-def mixer(n=4_000_000, clump="sphere", omega=2 * math.pi, mu=0.5, seed=7, R=None, vel_sigma=0.0) -> Scene:
+def mixer(n=4_000_000, clump="sphere", omega=2 * math.pi, mu=0.5, seed=7, R=None, vel_sigma=0.0,
+          start="above") -> Scene:
     """The mixer of Sec. 5: elements released at rest from a cylindrical region of radius
     0.5 m and height 1/3 m above a bladed mixer mesh (2,892 facets) that turns at
     omega = 2 pi rad/s inside a cylindrical container with a floor; material and step of
     Sec. 5's table (rho 2600, E 1e9, nu 0.3, CoR 0.2, dt 5e-7 s; mu is not printed:
     0.5).  clump: "sphere", "rod3" (three tangent spheres) or "six" (six on an
     octahedron); the element size follows from n (lattice of the region), as the paper
-    sizes elements to set the count."""
+    sizes elements to set the count.  start="bed": the same lattice starts at the floor
+    instead, leaving out the points within an element's reach of the blades (at their
+    pose at t = 0) and of the hub, so that the turning blades meet the elements from the
+    first step (a short run then times mixing, not the fall onto the blades)."""
     rng = np.random.default_rng(seed)
     Rc, h_mix, H = 0.5, 0.15, 1.0 / 3.0
     ext = {"sphere": 1.0, "rod3": 3.0, "six": 1.0 + math.sqrt(2)}[clump]
@@ -698,10 +702,24 @@ def mixer(n=4_000_000, clump="sphere", omega=2 * math.pi, mu=0.5, seed=7, R=None
     tpl = {"sphere": sphere_template, "rod3": rod_template, "six": six_template}[clump](R, rho=2600.0)
     span = ext * R * 1.05
     g = np.arange(-Rc + span, Rc - span + 1e-12, pitch)
-    zs = np.arange(h_mix + span, h_mix + H - span + 1e-12, pitch)
+    z0 = span if start == "bed" else h_mix + span
+    zs = np.arange(z0, z0 + H + (h_mix if start == "bed" else 0.0) - 2 * span + 1e-12, pitch)
     X, Y, Z = np.meshgrid(g, g, zs, indexing="ij")
     pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
     pts = pts[np.hypot(pts[:, 0], pts[:, 1]) < Rc - span]
+    if start == "bed":
+        # blades: boxes from r_in to r_out, |y| <= thickness / 2, z0 to z1, turned by k pi / 2
+        # (mixer_mesh's defaults), grown by the element's reach; hub prism inside radius hub_r
+        keep = np.hypot(pts[:, 0], pts[:, 1]) > 0.05 + span
+        for k in range(4):
+            c, sn = math.cos(-k * math.pi / 2), math.sin(-k * math.pi / 2)
+            u = c * pts[:, 0] - sn * pts[:, 1]
+            v = sn * pts[:, 0] + c * pts[:, 1]
+            inside = ((u > 0.05 - span) & (u < 0.45 + span) & (np.abs(v) < 0.01 + span)
+                      & (pts[:, 2] > 0.02 - span) & (pts[:, 2] < 0.12 + span))
+            keep &= ~inside
+        keep &= ~((pts[:, 2] > 0.15 - span) & (np.hypot(pts[:, 0], pts[:, 1]) < 0.05 + span))
+        pts = pts[keep]
     pts = pts[np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))][:n]
     m = len(pts)
     q = _identity_quats(m) if clump == "sphere" else _random_quats(rng, m)
@@ -713,4 +731,4 @@ def mixer(n=4_000_000, clump="sphere", omega=2 * math.pi, mu=0.5, seed=7, R=None
     walls += facet_walls(mixer_mesh(), p=(0.0, 0.0, 0.0), omega=(0.0, 0.0, omega))
     return Scene(lo, hi, Em, num, corm, mum, walls, [tpl], np.zeros(m, np.int64), None, pts, q,
                  rng.normal(scale=vel_sigma, size=(m, 3)), np.zeros((m, 3)), 5e-7, np.array([0.0, 0.0, -9.81]),
-                 r_max=R, name=f"mixer_{clump}_n{m}", meta=dict(element_radius=R, facets=2892))
+                 r_max=R, name=f"mixer_{clump}_{start}_n{m}", meta=dict(element_radius=R, facets=2892, start=start))

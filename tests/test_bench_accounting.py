@@ -92,6 +92,15 @@ def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(bench, monke
     assert bench.measured_traffic("contact", t["n"] + 1, m) is None       # another size
     assert bench.measured_traffic("contact", t["n"], 0.35 * m) is None    # another margin
     assert bench.measured_traffic("contact", t["n"]) is None              # margin unknown
+    # another build of the kernel than the captured one: no figure
+    ti = bench.MEASURED_TRAFFIC["integrate"]
+    same_i = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in ti["source"])
+    assert bench.measured_traffic("integrate", ti["n"], tuning={"integrate_staged": 0}) == (ti["bytes"] if same_i else None)
+    assert bench.measured_traffic("integrate", ti["n"], tuning={"integrate_staged": 1}) is None
+    assert bench.measured_traffic("contact", t["n"], m, tuning={"contact_lean": 1}) is None
+    # a forward declaration is not the definition it hashes
+    assert bench.kernel_source_hash("integrate_core(const Dev<F> &d") == bench.kernel_source_hash(
+        "integrate_core(const Dev<F> &d, DevStatus *stp")
     ti = bench.MEASURED_TRAFFIC["integrate"]                             # margin-free
     same_i = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in ti["source"])
     assert bench.measured_traffic("integrate", ti["n"], 0.35 * m) == (ti["bytes"] if same_i else None)

@@ -86,3 +86,20 @@ def test_batch_scenes_follow_their_distributions():
         assert 0.9e-3 <= r.min() and r.max() <= 1.1e-3
         pi, _ = oracle.listed_pairs_f64(np.asarray(sc.x), r, np.arange(len(r)), 0.0)
         assert len(pi) == 0
+
+
+def test_mixer_bed_starts_clear_of_blades_hub_floor_and_container():
+    # the bed start of the Sec. 5 mixer: every element inside the container, above the
+    # floor and clear of the 2,892 facets at their pose at t = 0 (the oracle's brute-force
+    # sphere-wall listing at zero margin), for spheres and three-sphere rods
+    for clump, n in (("sphere", 20_000), ("rod3", 8_000)):
+        s = W.mixer(n=n, clump=clump, start="bed")
+        assert s.n_owner == n and s.meta["start"] == "bed"
+        assert sum(1 for w in s.walls if w["type"] == W.TRIANGLE) == 2892
+        ow = oracle.OracleWorld(s, threads=oracle.max_threads())
+        p = ow.sphere_positions()
+        si, wi = ow.listed_wall_pairs(p, 0.0)
+        assert len(si) == 0
+        assert p[:, 2].min() > 0.0 and np.hypot(p[:, 0], p[:, 1]).max() < 0.5
+        # the bed reaches down among the blades (z from 0.02 to 0.12 m)
+        assert np.sum(p[:, 2] < 0.12) > n // 10
