@@ -29,7 +29,7 @@ constexpr uint64_t VOX_MASK = (1ull << VOX_BITS) - 1;
 enum : int { WALL_PLANE = 0, WALL_CYLINDER = 1, WALL_CONE = 2, WALL_TRIANGLE = 3 };
 
 // halt reasons written by the kernels into DevStatus::halt
-enum : int { HALT_NONE = 0, HALT_DIVERGED = 1, HALT_OVERFLOW = 2, HALT_TIMEOUT = 3 };
+enum : int { HALT_NONE = 0, HALT_DIVERGED = 1, HALT_OVERFLOW = 2, HALT_TIMEOUT = 3, HALT_FACETS = 4 };
 
 template <typename R> struct V3 { R x, y, z; };
 

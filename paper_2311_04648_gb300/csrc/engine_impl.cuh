@@ -363,24 +363,41 @@ public:
         db_.n_facets = (int)fw.size();
         mesh_slack_ = 0.0;
         if (fw.empty()) return DEM_OK;
+        // A facet is binned into the cells whose centre lies within rr = r_max + margin +
+        // half a cell diagonal of it (k_facet_bin; its FP32 allowance is below 1e-5 of
+        // the facet's extent).  Those cells lie inside the facet's neighbourhood of radius
+        // r2 = rr + half a diagonal, whose volume (Steiner's formula for a flat convex
+        // piece of area A and perimeter P: 2 A r + (pi / 2) P r^2 + (4 / 3) pi r^3) over
+        // the cell volume bounds their number.  The bound falls as cells grow, so the
+        // smallest cell gives each facet's share, at any pose and cell size.
         const double cell = m_.L_min;
-        const double reach = m_.r_max + m_.margin_max + 4.0 * cell;
         std::vector<int64_t> off(fw.size() + 1, 0);
         for (size_t f = 0; f < fw.size(); ++f) {
             const Wall &w = m_.walls[fw[f]];
-            double c[3] = {0, 0, 0}, rho = 0.0, rp = 0.0;
-            for (int a = 0; a < 3; ++a) c[a] = (w.tri[a] + w.tri[3 + a] + w.tri[6 + a]) / 3.0;
+            double rp = 0.0, e[3];
             for (int v = 0; v < 3; ++v) {
-                double dc = 0.0, dp = 0.0;
+                double dp = 0.0, de = 0.0;
+                const int v2 = (v + 1) % 3;
                 for (int a = 0; a < 3; ++a) {
-                    dc += (w.tri[3 * v + a] - c[a]) * (w.tri[3 * v + a] - c[a]);
                     dp += (w.tri[3 * v + a] - w.p[a]) * (w.tri[3 * v + a] - w.p[a]);
+                    de += (w.tri[3 * v2 + a] - w.tri[3 * v + a]) * (w.tri[3 * v2 + a] - w.tri[3 * v + a]);
                 }
-                rho = std::max(rho, std::sqrt(dc));
                 rp = std::max(rp, std::sqrt(dp));
+                e[v] = std::sqrt(de);
             }
-            const int64_t per = (int64_t)std::floor((2.0 * rho + 2.0 * reach) / cell) + 2;
-            off[f + 1] = off[f] + per * per * per;
+            const double perim = e[0] + e[1] + e[2];
+            double cr[3];
+            const double u[3] = {w.tri[3] - w.tri[0], w.tri[4] - w.tri[1], w.tri[5] - w.tri[2]};
+            const double q[3] = {w.tri[6] - w.tri[0], w.tri[7] - w.tri[1], w.tri[8] - w.tri[2]};
+            cr[0] = u[1] * q[2] - u[2] * q[1];
+            cr[1] = u[2] * q[0] - u[0] * q[2];
+            cr[2] = u[0] * q[1] - u[1] * q[0];
+            const double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            const double ext = std::max(std::max(e[0], e[1]), e[2]) * 2.0 + 8.0 * cell;
+            const double r2 = m_.r_max + m_.margin_max + std::sqrt(3.0) * cell + 2e-5 * ext + 1e-9;
+            const double vol = 2.0 * area * r2 + 0.5 * M_PI * perim * r2 * r2 + 4.0 / 3.0 * M_PI * r2 * r2 * r2;
+            const int64_t per = (int64_t)std::ceil(1.02 * vol / (cell * cell * cell)) + 8;
+            off[f + 1] = off[f] + per;
             const double wn = std::sqrt(w.omega[0] * w.omega[0] + w.omega[1] * w.omega[1] + w.omega[2] * w.omega[2]);
             mesh_slack_ = std::max(mesh_slack_, 1.000001 * wn * rp * m_.scenes[w.scene].h);
         }
@@ -1908,6 +1925,10 @@ private:
                   std::to_string(sth_->steps_done);
             return DEM_ERR_DIVERGED;
         }
+        if (sth_->halt == HALT_FACETS) {
+            err = "a mesh facet's cell bins overflowed their share";
+            return DEM_ERR_OVERFLOW;
+        }
         if (sth_->halt != HALT_NONE) {
             err = "halted (code " + std::to_string(sth_->halt) + ")";
             return DEM_ERR_TIMEOUT;
@@ -1944,7 +1965,7 @@ private:
         }
         if (db_.n_facets > 0) {
             // bin the facets at their pose of the snapshot and sort the pairs by cell
-            k_facet_bin<F><<<grid(db_.n_facets, 128), 128, 0, st>>>(d_, db_, m_.r_max);
+            k_facet_bin<F><<<grid((int64_t)db_.n_facets * 32, 128), 128, 0, st>>>(d_, db_, m_.r_max);
             uint32_t *fk, *fv;
             radix_sort_u32(db_.fkeys, db_.fvals, db_.fkeys_alt, db_.fvals_alt, db_.n_fpairs, db_.key_bits, db_.fhist,
                            db_.fhist_cap, st, &fk, &fv);

@@ -630,43 +630,112 @@ __global__ void __launch_bounds__(128) k_facet_pose(Dev<F> d, Wall *walls, const
     facet_pose(w, t, w.cur);
 }
 
-// Bin every facet, at its pose of the snapshot step, into the cells its reach covers
-// (its bounding box grown by reach = largest radius + margin + one cell edge): pairs
-// (cell key, facet) from the facet's first slot, the unused slots of its share keyed
-// past every cell.
+// Squared distance from p to the triangle (0, u, w) in FP32 (the region tests of the
+// closest-point-on-triangle algorithm); only used to decide, with an allowance, which
+// cells a facet is binned into.
+__device__ __forceinline__ float tri_dist2_f(float3 p, float3 u, float3 w)
+{
+    auto dt = [](float3 x, float3 y) { return x.x * y.x + x.y * y.y + x.z * y.z; };
+    auto sub = [](float3 x, float3 y) { return make_float3(x.x - y.x, x.y - y.y, x.z - y.z); };
+    float3 q;
+    const float d1 = dt(u, p), d2 = dt(w, p);
+    const float3 bp = sub(p, u), cp = sub(p, w);
+    const float d3 = dt(u, bp), d4 = dt(w, bp), d5 = dt(u, cp), d6 = dt(w, cp);
+    const float vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+    if (d1 <= 0.0f && d2 <= 0.0f) {
+        q = make_float3(0.0f, 0.0f, 0.0f);
+    } else if (d3 >= 0.0f && d4 <= d3) {
+        q = u;
+    } else if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) {
+        const float t = d1 / (d1 - d3);
+        q = make_float3(t * u.x, t * u.y, t * u.z);
+    } else if (d6 >= 0.0f && d5 <= d6) {
+        q = w;
+    } else if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) {
+        const float t = d2 / (d2 - d6);
+        q = make_float3(t * w.x, t * w.y, t * w.z);
+    } else if (va <= 0.0f && (d4 - d3) >= 0.0f && (d5 - d6) >= 0.0f) {
+        const float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        q = make_float3(u.x + t * (w.x - u.x), u.y + t * (w.y - u.y), u.z + t * (w.z - u.z));
+    } else {
+        const float den = 1.0f / (va + vb + vc);
+        const float v = vb * den, ww = vc * den;
+        q = make_float3(v * u.x + ww * w.x, v * u.y + ww * w.y, v * u.z + ww * w.z);
+    }
+    const float3 e = sub(p, q);
+    return dt(e, e);
+}
+
+// Bin every facet, at its pose of the snapshot step, into the cells whose centre lies
+// within rr = largest radius + margin + half a cell diagonal of it (a sphere centred in
+// the cell within R + margin of the facet implies that): pairs (cell key, facet) from the
+// facet's first slot, the unused slots of its share keyed past every cell.  One warp per
+// facet walks the facet's bounding box (grown by rr): a plane test, then the distance to
+// the triangle, in FP32 relative to the facet's first vertex with an allowance.  A share
+// holds every such cell (its size bounds the volume of the facet's neighbourhood, see
+// setup_facets); should it not, the step halts (HALT_FACETS) rather than lose a contact.
 template <class F>
 __global__ void __launch_bounds__(128) k_facet_bin(Dev<F> d, DetectBuffers b, double r_max)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= b.n_facets || d.status->halt) return;
+    const int f = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (f >= b.n_facets || d.status->halt) return;       // whole warps
     const Wall &w = d.walls[b.facet_wall[f]];
     const Scene &sc = d.scenes[w.scene];
     double v[9];
     facet_pose(w, rmul((double)d.status->snap_step, sc.h), v);
-    for (int q = 0; q < 9; ++q) b.tri_snap[9 * (int64_t)f + q] = v[q];
+    if (lane < 9) b.tri_snap[9 * (int64_t)f + lane] = v[lane];
     const double cell = 1.0 / d.invL;
-    const double reach = r_max + d.status->beta_next + cell;
-    int lo[3], hi[3];
+    const double rr = r_max + d.status->beta_next + 0.8660254037844387 * cell;
+    int lo[3], n[3];
     for (int a = 0; a < 3; ++a) {
-        const double mn = fmin(fmin(v[a], v[3 + a]), v[6 + a]) - reach;
-        const double mx = fmax(fmax(v[a], v[3 + a]), v[6 + a]) + reach;
-        lo[a] = (int)floor((mn - sc.lo[a]) * d.invL);
-        hi[a] = (int)floor((mx - sc.lo[a]) * d.invL);
-        lo[a] = min(max(lo[a], 0), sc.nc[a] - 1);
-        hi[a] = min(max(hi[a], 0), sc.nc[a] - 1);
+        const double mn = fmin(fmin(v[a], v[3 + a]), v[6 + a]) - rr;
+        const double mx = fmax(fmax(v[a], v[3 + a]), v[6 + a]) + rr;
+        int l = (int)floor((mn - sc.lo[a]) * d.invL), h = (int)floor((mx - sc.lo[a]) * d.invL);
+        l = min(max(l, 0), sc.nc[a] - 1);
+        h = min(max(h, 0), sc.nc[a] - 1);
+        lo[a] = l;
+        n[a] = h - l + 1;
     }
-    int64_t slot = b.facet_off[f];
-    const int64_t end = b.facet_off[f + 1];
-    for (int z = lo[2]; z <= hi[2]; ++z)
-        for (int y = lo[1]; y <= hi[1]; ++y)
-            for (int x = lo[0]; x <= hi[0] && slot < end; ++x) {
-                b.fkeys[slot] = sc.cell_base + (uint32_t)((z * sc.nc[1] + y) * sc.nc[0] + x);
-                b.fvals[slot] = (uint32_t)f;
-                ++slot;
+    const float3 u = make_float3((float)(v[3] - v[0]), (float)(v[4] - v[1]), (float)(v[5] - v[2]));
+    const float3 ww = make_float3((float)(v[6] - v[0]), (float)(v[7] - v[1]), (float)(v[8] - v[2]));
+    float3 nrm = make_float3(u.y * ww.z - u.z * ww.y, u.z * ww.x - u.x * ww.z, u.x * ww.y - u.y * ww.x);
+    const float nl = sqrtf(nrm.x * nrm.x + nrm.y * nrm.y + nrm.z * nrm.z);
+    nrm = make_float3(nrm.x / nl, nrm.y / nl, nrm.z / nl);
+    const float ext = fmaxf(fmaxf(fabsf(u.x) + fabsf(u.y) + fabsf(u.z), fabsf(ww.x) + fabsf(ww.y) + fabsf(ww.z)),
+                            (float)(rr + cell));
+    const float lim = (float)rr + 1e-5f * ext + 1e-9f;       // rr plus the FP32 allowance
+    const int64_t base = b.facet_off[f], end = b.facet_off[f + 1];
+    const int64_t total = (int64_t)n[0] * n[1] * n[2];
+    int64_t count = 0;                                        // the same in every lane
+    for (int64_t k0 = 0; k0 < total; k0 += 32) {
+        const int64_t k = k0 + lane;
+        bool hit = false;
+        uint32_t key = 0;
+        if (k < total) {
+            const int x = lo[0] + (int)(k % n[0]), y = lo[1] + (int)((k / n[0]) % n[1]),
+                      z = lo[2] + (int)(k / ((int64_t)n[0] * n[1]));
+            const float3 p = make_float3((float)(sc.lo[0] + (x + 0.5) * cell - v[0]),
+                                         (float)(sc.lo[1] + (y + 0.5) * cell - v[1]),
+                                         (float)(sc.lo[2] + (z + 0.5) * cell - v[2]));
+            const float pd = p.x * nrm.x + p.y * nrm.y + p.z * nrm.z;
+            if (fabsf(pd) <= lim && tri_dist2_f(p, u, ww) <= lim * lim) {
+                hit = true;
+                key = sc.cell_base + (uint32_t)((z * sc.nc[1] + y) * sc.nc[0] + x);
             }
-    for (; slot < end; ++slot) {
-        b.fkeys[slot] = b.n_cells_total;
-        b.fvals[slot] = (uint32_t)f;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, hit);
+        const int64_t pos = base + count + __popc(ball & ((1u << lane) - 1u));
+        if (hit && pos < end) {
+            b.fkeys[pos] = key;
+            b.fvals[pos] = (uint32_t)f;
+        }
+        count += __popc(ball);
+    }
+    if (base + count > end && lane == 0) atomicCAS(&d.status->halt, HALT_NONE, HALT_FACETS);
+    for (int64_t q = base + count + lane; q < end; q += 32) {
+        b.fkeys[q] = b.n_cells_total;
+        b.fvals[q] = (uint32_t)f;
     }
 }
 
