@@ -1971,6 +1971,7 @@ private:
                            db_.fhist_cap, st, &fk, &fv);
             db_.fkeys_sorted = fk;
             db_.fvals_sorted = fv;
+            k_facet_cells<<<grid(db_.n_fpairs, 256), 256, 0, st>>>(st_, db_);
         }
         if (m_.clumps) k_narrow<F, true><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
         else k_narrow<F, false><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
@@ -2203,18 +2204,23 @@ private:
     {
         const double h = m_.scenes.empty() ? 1e-6 : m_.scenes[0].h;
         double v = std::max(sth_->vmax_last, 1e-3) * 1.5;
-        long long c = (long long)std::floor(beta_ / (2.0 * h * v));
+        // the audit also counts a fixed slack per step (the position rounding of the voxel
+        // form and the largest facet displacement of a turning mesh): a cycle longer than
+        // the margin allows for that alone would always end in a fallback
+        const double slack = sth_->disp_slack;
+        long long c = (long long)std::floor(beta_ / (2.0 * (h * v + slack)));
         if (m_.schedule == DEM_SCHEDULE_LEARNED) {
             std::string err;
             long long lc = learned_cycle(err);
-            if (lc > 0) c = lc;
+            if (lc > 0) c = slack > 0.0 ? std::min<long long>(lc, (long long)std::floor(beta_ / (2.0 * slack))) : lc;
         }
         // a cycle cut short by the audit shrinks the next ones (x0.6); cycles that run to
         // their end let the factor recover (x1.1 up to 1): fewer inline fallback rebuilds
         // where the motion outgrows the bound, no change where it does not
         c = (long long)std::floor((double)c * cycle_scale_);
         cycle_scale_ = std::min(1.0, cycle_scale_ * 1.1);
-        last_cycle_ = std::max<long long>(1, std::min<long long>(c, 2000));
+        // at most 512 steps a cycle: a captured cycle graph stays a few thousand nodes
+        last_cycle_ = std::max<long long>(1, std::min<long long>(c, 512));
         return last_cycle_;
     }
     long long last_cycle_ = 0;

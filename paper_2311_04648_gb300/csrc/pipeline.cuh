@@ -383,7 +383,10 @@ __global__ void __launch_bounds__(256) k_cellstart(Dev<F> d, DetectBuffers b, co
     const uint32_t stamp = d.status->cell_stamp;
     if (k != sent) {
         // the first entry of a run writes (start, stamp), the last writes end: disjoint words
-        if (t == 0 || keys[t - 1] != k) reinterpret_cast<uint2 *>(&b.cell_tab[k])[0] = make_uint2((uint32_t)t, stamp);
+        if (t == 0 || keys[t - 1] != k) {
+            reinterpret_cast<uint2 *>(&b.cell_tab[k])[0] = make_uint2((uint32_t)t, stamp);
+            b.cell_tab[k].w = 0u;                 // no facet pairs until k_facet_cells says so
+        }
         if (t == b.n - 1 || keys[t + 1] != k) b.cell_tab[k].z = (uint32_t)(t + 1);
         if (t == b.n - 1 || keys[t + 1] == sent) *b.n_valid = (uint32_t)(t + 1);
     } else if (t == 0) {
@@ -604,8 +607,15 @@ __device__ __forceinline__ void facet_pose(const Wall &w, double t, double *v)
     }
     const V3<double> k = {__ddiv_rn(om.x, wn), __ddiv_rn(om.y, wn), __ddiv_rn(om.z, wn)};
     const double th = rmul(wn, t);
-    double sn, cs;
-    sincos(th, &sn, &cs);
+    // the lanes turning by the same angle (the facets of one mesh) share one FP64
+    // sine and cosine, computed by the first of them: the same values, far fewer FP64
+    // instructions on a part where they are scarce
+    const unsigned grp = __match_any_sync(__activemask(), (unsigned long long)__double_as_longlong(th));
+    const int leader = __ffs(grp) - 1;
+    double sn = 0.0, cs = 0.0;
+    if ((int)(threadIdx.x & 31) == leader) sincos(th, &sn, &cs);
+    sn = __shfl_sync(grp, sn, leader);
+    cs = __shfl_sync(grp, cs, leader);
     const double omc = rsub(1.0, cs);
     for (int m = 0; m < 3; ++m) {
         const V3<double> r = {rsub(w.tri[3 * m], w.p[0]), rsub(w.tri[3 * m + 1], w.p[1]), rsub(w.tri[3 * m + 2], w.p[2])};
@@ -739,6 +749,19 @@ __global__ void __launch_bounds__(128) k_facet_bin(Dev<F> d, DetectBuffers b, do
     }
 }
 
+// After the facet pairs are sorted by cell: the first pair of each cell's run, plus one,
+// into the fourth word of the cell's table entry (the binning wrote that word zero in
+// every cell holding spheres; cells without spheres are never looked up).
+static __global__ void __launch_bounds__(256) k_facet_cells(const DevStatus *stp, DetectBuffers b)
+{
+    if (stp->halt) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= b.n_fpairs) return;
+    const uint32_t key = b.fkeys_sorted[q];
+    if (key >= b.n_cells_total) return;
+    if (q == 0 || b.fkeys_sorted[q - 1] != key) b.cell_tab[key].w = (uint32_t)(q + 1);
+}
+
 // Per cell: 1 if a wall of its scene (facets excepted: they are binned) may be within
 // reach_max = largest radius + largest margin of a sphere centred anywhere in the cell.
 // Plane and cylinder gaps are 1-Lipschitz signed distances, so a cell whose FP64 gap at
@@ -839,6 +862,7 @@ __global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, co
         if (pos < K) prow[(int64_t)pos * d.Np + r] = e;
     };
     const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
+    uint32_t own_facets = 0;     // the own cell's first (cell, facet) pair + 1, 0 for none
     // runs (dz, dy): (0, 0) from t + 1, then (0, +1), (+1, -1), (+1, 0), (+1, +1)
 #pragma unroll 1
     for (int run = 0; run < 5; ++run) {
@@ -854,6 +878,7 @@ __global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, co
                 if (lo == 0xffffffffu) lo = r.x;
                 hi = r.z;
             }
+            if (run == 0 && x == cx) own_facets = r.w;
         }
         if (lo == 0xffffffffu) continue;
         // the own run holds this entry's cell: only the entries after it
@@ -876,15 +901,10 @@ __global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, co
     }
     // mesh facets binned into this cell: distance from the centre below R + beta (FP64, at
     // the facets' pose of the snapshot)
-    if (b.n_facets > 0) {
+    if (b.n_facets > 0 && own_facets) {
         const uint32_t *fk = b.fkeys_sorted;
-        int64_t lo = 0, hi = b.n_fpairs;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (fk[mid] < key) lo = mid + 1;
-            else hi = mid;
-        }
-        if (lo < b.n_fpairs && fk[lo] == key) {
+        const int64_t lo = (int64_t)own_facets - 1;      // k_facet_cells: the cell's first pair
+        {
             V3<double> pa;
             double Rs;
             if constexpr (F::voxel) {
