@@ -134,6 +134,36 @@ struct SphereK {
     uint32_t owner;
 };
 
+// A single sphere's position record (and, in the FP64 form, its radius and material)
+// without its velocities: the partner of a listed pair, whose velocities are read only
+// where the pair overlaps.  The same values as load_sphere<F, false, false> otherwise.
+template <class F>
+__device__ __forceinline__ SphereK<F> load_sphere_pos(const Dev<F> &d, int sp, uint32_t s)
+{
+    using R = typename F::R;
+    SphereK<F> k;
+    k.owner = s;
+    R mass;
+    typename F::Aux aux;
+    k.p = F::load(d.st.pos[sp], s, mass, aux);
+    k.mass = mass;
+    k.rl = {R(0), R(0), R(0)};
+    k.v = {R(0), R(0), R(0)};
+    k.w = {R(0), R(0), R(0)};
+    k.acc0 = k.acc1 = R(0);
+    if constexpr (F::voxel) {
+        k.rad = aux.rad;
+        k.rlo = aux.rlo;
+        k.mat = -1;
+    } else {
+        const auto pk = d.sph_pack[s];
+        k.rad = pk.x;
+        k.rlo = 0.0f;
+        k.mat = (int)pk.y;
+    }
+    return k;
+}
+
 // MAT false: the material is left at -1 where it would need a load of its own (a single
 // sphere in the voxel form, whose other constants ride in its position record); the
 // caller reads it only if the scene has several materials.
@@ -205,14 +235,12 @@ __device__ __forceinline__ V3<R> point_velocity(V3<R> v, V3<R> w, V3<R> r)
 // overlap is not positive.
 // ANY: the geometry whatever the sign of the overlap (bonded contacts act across a gap);
 // false only where the centres coincide.
-template <class F, bool PARAMS = true, bool ANY = false>
-__device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
-                                               ContactIn<typename F::R> &c, V3<typename F::R> &armA,
-                                               V3<typename F::R> &armB)
+// Centre difference, distance and overlap of two spheres (positions and radii only).
+template <class F>
+__device__ __forceinline__ void sphere_gap(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
+                                           V3<typename F::R> &dd, typename F::R &dist, typename F::R &delta)
 {
     using R = typename F::R;
-    V3<R> dd;
-    R dist, delta;
     if constexpr (F::voxel) {
         delta = overlap_ff(A.p, B.p, d.L, A.rad, A.rlo, B.rad, B.rlo, dd, dist);
     } else {
@@ -221,6 +249,39 @@ __device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F>
         dist = sqrt(ss);
         delta = rsub(radd(A.rad, B.rad), dist);
     }
+}
+
+// The rest of a sphere pair's contact geometry and kinematics from its gap: normal, arms,
+// contact-point velocities, effective radius and mass.
+template <class F, bool PARAMS = true>
+__device__ __forceinline__ void sphere_finish(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
+                                              V3<typename F::R> dd, typename F::R dist, typename F::R delta,
+                                              ContactIn<typename F::R> &c, V3<typename F::R> &armA,
+                                              V3<typename F::R> &armB)
+{
+    using R = typename F::R;
+    R inv = R(1) / dist;
+    c.n = {rmul(inv, dd.x), rmul(inv, dd.y), rmul(inv, dd.z)};
+    c.delta = delta;
+    const R half = rmul(R(0.5), delta);
+    armA = arm_of(A.rl, -rsub(A.rad, half), c.n);
+    armB = arm_of(B.rl, rsub(B.rad, half), c.n);
+    c.uA = point_velocity(A.v, A.w, armA);
+    c.uB = point_velocity(B.v, B.w, armB);
+    c.Rbar = (A.rad * B.rad) / (A.rad + B.rad);
+    c.mbar = (A.mass * B.mass) / (A.mass + B.mass);
+    if constexpr (PARAMS) load_pair(d.pairs, d.pairs_f, d.mat_scene, d.mat_local, d.scenes, A.mat, B.mat, c);
+}
+
+template <class F, bool PARAMS = true, bool ANY = false>
+__device__ __forceinline__ bool sphere_contact(const Dev<F> &d, const SphereK<F> &A, const SphereK<F> &B,
+                                               ContactIn<typename F::R> &c, V3<typename F::R> &armA,
+                                               V3<typename F::R> &armB)
+{
+    using R = typename F::R;
+    V3<R> dd;
+    R dist, delta;
+    sphere_gap<F>(d, A, B, dd, dist, delta);
     if ((!ANY && !(delta > R(0))) || !(dist > R(0))) return false;
     R inv = R(1) / dist;
     c.n = {rmul(inv, dd.x), rmul(inv, dd.y), rmul(inv, dd.z)};
@@ -1345,17 +1406,39 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
         const uint32_t j = j_next;
         if (k + 1 < n) j_next = prow[e + d.Np];      // next partner's id in flight early
         R age = R(0);
-        V3<R> ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
+        V3<R> ut = zero;
         ContactIn<R> c;
         V3<R> armA, armB;
         V3<R> wB = zero;                 // the partner's angular velocity (ROLL only)
         bool on;
-        int mb;
+        int mb = 0;
         if (j & WALL_BIT) {
+            ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
             const Wall &w = d.walls[j & ~WALL_BIT];
             mb = w.mat;
             on = wall_contact<F, false>(d, me, sc, w, c, armA);
+        } else if constexpr (!CLUMPS) {
+            // single spheres: the partner's position record first; its velocities, its
+            // activity and this entry's history only where the two overlap (most listed
+            // pairs do not touch).  The pair is evaluated in this thread's own orientation
+            // with this side's copy of the history (the partner's is its exact negation)
+            SphereK<F> other = load_sphere_pos<F>(d, sp, j);
+            V3<R> dd;
+            R dist, delta;
+            sphere_gap<F>(d, me, other, dd, dist, delta);
+            on = delta > R(0) && dist > R(0) && d.st.active[sp][j];
+            if (on) {
+                const auto v4 = d.st.kv[sp][2 * j];
+                const auto w4 = d.st.kv[sp][2 * j + 1];
+                ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
+                other.v = {v4.x, v4.y, v4.z};
+                other.w = {w4.x, w4.y, w4.z};
+                mb = other.mat >= 0 || one ? other.mat : (int)d.sph_mat[j];
+                sphere_finish<F, false>(d, me, other, dd, dist, delta, c, armA, armB);
+                if constexpr (ROLL) wB = other.w;
+            }
         } else {
+            ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
             SphereK<F> other = load_sphere<F, CLUMPS, false>(d, sp, j);
             if (!d.st.active[sp][other.owner]) {
                 if (MODE == MODE_STEP) hist_put(hout, e, zero);
