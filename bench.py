@@ -226,21 +226,30 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False, contact_inte
 # pairs are listed.  The integration streams every owner whatever the margin; only its
 # read of the force array (32 B per owner with listed partners, under 5% of its bytes
 # here) depends on the margin, so its figure carries no margin.
+_INTEGRATE_SOURCE = [("pipeline.cuh", "integrate_owner(const Dev<F> &d", "00969198b29d2bf1"),
+                     ("pipeline.cuh", "integrate_core(const Dev<F> &d", "b006b33b4402c18e"),
+                     ("pipeline.cuh", "audit_slots(unsigned int *audit", "bbac98b73df81d9c"),
+                     ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]
 MEASURED_TRAFFIC = {
-    "integrate": {"n": 4_000_000, "margin": None, "bytes": 730.4e6, "tuning": {"integrate_staged": 0},
-                  "source": [("pipeline.cuh", "k_integrate(Dev<F> d)", "2a86d66be349aff5"),
-                             ("pipeline.cuh", "integrate_owner(const Dev<F> &d", "00969198b29d2bf1"),
-                             ("pipeline.cuh", "integrate_core(const Dev<F> &d", "b006b33b4402c18e"),
-                             ("pipeline.cuh", "audit_slots(unsigned int *audit", "bbac98b73df81d9c"),
-                             ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]},
-    "contact": {"n": 4_000_000, "margin": 2.1e-5, "bytes": 595.4e6, "tuning": {"contact_lean": 0},
-                "source": [("pipeline.cuh", "k_contact(Dev<F> d, double *eval_F, double *eval_T)", "36e10c0e4e38a6ea"),
-                           ("pipeline.cuh", "contact_slot(const Dev<F> &d", "957e0acb822aecf6"),
-                           ("pipeline.cuh", "pair_sums(const Dev<F> &d", "1d7fda8702d98777"),
-                           ("pipeline.cuh", "wall_contact(const Dev<F> &d", "54458541bf779dd2"),
-                           ("pipeline.cuh", "sphere_contact(const Dev<F> &d", "d3359c7f3fec3d02"),
-                           ("pipeline.cuh", "load_sphere(const Dev<F> &d", "e464faf6f6eeda0b"),
-                           ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]},
+    "integrate": [
+        {"n": 4_000_000, "margin": None, "bytes": 730.4e6, "tuning": {"integrate_staged": 0},
+         "source": [("pipeline.cuh", "k_integrate(Dev<F> d)", "2a86d66be349aff5")] + _INTEGRATE_SOURCE},
+        {"n": 4_000_000, "margin": None, "bytes": 726.6e6, "tuning": {"integrate_staged": 1},
+         "source": [("pipeline.cuh", "k_integrate_staged(Dev<FormF32> d)", "a2d764678f9b801a"),
+                    ("pipeline.cuh", "struct StageLayout {", "a4f1f17d327f7a13")] + _INTEGRATE_SOURCE},
+    ],
+    "contact": [
+        {"n": 4_000_000, "margin": 2.1e-5, "bytes": 518.9e6, "tuning": {"contact_lean": 0},
+         "source": [("pipeline.cuh", "k_contact(Dev<F> d, double *eval_F, double *eval_T)", "36e10c0e4e38a6ea"),
+                    ("pipeline.cuh", "contact_slot(const Dev<F> &d", "957e0acb822aecf6"),
+                    ("pipeline.cuh", "pair_sums(const Dev<F> &d", "400936f26fc6c0f7"),
+                    ("pipeline.cuh", "wall_contact(const Dev<F> &d", "54458541bf779dd2"),
+                    ("pipeline.cuh", "sphere_gap(const Dev<F> &d", "64de1a81d6ab41e3"),
+                    ("pipeline.cuh", "sphere_finish(const Dev<F> &d", "3fde901e334f3796"),
+                    ("pipeline.cuh", "load_sphere_pos(const Dev<F> &d", "f767f41ecac8ae6a"),
+                    ("pipeline.cuh", "load_sphere(const Dev<F> &d", "e464faf6f6eeda0b"),
+                    ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]},
+    ],
 }
 
 
@@ -261,18 +270,22 @@ def kernel_source_hash(signature, fname="pipeline.cuh"):
 
 
 def measured_traffic(kernel, n, margin=None, tuning=None):
-    t = MEASURED_TRAFFIC.get(kernel)
-    if not t or t["n"] != n:
-        return None
-    # the capture's kernel build: a run that chose another (staged integration, lean
-    # contact kernel) has no recorded figure
-    if any((tuning or {}).get(k, v) != v for k, v in t.get("tuning", {}).items()):
-        return None
-    if t["margin"] is not None and (margin is None or abs(margin - t["margin"]) > 1e-6 * t["margin"]):
-        return None
-    if any(kernel_source_hash(sig, fn) != hv for fn, sig, hv in t["source"]):
-        return None
-    return t["bytes"]
+    """The recorded DRAM bytes per launch of `kernel` for a run of n owners at `margin` with
+    `tuning`, from the record whose capture matches: the same size, the same kernel build
+    (tuning fields such as staged integration or the lean contact kernel), for the contact
+    kernel the same margin, and kernel source that still hashes to the captured one;
+    None if no record matches."""
+    for t in MEASURED_TRAFFIC.get(kernel, []):
+        if t["n"] != n:
+            continue
+        if any((tuning or {}).get(k, v) != v for k, v in t.get("tuning", {}).items()):
+            continue
+        if t["margin"] is not None and (margin is None or abs(margin - t["margin"]) > 1e-6 * t["margin"]):
+            continue
+        if any(kernel_source_hash(sig, fn) != hv for fn, sig, hv in t["source"]):
+            continue
+        return t["bytes"]
+    return None
 
 
 def peaks():

@@ -85,28 +85,33 @@ def test_contact_kernel_integration_moves_the_busy_owners_bytes(bench):
 
 
 def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(bench, monkeypatch):
-    t = bench.MEASURED_TRAFFIC["contact"]
-    same = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in t["source"])
+    def current(rec):
+        return all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in rec["source"])
+
+    [t] = bench.MEASURED_TRAFFIC["contact"]
     m = t["margin"]
-    assert bench.measured_traffic("contact", t["n"], m) == (t["bytes"] if same else None)
+    assert bench.measured_traffic("contact", t["n"], m) == (t["bytes"] if current(t) else None)
     assert bench.measured_traffic("contact", t["n"] + 1, m) is None       # another size
     assert bench.measured_traffic("contact", t["n"], 0.35 * m) is None    # another margin
     assert bench.measured_traffic("contact", t["n"]) is None              # margin unknown
-    # another build of the kernel than the captured one: no figure
-    ti = bench.MEASURED_TRAFFIC["integrate"]
-    same_i = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in ti["source"])
-    assert bench.measured_traffic("integrate", ti["n"], tuning={"integrate_staged": 0}) == (ti["bytes"] if same_i else None)
-    assert bench.measured_traffic("integrate", ti["n"], tuning={"integrate_staged": 1}) is None
+    # each build of the integration has its own record; another build than the captured
+    # ones has none
+    plain, staged = bench.MEASURED_TRAFFIC["integrate"]
+    assert plain["tuning"] == {"integrate_staged": 0} and staged["tuning"] == {"integrate_staged": 1}
+    assert bench.measured_traffic("integrate", plain["n"], tuning={"integrate_staged": 0}) == (
+        plain["bytes"] if current(plain) else None)
+    assert bench.measured_traffic("integrate", staged["n"], tuning={"integrate_staged": 1}) == (
+        staged["bytes"] if current(staged) else None)
     assert bench.measured_traffic("contact", t["n"], m, tuning={"contact_lean": 1}) is None
+    # the integration's figure holds at any margin
+    assert bench.measured_traffic("integrate", plain["n"], 0.35 * m, tuning={"integrate_staged": 0}) == (
+        plain["bytes"] if current(plain) else None)
     # a forward declaration is not the definition it hashes
     assert bench.kernel_source_hash("integrate_core(const Dev<F> &d") == bench.kernel_source_hash(
         "integrate_core(const Dev<F> &d, DevStatus *stp")
-    ti = bench.MEASURED_TRAFFIC["integrate"]                             # margin-free
-    same_i = all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in ti["source"])
-    assert bench.measured_traffic("integrate", ti["n"], 0.35 * m) == (ti["bytes"] if same_i else None)
     fn, sig, hv = t["source"][0]
     changed = dict(t, source=[(fn, sig, "0" * 16)] + t["source"][1:])
-    monkeypatch.setitem(bench.MEASURED_TRAFFIC, "contact", changed)
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, "contact", [changed])
     assert bench.measured_traffic("contact", t["n"], m) is None
 
 
