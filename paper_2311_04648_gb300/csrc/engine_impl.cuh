@@ -108,6 +108,7 @@ public:
         if ((s = alloc(d_.inv_mass, Mp, err))) return s;
         if ((s = alloc(d_.owner_scene, Mp, err))) return s;
         if ((s = alloc(d_.owner_iso, Mp, err))) return s;
+        if ((s = alloc(d_.touched, std::max(Mp, d_.Np), err))) return s;
         if ((s = alloc(d_.fo, M, err))) return s;
         if ((s = alloc(d_.to, M, err))) return s;
         if ((s = alloc(d_.owner_first, M, err))) return s;

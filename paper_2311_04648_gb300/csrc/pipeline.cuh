@@ -59,6 +59,9 @@ struct Dev {
     // read from inv_mass / inv_moi
     int solid;
     float moi_coef;
+    // single spheres, two-kernel step: 1 where the contact kernel wrote the owner's force
+    // of the step (its entries touched something), per owner with listed partners
+    uint8_t *touched;
     int n_scenes;
     int vpc;                        // voxels per cell edge (voxel form)
     double bin_invL;                // the smallest cells (schedule bins are made of them)
@@ -1385,12 +1388,27 @@ __device__ __forceinline__ const double *crr_table(const Dev<F> &d, double)
 // ROLL compiles in rolling resistance (worlds where a material pair has C_r > 0): each
 // entry's age is kept in its history vector, and past the collision time the rolling
 // force's torque is added after the contact force's.
-template <class F, bool CLUMPS, int MODE, bool ROLL = false>
-__device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me, const Scene &sc, int64_t s, int n,
+// LAZY (single spheres): me comes without its velocities, which are read at the first
+// entry that needs them (a wall, or a sphere pair that overlaps).  Returns whether any
+// entry made contact (Fs and Ts are exactly zero otherwise).
+template <class F, bool CLUMPS, int MODE, bool ROLL = false, bool LAZY = false>
+__device__ __forceinline__ bool pair_sums(const Dev<F> &d, const SphereK<F> &me_in, const Scene &sc, int64_t s, int n,
                                           uint32_t j_first, int sp, int hp, int lc, V3<typename F::R> &Fs,
                                           V3<typename F::R> &Ts)
 {
+    static_assert(!LAZY || !CLUMPS, "only single spheres read their velocities late");
     using R = typename F::R;
+    SphereK<F> me = me_in;
+    bool have_v = !LAZY, any = false;
+    auto need_v = [&]() {
+        if (LAZY && !have_v) {
+            const auto v4 = d.st.kv[sp][2 * (int64_t)me.owner];
+            const auto w4 = d.st.kv[sp][2 * (int64_t)me.owner + 1];
+            me.v = {v4.x, v4.y, v4.z};
+            me.w = {w4.x, w4.y, w4.z};
+            have_v = true;
+        }
+    };
     const R h = F::voxel ? (R)sc.hf : (R)sc.h;
     const uint32_t *prow = d.lists.partner[lc];
     using H = typename HistVec<R>::T;
@@ -1413,6 +1431,7 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
         bool on;
         int mb = 0;
         if (j & WALL_BIT) {
+            need_v();
             ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
             const Wall &w = d.walls[j & ~WALL_BIT];
             mb = w.mat;
@@ -1428,6 +1447,7 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
             sphere_gap<F>(d, me, other, dd, dist, delta);
             on = delta > R(0) && dist > R(0) && d.st.active[sp][j];
             if (on) {
+                need_v();
                 const auto v4 = d.st.kv[sp][2 * j];
                 const auto w4 = d.st.kv[sp][2 * j + 1];
                 ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
@@ -1479,8 +1499,10 @@ __device__ __forceinline__ void pair_sums(const Dev<F> &d, const SphereK<F> &me,
                 Ts = Ts + cross(armA, Fc);
             }
         }
+        any = any || on;
         if (MODE == MODE_STEP) hist_put(hout, e, on ? ut : zero, on ? age : R(0));
     }
+    return any;
 }
 
 template <class F>
@@ -1683,13 +1705,21 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
     bool act = live && d.st.active[sp][o];
     if (!CLUMPS && MODE == MODE_STEP && (!act || n == 0)) return;
 
+    // single spheres in the two-kernel step: the sphere's velocities are read only if an
+    // entry needs them, and the force only written (with its flag) if an entry touched
+    constexpr bool LAZY = !CLUMPS && MODE == MODE_STEP && !INTEG && MODEL == FORCE_MODEL_BUILTIN;
     V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
     SphereK<F> me;
     int scene = 0;
     R4 q4 = {}, ii = {};
     R im = R(0);
     if (live) {
-        me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
+        if constexpr (LAZY) {
+            me = load_sphere_pos<F>(d, sp, (uint32_t)s);
+            if constexpr (F::voxel) me.mat = (int)d.sph_mat[s];
+        } else {
+            me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
+        }
         scene = d.owner_scene[o];
         if constexpr (INTEG) {
             // the rest of the owner's inputs are in flight while the pairs are summed
@@ -1702,15 +1732,16 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
             }
         }
     }
+    bool any = true;
     if (act) {
         if constexpr (MODEL == FORCE_MODEL_HERTZ_MINDLIN)
             pair_sums_model<F, CLUMPS, MODE, ModelHertzMindlin>(d, me, d.scenes[scene], s, n, sp, hp, lc, Fs, Ts);
         else if constexpr (MODEL == FORCE_MODEL_BONDED_BREAKAGE)
             pair_sums_model<F, CLUMPS, MODE, ModelBondedBreakage>(d, me, d.scenes[scene], s, n, sp, hp, lc, Fs, Ts);
         else
-            pair_sums<F, CLUMPS, MODE, ROLL>(d, me, d.scenes[scene], s, n,
-                                             n_known >= 0 ? j0_known : (n > 0 ? d.lists.partner[lc][s] : 0u), sp, hp,
-                                             lc, Fs, Ts);
+            any = pair_sums<F, CLUMPS, MODE, ROLL, LAZY>(
+                d, me, d.scenes[scene], s, n, n_known >= 0 ? j0_known : (n > 0 ? d.lists.partner[lc][s] : 0u), sp,
+                hp, lc, Fs, Ts);
     }
     if (CLUMPS) {
         // segmented suffix sums over the owner's consecutive lanes; the head lane ends
@@ -1753,6 +1784,12 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         aud[1] = fmaxf(aud[1], disp2);
         aud[2] = fmaxf(aud[2], speed);
     } else {
+        if constexpr (!CLUMPS) {
+            // the integration reads the force of an owner with listed partners only where
+            // this flag is set (an owner whose entries all missed has Fs = Ts = 0 exactly)
+            d.touched[o] = any ? 1 : 0;
+            if (!any) return;
+        }
         d.fo[o] = R4{Fs.x, Fs.y, Fs.z, R(0)};
         d.to[o] = R4{Ts.x, Ts.y, Ts.z, R(0)};
     }
@@ -1964,7 +2001,9 @@ __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp,
     // every load of this owner is issued before the first one is used: the thread waits
     // for one memory round trip, not a chain of them
     const bool act = src.active[i];
-    const bool has = FREE ? false : (CLUMPS ? true : src.cnt[i] > 0);
+    // the flag is read beside the row length, not after it (both are always valid)
+    const uint8_t touched = (FREE || CLUMPS) ? (uint8_t)1 : d.touched[o];
+    const bool has = FREE ? false : (CLUMPS ? true : (src.cnt[i] > 0) & (touched != 0));
     R mass;
     typename F::Aux aux;
     const typename F::Pos po = F::load(src.pos, i, mass, aux);
