@@ -1039,6 +1039,9 @@ public:
         }
         if ((s = dget(d_.st.kv[sp], 2 * M * sizeof(R4)))) return s;
         if ((s = dget(d_.st.quat[sp], M * sizeof(R4)))) return s;
+        if (!m_.clumps && M > 0)     // both orientation buffers hold the restored orientation
+            if ((s = copy_sync(d_.st.quat[sp ^ 1], d_.st.quat[sp], M * sizeof(R4), cudaMemcpyDeviceToDevice, err)))
+                return s;
         if ((s = dget(d_.st.active[sp], M))) return s;
         if ((s = dget(d_.lists.partner[lc], ne * 4))) return s;
         if ((s = dget(d_.lists.cnt[lc], d_.Np))) return s;
@@ -1317,6 +1320,7 @@ private:
         } else {
             k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, dw, da);
         }
+        if (!m_.clumps) k_mirror_quat<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n);
         DEM_CU(cudaGetLastError());
         DEM_CU(cudaStreamSynchronize(sf_));
         return DEM_OK;

@@ -1667,7 +1667,7 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
                                                typename F::R4 w4, typename F::R4 q4, typename F::R im,
                                                typename F::R4 ii, bool iso, const Scene &sc, V3<typename F::R> Fs,
                                                V3<typename F::R> Ts, const typename F::Aux &aux, float &disp,
-                                               float &disp2, float &speed);
+                                               float &disp2, float &speed, const typename F::R4 *qsrc = nullptr);
 __device__ __forceinline__ void audit_slots(unsigned int *audit, int64_t o, int lane, float disp, float disp2,
                                             float speed);
 
@@ -1722,8 +1722,8 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         }
         scene = d.owner_scene[o];
         if constexpr (INTEG) {
-            // the rest of the owner's inputs are in flight while the pairs are summed
-            q4 = d.st.quat[sp][o];
+            // the rest of the owner's inputs are in flight while the pairs are summed (its
+            // orientation is read by the integration only if the sphere turns)
             if (F::voxel && d.solid) {
                 solid_consts<F>(d, me.mass, (float)me.rad, im, ii);
             } else {
@@ -1779,7 +1779,7 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
         float disp = 0.0f, disp2 = 0.0f, speed = 0.0f;
         integrate_core<F, false>(d, d.status, o, sp, true, me.p, me.mass, R4{me.v.x, me.v.y, me.v.z, me.acc0},
                                  R4{me.w.x, me.w.y, me.w.z, me.acc1}, q4, im, ii, true, d.scenes[scene], Fs, Ts, aux,
-                                 disp, disp2, speed);
+                                 disp, disp2, speed, &d.st.quat[sp][o]);
         aud[0] = fmaxf(aud[0], disp);
         aud[1] = fmaxf(aud[1], disp2);
         aud[2] = fmaxf(aud[2], speed);
@@ -1881,7 +1881,7 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
                                                typename F::R4 w4, typename F::R4 q4, typename F::R im,
                                                typename F::R4 ii, bool iso, const Scene &sc, V3<typename F::R> Fs,
                                                V3<typename F::R> Ts, const typename F::Aux &aux, float &disp,
-                                               float &disp2, float &speed)
+                                               float &disp2, float &speed, const typename F::R4 *qsrc)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
@@ -1891,7 +1891,23 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
     float a0 = acc_a, a1 = acc_b;
     const int so = sp ^ 1;
     V3<R> vn = {v4.x, v4.y, v4.z}, wn = {w4.x, w4.y, w4.z};
+    // single spheres: a sphere that does not turn in a step keeps its orientation as it is
+    // (no rotation, no renormalisation).  While a sphere's stored angular velocity is zero
+    // both orientation buffers hold the same quaternion (uploads and restores write both;
+    // a step that ends with zero angular velocity writes both), so such a step reads and
+    // writes no quaternion.  With qsrc set, q4 was not read and is fetched from there if
+    // the sphere turns.
+    const bool w_zero0 = w4.x == R(0) && w4.y == R(0) && w4.z == R(0);
+    bool q_valid = qsrc == nullptr;
+    bool rot = true;
     R qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+    auto fetch_q = [&]() {
+        if (!q_valid) {
+            const R4 qq = *qsrc;
+            qw = qq.x; qx = qq.y; qy = qq.z; qz = qq.w;
+            q_valid = true;
+        }
+    };
     uint8_t active_out = act ? 1 : 0;
     typename F::Pos pn = po;
     if (act) {
@@ -1906,21 +1922,30 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
             if constexpr (F::voxel) vn = {pm->vf[0], pm->vf[1], pm->vf[2]};
             else vn = {(R)pm->v[0], (R)pm->v[1], (R)pm->v[2]};
         }
-        R nw, nx, ny, nz;
+        R nw = qw, nx = qx, ny = qy, nz = qz;
         if (pm && pm->fix_w) {
             // turn by the prescribed (global-frame) angular velocity: q <- dq(h w) q
             if constexpr (F::voxel) wn = {pm->wf[0], pm->wf[1], pm->wf[2]};
             else wn = {(R)pm->w[0], (R)pm->w[1], (R)pm->w[2]};
-            R dw, dx, dy, dz;
-            quat_increment<R>(wn, h, dw, dx, dy, dz);
-            quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+            rot = CLUMPS || !(wn.x == R(0) && wn.y == R(0) && wn.z == R(0));
+            if (rot) {
+                fetch_q();
+                R dw, dx, dy, dz;
+                quat_increment<R>(wn, h, dw, dx, dy, dz);
+                quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+            }
         } else if (iso) {
             // isotropic inertia: the body-frame update equals a world-frame one
             wn = vadd_rn(wn, vscale_rn(h, vscale_rn(ii.x, Ts)));
-            R dw, dx, dy, dz;
-            quat_increment<R>(wn, h, dw, dx, dy, dz);
-            quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+            rot = CLUMPS || !(wn.x == R(0) && wn.y == R(0) && wn.z == R(0));
+            if (rot) {
+                fetch_q();
+                R dw, dx, dy, dz;
+                quat_increment<R>(wn, h, dw, dx, dy, dz);
+                quat_mul<R>(dw, dx, dy, dz, qw, qx, qy, qz, nw, nx, ny, nz);
+            }
         } else {
+            fetch_q();
             R m[9];
             quat_mat_rn<R>(qw, qx, qy, qz, m);
             V3<R> wb = mat_tvec_rn<R>(m, wn);
@@ -1941,8 +1966,10 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
             quat_mat_rn<R>(rdiv(nw, qn), rdiv(nx, qn), rdiv(ny, qn), rdiv(nz, qn), m2);
             wn = mat_vec_rn<R>(m2, wb);
         }
-        R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
-        qw = rdiv(nw, qn); qx = rdiv(nx, qn); qy = rdiv(ny, qn); qz = rdiv(nz, qn);
+        if (rot) {
+            R qn = sqrt(radd(radd(radd(rmul(nw, nw), rmul(nx, nx)), rmul(ny, ny)), rmul(nz, nz)));
+            qw = rdiv(nw, qn); qx = rdiv(nx, qn); qy = rdiv(ny, qn); qz = rdiv(nz, qn);
+        }
         pn = F::advance(po, vscale_rn(h, vn), d.L);
         if (sc.has_sink) {
             V3<double> pa = F::absolute(pn, sc, d.Ld);
@@ -1981,7 +2008,19 @@ __device__ __forceinline__ void integrate_core(const Dev<F> &d, DevStatus *stp, 
     F::store(pos_out, o, pn, mass, aux);
     d.st.kv[so][2 * o] = R4{vn.x, vn.y, vn.z, (R)(ap == 0 ? a0 : a1)};
     d.st.kv[so][2 * o + 1] = R4{wn.x, wn.y, wn.z, (R)(ap == 0 ? a1 : a0)};
-    d.st.quat[so][o] = R4{qw, qx, qy, qz};
+    if constexpr (CLUMPS) {
+        d.st.quat[so][o] = R4{qw, qx, qy, qz};
+    } else {
+        const bool w_zero1 = wn.x == R(0) && wn.y == R(0) && wn.z == R(0);
+        // !act: the orientation is kept, as in a step without rotation
+        const bool turned = act && rot;
+        if (turned || !w_zero0) {
+            fetch_q();      // turned: already current; otherwise the stored orientation
+            d.st.quat[so][o] = R4{qw, qx, qy, qz};
+            // a turned sphere that ends at rest: both buffers hold its new orientation
+            if (turned && w_zero1) d.st.quat[sp][o] = R4{qw, qx, qy, qz};
+        }
+    }
     d.st.active[so][o] = active_out;
 }
 
@@ -2007,7 +2046,9 @@ __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp,
     R mass;
     typename F::Aux aux;
     const typename F::Pos po = F::load(src.pos, i, mass, aux);
-    const R4 v4 = src.kv[2 * i], w4 = src.kv[2 * i + 1], q4 = src.quat[i];
+    const R4 v4 = src.kv[2 * i], w4 = src.kv[2 * i + 1];
+    // clumps read their orientation at once; a single sphere's is read only if it turns
+    const R4 q4 = CLUMPS ? src.quat[i] : R4{};
     R im;
     R4 ii;
     if (!CLUMPS && F::voxel && d.solid) {
@@ -2028,7 +2069,7 @@ __device__ __forceinline__ void integrate_owner(const Dev<F> &d, DevStatus *stp,
         Ts = {t4.x, t4.y, t4.z};
     }
     integrate_core<F, CLUMPS>(d, stp, o, sp, act, po, mass, v4, w4, q4, im, ii, iso, sc, Fs, Ts, aux, disp, disp2,
-                              speed);
+                              speed, CLUMPS ? nullptr : &src.quat[i]);
 }
 
 // One thread per owner, reading its inputs straight from the state arrays.
@@ -2113,8 +2154,8 @@ __global__ void __launch_bounds__(FUSED_BLOCK_MAX, 2) k_step_fused(Dev<F> d)
             im = d.inv_mass[s];
             ii = d.inv_moi[s];
         }
-        integrate_core<F, false>(d, stp, s, sp, act, po, me.mass, v4, w4, d.st.quat[sp][s], im, ii, true, sc, Fs,
-                                 Ts, aux, disp, disp2, speed);
+        integrate_core<F, false>(d, stp, s, sp, act, po, me.mass, v4, w4, R4{}, im, ii, true, sc, Fs, Ts, aux, disp,
+                                 disp2, speed, &d.st.quat[sp][s]);
     }
     audit_slots(d.audit, g, lane, disp, disp2, speed);
 }
@@ -2700,6 +2741,17 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
         d.st.kv[sp][2 * o + 1] = R4{(R)wg.x, (R)wg.y, (R)wg.z, R(0)};
     }
     if (act) d.st.active[sp][o] = act[k];
+}
+
+// Both orientation buffers get the current orientation (single spheres: a sphere at rest
+// reads and writes none in a step, so both must hold it; see integrate_core).
+template <class F>
+__global__ void __launch_bounds__(256) k_mirror_quat(Dev<F> d, int64_t first, int64_t n)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int sp = d.status->state_par;
+    d.st.quat[sp ^ 1][first + k] = d.st.quat[sp][first + k];
 }
 
 // Sphere centres (FP64 world frame), radii, and the raw voxel encoding.

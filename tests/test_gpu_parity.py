@@ -379,6 +379,50 @@ def test_voxel_fp32_derived_owner_constants_stay_close_to_oracle():
     assert dem.World.from_scene(s, precision="fp64").stats()["derived_constants"] == 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "voxel_fp32"])
+def test_orientation_of_spheres_at_rest_and_turning(precision):
+    # a single sphere that does not turn keeps its orientation exactly; one that turns
+    # follows the oracle; a spin set to zero mid-run, the bounce off walls and contacts
+    # (which start spins) and a checkpoint restore keep both orientation buffers right
+    s = W.settle_box(n=600, vel_sigma=0.3, seed=21)
+    w = dem.World.from_scene(s, precision=precision)
+    ow = oracle.OracleWorld(s, threads=oracle_threads())
+    rng = np.random.default_rng(5)
+    x, q, v, wb = w.owner_state()
+    q = rng.normal(size=q.shape)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    wb = np.where((np.arange(len(wb)) % 3 == 0)[:, None], rng.normal(scale=50.0, size=wb.shape), 0.0)
+    w.set_owner_state(0, quat=q, omega=wb)
+    q_set = w.owner_state()[1].copy()
+    sync_oracle_to_gpu(w, ow, None)
+    tol = TOL64 if precision == "fp64" else 1e-4
+    for k in (30, 30):
+        w.step(k)
+        assert ow.step(k) == 0
+        st, ok = state_close(w, ow, tol)
+        assert ok, st
+    x1, q1, v1, w1 = w.owner_state()
+    rest = np.all(w1 == 0.0, axis=1) & np.all(wb == 0.0, axis=1)
+    assert rest.sum() > 50
+    assert np.array_equal(q1[rest], q_set[rest])            # never turned: the same bits
+    # stop every spin, then step on: the orientations stay as they are
+    blob = w.save_state()
+    w.set_owner_state(0, omega=np.zeros_like(w1))
+    q_stop = w.owner_state()[1].copy()
+    w.step(1)
+    q2, w2 = w.owner_state()[1], w.owner_state()[3]
+    still = np.all(w2 == 0.0, axis=1)
+    assert still.sum() > 50 and np.array_equal(q2[still], q_stop[still])
+    # a restore mid-run continues as the run it was taken from
+    w.step(10)
+    want = w.owner_state()
+    w.load_state(blob)
+    w.set_owner_state(0, omega=np.zeros_like(w1))
+    w.step(11)
+    for a, b in zip(w.owner_state(), want):
+        assert np.array_equal(a, b)
+
+
 # ----------------------------------------------------------------------------- schedules, determinism
 
 @pytest.mark.parametrize("precision", ["fp64", "voxel_fp32"])
