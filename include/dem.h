@@ -290,6 +290,10 @@ typedef struct {
                                       sphere slot, else radix sort), 1 = radix sort of the
                                       cell keys, 2 = counting sort (per-cell counts, a scan,
                                       a scatter).  The same contact lists either way       */
+    int32_t narrow_staged;         /* 1 = the narrow phase stages each block's candidate
+                                      ranges of the sorted snapshot in shared memory (256
+                                      threads per block, narrow_block ignored), 0 = its
+                                      threads read them from L1/L2.  The same lists        */
 } dem_tuning;
 
 dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);

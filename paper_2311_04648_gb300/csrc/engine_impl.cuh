@@ -1461,6 +1461,7 @@ private:
         tune_.contact_lean = t->contact_lean ? 1 : 0;
         tune_.fused_block = m_.clumps ? 0 : t->fused_block;
         tune_.contact_integrates = (!m_.clumps && t->contact_integrates) ? 1 : 0;
+        tune_.narrow_staged = (t->narrow_staged && prepare_narrow_staged()) ? 1 : 0;
         choose_binning();
         tune_.margin = 0.0;
         apply_margin(t->margin);
@@ -1535,6 +1536,23 @@ private:
         db_.cell_wall = cw;
         db_.ccount_len = len;
         return DEM_OK;
+    }
+
+    // Shared memory of the staged narrow phase: records, slots, owners, families.
+    static size_t narrow_smem() { return (size_t)NS_CAP * (32 + 4 + 4 + 1); }
+
+    // The staged narrow phase needs its shared-memory size allowed once.
+    bool prepare_narrow_staged()
+    {
+        const int smem = (int)narrow_smem();
+        if (cudaFuncSetAttribute(k_narrow<F, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_narrow<F, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
     }
 
     // Counting sort where the cells are not much more numerous than the sphere slots
@@ -1623,11 +1641,12 @@ private:
                     if (std::sscanf(line, "{\"key\": \"%299[^\"]\", \"contact_block\": %d, \"integrate_block\": %d, "
                                           "\"narrow_block\": %d, \"detect_inline\": %d, \"cell_factor\": %lf, "
                                           "\"integrate_staged\": %d, \"contact_lean\": %d, \"fused_block\": %d, "
-                                          "\"contact_integrates\": %d, \"binning\": %d, \"margin\": %lf, "
-                                          "\"step_ms\": %lf}",
+                                          "\"contact_integrates\": %d, \"binning\": %d, \"narrow_staged\": %d, "
+                                          "\"margin\": %lf, \"step_ms\": %lf}",
                                     k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
                                     &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.fused_block,
-                                    &t.contact_integrates, &t.binning, &t.margin, &t.step_ms) == 13 &&
+                                    &t.contact_integrates, &t.binning, &t.narrow_staged, &t.margin,
+                                    &t.step_ms) == 14 &&
                         key == k) {
                         best = t;
                         found = true;
@@ -1712,9 +1731,10 @@ private:
             if (f != b2.cell_factor)
                 if ((s = trial(dem_tuning{b2.contact_block, b2.integrate_block, b2.narrow_block, b2.detect_inline,
                                           0.0, f, b2.integrate_staged, b2.contact_lean, b2.fused_block, 0.0,
-                                          b2.contact_integrates, b2.binning})))
+                                          b2.contact_integrates, b2.binning, b2.narrow_staged})))
                     return s;
-        // the binning: radix sort against counting sort (the automatic choice is one of them)
+        // the binning: radix sort against counting sort (the automatic choice is one of
+        // them), then the narrow phase staged in shared memory
         {
             const dem_tuning b5 = best;
             for (int bn : {1, 2}) {
@@ -1723,6 +1743,10 @@ private:
                 t.step_ms = 0.0;
                 if ((s = trial(t))) return s;
             }
+            dem_tuning t = best;
+            t.narrow_staged = 1;
+            t.step_ms = 0.0;
+            if ((s = trial(t))) return s;
         }
         // phase 4 (delayed schedules): smaller detection margins list fewer pairs that do
         // not touch, at the price of more rebuilds; the results are the same bits
@@ -1748,10 +1772,11 @@ private:
                              "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
                              "%d, \"detect_inline\": %d, \"cell_factor\": %.3f, \"integrate_staged\": %d, "
                              "\"contact_lean\": %d, \"fused_block\": %d, \"contact_integrates\": %d, "
-                             "\"binning\": %d, \"margin\": %.17g, \"step_ms\": %.6f}\n",
+                             "\"binning\": %d, \"narrow_staged\": %d, \"margin\": %.17g, \"step_ms\": %.6f}\n",
                              key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
                              best.detect_inline, best.cell_factor, best.integrate_staged, best.contact_lean,
-                             best.fused_block, best.contact_integrates, best.binning, best.margin, best.step_ms);
+                             best.fused_block, best.contact_integrates, best.binning, best.narrow_staged, best.margin,
+                             best.step_ms);
                 std::fclose(f);
             }
         }
@@ -1978,8 +2003,15 @@ private:
             db_.fvals_sorted = fv;
             k_facet_cells<<<grid(db_.n_fpairs, 256), 256, 0, st>>>(st_, db_);
         }
-        if (m_.clumps) k_narrow<F, true><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
-        else k_narrow<F, false><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
+        if (tune_.narrow_staged) {
+            const size_t smem = narrow_smem();
+            if (m_.clumps) k_narrow<F, true, true><<<grid(d_.N, NS_THREADS), NS_THREADS, smem, st>>>(d_, db_, ks, vs);
+            else k_narrow<F, false, true><<<grid(d_.N, NS_THREADS), NS_THREADS, smem, st>>>(d_, db_, ks, vs);
+        } else if (m_.clumps) {
+            k_narrow<F, true><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
+        } else {
+            k_narrow<F, false><<<grid(d_.N, tune_.narrow_block), tune_.narrow_block, 0, st>>>(d_, db_, ks, vs);
+        }
         const unsigned nb = grid(d_.Np, 256);
         k_rows_finish<F><<<nb, 256, 0, st>>>(d_, db_, d_.lists.bcount[0]);
         // the offsets of the new list's compacted work, ahead of the switch

@@ -876,26 +876,38 @@ __global__ void __launch_bounds__(256) k_cell_walls(Dev<F> d, DetectBuffers b, d
 // thread also appends its sphere's walls and facets.  The listed predicate is symmetric
 // in its two spheres, so the rows hold what each sphere's own full scan would list; the
 // second pass (k_rows_finish) sorts them.
-template <class F, bool CLUMPS>
-__global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, const uint32_t *keys,
-                                                 const uint32_t *vals)
+constexpr int NS_THREADS = 256;     // block of the staged narrow phase
+constexpr int NS_CAP = 2048;        // snapshot entries a block stages in shared memory
+
+// STAGED: the block of NS_THREADS sorted entries first reduces its threads' candidate runs
+// to five ranges of the sorted order (one per run of the half shell: each the union of
+// its threads' runs, contiguous since cells are ordered z-major) and copies them into
+// shared memory, records, slots, owners and families; the candidate tests then read
+// shared memory instead of L1/L2.  A block whose ranges exceed NS_CAP entries reads
+// global memory as the plain kernel does.  The same tests in the same order: the same
+// rows.
+template <class F, bool CLUMPS, bool STAGED = false>
+__global__ void __launch_bounds__(256, STAGED ? 2 : 4) k_narrow(Dev<F> d, DetectBuffers b, const uint32_t *keys,
+                                                               const uint32_t *vals)
 {
     DevStatus *stp = d.status;
     if (stp->halt) return;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nvalid = *b.n_valid;
-    if (t >= nvalid) return;
+    const bool live = t < nvalid;
+    if (!STAGED && !live) return;
     const uint32_t stamp = stp->cell_stamp;
     const int ln = stp->list_cur ^ 1;
     const double beta = stp->beta_next;
     const float betaf = stp->beta_next_f;
-    const uint32_t i = vals[t];
-    const uint32_t key = keys[t];
-    const uint32_t oi = b.sorted_owner[t];
-    const Scene &sc = d.scenes[d.owner_scene[oi]];
+    // entries past the valid ones (staged blocks only) take part in the staging alone
+    const uint32_t i = live ? vals[t] : 0u;
+    const uint32_t key = live ? keys[t] : 0u;
+    const uint32_t oi = live ? b.sorted_owner[t] : 0u;
+    const Scene &sc = d.scenes[live ? d.owner_scene[oi] : 0];
     // families: candidates of a family whose contacts with this one are masked are skipped
     const bool fam = d.owner_family != nullptr;
-    const int fi = fam ? (int)b.sorted_family[t] : 0;
+    const int fi = (fam && live) ? (int)b.sorted_family[t] : 0;
     const uint32_t local = key - sc.cell_base;
     const int nx = sc.nc[0], ny = sc.nc[1], nz = sc.nc[2];
     const int cx = (int)(local % (uint32_t)nx);
@@ -906,12 +918,14 @@ __global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, co
     float4 acf = make_float4(0, 0, 0, 0);
     int4 ac = make_int4(0, 0, 0, 0);
     float4 ao = make_float4(0, 0, 0, 0);
-    if constexpr (F::voxel) {
-        acf = reinterpret_cast<const float4 *>(b.sorted)[t];
-        ac = make_int4((int)acf.x, (int)acf.y, (int)acf.z, 0);
-        ao = reinterpret_cast<const float4 *>(b.sorted_aux)[t];
-    } else {
-        a64 = reinterpret_cast<const double4_32a *>(b.sorted)[t];
+    if (live) {
+        if constexpr (F::voxel) {
+            acf = reinterpret_cast<const float4 *>(b.sorted)[t];
+            ac = make_int4((int)acf.x, (int)acf.y, (int)acf.z, 0);
+            ao = reinterpret_cast<const float4 *>(b.sorted_aux)[t];
+        } else {
+            a64 = reinterpret_cast<const double4_32a *>(b.sorted)[t];
+        }
     }
     const float b2f = 2.0f * betaf;
     const double b2d = 2.0 * beta;
@@ -927,13 +941,17 @@ __global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, co
     };
     const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
     uint32_t own_facets = 0;     // the own cell's first (cell, facet) pair + 1, 0 for none
-    // runs (dz, dy): (0, 0) from t + 1, then (0, +1), (+1, -1), (+1, 0), (+1, +1)
-#pragma unroll 1
+    // runs (dz, dy): (0, 0) from t + 1, then (0, +1), (+1, -1), (+1, 0), (+1, +1); an
+    // empty run has rlo = rhi
+    uint32_t rlo[5], rhi[5];
+#pragma unroll
     for (int run = 0; run < 5; ++run) {
+        rlo[run] = 0u;
+        rhi[run] = 0u;
         const int dz = run < 2 ? 0 : 1;
         const int dy = run == 0 ? 0 : (run == 1 ? 1 : run - 3);
         const int z = cz + dz, y = cy + dy;
-        if (z >= nz || y < 0 || y >= ny) continue;
+        if (!live || z >= nz || y < 0 || y >= ny) continue;
         const uint32_t rowbase = sc.cell_base + (uint32_t)((z * ny + y) * nx);
         uint32_t lo = 0xffffffffu, hi = 0;
         for (int x = x0; x <= x1; ++x) {
@@ -947,17 +965,94 @@ __global__ void __launch_bounds__(256, 4) k_narrow(Dev<F> d, DetectBuffers b, co
         if (lo == 0xffffffffu) continue;
         // the own run holds this entry's cell: only the entries after it
         if (run == 0) lo = (uint32_t)t + 1u;
+        if (lo < hi) {
+            rlo[run] = lo;
+            rhi[run] = hi;
+        }
+    }
+    // staging (STAGED): five ranges of the sorted order into shared memory
+    extern __shared__ __align__(32) unsigned char ns_mem[];
+    __shared__ uint32_t seg_lo[5], seg_hi[5], seg_base[5];
+    __shared__ int seg_ok;
+    bool staged = false;
+    if constexpr (STAGED) {
+        if (threadIdx.x < 5) {
+            seg_lo[threadIdx.x] = 0xffffffffu;
+            seg_hi[threadIdx.x] = 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int run = 0; run < 5; ++run)
+            if (rlo[run] < rhi[run]) {
+                atomicMin(&seg_lo[run], rlo[run]);
+                atomicMax(&seg_hi[run], rhi[run]);
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int r = 0; r < 5; ++r) {
+                if (seg_hi[r] <= seg_lo[r] || seg_lo[r] == 0xffffffffu) {
+                    seg_lo[r] = 0u;
+                    seg_hi[r] = 0u;
+                }
+                seg_base[r] = tot;
+                tot += seg_hi[r] - seg_lo[r];
+            }
+            seg_ok = tot <= (uint32_t)NS_CAP ? 1 : 0;
+        }
+        __syncthreads();
+        staged = seg_ok != 0;
+        if (staged) {
+            float4 *srec = reinterpret_cast<float4 *>(ns_mem);
+            uint32_t *sval = reinterpret_cast<uint32_t *>(ns_mem + 32 * NS_CAP);
+            uint32_t *sown = sval + NS_CAP;
+            uint8_t *sfam = reinterpret_cast<uint8_t *>(sown + NS_CAP);
+            for (int r = 0; r < 5; ++r) {
+                const uint32_t lo = seg_lo[r], sz = seg_hi[r] - lo, base = seg_base[r];
+                for (uint32_t q = threadIdx.x; q < sz; q += blockDim.x) {
+                    const uint32_t src = lo + q, dst = base + q;
+                    if constexpr (F::voxel) {
+                        srec[2 * dst] = reinterpret_cast<const float4 *>(b.sorted)[src];
+                        srec[2 * dst + 1] = reinterpret_cast<const float4 *>(b.sorted_aux)[src];
+                    } else {
+                        srec[2 * dst] = reinterpret_cast<const float4 *>(b.sorted)[2 * (int64_t)src];
+                        srec[2 * dst + 1] = reinterpret_cast<const float4 *>(b.sorted)[2 * (int64_t)src + 1];
+                    }
+                    sval[dst] = vals[src];
+                    if (CLUMPS) sown[dst] = b.sorted_owner[src];
+                    if (fam) sfam[dst] = b.sorted_family[src];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!live) return;
+    const float4 *srec = reinterpret_cast<const float4 *>(ns_mem);
+    const uint32_t *sval = reinterpret_cast<const uint32_t *>(ns_mem + 32 * NS_CAP);
+    const uint32_t *sown = sval + NS_CAP;
+    const uint8_t *sfam = reinterpret_cast<const uint8_t *>(sown + NS_CAP);
+#pragma unroll 1
+    for (int run = 0; run < 5; ++run) {
+        const uint32_t lo = rlo[run], hi = rhi[run];
+        if (lo >= hi) continue;
+        // the offset from a sorted position to its staged slot
+        const int64_t off = staged ? (int64_t)seg_base[run] - (int64_t)seg_lo[run] : 0;
         for (uint32_t u = lo; u < hi; ++u) {
-            if (CLUMPS && b.sorted_owner[u] == oi) continue;
-            if (fam && !families_meet(d.fam_mask, fi, b.sorted_family[u])) continue;
+            const int64_t su = (int64_t)u + off;
+            if (CLUMPS && (staged ? sown[su] : b.sorted_owner[u]) == oi) continue;
+            if (fam && !families_meet(d.fam_mask, fi, staged ? sfam[su] : b.sorted_family[u])) continue;
             bool hit;
-            if constexpr (F::voxel)
-                hit = listed_f32(acf, ao, reinterpret_cast<const float4 *>(b.sorted)[u],
-                                 reinterpret_cast<const float4 *>(b.sorted_aux)[u], d.L, b2f);
-            else
-                hit = listed_f64(a64, reinterpret_cast<const double4_32a *>(b.sorted)[u], b2d);
+            if constexpr (F::voxel) {
+                const float4 c0 = staged ? srec[2 * su] : reinterpret_cast<const float4 *>(b.sorted)[u];
+                const float4 c1 = staged ? srec[2 * su + 1] : reinterpret_cast<const float4 *>(b.sorted_aux)[u];
+                hit = listed_f32(acf, ao, c0, c1, d.L, b2f);
+            } else {
+                const double4_32a c = staged ? reinterpret_cast<const double4_32a *>(srec)[su]
+                                             : reinterpret_cast<const double4_32a *>(b.sorted)[u];
+                hit = listed_f64(a64, c, b2d);
+            }
             if (hit) {
-                const uint32_t j = vals[u];
+                const uint32_t j = staged ? sval[su] : vals[u];
                 put(i, j);
                 put(j, i);
             }

@@ -62,7 +62,8 @@ class Tuning(C.Structure):
     _fields_ = [("contact_block", C.c_int32), ("integrate_block", C.c_int32), ("narrow_block", C.c_int32),
                 ("detect_inline", C.c_int32), ("step_ms", C.c_double), ("cell_factor", C.c_double),
                 ("integrate_staged", C.c_int32), ("contact_lean", C.c_int32), ("fused_block", C.c_int32),
-                ("margin", C.c_double), ("contact_integrates", C.c_int32), ("binning", C.c_int32)]
+                ("margin", C.c_double), ("contact_integrates", C.c_int32), ("binning", C.c_int32),
+                ("narrow_staged", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -314,6 +314,32 @@ def test_counting_sort_binning_equals_radix_sort_binning(prec, scene):
         assert pa == pb and wa == wb and ra == rb
 
 
+@pytest.mark.parametrize("prec", ["voxel_fp32", "fp64"])
+@pytest.mark.parametrize("scene", ["dense", "clumps", "cone", "paddle", "families"])
+def test_staged_narrow_phase_builds_the_same_lists(prec, scene):
+    # the narrow phase reading its candidates from ranges staged in shared memory against
+    # reading them from L1/L2: the same lists and the same runs, bit for bit
+    s = {"dense": lambda: W.dense_lattice(n=900, seed=39, vel_sigma=0.3),
+         "clumps": lambda: W.packed_clumps(n=120, seed=40),
+         "cone": lambda: W.cone_bed(n=300, seed=13),
+         "paddle": lambda: W.paddle_bed(n=300, seed=3),
+         "families": lambda: W.dense_lattice(n=400, seed=47, vel_sigma=0.3)}[scene]()
+    runs = []
+    for staged in (0, 1):
+        w = dem.World.from_scene(s, precision=prec, schedule="velocity_bound")
+        if scene == "families":
+            w.set_family(0, np.arange(s.n_owner) % 3)
+            w.set_family_contacts(1, 2, False)
+        w.set_tuning(narrow_staged=staged)
+        assert w.tuning()["narrow_staged"] == staged
+        w.step(120)
+        runs.append((_state(w), w.listed_pairs()[0].tolist(), w.listed_wall_pairs()[0].tolist()))
+    (sa, pa, wa), (sb, pb, wb) = runs
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+    assert pa == pb and wa == wb and len(pa) > 0
+
+
 def test_counting_sort_binning_with_families_in_a_batch():
     scenes = [W.dense_lattice(n=150 + 97 * k, seed=45 + k, vel_sigma=0.3) for k in range(3)]
     beta = 5e-5
