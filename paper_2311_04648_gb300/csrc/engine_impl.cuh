@@ -2014,15 +2014,25 @@ private:
         }
         const unsigned nb = grid(d_.Np, 256);
         k_rows_finish<F><<<nb, 256, 0, st>>>(d_, db_, d_.lists.bcount[0]);
-        // the offsets of the new list's compacted work, ahead of the switch
-        if (!m_.clumps) k_cscan_tiles<<<1, 1024, 0, st>>>(st_, d_.lists.bcount[0], (int64_t)nb, d_.lists.bcount[0] + nb);
+        // single spheres: the new list's compacted work (scan of the busy slots per block,
+        // then the entries), ahead of the switch: it writes only the new list's arrays
+        if (!m_.clumps) {
+            k_cscan_tiles<<<1, 1024, 0, st>>>(st_, d_.lists.bcount[0], (int64_t)nb, d_.lists.bcount[0] + nb);
+            k_compact<F><<<nb, 256, 0, st>>>(d_, 0, 1, d_.lists.bcount[0], (int64_t)nb);
+        }
     }
 
     void launch_link(cudaStream_t st)
     {
-        k_act_reset<F><<<1, 1, 0, st>>>(d_, 0);
-        k_link<F><<<grid(d_.N, 256), 256, 0, st>>>(d_);
-        launch_compact(st, 0);
+        if (m_.clumps) {
+            k_act_reset<F><<<1, 1, 0, st>>>(d_, 0);
+            k_link<F><<<grid(d_.N, 256), 256, 0, st>>>(d_);
+            launch_compact(st, 0);
+        } else {
+            // the new list's work was compacted with its detection: link its busy slots only
+            k_act_reset<F><<<1, 1, 0, st>>>(d_, 0, 1);
+            k_link<F, true><<<grid(d_.Np, 256), 256, 0, st>>>(d_);
+        }
         k_commit<<<1, 1, 0, st>>>(st_);
     }
 

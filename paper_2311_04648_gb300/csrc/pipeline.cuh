@@ -1175,12 +1175,16 @@ __global__ void __launch_bounds__(256) k_clear_rows(Dev<F> d, DetectBuffers b)
 }
 
 // Reset the work counter of the new list (which = 0) or of the list in use (which = 1).
+// pairs_only: the compacted work of the new list was built on the detection stream (its
+// count and busy slots are set); only its pair count starts again.
 template <class F>
-__global__ void k_act_reset(Dev<F> d, int which)
+__global__ void k_act_reset(Dev<F> d, int which, int pairs_only = 0)
 {
     const int l = d.status->list_cur ^ (which ? 0 : 1);
-    *d.lists.n_act[l] = 0;
-    d.status->list_busy[l] = 0;
+    if (!pairs_only) {
+        *d.lists.n_act[l] = 0;
+        d.status->list_busy[l] = 0;
+    }
     if (!which) d.status->list_pairs[l] = 0;
 }
 
@@ -1288,19 +1292,32 @@ __global__ void __launch_bounds__(256) k_compact(Dev<F> d, int which, int phase,
 // Link the new list: every entry carries its tangential history over from the same pair
 // in the list in use (zero for a pair that is new: Sec. 4.2, contact wildcards start at
 // zero); each side its own copy.
-template <class F>
+// ACT (single spheres): one thread per entry of the new list's compacted work (its slots
+// with entries, compacted on the detection stream), not per slot.
+template <class F, bool ACT = false>
 __global__ void __launch_bounds__(256) k_link(Dev<F> d)
 {
     using R = typename F::R;
     DevStatus *stp = d.status;
     if (stp->halt) return;
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = s < d.N;               // every lane stays for the warp sum below
     const int lo = stp->list_cur, ln = lo ^ 1;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t s = g;
+    bool live;                               // every lane stays for the warp sum below
+    int n;
+    if constexpr (ACT) {
+        const int64_t na = min((int64_t)*d.lists.n_act[ln], d.Np);
+        live = g < na;
+        const uint4 a = live ? d.lists.act[ln][g] : make_uint4(0u, 0u, 0u, 0u);
+        s = a.x;
+        n = live ? (int)a.y : 0;
+    } else {
+        live = s < d.N;
+        n = live ? d.lists.cnt[ln][s] : 0;
+    }
     const int hs = stp->hist_par, hd = hs ^ 1;
     const uint32_t *pn = d.lists.partner[ln];
     const uint32_t *po = d.lists.partner[lo];
-    const int n = live ? d.lists.cnt[ln][s] : 0;
     const int nold = live ? d.lists.cnt[lo][s] : 0;
     unsigned int owned = 0;                  // pairs this slot owns (partner id above its own)
     // the first LINK_REG entries of the old row in one batch of independent loads; a new
