@@ -226,23 +226,23 @@ def layout_bytes(precision, n, n_with_entries, pairs, clumps=False, contact_inte
 # pairs are listed.  The integration streams every owner whatever the margin; only its
 # read of the force array (32 B per owner with listed partners, under 5% of its bytes
 # here) depends on the margin, so its figure carries no margin.
-_INTEGRATE_SOURCE = [("pipeline.cuh", "integrate_owner(const Dev<F> &d", "00969198b29d2bf1"),
-                     ("pipeline.cuh", "integrate_core(const Dev<F> &d", "b006b33b4402c18e"),
+_INTEGRATE_SOURCE = [("pipeline.cuh", "integrate_owner(const Dev<F> &d", "81371d9d1a4c53fd"),
+                     ("pipeline.cuh", "integrate_core(const Dev<F> &d", "ceab88a14f25d2a5"),
                      ("pipeline.cuh", "audit_slots(unsigned int *audit", "bbac98b73df81d9c"),
                      ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]
 MEASURED_TRAFFIC = {
     "integrate": [
-        {"n": 4_000_000, "margin": None, "bytes": 730.4e6, "tuning": {"integrate_staged": 0},
+        {"n": 4_000_000, "margin": None, "bytes": 670.0e6, "tuning": {"integrate_staged": 0},
          "source": [("pipeline.cuh", "k_integrate(Dev<F> d)", "2a86d66be349aff5")] + _INTEGRATE_SOURCE},
-        {"n": 4_000_000, "margin": None, "bytes": 726.6e6, "tuning": {"integrate_staged": 1},
+        {"n": 4_000_000, "margin": None, "bytes": 665.4e6, "tuning": {"integrate_staged": 1},
          "source": [("pipeline.cuh", "k_integrate_staged(Dev<FormF32> d)", "a2d764678f9b801a"),
                     ("pipeline.cuh", "struct StageLayout {", "a4f1f17d327f7a13")] + _INTEGRATE_SOURCE},
     ],
     "contact": [
-        {"n": 4_000_000, "margin": 2.1e-5, "bytes": 518.9e6, "tuning": {"contact_lean": 0},
+        {"n": 4_000_000, "margin": 2.1e-5, "bytes": 331.4e6, "tuning": {"contact_lean": 0},
          "source": [("pipeline.cuh", "k_contact(Dev<F> d, double *eval_F, double *eval_T)", "36e10c0e4e38a6ea"),
-                    ("pipeline.cuh", "contact_slot(const Dev<F> &d", "957e0acb822aecf6"),
-                    ("pipeline.cuh", "pair_sums(const Dev<F> &d", "400936f26fc6c0f7"),
+                    ("pipeline.cuh", "contact_slot(const Dev<F> &d", "363d4cb673f86026"),
+                    ("pipeline.cuh", "pair_sums(const Dev<F> &d", "de27f25f313b3b49"),
                     ("pipeline.cuh", "wall_contact(const Dev<F> &d", "54458541bf779dd2"),
                     ("pipeline.cuh", "sphere_gap(const Dev<F> &d", "64de1a81d6ab41e3"),
                     ("pipeline.cuh", "sphere_finish(const Dev<F> &d", "3fde901e334f3796"),

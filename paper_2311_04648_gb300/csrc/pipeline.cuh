@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256) k_hash(Dev<F> d, DetectBuffers b, double 
         }
     }
     b.keys[s] = key;
-    b.vals[s] = (uint32_t)s;
+    if (!b.counting) b.vals[s] = (uint32_t)s;      // the counting sort scatters slots itself
 }
 
 // Cell table from the sorted keys (no clearing: an entry is valid only if it carries this
@@ -1826,13 +1826,17 @@ __device__ __forceinline__ void contact_slot(const Dev<F> &d, int64_t s, int n_k
     R4 q4 = {}, ii = {};
     R im = R(0);
     if (live) {
+        // a world of one scene and a scene of one material need neither index read
+        scene = d.n_scenes > 1 ? d.owner_scene[o] : 0;
         if constexpr (LAZY) {
             me = load_sphere_pos<F>(d, sp, (uint32_t)s);
-            if constexpr (F::voxel) me.mat = (int)d.sph_mat[s];
+            if constexpr (F::voxel) {
+                const Scene &sc0 = d.scenes[scene];
+                me.mat = sc0.n_mat == 1 ? sc0.mat_base : (int)d.sph_mat[s];
+            }
         } else {
             me = load_sphere<F, CLUMPS>(d, sp, (uint32_t)s);
         }
-        scene = d.owner_scene[o];
         if constexpr (INTEG) {
             // the rest of the owner's inputs are in flight while the pairs are summed (its
             // orientation is read by the integration only if the sphere turns)
