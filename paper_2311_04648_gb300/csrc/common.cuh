@@ -181,6 +181,8 @@ struct DevStatus {
     int acc_par;                 // displacement accumulator of the list in use (the other: next)
     unsigned int step_disp_bits; // max over owners of this step's displacement bound (float bits)
     unsigned int vmax_bits;      // max |v| over owners this step (float bits)
+    unsigned int upload_disp_bits; // max over uploaded owners of the in-use list's bound after
+                                   // their displacement by a state upload (float bits)
     double disp_cur;             // displacement bound since the snapshot of the list in use
     double disp_next;            // ... since the snapshot of the list being built
     double beta_cur, beta_next;  // margins of those lists

@@ -469,12 +469,21 @@ public:
                     force_step();
                 }
             } else {
-                long long c = quantize_cycle(std::min<long long>(left, cycle_length()));
-                cudaGraphExec_t gx = use_graphs ? graph_for(c) : nullptr;
-                if (gx) {
-                    DEM_CU(cudaGraphLaunch(gx, sf_));
+                const long long cl = cycle_length();
+                if (left < cl) {
+                    // fewer steps than a cycle (a caller stepping a little at a time): step
+                    // on with the list in use, no detection; the audit after each step flags
+                    // it stale once its margin is used up, the steps launched after that do
+                    // nothing, and the next pass rebuilds
+                    for (long long k = 0; k < left; ++k) force_step();
                 } else {
-                    enqueue_cycle(c);
+                    long long c = quantize_cycle(std::min<long long>(left, cl));
+                    cudaGraphExec_t gx = use_graphs ? graph_for(c) : nullptr;
+                    if (gx) {
+                        DEM_CU(cudaGraphLaunch(gx, sf_));
+                    } else {
+                        enqueue_cycle(c);
+                    }
                 }
             }
             if ((s = settle(err))) return s;
@@ -519,8 +528,19 @@ public:
                                const double *w, std::string &err) override
     {
         dem_status s;
-        if ((s = upload_state(first, n, x, q, v, w, nullptr, err))) return s;
-        if (x || q) dirty_ = true;
+        // single spheres, delayed schedules: the list in use stays where no owner moved past
+        // its margin (the audit's rule), with the upload's displacements in the bounds; a
+        // clump's orientation moves its spheres, so that rebuilds
+        const bool keep = !m_.clumps && m_.schedule != DEM_SCHEDULE_EVERY_STEP && !dirty_ && !sth_->list_stale;
+        double bound = 0.0;
+        if ((s = upload_state(first, n, x, q, v, w, nullptr, err, keep, &bound))) return s;
+        if (keep) {
+            if (x && std::max(bound, sth_->disp_cur) > sth_->beta_cur) dirty_ = true;
+            // the next upload before a step compares against this one's bounds too
+            sth_->disp_cur = std::max(sth_->disp_cur, bound);
+        } else if (x || q) {
+            dirty_ = true;
+        }
         return DEM_OK;
     }
 
@@ -1282,8 +1302,12 @@ private:
         return DEM_OK;
     }
 
+    // keep_bounds (an upload between steps): the audit accumulators grow by each owner's
+    // displacement instead of restarting; *max_bound (nullable) receives the largest one of
+    // the list in use among the uploaded owners.
     dem_status upload_state(int64_t first, int64_t n, const double *x, const double *q, const double *v,
-                            const double *w, const uint8_t *act, std::string &err)
+                            const double *w, const uint8_t *act, std::string &err, bool keep_bounds = false,
+                            double *max_bound = nullptr)
     {
         learned_left_ = 0;
         if (n <= 0) return DEM_OK;
@@ -1314,15 +1338,26 @@ private:
             }
         }
         // the angular velocity conversion needs the new orientation: quaternion first
+        const int bounds = keep_bounds ? 1 : 0;
+        if (keep_bounds)
+            DEM_CU(cudaMemsetAsync(&st_->upload_disp_bits, 0, sizeof(unsigned int), sf_));
         if (q && w) {
-            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, nullptr, da);
-            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, nullptr, nullptr, nullptr, dw, nullptr);
+            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, nullptr, da, bounds);
+            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, nullptr, nullptr, nullptr, dw, nullptr,
+                                                             keep_bounds ? 2 : 0);
         } else {
-            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, dw, da);
+            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, dw, da, bounds);
         }
         if (!m_.clumps) k_mirror_quat<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n);
         DEM_CU(cudaGetLastError());
+        unsigned int bits = 0;
+        if (keep_bounds) DEM_CU(cudaMemcpyAsync(&bits, &st_->upload_disp_bits, sizeof(bits), cudaMemcpyDeviceToHost, sf_));
         DEM_CU(cudaStreamSynchronize(sf_));
+        if (max_bound) {
+            float f;
+            std::memcpy(&f, &bits, sizeof(f));
+            *max_bound = (double)f;
+        }
         return DEM_OK;
     }
 

@@ -2813,9 +2813,14 @@ __global__ void k_owner_download(Dev<F> d, int64_t first, int64_t n, double *x, 
 // FP64 host layout to owner state (both buffers' current one); world-frame angular
 // velocity stored.  In the voxel form the position is split into voxel index and
 // offset: c = floor((x - lo) / L), o = (float)((x - lo) - c L), then carried into [0, L).
+// bounds: 0 restarts the audit accumulators (the upload at initialisation); 1 (a state
+// upload between steps) adds each owner's displacement by the upload, rounded up, to
+// both of them, and the largest accumulator of the list in use goes to
+// upload_disp_bits, so that the host keeps the list where no owner moved past its
+// margin; 2 leaves them as they are (a second pass over the same owners).
 template <class F>
 __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double *x, const double *q, const double *v,
-                               const double *w, const uint8_t *act)
+                               const double *w, const uint8_t *act, int bounds)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
@@ -2827,6 +2832,8 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
     typename F::Aux aux;
     typename F::Pos p = F::load(d.st.pos[sp], o, mass, aux);
     const Scene &sc = d.scenes[d.owner_scene[o]];
+    double moved = 0.0;
+    const V3<double> before = F::absolute(p, sc, d.Ld);
     if (x) {
         if constexpr (F::voxel) {
             PosF32 &pv = p;
@@ -2843,19 +2850,41 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
             p.x = x[3 * k]; p.y = x[3 * k + 1]; p.z = x[3 * k + 2];
         }
         F::store(d.st.pos[sp], o, p, mass, aux);
+        const V3<double> after = F::absolute(p, sc, d.Ld);
+        const double dx = after.x - before.x, dy = after.y - before.y, dz = after.z - before.z;
+        moved = sqrt(dx * dx + dy * dy + dz * dz) * (1.0 + 1e-12) + 1e-15;
     }
     R4 q4 = d.st.quat[sp][o];
     if (q) {
         q4 = R4{(R)q[4 * k], (R)q[4 * k + 1], (R)q[4 * k + 2], (R)q[4 * k + 3]};
         d.st.quat[sp][o] = q4;
     }
-    if (v) d.st.kv[sp][2 * o] = R4{(R)v[3 * k], (R)v[3 * k + 1], (R)v[3 * k + 2], R(0)};
+    R4 kv0 = d.st.kv[sp][2 * o], kv1 = d.st.kv[sp][2 * o + 1];
+    if (bounds == 1) {
+        // the bounds grow by the displacement (rounded up in the voxel form's FP32)
+        if constexpr (F::voxel) {
+            const float m = __double2float_ru(moved);
+            kv0.w = __fadd_ru(kv0.w, m);
+            kv1.w = __fadd_ru(kv1.w, m);
+        } else {
+            kv0.w = kv0.w + moved;
+            kv1.w = kv1.w + moved;
+        }
+        const R in_use = d.status->acc_par == 0 ? kv0.w : kv1.w;
+        atomicMax(&d.status->upload_disp_bits, __float_as_uint(__double2float_ru((double)in_use)));
+    } else if (bounds == 0) {
+        kv0.w = R(0);
+        kv1.w = R(0);
+    }
+    if (v) kv0 = R4{(R)v[3 * k], (R)v[3 * k + 1], (R)v[3 * k + 2], kv0.w};
     if (w) {
         double m[9];
         quat_mat<double>((double)q4.x, (double)q4.y, (double)q4.z, (double)q4.w, m);
         V3<double> wg = mat_vec<double>(m, V3<double>{w[3 * k], w[3 * k + 1], w[3 * k + 2]});
-        d.st.kv[sp][2 * o + 1] = R4{(R)wg.x, (R)wg.y, (R)wg.z, R(0)};
+        kv1 = R4{(R)wg.x, (R)wg.y, (R)wg.z, kv1.w};
     }
+    if (v || bounds == 1) d.st.kv[sp][2 * o] = kv0;
+    if (w || bounds == 1) d.st.kv[sp][2 * o + 1] = kv1;
     if (act) d.st.active[sp][o] = act[k];
 }
 

@@ -542,6 +542,62 @@ def test_set_owner_state_forces_a_rebuild_and_keeps_history():
     assert ok, errs
 
 
+def test_state_upload_keeps_the_list_within_the_margin():
+    # delayed schedule: an upload adds each owner's displacement to the audit bounds; the
+    # list stays where no owner moved past the margin, and the run is the same bits as
+    # one without the round trip; a larger shift rebuilds the list, and both follow the
+    # oracle
+    s = W.dense_lattice(n=900, seed=23, vel_sigma=0.3)
+    beta = 5e-5
+    kw = dict(precision="fp64", schedule="velocity_bound", margin=beta, margin_max=beta)
+    a = dem.World.from_scene(s, **kw)
+    b = dem.World.from_scene(s, **kw)
+    a.step(50)
+    b.step(50)
+    r0 = b.stats()["rebuilds"]
+    # positions and velocities pass through the host unchanged (the angular velocity is
+    # read in the body frame and rotated back, which rounds once a sphere has turned)
+    for _ in range(40):
+        a.step(1)
+        x, q, v, wb = b.owner_state()
+        b.set_owner_state(0, xyz=x, vel=v)
+        b.step(1)
+    for x, y in zip(a.owner_state(), b.owner_state()):
+        assert np.array_equal(x, y)
+    assert b.stats()["rebuilds"] - r0 <= a.stats()["rebuilds"] - r0 + 1
+    # the whole state through the host every step follows the oracle
+    c = dem.World.from_scene(s, **kw)
+    oc = oracle.OracleWorld(s)
+    c.step(50)
+    assert oc.step(50) == 0
+    for _ in range(20):
+        x, q, v, wb = c.owner_state()
+        c.set_owner_state(0, xyz=x, quat=q, vel=v, omega=wb)
+        c.step(1)
+        assert oc.step(1) == 0
+    errs, ok = state_close(c, oc, 1e-8)
+    assert ok, errs
+    for shift, rebuilt in ((0.1 * beta, False), (3.0 * beta, True)):
+        w = dem.World.from_scene(s, **kw)
+        ow = oracle.OracleWorld(s)
+        w.step(29)
+        stored = w.contacts()               # the history the 30th step leaves
+        w.step(1)
+        x, q, v, wb = w.owner_state()
+        x2 = x.copy()
+        x2[::7, 0] += shift
+        n0 = w.stats()["rebuilds"]
+        w.set_owner_state(0, xyz=x2)
+        sync_oracle_to_gpu(w, ow, stored)
+        w.step(1)
+        assert (w.stats()["rebuilds"] > n0) == rebuilt
+        assert ow.step(1) == 0
+        w.step(9)
+        assert ow.step(9) == 0
+        errs, ok = state_close(w, ow, 1e-8)
+        assert ok, (shift, errs)
+
+
 def test_diagnostics_match_oracle():
     """The GPU's fixed-order FP64 sums against the oracle's compensated sums of the same
     state, at 1e-9 of the summed magnitudes (energies: the sums themselves, every term
