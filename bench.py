@@ -239,7 +239,7 @@ MEASURED_TRAFFIC = {
                     ("pipeline.cuh", "struct StageLayout {", "a4f1f17d327f7a13")] + _INTEGRATE_SOURCE},
     ],
     "contact": [
-        {"n": 4_000_000, "margin": 2.1e-5, "bytes": 331.4e6, "tuning": {"contact_lean": 0},
+        {"n": 4_000_000, "margin": 2.1e-5, "bytes": 331.4e6, "tuning": {"contact_lean": 0, "contact_screen": 0},
          "source": [("pipeline.cuh", "k_contact(Dev<F> d, double *eval_F, double *eval_T)", "36e10c0e4e38a6ea"),
                     ("pipeline.cuh", "contact_slot(const Dev<F> &d", "363d4cb673f86026"),
                     ("pipeline.cuh", "pair_sums(const Dev<F> &d", "de27f25f313b3b49"),
@@ -390,7 +390,11 @@ def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step
     if ci:
         name = {"contact": "k_contact (pair forces + per-owner sums + update of the owners with partners)",
                 "integrate": "k_integrate (update of the owners without partners + audit)"}.get(dom, name)
-    return {"bound": "hbm", "kernel": name, "contact_integrates": ci,
+    screen = bool((tuning or {}).get("contact_screen", 0)) and not ci and not fused_step(prof)
+    if screen:
+        name = {"contact": "k_contact_screen + k_contact_eval (overlap screening of every listed entry, then "
+                           "pair forces + per-owner sums of the spheres with touching entries)"}.get(dom, name)
+    return {"bound": "hbm", "kernel": name, "contact_integrates": ci, "contact_screen": screen,
             "achieved": a, "peak": peak, "unit": "GB/s", "frac": (a / peak) if a else None,
             "traffic": per[dom]["traffic"],
             "peak_kind": peak_kind, "bytes_per_launch": per[dom]["bytes"], "avg_launch_ms": per[dom]["ms"],

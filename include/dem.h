@@ -294,6 +294,13 @@ typedef struct {
                                       ranges of the sorted snapshot in shared memory (256
                                       threads per block, narrow_block ignored), 0 = its
                                       threads read them from L1/L2.  The same lists        */
+    int32_t contact_screen;        /* worlds of single spheres with the two-kernel step, no
+                                      rolling resistance, the built-in contact model and
+                                      contact_integrates 0: 1 = two contact passes, a
+                                      screening kernel that tests every listed entry's
+                                      overlap and an evaluation kernel for the spheres
+                                      with touching entries; 0 = one contact kernel.  The
+                                      same bits either way; ignored elsewhere              */
 } dem_tuning;
 
 dem_status dem_set_tuning(dem_world *w, const dem_tuning *t);

@@ -204,6 +204,8 @@ struct DevStatus {
     int diverged;                // set by the force kernel, turned into a halt by the audit
     unsigned int list_pairs[2];  // sphere-sphere pairs of each list (each pair once)
     unsigned int list_busy[2];   // slots of each list with listed partners
+    unsigned int n_screen;       // spheres the screening pass of this step passed on to the
+                                 // evaluation (zeroed by the audit after every step)
 };
 
 // ------------------------------------------------------------------ position forms

@@ -109,6 +109,8 @@ public:
         if ((s = alloc(d_.owner_scene, Mp, err))) return s;
         if ((s = alloc(d_.owner_iso, Mp, err))) return s;
         if ((s = alloc(d_.touched, std::max(Mp, d_.Np), err))) return s;
+        if (!m_.clumps)
+            if ((s = alloc(d_.screen, std::max<int64_t>(d_.Np, 1), err))) return s;
         if ((s = alloc(d_.fo, M, err))) return s;
         if ((s = alloc(d_.to, M, err))) return s;
         if ((s = alloc(d_.owner_first, M, err))) return s;
@@ -510,12 +512,36 @@ public:
                            std::string &err) override
     {
         if (n <= 0) return DEM_OK;
+        // pinned (mapped) caller buffers are written by the kernel itself across the host
+        // link; any other buffer goes through device scratch and a copy
+        double *out[4] = {x, q, v, w};
+        bool direct = true;
+        for (double *&p : out) {
+            if (!p) continue;
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+                (void)cudaGetLastError();
+                direct = false;
+            } else if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+                p = static_cast<double *>(a.devicePointer);
+            } else {
+                direct = false;
+            }
+        }
+        if (direct) {
+            k_owner_download<F><<<grid(n, DOWNLOAD_BLOCK), DOWNLOAD_BLOCK, 0, sf_>>>(d_, first, n, out[0], out[1],
+                                                                                    out[2], out[3]);
+            DEM_CU(cudaGetLastError());
+            DEM_CU(cudaStreamSynchronize(sf_));
+            return DEM_OK;
+        }
         double *buf;
         dem_status s;
         if ((s = scratch(buf, 13 * n, err))) return s;
-        k_owner_download<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, buf, buf + 3 * n, buf + 7 * n, buf + 10 * n);
+        k_owner_download<F><<<grid(n, DOWNLOAD_BLOCK), DOWNLOAD_BLOCK, 0, sf_>>>(
+            d_, first, n, x ? buf : nullptr, q ? buf + 3 * n : nullptr, v ? buf + 7 * n : nullptr,
+            w ? buf + 10 * n : nullptr);
         DEM_CU(cudaGetLastError());
-        // straight into the caller's buffers (full link speed when they are pinned)
         if (x) DEM_CU(cudaMemcpyAsync(x, buf, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
         if (q) DEM_CU(cudaMemcpyAsync(q, buf + 3 * n, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
         if (v) DEM_CU(cudaMemcpyAsync(v, buf + 7 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, sf_));
@@ -1337,17 +1363,14 @@ private:
                 return DEM_ERR_ARG;
             }
         }
-        // the angular velocity conversion needs the new orientation: quaternion first
         const int bounds = keep_bounds ? 1 : 0;
         if (keep_bounds)
             DEM_CU(cudaMemsetAsync(&st_->upload_disp_bits, 0, sizeof(unsigned int), sf_));
-        if (q && w) {
-            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, nullptr, da, bounds);
-            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, nullptr, nullptr, nullptr, dw, nullptr,
-                                                             keep_bounds ? 2 : 0);
-        } else {
-            k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, dw, da, bounds);
-        }
+        // one pass: a thread converts its angular velocity with the orientation it has just
+        // stored
+        int ex = 0;
+        const double inv_ld = (F::voxel && std::frexp(d_.Ld, &ex) == 0.5) ? 1.0 / d_.Ld : 0.0;
+        k_owner_upload<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n, dx, dq, dv, dw, da, bounds, inv_ld);
         if (!m_.clumps) k_mirror_quat<F><<<grid(n, 256), 256, 0, sf_>>>(d_, first, n);
         DEM_CU(cudaGetLastError());
         unsigned int bits = 0;
@@ -1497,6 +1520,7 @@ private:
         tune_.fused_block = m_.clumps ? 0 : t->fused_block;
         tune_.contact_integrates = (!m_.clumps && t->contact_integrates) ? 1 : 0;
         tune_.narrow_staged = (t->narrow_staged && prepare_narrow_staged()) ? 1 : 0;
+        tune_.contact_screen = (!m_.clumps && t->contact_screen) ? 1 : 0;
         choose_binning();
         tune_.margin = 0.0;
         apply_margin(t->margin);
@@ -1677,11 +1701,11 @@ private:
                                           "\"narrow_block\": %d, \"detect_inline\": %d, \"cell_factor\": %lf, "
                                           "\"integrate_staged\": %d, \"contact_lean\": %d, \"fused_block\": %d, "
                                           "\"contact_integrates\": %d, \"binning\": %d, \"narrow_staged\": %d, "
-                                          "\"margin\": %lf, \"step_ms\": %lf}",
+                                          "\"contact_screen\": %d, \"margin\": %lf, \"step_ms\": %lf}",
                                     k, &t.contact_block, &t.integrate_block, &t.narrow_block, &t.detect_inline,
                                     &t.cell_factor, &t.integrate_staged, &t.contact_lean, &t.fused_block,
-                                    &t.contact_integrates, &t.binning, &t.narrow_staged, &t.margin,
-                                    &t.step_ms) == 14 &&
+                                    &t.contact_integrates, &t.binning, &t.narrow_staged, &t.contact_screen,
+                                    &t.margin, &t.step_ms) == 15 &&
                         key == k) {
                         best = t;
                         found = true;
@@ -1742,13 +1766,22 @@ private:
             t.step_ms = 0.0;
             if ((s = trial(t))) return s;
         }
-        // single spheres: the contact kernel integrating the owners with partners (each
-        // contact build), then forces and integration in one kernel, each block size
+        // single spheres: the two-pass contact step (built-in model, no rolling resistance),
+        // the contact kernel integrating the owners with partners (each contact build),
+        // then forces and integration in one kernel, each block size
+        if (!m_.clumps && !m_.rolling && m_.model == FORCE_MODEL_BUILTIN) {
+            dem_tuning t = best;
+            t.contact_screen = 1;
+            t.contact_lean = 0;
+            t.step_ms = 0.0;
+            if ((s = trial(t))) return s;
+        }
         if (!m_.clumps) {
             const dem_tuning b3 = best;
             for (int lean = 0; lean <= 1; ++lean) {
                 dem_tuning t = b3;
                 t.contact_integrates = 1;
+                t.contact_screen = 0;
                 t.contact_lean = lean;
                 t.step_ms = 0.0;
                 if ((s = trial(t))) return s;
@@ -1757,6 +1790,7 @@ private:
                 dem_tuning t = b3;
                 t.fused_block = fb;
                 t.contact_integrates = 0;
+                t.contact_screen = 0;
                 t.step_ms = 0.0;
                 if ((s = trial(t))) return s;
             }
@@ -1766,7 +1800,8 @@ private:
             if (f != b2.cell_factor)
                 if ((s = trial(dem_tuning{b2.contact_block, b2.integrate_block, b2.narrow_block, b2.detect_inline,
                                           0.0, f, b2.integrate_staged, b2.contact_lean, b2.fused_block, 0.0,
-                                          b2.contact_integrates, b2.binning, b2.narrow_staged})))
+                                          b2.contact_integrates, b2.binning, b2.narrow_staged,
+                                          b2.contact_screen})))
                     return s;
         // the binning: radix sort against counting sort (the automatic choice is one of
         // them), then the narrow phase staged in shared memory
@@ -1807,11 +1842,12 @@ private:
                              "{\"key\": \"%s\", \"contact_block\": %d, \"integrate_block\": %d, \"narrow_block\": "
                              "%d, \"detect_inline\": %d, \"cell_factor\": %.3f, \"integrate_staged\": %d, "
                              "\"contact_lean\": %d, \"fused_block\": %d, \"contact_integrates\": %d, "
-                             "\"binning\": %d, \"narrow_staged\": %d, \"margin\": %.17g, \"step_ms\": %.6f}\n",
+                             "\"binning\": %d, \"narrow_staged\": %d, \"contact_screen\": %d, \"margin\": %.17g, "
+                             "\"step_ms\": %.6f}\n",
                              key.c_str(), best.contact_block, best.integrate_block, best.narrow_block,
                              best.detect_inline, best.cell_factor, best.integrate_staged, best.contact_lean,
-                             best.fused_block, best.contact_integrates, best.binning, best.narrow_staged, best.margin,
-                             best.step_ms);
+                             best.fused_block, best.contact_integrates, best.binning, best.narrow_staged,
+                             best.contact_screen, best.margin, best.step_ms);
                 std::fclose(f);
             }
         }
@@ -2169,10 +2205,33 @@ private:
         } else if (MODE == MODE_STEP && integ()) {
             if (lean) k_contact<F, false, MODE_STEP, 1, false, FORCE_MODEL_BUILTIN, true><<<g, b, 0, sf_>>>(d_, eF, eT);
             else k_contact<F, false, MODE_STEP, 0, false, FORCE_MODEL_BUILTIN, true><<<g, b, 0, sf_>>>(d_, eF, eT);
+        } else if (MODE == MODE_STEP && screen()) {
+            k_contact_screen<F><<<(unsigned)screen_per_sm() * (unsigned)n_sm_, SCREEN_BLOCK, 0, sf_>>>(d_);
+            k_contact_eval<F><<<(unsigned)eval_per_sm(b) * (unsigned)n_sm_, b, 0, sf_>>>(d_);
         } else {
             if (lean) k_contact<F, false, MODE_STEP, 1><<<g, b, 0, sf_>>>(d_, eF, eT);
             else k_contact<F, false, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
         }
+    }
+
+    // resident blocks per SM of the two passes of the two-pass contact step
+    int screen_per_sm()
+    {
+        if (screen_occ_ > 0) return screen_occ_;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact_screen<F>, SCREEN_BLOCK, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        return screen_occ_ = per_sm;
+    }
+    int eval_per_sm(int b)
+    {
+        if (b == eval_occ_block_) return eval_occ_;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_contact_eval<F>, b, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        eval_occ_block_ = b;
+        return eval_occ_ = per_sm;
     }
 
     int contact_per_sm(int b)
@@ -2239,6 +2298,12 @@ private:
 
     // Single spheres with the fused step chosen: one kernel for forces and integration.
     bool fused() const { return !m_.clumps && !m_.rolling && m_.model == FORCE_MODEL_BUILTIN && tune_.fused_block > 0; }
+    // Single spheres, two-kernel step: contacts in two passes (screening, evaluation).
+    bool screen() const
+    {
+        return !m_.clumps && !m_.rolling && m_.model == FORCE_MODEL_BUILTIN && tune_.fused_block == 0 &&
+               !tune_.contact_integrates && tune_.contact_screen;
+    }
     // Single spheres, two-kernel step: the contact kernel integrates the owners it holds.
     bool integ() const
     {
@@ -2352,6 +2417,7 @@ private:
     double ms_total_ = 0.0;
     dem_tuning tune_{64, 256, 128, 0, 0.0, 1.0, 0, 0, 0};   // fused_block last: the two-kernel step
     int n_sm_ = 1, occ_block_ = 0, occ_per_sm_ = 1;
+    int screen_occ_ = 0, eval_occ_block_ = 0, eval_occ_ = 1;
     int64_t Mp_ = 0;                // owners rounded up to whole staging tiles
     int staged_per_sm_ = 0;
     bool act_alloc_ = false;

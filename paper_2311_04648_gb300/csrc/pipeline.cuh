@@ -62,6 +62,8 @@ struct Dev {
     // single spheres, two-kernel step: 1 where the contact kernel wrote the owner's force
     // of the step (its entries touched something), per owner with listed partners
     uint8_t *touched;
+    uint4 *screen;          // two-pass contact step: spheres with entries to evaluate (slot, row
+                            // length, entry mask low and high words)
     int n_scenes;
     int vpc;                        // voxels per cell edge (voxel form)
     double bin_invL;                // the smallest cells (schedule bins are made of them)
@@ -1503,10 +1505,13 @@ __device__ __forceinline__ const double *crr_table(const Dev<F> &d, double)
 // LAZY (single spheres): me comes without its velocities, which are read at the first
 // entry that needs them (a wall, or a sphere pair that overlaps).  Returns whether any
 // entry made contact (Fs and Ts are exactly zero otherwise).
-template <class F, bool CLUMPS, int MODE, bool ROLL = false, bool LAZY = false>
+// MASKED (the evaluation pass of the two-pass step): only the entries whose bit is set in
+// mask are evaluated (the screening pass wrote the others' zero history), in row order,
+// each partner's id read from its row.
+template <class F, bool CLUMPS, int MODE, bool ROLL = false, bool LAZY = false, bool MASKED = false>
 __device__ __forceinline__ bool pair_sums(const Dev<F> &d, const SphereK<F> &me_in, const Scene &sc, int64_t s, int n,
                                           uint32_t j_first, int sp, int hp, int lc, V3<typename F::R> &Fs,
-                                          V3<typename F::R> &Ts)
+                                          V3<typename F::R> &Ts, uint64_t mask = ~0ull)
 {
     static_assert(!LAZY || !CLUMPS, "only single spheres read their velocities late");
     using R = typename F::R;
@@ -1532,9 +1537,17 @@ __device__ __forceinline__ bool pair_sums(const Dev<F> &d, const SphereK<F> &me_
     const int row = sc.pair_base + (me.mat - sc.mat_base) * sc.n_mat - sc.mat_base;
     uint32_t j_next = j_first;
     for (int k = 0; k < n; ++k) {
+        if constexpr (MASKED) {
+            if (!((mask >> k) & 1ull)) continue;
+        }
         const int64_t e = (int64_t)k * d.Np + s;
-        const uint32_t j = j_next;
-        if (k + 1 < n) j_next = prow[e + d.Np];      // next partner's id in flight early
+        uint32_t j;
+        if constexpr (MASKED) {
+            j = prow[e];
+        } else {
+            j = j_next;
+            if (k + 1 < n) j_next = prow[e + d.Np];  // next partner's id in flight early
+        }
         R age = R(0);
         V3<R> ut = zero;
         ContactIn<R> c;
@@ -1954,6 +1967,115 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
         }
         // every lane of the warp gets here (the loop's exit is the only divergence)
         if constexpr (INTEG) audit_slots(d.audit, t0, threadIdx.x & 31, aud[0], aud[1], aud[2]);
+    }
+}
+
+// Two-pass contact step (single spheres, the built-in model without rolling resistance).
+// Most listed pairs do not touch: in one kernel, a warp's lanes split between the whole
+// Hertz-Mindlin evaluation and an early exit, and the evaluation's registers leave few
+// warps to hide the gathers.  The screening pass takes each sphere of the compacted work
+// with few registers, gathers its partners' position records and tests their overlap
+// exactly as the evaluation does; an entry that does not touch gets its zero history
+// here, a sphere none of whose entries touches its cleared flag, and a sphere with
+// touching entries (or wall entries, which only the evaluation tests) is appended to
+// d.screen with the mask of those entries (one atomic per warp).  The evaluation pass
+// (k_contact_eval) takes the appended spheres and evaluates only the masked entries, in
+// row order: the same sums, histories, forces and flags as k_contact, bit for bit.  The
+// order of d.screen depends on scheduling; results do not (each sphere's outputs are
+// its own).
+constexpr int SCREEN_BLOCK = 256;
+template <class F>
+__global__ void __launch_bounds__(SCREEN_BLOCK) k_contact_screen(Dev<F> d)
+{
+    using R = typename F::R;
+    using H = typename HistVec<R>::T;
+    DevStatus *stp = d.status;
+    if (stp->halt || stp->list_stale) return;
+    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
+    // the counter never exceeds the slots; the clamp keeps every index in bounds
+    const int64_t nw = min((int64_t)*d.lists.n_act[lc], d.Np);
+    const uint4 *act = d.lists.act[lc];
+    const uint32_t *prow = d.lists.partner[lc];
+    H *hout = d.lists.hist[hp ^ 1];
+    const V3<R> zero = {R(0), R(0), R(0)};
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together: the append below is warp-wide
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nw; base += stride) {
+        const int64_t t = base + lane;
+        bool cand = false;
+        uint4 item = make_uint4(0u, 0u, 0u, 0u);
+        if (t < nw) {
+            const uint4 a = act[t];
+            const uint32_t s = a.x;
+            const int n = (int)a.y;
+            if (n > 0 && d.st.active[sp][s]) {
+                const SphereK<F> me = load_sphere_pos<F>(d, sp, s);
+                uint64_t mask = 0;
+                uint32_t j_next = a.z;
+                for (int k = 0; k < n; ++k) {
+                    const int64_t e = (int64_t)k * d.Np + s;
+                    const uint32_t j = j_next;
+                    if (k + 1 < n) j_next = prow[e + d.Np];
+                    bool c = true;
+                    if (!(j & WALL_BIT)) {
+                        const SphereK<F> other = load_sphere_pos<F>(d, sp, j);
+                        V3<R> dd;
+                        R dist, delta;
+                        sphere_gap<F>(d, me, other, dd, dist, delta);
+                        c = delta > R(0) && dist > R(0) && d.st.active[sp][j];
+                    }
+                    if (c) mask |= 1ull << k;
+                    else hist_put(hout, e, zero, R(0));
+                }
+                if (mask) {
+                    cand = true;
+                    item = make_uint4(s, (uint32_t)n, (uint32_t)mask, (uint32_t)(mask >> 32));
+                } else {
+                    d.touched[s] = 0;
+                }
+            }
+        }
+        const unsigned int ball = __ballot_sync(0xffffffffu, cand);
+        if (ball) {
+            const int leader = __ffs(ball) - 1;
+            unsigned int at = 0;
+            if (lane == leader) at = atomicAdd(&stp->n_screen, (unsigned int)__popc(ball));
+            at = __shfl_sync(0xffffffffu, at, leader);
+            if (cand) d.screen[at + __popc(ball & ((1u << lane) - 1u))] = item;
+        }
+    }
+}
+
+// The evaluation pass of the two-pass step: a persistent grid over the spheres the
+// screening pass appended, each evaluating its masked entries (pair_sums<..., MASKED>)
+// and writing its force and flag as k_contact does.
+template <class F>
+__global__ void __launch_bounds__(CONTACT_BLOCK_MAX, 4) k_contact_eval(Dev<F> d)
+{
+    using R = typename F::R;
+    using R4 = typename F::R4;
+    DevStatus *stp = d.status;
+    if (stp->halt || stp->list_stale) return;
+    const int sp = stp->state_par, hp = stp->hist_par, lc = stp->list_cur;
+    const int64_t nw = min((int64_t)stp->n_screen, d.Np);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += stride) {
+        const uint4 a = d.screen[t];
+        const uint32_t s = a.x;
+        const uint64_t mask = (uint64_t)a.z | ((uint64_t)a.w << 32);
+        const int scene = d.n_scenes > 1 ? d.owner_scene[s] : 0;
+        const Scene &sc = d.scenes[scene];
+        SphereK<F> me = load_sphere_pos<F>(d, sp, s);
+        if constexpr (F::voxel) me.mat = sc.n_mat == 1 ? sc.mat_base : (int)d.sph_mat[s];
+        V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
+        const bool any = pair_sums<F, false, MODE_STEP, false, true, true>(d, me, sc, s, (int)a.y, 0u, sp, hp, lc,
+                                                                            Fs, Ts, mask);
+        d.touched[s] = any ? 1 : 0;
+        if (any) {
+            d.fo[s] = R4{Fs.x, Fs.y, Fs.z, R(0)};
+            d.to[s] = R4{Ts.x, Ts.y, Ts.z, R(0)};
+        }
     }
 }
 
@@ -2395,6 +2517,8 @@ __global__ void __launch_bounds__(ITILE) k_integrate_staged(Dev<FormF32> d)
 static __global__ void k_audit(DevStatus *stp, unsigned int *audit)
 {
     // one warp: each lane reads and clears AUDIT_SLOTS / 32 slots, a warp max combines them
+    // (the screening pass's counter restarts after every step, whatever happened in it)
+    if (threadIdx.x == 0) stp->n_screen = 0;
     if (stp->halt || stp->list_stale) return;
     const int lane = threadIdx.x & 31;
     unsigned int md = 0, md2 = 0, mv = 0;
@@ -2786,28 +2910,46 @@ __global__ void __launch_bounds__(256) k_active_box(Dev<F> d, int64_t first, int
     family[o] = (uint8_t)(in ? fin : fout);
 }
 
+// Owner state in the FP64 host layout (position, orientation, velocity, body-frame
+// angular velocity; 3, 4, 3 and 3 doubles per owner), each output optional (null: not
+// written).  A block of 256 owners stages its values in shared memory and writes each
+// array as one contiguous run of whole warps' 8-byte stores, so that the outputs may be
+// mapped host memory written across the host link without partial lines.
+constexpr int DOWNLOAD_BLOCK = 256;
 template <class F>
-__global__ void k_owner_download(Dev<F> d, int64_t first, int64_t n, double *x, double *q, double *v, double *w)
+__global__ void __launch_bounds__(DOWNLOAD_BLOCK) k_owner_download(Dev<F> d, int64_t first, int64_t n, double *x,
+                                                                   double *q, double *v, double *w)
 {
     using R = typename F::R;
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int64_t o = first + k;
-    const int sp = d.status->state_par;
-    R mass;
-    typename F::Pos p = F::load(d.st.pos[sp], o, mass);
-    const Scene &sc = d.scenes[d.owner_scene[o]];
-    V3<double> pa = F::absolute(p, sc, d.Ld);
-    x[3 * k] = pa.x; x[3 * k + 1] = pa.y; x[3 * k + 2] = pa.z;
-    auto q4 = d.st.quat[sp][o];
-    q[4 * k] = q4.x; q[4 * k + 1] = q4.y; q[4 * k + 2] = q4.z; q[4 * k + 3] = q4.w;
-    auto v4 = d.st.kv[sp][2 * o];
-    v[3 * k] = v4.x; v[3 * k + 1] = v4.y; v[3 * k + 2] = v4.z;
-    auto w4 = d.st.kv[sp][2 * o + 1];
-    R m[9];
-    quat_mat<R>(q4.x, q4.y, q4.z, q4.w, m);
-    V3<R> wb = mat_tvec<R>(m, V3<R>{w4.x, w4.y, w4.z});
-    w[3 * k] = wb.x; w[3 * k + 1] = wb.y; w[3 * k + 2] = wb.z;
+    __shared__ double sx[3 * DOWNLOAD_BLOCK], sq[4 * DOWNLOAD_BLOCK], sv[3 * DOWNLOAD_BLOCK],
+        sw[3 * DOWNLOAD_BLOCK];
+    const int t = threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.x * DOWNLOAD_BLOCK;
+    const int64_t k = k0 + t;
+    if (k < n) {
+        const int64_t o = first + k;
+        const int sp = d.status->state_par;
+        R mass;
+        typename F::Pos p = F::load(d.st.pos[sp], o, mass);
+        const Scene &sc = d.scenes[d.owner_scene[o]];
+        const V3<double> pa = F::absolute(p, sc, d.Ld);
+        sx[3 * t] = pa.x; sx[3 * t + 1] = pa.y; sx[3 * t + 2] = pa.z;
+        const auto q4 = d.st.quat[sp][o];
+        sq[4 * t] = q4.x; sq[4 * t + 1] = q4.y; sq[4 * t + 2] = q4.z; sq[4 * t + 3] = q4.w;
+        const auto v4 = d.st.kv[sp][2 * o];
+        sv[3 * t] = v4.x; sv[3 * t + 1] = v4.y; sv[3 * t + 2] = v4.z;
+        const auto w4 = d.st.kv[sp][2 * o + 1];
+        R m[9];
+        quat_mat<R>(q4.x, q4.y, q4.z, q4.w, m);
+        const V3<R> wb = mat_tvec<R>(m, V3<R>{w4.x, w4.y, w4.z});
+        sw[3 * t] = wb.x; sw[3 * t + 1] = wb.y; sw[3 * t + 2] = wb.z;
+    }
+    __syncthreads();
+    const int nb = (int)min((int64_t)DOWNLOAD_BLOCK, n - k0);
+    if (x) for (int i = t; i < 3 * nb; i += DOWNLOAD_BLOCK) x[3 * k0 + i] = sx[i];
+    if (q) for (int i = t; i < 4 * nb; i += DOWNLOAD_BLOCK) q[4 * k0 + i] = sq[i];
+    if (v) for (int i = t; i < 3 * nb; i += DOWNLOAD_BLOCK) v[3 * k0 + i] = sv[i];
+    if (w) for (int i = t; i < 3 * nb; i += DOWNLOAD_BLOCK) w[3 * k0 + i] = sw[i];
 }
 
 // FP64 host layout to owner state (both buffers' current one); world-frame angular
@@ -2817,28 +2959,36 @@ __global__ void k_owner_download(Dev<F> d, int64_t first, int64_t n, double *x, 
 // upload between steps) adds each owner's displacement by the upload, rounded up, to
 // both of them, and the largest accumulator of the list in use goes to
 // upload_disp_bits, so that the host keeps the list where no owner moved past its
-// margin; 2 leaves them as they are (a second pass over the same owners).
+// margin; 2 leaves them as they are.  inv_ld: the reciprocal of the voxel edge where
+// that edge is a power of two (the quotient by it is then a product), else 0.
 template <class F>
-__global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double *x, const double *q, const double *v,
-                               const double *w, const uint8_t *act, int bounds)
+__device__ __forceinline__ unsigned int owner_upload_one(const Dev<F> &d, int64_t first, int64_t k, const double *x,
+                                                         const double *q, const double *v, const double *w,
+                                                         const uint8_t *act, int bounds, double inv_ld)
 {
     using R = typename F::R;
     using R4 = typename F::R4;
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int64_t o = first + k;
+    unsigned int bits = 0;
+    const int64_t o = first + k;
     const int sp = d.status->state_par;
     R mass;
     typename F::Aux aux;
     typename F::Pos p = F::load(d.st.pos[sp], o, mass, aux);
     const Scene &sc = d.scenes[d.owner_scene[o]];
-    double moved = 0.0;
-    const V3<double> before = F::absolute(p, sc, d.Ld);
+    float moved_f = 0.0f;
+    const typename F::Pos p0 = p;
     if (x) {
         if constexpr (F::voxel) {
             PosF32 &pv = p;
             double rx = rsub(x[3 * k], sc.lo[0]), ry = rsub(x[3 * k + 1], sc.lo[1]), rz = rsub(x[3 * k + 2], sc.lo[2]);
-            double fx = floor(__ddiv_rn(rx, d.Ld)), fy = floor(__ddiv_rn(ry, d.Ld)), fz = floor(__ddiv_rn(rz, d.Ld));
+            // the voxel edge is a power of two: scaling by its reciprocal is the quotient
+            // exactly, without a division per coordinate (slow in FP64)
+            double fx, fy, fz;
+            if (inv_ld > 0.0) {
+                fx = floor(rx * inv_ld); fy = floor(ry * inv_ld); fz = floor(rz * inv_ld);
+            } else {
+                fx = floor(__ddiv_rn(rx, d.Ld)); fy = floor(__ddiv_rn(ry, d.Ld)); fz = floor(__ddiv_rn(rz, d.Ld));
+            }
             pv.cx = (int)fx; pv.cy = (int)fy; pv.cz = (int)fz;
             pv.x = (float)rsub(rx, rmul(fx, d.Ld));
             pv.y = (float)rsub(ry, rmul(fy, d.Ld));
@@ -2849,10 +2999,25 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
         } else {
             p.x = x[3 * k]; p.y = x[3 * k + 1]; p.z = x[3 * k + 2];
         }
-        F::store(d.st.pos[sp], o, p, mass, aux);
-        const V3<double> after = F::absolute(p, sc, d.Ld);
-        const double dx = after.x - before.x, dy = after.y - before.y, dz = after.z - before.z;
-        moved = sqrt(dx * dx + dy * dy + dz * dz) * (1.0 + 1e-12) + 1e-15;
+        typename F::PosStore pos_out = d.st.pos[sp];
+        F::store(pos_out, o, p, mass, aux);
+        // the displacement from the two encodings: in the voxel form the voxel difference
+        // times the power-of-two edge (exact) plus the offsets' difference, each component
+        // within two roundings of its own size; then an upper bound in FP32 with every
+        // operation rounded up (the bound is kept in FP32 in the voxel form anyway)
+        V3<double> dm;
+        if constexpr (F::voxel) {
+            const PosF32 &a = p, &b = p0;
+            dm = {(double)(a.cx - b.cx) * d.Ld + ((double)a.x - (double)b.x),
+                  (double)(a.cy - b.cy) * d.Ld + ((double)a.y - (double)b.y),
+                  (double)(a.cz - b.cz) * d.Ld + ((double)a.z - (double)b.z)};
+        } else {
+            dm = {p.x - p0.x, p.y - p0.y, p.z - p0.z};
+        }
+        const float ax = __double2float_ru(fabs(dm.x) * (1.0 + 1e-15));
+        const float ay = __double2float_ru(fabs(dm.y) * (1.0 + 1e-15));
+        const float az = __double2float_ru(fabs(dm.z) * (1.0 + 1e-15));
+        moved_f = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(ax, ax), __fmul_ru(ay, ay)), __fmul_ru(az, az)));
     }
     R4 q4 = d.st.quat[sp][o];
     if (q) {
@@ -2863,15 +3028,14 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
     if (bounds == 1) {
         // the bounds grow by the displacement (rounded up in the voxel form's FP32)
         if constexpr (F::voxel) {
-            const float m = __double2float_ru(moved);
-            kv0.w = __fadd_ru(kv0.w, m);
-            kv1.w = __fadd_ru(kv1.w, m);
+            kv0.w = __fadd_ru(kv0.w, moved_f);
+            kv1.w = __fadd_ru(kv1.w, moved_f);
         } else {
-            kv0.w = kv0.w + moved;
-            kv1.w = kv1.w + moved;
+            kv0.w = __dadd_ru(kv0.w, (double)moved_f);
+            kv1.w = __dadd_ru(kv1.w, (double)moved_f);
         }
         const R in_use = d.status->acc_par == 0 ? kv0.w : kv1.w;
-        atomicMax(&d.status->upload_disp_bits, __float_as_uint(__double2float_ru((double)in_use)));
+        bits = __float_as_uint(__double2float_ru((double)in_use));
     } else if (bounds == 0) {
         kv0.w = R(0);
         kv1.w = R(0);
@@ -2886,6 +3050,24 @@ __global__ void k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double 
     if (v || bounds == 1) d.st.kv[sp][2 * o] = kv0;
     if (w || bounds == 1) d.st.kv[sp][2 * o + 1] = kv1;
     if (act) d.st.active[sp][o] = act[k];
+    return bits;
+}
+
+// One thread per uploaded owner (blocks of whole warps).  bounds 1: the largest in-use
+// bound of the upload goes to status->upload_disp_bits (a non-negative float's bits
+// order as the float), one atomic per warp.
+template <class F>
+__global__ void __launch_bounds__(256) k_owner_upload(Dev<F> d, int64_t first, int64_t n, const double *x,
+                                                      const double *q, const double *v, const double *w,
+                                                      const uint8_t *act, int bounds, double inv_ld)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int bits = 0;
+    if (k < n) bits = owner_upload_one<F>(d, first, k, x, q, v, w, act, bounds, inv_ld);
+    if (bounds == 1) {
+        bits = __reduce_max_sync(0xffffffffu, bits);
+        if ((threadIdx.x & 31) == 0 && bits != 0) atomicMax(&d.status->upload_disp_bits, bits);
+    }
 }
 
 // Both orientation buffers get the current orientation (single spheres: a sphere at rest

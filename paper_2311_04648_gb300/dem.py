@@ -63,7 +63,8 @@ class Tuning(C.Structure):
                 ("detect_inline", C.c_int32), ("step_ms", C.c_double), ("cell_factor", C.c_double),
                 ("integrate_staged", C.c_int32), ("contact_lean", C.c_int32), ("fused_block", C.c_int32),
                 ("margin", C.c_double), ("contact_integrates", C.c_int32), ("binning", C.c_int32),
-                ("narrow_staged", C.c_int32)]
+                ("narrow_staged", C.c_int32),
+                ("contact_screen", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -382,10 +383,20 @@ class World:
         return s.value
 
     # ---- read back
-    def owner_state(self, first=0, n=None):
+    def owner_state(self, first=0, n=None, out=None):
+        """Positions, orientations, velocities and body-frame angular velocities of owners
+        first..first+n-1 as four float64 arrays; ``out``: four C-contiguous float64 arrays
+        of shapes (n, 3), (n, 4), (n, 3), (n, 3) to fill instead (pinned host memory is
+        written by the device directly)."""
         if n is None:
             n = self.n_owner
-        x = np.empty((n, 3)); q = np.empty((n, 4)); v = np.empty((n, 3)); w = np.empty((n, 3))
+        if out is not None:
+            x, q, v, w = out
+            for a, c in zip(out, (3, 4, 3, 3)):
+                if a.dtype != np.float64 or a.shape != (n, c) or not a.flags.c_contiguous:
+                    raise ValueError("out arrays must be C-contiguous float64 of shapes (n,3),(n,4),(n,3),(n,3)")
+        else:
+            x = np.empty((n, 3)); q = np.empty((n, 4)); v = np.empty((n, 3)); w = np.empty((n, 3))
         self._c(self.L.dem_get_owner_state(self.h, first, n, _p(x), _p(q), _p(v), _p(w)))
         return x, q, v, w
 

@@ -61,3 +61,26 @@ def test_world_on_torch_memory_and_streams_matches_a_self_allocating_world(preci
     assert live == {}                       # every allocation was handed back
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated(dev) == before
+
+
+def test_owner_state_into_pinned_host_buffers_equals_the_copied_state():
+    # pinned caller buffers are written by the device across the host link; pageable ones
+    # through device scratch and copies: the same values, on ragged ranges (not a whole
+    # number of 256-owner blocks) and at an interior address of a pinned allocation
+    torch = pytest.importorskip("torch")
+    w = dem.World.from_scene(_scene(), precision="voxel_fp32", schedule="velocity_bound")
+    try:
+        w.step(60)
+        for first, n in ((0, w.n_owner), (37, 1000), (w.n_owner - 1, 1)):
+            ref = w.owner_state(first, n)
+            pads = []
+            for c in (3, 4, 3, 3):
+                t = torch.full((n + 5, c), np.nan, dtype=torch.float64).pin_memory()
+                pads.append(t.numpy())
+            out = tuple(p[5:] for p in pads)          # interior of the pinned block
+            got = w.owner_state(first, n, out=out)
+            for a, b, p in zip(ref, got, pads):
+                assert np.array_equal(a, b)
+                assert np.isnan(p[:5]).all()          # nothing written before the range
+    finally:
+        w.close()

@@ -368,3 +368,69 @@ def test_counting_sort_binning_with_families_in_a_batch():
     assert res[0][1] == res[1][1]
     with pytest.raises(Exception):
         w.set_tuning(binning=3)
+
+
+@pytest.mark.parametrize("prec", ["voxel_fp32", "fp64"])
+def test_two_pass_contact_step_is_bit_identical(prec):
+    # screening and evaluation passes against the single contact kernel: both schedules,
+    # switched in mid-run; with a wide margin the rows pass 32 entries (the entry mask's
+    # high word)
+    for s, beta in ((W.dense_lattice(n=900, seed=37, vel_sigma=0.3), 5e-5),
+                    (W.dense_lattice(n=700, seed=41, vel_sigma=0.3), 1.2e-3)):
+        for sched in ("every_step", "velocity_bound"):
+            kw = dict(precision=prec, schedule=sched, margin_max=beta)
+            if sched != "every_step":
+                kw["margin"] = beta
+            a = dem.World.from_scene(s, **kw)
+            a.set_tuning(fused_block=0, contact_integrates=0, contact_screen=0)
+            for k in (50, 20, 50):
+                a.step(k)
+            b = dem.World.from_scene(s, **kw)
+            b.set_tuning(fused_block=0, contact_integrates=0, contact_screen=1)
+            assert b.tuning()["contact_screen"] == 1
+            b.step(50)
+            b.set_tuning(fused_block=0, contact_integrates=0, contact_screen=0)
+            b.step(20)
+            b.set_tuning(fused_block=0, contact_integrates=0, contact_screen=1)
+            b.step(50)
+            for x, y in zip(_state(b), _state(a)):
+                assert np.array_equal(x, y)
+            ca, cb = a.contacts(), b.contacts()
+            assert len(ca["i"]) > 100
+            for k in ca:
+                assert np.array_equal(ca[k], cb[k]), k
+            assert b.listed_pairs()[0].tolist() == a.listed_pairs()[0].tolist()
+            sa, sb = a.stats(), b.stats()
+            assert sa["audit_fallbacks"] == sb["audit_fallbacks"] and sa["rebuilds"] == sb["rebuilds"]
+            if beta > 1e-4 and sched != "every_step":
+                assert sb["list_max_row"] > 32      # the every-step lists use no margin
+
+
+def test_two_pass_contact_step_with_a_sink_in_a_batch_and_ignored_for_clumps():
+    s = W.cone_bed(n=300, seed=13)
+    a = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    b = dem.World.from_scene(s, precision="voxel_fp32", schedule="velocity_bound")
+    a.set_tuning(fused_block=0, contact_integrates=0, contact_screen=0)
+    b.set_tuning(fused_block=0, contact_integrates=0, contact_screen=1)
+    a.step(900)
+    b.step(900)
+    for x, y in zip(_state(a), _state(b)):
+        assert np.array_equal(x, y)
+    v = _state(b)[2]
+    assert np.count_nonzero(np.all(v == 0.0, axis=1)) > 0     # the sink removed some
+    scenes = [W.dense_lattice(n=150 + 97 * k, seed=45 + k, vel_sigma=0.3) for k in range(3)]
+    beta = 5e-5
+    p = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    q = dem.Batch(scenes, schedule="velocity_bound", margin=beta, margin_max=beta)
+    p.initialize()
+    q.initialize()
+    p.worlds[0].set_tuning(fused_block=0, contact_integrates=0, contact_screen=0)
+    q.worlds[0].set_tuning(fused_block=0, contact_integrates=0, contact_screen=1)
+    p.step(60)
+    q.step(60)
+    for wp, wq in zip(p.worlds, q.worlds):
+        for x, y in zip(_state(wp), _state(wq)):
+            assert np.array_equal(x, y)
+    c = dem.World.from_scene(W.packed_clumps(n=100, seed=38), precision="voxel_fp32", schedule="every_step")
+    c.set_tuning(contact_screen=1)
+    assert c.tuning()["contact_screen"] == 0
