@@ -249,6 +249,18 @@ MEASURED_TRAFFIC = {
                     ("pipeline.cuh", "load_sphere_pos(const Dev<F> &d", "f767f41ecac8ae6a"),
                     ("pipeline.cuh", "load_sphere(const Dev<F> &d", "e464faf6f6eeda0b"),
                     ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]},
+        # the two-pass contact step: both kernels of one step (the contact phase's time
+        # covers both)
+        {"n": 4_000_000, "margin": 3.0e-5, "bytes": 422.9e6, "tuning": {"contact_screen": 1},
+         "source": [("pipeline.cuh", "k_contact_screen(Dev<F> d)", "eee7a70e82cd02b0"),
+                    ("pipeline.cuh", "k_contact_eval(Dev<F> d)", "7cb6d5353d4b1f84"),
+                    ("pipeline.cuh", "pair_sums(const Dev<F> &d", "c91a142e9d5d3105"),
+                    ("pipeline.cuh", "wall_contact(const Dev<F> &d", "54458541bf779dd2"),
+                    ("pipeline.cuh", "sphere_gap(const Dev<F> &d", "64de1a81d6ab41e3"),
+                    ("pipeline.cuh", "sphere_finish(const Dev<F> &d", "3fde901e334f3796"),
+                    ("pipeline.cuh", "load_sphere_pos(const Dev<F> &d", "f767f41ecac8ae6a"),
+                    ("pipeline.cuh", "load_sphere(const Dev<F> &d", "e464faf6f6eeda0b"),
+                    ("common.cuh", "struct FormF32 {", "02359980dafed2e7")]},
     ],
 }
 

@@ -62,8 +62,8 @@ struct Dev {
     // single spheres, two-kernel step: 1 where the contact kernel wrote the owner's force
     // of the step (its entries touched something), per owner with listed partners
     uint8_t *touched;
-    uint4 *screen;          // two-pass contact step: spheres with entries to evaluate (slot, row
-                            // length, entry mask low and high words)
+    uint4 *screen;          // two-pass contact step: spheres with entries to evaluate (slot, first
+                            // masked partner, entry mask low and high words)
     int n_scenes;
     int vpc;                        // voxels per cell edge (voxel form)
     double bin_invL;                // the smallest cells (schedule bins are made of them)
@@ -1506,8 +1506,10 @@ __device__ __forceinline__ const double *crr_table(const Dev<F> &d, double)
 // entry that needs them (a wall, or a sphere pair that overlaps).  Returns whether any
 // entry made contact (Fs and Ts are exactly zero otherwise).
 // MASKED (the evaluation pass of the two-pass step): only the entries whose bit is set in
-// mask are evaluated (the screening pass wrote the others' zero history), in row order,
-// each partner's id read from its row.
+// mask are evaluated (the screening pass wrote the others' zero history), in row order;
+// j_first is the first masked entry's partner, the others' ids are read from the row.
+// A masked sphere entry is known to overlap (the screening pass took the same test on
+// the same values), so its velocities and history are loaded with its position record.
 template <class F, bool CLUMPS, int MODE, bool ROLL = false, bool LAZY = false, bool MASKED = false>
 __device__ __forceinline__ bool pair_sums(const Dev<F> &d, const SphereK<F> &me_in, const Scene &sc, int64_t s, int n,
                                           uint32_t j_first, int sp, int hp, int lc, V3<typename F::R> &Fs,
@@ -1536,6 +1538,7 @@ __device__ __forceinline__ bool pair_sums(const Dev<F> &d, const SphereK<F> &me_
     const bool one = sc.n_mat == 1;
     const int row = sc.pair_base + (me.mat - sc.mat_base) * sc.n_mat - sc.mat_base;
     uint32_t j_next = j_first;
+    bool first = true;
     for (int k = 0; k < n; ++k) {
         if constexpr (MASKED) {
             if (!((mask >> k) & 1ull)) continue;
@@ -1543,7 +1546,8 @@ __device__ __forceinline__ bool pair_sums(const Dev<F> &d, const SphereK<F> &me_
         const int64_t e = (int64_t)k * d.Np + s;
         uint32_t j;
         if constexpr (MASKED) {
-            j = prow[e];
+            j = first ? j_first : prow[e];
+            first = false;
         } else {
             j = j_next;
             if (k + 1 < n) j_next = prow[e + d.Np];  // next partner's id in flight early
@@ -1567,15 +1571,23 @@ __device__ __forceinline__ bool pair_sums(const Dev<F> &d, const SphereK<F> &me_
             // pairs do not touch).  The pair is evaluated in this thread's own orientation
             // with this side's copy of the history (the partner's is its exact negation)
             SphereK<F> other = load_sphere_pos<F>(d, sp, j);
+            typename F::R4 v4{}, w4{};
+            if constexpr (MASKED) {
+                v4 = d.st.kv[sp][2 * j];
+                w4 = d.st.kv[sp][2 * j + 1];
+                ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
+            }
             V3<R> dd;
             R dist, delta;
             sphere_gap<F>(d, me, other, dd, dist, delta);
             on = delta > R(0) && dist > R(0) && d.st.active[sp][j];
             if (on) {
                 need_v();
-                const auto v4 = d.st.kv[sp][2 * j];
-                const auto w4 = d.st.kv[sp][2 * j + 1];
-                ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
+                if constexpr (!MASKED) {
+                    v4 = d.st.kv[sp][2 * j];
+                    w4 = d.st.kv[sp][2 * j + 1];
+                    ut = ROLL ? hist_get<H, R>(hin, e, age) : hist_get<H, R>(hin, e);
+                }
                 other.v = {v4.x, v4.y, v4.z};
                 other.w = {w4.x, w4.y, w4.z};
                 mb = other.mat >= 0 || one ? other.mat : (int)d.sph_mat[j];
@@ -1985,7 +1997,7 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, LEAN ? 5 : 4) k_contact(Dev
 // its own).
 constexpr int SCREEN_BLOCK = 256;
 template <class F>
-__global__ void __launch_bounds__(SCREEN_BLOCK) k_contact_screen(Dev<F> d)
+__global__ void __launch_bounds__(SCREEN_BLOCK, 5) k_contact_screen(Dev<F> d)
 {
     using R = typename F::R;
     using H = typename HistVec<R>::T;
@@ -2009,28 +2021,43 @@ __global__ void __launch_bounds__(SCREEN_BLOCK) k_contact_screen(Dev<F> d)
             const uint4 a = act[t];
             const uint32_t s = a.x;
             const int n = (int)a.y;
-            if (n > 0 && d.st.active[sp][s]) {
-                const SphereK<F> me = load_sphere_pos<F>(d, sp, s);
+            // the sphere's flag and record, its first partner's record and the second
+            // partner's id are independent loads, issued together
+            const bool live = n > 0 && d.st.active[sp][s];
+            const SphereK<F> me = load_sphere_pos<F>(d, sp, s);
+            uint32_t j = a.z;
+            SphereK<F> other = (j & WALL_BIT) ? me : load_sphere_pos<F>(d, sp, j);
+            uint32_t j_next = n > 1 ? prow[(int64_t)d.Np + s] : WALL_BIT;
+            if (live) {
                 uint64_t mask = 0;
-                uint32_t j_next = a.z;
+                uint32_t j_first = 0;
                 for (int k = 0; k < n; ++k) {
                     const int64_t e = (int64_t)k * d.Np + s;
-                    const uint32_t j = j_next;
-                    if (k + 1 < n) j_next = prow[e + d.Np];
+                    // the next partner's record and the id after it are in flight while
+                    // this entry is tested
+                    SphereK<F> nxt = other;
+                    if (k + 1 < n && !(j_next & WALL_BIT)) nxt = load_sphere_pos<F>(d, sp, j_next);
+                    const uint32_t j_after = k + 2 < n ? prow[e + 2 * (int64_t)d.Np] : WALL_BIT;
                     bool c = true;
                     if (!(j & WALL_BIT)) {
-                        const SphereK<F> other = load_sphere_pos<F>(d, sp, j);
                         V3<R> dd;
                         R dist, delta;
                         sphere_gap<F>(d, me, other, dd, dist, delta);
                         c = delta > R(0) && dist > R(0) && d.st.active[sp][j];
                     }
-                    if (c) mask |= 1ull << k;
-                    else hist_put(hout, e, zero, R(0));
+                    if (c) {
+                        if (!mask) j_first = j;
+                        mask |= 1ull << k;
+                    } else {
+                        hist_put(hout, e, zero, R(0));
+                    }
+                    j = j_next;
+                    other = nxt;
+                    j_next = j_after;
                 }
                 if (mask) {
                     cand = true;
-                    item = make_uint4(s, (uint32_t)n, (uint32_t)mask, (uint32_t)(mask >> 32));
+                    item = make_uint4(s, j_first, (uint32_t)mask, (uint32_t)(mask >> 32));
                 } else {
                     d.touched[s] = 0;
                 }
@@ -2064,13 +2091,15 @@ __global__ void __launch_bounds__(CONTACT_BLOCK_MAX, 4) k_contact_eval(Dev<F> d)
         const uint4 a = d.screen[t];
         const uint32_t s = a.x;
         const uint64_t mask = (uint64_t)a.z | ((uint64_t)a.w << 32);
+        const int n = 64 - __clzll((long long)mask);       // past the last masked entry
         const int scene = d.n_scenes > 1 ? d.owner_scene[s] : 0;
         const Scene &sc = d.scenes[scene];
-        SphereK<F> me = load_sphere_pos<F>(d, sp, s);
+        // nearly every sphere here has a touching entry: its velocities are read at once
+        SphereK<F> me = load_sphere<F, false, false>(d, sp, s);
         if constexpr (F::voxel) me.mat = sc.n_mat == 1 ? sc.mat_base : (int)d.sph_mat[s];
         V3<R> Fs = {R(0), R(0), R(0)}, Ts = {R(0), R(0), R(0)};
-        const bool any = pair_sums<F, false, MODE_STEP, false, true, true>(d, me, sc, s, (int)a.y, 0u, sp, hp, lc,
-                                                                            Fs, Ts, mask);
+        const bool any = pair_sums<F, false, MODE_STEP, false, false, true>(d, me, sc, s, n, a.y, sp, hp, lc, Fs,
+                                                                             Ts, mask);
         d.touched[s] = any ? 1 : 0;
         if (any) {
             d.fo[s] = R4{Fs.x, Fs.y, Fs.z, R(0)};

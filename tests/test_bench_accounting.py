@@ -88,12 +88,19 @@ def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(bench, monke
     def current(rec):
         return all(bench.kernel_source_hash(sig, fn) == hv for fn, sig, hv in rec["source"])
 
-    [t] = bench.MEASURED_TRAFFIC["contact"]
+    # the single contact kernel and the two-pass step each have their own record
+    t, two = bench.MEASURED_TRAFFIC["contact"]
+    assert t["tuning"]["contact_screen"] == 0 and two["tuning"] == {"contact_screen": 1}
+    for r in (t, two):
+        m = r["margin"]
+        assert bench.measured_traffic("contact", r["n"], m, tuning=r["tuning"]) == (
+            r["bytes"] if current(r) else None)
+        assert bench.measured_traffic("contact", r["n"] + 1, m, tuning=r["tuning"]) is None   # another size
+        assert bench.measured_traffic("contact", r["n"], 0.35 * m, tuning=r["tuning"]) is None  # another margin
+        assert bench.measured_traffic("contact", r["n"], tuning=r["tuning"]) is None          # margin unknown
+    # one build's record is not taken for the other
+    assert bench.measured_traffic("contact", two["n"], two["margin"], tuning={"contact_screen": 0}) is None
     m = t["margin"]
-    assert bench.measured_traffic("contact", t["n"], m) == (t["bytes"] if current(t) else None)
-    assert bench.measured_traffic("contact", t["n"] + 1, m) is None       # another size
-    assert bench.measured_traffic("contact", t["n"], 0.35 * m) is None    # another margin
-    assert bench.measured_traffic("contact", t["n"]) is None              # margin unknown
     # each build of the integration has its own record; another build than the captured
     # ones has none
     plain, staged = bench.MEASURED_TRAFFIC["integrate"]
@@ -113,6 +120,10 @@ def test_recorded_traffic_is_dropped_when_the_kernel_source_changes(bench, monke
     changed = dict(t, source=[(fn, sig, "0" * 16)] + t["source"][1:])
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, "contact", [changed])
     assert bench.measured_traffic("contact", t["n"], m) is None
+    fn, sig, hv = two["source"][0]
+    changed = dict(two, source=[(fn, sig, "0" * 16)] + two["source"][1:])
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, "contact", [changed])
+    assert bench.measured_traffic("contact", two["n"], two["margin"], tuning={"contact_screen": 1}) is None
 
 
 def test_bench_line_carries_the_contract_keys(bench, monkeypatch, capsys):
