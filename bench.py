@@ -414,6 +414,15 @@ def roofline(precision, n, prof, peak, peak_kind, margin=None, rebuilds_per_step
             "kernels": per, "listed_pairs": prof["listed_pairs"], "spheres_with_entries": prof["with_entries"]}
 
 
+def parse_tuning(text):
+    """'name=value,...' of --set-tuning as keyword arguments of World.set_tuning."""
+    kw = {}
+    for item in text.split(","):
+        k, v = item.split("=")
+        kw[k.strip()] = float(v) if k.strip() in ("cell_factor", "margin") else int(v)
+    return kw
+
+
 def run_ours(args, device):
     import torch
     from paper_2311_04648_gb300 import dem
@@ -461,11 +470,7 @@ def run_ours(args, device):
         w.step(start_at)
         out["tuning"] = w.tuning()
     if args.set_tuning:
-        kw = {}
-        for item in args.set_tuning.split(","):
-            k, v = item.split("=")
-            kw[k.strip()] = float(v) if k.strip() in ("cell_factor", "margin") else int(v)
-        w.set_tuning(**kw)
+        w.set_tuning(**parse_tuning(args.set_tuning))
         out["tuning"] = w.tuning()
     # the state at the start of the warm-up, for the plain form's run from the same state
     window_state = w.owner_state()
@@ -557,7 +562,8 @@ def run_scale(args, device, rank=0, world=1):
               (network trained on trajectories of the 2k-sphere box and a 1M-sphere
               section of the settling column) against the velocity-bound and every-step
               schedules, all audited;
-    batch  -- 512 column collapses of 1k-50k spheres in one engine, autotuned; with N
+    batch  -- 512 column collapses of 1k-50k spheres in one engine, autotuned on the state
+              after half the timed steps (then restored to the start); with N
               ranks the scenes are split by greedy bin packing on spheres x steps and
               each rank steps its share as one batch (no exchange until the end)."""
     import torch
@@ -587,6 +593,9 @@ def run_scale(args, device, rank=0, world=1):
         w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
         out["setup_s"] = time.perf_counter() - t0
         out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache) if args.tune_steps > 0 else w.tuning()
+        if args.set_tuning:
+            w.set_tuning(**parse_tuning(args.set_tuning))
+            out["tuning"] = w.tuning()
         w.step(args.warmup)
         s0 = w.stats()
         with ClockSampler(device) as clk:
@@ -623,6 +632,9 @@ def run_scale(args, device, rank=0, world=1):
                                      margin=None if sched == "every_step" else 6e-5, margin_max=6e-5)
             if sched == "learned":
                 w.load_schedule_model(blob)
+            if args.set_tuning:
+                w.set_tuning(**parse_tuning(args.set_tuning))
+            out[f"tuning_{sched}"] = w.tuning()
             w.step(args.warmup)
             s0 = w.stats()
             k = steps if sched != "every_step" else max(1, min(steps, args.plain_steps))
@@ -641,6 +653,9 @@ def run_scale(args, device, rank=0, world=1):
         w = dem.World.from_scene(scene, precision="voxel_fp32", schedule="velocity_bound", device=device)
         out["setup_s"] = time.perf_counter() - t0
         out["tuning"] = w.autotune(steps=args.tune_steps, cache_path=args.tune_cache) if args.tune_steps > 0 else w.tuning()
+        if args.set_tuning:
+            w.set_tuning(**parse_tuning(args.set_tuning))
+            out["tuning"] = w.tuning()
         w.step(args.warmup)
         s0 = w.stats()
         with ClockSampler(device) as clk:
@@ -664,7 +679,20 @@ def run_scale(args, device, rank=0, world=1):
         b.initialize()
         out["setup_s"] = time.perf_counter() - t0
         w0 = b.worlds[0]
-        out["tuning"] = w0.autotune(steps=args.tune_steps, cache_path=args.tune_cache) if args.tune_steps > 0 else w0.tuning()
+        # tuned on a state in contact (the collapses under way at the tuning step), then
+        # restored to the start: trials from the initial state favour shapes that lose
+        # once contacts develop
+        if args.tune_steps > 0:
+            start = w0.save_state()
+            b.step(min(args.tune_at, max(0, steps // 2)))
+            out["tuning"] = w0.autotune(steps=args.tune_steps, cache_path=args.tune_cache)
+            w0.load_state(start)
+            del start
+        else:
+            out["tuning"] = w0.tuning()
+        if args.set_tuning:
+            w0.set_tuning(**parse_tuning(args.set_tuning))
+            out["tuning"] = w0.tuning()
         b.step(args.warmup)
         s0 = w0.stats()
         with ClockSampler(device) as clk:
