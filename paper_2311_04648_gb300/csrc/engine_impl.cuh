@@ -65,6 +65,10 @@ public:
         DEM_CU(cudaEventCreate(&ev_a_));
         DEM_CU(cudaEventCreate(&ev_b_));
         DEM_CU(cudaEventCreate(&ev_c_));
+        // host uploads are copied on a stream of their own, so that the force stream can
+        // check each piece while the next one is copied
+        DEM_CU(cudaStreamCreateWithFlags(&sc_, cudaStreamNonBlocking));
+        DEM_CU(cudaEventCreateWithFlags(&ev_up_, cudaEventDisableTiming));
 
         const int64_t M = (int64_t)m_.mass.size();
         const int64_t N = (int64_t)m_.sph_owner.size();
@@ -1344,17 +1348,40 @@ private:
                *dw = w ? buf + 10 * n : nullptr;
         uint8_t *da = act ? reinterpret_cast<uint8_t *>(buf + 13 * n) : nullptr;
         int *bad = reinterpret_cast<int *>(buf + 13 * n + (n + 7) / 8);
-        if (x) DEM_CU(cudaMemcpyAsync(dx, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
-        if (q) DEM_CU(cudaMemcpyAsync(dq, q, 4 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
-        if (v) DEM_CU(cudaMemcpyAsync(dv, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
-        if (w) DEM_CU(cudaMemcpyAsync(dw, w, 3 * n * sizeof(double), cudaMemcpyHostToDevice, sf_));
-        if (act) DEM_CU(cudaMemcpyAsync(da, act, n, cudaMemcpyHostToDevice, sf_));
-        // reject non-finite positions and velocities before anything is applied
+        // the arrays are copied in pieces on the copy stream (after the force stream's
+        // earlier work, which may still read the scratch); the force stream checks each
+        // piece for non-finite positions and velocities as soon as it has landed, while
+        // the next piece is copied, and nothing is applied before every piece has passed
+        DEM_CU(cudaEventRecord(ev_up_, sf_));
+        DEM_CU(cudaStreamWaitEvent(sc_, ev_up_, 0));
+        if (x || v || w) DEM_CU(cudaMemsetAsync(bad, 0, sizeof(int), sf_));
+        struct Piece {
+            const double *h;   // caller's array
+            double *dev;       // its scratch copy
+            int c;             // doubles per owner
+            bool check;        // rejected if not finite
+        };
+        const Piece arrs[4] = {{x, dx, 3, true}, {q, dq, 4, false}, {v, dv, 3, true}, {w, dw, 3, true}};
+        const int64_t chunk = n >= (int64_t)1 << 20 ? (n + 3) / 4 : n;
+        for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+            const int64_t cn = std::min(chunk, n - c0);
+            for (const Piece &a : arrs)
+                if (a.h)
+                    DEM_CU(cudaMemcpyAsync(a.dev + a.c * c0, a.h + a.c * c0, a.c * cn * sizeof(double),
+                                           cudaMemcpyHostToDevice, sc_));
+            DEM_CU(cudaEventRecord(ev_up_, sc_));
+            DEM_CU(cudaStreamWaitEvent(sf_, ev_up_, 0));
+            for (const Piece &a : arrs)
+                if (a.h && a.check)
+                    k_nonfinite<<<grid(a.c * cn, 256), 256, 0, sf_>>>(a.dev + a.c * c0, a.c * cn, bad);
+        }
+        if (act) {
+            DEM_CU(cudaMemcpyAsync(da, act, n, cudaMemcpyHostToDevice, sc_));
+            DEM_CU(cudaEventRecord(ev_up_, sc_));
+            DEM_CU(cudaStreamWaitEvent(sf_, ev_up_, 0));
+        }
+        DEM_CU(cudaGetLastError());
         if (x || v || w) {
-            DEM_CU(cudaMemsetAsync(bad, 0, sizeof(int), sf_));
-            const double *arr[3] = {dx, dv, dw};
-            for (const double *a : arr)
-                if (a) k_nonfinite<<<grid(3 * n, 256), 256, 0, sf_>>>(a, 3 * n, bad);
             int hbad = 0;
             DEM_CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, sf_));
             DEM_CU(cudaStreamSynchronize(sf_));
@@ -2392,7 +2419,10 @@ private:
         if (ev_a_) cudaEventDestroy(ev_a_);
         if (ev_b_) cudaEventDestroy(ev_b_);
         if (ev_c_) cudaEventDestroy(ev_c_);
-        ev_snap_ = ev_det_ = ev_a_ = ev_b_ = ev_c_ = nullptr;
+        if (ev_up_) cudaEventDestroy(ev_up_);
+        ev_snap_ = ev_det_ = ev_a_ = ev_b_ = ev_c_ = ev_up_ = nullptr;
+        if (sc_) cudaStreamDestroy(sc_);
+        sc_ = nullptr;
         if (own_sf_ && sf_) cudaStreamDestroy(sf_);
         if (own_sd_ && sd_) cudaStreamDestroy(sd_);
         sf_ = sd_ = nullptr;
@@ -2405,9 +2435,10 @@ private:
     DetectBuffers db_{};
     DevStatus *st_ = nullptr;
     DevStatus *sth_ = nullptr;
-    cudaStream_t sf_ = nullptr, sd_ = nullptr;
+    cudaStream_t sf_ = nullptr, sd_ = nullptr, sc_ = nullptr;
     bool own_sf_ = false, own_sd_ = false;
-    cudaEvent_t ev_snap_ = nullptr, ev_det_ = nullptr, ev_a_ = nullptr, ev_b_ = nullptr, ev_c_ = nullptr;
+    cudaEvent_t ev_snap_ = nullptr, ev_det_ = nullptr, ev_a_ = nullptr, ev_b_ = nullptr, ev_c_ = nullptr,
+                ev_up_ = nullptr;
     std::vector<void *> allocs_;
     double *scratch_ = nullptr;
     int64_t scratch_n_ = 0;

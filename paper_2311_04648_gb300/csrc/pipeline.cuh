@@ -3071,10 +3071,20 @@ __device__ __forceinline__ unsigned int owner_upload_one(const Dev<F> &d, int64_
     }
     if (v) kv0 = R4{(R)v[3 * k], (R)v[3 * k + 1], (R)v[3 * k + 2], kv0.w};
     if (w) {
-        double m[9];
-        quat_mat<double>((double)q4.x, (double)q4.y, (double)q4.z, (double)q4.w, m);
-        V3<double> wg = mat_vec<double>(m, V3<double>{w[3 * k], w[3 * k + 1], w[3 * k + 2]});
-        kv1 = R4{(R)wg.x, (R)wg.y, (R)wg.z, kv1.w};
+        if constexpr (F::voxel) {
+            // the voxel form keeps the angular velocity in FP32 and reads it back with an
+            // FP32 rotation: the upload rotates in FP32 too (GB300's FP64 rate is low)
+            float m[9];
+            quat_mat<float>(q4.x, q4.y, q4.z, q4.w, m);
+            const V3<float> wg =
+                mat_vec<float>(m, V3<float>{(float)w[3 * k], (float)w[3 * k + 1], (float)w[3 * k + 2]});
+            kv1 = R4{wg.x, wg.y, wg.z, kv1.w};
+        } else {
+            double m[9];
+            quat_mat<double>((double)q4.x, (double)q4.y, (double)q4.z, (double)q4.w, m);
+            V3<double> wg = mat_vec<double>(m, V3<double>{w[3 * k], w[3 * k + 1], w[3 * k + 2]});
+            kv1 = R4{(R)wg.x, (R)wg.y, (R)wg.z, kv1.w};
+        }
     }
     if (v || bounds == 1) d.st.kv[sp][2 * o] = kv0;
     if (w || bounds == 1) d.st.kv[sp][2 * o + 1] = kv1;
