@@ -1085,3 +1085,41 @@ def test_voxel_fp32_mesh_facets_stay_close_to_fp64():
     assert np.max(np.abs(x - ow.x)) < 1e-6
     c = w.contacts()
     assert np.sum(c["j"] <= -7) > 10
+
+
+def test_large_state_upload_in_pieces_is_checked_whole():
+    # from 2^20 owners the upload is copied in four pieces, each checked for non-finite
+    # values as it lands: a NaN in the last piece rejects the whole upload with nothing
+    # applied; without it every piece lands at its place (FP64 positions, orientations and
+    # velocities come back exactly); a ragged range overwrites only itself
+    s = W.dense_lattice(n=1_100_000, seed=5, vel_sigma=0.3)
+    w = dem.World.from_scene(s, precision="fp64", schedule="velocity_bound")
+    try:
+        w.step(2)
+        x, q, v, wb = w.owner_state()
+        rng = np.random.default_rng(0)
+        x2 = x + rng.uniform(-1e-7, 1e-7, size=x.shape)
+        v2 = v + 0.01
+        w2 = 0.5 * wb
+        bad = v2.copy()
+        bad[-3, 1] = np.nan
+        with pytest.raises(dem.DemError) as ei:
+            w.set_owner_state(0, xyz=x2, quat=q, vel=bad, omega=w2)
+        assert ei.value.status == dem.ERR_ARG
+        for a, b in zip(w.owner_state(), (x, q, v, wb)):
+            assert np.array_equal(a, b)
+        w.set_owner_state(0, xyz=x2, quat=q, vel=v2, omega=w2)
+        xa, qa, va, wa = w.owner_state()
+        assert np.array_equal(xa, x2) and np.array_equal(qa, q) and np.array_equal(va, v2)
+        np.testing.assert_allclose(wa, w2, rtol=1e-12, atol=1e-9 * float(np.abs(w2).max()))
+        f, m = 33_333, 1_050_000                    # a ragged range, in four pieces too
+        w.set_owner_state(f, xyz=x[f:f + m], vel=v[f:f + m])
+        xb, _, vb, _ = w.owner_state()
+        ex, ev = x2.copy(), v2.copy()
+        ex[f:f + m] = x[f:f + m]
+        ev[f:f + m] = v[f:f + m]
+        assert np.array_equal(xb, ex) and np.array_equal(vb, ev)
+        w.step(2)                                   # and it steps on from there
+        assert np.all(np.isfinite(w.owner_state()[0]))
+    finally:
+        w.close()
