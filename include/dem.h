@@ -120,6 +120,10 @@ typedef struct {
                                       inertia is c m R^2 for one c) instead of reading them */
     int32_t counting_sort;         /* 1: detection orders spheres by cell with the counting
                                       sort, 0: with the radix sort                         */
+    double ms_contact_eval;        /* two-pass contact step: profiled GPU time of its
+                                      evaluation pass (within ms_force, which spans both
+                                      passes)                                              */
+    int64_t n_contact_eval;        /* profiled launches of it                              */
 } dem_stats;
 
 typedef struct {

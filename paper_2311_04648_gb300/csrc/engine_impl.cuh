@@ -956,6 +956,8 @@ public:
         o->n_detect = prof_n_[P_DETECT];
         o->ms_integrate = prof_ms_[P_INTEG];
         o->n_integrate = prof_n_[P_INTEG];
+        o->ms_contact_eval = prof_ms_[P_EVAL];
+        o->n_contact_eval = prof_n_[P_EVAL];
         o->ms_total = ms_total_;
         o->last_cycle = last_cycle_;
         o->schedule_samples = (int64_t)(ds_y_.size() / MLP_OUT);
@@ -2234,7 +2236,10 @@ private:
             else k_contact<F, false, MODE_STEP, 0, false, FORCE_MODEL_BUILTIN, true><<<g, b, 0, sf_>>>(d_, eF, eT);
         } else if (MODE == MODE_STEP && screen()) {
             k_contact_screen<F><<<(unsigned)screen_per_sm() * (unsigned)n_sm_, SCREEN_BLOCK, 0, sf_>>>(d_);
+            Mark me;                         // the evaluation pass, within the contact phase's mark
+            mark_begin(P_EVAL, sf_, me);
             k_contact_eval<F><<<(unsigned)eval_per_sm(b) * (unsigned)n_sm_, b, 0, sf_>>>(d_);
+            mark_end(sf_, me);
         } else {
             if (lean) k_contact<F, false, MODE_STEP, 1><<<g, b, 0, sf_>>>(d_, eF, eT);
             else k_contact<F, false, MODE><<<g, b, 0, sf_>>>(d_, eF, eT);
@@ -2466,12 +2471,12 @@ private:
     std::vector<int> win_valid_;
     std::vector<float> ds_x_, ds_y_;
     // profiling: event pairs recorded on the stream of the bracketed work
-    enum { P_FORCE = 0, P_DETECT = 1, P_HASH = 2, P_LINK = 3, P_INTEG = 4 };
+    enum { P_FORCE = 0, P_DETECT = 1, P_HASH = 2, P_LINK = 3, P_INTEG = 4, P_EVAL = 5, P_KINDS = 6 };
     bool prof_ = false;
     struct Mark { cudaEvent_t a, b; int kind; };
     std::vector<Mark> marks_, pool_;
-    double prof_ms_[5] = {0, 0, 0, 0, 0};
-    int64_t prof_n_[5] = {0, 0, 0, 0, 0};
+    double prof_ms_[P_KINDS] = {};
+    int64_t prof_n_[P_KINDS] = {};
 
     Mark take()
     {

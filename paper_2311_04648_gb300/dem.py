@@ -52,7 +52,7 @@ class Stats(C.Structure):
                 ("last_cycle", C.c_int64), ("schedule_samples", C.c_int64), ("ms_integrate", C.c_double),
                 ("n_integrate", C.c_int64), ("spheres_with_entries", C.c_int64),
                 ("pair_steps", C.c_int64), ("busy_steps", C.c_int64), ("derived_constants", C.c_int32),
-                ("counting_sort", C.c_int32)]
+                ("counting_sort", C.c_int32), ("ms_contact_eval", C.c_double), ("n_contact_eval", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -158,3 +158,19 @@ def test_bench_line_carries_the_contract_keys(bench, monkeypatch, capsys):
     assert line["e2e"]["h2d_bytes_per_step"] == 416_000_000
     assert line["config"]["listed_pairs_per_sphere"] == pytest.approx(0.25)
     assert "detect" in r["kernels"]
+
+
+def test_two_pass_contact_phase_competes_by_its_longer_pass(bench):
+    # the contact phase of the two-pass step spans two kernels: the dominant kernel is the
+    # single kernel with the largest time, so a 0.146 ms phase of 0.096 + 0.050 ms passes
+    # loses to a 0.133 ms integration; the phase keeps its bytes and time, with both passes
+    prof = dict(_prof(100, contact_ms=0.146, integrate_ms=0.133), eval_ms=0.050, n_eval=100)
+    r = bench.roofline("voxel_fp32", 4_000_000, prof, 6686.5, "measured", tuning={"contact_screen": 1})
+    assert r["kernel"].startswith("k_integrate") and r["contact_screen"]
+    c = r["kernels"]["contact"]
+    assert c["ms"] == 0.146 and c["passes"]["k_contact_eval_ms"] == 0.050
+    assert abs(c["passes"]["k_contact_screen_ms"] - 0.096) < 1e-12
+    # without the evaluation pass's time (one contact kernel) the phase competes whole
+    r1 = bench.roofline("voxel_fp32", 4_000_000, _prof(100, contact_ms=0.146, integrate_ms=0.133), 6686.5,
+                        "measured")
+    assert r1["kernel"].startswith("k_contact") and "passes" not in r1["kernels"]["contact"]
