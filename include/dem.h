@@ -327,11 +327,21 @@ dem_status dem_get_stream(dem_world *w, void **stream);
 /* ---------------------------------------------------------------- read back / set state */
 
 /* Owner state for ids [first, first + n); any output may be NULL.  xyz[3n], quat[4n],
- * vel[3n], omega[3n] (body frame).  Tracker Pos / Vel / AngVel in the paper. */
+ * vel[3n], omega[3n] (body frame).  Tracker Pos / Vel / AngVel in the paper.  Outputs in
+ * pinned (page-locked, mapped) host memory are written by the device directly across the
+ * host link; any other memory through device scratch and a copy.  Returns when the
+ * outputs hold the values (the world's streams are synchronised). */
 dem_status dem_get_owner_state(dem_world *w, int64_t first, int64_t n, double *xyz, double *quat,
                                double *vel, double *omega);
 /* Overwrite owner state (tracker SetPos etc.); NULL inputs keep the current value.
- * Forces a contact-list rebuild before the next step (history is carried over). */
+ * Inputs are FP64 in the layouts of dem_get_owner_state (omega in the body frame).  A
+ * non-finite position, velocity or angular velocity rejects the whole call with
+ * DEM_ERR_ARG before anything is applied.  Worlds of single spheres on a delayed schedule keep the contact
+ * list in use: each owner's displacement by the call is added to its audit bounds, and
+ * the next step rebuilds the list (history carried over) only if the largest bound then
+ * exceeds the margin.  Clump worlds and the every-step schedule rebuild the list before
+ * the next step after any change of positions or orientations.  Inputs are read before
+ * the call returns. */
 dem_status dem_set_owner_state(dem_world *w, int64_t first, int64_t n, const double *xyz,
                                const double *quat, const double *vel, const double *omega);
 /* Sphere centres (world frame) and radii for sphere ids [first, first + n). */
